@@ -1,0 +1,60 @@
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a GB300 (sm_103a) GPU and the built CUDA library")
+    config.addinivalue_line("markers", "slow: long CPU run, only with NL_SLOW=1")
+
+
+def pytest_collection_modifyitems(config, items):
+    if os.environ.get("NL_SLOW") == "1":
+        return
+    skip = pytest.mark.skip(reason="slow oracle run; set NL_SLOW=1")
+    for it in items:
+        if "slow" in it.keywords:
+            it.add_marker(skip)
+
+
+def load_table(name):
+    """Parse a residual-history fixture: dict column -> list (None where blank)."""
+    cols = ["F64", "F32", "F16", "IR32-16", "IR-GM"]
+    out = {c: [] for c in cols}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            parts = line.split()
+            for c, v in zip(cols, parts[1:]):
+                out[c].append(None if v == "-" else float(v))
+    for c in cols:
+        while out[c] and out[c][-1] is None:
+            out[c].pop()
+    return out
+
+
+@pytest.fixture(scope="session")
+def table2():
+    return load_table("table2_c099.txt")
+
+
+@pytest.fixture(scope="session")
+def table3():
+    return load_table("table3_c09999.txt")
+
+
+def agrees_4digits(computed, printed):
+    """True when `computed` prints as `printed` to the paper's 4 significant
+    digits (half a unit in the last printed place, plus a hair for ties)."""
+    e = np.floor(np.log10(abs(printed)))
+    return abs(computed - printed) <= 0.5e-3 * 10 ** e * 1.0001

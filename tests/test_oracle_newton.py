@@ -1,0 +1,168 @@
+"""Pins for the oracle's problem (Section 3, eq. (3.2)) and Newton drivers
+(Algorithm 1.1 [newton], Algorithm 2.1 [newton3p]).
+
+What fixes the answers independently of the oracle:
+  * c = 0: F(ones) = 0 exactly, so Newton takes no step (eq. (3.2)).
+  * N = 1: eq. (3.2) reduces to x (1 - c x / 4) = 1, whose smaller root is
+    x = 2 (1 - sqrt(1 - c)) / c.
+  * The discrete moment identity: multiplying eq. (3.2) by x_i and summing
+    with weight c/(2N), the symmetric double sum halves, so
+    m = c/(2N) sum x_i satisfies m - m^2/2 = c/2, i.e. m = 1 - sqrt(1 - c)
+    exactly for the discrete system (the physical root).
+  * The analytic Jacobian must equal central finite differences of F.
+  * The paper's printed residual histories (Tables 2 and 3).  The history is
+    mesh independent, so N = 1024 reproduces the F64 columns printed for
+    N = 4096 to every digit.
+  * Quadratic convergence for c well below 1 (eq. (1.5) with small errors).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from tests.conftest import agrees_4digits
+
+
+def test_c_zero_is_exact_solution():
+    for N in (1, 7, 64):
+        x = np.ones(N)
+        assert np.all(O.F(N, 0.0, x) == 0.0)
+        xs, r = O.newton(N, 0.0, "FP64LU")
+        assert r["newton_iters"] == 0 and r["status"] == 0 and np.all(xs == 1.0)
+        xs, r = O.newton(N, 0.0, "IR16")
+        assert r["newton_iters"] == 0
+
+
+@pytest.mark.parametrize("c", [0.1, 0.5, 0.9, 0.99, 0.9999])
+def test_n1_closed_form(c):
+    xstar = 2.0 * (1.0 - math.sqrt(1.0 - c)) / c
+    assert abs(O.F(1, c, np.array([xstar]))[0]) <= 1e-14
+    for mode in ("FP64LU", "IR16", "GMRESIR16"):
+        x, r = O.newton(1, c, mode, tol=1e-13)
+        assert r["status"] == 0
+        assert abs(x[0] - xstar) <= 1e-12 * xstar
+
+
+def test_jacobian_matches_finite_differences():
+    g = np.random.default_rng(3)
+    for N, c in [(5, 0.7), (33, 0.99), (64, 0.5)]:
+        x = 1.0 + g.uniform(0.0, 1.0, N)
+        J = O.jacobian(N, c, x)
+        h = 1e-6
+        Jfd = np.empty((N, N))
+        for j in range(N):
+            e = np.zeros(N)
+            e[j] = h
+            Jfd[:, j] = (O.F(N, c, x + e) - O.F(N, c, x - e)) / (2 * h)
+        assert np.max(np.abs(J - Jfd)) <= 1e-7 * max(1.0, np.max(np.abs(J)))
+
+
+def test_jacobian_at_c_zero_is_identity():
+    assert np.array_equal(O.jacobian(9, 0.0, np.ones(9)), np.eye(9))
+
+
+@pytest.mark.parametrize("N", [64, 512])
+@pytest.mark.parametrize("c", [0.5, 0.9, 0.99, 0.9999])
+def test_moment_identity(N, c):
+    x, r = O.newton(N, c, "FP64LU", tol=1e-13)
+    assert r["status"] == 0
+    m = c / (2 * N) * x.sum()
+    assert abs(m - (1 - math.sqrt(1 - c))) <= 1e-12 / math.sqrt(1 - c)
+    # the other positive root m = 1 + sqrt(1-c) would be the unphysical branch
+    assert m < 1.0
+
+
+@pytest.mark.parametrize("c,expected", [(0.5, 3), (0.9, 4), (0.99, 6), (0.9999, 9), (0.999999, 11)])
+def test_fp64_newton_counts_to_1e10(c, expected):
+    """Steps to ||F||/||F0|| <= 1e-10 (one more than the paper's tables show,
+    whose stopping tolerance was looser)."""
+    _, r = O.newton(512, c, "FP64LU", tol=1e-10)
+    assert r["status"] == 0 and r["newton_iters"] == expected
+
+
+def test_quadratic_convergence():
+    for c in (0.5, 0.9):
+        xs, _ = O.newton(256, c, "FP64LU", tol=1e-15)
+        x = np.ones(256)
+        errs = []
+        for k in range(4):
+            errs.append(np.max(np.abs(x - xs)))
+            F = O.F(256, c, x)
+            J = O.jacobian(256, c, x)
+            x = x - np.linalg.solve(J, F)
+        ratios = [errs[k + 1] / errs[k] ** 2 for k in range(3) if errs[k + 1] > 1e-14]
+        assert ratios and max(ratios) < 5.0
+
+
+def _check_column(hist, printed, exact_upto, last_rel=None):
+    for n in range(1, exact_upto + 1):
+        assert agrees_4digits(hist[n], printed[n]), (n, hist[n], printed[n])
+    if last_rel is not None:
+        n = len(printed) - 1
+        assert abs(hist[n] - printed[n]) <= last_rel * printed[n], (hist[n], printed[n])
+
+
+def test_table2_f64_column_n1024(table2):
+    _, r = O.newton(1024, 0.99, "FP64LU", paper=True, tol=1e-9)
+    p = table2["F64"]
+    assert r["newton_iters"] == len(p) - 1
+    _check_column(r["hist"], p, len(p) - 1)
+
+
+def test_table3_f64_column_n1024(table3):
+    _, r = O.newton(1024, 0.9999, "FP64LU", paper=True, tol=1e-9)
+    p = table3["F64"]
+    assert r["newton_iters"] == len(p) - 1
+    _check_column(r["hist"], p, len(p) - 1)
+
+
+def test_table2_three_precision_columns_n1024(table2):
+    """IR 32-16 and IR-GM with eta_J = 1e-6 (Section 3.1): the same number of
+    Newton steps as F64 (the count-equality claim after eq. (2.13)), steps
+    1-4 to the printed digits, the last step within 2%."""
+    for mode, col in (("IR16", "IR32-16"), ("GMRESIR16", "IR-GM")):
+        _, r = O.newton(1024, 0.99, mode, paper=True, tol=1e-9)
+        p = table2[col]
+        assert r["newton_iters"] == len(p) - 1
+        _check_column(r["hist"], p, 4, last_rel=0.02)
+        assert not any(r["lin_failed"])
+
+
+def test_table3_gmres_ir_column_n1024(table3):
+    _, r = O.newton(1024, 0.9999, "GMRESIR16", paper=True, tol=1e-9)
+    p = table3["IR-GM"]
+    assert r["newton_iters"] == len(p) - 1
+    _check_column(r["hist"], p, 7, last_rel=0.02)
+
+
+def test_count_equality_three_precision_vs_fp64():
+    """Analysis after eq. (2.13): with eta_J = O(u_s) the three-precision
+    iteration takes as many Newton steps as Newton with an FP64 Jacobian,
+    except for very ill-conditioned problems."""
+    for c in (0.5, 0.9, 0.99):
+        _, r64 = O.newton(512, c, "FP64LU", tol=1e-10)
+        for mode in ("IR16", "GMRESIR16"):
+            _, r = O.newton(512, c, mode, paper=True, tol=1e-10)
+            assert r["newton_iters"] == r64["newton_iters"], (c, mode)
+
+
+def test_fp16_two_precision_newton_converges_slowly():
+    """Section 1.3: storing and factoring J in half precision degrades the
+    nonlinear iteration for ill-conditioned problems (F16 column)."""
+    _, r16 = O.newton(1024, 0.99, "F16", paper=True, tol=1e-9)
+    _, r64 = O.newton(1024, 0.99, "FP64LU", paper=True, tol=1e-9)
+    h = r16["hist"]
+    assert r16["newton_iters"] >= 2 * r64["newton_iters"]
+    # linear, not quadratic: the contraction factor stays bounded away from 0
+    assert all(h[k + 1] / h[k] > 0.02 for k in range(2, len(h) - 1))
+
+
+@pytest.mark.slow
+def test_tables_full_size_n4096(table2, table3):
+    """Full-size reproduction of the paper's Tables 2 and 3 (minutes)."""
+    for c, tab in ((0.99, table2), (0.9999, table3)):
+        _, r = O.newton(4096, c, "FP64LU", paper=True, tol=1e-9)
+        _check_column(r["hist"], tab["F64"], len(tab["F64"]) - 1)
+        _, r = O.newton(4096, c, "GMRESIR16", paper=True, tol=1e-9)
+        _check_column(r["hist"], tab["IR-GM"], len(tab["IR-GM"]) - 2, last_rel=0.02)
