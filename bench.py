@@ -1,0 +1,275 @@
+"""Benchmark: three-precision Newton solves on GB300 versus FP64-LU Newton.
+
+Workload (one "step"): the paper's conditioning sweep of the H-equation
+(Section 3, eq. (3.2)) at N = 4096, c in {.5, .9, .99, .9999, .999999},
+x0 = ones, each solved to ||F||/||F0|| <= 1e-10 with GMRES-IR16 (restart 30,
+inner tolerance 1e-4, eta = 1e-4): five Newton solves per step.
+
+value     : solves/s with x0/x in HBM (nl_solve_device), CUDA events.
+e2e       : solves/s through nl_solve with host buffers (copies included).
+baselines : the same sweep with FP64-LU Newton and with IR16 on the same GPU,
+            and the CPU oracle on the host cores (a bounded sample).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEP = (0.5, 0.9, 0.99, 0.9999, 0.999999)
+N_BENCH = 4096
+TOL = 1e-10
+WORKLOAD = ("H-equation (eq. 3.2) N=4096, c in {.5,.9,.99,.9999,.999999}, x0=ones, "
+            "to ||F||/||F0||<=1e-10, GMRES-IR16 restart 30 inner tol 1e-4, eta 1e-4")
+METRIC = "Newton solves/s to ||F||/||F0||<=1e-10 (N=4096 conditioning sweep, three-precision GMRES-IR16)"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), float(d.get("bf16_tflops_sustained", d["bf16_tflops"])), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("NL_BENCH_GLOO") != "1" else "gloo")
+    return ws, rank, local
+
+
+def barrier_max(value, ws):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.barrier()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample(n_newton_steps_per_step):
+    """The oracle as it stands on the host cores: one three-precision Newton
+    step (Jacobian, binary16-storage LU, GMRES-IR) at N=4096, c=.99, scaled to
+    solves/s with the GPU's Newton step count for the sweep."""
+    from oracle import oracle as O
+    O.build()
+    t = time.time()
+    O.newton(N_BENCH, 0.99, "GMRESIR16", tol=TOL, newton_maxit=1)
+    dt = time.time() - t
+    per_solve = dt * n_newton_steps_per_step / len(SWEEP)
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"one oracle Newton step (J, LU16 binary16-storage/binary32 arithmetic, GMRES-IR) at N=4096 "
+                       f"c=0.99 took {dt:.1f}s; scaled by the sweep's {n_newton_steps_per_step} Newton steps per "
+                       f"{len(SWEEP)} solves")}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    # per step: one oracle Newton step (bounded sample), extrapolated to solves/s
+    from oracle import oracle as O
+    O.build()
+    steps_per_sweep = 3 + 4 + 6 + 9 + 11  # FP64 Newton counts of the sweep to 1e-10
+    for _ in range(args.warmup):
+        O.newton(512, 0.99, "GMRESIR16", tol=TOL, newton_maxit=1)
+    times = []
+    for _ in range(args.steps):
+        t = time.time()
+        O.newton(N_BENCH, 0.99, "GMRESIR16", tol=TOL, newton_maxit=1)
+        times.append(time.time() - t)
+    dt = sum(times) / len(times)
+    value = len(SWEEP) / (dt * steps_per_sweep)
+    sample = (f"each step: one oracle Newton step at N=4096 c=0.99 (GMRES-IR16), {dt:.1f}s, extrapolated by "
+              f"{steps_per_sweep} Newton steps per 5-solve sweep")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * steps_per_sweep * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16/f32/f64 (emulated)",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "N": N_BENCH, "c": list(SWEEP)},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2307_16051_gb300 import nl
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbm_peak, tc_peak, tc_sust, peak_kind = peaks()
+    solvers = {c: nl.Solver(N_BENCH, c) for c in SWEEP}
+    xdev = {c: torch.empty(N_BENCH, device=dev, dtype=torch.float64) for c in SWEEP}
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
+
+    def step(mode, device_api=True):
+        st = {}
+        for c in SWEEP:
+            if device_api:
+                solvers[c].solve_device(xdev[c], tol=TOL, mode=mode)
+            else:
+                solvers[c].solve(tol=TOL, mode=mode)
+            st[c] = solvers[c].stats()
+        return st
+
+    def timed(mode, k, device_api=True):
+        ms = []
+        stats = None
+        for _ in range(k):
+            flush.fill_(1.0)  # L2 flush between steps (256 MiB write)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            stats = step(mode, device_api)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, stats
+
+    for _ in range(max(3, args.warmup)):
+        step("GMRESIR16")
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        ms, stats = timed("GMRESIR16", args.steps)
+    torch.cuda.synchronize()
+    ms_step = barrier_max(sum(ms) / len(ms), ws)
+    solves = len(SWEEP) * ws
+    value = solves / (ms_step / 1e3)
+    # end to end through the host-buffer API
+    ms_e2e, _ = timed("GMRESIR16", max(1, args.steps), device_api=False)
+    ms_e2e_step = barrier_max(sum(ms_e2e) / len(ms_e2e), ws)
+    e2e = {"value": solves / (ms_e2e_step / 1e3), "unit": "solves/s", "h2d_bytes_per_step": 0,
+           "d2h_bytes_per_step": len(SWEEP) * N_BENCH * 8}
+    # per-phase device times of the GMRES-IR16 sweep
+    lu_ms = sum(s["t_lu_ms"] for s in stats.values())
+    n_lu = sum(s["newton_iters"] for s in stats.values())
+    launches = sum(s["gpu_launches"] for s in stats.values())
+    lu_flops = 2.0 * N_BENCH ** 3 / 3.0
+    achieved = lu_flops / (lu_ms / n_lu / 1e3) / 1e12 if n_lu else 0.0
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
+                "frac": achieved / tc_peak, "traffic": None,
+                "kernel": "binary16 LU (whole factorisation, all its kernels)",
+                "peak_kind": f"{peak_kind} bf16 dense (fp16 same rate)"}
+    per_c = {str(c): {"newton": s["newton_iters"], "lin_iters": s["lin_iters"], "ms": s["t_total_ms"],
+                      "final_rel_res": s["hist"][-1], "lu_ms": s["t_lu_ms"], "lin_ms": s["t_lin_ms"]}
+             for c, s in stats.items()}
+    extra = {}
+    if not args.no_fp64:
+        ms64, st64 = timed("FP64LU", 1)
+        extra["fp64lu"] = {"solves_per_s": len(SWEEP) / (sum(ms64) / 1e3), "ms_per_sweep": sum(ms64),
+                           "per_c_ms": {str(c): s["t_total_ms"] for c, s in st64.items()},
+                           "newton": {str(c): s["newton_iters"] for c, s in st64.items()}}
+        extra["speedup_vs_fp64lu"] = extra["fp64lu"]["ms_per_sweep"] / ms_step
+    msir, stir = timed("IR16", 1)
+    extra["ir16"] = {"ms_per_sweep": sum(msir), "per_c": {str(c): {"status": nl.STATUS_NAMES[s["status"]],
+                                                                     "newton": s["newton_iters"], "ms": s["t_total_ms"]}
+                                                            for c, s in stir.items()}}
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16/f32/f64", "data": "synthetic (the paper's H-equation, x0=ones)",
+            "config": {"workload": WORKLOAD, "N": N_BENCH, "c": list(SWEEP), "mode": "GMRESIR16",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "per_c": per_c, **extra}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_sample(n_lu)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in solvers.values():
+        s.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

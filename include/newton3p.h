@@ -1,0 +1,215 @@
+/*
+ * newton3p.h — C ABI of the GB300 (sm_103a) three-precision Newton solver.
+ *
+ * Method: C. T. Kelley, "Newton's Method in Three Precisions" (arXiv
+ * 2307.16051).  The nonlinear residual F is evaluated in double precision,
+ * the Jacobian is stored in single precision (J32), a half-precision copy
+ * J_h = I_s^h(J32) is factored with partial pivoting, and the Newton step is
+ * computed by iterative refinement (IR) or GMRES-IR with those factors
+ * (Algorithm 2.1 [newton3p], Section 2.2).  The test problem is the
+ * composite-midpoint Chandrasekhar H-equation of Section 3, eq. (3.2):
+ *     F(x)_i = x_i - (1 - c/(2N) sum_j x_j mu_i/(mu_j + mu_i))^{-1},
+ *     mu_i = (i - 1/2)/N.
+ *
+ * Conventions for every function:
+ *  - The return value is an nl_status.  On NL_EINVAL nothing is written.
+ *    nl_last_error() gives a human-readable message for the calling thread.
+ *  - "host" pointers are ordinary CPU memory owned by the caller; "device"
+ *    pointers are CUDA global memory on the current device, owned by the
+ *    caller unless stated otherwise.
+ *  - Matrices are row-major with a leading dimension `ld` (elements between
+ *    the starts of consecutive rows), ld >= N.  Half-precision matrices are
+ *    IEEE binary16 (`uint16_t` bit patterns, CUDA __half in memory).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Kernel
+ *    entry points are asynchronous unless they return host data.
+ *  - There is no CPU fallback: without a CUDA device every call that needs
+ *    one returns NL_ECUDA.
+ */
+#ifndef NEWTON3P_H
+#define NEWTON3P_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NL_OK = 0,
+    NL_EINVAL = 1,     /* bad argument (N < 1, c outside [0,1), null pointer, ...) */
+    NL_ENOMEM = 2,     /* device allocation failed */
+    NL_ENOTCONV = 3,   /* Newton cap reached; the best iterate is returned */
+    NL_ESINGULAR = 4,  /* exactly zero pivot in a factorisation */
+    NL_ENUMERIC = 5,   /* NaN/Inf in F, or binary16 overflow of the Jacobian */
+    NL_ETIMEOUT = 6,   /* a device-side bounded wait gave up (no hang, context intact) */
+    NL_ECUDA = 7       /* CUDA runtime error, or no device / library */
+} nl_status;
+
+/* Linear solver for the Newton step.
+ *  NL_FP64LU:    J in double, LU in double, one direct solve (Algorithm 1.1,
+ *                column F64 of Tables 2-3): the on-GPU baseline.
+ *  NL_IR16:      J32 + half-precision LU + IR (Algorithm IR, Section 2.2).
+ *  NL_GMRESIR16: J32 + half-precision LU as left preconditioner of GMRES,
+ *                wrapped in IR (GMRES-IR, Section 2.2). */
+typedef enum { NL_FP64LU = 0, NL_IR16 = 1, NL_GMRESIR16 = 2 } nl_mode;
+
+/* Solver parameters (nl_config_default fills the defaults in brackets). */
+typedef struct {
+    double eta_j;        /* [1e-4] IR/GMRES-IR stops at ||J32 u - b|| <= eta_j ||b||, eq. (2.3) */
+    int ir_maxit;        /* [20]  cap on IR (or GMRES-IR outer) corrections per Newton step */
+    int gmres_restart;   /* [30]  GMRES restart length m */
+    double gmres_tol;    /* [1e-4] inner GMRES tolerance, relative to the initial preconditioned residual */
+    int gmres_maxcycles; /* [10]  GMRES restart cycles per outer correction */
+    int newton_maxit;    /* [30]  cap on Newton steps */
+    double tau_a;        /* [0]   absolute tolerance tau_a of Algorithm 1.1 */
+    int lu_nb;           /* [0 = auto (128)] outer block of the LU (multiple of 16, <= 128); also its
+                            binary16 rounding period */
+    int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update */
+    int reserved[8];
+} nl_config;
+
+#define NL_MAX_HIST 128
+
+/* Statistics of the last nl_solve on a handle (all host values). */
+typedef struct {
+    int status;                       /* nl_status of the solve */
+    int mode;                         /* nl_mode */
+    int newton_iters;                 /* Newton steps taken */
+    int lu_nb;                        /* LU outer block used */
+    double fnorm0;                    /* ||F(x0)||_2 */
+    double fnorm;                     /* ||F(x_final)||_2 */
+    double hist[NL_MAX_HIST];         /* ||F(x_n)|| / ||F(x_0)||, n = 0..newton_iters */
+    int lin_iters[NL_MAX_HIST];       /* per Newton step: IR corrections or GMRES Arnoldi steps */
+    int lin_outer[NL_MAX_HIST];       /* per Newton step: IR / GMRES-IR outer corrections */
+    int lin_failed[NL_MAX_HIST];      /* per Newton step: IR failure rule fired (Section 3.1) */
+    double lin_relres[NL_MAX_HIST];   /* per Newton step: final ||J32 u - b|| / ||b|| */
+    double t_total_ms;                /* wall time of nl_solve (host clock) */
+    double t_f_ms, t_jac_ms, t_lu_ms, t_lin_ms; /* device time per phase (CUDA events), summed */
+    int gpu_launches;                 /* kernels launched by the solve */
+    int reserved[15];
+} nl_stats_t;
+
+typedef struct nl_solver nl_solver;
+
+/* Fill *cfg with the defaults.  Returns NL_EINVAL on NULL. */
+nl_status nl_config_default(nl_config* cfg);
+
+/* Create a solver for the H-equation of size N and albedo c (Section 3).
+ * Allocates all device state for all three modes except the double Jacobian
+ * (allocated on the first NL_FP64LU solve).  N >= 1, 0 <= c < 1 (J(x*) is
+ * singular at c = 1).  cfg may be NULL (defaults).  *out receives the handle,
+ * owned by the caller until nl_destroy. */
+nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out);
+
+/* Use `stream` (cudaStream_t) for all later work of this handle. */
+nl_status nl_set_stream(nl_solver* s, void* stream);
+
+/* Newton solve from x0 (host, N doubles; NULL = ones) to
+ * ||F(x)||_2 <= tol ||F(x0)||_2 + tau_a (Algorithm 1.1 / 2.1 with tau_r = tol).
+ * The step uses the scaled right-hand side of eqs. (2.17)-(2.18): the linear
+ * solver works on b = -F/||F|| and s = ||F|| u.  x_out (host, N doubles) gets
+ * the final iterate (the last one on NL_ENOTCONV).  Blocks until done. */
+nl_status nl_solve(nl_solver* s, const double* x0, double tol, nl_mode mode, double* x_out);
+
+/* As nl_solve with x0 and x_out in device memory (x0 may be NULL = ones):
+ * no host-device copy of vectors, only scalars are read back. */
+nl_status nl_solve_device(nl_solver* s, const double* x0_dev, double tol, nl_mode mode, double* x_out_dev);
+
+/* Copy the statistics of the last solve into *out (caller-owned). */
+nl_status nl_stats(const nl_solver* s, nl_stats_t* out);
+
+/* Bytes of device memory the handle holds. */
+int64_t nl_device_bytes(const nl_solver* s);
+
+/* Release the handle and its device memory.  NULL is a no-op. */
+void nl_destroy(nl_solver* s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* nl_last_error(void);
+
+/* Library version string. */
+const char* nl_version(void);
+
+/* ----------------------------------------------------------------------- */
+/* Kernel-level entry points (device pointers).  These expose each step of */
+/* the hot path on its own, for tests and for callers with their own loop.  */
+/* ----------------------------------------------------------------------- */
+
+/* Residual of eq. (3.2) with the fused Newton update (Algorithm 1.1, last two
+ * lines):  x_out = x + fnorm_scale * u  (u NULL: x_out = x), then
+ *   r_i = (1 - c/(2N) sum_j x_out_j mu_i/(mu_j+mu_i))^{-1},  F_i = x_out_i - r_i,
+ * all in double, and *fnorm_dev = ||F||_2.  u is single precision (the step
+ * from the linear solver before unscaling, eq. (2.18)) or double when
+ * u_is_double != 0.  x, x_out, F, r: N doubles; x_out must not alias x.
+ * fnorm_dev: one device double. */
+nl_status nl_k_residual(int64_t N, double c, const double* x, const void* u, int u_is_double,
+                        double fnorm_scale, double* x_out, double* F, double* r, double* fnorm_dev,
+                        void* stream);
+
+/* Analytic Jacobian of eq. (3.2) at x, given r from nl_k_residual:
+ *   J_ij = delta_ij - (c/(2N)) r_i^2 mu_i/(mu_i+mu_j)   (Sections 1.1, 3),
+ * written in one pass as J32 (single, computed in single from the double row
+ * factor) and J16 = I_s^h(J32) (binary16, round to nearest even; Section 2).
+ * Either output may be NULL.  Padding columns N..ld-1 are set to 0. */
+nl_status nl_k_jacobian(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16,
+                        int64_t ld16, void* stream);
+
+/* The same Jacobian in double (for NL_FP64LU). */
+nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int64_t ld, void* stream);
+
+/* Half-precision LU with partial pivoting of A16 (N x N binary16, in place):
+ * P A = L U with L unit lower (below the diagonal) and U upper, both binary16.
+ * Arithmetic model: binary32 arithmetic, binary16 storage, L and U entries
+ * rounded to binary16 as they are formed and the unfinished submatrix rounded
+ * to binary16 every nb elimination steps (nb = outer block; the paper's
+ * Section 2 says only that J_h is factored in half precision).
+ * ipiv (device, N int32): LAPACK-style 0-based interchanges.  *info_host: 0,
+ * or k+1 for the first exactly-zero pivot k.  nb: 0 = 128, else a multiple
+ * of 16 in [16, 128].  gemm: 0 auto, 1 SIMT, 2 tcgen05.  Allocates its
+ * workspace with cudaMallocAsync on `stream`.  Synchronises the stream. */
+nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int32_t* info_host,
+                  void* stream);
+
+/* Double-precision LU with partial pivoting (the F64 baseline), same layout
+ * and ipiv convention.  nb: 0 = 64, else a multiple of 16 in [16, 128].
+ * Synchronises the stream. */
+nl_status nl_lu64(int64_t N, double* A, int64_t ld, int32_t* ipiv, int nb, int32_t* info_host, void* stream);
+
+/* b <- U^{-1} L^{-1} P b with the binary16 factors of nl_lu16 promoted to
+ * single on the fly (eq. (2.16)), b single precision (device, N floats).
+ * Allocates its workspace with cudaMallocAsync.  Returns NL_ETIMEOUT if a
+ * bounded wait gave up. Synchronises the stream. */
+nl_status nl_lusolve16(int64_t N, const void* LU16, int64_t ld, const int32_t* ipiv, float* b, void* stream);
+
+/* b <- U^{-1} L^{-1} P b in double with the factors of nl_lu64. */
+nl_status nl_lusolve64(int64_t N, const double* LU, int64_t ld, const int32_t* ipiv, double* b, void* stream);
+
+/* r = b - A u in single precision (Algorithm IR, residual line), A N x N
+ * single row-major; *rnorm_dev = ||r||_2 (double, device). */
+nl_status nl_k_gemv_residual(int64_t N, const float* A, int64_t ld, const float* b, const float* u, float* r,
+                             double* rnorm_dev, void* stream);
+
+/* Trailing update of the half-precision LU:  C <- fl16(C - A B) with A M x K,
+ * B K x Nc, C M x Nc binary16 row-major (lda, ldb, ldc), products accumulated
+ * in single.  gemm: 1 SIMT (sequential fused multiply-adds over k),
+ * 2 tcgen05 tensor cores (K a multiple of 64, lda/ldb/ldc multiples of 8,
+ * pointers 16-byte aligned). */
+nl_status nl_k_gemm16_update(int64_t M, int64_t Nc, int64_t K, const void* A, int64_t lda, const void* B,
+                             int64_t ldb, void* C, int64_t ldc, int gemm, void* stream);
+
+/* IR / GMRES-IR for J32 u = b with given half-precision factors (Section 2.2):
+ * u0 = 0; success at ||b - J32 u|| <= eta ||b||; failure when the residual
+ * norm increases (the best iterate is returned, Section 3.1); at most maxit
+ * outer corrections.  solver: 0 = IR, 2 = GMRES-IR (restart m, inner tol
+ * gtol, gcycles cycles).  u: device, N floats (output).  stats_host (may be
+ * NULL): int[4] = {linear iterations, outer corrections, failed, converged}
+ * and relres_host (may be NULL): final relative residual.  Synchronises. */
+nl_status nl_linsolve16(int64_t N, const float* J32, int64_t ld32, const void* LU16, int64_t ld16,
+                        const int32_t* ipiv, const float* b, float* u, double eta, int maxit, int solver, int m,
+                        double gtol, int gcycles, int32_t* stats_host, double* relres_host, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NEWTON3P_H */

@@ -2,15 +2,7 @@
 Three Precisions", arXiv 2307.16051).
 
 The solver lives in a C-ABI CUDA library (``libnewton3p.so``, sources under
-``csrc/``); ``nl`` is its thin ctypes binding.  The library is loaded on first
-use and any failure to find it is an error: there is no CPU path.
+``csrc/``); ``paper_2307_16051_gb300.nl`` is its thin ctypes binding.  The
+library is loaded on first use and any failure to find it is an error: there
+is no CPU path.
 """
-
-__all__ = ["nl", "workloads"]
-
-
-def __getattr__(name):
-    if name == "nl":
-        from . import nl as _nl
-        return _nl
-    raise AttributeError(name)

@@ -1,0 +1,88 @@
+// common.cuh — shared device/host helpers for the sm_103a kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+namespace nl {
+
+// ---------------------------------------------------------------- host side --
+
+// Thread-local last-error text, surfaced by nl_last_error().
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+#define NL_CUDA_OK(expr)                                                                   \
+    do {                                                                                   \
+        cudaError_t _e = (expr);                                                           \
+        if (_e != cudaSuccess) {                                                           \
+            ::nl::set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(_e)); \
+            return NL_ECUDA;                                                               \
+        }                                                                                  \
+    } while (0)
+
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+int num_sms();
+
+// Device-side error word bits (solver status block).
+enum : unsigned {
+    ERR_TIMEOUT_TRSV = 1u << 0,  // a triangular-solve block gave up waiting on a predecessor
+    ERR_TIMEOUT_OTHER = 1u << 1,
+    ERR_NONFINITE = 1u << 2,
+};
+
+// Bounded spin limit for inter-CTA waits: about a second at the spin period.
+constexpr long long kSpinLimit = 1LL << 24;
+
+// -------------------------------------------------------------- device side --
+
+__device__ __forceinline__ float round_h(float v) { return __half2float(__float2half_rn(v)); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block-wide sum (fixed reduction tree).  `red` needs
+// blockDim.x/32 entries.  Result valid in every thread.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T* red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    T s = T(0);
+    for (int w = 0; w < nw; ++w) s += red[w];
+    return s;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* p, int v)
+{
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Element loads/stores for the two factor storage types.
+__device__ __forceinline__ float ld_elem(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ double ld_elem(const double* p) { return *p; }
+__device__ __forceinline__ void st_elem(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st_elem(double* p, double v) { *p = v; }
+
+}  // namespace nl

@@ -1,0 +1,285 @@
+// gemm_tc.cu — trailing update of the half-precision LU on the 5th-generation
+// tensor cores:  C <- fl16(C - A Bt^T), A = L21 (M x K), Bt = U12^T (Nc x K),
+// binary16 operands, binary32 accumulation in tensor memory (Section 2: the
+// factorisation of J_h in half precision; the update is its O(N^3) part).
+//
+// One CTA per 128 x 128 output tile, 128 threads:
+//   * thread 0 loads all K/64 operand slabs of the tile with TMA (128-byte
+//     swizzle, one mbarrier with a transaction count), then issues K/16
+//     tcgen05.mma (kind::f16, M=128, N=128, K=16) into a 128-column TMEM
+//     accumulator and commits them to a second mbarrier;
+//   * all four warps read their 32 TMEM lanes (tcgen05.ld 32x32b) and apply
+//     C = fl16(C - acc) in the epilogue.
+// K <= 256 (the LU's outer block), so the whole K extent is staged at once.
+// Each wait is bounded; on timeout the CTA records the error, waits (again
+// bounded) for its own copies, releases its tensor memory and returns.
+// No cluster multicast: every CTA loads its own tiles.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nl {
+
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 64;
+constexpr int kTcThreads = 128;
+constexpr long long kTcWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor for a K-major operand slab written by TMA
+// with 128-byte swizzle: 8-row x 128-byte swizzle atoms stacked every 1024 B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);      // start address
+    d |= (uint64_t)(16u >> 4) << 16;              // leading-dimension byte offset (unused for this layout)
+    d |= (uint64_t)(1024u >> 4) << 32;            // stride-dimension byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                       // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = binary16, D = binary32, both
+// operands K-major, M = 128, N = kTcBN.
+__host__ __device__ constexpr uint32_t tc_idesc()
+{
+    return (1u << 4)                        // D format: f32
+           | (0u << 7) | (0u << 10)         // A, B format: f16
+           | (0u << 15) | (0u << 16)        // A, B K-major
+           | ((uint32_t)(kTcBN >> 3) << 17)  // N / 8
+           | ((uint32_t)(kTcBM >> 4) << 24); // M / 16
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit)
+{
+    long long t0 = clock64();
+    uint32_t done = 0;
+    while (true) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmB, int M, int Nc,
+                                                        int K, __half* __restrict__ C, int64_t ldc,
+                                                        unsigned* __restrict__ err)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* basep = smem_raw + (base - raw);
+    const int KT = K / kTcBK;
+    const uint32_t a_sz = kTcBM * 128, b_sz = kTcBN * 128;  // bytes per 64-wide slab
+    const uint32_t sA = base, sB = base + KT * a_sz;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(basep + KT * (a_sz + b_sz));
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    const uint32_t bar_load = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
+    __shared__ int failed;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)kTcBN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_load));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_mma));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)KT * (a_sz + b_sz);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_load), "r"(bytes) : "memory");
+        for (int kt = 0; kt < KT; ++kt) {
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                    sA + kt * a_sz),
+                "l"(&tmA), "r"(kt * kTcBK), "r"(m0), "r"(bar_load)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+                    sB + kt * b_sz),
+                "l"(&tmB), "r"(kt * kTcBK), "r"(n0), "r"(bar_load)
+                : "memory");
+        }
+        if (!mbar_wait(bar_load, 0, kTcWaitCycles)) {
+            atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+            failed = 1;
+            mbar_wait(bar_load, 0, kTcWaitCycles);  // let copies in flight land
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t idesc = tc_idesc();
+            for (int kt = 0; kt < KT; ++kt) {
+#pragma unroll
+                for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                    uint64_t ad = sw128_desc(sA + kt * a_sz + kk * 32);
+                    uint64_t bd = sw128_desc(sB + kt * b_sz + kk * 32);
+                    uint32_t acc = (kt | kk) ? 1u : 0u;
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_mma)
+                         : "memory");
+        }
+    }
+    __syncthreads();
+    bool ok = !failed;
+    if (ok && !mbar_wait(bar_mma, 0, kTcWaitCycles)) {
+        atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+        mbar_wait(bar_mma, 0, kTcWaitCycles);  // let the MMAs in flight finish
+        ok = false;
+    }
+    ok = !__syncthreads_or(!ok);  // warp-uniform: the TMEM loads below are warp-collective
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        __half* Crow = C + (int64_t)min(row, M - 1) * ldc;
+        for (int c = 0; c < kTcBN; c += 32) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            const int col0 = n0 + c;
+            if (row < M) {
+                if (col0 + 32 <= Nc) {
+                    uint4* p = reinterpret_cast<uint4*>(Crow + col0);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint4 v = p[q];
+                        uint32_t wds[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            __half2 h2;
+                            memcpy(&h2, &wds[e], 4);
+                            float2 f = __half22float2(h2);
+                            f.x -= __uint_as_float(r[q * 8 + 2 * e]);
+                            f.y -= __uint_as_float(r[q * 8 + 2 * e + 1]);
+                            h2 = __floats2half2_rn(f.x, f.y);
+                            memcpy(&wds[e], &h2, 4);
+                        }
+                        p[q] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (col0 + e < Nc)
+                            Crow[col0 + e] = __float2half_rn(__half2float(Crow[col0 + e]) - __uint_as_float(r[e]));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)kTcBN));
+    }
+}
+
+// ------------------------------------------------------------------- host --
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static int g_tc_state = -1;  // -1 unknown, 0 unsupported, 1 supported
+static unsigned* g_tc_err = nullptr;
+
+bool tc_gemm_supported()
+{
+    if (g_tc_state >= 0) return g_tc_state == 1;
+    g_tc_state = 0;
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10) return false;
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return false;
+    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    if (cudaMalloc((void**)&g_tc_err, sizeof(unsigned)) != cudaSuccess) return false;
+    cudaMemset(g_tc_err, 0, sizeof(unsigned));
+    if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
+        return false;
+    g_tc_state = 1;
+    return true;
+}
+
+static bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                      uint32_t box_inner, uint32_t box_outer)
+{
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {ld_elems * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
+                           __half* C, int64_t ldc, cudaStream_t st)
+{
+    if (M <= 0 || Nc <= 0) return NL_OK;
+    if (!tc_gemm_supported()) {
+        set_error("tcgen05 GEMM: needs an sm_100-family device and the tensor-map driver entry point");
+        return NL_ECUDA;
+    }
+    if (K % kTcBK || K > 256 || (lda % 8) || (ldbt % 8) || (ldc % 8) || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) ||
+        ((uintptr_t)C & 15)) {
+        set_error("tcgen05 GEMM: K must be a multiple of 64 (<= 256), leading dimensions multiples of 8, "
+                  "pointers 16-byte aligned");
+        return NL_EINVAL;
+    }
+    CUtensorMap tmA, tmB;
+    if (!encode_2d(&tmA, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, kTcBK, kTcBM) ||
+        !encode_2d(&tmB, Bt, (uint64_t)K, (uint64_t)Nc, (uint64_t)ldbt, kTcBK, kTcBN)) {
+        set_error("tcgen05 GEMM: cuTensorMapEncodeTiled failed");
+        return NL_ECUDA;
+    }
+    const int KT = K / kTcBK;
+    // at least 58 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
+    const size_t smem = std::max<size_t>(1024 + (size_t)KT * (kTcBM + kTcBN) * 128 + 64, 58 * 1024);
+    dim3 grid((unsigned)cdiv(Nc, kTcBN), (unsigned)cdiv(M, kTcBM));
+    k_tc_gemm<<<grid, kTcThreads, smem, st>>>(tmA, tmB, M, Nc, K, C, ldc, g_tc_err);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+// Device error word of the tensor-core path (read by the solver after a factorisation).
+unsigned* tc_error_word() { return g_tc_err; }
+
+}  // namespace nl

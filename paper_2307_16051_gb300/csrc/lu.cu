@@ -1,0 +1,672 @@
+// lu.cu — blocked right-looking LU with partial pivoting (Section 1.3:
+// Gaussian elimination; Section 2: the half-precision factorisation of J_h).
+//
+// Two-level blocking.  The matrix is processed in outer panels of NB columns.
+// Each outer panel is copied into a working array P (binary32 for the
+// half-precision LU, binary64 for the double LU) and factored leaf by leaf
+// (leaf = kLeaf columns):
+//   * k_leaf: one thread-block cluster holds the leaf's rows in registers.
+//     Per column, each CTA finds its best pivot candidate (warp shuffles),
+//     broadcasts the candidate row to every CTA of the cluster through
+//     distributed shared memory, and after one cluster barrier every CTA
+//     picks the same pivot (largest |a|, first in the current row order)
+//     and eliminates.  Rows stay in place; positions are tracked, and the
+//     rows are written to their final positions at the end.  The epilogue
+//     applies the leaf's interchanges to the other panel columns and forms
+//     the leaf's U rows for the remaining panel columns.
+//   * k_panel_gemm: the rest of the panel below the leaf is updated.
+// After the panel: interchanges on the other columns of the matrix (k_laswp),
+// U12 = L11^{-1} A12 (k_trsm_u12), and the trailing update
+// A22 <- A22 - L21 U12 (SIMT here, or tcgen05 in gemm_tc.cu).
+//
+// Half-precision arithmetic model: binary32 arithmetic on binary16 data; the
+// multipliers and the pivot rows' entries are rounded to binary16 as soon as
+// they are formed, and everything not yet eliminated is rounded to binary16
+// once per outer panel (when P is written back and when the trailing update
+// is stored).  With the SIMT trailing update this reproduces, operation for
+// operation, Gaussian elimination with that rounding schedule.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <climits>
+#include <type_traits>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace nl {
+
+constexpr int kLeafThreads = 256;
+constexpr int kMaxCluster = 16;
+
+template <typename T, int NBL>
+struct alignas(16) LeafRec {
+    T abs;      // |candidate|, -1 when the CTA has no live row
+    int pos;    // candidate's current position (relative to the leaf's first row)
+    int pad;
+    T v[NBL];   // candidate row over the leaf's columns
+};
+
+template <typename T>
+__device__ __forceinline__ bool better(T a, int pa, T b, int pb)
+{
+    return a > b || (a == b && pa < pb);
+}
+
+template <typename T>
+__device__ __forceinline__ T maybe_round(T v, bool r)
+{
+    return v;
+}
+template <>
+__device__ __forceinline__ float maybe_round<float>(float v, bool r)
+{
+    return r ? round_h(v) : v;
+}
+
+// Register-array element at a runtime index, by static selects (keeps the
+// array in registers).
+template <int NBL, typename T>
+__device__ __forceinline__ T pick(const T (&row)[NBL], int j)
+{
+    T r = row[0];
+#pragma unroll
+    for (int t = 1; t < NBL; ++t)
+        if (t == j) r = row[t];
+    return r;
+}
+template <int NBL, typename T>
+__device__ __forceinline__ void place(T (&row)[NBL], int j, T v)
+{
+#pragma unroll
+    for (int t = 0; t < NBL; ++t)
+        if (t == j) row[t] = v;
+}
+
+// P: working panel, row r (relative to the panel's first row K), column t
+// (relative to K), leading dimension ldp.  The leaf covers columns
+// [k0, k0+wl) and rows [k0, M).  ipiv_out points at ipiv[K + k0].
+template <typename T, int NBL, int R, bool RND>
+__global__ void __launch_bounds__(kLeafThreads, 1) k_leaf(T* __restrict__ P, int ldp, int k0, int M, int w, int wl,
+                                                       int* __restrict__ ipiv_out, int piv_base,
+                                                       int* __restrict__ info, int C, int rows_per_cta)
+{
+    using Rec = LeafRec<T, NBL>;
+    __shared__ Rec inbox[2][kMaxCluster];
+    __shared__ Rec outbox;
+    __shared__ Rec prow_save[NBL];  // pivot row of each step: L11 (below diag) and U11
+    __shared__ T wabs[kLeafThreads / 32];
+    __shared__ int wpos[kLeafThreads / 32];
+    __shared__ int piv_s[NBL];
+
+    const int rank = (C > 1) ? (int)cg::this_cluster().block_rank() : 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int Ml = M - k0;
+    const int lo = rank * rows_per_cta, hi = min(Ml, lo + rows_per_cta);
+
+    T v[R][NBL];
+    int pos[R];
+    bool live[R];
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        int lr = lo + tid + s * kLeafThreads;
+        live[s] = lr < hi;
+        pos[s] = lr;
+#pragma unroll
+        for (int t = 0; t < NBL; ++t)
+            v[s][t] = (live[s] && t < wl) ? P[(int64_t)(k0 + lr) * ldp + k0 + t] : T(0);
+    }
+
+    for (int j = 0; j < wl; ++j) {
+        // ---- local and CTA-wide candidate: largest |a_ij|, then smallest position
+        T babs = T(-1);
+        int bpos = INT_MAX, bs = -1;
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            if (live[s]) {
+                T a = pick<NBL>(v[s], j);
+                a = a < T(0) ? -a : a;
+                if (!(a == a)) a = T(-0.5);  // NaN never wins over a number
+                if (better(a, pos[s], babs, bpos)) {
+                    babs = a;
+                    bpos = pos[s];
+                    bs = s;
+                }
+            }
+        }
+        T wa = babs;
+        int wp = bpos;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            T oa = __shfl_xor_sync(0xffffffffu, wa, o);
+            int op = __shfl_xor_sync(0xffffffffu, wp, o);
+            if (better(oa, op, wa, wp)) {
+                wa = oa;
+                wp = op;
+            }
+        }
+        if (lane == 0) {
+            wabs[warp] = wa;
+            wpos[warp] = wp;
+        }
+        __syncthreads();
+        T ca = T(-1);
+        int cp = INT_MAX;
+        for (int q = 0; q < kLeafThreads / 32; ++q)
+            if (better(wabs[q], wpos[q], ca, cp)) {
+                ca = wabs[q];
+                cp = wpos[q];
+            }
+        if (bs >= 0 && bpos == cp) {
+            outbox.abs = ca;
+            outbox.pos = cp;
+#pragma unroll
+            for (int s = 0; s < R; ++s)
+                if (s == bs) {
+#pragma unroll
+                    for (int t = 0; t < NBL; ++t) outbox.v[t] = v[s][t];
+                }
+        }
+        if (cp == INT_MAX && tid == 0) {
+            outbox.abs = T(-1);
+            outbox.pos = INT_MAX;
+        }
+        __syncthreads();
+
+        // ---- exchange candidates across the cluster
+        const Rec* recs;
+        int nrec;
+        if (C > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+            constexpr int kWords = sizeof(Rec) / 16;
+            for (int q = tid; q < C * kWords; q += kLeafThreads) {
+                int peer = q / kWords, wd = q % kWords;
+                float4* dst = reinterpret_cast<float4*>(cl.map_shared_rank(&inbox[j & 1][rank], peer));
+                dst[wd] = reinterpret_cast<const float4*>(&outbox)[wd];
+            }
+            cl.sync();
+            recs = inbox[j & 1];
+            nrec = C;
+        } else {
+            recs = &outbox;
+            nrec = 1;
+        }
+        T ga = T(-1);
+        int gp = INT_MAX, gsrc = 0;
+        for (int q = 0; q < nrec; ++q)
+            if (better(recs[q].abs, recs[q].pos, ga, gp)) {
+                ga = recs[q].abs;
+                gp = recs[q].pos;
+                gsrc = q;
+            }
+        const Rec& pr = recs[gsrc];
+        T u[NBL];
+#pragma unroll
+        for (int t = 0; t < NBL; ++t) u[t] = (t >= j) ? maybe_round(pr.v[t], RND) : T(0);
+        if (tid == 0) {
+            piv_s[j] = gp;
+            if (rank == 0) ipiv_out[j] = piv_base + gp;
+            // keep the pivot row: entries left of j are its multipliers
+#pragma unroll
+            for (int t = 0; t < NBL; ++t) prow_save[j].v[t] = (t >= j) ? u[t] : pr.v[t];
+        }
+
+        // ---- interchange bookkeeping: the pivot row moves to position j,
+        //      the row at position j moves to the pivot's old position
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+            if (live[s]) {
+                if (pos[s] == gp) {
+                    live[s] = false;
+                    pos[s] = j;
+#pragma unroll
+                    for (int t = 0; t < NBL; ++t)
+                        if (t >= j) v[s][t] = u[t];
+                } else if (pos[s] == j) {
+                    pos[s] = gp;
+                }
+            }
+        }
+
+        // ---- elimination of column j in the live rows
+        const T ukk = pick<NBL>(u, j);
+        if (ukk != T(0)) {
+#pragma unroll
+            for (int s = 0; s < R; ++s) {
+                if (live[s]) {
+                    T l = maybe_round(pick<NBL>(v[s], j) / ukk, RND);
+                    place<NBL>(v[s], j, l);
+#pragma unroll
+                    for (int t = 0; t < NBL; ++t)
+                        if (t > j) v[s][t] = fma(-l, u[t], v[s][t]);
+                }
+            }
+        } else if (tid == 0 && rank == 0) {
+            atomicCAS(info, 0, piv_base + j + 1);
+        }
+    }
+
+    // ---- rows to their final positions (leaf columns)
+#pragma unroll
+    for (int s = 0; s < R; ++s) {
+        int lr = lo + tid + s * kLeafThreads;
+        if (lr < hi) {
+#pragma unroll
+            for (int t = 0; t < NBL; ++t)
+                if (t < wl) P[(int64_t)(k0 + pos[s]) * ldp + k0 + t] = v[s][t];
+        }
+    }
+    if (rank != 0) return;
+    __syncthreads();
+
+    // ---- epilogue (one CTA): interchanges on the other panel columns, then
+    //      the leaf's U rows for the panel columns right of the leaf
+    const int nother = w - wl;
+    for (int q = tid; q < nother; q += kLeafThreads) {
+        int col = (q < k0) ? q : q + wl;
+        for (int jj = 0; jj < wl; ++jj) {
+            int p = piv_s[jj];
+            if (p != jj) {
+                T* a = P + (int64_t)(k0 + jj) * ldp + col;
+                T* b = P + (int64_t)(k0 + p) * ldp + col;
+                T tmp = *a;
+                *a = *b;
+                *b = tmp;
+            }
+        }
+        if (col >= k0 + wl) {
+            T uu[NBL];
+#pragma unroll
+            for (int kk = 0; kk < NBL; ++kk) {
+                if (kk < wl) {
+                    T a = P[(int64_t)(k0 + kk) * ldp + col];
+#pragma unroll
+                    for (int t = 0; t < NBL; ++t)
+                        if (t < kk) a = fma(-prow_save[kk].v[t], uu[t], a);
+                    a = maybe_round(a, RND);
+                    uu[kk] = a;
+                    P[(int64_t)(k0 + kk) * ldp + col] = a;
+                } else {
+                    uu[kk] = T(0);
+                }
+            }
+        }
+    }
+}
+
+// Rest of the panel below a leaf: P[i][c] -= sum_t P[i][k0+t] P[k0+t][c],
+// rows i in [k0+wl, M), columns c in [k0+wl, w), t in [0, wl) in order,
+// kept in the working precision (no rounding).
+template <typename T, int NBL>
+__global__ void __launch_bounds__(256) k_panel_gemm(T* __restrict__ P, int ldp, int k0, int wl, int M, int w)
+{
+    __shared__ T Us[NBL][64];
+    const int c0 = k0 + wl;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+    const int rbase = c0 + blockIdx.x * 64;
+    for (int cc = 0; cc < w - c0; cc += 64) {
+        const int c = c0 + cc + tx;
+        __syncthreads();
+        for (int q = threadIdx.x; q < NBL * 64; q += 256) {
+            int t = q / 64, x = q % 64;
+            Us[t][x] = (t < wl && c0 + cc + x < w) ? P[(int64_t)(k0 + t) * ldp + c0 + cc + x] : T(0);
+        }
+        __syncthreads();
+        if (c < w) {
+            for (int rr = ty; rr < 64; rr += 4) {
+                int i = rbase + rr;
+                if (i >= M) break;
+                const T* Li = P + (int64_t)i * ldp + k0;
+                T acc = P[(int64_t)i * ldp + c];
+#pragma unroll
+                for (int t = 0; t < NBL; ++t)
+                    if (t < wl) acc = fma(-Li[t], Us[t][tx], acc);
+                P[(int64_t)i * ldp + c] = acc;
+            }
+        }
+    }
+}
+
+template <typename T, typename S>
+__global__ void k_panel_load(const S* __restrict__ A, int64_t lda, int K, int M, int w, T* __restrict__ P, int ldp)
+{
+    const int i = blockIdx.x;
+    for (int t = threadIdx.x; t < w; t += blockDim.x) P[(int64_t)i * ldp + t] = (T)ld_elem(A + (int64_t)(K + i) * lda + K + t);
+}
+
+template <typename T, typename S>
+__global__ void k_panel_store(S* __restrict__ A, int64_t lda, int K, int M, int w, const T* __restrict__ P, int ldp)
+{
+    const int i = blockIdx.x;
+    for (int t = threadIdx.x; t < w; t += blockDim.x) st_elem(A + (int64_t)(K + i) * lda + K + t, P[(int64_t)i * ldp + t]);
+}
+
+// Row interchanges of panel [K, K+w) on all other columns, in order.
+template <typename S>
+__global__ void __launch_bounds__(256) k_laswp(S* __restrict__ A, int64_t lda, int K, int w, int N,
+                                               const int* __restrict__ ipiv)
+{
+    __shared__ int ps[256];
+    for (int q = threadIdx.x; q < w; q += blockDim.x) ps[q] = ipiv[K + q];
+    __syncthreads();
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N - w) return;
+    const int col = (q < K) ? q : q + w;
+    for (int jj = 0; jj < w; ++jj) {
+        int p = ps[jj];
+        if (p != K + jj) {
+            S* a = A + (int64_t)(K + jj) * lda + col;
+            S* b = A + (int64_t)p * lda + col;
+            S t = *a;
+            *a = *b;
+            *b = t;
+        }
+    }
+}
+
+// U12 = L11^{-1} A12 for rows [K, K+w), columns [K+w, N); each thread forms
+// one column by forward substitution (sequential fused multiply-adds in row
+// order), rounding each entry when formed (half LU).  Optionally also writes
+// U12^T (binary16, ldut) for the tensor-core update.
+template <typename T, typename S, bool RND>
+__global__ void __launch_bounds__(128) k_trsm_u12(S* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                  __half* __restrict__ Ut, int ldut)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* L = reinterpret_cast<T*>(smem_raw);  // w x w
+    T* us = L + w * w;                       // w x 128 (column per thread)
+    for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
+        int r = q / w, t = q % w;
+        L[q] = (t < r) ? (T)ld_elem(A + (int64_t)(K + r) * lda + K + t) : T(0);
+    }
+    __syncthreads();
+    const int c0 = K + w + blockIdx.x * 128;
+    const int c = c0 + threadIdx.x;
+    if (c < N) {
+        for (int kk = 0; kk < w; ++kk) {
+            T a = (T)ld_elem(A + (int64_t)(K + kk) * lda + c);
+            const T* Lk = L + kk * w;
+            for (int t = 0; t < kk; ++t) a = fma(-Lk[t], us[t * 128 + threadIdx.x], a);
+            a = maybe_round(a, RND);
+            us[kk * 128 + threadIdx.x] = a;
+            st_elem(A + (int64_t)(K + kk) * lda + c, a);
+        }
+    }
+    if (Ut) {
+        __syncthreads();
+        const int ncol = min(128, N - c0);
+        for (int q = threadIdx.x; q < ncol * w; q += blockDim.x) {
+            int col = q / w, kk = q % w;
+            Ut[(int64_t)(c0 - K - w + col) * ldut + kk] = __float2half_rn((float)us[kk * 128 + col]);
+        }
+    }
+}
+
+// C <- C - A B with per-element sequential fused multiply-adds over k in
+// order, accumulated in T and stored once (rounded to binary16 for __half).
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) k_gemm_simt(int M, int Nc, int K, const S* __restrict__ A, int64_t lda,
+                                                   const S* __restrict__ B, int64_t ldb, S* __restrict__ C,
+                                                   int64_t ldc)
+{
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int i = m0 + ty + 16 * a, j = n0 + tx + 16 * b;
+            acc[a][b] = (i < M && j < Nc) ? (T)ld_elem(C + (int64_t)i * ldc + j) : T(0);
+        }
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < BM * BK; q += 256) {
+            int r = q / BK, kk = q % BK;
+            int i = m0 + r, k = k0 + kk;
+            As[kk][r] = (i < M && k < K) ? (T)ld_elem(A + (int64_t)i * lda + k) : T(0);
+        }
+        for (int q = threadIdx.x; q < BK * BN; q += 256) {
+            int kk = q / BN, x = q % BN;
+            int k = k0 + kk, j = n0 + x;
+            Bs[kk][x] = (k < K && j < Nc) ? (T)ld_elem(B + (int64_t)k * ldb + j) : T(0);
+        }
+        __syncthreads();
+        const int kmax = min(BK, K - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fma(-av[a], bv[b], acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            int i = m0 + ty + 16 * a, j = n0 + tx + 16 * b;
+            if (i < M && j < Nc) st_elem(C + (int64_t)i * ldc + j, acc[a][b]);
+        }
+}
+
+// ------------------------------------------------------------------ host --
+
+size_t lu_work_bytes(int N, int nb, bool fp64)
+{
+    size_t el = fp64 ? 8 : 4;
+    size_t pnl = (size_t)N * nb * el;
+    size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
+    return round_up(pnl, 256) + round_up(ut, 256) + 256;
+}
+
+void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
+{
+    char* p = (char*)base;
+    size_t el = fp64 ? 8 : 4;
+    w->pnl = p;
+    p += round_up((size_t)N * nb * el, 256);
+    size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
+    w->ut = fp64 ? nullptr : (__half*)p;
+    p += round_up(ut, 256);
+    w->info = (int*)p;
+}
+
+template <typename T, int NBL, int R, bool RND>
+static nl_status launch_leaf_r(T* P, int ldp, int k0, int M, int w, int wl, int* ipiv_out, int piv_base, int* info,
+                               int C, int rows_per_cta, cudaStream_t st)
+{
+    auto kern = k_leaf<T, NBL, R, RND>;
+    if (C > 1) {
+        static bool attr_done = false;
+        if (!attr_done) {
+            NL_CUDA_OK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+            attr_done = true;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(kLeafThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        NL_CUDA_OK(cudaLaunchKernelEx(&cfg, kern, P, ldp, k0, M, w, wl, ipiv_out, piv_base, info, C, rows_per_cta));
+    } else {
+        kern<<<1, kLeafThreads, 0, st>>>(P, ldp, k0, M, w, wl, ipiv_out, piv_base, info, 1, rows_per_cta);
+        NL_CUDA_OK(cudaGetLastError());
+    }
+    return NL_OK;
+}
+
+// Cluster size and rows per thread for a leaf of Ml rows: the fewest CTAs
+// (cheapest exchange) with at most 4 (8 beyond 16384 rows) rows per thread.
+template <typename T, int NBL, bool RND>
+static nl_status launch_leaf(T* P, int ldp, int k0, int M, int w, int wl, int* ipiv_out, int piv_base, int* info,
+                             cudaStream_t st)
+{
+    const int Ml = M - k0;
+    // at most 4 rows per thread (spill-free) unless the leaf needs more than
+    // 16 CTAs at that density
+    int C = (int)cdiv(Ml, 4 * kLeafThreads);
+    if (C > kMaxCluster) C = (int)cdiv(Ml, 8 * kLeafThreads);
+    if (C > kMaxCluster) {
+        set_error("LU leaf: %d rows exceed the register-resident limit", Ml);
+        return NL_EINVAL;
+    }
+    if (C > 8) C = 16;
+    else if (C > 4) C = 8;
+    else if (C > 2) C = 4;
+    const int rows_per_cta = (int)cdiv(Ml, C);
+    const int R = (int)cdiv(rows_per_cta, kLeafThreads);
+    if (R <= 1) return launch_leaf_r<T, NBL, 1, RND>(P, ldp, k0, M, w, wl, ipiv_out, piv_base, info, C, rows_per_cta, st);
+    if (R <= 2) return launch_leaf_r<T, NBL, 2, RND>(P, ldp, k0, M, w, wl, ipiv_out, piv_base, info, C, rows_per_cta, st);
+    if (R <= 4) return launch_leaf_r<T, NBL, 4, RND>(P, ldp, k0, M, w, wl, ipiv_out, piv_base, info, C, rows_per_cta, st);
+    return launch_leaf_r<T, NBL, 8, RND>(P, ldp, k0, M, w, wl, ipiv_out, piv_base, info, C, rows_per_cta, st);
+}
+
+template <typename S, typename T>
+static nl_status launch_gemm_simt(int M, int Nc, int K, const S* A, int64_t lda, const S* B, int64_t ldb, S* C,
+                                  int64_t ldc, cudaStream_t st)
+{
+    if (M <= 0 || Nc <= 0 || K <= 0) return NL_OK;
+    dim3 grid((unsigned)cdiv(Nc, 64), (unsigned)cdiv(M, 64));
+    k_gemm_simt<S, T><<<grid, 256, 0, st>>>(M, Nc, K, A, lda, B, ldb, C, ldc);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+__global__ void k_transpose16(int R, int Cc, const __half* __restrict__ in, int64_t ldi, __half* __restrict__ out,
+                              int64_t ldo)
+{
+    __shared__ __half tile[32][33];
+    int c = blockIdx.x * 32 + threadIdx.x, r = blockIdx.y * 32 + threadIdx.y;
+    for (int k = 0; k < 32; k += 8)
+        if (r + k < R && c < Cc) tile[threadIdx.y + k][threadIdx.x] = in[(int64_t)(r + k) * ldi + c];
+    __syncthreads();
+    c = blockIdx.y * 32 + threadIdx.x;
+    r = blockIdx.x * 32 + threadIdx.y;
+    for (int k = 0; k < 32; k += 8)
+        if (r + k < Cc && c < R) out[(int64_t)(r + k) * ldo + c] = tile[threadIdx.x][threadIdx.y + k];
+}
+
+nl_status launch_transpose16(int R, int Cc, const __half* in, int64_t ldi, __half* out, int64_t ldo, cudaStream_t st)
+{
+    dim3 grid((unsigned)cdiv(Cc, 32), (unsigned)cdiv(R, 32));
+    k_transpose16<<<grid, dim3(32, 8), 0, st>>>(R, Cc, in, ldi, out, ldo);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* B, int64_t ldb, __half* C,
+                        int64_t ldc, int gemm, cudaStream_t st)
+{
+    if (gemm == 2) {
+        // the tensor-core path takes B transposed (K-major): build it
+        __half* Bt = nullptr;
+        NL_CUDA_OK(cudaMallocAsync((void**)&Bt, (size_t)round_up(Nc, 128) * K * 2, st));
+        nl_status s = launch_transpose16(K, Nc, B, ldb, Bt, K, st);
+        if (s == NL_OK) s = tc_gemm16_update(M, Nc, K, A, lda, Bt, K, C, ldc, st);
+        cudaFreeAsync(Bt, st);
+        return s;
+    }
+    return launch_gemm_simt<__half, float>(M, Nc, K, A, lda, B, ldb, C, ldc, st);
+}
+
+template <typename T, typename S, int NBL, bool RND>
+static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int gemm, const LuWork& w,
+                                cudaStream_t st, int* launches)
+{
+    T* P = (T*)w.pnl;
+    const int ldp = nb;
+    int nl = 0;
+    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, sizeof(int), st));
+    const size_t trsm_smem = (size_t)nb * nb * sizeof(T) + (size_t)nb * 128 * sizeof(T);
+    static bool smem_set = false;
+    if (!smem_set) {
+        NL_CUDA_OK(cudaFuncSetAttribute(k_trsm_u12<T, S, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024));
+        smem_set = true;
+    }
+    for (int K = 0; K < N; K += nb) {
+        const int wd = std::min(nb, N - K), M = N - K;
+        k_panel_load<T, S><<<M, 128, 0, st>>>(A, ld, K, M, wd, P, ldp);
+        ++nl;
+        for (int k0 = 0; k0 < wd; k0 += NBL) {
+            const int wl = std::min(NBL, wd - k0);
+            nl_status s = launch_leaf<T, NBL, RND>(P, ldp, k0, M, wd, wl, ipiv + K + k0, K + k0, w.info, st);
+            if (s != NL_OK) return s;
+            ++nl;
+            if (k0 + wl < wd && M > k0 + wl) {
+                unsigned g = (unsigned)cdiv(M - k0 - wl, 64);
+                k_panel_gemm<T, NBL><<<g, 256, 0, st>>>(P, ldp, k0, wl, M, wd);
+                ++nl;
+            }
+        }
+        k_panel_store<T, S><<<M, 128, 0, st>>>(A, ld, K, M, wd, P, ldp);
+        ++nl;
+        if (N - wd > 0) {
+            k_laswp<S><<<(unsigned)cdiv(N - wd, 256), 256, 0, st>>>(A, ld, K, wd, N, ipiv);
+            ++nl;
+        }
+        if (K + wd < N) {
+            const int rest = N - K - wd;
+            const bool tc = (gemm == 2) && std::is_same<S, __half>::value && (wd % 64 == 0);
+            k_trsm_u12<T, S, RND><<<(unsigned)cdiv(rest, 128), 128, trsm_smem, st>>>(A, ld, K, wd, N,
+                                                                                     tc ? w.ut : nullptr, nb);
+            ++nl;
+            S* L21 = A + (int64_t)(K + wd) * ld + K;
+            S* U12 = A + (int64_t)K * ld + K + wd;
+            S* A22 = A + (int64_t)(K + wd) * ld + K + wd;
+            if (tc) {
+                if constexpr (std::is_same<S, __half>::value) {
+                    nl_status s = tc_gemm16_update(rest, rest, wd, L21, ld, w.ut, nb, A22, ld, st);
+                    if (s != NL_OK) return s;
+                }
+            } else {
+                nl_status s = launch_gemm_simt<S, T>(rest, rest, wd, L21, ld, U12, ld, A22, ld, st);
+                if (s != NL_OK) return s;
+            }
+            ++nl;
+        }
+        NL_CUDA_OK(cudaGetLastError());
+    }
+    if (launches) *launches += nl;
+    return NL_OK;
+}
+
+nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm, const LuWork& w, cudaStream_t st,
+                      int* launches)
+{
+    if (nb < 16 || nb > 128 || nb % 16) {
+        set_error("lu16: nb must be a multiple of 16 in [16, 128]");
+        return NL_EINVAL;
+    }
+    if (gemm == 2 && !tc_gemm_supported()) gemm = 1;
+    return lu_factor_impl<float, __half, 16, true>(N, A, ld, ipiv, nb, gemm, w, st, launches);
+}
+
+nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, const LuWork& w, cudaStream_t st,
+                      int* launches)
+{
+    if (nb < 16 || nb > 128 || nb % 16) {
+        set_error("lu64: nb must be a multiple of 16 in [16, 128]");
+        return NL_EINVAL;
+    }
+    return lu_factor_impl<double, double, 8, false>(N, A, ld, ipiv, nb, 1, w, st, launches);
+}
+
+}  // namespace nl

@@ -1,0 +1,197 @@
+// problem.cu — the H-equation residual (fused with the Newton update) and
+// the analytic Jacobian, Section 3 eq. (3.2).
+//
+// With 0-based i, j the kernel entry is mu_i/(mu_j+mu_i) = (i+1/2)/(i+j+1),
+// so the sum of eq. (3.2) is a Hankel matrix-vector product
+//   t_i = c/(2N) (i + 1/2) sum_j x_j h[i+j],   h[k] = 1/(k+1),
+// evaluated from a 2N-1 entry table of reciprocals: no N x N matrix is read.
+#include "common.cuh"
+#include "internal.h"
+
+namespace nl {
+
+// ---------------------------------------------------------------- K1: F(x) --
+// Block = kFRows rows x kFSlices j-slices; rows and j-chunks are staged in
+// shared memory (x + scale*u for the chunk, and the h window it needs).
+constexpr int kFRows = 32, kFSlices = 8, kFChunk = 256;
+
+template <typename TU>
+__global__ void __launch_bounds__(kFRows* kFSlices)
+    k_residual(int N, double c, const double* __restrict__ x, const TU* __restrict__ u, double scale,
+               const double* __restrict__ htab, double* __restrict__ xout, double* __restrict__ F,
+               double* __restrict__ rr, double* __restrict__ partial, unsigned* __restrict__ counter,
+               double* __restrict__ fnorm)
+{
+    __shared__ double xs[kFChunk];
+    __shared__ double hw[kFChunk + kFRows];
+    __shared__ double red[kFSlices][kFRows + 1];
+    __shared__ bool last;
+    const int r = threadIdx.x % kFRows, q = threadIdx.x / kFRows;
+    const int i0 = blockIdx.x * kFRows;
+    const int i = i0 + r;
+    double acc = 0.0;
+    for (int j0 = 0; j0 < N; j0 += kFChunk) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kFChunk; t += blockDim.x) {
+            int j = j0 + t;
+            double v = 0.0;
+            if (j < N) {
+                v = x[j];
+                if (u) v += scale * (double)u[j];
+            }
+            xs[t] = v;
+        }
+        for (int t = threadIdx.x; t < kFChunk + kFRows; t += blockDim.x) {
+            int k = i0 + j0 + t;
+            hw[t] = (k < 2 * N - 1) ? htab[k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int jj = q; jj < kFChunk; jj += kFSlices) acc = fma(xs[jj], hw[r + jj], acc);
+    }
+    red[q][r] = acc;
+    __syncthreads();
+    double f2 = 0.0;
+    if (q == 0 && i < N) {
+        double s = 0.0;
+        for (int k = 0; k < kFSlices; ++k) s += red[k][r];
+        double t = c / (2.0 * (double)N) * ((double)i + 0.5) * s;
+        double ri = 1.0 / (1.0 - t);
+        double xi = x[i];
+        if (u) xi += scale * (double)u[i];
+        double fi = xi - ri;
+        if (xout) xout[i] = xi;
+        F[i] = fi;
+        rr[i] = ri;
+        f2 = fi * fi;
+    }
+    // deterministic norm: per-block partial, the last block sums them in order
+    __syncthreads();
+    if (q == 0) {
+        double v = f2;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (r == 0) partial[blockIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned done = atomicAdd(counter, 1u);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[b]);
+        *fnorm = sqrt(s);
+        *counter = 0u;
+    }
+}
+
+__global__ void k_htab(int N, double* htab)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < 2 * N - 1) htab[k] = 1.0 / (double)(k + 1);
+}
+
+nl_status launch_htab(int N, double* htab, cudaStream_t st)
+{
+    k_htab<<<(unsigned)cdiv(2 * (int64_t)N, 256), 256, 0, st>>>(N, htab);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+nl_status launch_residual(int N, double c, const double* x, const void* u, int u_is_double, double scale,
+                          const double* htab, double* xout, double* F, double* rr, double* partial,
+                          unsigned* counter, double* fnorm, cudaStream_t st)
+{
+    unsigned grid = (unsigned)cdiv(N, kFRows);
+    if (u_is_double)
+        k_residual<double><<<grid, kFRows * kFSlices, 0, st>>>(N, c, x, (const double*)u, scale, htab, xout, F,
+                                                               rr, partial, counter, fnorm);
+    else
+        k_residual<float><<<grid, kFRows * kFSlices, 0, st>>>(N, c, x, (const float*)u, scale, htab, xout, F,
+                                                              rr, partial, counter, fnorm);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+int residual_partials(int N) { return (int)cdiv(N, kFRows); }
+
+// ------------------------------------------------------- K2: the Jacobian --
+// J_ij = delta_ij - w_i h[i+j],  w_i = c/(2N) r_i^2 (i + 1/2).  Each thread
+// writes 8 consecutive columns of one row: two 16-byte stores of J32 and one
+// of J16.  w_i is formed in double and rounded to single; the product with
+// the single-rounded h[i+j] and the subtraction are one single-precision FMA.
+constexpr int kJCols = 8;
+
+__global__ void __launch_bounds__(256) k_jacobian(int N, double c, const double* __restrict__ rr,
+                                                  const double* __restrict__ htab, float* __restrict__ J32,
+                                                  int64_t ld32, __half* __restrict__ J16, int64_t ld16,
+                                                  int ldmax)
+{
+    const int i = blockIdx.y;
+    const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * kJCols;
+    if (j0 >= ldmax) return;
+    const double ri = rr[i];
+    const float w = (float)(c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5));
+    float v[kJCols];
+#pragma unroll
+    for (int t = 0; t < kJCols; ++t) {
+        int j = j0 + t;
+        float e = 0.0f;
+        if (j < N) {
+            float h = (float)htab[i + j];
+            e = fmaf(-w, h, (i == j) ? 1.0f : 0.0f);
+        }
+        v[t] = e;
+    }
+    if (J32 && j0 < ld32) {
+        float4* p = reinterpret_cast<float4*>(J32 + (int64_t)i * ld32 + j0);
+        p[0] = make_float4(v[0], v[1], v[2], v[3]);
+        p[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+    if (J16 && j0 < ld16) {
+        __align__(16) __half h[kJCols];
+#pragma unroll
+        for (int t = 0; t < kJCols; ++t) h[t] = __float2half_rn(v[t]);
+        *reinterpret_cast<uint4*>(J16 + (int64_t)i * ld16 + j0) = *reinterpret_cast<uint4*>(h);
+    }
+}
+
+nl_status launch_jacobian(int N, double c, const double* rr, const double* htab, float* J32, int64_t ld32,
+                          __half* J16, int64_t ld16, cudaStream_t st)
+{
+    if ((J32 && (ld32 % kJCols)) || (J16 && (ld16 % kJCols))) {
+        set_error("jacobian: leading dimensions must be multiples of %d", kJCols);
+        return NL_EINVAL;
+    }
+    int ldmax = (int)std::max(J32 ? ld32 : 0, J16 ? ld16 : 0);
+    dim3 grid((unsigned)cdiv(cdiv(ldmax, kJCols), 256), (unsigned)N);
+    k_jacobian<<<grid, 256, 0, st>>>(N, c, rr, htab, J32, ld32, J16, ld16, ldmax);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+__global__ void __launch_bounds__(256) k_jacobian64(int N, double c, const double* __restrict__ rr,
+                                                    const double* __restrict__ htab, double* __restrict__ J,
+                                                    int64_t ld)
+{
+    const int i = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ld) return;
+    const double ri = rr[i];
+    const double w = c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5);
+    J[(int64_t)i * ld + j] = (j < N) ? fma(-w, htab[i + j], (i == j) ? 1.0 : 0.0) : 0.0;
+}
+
+nl_status launch_jacobian64(int N, double c, const double* rr, const double* htab, double* J, int64_t ld,
+                            cudaStream_t st)
+{
+    dim3 grid((unsigned)cdiv(ld, 256), (unsigned)N);
+    k_jacobian64<<<grid, 256, 0, st>>>(N, c, rr, htab, J, ld);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+}  // namespace nl

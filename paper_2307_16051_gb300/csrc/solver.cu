@@ -1,0 +1,886 @@
+// solver.cu — the Newton drivers and the C ABI (include/newton3p.h).
+//
+// Algorithm 1.1 [newton] / Algorithm 2.1 [newton3p]: evaluate F in double,
+// tau = tau_r ||F(x0)|| + tau_a, and while ||F|| > tau: form the Jacobian,
+// factor it, solve J s = -F with the scaled right-hand side of
+// eqs. (2.17)-(2.18) (b = -F/||F||, s = ||F|| u), update x and re-evaluate F.
+// The update x += s is fused into the next residual evaluation.
+//
+// Linear solvers (Section 2.2): IR (Algorithm IR) and GMRES-IR with the
+// half-precision factors; success at ||b - J32 u|| <= eta ||b||, failure
+// when the residual norm increases (the best iterate is kept), Section 3.1.
+// Control runs on the host; each decision reads one device scalar back.
+#include <chrono>
+#include <type_traits>
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace nl {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+const char* get_error() { return g_err; }
+
+int num_sms()
+{
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+__global__ void k_fill64(int N, double v, double* x)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) x[i] = v;
+}
+
+// Carves aligned sub-buffers out of one device allocation.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(size_t n)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+struct LinBufs {
+    float *r, *d, *t, *w, *ubest, *V;
+    int64_t ldv;
+    double* gws;
+    double* partial;
+    unsigned* counter;
+    double* dscal;  // device scalars: [0] norm(b), [1] residual norm
+};
+
+struct LinResult {
+    int iters = 0, outer = 0, failed = 0, converged = 0;
+    double relres = 0.0;
+};
+
+struct Host {
+    double* pin;  // pinned host scalars
+    cudaStream_t st;
+    int* launches;
+    double read(const double* dev)
+    {
+        cudaMemcpyAsync(pin, dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        return pin[0];
+    }
+    void read2(const double* dev, double* out)
+    {
+        cudaMemcpyAsync(pin, dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        out[0] = pin[0];
+        out[1] = pin[1];
+        out[2] = pin[2];
+    }
+};
+
+#define NL_TRY(expr)                    \
+    do {                                \
+        nl_status _s = (expr);          \
+        if (_s != NL_OK) return _s;     \
+    } while (0)
+
+// Left-preconditioned restarted GMRES(m) from d0 = 0 for M^{-1} A d = M^{-1} r.
+static nl_status gmres16(int N, const float* J32, int64_t ld32, const __half* LU, int64_t ld16, const TrsvWork& tw,
+                         int& epoch, const float* r, float* d, int m, double gtol, int gcycles, LinBufs& B, Host& H,
+                         int* steps_out)
+{
+    cudaStream_t st = H.st;
+    const int so = gmres_scal_offset(m);
+    int steps = 0;
+    double beta0 = -1.0;
+    NL_CUDA_OK(cudaMemsetAsync(d, 0, sizeof(float) * N, st));
+    for (int cycle = 0; cycle < gcycles; ++cycle) {
+        if (cycle == 0) {
+            NL_CUDA_OK(cudaMemcpyAsync(B.t, r, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
+        } else {
+            NL_TRY(launch_gemv_residual(N, J32, ld32, r, d, B.t, B.partial, B.counter, nullptr, st));
+            ++*H.launches;
+        }
+        NL_TRY(trsv_solve16(N, LU, ld16, B.t, B.w, tw, ++epoch, st, H.launches));
+        NL_TRY(launch_gmres_start(N, B.w, B.V, B.gws, m, st));
+        ++*H.launches;
+        double sc[3];
+        H.read2(B.gws + so, sc);
+        const double beta = sc[0];
+        if (beta0 < 0.0) beta0 = beta;
+        if (beta == 0.0 || beta <= gtol * beta0) break;
+        int jcols = 0;
+        bool done = false;
+        for (int j = 0; j < m; ++j) {
+            NL_TRY(launch_gemv_residual(N, J32, ld32, nullptr, B.V + (int64_t)j * B.ldv, B.t, B.partial, B.counter,
+                                        nullptr, st));
+            NL_TRY(trsv_solve16(N, LU, ld16, B.t, B.w, tw, ++epoch, st, H.launches));
+            NL_TRY(launch_arnoldi(N, B.ldv, B.w, B.V, j, B.gws, m, st));
+            *H.launches += 2;
+            H.read2(B.gws + so, sc);
+            ++steps;
+            jcols = j + 1;
+            if (sc[1] <= gtol * beta0 || sc[2] != 0.0) {
+                done = true;
+                break;
+            }
+        }
+        NL_TRY(launch_gmres_update(N, B.ldv, B.V, B.gws, m, jcols, d, st));
+        ++*H.launches;
+        if (done) break;
+    }
+    *steps_out = steps;
+    return NL_OK;
+}
+
+// IR (solver 0) or GMRES-IR (solver 2) for J32 u = b, u0 = 0.
+static nl_status linsolve16(int N, const float* J32, int64_t ld32, const __half* LU, int64_t ld16, const TrsvWork& tw,
+                            int& epoch, const float* b, float* u, double eta, int maxit, int solver, int m,
+                            double gtol, int gcycles, LinBufs& B, Host& H, LinResult* res)
+{
+    cudaStream_t st = H.st;
+    *res = LinResult();
+    NL_CUDA_OK(cudaMemsetAsync(u, 0, sizeof(float) * N, st));
+    NL_CUDA_OK(cudaMemsetAsync(B.ubest, 0, sizeof(float) * N, st));
+    NL_CUDA_OK(cudaMemcpyAsync(B.r, b, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
+    NL_TRY(launch_norm32(N, b, B.partial, B.counter, B.dscal, st));
+    ++*H.launches;
+    const double nb = H.read(B.dscal);
+    double nr = nb, best = nr, prev = nr;
+    for (;;) {
+        if (nr <= eta * nb) {
+            res->converged = 1;
+            break;
+        }
+        if (res->outer >= maxit) break;
+        if (solver == 2) {
+            int steps = 0;
+            NL_TRY(gmres16(N, J32, ld32, LU, ld16, tw, epoch, B.r, B.d, m, gtol, gcycles, B, H, &steps));
+            res->iters += steps;
+        } else {
+            NL_TRY(trsv_solve16(N, LU, ld16, B.r, B.d, tw, ++epoch, st, H.launches));
+            res->iters += 1;
+        }
+        NL_TRY(launch_axpy32(N, 1.0f, B.d, u, st));
+        res->outer += 1;
+        NL_TRY(launch_gemv_residual(N, J32, ld32, b, u, B.r, B.partial, B.counter, B.dscal + 1, st));
+        *H.launches += 2;
+        nr = H.read(B.dscal + 1);
+        if (nr > prev) {
+            res->failed = 1;
+            NL_CUDA_OK(cudaMemcpyAsync(u, B.ubest, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
+            nr = best;
+            break;
+        }
+        prev = nr;
+        if (nr < best) {
+            best = nr;
+            NL_CUDA_OK(cudaMemcpyAsync(B.ubest, u, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    res->relres = nb > 0.0 ? nr / nb : 0.0;
+    return NL_OK;
+}
+
+}  // namespace nl
+
+using namespace nl;
+
+struct nl_solver {
+    int N = 0;
+    double c = 0.0;
+    nl_config cfg;
+    cudaStream_t st = nullptr;
+    int64_t ld = 0;  // leading dimension of J32 / J16 / J64 (multiple of 64)
+    void* pool = nullptr;
+    size_t pool_bytes = 0;
+    void* pool64 = nullptr;
+    size_t pool64_bytes = 0;
+    double* pin = nullptr;
+    // state
+    double *xa = nullptr, *xb = nullptr, *F = nullptr, *rr = nullptr, *htab = nullptr, *partial = nullptr,
+           *dscal = nullptr, *gws = nullptr;
+    unsigned* counter = nullptr;
+    float *J32 = nullptr, *b = nullptr, *u = nullptr;
+    __half* J16 = nullptr;
+    int* ipiv = nullptr;
+    LinBufs lb;
+    LuWork luw;
+    TrsvWork tw;
+    // double-precision mode
+    double *J64 = nullptr, *b64 = nullptr, *u64 = nullptr;
+    int* ipiv64 = nullptr;
+    LuWork luw64;
+    TrsvWork tw64;
+    int epoch = 0;
+    int nb = 128;
+    int gemm = 2;
+    nl_stats_t stats;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+};
+
+static bool valid_mode(int m) { return m == NL_FP64LU || m == NL_IR16 || m == NL_GMRESIR16; }
+
+extern "C" {
+
+nl_status nl_config_default(nl_config* cfg)
+{
+    if (!cfg) {
+        set_error("nl_config_default: cfg is NULL");
+        return NL_EINVAL;
+    }
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->eta_j = 1e-4;
+    cfg->ir_maxit = 20;
+    cfg->gmres_restart = 30;
+    cfg->gmres_tol = 1e-4;
+    cfg->gmres_maxcycles = 10;
+    cfg->newton_maxit = 30;
+    cfg->tau_a = 0.0;
+    cfg->lu_nb = 0;
+    cfg->trailing_gemm = 0;
+    return NL_OK;
+}
+
+const char* nl_last_error(void) { return get_error(); }
+const char* nl_version(void) { return "newton3p-gb300 0.1 (sm_103a)"; }
+
+nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
+{
+    set_error("");
+    if (!out || N < 1 || N > 32768 || !(c >= 0.0 && c < 1.0)) {
+        set_error("nl_create: need N in [1, 32768], 0 <= c < 1 and out != NULL");
+        return NL_EINVAL;
+    }
+    nl_config d;
+    nl_config_default(&d);
+    if (cfg) d = *cfg;
+    if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 ||
+        d.newton_maxit >= NL_MAX_HIST || (d.lu_nb && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16))) {
+        set_error("nl_create: invalid configuration");
+        return NL_EINVAL;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        set_error("nl_create: no CUDA device");
+        return NL_ECUDA;
+    }
+    nl_solver* s = new nl_solver();
+    s->N = (int)N;
+    s->c = c;
+    s->cfg = d;
+    s->nb = d.lu_nb ? d.lu_nb : 128;
+    s->gemm = d.trailing_gemm ? d.trailing_gemm : 2;
+    if (s->gemm == 2 && (!tc_gemm_supported() || s->nb % 64)) s->gemm = 1;
+    s->ld = round_up(N, 64);
+    const int n = s->N;
+    const int m = d.gmres_restart;
+    const int64_t ldv = round_up(N, 64);
+    const size_t npart = (size_t)std::max(residual_partials(n), gemv_partials(n)) + 64;
+    // sizes
+    size_t bytes = 0;
+    {
+        Carver cv(nullptr);
+        cv.take<double>(n);            // xa
+        cv.take<double>(n);            // xb
+        cv.take<double>(n);            // F
+        cv.take<double>(n);            // rr
+        cv.take<double>(2 * n);        // htab
+        cv.take<double>(npart);        // partial
+        cv.take<double>(16);           // dscal
+        cv.take<unsigned>(4);          // counter
+        cv.take<double>(gmres_ws_doubles(m));
+        cv.take<float>((size_t)n * s->ld);     // J32
+        cv.take<__half>((size_t)n * s->ld);    // J16
+        cv.take<int>(n);               // ipiv
+        cv.take<float>(ldv);           // b
+        cv.take<float>(ldv);           // u
+        for (int q = 0; q < 5; ++q) cv.take<float>(ldv);  // r d t w ubest
+        cv.take<float>((size_t)(m + 1) * ldv);            // V
+        cv.take<char>(lu_work_bytes(n, s->nb, false));
+        cv.take<char>(trsv_work_bytes(n, false));
+        bytes = cv.off + 256;
+    }
+    if (cudaMalloc(&s->pool, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        set_error("nl_create: cudaMalloc of %zu bytes failed", bytes);
+        return NL_ENOMEM;
+    }
+    s->pool_bytes = bytes;
+    cudaMemset(s->pool, 0, bytes);
+    Carver cv(s->pool);
+    s->xa = cv.take<double>(n);
+    s->xb = cv.take<double>(n);
+    s->F = cv.take<double>(n);
+    s->rr = cv.take<double>(n);
+    s->htab = cv.take<double>(2 * n);
+    s->partial = cv.take<double>(npart);
+    s->dscal = cv.take<double>(16);
+    s->counter = cv.take<unsigned>(4);
+    s->gws = cv.take<double>(gmres_ws_doubles(m));
+    s->J32 = cv.take<float>((size_t)n * s->ld);
+    s->J16 = cv.take<__half>((size_t)n * s->ld);
+    s->ipiv = cv.take<int>(n);
+    s->b = cv.take<float>(ldv);
+    s->u = cv.take<float>(ldv);
+    s->lb.r = cv.take<float>(ldv);
+    s->lb.d = cv.take<float>(ldv);
+    s->lb.t = cv.take<float>(ldv);
+    s->lb.w = cv.take<float>(ldv);
+    s->lb.ubest = cv.take<float>(ldv);
+    s->lb.V = cv.take<float>((size_t)(m + 1) * ldv);
+    s->lb.ldv = ldv;
+    s->lb.gws = s->gws;
+    s->lb.partial = s->partial;
+    s->lb.counter = s->counter;
+    s->lb.dscal = s->dscal + 4;
+    lu_work_carve(cv.take<char>(lu_work_bytes(n, s->nb, false)), n, s->nb, false, &s->luw);
+    trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &s->tw);
+    if (cudaMallocHost((void**)&s->pin, 64) != cudaSuccess || cudaEventCreate(&s->ev[0]) != cudaSuccess ||
+        cudaEventCreate(&s->ev[1]) != cudaSuccess) {
+        cudaFree(s->pool);
+        delete s;
+        set_error("nl_create: host/event allocation failed");
+        return NL_ENOMEM;
+    }
+    if (launch_htab(n, s->htab, s->st) != NL_OK || cudaStreamSynchronize(s->st) != cudaSuccess) {
+        nl_destroy(s);
+        return NL_ECUDA;
+    }
+    memset(&s->stats, 0, sizeof(s->stats));
+    *out = s;
+    return NL_OK;
+}
+
+nl_status nl_set_stream(nl_solver* s, void* stream)
+{
+    if (!s) {
+        set_error("nl_set_stream: NULL handle");
+        return NL_EINVAL;
+    }
+    s->st = (cudaStream_t)stream;
+    return NL_OK;
+}
+
+int64_t nl_device_bytes(const nl_solver* s) { return s ? (int64_t)(s->pool_bytes + s->pool64_bytes) : 0; }
+
+void nl_destroy(nl_solver* s)
+{
+    if (!s) return;
+    if (s->st) cudaStreamSynchronize(s->st);
+    else cudaDeviceSynchronize();
+    if (s->pool) cudaFree(s->pool);
+    if (s->pool64) cudaFree(s->pool64);
+    if (s->pin) cudaFreeHost(s->pin);
+    if (s->ev[0]) cudaEventDestroy(s->ev[0]);
+    if (s->ev[1]) cudaEventDestroy(s->ev[1]);
+    delete s;
+}
+
+static nl_status ensure_fp64(nl_solver* s)
+{
+    if (s->pool64) return NL_OK;
+    const int n = s->N;
+    const int nb64 = 64;
+    size_t bytes;
+    {
+        Carver cv(nullptr);
+        cv.take<double>((size_t)n * s->ld);
+        cv.take<double>(n);
+        cv.take<double>(n);
+        cv.take<int>(n);
+        cv.take<char>(lu_work_bytes(n, nb64, true));
+        cv.take<char>(trsv_work_bytes(n, true));
+        bytes = cv.off + 256;
+    }
+    if (cudaMalloc(&s->pool64, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->pool64 = nullptr;
+        set_error("double-precision Jacobian: cudaMalloc of %zu bytes failed", bytes);
+        return NL_ENOMEM;
+    }
+    s->pool64_bytes = bytes;
+    cudaMemsetAsync(s->pool64, 0, bytes, s->st);
+    Carver cv(s->pool64);
+    s->J64 = cv.take<double>((size_t)n * s->ld);
+    s->b64 = cv.take<double>(n);
+    s->u64 = cv.take<double>(n);
+    s->ipiv64 = cv.take<int>(n);
+    lu_work_carve(cv.take<char>(lu_work_bytes(n, nb64, true)), n, nb64, true, &s->luw64);
+    trsv_work_carve(cv.take<char>(trsv_work_bytes(n, true)), n, true, &s->tw64);
+    return NL_OK;
+}
+
+static float elapsed_ms(nl_solver* s)
+{
+    float ms = 0.0f;
+    cudaEventSynchronize(s->ev[1]);
+    cudaEventElapsedTime(&ms, s->ev[0], s->ev[1]);
+    return ms;
+}
+
+static nl_status check_device_errors(nl_solver* s)
+{
+    unsigned e[2] = {0, 0};
+    cudaMemcpyAsync(&e[0], s->tw.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st);
+    if (s->tw64.err) cudaMemcpyAsync(&e[1], s->tw64.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st);
+    NL_CUDA_OK(cudaStreamSynchronize(s->st));
+    unsigned* tce = tc_error_word();
+    unsigned e3 = 0;
+    if (tce) NL_CUDA_OK(cudaMemcpy(&e3, tce, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (e[0] | e[1] | e3) {
+        set_error("a device-side bounded wait gave up (error word 0x%x/0x%x/0x%x)", e[0], e[1], e3);
+        cudaMemsetAsync(s->tw.err, 0, sizeof(unsigned), s->st);
+        if (s->tw64.err) cudaMemsetAsync(s->tw64.err, 0, sizeof(unsigned), s->st);
+        if (tce) cudaMemsetAsync(tce, 0, sizeof(unsigned), s->st);
+        return NL_ETIMEOUT;
+    }
+    return NL_OK;
+}
+
+static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double tol, nl_mode mode, double* x_out,
+                            bool out_host)
+{
+    auto t_start = std::chrono::steady_clock::now();
+    const int n = s->N;
+    cudaStream_t st = s->st;
+    nl_stats_t& S = s->stats;
+    memset(&S, 0, sizeof(S));
+    S.mode = mode;
+    S.lu_nb = (mode == NL_FP64LU) ? 64 : s->nb;
+    int launches = 0;
+    Host H{s->pin, st, &launches};
+    if (mode == NL_FP64LU) NL_TRY(ensure_fp64(s));
+
+    double* x = s->xa;
+    double* xn = s->xb;
+    if (x0) {
+        NL_CUDA_OK(cudaMemcpyAsync(x, x0, sizeof(double) * n, x0_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                                   st));
+    } else {
+        k_fill64<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, 1.0, x);
+        ++launches;
+    }
+    double* fn_dev = s->dscal;
+    cudaEventRecord(s->ev[0], st);
+    NL_TRY(launch_residual(n, s->c, x, nullptr, 0, 0.0, s->htab, nullptr, s->F, s->rr, s->partial, s->counter, fn_dev,
+                           st));
+    cudaEventRecord(s->ev[1], st);
+    ++launches;
+    const double f0 = H.read(fn_dev);
+    S.t_f_ms += elapsed_ms(s);
+    double fn = f0;
+    const double tau = tol * f0 + s->cfg.tau_a;
+    S.fnorm0 = f0;
+    S.hist[0] = 1.0;
+    int it = 0;
+    nl_status status = NL_ENOTCONV;
+    while (!(fn <= tau)) {
+        if (!std::isfinite(fn)) {
+            status = NL_ENUMERIC;
+            set_error("non-finite residual norm");
+            break;
+        }
+        if (it >= s->cfg.newton_maxit) break;
+        // Jacobian
+        cudaEventRecord(s->ev[0], st);
+        if (mode == NL_FP64LU)
+            NL_TRY(launch_jacobian64(n, s->c, s->rr, s->htab, s->J64, s->ld, st));
+        else
+            NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st));
+        cudaEventRecord(s->ev[1], st);
+        ++launches;
+        S.t_jac_ms += elapsed_ms(s);
+        // factorisation
+        cudaEventRecord(s->ev[0], st);
+        int info = 0;
+        if (mode == NL_FP64LU) {
+            NL_TRY(lu64_factor(n, s->J64, s->ld, s->ipiv64, 64, s->luw64, st, &launches));
+            NL_TRY(trsv_prepare64(n, s->J64, s->ld, s->ipiv64, s->tw64, st, &launches));
+            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw64.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+        } else {
+            NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, s->luw, st, &launches));
+            NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
+            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+        }
+        cudaEventRecord(s->ev[1], st);
+        NL_CUDA_OK(cudaStreamSynchronize(st));
+        memcpy(&info, s->pin, sizeof(int));
+        S.t_lu_ms += elapsed_ms(s);
+        if (info != 0) {
+            status = NL_ESINGULAR;
+            set_error("zero pivot at column %d", info);
+            break;
+        }
+        // linear solve for the scaled step
+        cudaEventRecord(s->ev[0], st);
+        const void* ustep;
+        int u_is_double = 0;
+        if (mode == NL_FP64LU) {
+            NL_TRY(launch_scale_rhs64(n, s->F, fn_dev, s->b64, st));
+            NL_TRY(trsv_solve64(n, s->J64, s->ld, s->b64, s->u64, s->tw64, ++s->epoch, st, &launches));
+            ++launches;
+            ustep = s->u64;
+            u_is_double = 1;
+        } else {
+            NL_TRY(launch_scale_rhs32(n, s->F, fn_dev, s->b, st));
+            ++launches;
+            LinResult lr;
+            NL_TRY(linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
+                              s->cfg.ir_maxit, mode == NL_GMRESIR16 ? 2 : 0, s->cfg.gmres_restart, s->cfg.gmres_tol,
+                              s->cfg.gmres_maxcycles, s->lb, H, &lr));
+            S.lin_iters[it] = lr.iters;
+            S.lin_outer[it] = lr.outer;
+            S.lin_failed[it] = lr.failed;
+            S.lin_relres[it] = lr.relres;
+            ustep = s->u;
+        }
+        cudaEventRecord(s->ev[1], st);
+        // x_{n+1} = x_n + ||F|| u, fused with F(x_{n+1})
+        NL_TRY(launch_residual(n, s->c, x, ustep, u_is_double, fn, s->htab, xn, s->F, s->rr, s->partial, s->counter,
+                               fn_dev, st));
+        ++launches;
+        S.t_lin_ms += elapsed_ms(s);
+        cudaEventRecord(s->ev[0], st);
+        fn = H.read(fn_dev);
+        std::swap(x, xn);
+        ++it;
+        S.hist[it] = f0 > 0.0 ? fn / f0 : 0.0;
+        nl_status e = check_device_errors(s);
+        if (e != NL_OK) return e;
+    }
+    if (fn <= tau) status = NL_OK;
+    NL_CUDA_OK(cudaMemcpyAsync(x_out, x, sizeof(double) * n, out_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                               st));
+    NL_CUDA_OK(cudaStreamSynchronize(st));
+    S.status = status;
+    S.newton_iters = it;
+    S.fnorm = fn;
+    S.gpu_launches = launches;
+    S.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    return status;
+}
+
+nl_status nl_solve(nl_solver* s, const double* x0, double tol, nl_mode mode, double* x_out)
+{
+    set_error("");
+    if (!s || !x_out || !valid_mode(mode) || !(tol >= 0.0)) {
+        set_error("nl_solve: bad argument");
+        return NL_EINVAL;
+    }
+    return solve_impl(s, x0, true, tol, mode, x_out, true);
+}
+
+nl_status nl_solve_device(nl_solver* s, const double* x0_dev, double tol, nl_mode mode, double* x_out_dev)
+{
+    set_error("");
+    if (!s || !x_out_dev || !valid_mode(mode) || !(tol >= 0.0)) {
+        set_error("nl_solve_device: bad argument");
+        return NL_EINVAL;
+    }
+    return solve_impl(s, x0_dev, false, tol, mode, x_out_dev, false);
+}
+
+nl_status nl_stats(const nl_solver* s, nl_stats_t* out)
+{
+    if (!s || !out) {
+        set_error("nl_stats: NULL argument");
+        return NL_EINVAL;
+    }
+    *out = s->stats;
+    return NL_OK;
+}
+
+// ------------------------------------------------------ kernel-level API --
+
+nl_status nl_k_residual(int64_t N, double c, const double* x, const void* u, int u_is_double, double fnorm_scale,
+                        double* x_out, double* F, double* r, double* fnorm_dev, void* stream)
+{
+    if (N < 1 || N > 32768 || !x || !F || !r || !fnorm_dev || (u && !x_out) || (x_out && x_out == x)) {
+        set_error("nl_k_residual: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    double *htab = nullptr, *partial = nullptr;
+    unsigned* counter = nullptr;
+    const size_t np = residual_partials(n);
+    NL_CUDA_OK(cudaMallocAsync((void**)&htab, sizeof(double) * (2 * n + np) + 256, st));
+    partial = htab + 2 * n;
+    counter = (unsigned*)(partial + np);
+    NL_CUDA_OK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    nl_status s = launch_htab(n, htab, st);
+    if (s == NL_OK)
+        s = launch_residual(n, c, x, u, u_is_double, fnorm_scale, htab, x_out, F, r, partial, counter, fnorm_dev, st);
+    cudaFreeAsync(htab, st);
+    return s;
+}
+
+nl_status nl_k_jacobian(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16, int64_t ld16,
+                        void* stream)
+{
+    if (N < 1 || N > 32768 || !r || (J32 && ld32 < N) || (J16 && ld16 < N)) {
+        set_error("nl_k_jacobian: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    double* htab = nullptr;
+    NL_CUDA_OK(cudaMallocAsync((void**)&htab, sizeof(double) * 2 * n, st));
+    nl_status s = launch_htab(n, htab, st);
+    if (s == NL_OK) s = launch_jacobian(n, c, r, htab, J32, ld32, (__half*)J16, ld16, st);
+    cudaFreeAsync(htab, st);
+    return s;
+}
+
+nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int64_t ld, void* stream)
+{
+    if (N < 1 || N > 32768 || !r || !J64 || ld < N) {
+        set_error("nl_k_jacobian64: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    double* htab = nullptr;
+    NL_CUDA_OK(cudaMallocAsync((void**)&htab, sizeof(double) * 2 * n, st));
+    nl_status s = launch_htab(n, htab, st);
+    if (s == NL_OK) s = launch_jacobian64(n, c, r, htab, J64, ld, st);
+    cudaFreeAsync(htab, st);
+    return s;
+}
+
+nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int32_t* info_host, void* stream)
+{
+    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2) {
+        set_error("nl_lu16: bad argument");
+        return NL_EINVAL;
+    }
+    if (nb == 0) nb = 128;
+    if (gemm == 0) gemm = 2;
+    if (gemm == 2 && (nb % 64 || !tc_gemm_supported())) gemm = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    void* wk = nullptr;
+    NL_CUDA_OK(cudaMallocAsync(&wk, lu_work_bytes(n, nb, false), st));
+    LuWork w;
+    lu_work_carve(wk, n, nb, false, &w);
+    nl_status s = lu16_factor(n, (__half*)A16, ld, ipiv, nb, gemm, w, st, nullptr);
+    int info = 0;
+    if (s == NL_OK) s = (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess) ? NL_OK : NL_ECUDA;
+    cudaFreeAsync(wk, st);
+    NL_CUDA_OK(cudaStreamSynchronize(st));
+    unsigned* tce = tc_error_word();
+    if (s == NL_OK && tce) {
+        unsigned e = 0;
+        NL_CUDA_OK(cudaMemcpy(&e, tce, sizeof(unsigned), cudaMemcpyDeviceToHost));
+        if (e) {
+            cudaMemset(tce, 0, sizeof(unsigned));
+            set_error("tensor-core update: bounded wait gave up");
+            return NL_ETIMEOUT;
+        }
+    }
+    if (info_host) *info_host = info;
+    if (s == NL_OK && info) return NL_ESINGULAR;
+    return s;
+}
+
+nl_status nl_lu64(int64_t N, double* A, int64_t ld, int32_t* ipiv, int nb, int32_t* info_host, void* stream)
+{
+    if (N < 1 || N > 32768 || !A || !ipiv || ld < N) {
+        set_error("nl_lu64: bad argument");
+        return NL_EINVAL;
+    }
+    if (nb == 0) nb = 64;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    void* wk = nullptr;
+    NL_CUDA_OK(cudaMallocAsync(&wk, lu_work_bytes(n, nb, true), st));
+    LuWork w;
+    lu_work_carve(wk, n, nb, true, &w);
+    nl_status s = lu64_factor(n, A, ld, ipiv, nb, w, st, nullptr);
+    int info = 0;
+    if (s == NL_OK) cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(wk, st);
+    NL_CUDA_OK(cudaStreamSynchronize(st));
+    if (info_host) *info_host = info;
+    if (s == NL_OK && info) return NL_ESINGULAR;
+    return s;
+}
+
+}  // extern "C"
+
+template <typename S, typename T>
+static nl_status lusolve_entry(int64_t N, const S* LU, int64_t ld, const int32_t* ipiv, T* b, void* stream, bool fp64)
+{
+    if (N < 1 || N > 32768 || !LU || !ipiv || !b || ld < N) {
+        set_error("nl_lusolve: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    void* wk = nullptr;
+    const size_t bytes = trsv_work_bytes(n, fp64);
+    NL_CUDA_OK(cudaMallocAsync(&wk, bytes, st));
+    NL_CUDA_OK(cudaMemsetAsync(wk, 0, bytes, st));
+    TrsvWork w;
+    trsv_work_carve(wk, n, fp64, &w);
+    nl_status s;
+    if constexpr (std::is_same<S, __half>::value) {
+        s = trsv_prepare16(n, LU, ld, ipiv, w, st, nullptr);
+        if (s == NL_OK) s = trsv_solve16(n, LU, ld, b, b, w, 1, st, nullptr);
+    } else {
+        s = trsv_prepare64(n, LU, ld, ipiv, w, st, nullptr);
+        if (s == NL_OK) s = trsv_solve64(n, LU, ld, b, b, w, 1, st, nullptr);
+    }
+    unsigned e = 0;
+    cudaMemcpyAsync(&e, w.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(wk, st);
+    NL_CUDA_OK(cudaStreamSynchronize(st));
+    if (s == NL_OK && e) {
+        set_error("triangular solve: bounded wait gave up");
+        return NL_ETIMEOUT;
+    }
+    return s;
+}
+
+extern "C" {
+
+nl_status nl_lusolve16(int64_t N, const void* LU16, int64_t ld, const int32_t* ipiv, float* b, void* stream)
+{
+    return lusolve_entry<__half, float>(N, (const __half*)LU16, ld, ipiv, b, stream, false);
+}
+
+nl_status nl_lusolve64(int64_t N, const double* LU, int64_t ld, const int32_t* ipiv, double* b, void* stream)
+{
+    return lusolve_entry<double, double>(N, LU, ld, ipiv, b, stream, true);
+}
+
+nl_status nl_k_gemv_residual(int64_t N, const float* A, int64_t ld, const float* b, const float* u, float* r,
+                             double* rnorm_dev, void* stream)
+{
+    if (N < 1 || N > 32768 || !A || !u || !r || ld < N) {
+        set_error("nl_k_gemv_residual: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    const size_t np = gemv_partials(n);
+    double* partial = nullptr;
+    NL_CUDA_OK(cudaMallocAsync((void**)&partial, sizeof(double) * np + 256, st));
+    unsigned* counter = (unsigned*)(partial + np);
+    NL_CUDA_OK(cudaMemsetAsync(counter, 0, sizeof(unsigned), st));
+    nl_status s = launch_gemv_residual(n, A, ld, b, u, r, partial, counter, rnorm_dev, st);
+    cudaFreeAsync(partial, st);
+    return s;
+}
+
+nl_status nl_k_gemm16_update(int64_t M, int64_t Nc, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                             void* C, int64_t ldc, int gemm, void* stream)
+{
+    if (M < 0 || Nc < 0 || K < 1 || !A || !B || !C || (gemm != 1 && gemm != 2)) {
+        set_error("nl_k_gemm16_update: bad argument");
+        return NL_EINVAL;
+    }
+    return gemm16_update((int)M, (int)Nc, (int)K, (const __half*)A, lda, (const __half*)B, ldb, (__half*)C, ldc, gemm,
+                         (cudaStream_t)stream);
+}
+
+nl_status nl_linsolve16(int64_t N, const float* J32, int64_t ld32, const void* LU16, int64_t ld16, const int32_t* ipiv,
+                        const float* b, float* u, double eta, int maxit, int solver, int m, double gtol, int gcycles,
+                        int32_t* stats_host, double* relres_host, void* stream)
+{
+    if (N < 1 || N > 32768 || !J32 || !LU16 || !ipiv || !b || !u || (solver != 0 && solver != 2) || m < 1 || m > 62 ||
+        (ld32 % 4) || ld32 < N || ld16 < N) {
+        set_error("nl_linsolve16: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    const int64_t ldv = round_up(N, 64);
+    size_t bytes;
+    {
+        Carver cv(nullptr);
+        for (int q = 0; q < 5; ++q) cv.take<float>(ldv);
+        cv.take<float>((size_t)(m + 1) * ldv);
+        cv.take<double>(gmres_ws_doubles(m));
+        cv.take<double>(gemv_partials(n) + 64);
+        cv.take<unsigned>(4);
+        cv.take<double>(8);
+        cv.take<char>(trsv_work_bytes(n, false));
+        bytes = cv.off + 256;
+    }
+    void* wk = nullptr;
+    NL_CUDA_OK(cudaMallocAsync(&wk, bytes, st));
+    NL_CUDA_OK(cudaMemsetAsync(wk, 0, bytes, st));
+    double* pin = nullptr;
+    if (cudaMallocHost((void**)&pin, 64) != cudaSuccess) {
+        cudaFreeAsync(wk, st);
+        set_error("nl_linsolve16: pinned allocation failed");
+        return NL_ENOMEM;
+    }
+    Carver cv(wk);
+    LinBufs B;
+    B.r = cv.take<float>(ldv);
+    B.d = cv.take<float>(ldv);
+    B.t = cv.take<float>(ldv);
+    B.w = cv.take<float>(ldv);
+    B.ubest = cv.take<float>(ldv);
+    B.V = cv.take<float>((size_t)(m + 1) * ldv);
+    B.ldv = ldv;
+    B.gws = cv.take<double>(gmres_ws_doubles(m));
+    B.partial = cv.take<double>(gemv_partials(n) + 64);
+    B.counter = cv.take<unsigned>(4);
+    B.dscal = cv.take<double>(8);
+    TrsvWork tw;
+    trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &tw);
+    int launches = 0;
+    Host H{pin, st, &launches};
+    int epoch = 0;
+    LinResult lr;
+    nl_status s = trsv_prepare16(n, (const __half*)LU16, ld16, ipiv, tw, st, &launches);
+    if (s == NL_OK)
+        s = linsolve16(n, J32, ld32, (const __half*)LU16, ld16, tw, epoch, b, u, eta, maxit, solver, m, gtol, gcycles,
+                       B, H, &lr);
+    unsigned e = 0;
+    cudaMemcpyAsync(&e, tw.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(wk, st);
+    cudaStreamSynchronize(st);
+    cudaFreeHost(pin);
+    if (s == NL_OK && e) {
+        set_error("triangular solve: bounded wait gave up");
+        return NL_ETIMEOUT;
+    }
+    if (stats_host) {
+        stats_host[0] = lr.iters;
+        stats_host[1] = lr.outer;
+        stats_host[2] = lr.failed;
+        stats_host[3] = lr.converged;
+    }
+    if (relres_host) *relres_host = lr.relres;
+    return s;
+}
+
+}  // extern "C"

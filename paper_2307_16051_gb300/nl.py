@@ -1,0 +1,247 @@
+"""ctypes binding of libnewton3p.so (the C ABI in include/newton3p.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Device arrays may be passed as torch tensors (their
+``data_ptr()`` is used) or as integer addresses.  If the library cannot be
+loaded the first call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+NL_OK, NL_EINVAL, NL_ENOMEM, NL_ENOTCONV, NL_ESINGULAR, NL_ENUMERIC, NL_ETIMEOUT, NL_ECUDA = range(8)
+STATUS_NAMES = ["NL_OK", "NL_EINVAL", "NL_ENOMEM", "NL_ENOTCONV", "NL_ESINGULAR", "NL_ENUMERIC", "NL_ETIMEOUT",
+                "NL_ECUDA"]
+NL_FP64LU, NL_IR16, NL_GMRESIR16 = 0, 1, 2
+MODES = {"FP64LU": NL_FP64LU, "IR16": NL_IR16, "GMRESIR16": NL_GMRESIR16}
+MAX_HIST = 128
+
+
+class NLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {msg}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("eta_j", ctypes.c_double), ("ir_maxit", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+                ("gmres_tol", ctypes.c_double), ("gmres_maxcycles", ctypes.c_int), ("newton_maxit", ctypes.c_int),
+                ("tau_a", ctypes.c_double), ("lu_nb", ctypes.c_int), ("trailing_gemm", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("mode", ctypes.c_int), ("newton_iters", ctypes.c_int),
+                ("lu_nb", ctypes.c_int), ("fnorm0", ctypes.c_double), ("fnorm", ctypes.c_double),
+                ("hist", ctypes.c_double * MAX_HIST), ("lin_iters", ctypes.c_int * MAX_HIST),
+                ("lin_outer", ctypes.c_int * MAX_HIST), ("lin_failed", ctypes.c_int * MAX_HIST),
+                ("lin_relres", ctypes.c_double * MAX_HIST), ("t_total_ms", ctypes.c_double),
+                ("t_f_ms", ctypes.c_double), ("t_jac_ms", ctypes.c_double), ("t_lu_ms", ctypes.c_double),
+                ("t_lin_ms", ctypes.c_double), ("gpu_launches", ctypes.c_int), ("reserved", ctypes.c_int * 15)]
+
+
+_lock = threading.Lock()
+_lib = None
+_P = ctypes.c_void_p
+_i64, _dbl, _int = ctypes.c_int64, ctypes.c_double, ctypes.c_int
+
+# name -> (restype, argtypes); kept in the order of include/newton3p.h
+SIGNATURES = {
+    "nl_config_default": (_int, [ctypes.POINTER(Config)]),
+    "nl_create": (_int, [_i64, _dbl, ctypes.POINTER(Config), ctypes.POINTER(_P)]),
+    "nl_set_stream": (_int, [_P, _P]),
+    "nl_solve": (_int, [_P, _P, _dbl, _int, _P]),
+    "nl_solve_device": (_int, [_P, _P, _dbl, _int, _P]),
+    "nl_stats": (_int, [_P, ctypes.POINTER(Stats)]),
+    "nl_device_bytes": (_i64, [_P]),
+    "nl_destroy": (None, [_P]),
+    "nl_last_error": (ctypes.c_char_p, []),
+    "nl_version": (ctypes.c_char_p, []),
+    "nl_k_residual": (_int, [_i64, _dbl, _P, _P, _int, _dbl, _P, _P, _P, _P, _P]),
+    "nl_k_jacobian": (_int, [_i64, _dbl, _P, _P, _i64, _P, _i64, _P]),
+    "nl_k_jacobian64": (_int, [_i64, _dbl, _P, _P, _i64, _P]),
+    "nl_lu16": (_int, [_i64, _P, _i64, _P, _int, _int, ctypes.POINTER(ctypes.c_int32), _P]),
+    "nl_lu64": (_int, [_i64, _P, _i64, _P, _int, ctypes.POINTER(ctypes.c_int32), _P]),
+    "nl_lusolve16": (_int, [_i64, _P, _i64, _P, _P, _P]),
+    "nl_lusolve64": (_int, [_i64, _P, _i64, _P, _P, _P]),
+    "nl_k_gemv_residual": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
+    "nl_k_gemm16_update": (_int, [_i64, _i64, _i64, _P, _i64, _P, _i64, _P, _i64, _int, _P]),
+    "nl_linsolve16": (_int, [_i64, _P, _i64, _P, _i64, _P, _P, _P, _dbl, _int, _int, _int, _dbl, _int,
+                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _P]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libnewton3p.so (building it in-tree if missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise NLError(NL_ECUDA, f"CUDA library not found at {path}")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype, f.argtypes = res, args
+            _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().nl_last_error().decode()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def check(status, allow=()):
+    if status != NL_OK and status not in allow:
+        raise NLError(status, last_error())
+    return status
+
+
+def config(**kw) -> Config:
+    c = Config()
+    check(lib().nl_config_default(ctypes.byref(c)))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+class Solver:
+    """Owns one nl_solver handle (device state for one (N, c) problem)."""
+
+    def __init__(self, N: int, c: float, stream=None, **cfg):
+        self._h = _P()
+        check(lib().nl_create(int(N), float(c), ctypes.byref(config(**cfg)), ctypes.byref(self._h)))
+        self.N, self.c = int(N), float(c)
+        if stream is not None:
+            check(lib().nl_set_stream(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().nl_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, tol=1e-10, mode="GMRESIR16", x0=None):
+        """Host-memory solve (nl_solve).  Returns (x, status)."""
+        x = np.empty(self.N)
+        x0p = None
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            x0p = x0.ctypes.data
+        st = lib().nl_solve(self._h, x0p, float(tol), MODES[mode] if isinstance(mode, str) else int(mode),
+                            x.ctypes.data)
+        check(st, allow=(NL_ENOTCONV,))
+        return x, st
+
+    def solve_device(self, x_out, tol=1e-10, mode="GMRESIR16", x0=None):
+        st = lib().nl_solve_device(self._h, _ptr(x0), float(tol), MODES[mode] if isinstance(mode, str) else int(mode),
+                                   _ptr(x_out))
+        return check(st, allow=(NL_ENOTCONV,))
+
+    def stats(self) -> dict:
+        s = Stats()
+        check(lib().nl_stats(self._h, ctypes.byref(s)))
+        n = s.newton_iters
+        return dict(status=s.status, mode=s.mode, newton_iters=n, lu_nb=s.lu_nb, fnorm0=s.fnorm0, fnorm=s.fnorm,
+                    hist=list(s.hist[: n + 1]), lin_iters=list(s.lin_iters[:n]), lin_outer=list(s.lin_outer[:n]),
+                    lin_failed=list(s.lin_failed[:n]), lin_relres=list(s.lin_relres[:n]),
+                    t_total_ms=s.t_total_ms, t_f_ms=s.t_f_ms, t_jac_ms=s.t_jac_ms, t_lu_ms=s.t_lu_ms,
+                    t_lin_ms=s.t_lin_ms, gpu_launches=s.gpu_launches)
+
+    def device_bytes(self) -> int:
+        return lib().nl_device_bytes(self._h)
+
+
+# ---------------------------------------------------------------- kernels --
+
+def k_residual(N, c, x, F, r, fnorm, u=None, u_is_double=False, scale=0.0, x_out=None, stream=None):
+    return check(lib().nl_k_residual(N, c, _ptr(x), _ptr(u), int(u_is_double), float(scale), _ptr(x_out), _ptr(F),
+                                     _ptr(r), _ptr(fnorm), _stream(stream)))
+
+
+def k_jacobian(N, c, r, J32, ld32, J16, ld16, stream=None):
+    return check(lib().nl_k_jacobian(N, c, _ptr(r), _ptr(J32), ld32, _ptr(J16), ld16, _stream(stream)))
+
+
+def k_jacobian64(N, c, r, J64, ld, stream=None):
+    return check(lib().nl_k_jacobian64(N, c, _ptr(r), _ptr(J64), ld, _stream(stream)))
+
+
+def lu16(N, A16, ld, ipiv, nb=0, gemm=0, stream=None):
+    info = ctypes.c_int32(0)
+    st = lib().nl_lu16(N, _ptr(A16), ld, _ptr(ipiv), nb, gemm, ctypes.byref(info), _stream(stream))
+    check(st, allow=(NL_ESINGULAR,))
+    return info.value
+
+
+def lu64(N, A, ld, ipiv, nb=0, stream=None):
+    info = ctypes.c_int32(0)
+    st = lib().nl_lu64(N, _ptr(A), ld, _ptr(ipiv), nb, ctypes.byref(info), _stream(stream))
+    check(st, allow=(NL_ESINGULAR,))
+    return info.value
+
+
+def lusolve16(N, LU16, ld, ipiv, b, stream=None):
+    return check(lib().nl_lusolve16(N, _ptr(LU16), ld, _ptr(ipiv), _ptr(b), _stream(stream)))
+
+
+def lusolve64(N, LU, ld, ipiv, b, stream=None):
+    return check(lib().nl_lusolve64(N, _ptr(LU), ld, _ptr(ipiv), _ptr(b), _stream(stream)))
+
+
+def k_gemv_residual(N, A, ld, b, u, r, rnorm, stream=None):
+    return check(lib().nl_k_gemv_residual(N, _ptr(A), ld, _ptr(b), _ptr(u), _ptr(r), _ptr(rnorm), _stream(stream)))
+
+
+def k_gemm16_update(M, Nc, K, A, lda, B, ldb, C, ldc, gemm=1, stream=None):
+    return check(lib().nl_k_gemm16_update(M, Nc, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, gemm, _stream(stream)))
+
+
+def linsolve16(N, J32, ld32, LU16, ld16, ipiv, b, u, eta=1e-4, maxit=20, solver=0, m=30, gtol=1e-4, gcycles=10,
+               stream=None):
+    stats = (ctypes.c_int32 * 4)()
+    rel = ctypes.c_double(0.0)
+    check(lib().nl_linsolve16(N, _ptr(J32), ld32, _ptr(LU16), ld16, _ptr(ipiv), _ptr(b), _ptr(u), eta, maxit, solver,
+                              m, gtol, gcycles, stats, ctypes.byref(rel), _stream(stream)))
+    return dict(iters=stats[0], outer=stats[1], failed=stats[2], converged=stats[3], relres=rel.value)

@@ -1,0 +1,65 @@
+"""CPU-side checks of the C-ABI library: it builds for sm_103a, loads, and
+exports every entry point that include/newton3p.h declares; argument
+validation and the no-device path return the documented statuses."""
+import os
+import re
+
+import pytest
+
+from paper_2307_16051_gb300 import nl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:[\w\s\*]+?)\b(nl_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ("nl_create", "nl_solve", "nl_stats", "nl_destroy", "nl_lu16", "nl_lusolve16", "nl_linsolve16"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = nl.lib()
+    missing = [n for n in declared_symbols() if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(declared_symbols()) <= set(nl.SIGNATURES), "binding lacks a signature"
+
+
+def test_version_and_defaults():
+    L = nl.lib()
+    assert b"sm_103a" in L.nl_version()
+    c = nl.config()
+    assert c.eta_j == 1e-4 and c.ir_maxit == 20 and c.gmres_restart == 30 and c.gmres_tol == 1e-4
+    assert c.newton_maxit == 30 and c.tau_a == 0.0
+
+
+def test_invalid_arguments_rejected_before_device_use():
+    L = nl.lib()
+    h = nl._P()
+    for N, c in [(0, 0.5), (-3, 0.5), (10, 1.0), (10, -0.1), (10, float("nan")), (40000, 0.5)]:
+        assert L.nl_create(N, c, None, nl.ctypes.byref(h)) == nl.NL_EINVAL
+    assert L.nl_create(10, 0.5, None, None) == nl.NL_EINVAL
+    assert L.nl_solve(None, None, 1e-10, 1, None) == nl.NL_EINVAL
+    assert L.nl_config_default(None) == nl.NL_EINVAL
+    assert L.nl_stats(None, None) == nl.NL_EINVAL
+    assert "bad" in nl.last_error() or "NULL" in nl.last_error()
+    L.nl_destroy(None)  # no-op
+
+
+def test_no_device_is_an_error_not_a_fallback():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = nl._P()
+    assert nl.lib().nl_create(64, 0.5, None, nl.ctypes.byref(h)) == nl.NL_ECUDA
+    with pytest.raises(nl.NLError):
+        nl.Solver(64, 0.5)

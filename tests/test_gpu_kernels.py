@@ -1,0 +1,279 @@
+"""Kernel-level parity of the CUDA path (through the C ABI) against the CPU
+oracle, on seeded inputs spanning several tiles and ragged tails."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2307_16051_gb300 import nl
+from paper_2307_16051_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch.device("cuda:0")
+
+
+def T(a, dtype=None):
+    return torch.as_tensor(np.ascontiguousarray(a), device=dev(), dtype=dtype)
+
+
+def ulp32(x):
+    x = np.abs(np.asarray(x, np.float32))
+    return np.spacing(np.maximum(x, np.float32(2.0 ** -126)))
+
+
+# ---------------------------------------------------------------- K1 / K2 --
+
+@pytest.mark.parametrize("N", [1, 7, 100, 517, 2048])
+@pytest.mark.parametrize("c", [0.5, 0.99])
+def test_residual_matches_oracle(N, c):
+    g = np.random.default_rng(N)
+    x = 1.0 + g.uniform(0.0, 1.0, N)
+    u = g.standard_normal(N).astype(np.float32)
+    scale = 0.37
+    F = torch.empty(N, device=dev(), dtype=torch.float64)
+    r = torch.empty_like(F)
+    xo = torch.empty_like(F)
+    fn = torch.empty(1, device=dev(), dtype=torch.float64)
+    # plain evaluation
+    nl.k_residual(N, c, T(x), F, r, fn)
+    Fo = O.F(N, c, x)
+    assert np.allclose(F.cpu().numpy(), Fo, rtol=1e-12, atol=1e-13)
+    assert abs(fn.item() - np.linalg.norm(Fo)) <= 1e-12 * max(1.0, np.linalg.norm(Fo))
+    # fused update x + scale * u
+    nl.k_residual(N, c, T(x), F, r, fn, u=T(u), scale=scale, x_out=xo)
+    xn = x + scale * u.astype(np.float64)
+    assert np.array_equal(xo.cpu().numpy(), xn)
+    Fo = O.F(N, c, xn)
+    assert np.allclose(F.cpu().numpy(), Fo, rtol=1e-12, atol=1e-13)
+    # r_i = 1/(1 - t_i) is what the Jacobian needs: F = x - r
+    assert np.allclose(r.cpu().numpy(), xn - Fo, rtol=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 9, 130, 1000])
+def test_jacobian_matches_oracle(N):
+    c = 0.99
+    g = np.random.default_rng(10 + N)
+    x = 1.0 + g.uniform(0.0, 1.0, N)
+    ld = ((N + 63) // 64) * 64
+    F = torch.empty(N, device=dev(), dtype=torch.float64)
+    r = torch.empty_like(F)
+    fn = torch.empty(1, device=dev(), dtype=torch.float64)
+    nl.k_residual(N, c, T(x), F, r, fn)
+    J32 = torch.full((N, ld), 7.0, device=dev(), dtype=torch.float32)
+    J16 = torch.full((N, ld), 7.0, device=dev(), dtype=torch.float16)
+    nl.k_jacobian(N, c, r, J32, ld, J16, ld)
+    J32h = J32.cpu().numpy()
+    J16h = J16.cpu().numpy()
+    Jo = O.jacobian(N, c, x)
+    ref32 = Jo.astype(np.float32)
+    # single-precision formation: within 2 units in the last place of the
+    # correctly rounded value (eq. (2.1): error O(u_s))
+    err = np.abs(J32h[:, :N].astype(np.float64) - ref32.astype(np.float64))
+    assert np.all(err <= 2 * ulp32(ref32) + 1e-30)
+    # J_h = I_s^h(J32) exactly (round to nearest even, Section 2)
+    bits = O.f16_bits_from_f32(J32h[:, :N])
+    assert np.array_equal(bits.reshape(N, N), J16h[:, :N].view(np.uint16))
+    assert np.all(J32h[:, N:] == 0) and np.all(J16h[:, N:] == 0)
+    J64 = torch.full((N, ld), 7.0, device=dev(), dtype=torch.float64)
+    nl.k_jacobian64(N, c, r, J64, ld)
+    assert np.allclose(J64.cpu().numpy()[:, :N], Jo, rtol=4e-16 * 8, atol=1e-18)
+
+
+# -------------------------------------------------------------- K3: LU16 --
+
+def _lu16_gpu(A16, nb, gemm):
+    N = A16.shape[0]
+    ld = ((N + 63) // 64) * 64
+    Ad = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    Ad[:, :N] = T(A16.astype(np.float16))
+    ipiv = torch.empty(N, device=dev(), dtype=torch.int32)
+    info = nl.lu16(N, Ad, ld, ipiv, nb=nb, gemm=gemm)
+    return Ad.cpu().numpy()[:, :N].astype(np.float64), ipiv.cpu().numpy(), info
+
+
+@pytest.mark.parametrize("N,nb", [(1, 16), (16, 16), (37, 16), (100, 32), (200, 64), (333, 128), (517, 128)])
+def test_lu16_simt_bit_exact_vs_oracle(N, nb):
+    """SIMT trailing update: the GPU factorisation is operation-for-operation
+    the oracle's binary16-storage / binary32-arithmetic elimination."""
+    A, _ = W.pivot_forcing_matrix(N, 1000 + N)
+    A16 = O.fl16(A)
+    LU, ipiv, info = _lu16_gpu(A16, nb, 1)
+    LUo, ipivo, infoo, _ = O.lu16_dev(A16, nb)
+    assert info == infoo == 0
+    assert np.array_equal(ipiv, ipivo)
+    assert np.array_equal(LU, LUo)
+
+
+def test_lu16_simt_bit_exact_on_jacobian():
+    N, c = 600, 0.99
+    x = np.ones(N)
+    J16 = O.fl16(O.jacobian(N, c, x).astype(np.float32).astype(np.float64))
+    LU, ipiv, _ = _lu16_gpu(J16, 128, 1)
+    LUo, ipivo, _, _ = O.lu16_dev(J16, 128)
+    assert np.array_equal(ipiv, ipivo) and np.array_equal(LU, LUo)
+
+
+def test_lu16_random_pivoting_valid():
+    """Gaussian matrices (near-ties possible): pivots are a valid partial
+    pivoting sequence and P A = L U to binary16 accuracy."""
+    N = 300
+    A16 = O.fl16(W.random_matrix(N, 77))
+    LU, ipiv, info = _lu16_gpu(A16, 64, 1)
+    assert info == 0
+    L = np.tril(LU, -1) + np.eye(N)
+    U = np.triu(LU)
+    PA = A16.copy()
+    for k, p in enumerate(ipiv):
+        PA[[k, p]] = PA[[p, k]]
+    assert np.max(np.abs(L)) <= 1.0
+    rel = np.linalg.norm(PA - L @ U) / np.linalg.norm(A16)
+    assert rel <= 0.05 * np.sqrt(N) * 2.0 ** -11 * 10
+
+
+@pytest.mark.parametrize("N,nb", [(200, 64), (517, 128), (1024, 128), (777, 64)])
+def test_lu16_tensor_core_close_to_oracle(N, nb):
+    """tcgen05 trailing update: same pivots, factors within binary16
+    rounding of the oracle (the tensor cores sum the K products in their own
+    order, so a few entries round to the neighbouring binary16 value)."""
+    A, _ = W.pivot_forcing_matrix(N, 2000 + N)
+    A16 = O.fl16(A)
+    LU, ipiv, info = _lu16_gpu(A16, nb, 2)
+    LUo, ipivo, _, _ = O.lu16_dev(A16, nb)
+    assert info == 0 and np.array_equal(ipiv, ipivo)
+    scale = np.maximum(np.abs(LUo), np.abs(np.diag(LUo)).max() * 2.0 ** -11)
+    assert np.max(np.abs(LU - LUo) / scale) <= 8 * 2.0 ** -11
+    assert np.mean(LU == LUo) >= 0.95
+
+
+def test_lu16_zero_column_reports_info():
+    N = 40
+    A, _ = W.pivot_forcing_matrix(N, 5)
+    A[:, 17] = 0.0
+    A16 = O.fl16(A)
+    _, _, info = _lu16_gpu(A16, 16, 1)
+    _, _, infoo, _ = O.lu16_dev(A16, 16)
+    assert info == infoo == 18
+
+
+# ------------------------------------------------------------ GEMM update --
+
+@pytest.mark.parametrize("M,Nc,K", [(64, 64, 64), (300, 200, 128), (129, 1000, 256), (1, 5, 64)])
+def test_gemm16_update(M, Nc, K):
+    g = np.random.default_rng(M * 7 + Nc)
+    A = g.uniform(-1, 1, (M, K)).astype(np.float16)
+    B = g.uniform(-1, 1, (K, Nc)).astype(np.float16)
+    C = g.uniform(-4, 4, (M, Nc)).astype(np.float16)
+    ld = lambda n: ((n + 63) // 64) * 64
+    res = {}
+    for gemm in (1, 2):
+        Ad = torch.zeros((M, ld(K)), device=dev(), dtype=torch.float16)
+        Bd = torch.zeros((K, ld(Nc)), device=dev(), dtype=torch.float16)
+        Cd = torch.zeros((M, ld(Nc)), device=dev(), dtype=torch.float16)
+        Ad[:, :K] = T(A)
+        Bd[:, :Nc] = T(B)
+        Cd[:, :Nc] = T(C)
+        nl.k_gemm16_update(M, Nc, K, Ad, ld(K), Bd, ld(Nc), Cd, ld(Nc), gemm=gemm)
+        res[gemm] = Cd.cpu().numpy()[:, :Nc]
+    # SIMT: sequential single-precision fused multiply-adds (the product of two
+    # binary16 numbers is exact in single, so this is a - a_k b_k rounded)
+    acc = C.astype(np.float32)
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    for k in range(K):
+        acc = (acc - A32[:, k:k + 1] * B32[k:k + 1, :]).astype(np.float32)
+    assert np.array_equal(res[1], acc.astype(np.float16))
+    exact = C.astype(np.float64) - A.astype(np.float64) @ B.astype(np.float64)
+    tol = np.abs(exact) * 2.0 ** -10 + K * 2.0 ** -20 * 4
+    assert np.all(np.abs(res[2].astype(np.float64) - exact) <= tol)
+
+
+# -------------------------------------------------------------- K4 / K7 --
+
+@pytest.mark.parametrize("N", [1, 5, 64, 100, 333, 1000])
+def test_lusolve16_matches_oracle_fly(N):
+    A, _ = W.pivot_forcing_matrix(N, 3000 + N)
+    A16 = O.fl16(A)
+    LUo, ipivo, _, _ = O.lu16_dev(A16, 64)
+    b = W.random_vector(N, 4000 + N).astype(np.float32)
+    ref = O.lusolve_fly(LUo, ipivo, b).astype(np.float64)
+    ld = ((N + 63) // 64) * 64
+    LUd = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    LUd[:, :N] = T(LUo.astype(np.float16))
+    bd = T(b)
+    nl.lusolve16(N, LUd, ld, T(ipivo.astype(np.int32)), bd)
+    got = bd.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("N,nb", [(1, 16), (50, 16), (200, 64), (301, 64)])
+def test_lu64_and_solve_match_oracle(N, nb):
+    A = W.random_matrix(N, 5000 + N)
+    ld = ((N + 63) // 64) * 64
+    Ad = torch.zeros((N, ld), device=dev(), dtype=torch.float64)
+    Ad[:, :N] = T(A)
+    ipiv = torch.empty(N, device=dev(), dtype=torch.int32)
+    info = nl.lu64(N, Ad, ld, ipiv, nb=nb)
+    LUo, ipivo, infoo = O.lu64(A)
+    assert info == infoo == 0
+    assert np.array_equal(ipiv.cpu().numpy(), ipivo)
+    LU = Ad.cpu().numpy()[:, :N]
+    assert np.max(np.abs(LU - LUo)) <= 1e-11 * max(1.0, np.max(np.abs(LUo)))
+    b = W.random_vector(N, 6000 + N)
+    bd = T(b)
+    nl.lusolve64(N, Ad, ld, ipiv, bd)
+    ref = O.lusolve64(LUo, ipivo, b)
+    assert np.linalg.norm(bd.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref) * max(1, np.linalg.cond(A) / 1e3)
+
+
+# ------------------------------------------------------------ K5 / IR / GMRES
+
+@pytest.mark.parametrize("N", [3, 256, 1001])
+def test_gemv_residual(N):
+    g = np.random.default_rng(N)
+    A = g.standard_normal((N, N)).astype(np.float32)
+    u = g.standard_normal(N).astype(np.float32)
+    b = g.standard_normal(N).astype(np.float32)
+    ld = ((N + 63) // 64) * 64
+    Ad = torch.zeros((N, ld), device=dev(), dtype=torch.float32)
+    Ad[:, :N] = T(A)
+    ud = torch.zeros(ld, device=dev(), dtype=torch.float32)
+    ud[:N] = T(u)
+    r = torch.empty(N, device=dev(), dtype=torch.float32)
+    rn = torch.empty(1, device=dev(), dtype=torch.float64)
+    nl.k_gemv_residual(N, Ad, ld, T(b), ud, r, rn)
+    exact = b.astype(np.float64) - A.astype(np.float64) @ u.astype(np.float64)
+    bound = 2 * N * 2.0 ** -24 * (np.abs(A).astype(np.float64) @ np.abs(u) + np.abs(b))
+    got = r.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - exact) <= bound)
+    assert abs(rn.item() - np.linalg.norm(got)) <= 1e-12 * np.linalg.norm(got)
+
+
+@pytest.mark.parametrize("solver", [0, 2])
+@pytest.mark.parametrize("N,c", [(300, 0.9), (1000, 0.99)])
+def test_linsolve16_matches_oracle(solver, N, c):
+    """IR and GMRES-IR with identical inputs (J32, binary16 factors, b):
+    same outcome, iteration counts within one, solutions within eta."""
+    x = np.ones(N)
+    J = O.jacobian(N, c, x)
+    J32 = J.astype(np.float32)
+    LUo, ipivo, _, _ = O.lu16_dev(O.fl16(J32.astype(np.float64)), 128)
+    F = O.F(N, c, x)
+    b = (-F / np.linalg.norm(F)).astype(np.float32)
+    eta = 1e-6
+    uo, sto = O.linsolve(J32, LUo, ipivo, b, solver=solver, eta=eta, maxit=20)
+    ld = ((N + 63) // 64) * 64
+    Jd = torch.zeros((N, ld), device=dev(), dtype=torch.float32)
+    Jd[:, :N] = T(J32)
+    LUd = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    LUd[:, :N] = T(LUo.astype(np.float16))
+    ud = torch.zeros(ld, device=dev(), dtype=torch.float32)
+    st = nl.linsolve16(N, Jd, ld, LUd, ld, T(ipivo.astype(np.int32)), T(b), ud, eta=eta, maxit=20, solver=solver)
+    assert st["converged"] == sto["converged"] == 1
+    assert abs(st["iters"] - sto["iters"]) <= 1 and st["failed"] == sto["failed"] == 0
+    got = ud.cpu().numpy()[:N].astype(np.float64)
+    assert np.linalg.norm(got - uo) <= 10 * eta * np.linalg.norm(uo) * np.linalg.cond(J32.astype(np.float64))
+    assert st["relres"] <= eta

@@ -1,0 +1,155 @@
+"""End-to-end parity of the GPU Newton solver (C ABI nl_solve) with the CPU
+oracle: identical Newton iteration counts, linear-iteration counts within
+one per step, and ||x_gpu - x_oracle||_inf / ||x_oracle||_inf <= 1e-10."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2307_16051_gb300 import nl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sweep_n4096.json")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.init()
+
+
+def rel_inf(a, b):
+    return np.max(np.abs(a - b)) / np.max(np.abs(b))
+
+
+def check_counts(st, ro, mode, allow_stall=False):
+    assert st["newton_iters"] == ro["newton_iters"], (st["newton_iters"], ro["newton_iters"])
+    if mode != "FP64LU" and not allow_stall:
+        for a, b in zip(st["lin_iters"], ro["lin_iters"]):
+            assert abs(a - b) <= 1, (st["lin_iters"], ro["lin_iters"])
+
+
+@pytest.mark.parametrize("mode", ["FP64LU", "IR16", "GMRESIR16"])
+def test_small_config_n512_c09(mode):
+    """N = 512, c = 0.9, x0 = ones, eta = 1e-4, tol 1e-10."""
+    N, c = 512, 0.9
+    with nl.Solver(N, c) as s:
+        x, status = s.solve(tol=1e-10, mode=mode)
+        st = s.stats()
+    xo, ro = O.newton(N, c, mode, tol=1e-10)
+    assert status == nl.NL_OK and ro["status"] == 0
+    check_counts(st, ro, mode)
+    assert rel_inf(x, xo) <= 1e-10
+    assert st["hist"][-1] <= 1e-10
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 17, 63, 65, 127, 129, 255, 1000])
+@pytest.mark.parametrize("mode", ["FP64LU", "IR16", "GMRESIR16"])
+def test_ragged_sizes(N, mode):
+    c = 0.99
+    with nl.Solver(N, c) as s:
+        x, status = s.solve(tol=1e-10, mode=mode)
+        st = s.stats()
+    xo, ro = O.newton(N, c, mode, tol=1e-10)
+    assert status == nl.NL_OK
+    check_counts(st, ro, mode)
+    assert rel_inf(x, xo) <= 1e-10
+    if N == 1:
+        assert abs(x[0] - 2 * (1 - math.sqrt(1 - c)) / c) <= 1e-12
+
+
+def test_c_zero_takes_no_step():
+    with nl.Solver(100, 0.0) as s:
+        x, status = s.solve(mode="IR16")
+        assert status == nl.NL_OK and s.stats()["newton_iters"] == 0 and np.all(x == 1.0)
+
+
+def test_nan_start_is_numeric_error():
+    with nl.Solver(64, 0.5) as s:
+        x0 = np.ones(64)
+        x0[3] = np.nan
+        st = nl.lib().nl_solve(s._h, x0.ctypes.data, 1e-10, nl.NL_IR16, np.empty(64).ctypes.data)
+        assert st == nl.NL_ENUMERIC
+
+
+def test_custom_start_and_device_api():
+    N, c = 300, 0.9
+    x0 = np.linspace(0.5, 1.5, N)
+    xo, ro = O.newton(N, c, "GMRESIR16", tol=1e-10, x0=x0)
+    with nl.Solver(N, c) as s:
+        x, _ = s.solve(tol=1e-10, mode="GMRESIR16", x0=x0)
+        xd = torch.empty(N, device="cuda", dtype=torch.float64)
+        st = s.solve_device(xd, tol=1e-10, mode="GMRESIR16", x0=torch.as_tensor(x0, device="cuda"))
+        assert st == nl.NL_OK
+        assert np.array_equal(xd.cpu().numpy(), x)  # same path, bitwise
+        assert s.stats()["newton_iters"] == ro["newton_iters"]
+    assert rel_inf(x, xo) <= 1e-10
+
+
+def test_repeatable_bitwise():
+    with nl.Solver(700, 0.99) as s:
+        a, _ = s.solve(mode="GMRESIR16")
+        b, _ = s.solve(mode="GMRESIR16")
+    assert np.array_equal(a, b)
+
+
+def test_paper_mode_table2_columns_n1024(table2):
+    """eta_J = 1e-6 (Section 3.1): the IR 32-16 and IR-GM histories of the
+    paper's Table 2 (c = .99): steps 1-4 to the printed digits."""
+    from tests.conftest import agrees_4digits
+    for mode, col in (("IR16", "IR32-16"), ("GMRESIR16", "IR-GM"), ("FP64LU", "F64")):
+        with nl.Solver(1024, 0.99, eta_j=1e-6, newton_maxit=10) as s:
+            s.solve(tol=1e-9, mode=mode)
+            h = s.stats()["hist"]
+        p = table2[col]
+        assert len(h) == len(p)
+        for n in range(1, 5):
+            assert agrees_4digits(h[n], p[n]), (mode, n, h[n], p[n])
+
+
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden sweep file not generated")
+@pytest.mark.parametrize("c", [0.5, 0.9, 0.99, 0.9999, 0.999999])
+@pytest.mark.parametrize("mode", ["FP64LU", "IR16", "GMRESIR16"])
+def test_sweep_n4096_vs_golden(c, mode):
+    """Conditioning sweep at N = 4096 against stored oracle results."""
+    gold = json.load(open(GOLDEN))
+    N = gold["N"]
+    ro = gold["cases"][f"{c}/{mode}"]
+    ref = gold["cases"][f"{c}/FP64LU"]
+    with nl.Solver(N, c) as s:
+        x, status = s.solve(tol=1e-10, mode=mode)
+        st = s.stats()
+    stall = mode == "IR16" and c >= 0.9999
+    if ro["status"] == 0 and not stall:
+        assert status == nl.NL_OK
+        check_counts(st, ro, mode)
+        idx = gold["sample_idx"]
+        xs = np.array(ref["x_sample"])
+        assert np.max(np.abs(x[idx] - xs)) / np.max(np.abs(xs)) <= 1e-10
+        assert abs(x.sum() - ref["x_sum"]) <= 1e-10 * abs(ref["x_sum"])
+    # properties that hold at any size: residual and the moment identity
+    F = O.F(N, c, x)
+    if status == nl.NL_OK:
+        assert np.linalg.norm(F) <= 1e-10 * st["fnorm0"] * 1.0001
+        m = c / (2 * N) * x.sum()
+        assert abs(m - (1 - math.sqrt(1 - c))) <= 1e-9 / math.sqrt(1 - c)
+
+
+def test_large_n32768_gmresir():
+    """N = 32768, c = 0.99, GMRES-IR16: the oracle's Newton is too slow here, so
+    the result is checked by properties: the oracle's double-precision
+    residual of the GPU iterate and the moment identity."""
+    N, c = 32768, 0.99
+    with nl.Solver(N, c) as s:
+        x, status = s.solve(tol=1e-10, mode="GMRESIR16")
+        st = s.stats()
+    assert status == nl.NL_OK and st["newton_iters"] == 6
+    F = O.F(N, c, x)
+    assert np.linalg.norm(F) <= 1e-10 * st["fnorm0"] * 1.0001
+    m = c / (2 * N) * x.sum()
+    assert abs(m - (1 - math.sqrt(1 - c))) <= 1e-10
