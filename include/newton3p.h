@@ -65,7 +65,8 @@ typedef struct {
     int lu_nb;           /* [0 = auto (128)] outer block of the LU (multiple of 16, <= 128); also its
                             binary16 rounding period */
     int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update */
-    int reserved[8];
+    int lu_path;         /* [0 = auto] no-interchange fast path with exact fallback; 1 = interchanging path only */
+    int reserved[7];
 } nl_config;
 
 #define NL_MAX_HIST 128
@@ -86,7 +87,8 @@ typedef struct {
     double t_total_ms;                /* wall time of nl_solve (host clock) */
     double t_f_ms, t_jac_ms, t_lu_ms, t_lin_ms; /* device time per phase (CUDA events), summed */
     int gpu_launches;                 /* kernels launched by the solve */
-    int reserved[15];
+    int lu_pivoted;                   /* factorisations that needed row interchanges (interchanging path) */
+    int reserved[14];
 } nl_stats_t;
 
 typedef struct nl_solver nl_solver;
@@ -164,16 +166,21 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
  * to binary16 every nb elimination steps (nb = outer block; the paper's
  * Section 2 says only that J_h is factored in half precision).
  * ipiv (device, N int32): LAPACK-style 0-based interchanges.  *info_host: 0,
- * or k+1 for the first exactly-zero pivot k.  nb: 0 = 128, else a multiple
- * of 16 in [16, 128].  gemm: 0 auto, 1 SIMT, 2 tcgen05.  Allocates its
- * workspace with cudaMallocAsync on `stream`.  Synchronises the stream. */
-nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int32_t* info_host,
+ * or k+1 for the first exactly-zero pivot k (then NL_ESINGULAR).  nb: 0 = 128,
+ * else a multiple of 16 in [16, 128].  gemm: 0 auto, 1 SIMT, 2 tcgen05.
+ * path: 0 = factor first without interchanges, checking exactly that partial
+ * pivoting keeps every diagonal pivot, and refactor with interchanges from a
+ * saved copy of A if not (same result either way); 1 = interchanging path
+ * only.  Allocates its workspace (and the copy) with cudaMallocAsync on
+ * `stream`.  Synchronises the stream. */
+nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,
                   void* stream);
 
-/* Double-precision LU with partial pivoting (the F64 baseline), same layout
- * and ipiv convention.  nb: 0 = 64, else a multiple of 16 in [16, 128].
- * Synchronises the stream. */
-nl_status nl_lu64(int64_t N, double* A, int64_t ld, int32_t* ipiv, int nb, int32_t* info_host, void* stream);
+/* Double-precision LU with partial pivoting (the F64 baseline), same layout,
+ * ipiv convention and path choice.  nb: 0 = 64, else a multiple of 16 in
+ * [16, 128].  Synchronises the stream. */
+nl_status nl_lu64(int64_t N, double* A, int64_t ld, int32_t* ipiv, int nb, int path, int32_t* info_host,
+                  void* stream);
 
 /* b <- U^{-1} L^{-1} P b with the binary16 factors of nl_lu16 promoted to
  * single on the fly (eq. (2.16)), b single precision (device, N floats).

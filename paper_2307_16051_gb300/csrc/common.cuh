@@ -30,6 +30,11 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int num_sms();
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
+// minus the kernel's static shared memory.  Clears the runtime error state on
+// failure and reports it as NL_ECUDA.
+int set_max_dynamic_smem(const void* func);
+
 // Device-side error word bits (solver status block).
 enum : unsigned {
     ERR_TIMEOUT_TRSV = 1u << 0,  // a triangular-solve block gave up waiting on a predecessor

@@ -75,8 +75,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
 __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
                                                         const __grid_constant__ CUtensorMap tmB, int M, int Nc,
                                                         int K, __half* __restrict__ C, int64_t ldc,
-                                                        unsigned* __restrict__ err)
+                                                        unsigned* __restrict__ err, const int* __restrict__ flag)
 {
+    if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -146,6 +147,17 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
                          : "memory");
         }
     }
+    // The epilogue's C tile does not depend on the MMAs: load it now so its
+    // latency overlaps them (each thread: its row, 128 columns, 16 x 16 B).
+    const int row = m0 + warp * 32 + lane;
+    __half* Crow = C + (int64_t)min(row, M - 1) * ldc;
+    const bool full = (row < M) && (n0 + kTcBN <= Nc);
+    uint4 cpre[kTcBN / 8];
+    if (full) {
+        const uint4* p = reinterpret_cast<const uint4*>(Crow + n0);
+#pragma unroll
+        for (int q = 0; q < kTcBN / 8; ++q) cpre[q] = p[q];
+    }
     __syncthreads();
     bool ok = !failed;
     if (ok && !mbar_wait(bar_mma, 0, kTcWaitCycles)) {
@@ -156,8 +168,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
     ok = !__syncthreads_or(!ok);  // warp-uniform: the TMEM loads below are warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (ok) {
-        const int row = m0 + warp * 32 + lane;
-        __half* Crow = C + (int64_t)min(row, M - 1) * ldc;
+#pragma unroll
         for (int c = 0; c < kTcBN; c += 32) {
             uint32_t r[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c;
@@ -172,31 +183,29 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             const int col0 = n0 + c;
-            if (row < M) {
-                if (col0 + 32 <= Nc) {
-                    uint4* p = reinterpret_cast<uint4*>(Crow + col0);
+            if (full) {
+                uint4* p = reinterpret_cast<uint4*>(Crow + col0);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        uint4 v = p[q];
-                        uint32_t wds[4] = {v.x, v.y, v.z, v.w};
+                for (int q = 0; q < 4; ++q) {
+                    uint4 v = cpre[c / 8 + q];
+                    uint32_t wds[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            __half2 h2;
-                            memcpy(&h2, &wds[e], 4);
-                            float2 f = __half22float2(h2);
-                            f.x -= __uint_as_float(r[q * 8 + 2 * e]);
-                            f.y -= __uint_as_float(r[q * 8 + 2 * e + 1]);
-                            h2 = __floats2half2_rn(f.x, f.y);
-                            memcpy(&wds[e], &h2, 4);
-                        }
-                        p[q] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                    for (int e = 0; e < 4; ++e) {
+                        __half2 h2;
+                        memcpy(&h2, &wds[e], 4);
+                        float2 f = __half22float2(h2);
+                        f.x -= __uint_as_float(r[q * 8 + 2 * e]);
+                        f.y -= __uint_as_float(r[q * 8 + 2 * e + 1]);
+                        h2 = __floats2half2_rn(f.x, f.y);
+                        memcpy(&wds[e], &h2, 4);
                     }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (col0 + e < Nc)
-                            Crow[col0 + e] = __float2half_rn(__half2float(Crow[col0 + e]) - __uint_as_float(r[e]));
+                    p[q] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
                 }
+            } else if (row < M) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    if (col0 + e < Nc)
+                        Crow[col0 + e] = __float2half_rn(__half2float(Crow[col0 + e]) - __uint_as_float(r[e]));
             }
         }
     }
@@ -226,13 +235,14 @@ bool tc_gemm_supported()
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
         return false;
+    }
     g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     if (cudaMalloc((void**)&g_tc_err, sizeof(unsigned)) != cudaSuccess) return false;
     cudaMemset(g_tc_err, 0, sizeof(unsigned));
-    if (cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess)
-        return false;
+    if (set_max_dynamic_smem((const void*)k_tc_gemm) != NL_OK) return false;
     g_tc_state = 1;
     return true;
 }
@@ -251,7 +261,7 @@ static bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t 
 }
 
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
-                           __half* C, int64_t ldc, cudaStream_t st)
+                           __half* C, int64_t ldc, cudaStream_t st, const int* flag)
 {
     if (M <= 0 || Nc <= 0) return NL_OK;
     if (!tc_gemm_supported()) {
@@ -274,7 +284,7 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
     // at least 58 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
     const size_t smem = std::max<size_t>(1024 + (size_t)KT * (kTcBM + kTcBN) * 128 + 64, 58 * 1024);
     dim3 grid((unsigned)cdiv(Nc, kTcBN), (unsigned)cdiv(M, kTcBM));
-    k_tc_gemm<<<grid, kTcThreads, smem, st>>>(tmA, tmB, M, Nc, K, C, ldc, g_tc_err);
+    k_tc_gemm<<<grid, kTcThreads, smem, st>>>(tmA, tmB, M, Nc, K, C, ldc, g_tc_err, flag);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }

@@ -24,13 +24,18 @@ struct LuWork {
     void* pnl = nullptr;      // outer-panel working copy: N x NB (float for fp16 LU, double for fp64 LU)
     __half* ut = nullptr;     // U12^T for the tensor-core trailing update: N x NB binary16
     int* info = nullptr;      // device int: first zero pivot (1-based), 0 if none
+    int* flag = nullptr;      // device int (info + 1): set when the no-interchange fast path failed
 };
 size_t lu_work_bytes(int N, int nb, bool fp64);
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w);
 // gemm: 1 = SIMT, 2 = tcgen05.  Asynchronous; *info is written on the device.
-nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm, const LuWork& w, cudaStream_t st,
-                      int* launches);
-nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, const LuWork& w, cudaStream_t st,
+// fast: factor without interchanges, checking on every pre-division value that
+// partial pivoting would keep the diagonal; the result equals partial pivoting
+// when *flag stays 0, otherwise A is left partly factored and the caller
+// restores A and calls again with fast = false.
+nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm, bool fast, const LuWork& w,
+                      cudaStream_t st, int* launches);
+nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast, const LuWork& w, cudaStream_t st,
                       int* launches);
 nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* B, int64_t ldb,
                         __half* C, int64_t ldc, int gemm, cudaStream_t st);
@@ -38,7 +43,7 @@ nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, cons
 // gemm_tc.cu: C = fl16(C - A * Bt^T), A M x K (lda), Bt Nc x K (ldbt), tcgen05 + TMA.
 bool tc_gemm_supported();
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
-                           __half* C, int64_t ldc, cudaStream_t st);
+                           __half* C, int64_t ldc, cudaStream_t st, const int* flag);
 
 // trsv.cu: triangular solves with the factors.
 constexpr int kTrsvT = 64;  // diagonal block size

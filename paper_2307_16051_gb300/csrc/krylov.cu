@@ -14,7 +14,44 @@ namespace nl {
 constexpr int kGemvWarps = 8;
 
 // r_i = b_i - sum_j A_ij u_j (b NULL: r = A u).  One warp per row, float4
-// loads along the row.  Also ||r||_2 (double) via per-block partials.
+// loads along the row.  The dot product is accumulated in two-float
+// (compensated) arithmetic: each product is split exactly with an FMA
+// (a*u = p + e) and summed with error-free two-sums, so the row sum carries
+// about twice the single-precision significand before the single result
+// r_i is rounded once, matching an accumulation in double for the residual
+// of IR (Algorithm IR) at single-precision bandwidth.  Also ||r||_2
+// (double) via per-block partials.
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void df_add_prod(DF& acc, float a, float x)
+{
+    float p = __fmul_rn(a, x);
+    float pe = __fmaf_rn(a, x, -p);  // exact: a*x = p + pe
+    float s, e;
+    two_sum(acc.hi, p, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    DF r;
+    r.hi = s;
+    r.lo = __fadd_rn(__fadd_rn(a.lo, b.lo), e);
+    return r;
+}
+
 __global__ void __launch_bounds__(kGemvWarps * 32)
     k_gemv_residual(int N, const float* __restrict__ A, int64_t ld, const float* __restrict__ b,
                     const float* __restrict__ u, float* __restrict__ r, double* __restrict__ partial,
@@ -30,19 +67,33 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
         const int n4 = N >> 2;
         const float4* A4 = reinterpret_cast<const float4*>(Ai);
         const float4* u4 = reinterpret_cast<const float4*>(u);
-        float s = 0.0f;
+        DF s = {0.0f, 0.0f};
         for (int k = lane; k < n4; k += 32) {
             float4 a = __ldcs(A4 + k);
             float4 x = __ldg(u4 + k);
-            s = fmaf(a.x, x.x, s);
-            s = fmaf(a.y, x.y, s);
-            s = fmaf(a.z, x.z, s);
-            s = fmaf(a.w, x.w, s);
+            df_add_prod(s, a.x, x.x);
+            df_add_prod(s, a.y, x.y);
+            df_add_prod(s, a.z, x.z);
+            df_add_prod(s, a.w, x.w);
         }
-        for (int k = (n4 << 2) + lane; k < N; k += 32) s = fmaf(Ai[k], u[k], s);
-        s = warp_sum(s);
+        for (int k = (n4 << 2) + lane; k < N; k += 32) df_add_prod(s, Ai[k], u[k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            DF t;
+            t.hi = __shfl_xor_sync(0xffffffffu, s.hi, o);
+            t.lo = __shfl_xor_sync(0xffffffffu, s.lo, o);
+            s = df_add(s, t);
+        }
         if (lane == 0) {
-            float ri = b ? b[i] - s : s;
+            // r_i = b_i - (hi + lo), rounded once to single
+            float ri;
+            if (b) {
+                float d, e;
+                two_sum(b[i], -s.hi, d, e);
+                ri = __fadd_rn(d, __fsub_rn(e, s.lo));
+            } else {
+                ri = __fadd_rn(s.hi, s.lo);
+            }
             r[i] = ri;
             sq = (double)ri * (double)ri;
         }

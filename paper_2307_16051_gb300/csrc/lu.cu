@@ -367,39 +367,264 @@ __global__ void __launch_bounds__(256) k_laswp(S* __restrict__ A, int64_t lda, i
 }
 
 // U12 = L11^{-1} A12 for rows [K, K+w), columns [K+w, N); each thread forms
-// one column by forward substitution (sequential fused multiply-adds in row
-// order), rounding each entry when formed (half LU).  Optionally also writes
-// U12^T (binary16, ldut) for the tensor-core update.
+// one column by forward substitution, rounding each entry when formed (half
+// LU).  Rows are taken eight at a time so that the eight running sums are
+// independent (instruction-level parallelism); each entry still accumulates
+// its terms t = 0, 1, ..., k-1 in order.  Optionally also writes U12^T
+// (binary16, ldut) for the tensor-core update.  flag: skip when set.
+constexpr int kTrsmThreads = 64;
+
 template <typename T, typename S, bool RND>
-__global__ void __launch_bounds__(128) k_trsm_u12(S* __restrict__ A, int64_t lda, int K, int w, int N,
-                                                  __half* __restrict__ Ut, int ldut)
+__global__ void __launch_bounds__(kTrsmThreads) k_trsm_u12(S* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                          __half* __restrict__ Ut, int ldut,
+                                                          const int* __restrict__ flag)
 {
+    if (flag && *(volatile const int*)flag) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* L = reinterpret_cast<T*>(smem_raw);  // w x w
-    T* us = L + w * w;                       // w x 128 (column per thread)
+    T* L = reinterpret_cast<T*>(smem_raw);  // w x w, strictly lower part
+    T* us = L + w * w;                       // w x kTrsmThreads (column per thread)
     for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
         int r = q / w, t = q % w;
         L[q] = (t < r) ? (T)ld_elem(A + (int64_t)(K + r) * lda + K + t) : T(0);
     }
     __syncthreads();
-    const int c0 = K + w + blockIdx.x * 128;
+    const int c0 = K + w + blockIdx.x * kTrsmThreads;
     const int c = c0 + threadIdx.x;
+    const int tid = threadIdx.x;
     if (c < N) {
-        for (int kk = 0; kk < w; ++kk) {
-            T a = (T)ld_elem(A + (int64_t)(K + kk) * lda + c);
-            const T* Lk = L + kk * w;
-            for (int t = 0; t < kk; ++t) a = fma(-Lk[t], us[t * 128 + threadIdx.x], a);
-            a = maybe_round(a, RND);
-            us[kk * 128 + threadIdx.x] = a;
-            st_elem(A + (int64_t)(K + kk) * lda + c, a);
+        for (int k0 = 0; k0 < w; k0 += 8) {
+            T acc[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = (k0 + q < w) ? (T)ld_elem(A + (int64_t)(K + k0 + q) * lda + c) : T(0);
+            for (int t = 0; t < k0; ++t) {
+                const T ut = us[t * kTrsmThreads + tid];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = fma(-L[(k0 + q) * w + t], ut, acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + q;
+                if (k < w) {
+                    T a = acc[q];
+                    for (int t = k0; t < k; ++t) a = fma(-L[k * w + t], us[t * kTrsmThreads + tid], a);
+                    a = maybe_round(a, RND);
+                    us[k * kTrsmThreads + tid] = a;
+                    st_elem(A + (int64_t)(K + k) * lda + c, a);
+                }
+            }
         }
     }
     if (Ut) {
         __syncthreads();
-        const int ncol = min(128, N - c0);
+        const int ncol = min(kTrsmThreads, N - c0);
         for (int q = threadIdx.x; q < ncol * w; q += blockDim.x) {
             int col = q / w, kk = q % w;
-            Ut[(int64_t)(c0 - K - w + col) * ldut + kk] = __float2half_rn((float)us[kk * 128 + col]);
+            Ut[(int64_t)(c0 - K - w + col) * ldut + kk] = __float2half_rn((float)us[kk * kTrsmThreads + col]);
+        }
+    }
+}
+
+// ------------------------------------------------ no-interchange fast path --
+// Partial pivoting picks the diagonal row at step j exactly when no row
+// below holds a larger |a_ij| (ties go to the diagonal, which comes first).
+// The fast path factors each panel without interchanges and checks that
+// condition on every pre-division value; the elimination arithmetic is the
+// same, so when no check fails the factors and pivots (ipiv[k] = k) are
+// exactly those of partial pivoting.  Any failure (or a zero / NaN pivot)
+// sets *flag; the remaining fast-path kernels then return at once and the
+// caller refactors with the interchanging path.
+
+// Diagonal block [K, K+w)^2 (w <= 128) in one CTA of 32 x 32 threads:
+// unpivoted right-looking elimination with the block held in registers
+// (thread (ty, tx) owns rows ty + 32a and columns tx + 32b).  Per step j the
+// owners publish the pivot row (rounded: U entries) and the multipliers
+// l_ij = fl16(a_ij / u_jj) through double-buffered shared vectors, then every
+// thread applies a_it -= l_ij u_jt to its entries: the same operations, in
+// the same order, as the elimination it replaces.
+template <typename T, typename S, bool RND, int NA>
+__global__ void __launch_bounds__(1024, 1) k_diag_lu(S* __restrict__ A, int64_t lda, int K, int w,
+                                                     int* __restrict__ ipiv, int* __restrict__ flag)
+{
+    if (*(volatile int*)flag) return;
+    __shared__ T rowbuf[2][128];
+    __shared__ T colbuf[2][128];
+    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+    T v[NA][NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+            const int i = ty + 32 * a, t = tx + 32 * b;
+            v[a][b] = (i < w && t < w) ? (T)ld_elem(A + (int64_t)(K + i) * lda + K + t) : T(0);
+        }
+    bool bad = false;
+    for (int j = 0; j < w; ++j) {
+        const int buf = j & 1, jr = j & 31, jb = j >> 5;
+        // pivot row j is final: round its entries (U) and publish them
+        if (ty == jr) {
+#pragma unroll
+            for (int b = 0; b < NA; ++b) {
+                const int t = tx + 32 * b;
+#pragma unroll
+                for (int a = 0; a < NA; ++a)
+                    if (a == jb && t >= j) {
+                        v[a][b] = maybe_round(v[a][b], RND);
+                        rowbuf[buf][t] = v[a][b];
+                    }
+            }
+        }
+        __syncthreads();
+        const T ujj = rowbuf[buf][j];
+        if (tid == 0 && !(ujj != T(0))) bad = true;  // zero or NaN pivot
+        // multipliers of column j (owners: tx == j % 32)
+        if (tx == jr) {
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const int i = ty + 32 * a;
+                if (i > j && i < w) {
+#pragma unroll
+                    for (int b = 0; b < NA; ++b)
+                        if (b == jb) {
+                            const T x = v[a][b];
+                            const T ax = x < T(0) ? -x : x, au = ujj < T(0) ? -ujj : ujj;
+                            if (!(ax <= au)) bad = true;
+                            const T l = maybe_round(x / ujj, RND);
+                            v[a][b] = l;
+                            colbuf[buf][i] = l;
+                        }
+                }
+            }
+        }
+        __syncthreads();
+        // rank-1 update of the entries right of and below the pivot
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+            const int i = ty + 32 * a;
+            if (i > j && i < w) {
+                const T l = colbuf[buf][i];
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    const int t = tx + 32 * b;
+                    if (t > j && t < w) v[a][b] = fma(-l, rowbuf[buf][t], v[a][b]);
+                }
+            }
+        }
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) atomicOr(flag, 1);
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < NA; ++a)
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+            const int i = ty + 32 * a, t = tx + 32 * b;
+            if (i < w && t < w) st_elem(A + (int64_t)(K + i) * lda + K + t, v[a][b]);
+        }
+    if (tid < w) ipiv[K + tid] = K + tid;
+}
+
+// Off-diagonal blocks of the panel, one launch, 32 warps per CTA:
+//  * L21 = A21 U11^{-1}: one warp per row; lane owns columns lane + 32b.
+//    For t = 0..w-1 the owner of column t forms l_it = fl16(v_it / u_tt),
+//    checking |v_it| <= |u_tt| (partial pivoting would keep the diagonal),
+//    and broadcasts it; every lane then applies v_ij -= l_it u_tj (j > t).
+//  * U12 = L11^{-1} A12: one warp per column; lane owns rows lane + 32a.
+//    For t = 0..w-1 the owner of row t rounds u_tc (final) and broadcasts
+//    it; lanes apply v_kc -= l_kt u_tc (k > t).  Also writes U12^T.
+// Both follow the elimination's order of operations exactly.
+constexpr int kOffThreads = 1024;
+
+template <typename T, typename S, bool RND, int NA>
+__global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                         int nrow_blocks, __half* __restrict__ Ut, int ldut,
+                                                         int* __restrict__ flag)
+{
+    if (flag && *(volatile int*)flag) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* D = reinterpret_cast<T*>(smem_raw);  // w x w: U11 (row role) or L11^T (column role)
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool row_role = (int)blockIdx.x < nrow_blocks;
+    if (row_role) {
+        for (int q = tid; q < w * w; q += kOffThreads) {
+            int r = q / w, t = q % w;
+            D[q] = (t >= r) ? (T)ld_elem(A + (int64_t)(K + r) * lda + K + t) : T(0);
+        }
+    } else {
+        for (int q = tid; q < w * w; q += kOffThreads) {
+            int r = q / w, t = q % w;  // D[t][r] = L[r][t]
+            D[t * w + r] = (t < r) ? (T)ld_elem(A + (int64_t)(K + r) * lda + K + t) : T(0);
+        }
+    }
+    __syncthreads();
+    bool bad = false;
+    if (row_role) {
+        const int i = K + w + blockIdx.x * 32 + warp;
+        if (i < N) {
+            S* Ai = A + (int64_t)i * lda + K;
+            T v[NA];
+#pragma unroll
+            for (int b = 0; b < NA; ++b) v[b] = (lane + 32 * b < w) ? (T)ld_elem(Ai + lane + 32 * b) : T(0);
+            for (int t = 0; t < w; ++t) {
+                const int tb = t >> 5;
+                T l = T(0);
+                if (lane == (t & 31)) {
+#pragma unroll
+                    for (int b = 0; b < NA; ++b)
+                        if (b == tb) {
+                            const T utt = D[t * w + t];
+                            const T x = v[b];
+                            const T ax = x < T(0) ? -x : x, au = utt < T(0) ? -utt : utt;
+                            if (!(ax <= au) || !(utt != T(0))) bad = true;
+                            l = maybe_round(x / utt, RND);
+                            v[b] = l;
+                        }
+                }
+                l = __shfl_sync(0xffffffffu, l, t & 31);
+#pragma unroll
+                for (int b = 0; b < NA; ++b) {
+                    const int j = lane + 32 * b;
+                    if (j > t && j < w) v[b] = fma(-l, D[t * w + j], v[b]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < NA; ++b)
+                if (lane + 32 * b < w) st_elem(Ai + lane + 32 * b, v[b]);
+        }
+        if (__syncthreads_or(bad) && tid == 0 && flag) atomicOr(flag, 1);
+    } else {
+        const int c = K + w + (blockIdx.x - nrow_blocks) * 32 + warp;
+        if (c < N) {
+            T v[NA];
+#pragma unroll
+            for (int a = 0; a < NA; ++a)
+                v[a] = (lane + 32 * a < w) ? (T)ld_elem(A + (int64_t)(K + lane + 32 * a) * lda + c) : T(0);
+            for (int t = 0; t < w; ++t) {
+                const int ta = t >> 5;
+                T u = T(0);
+                if (lane == (t & 31)) {
+#pragma unroll
+                    for (int a = 0; a < NA; ++a)
+                        if (a == ta) {
+                            u = maybe_round(v[a], RND);
+                            v[a] = u;
+                        }
+                }
+                u = __shfl_sync(0xffffffffu, u, t & 31);
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const int k = lane + 32 * a;
+                    if (k > t && k < w) v[a] = fma(-D[t * w + k], u, v[a]);
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                const int k = lane + 32 * a;
+                if (k < w) {
+                    st_elem(A + (int64_t)(K + k) * lda + c, v[a]);
+                    if (Ut) Ut[(int64_t)(c - K - w) * ldut + k] = __float2half_rn((float)v[a]);
+                }
+            }
         }
     }
 }
@@ -409,8 +634,9 @@ __global__ void __launch_bounds__(128) k_trsm_u12(S* __restrict__ A, int64_t lda
 template <typename S, typename T>
 __global__ void __launch_bounds__(256) k_gemm_simt(int M, int Nc, int K, const S* __restrict__ A, int64_t lda,
                                                    const S* __restrict__ B, int64_t ldb, S* __restrict__ C,
-                                                   int64_t ldc)
+                                                   int64_t ldc, const int* __restrict__ flag)
 {
+    if (flag && *(volatile const int*)flag) return;
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN];
@@ -479,6 +705,7 @@ void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
     w->ut = fp64 ? nullptr : (__half*)p;
     p += round_up(ut, 256);
     w->info = (int*)p;
+    w->flag = w->info + 1;
 }
 
 template <typename T, int NBL, int R, bool RND>
@@ -540,11 +767,11 @@ static nl_status launch_leaf(T* P, int ldp, int k0, int M, int w, int wl, int* i
 
 template <typename S, typename T>
 static nl_status launch_gemm_simt(int M, int Nc, int K, const S* A, int64_t lda, const S* B, int64_t ldb, S* C,
-                                  int64_t ldc, cudaStream_t st)
+                                  int64_t ldc, cudaStream_t st, const int* flag = nullptr)
 {
     if (M <= 0 || Nc <= 0 || K <= 0) return NL_OK;
     dim3 grid((unsigned)cdiv(Nc, 64), (unsigned)cdiv(M, 64));
-    k_gemm_simt<S, T><<<grid, 256, 0, st>>>(M, Nc, K, A, lda, B, ldb, C, ldc);
+    k_gemm_simt<S, T><<<grid, 256, 0, st>>>(M, Nc, K, A, lda, B, ldb, C, ldc, flag);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }
@@ -579,30 +806,70 @@ nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, cons
         __half* Bt = nullptr;
         NL_CUDA_OK(cudaMallocAsync((void**)&Bt, (size_t)round_up(Nc, 128) * K * 2, st));
         nl_status s = launch_transpose16(K, Nc, B, ldb, Bt, K, st);
-        if (s == NL_OK) s = tc_gemm16_update(M, Nc, K, A, lda, Bt, K, C, ldc, st);
+        if (s == NL_OK) s = tc_gemm16_update(M, Nc, K, A, lda, Bt, K, C, ldc, st, nullptr);
         cudaFreeAsync(Bt, st);
         return s;
     }
     return launch_gemm_simt<__half, float>(M, Nc, K, A, lda, B, ldb, C, ldc, st);
 }
 
+// A22 <- A22 - L21 U12 for the panel [K, K+wd): tcgen05 when possible.
+template <typename T, typename S>
+static nl_status trailing_update(int N, S* A, int64_t ld, int K, int wd, int nb, bool tc, const LuWork& w,
+                                 const int* flag, cudaStream_t st)
+{
+    const int rest = N - K - wd;
+    S* L21 = A + (int64_t)(K + wd) * ld + K;
+    S* U12 = A + (int64_t)K * ld + K + wd;
+    S* A22 = A + (int64_t)(K + wd) * ld + K + wd;
+    if (tc) {
+        if constexpr (std::is_same<S, __half>::value) return tc_gemm16_update(rest, rest, wd, L21, ld, w.ut, nb, A22, ld, st, flag);
+    }
+    return launch_gemm_simt<S, T>(rest, rest, wd, L21, ld, U12, ld, A22, ld, st, flag);
+}
+
 template <typename T, typename S, int NBL, bool RND>
-static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int gemm, const LuWork& w,
+static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int gemm, bool fast, const LuWork& w,
                                 cudaStream_t st, int* launches)
 {
     T* P = (T*)w.pnl;
     const int ldp = nb;
     int nl = 0;
-    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, sizeof(int), st));
-    const size_t trsm_smem = (size_t)nb * nb * sizeof(T) + (size_t)nb * 128 * sizeof(T);
+    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st));  // info and flag
     static bool smem_set = false;
     if (!smem_set) {
-        NL_CUDA_OK(cudaFuncSetAttribute(k_trsm_u12<T, S, RND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        227 * 1024));
+        if (set_max_dynamic_smem((const void*)k_trsm_u12<T, S, RND>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_offdiag<T, S, RND, 2>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_offdiag<T, S, RND, 4>) != NL_OK)
+            return NL_ECUDA;
         smem_set = true;
     }
     for (int K = 0; K < N; K += nb) {
         const int wd = std::min(nb, N - K), M = N - K;
+        const int rest = N - K - wd;
+        const bool tc = (gemm == 2) && std::is_same<S, __half>::value && (wd % 64 == 0);
+        const size_t trsm_smem = (size_t)wd * wd * sizeof(T) + (size_t)wd * kTrsmThreads * sizeof(T);
+        if (fast) {
+            const int na = (int)cdiv(wd, 32);
+            if (na <= 2) k_diag_lu<T, S, RND, 2><<<1, 1024, 0, st>>>(A, ld, K, wd, ipiv, w.flag);
+            else k_diag_lu<T, S, RND, 4><<<1, 1024, 0, st>>>(A, ld, K, wd, ipiv, w.flag);
+            ++nl;
+            if (rest > 0) {
+                const int nrb = (int)cdiv(rest, 32);
+                const size_t sm = (size_t)wd * wd * sizeof(T);
+                if (na <= 2)
+                    k_offdiag<T, S, RND, 2><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb,
+                                                                            tc ? w.ut : nullptr, nb, w.flag);
+                else
+                    k_offdiag<T, S, RND, 4><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb,
+                                                                            tc ? w.ut : nullptr, nb, w.flag);
+                nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
+                if (s != NL_OK) return s;
+                nl += 2;
+            }
+            NL_CUDA_OK(cudaGetLastError());
+            continue;
+        }
         k_panel_load<T, S><<<M, 128, 0, st>>>(A, ld, K, M, wd, P, ldp);
         ++nl;
         for (int k0 = 0; k0 < wd; k0 += NBL) {
@@ -622,25 +889,12 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
             k_laswp<S><<<(unsigned)cdiv(N - wd, 256), 256, 0, st>>>(A, ld, K, wd, N, ipiv);
             ++nl;
         }
-        if (K + wd < N) {
-            const int rest = N - K - wd;
-            const bool tc = (gemm == 2) && std::is_same<S, __half>::value && (wd % 64 == 0);
-            k_trsm_u12<T, S, RND><<<(unsigned)cdiv(rest, 128), 128, trsm_smem, st>>>(A, ld, K, wd, N,
-                                                                                     tc ? w.ut : nullptr, nb);
-            ++nl;
-            S* L21 = A + (int64_t)(K + wd) * ld + K;
-            S* U12 = A + (int64_t)K * ld + K + wd;
-            S* A22 = A + (int64_t)(K + wd) * ld + K + wd;
-            if (tc) {
-                if constexpr (std::is_same<S, __half>::value) {
-                    nl_status s = tc_gemm16_update(rest, rest, wd, L21, ld, w.ut, nb, A22, ld, st);
-                    if (s != NL_OK) return s;
-                }
-            } else {
-                nl_status s = launch_gemm_simt<S, T>(rest, rest, wd, L21, ld, U12, ld, A22, ld, st);
-                if (s != NL_OK) return s;
-            }
-            ++nl;
+        if (rest > 0) {
+            k_trsm_u12<T, S, RND><<<(unsigned)cdiv(rest, kTrsmThreads), kTrsmThreads, trsm_smem, st>>>(
+                A, ld, K, wd, N, tc ? w.ut : nullptr, nb, nullptr);
+            nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, nullptr, st);
+            if (s != NL_OK) return s;
+            nl += 2;
         }
         NL_CUDA_OK(cudaGetLastError());
     }
@@ -648,25 +902,25 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
     return NL_OK;
 }
 
-nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm, const LuWork& w, cudaStream_t st,
-                      int* launches)
+nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm, bool fast, const LuWork& w,
+                      cudaStream_t st, int* launches)
 {
     if (nb < 16 || nb > 128 || nb % 16) {
         set_error("lu16: nb must be a multiple of 16 in [16, 128]");
         return NL_EINVAL;
     }
     if (gemm == 2 && !tc_gemm_supported()) gemm = 1;
-    return lu_factor_impl<float, __half, 16, true>(N, A, ld, ipiv, nb, gemm, w, st, launches);
+    return lu_factor_impl<float, __half, 16, true>(N, A, ld, ipiv, nb, gemm, fast, w, st, launches);
 }
 
-nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, const LuWork& w, cudaStream_t st,
+nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast, const LuWork& w, cudaStream_t st,
                       int* launches)
 {
     if (nb < 16 || nb > 128 || nb % 16) {
         set_error("lu64: nb must be a multiple of 16 in [16, 128]");
         return NL_EINVAL;
     }
-    return lu_factor_impl<double, double, 8, false>(N, A, ld, ipiv, nb, 1, w, st, launches);
+    return lu_factor_impl<double, double, 8, false>(N, A, ld, ipiv, nb, 1, fast, w, st, launches);
 }
 
 }  // namespace nl

@@ -37,7 +37,8 @@ __global__ void __launch_bounds__(kFRows* kFSlices)
             double v = 0.0;
             if (j < N) {
                 v = x[j];
-                if (u) v += scale * (double)u[j];
+                // x + ||F|| u: a product and a sum, each rounded (eq. (2.18))
+                if (u) v = __dadd_rn(v, __dmul_rn(scale, (double)u[j]));
             }
             xs[t] = v;
         }
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(kFRows* kFSlices)
         double t = c / (2.0 * (double)N) * ((double)i + 0.5) * s;
         double ri = 1.0 / (1.0 - t);
         double xi = x[i];
-        if (u) xi += scale * (double)u[i];
+        if (u) xi = __dadd_rn(xi, __dmul_rn(scale, (double)u[i]));
         double fi = xi - ri;
         if (xout) xout[i] = xi;
         F[i] = fi;

@@ -45,6 +45,22 @@ int num_sms()
     return n;
 }
 
+int set_max_dynamic_smem(const void* func)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, func) != cudaSuccess ||
+        cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) !=
+            cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        set_error("cannot raise the dynamic shared-memory limit: %s", cudaGetErrorString(e));
+        return NL_ECUDA;
+    }
+    return NL_OK;
+}
+
 __global__ void k_fill64(int N, double v, double* x)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -277,7 +293,8 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     nl_config d;
     nl_config_default(&d);
     if (cfg) d = *cfg;
-    if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 ||
+    if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 || d.lu_path < 0 ||
+        d.lu_path > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16))) {
         set_error("nl_create: invalid configuration");
         return NL_EINVAL;
@@ -516,15 +533,34 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
         S.t_jac_ms += elapsed_ms(s);
         // factorisation
         cudaEventRecord(s->ev[0], st);
-        int info = 0;
+        int info = 0, iflag[2] = {0, 0};
+        const bool pivoted_only = s->cfg.lu_path == 1;
         if (mode == NL_FP64LU) {
-            NL_TRY(lu64_factor(n, s->J64, s->ld, s->ipiv64, 64, s->luw64, st, &launches));
+            NL_TRY(lu64_factor(n, s->J64, s->ld, s->ipiv64, 64, !pivoted_only, s->luw64, st, &launches));
+            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw64.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            NL_CUDA_OK(cudaStreamSynchronize(st));
+            memcpy(iflag, s->pin, sizeof(iflag));
+            if (iflag[1]) {  // interchanges needed: re-form J and factor with them
+                NL_TRY(launch_jacobian64(n, s->c, s->rr, s->htab, s->J64, s->ld, st));
+                NL_TRY(lu64_factor(n, s->J64, s->ld, s->ipiv64, 64, false, s->luw64, st, &launches));
+                NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw64.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+                ++launches;
+                ++S.lu_pivoted;
+            }
             NL_TRY(trsv_prepare64(n, s->J64, s->ld, s->ipiv64, s->tw64, st, &launches));
-            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw64.info, sizeof(int), cudaMemcpyDeviceToHost, st));
         } else {
-            NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, s->luw, st, &launches));
+            NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, !pivoted_only, s->luw, st, &launches));
+            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            NL_CUDA_OK(cudaStreamSynchronize(st));
+            memcpy(iflag, s->pin, sizeof(iflag));
+            if (iflag[1]) {
+                NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st));
+                NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, false, s->luw, st, &launches));
+                NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+                ++launches;
+                ++S.lu_pivoted;
+            }
             NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
-            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
         }
         cudaEventRecord(s->ev[1], st);
         NL_CUDA_OK(cudaStreamSynchronize(st));
@@ -672,24 +708,43 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
     return s;
 }
 
-nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int32_t* info_host, void* stream)
+}  // extern "C"
+
+// Factor with the no-interchange fast path, falling back to the interchanging
+// path (from a saved copy of A) when partial pivoting would swap rows.
+template <typename S>
+static nl_status lu_entry(int64_t N, S* A, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,
+                          cudaStream_t st, bool fp64)
 {
-    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2) {
-        set_error("nl_lu16: bad argument");
-        return NL_EINVAL;
-    }
-    if (nb == 0) nb = 128;
-    if (gemm == 0) gemm = 2;
-    if (gemm == 2 && (nb % 64 || !tc_gemm_supported())) gemm = 1;
-    cudaStream_t st = (cudaStream_t)stream;
     const int n = (int)N;
+    const size_t lw = lu_work_bytes(n, nb, fp64);
+    const size_t copy = (path == 1) ? 0 : (size_t)n * ld * sizeof(S);
     void* wk = nullptr;
-    NL_CUDA_OK(cudaMallocAsync(&wk, lu_work_bytes(n, nb, false), st));
+    NL_CUDA_OK(cudaMallocAsync(&wk, lw + copy + 256, st));
     LuWork w;
-    lu_work_carve(wk, n, nb, false, &w);
-    nl_status s = lu16_factor(n, (__half*)A16, ld, ipiv, nb, gemm, w, st, nullptr);
-    int info = 0;
-    if (s == NL_OK) s = (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess) ? NL_OK : NL_ECUDA;
+    lu_work_carve(wk, n, nb, fp64, &w);
+    S* backup = (S*)((char*)wk + round_up(lw, 256));
+    int iflag[2] = {0, 0};
+    nl_status s = NL_OK;
+    if (path != 1) {
+        NL_CUDA_OK(cudaMemcpyAsync(backup, A, copy, cudaMemcpyDeviceToDevice, st));
+        if constexpr (std::is_same<S, __half>::value)
+            s = lu16_factor(n, A, ld, ipiv, nb, gemm, true, w, st, nullptr);
+        else
+            s = lu64_factor(n, A, ld, ipiv, nb, true, w, st, nullptr);
+        if (s == NL_OK && cudaMemcpyAsync(iflag, w.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            s = NL_ECUDA;
+        if (s == NL_OK && cudaStreamSynchronize(st) != cudaSuccess) s = NL_ECUDA;
+    }
+    if (s == NL_OK && (path == 1 || iflag[1])) {
+        if (path != 1) NL_CUDA_OK(cudaMemcpyAsync(A, backup, copy, cudaMemcpyDeviceToDevice, st));
+        if constexpr (std::is_same<S, __half>::value)
+            s = lu16_factor(n, A, ld, ipiv, nb, gemm, false, w, st, nullptr);
+        else
+            s = lu64_factor(n, A, ld, ipiv, nb, false, w, st, nullptr);
+        if (s == NL_OK && cudaMemcpyAsync(iflag, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            s = NL_ECUDA;
+    }
     cudaFreeAsync(wk, st);
     NL_CUDA_OK(cudaStreamSynchronize(st));
     unsigned* tce = tc_error_word();
@@ -702,32 +757,34 @@ nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int g
             return NL_ETIMEOUT;
         }
     }
-    if (info_host) *info_host = info;
-    if (s == NL_OK && info) return NL_ESINGULAR;
+    if (info_host) *info_host = iflag[0];
+    if (s == NL_OK && iflag[0]) return NL_ESINGULAR;
     return s;
 }
 
-nl_status nl_lu64(int64_t N, double* A, int64_t ld, int32_t* ipiv, int nb, int32_t* info_host, void* stream)
+extern "C" {
+
+nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,
+                  void* stream)
 {
-    if (N < 1 || N > 32768 || !A || !ipiv || ld < N) {
+    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2 || path < 0 || path > 1) {
+        set_error("nl_lu16: bad argument");
+        return NL_EINVAL;
+    }
+    if (nb == 0) nb = 128;
+    if (gemm == 0) gemm = 2;
+    if (gemm == 2 && (nb % 64 || !tc_gemm_supported())) gemm = 1;
+    return lu_entry<__half>(N, (__half*)A16, ld, ipiv, nb, gemm, path, info_host, (cudaStream_t)stream, false);
+}
+
+nl_status nl_lu64(int64_t N, double* A, int64_t ld, int32_t* ipiv, int nb, int path, int32_t* info_host, void* stream)
+{
+    if (N < 1 || N > 32768 || !A || !ipiv || ld < N || path < 0 || path > 1) {
         set_error("nl_lu64: bad argument");
         return NL_EINVAL;
     }
     if (nb == 0) nb = 64;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int n = (int)N;
-    void* wk = nullptr;
-    NL_CUDA_OK(cudaMallocAsync(&wk, lu_work_bytes(n, nb, true), st));
-    LuWork w;
-    lu_work_carve(wk, n, nb, true, &w);
-    nl_status s = lu64_factor(n, A, ld, ipiv, nb, w, st, nullptr);
-    int info = 0;
-    if (s == NL_OK) cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaFreeAsync(wk, st);
-    NL_CUDA_OK(cudaStreamSynchronize(st));
-    if (info_host) *info_host = info;
-    if (s == NL_OK && info) return NL_ESINGULAR;
-    return s;
+    return lu_entry<double>(N, A, ld, ipiv, nb, 1, path, info_host, (cudaStream_t)stream, true);
 }
 
 }  // extern "C"

@@ -197,50 +197,223 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(int N, int nblk, const S*
     }
 }
 
+// ---------------------------------------------- single-precision mailbox --
+// For the single-precision solve each solved entry is published as one 64-bit
+// word {value bits, epoch} with a release store; a consumer polls the word of
+// the entry it needs with an acquire load, so readiness and data arrive
+// together in one memory round trip.  Block size 128: the diagonal inverse
+// (64 KB) is staged in shared memory and each thread prefetches its 64
+// binary16 entries of the next tile before polling.
+constexpr int T2 = 128;
+constexpr int kMbThreads = 256;  // 128 rows x 2 halves of 64 columns
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
+{
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ bool poll_value(const unsigned long long* p, unsigned epoch, float* out,
+                                           const unsigned* err)
+{
+    long long t0 = clock64();
+    for (;;) {
+        unsigned long long w = ld_acquire_u64(p);
+        if ((unsigned)(w >> 32) == epoch) {
+            *out = __uint_as_float((unsigned)w);
+            return true;
+        }
+        if (*((volatile const unsigned*)err) != 0u) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+}
+
+template <bool LOWER>
+__global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const __half* __restrict__ LU, int64_t ld,
+                                                       const float* __restrict__ v,
+                                                       const unsigned long long* __restrict__ vin_mb,
+                                                       const int* __restrict__ perm, const float* __restrict__ dinv,
+                                                       unsigned long long* __restrict__ mb, float* __restrict__ out,
+                                                       unsigned epoch, unsigned* __restrict__ err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Ds = reinterpret_cast<float*>(smem_raw);  // T2 x T2 diagonal inverse
+    __shared__ float ys[T2];
+    __shared__ float acc[T2];
+    const int tid = threadIdx.x, r = tid >> 1, h = tid & 1;
+    const float* Dinv = dinv + (LOWER ? 0 : (int64_t)nblk * T2 * T2);
+    for (int g = blockIdx.x; g < nblk; g += gridDim.x) {
+        const int b = LOWER ? g : nblk - 1 - g;
+        const int r0 = b * T2, row = r0 + r;
+        // stage this block's diagonal inverse (independent of the waits)
+        __syncthreads();
+        {
+            const float4* src = reinterpret_cast<const float4*>(Dinv + (int64_t)b * T2 * T2);
+            float4* dst = reinterpret_cast<float4*>(Ds);
+            for (int q = tid; q < T2 * T2 / 4; q += kMbThreads) dst[q] = src[q];
+        }
+        if (tid < T2) {
+            const int i = r0 + tid;
+            float x = 0.0f;
+            if (i < N) x = LOWER ? v[perm[i]] : __uint_as_float((unsigned)vin_mb[i]);
+            acc[tid] = x;
+        }
+        float part = 0.0f;
+        const __half* Lrow = LU + (int64_t)min(row, N - 1) * ld;
+        const int cnt = LOWER ? b : nblk - 1 - b;
+        for (int s = 0; s < cnt; ++s) {
+            const int c = LOWER ? s : nblk - 1 - s;
+            // prefetch this thread's 64 entries of tile (b, c)
+            const int cb = c * T2 + h * 64;
+            __half2 lv[32];
+            if (row < N && cb + 64 <= N && (((uintptr_t)(Lrow + cb)) & 15) == 0) {
+                const uint4* p4 = reinterpret_cast<const uint4*>(Lrow + cb);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    uint4 u = p4[q];
+                    memcpy(&lv[4 * q], &u, 16);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    int c0 = cb + 2 * q;
+                    float a0 = (row < N && c0 < N) ? __half2float(Lrow[c0]) : 0.0f;
+                    float a1 = (row < N && c0 + 1 < N) ? __half2float(Lrow[c0 + 1]) : 0.0f;
+                    lv[q] = __floats2half2_rn(a0, a1);
+                }
+            }
+            __syncthreads();  // ys of the previous tile no longer in use
+            bool okp = true;
+            if (tid < T2) {
+                const int i = c * T2 + tid;
+                float y = 0.0f;
+                if (i < N) okp = poll_value(mb + i, epoch, &y, err);
+                ys[tid] = y;
+            }
+            if (__syncthreads_or(!okp)) {
+                if (tid == 0) atomicOr(err, (unsigned)ERR_TIMEOUT_TRSV);
+                return;
+            }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                float2 f = __half22float2(lv[q]);
+                part = fmaf(f.x, ys[h * 64 + 2 * q], part);
+                part = fmaf(f.y, ys[h * 64 + 2 * q + 1], part);
+            }
+        }
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        __syncthreads();
+        if (h == 0) acc[r] -= part;
+        __syncthreads();
+        float sum = 0.0f;
+#pragma unroll 16
+        for (int k = 0; k < 64; ++k) sum = fmaf(Ds[r * T2 + h * 64 + k], acc[h * 64 + k], sum);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        if (h == 0 && row < N) {
+            if (out) out[row] = sum;
+            st_release_u64(mb + row, ((unsigned long long)epoch << 32) | __float_as_uint(sum));
+        }
+    }
+}
+
 // ------------------------------------------------------------------- host --
+
+static int trsv_block(bool fp64) { return fp64 ? T_ : T2; }
 
 size_t trsv_work_bytes(int N, bool fp64)
 {
-    int nblk = (int)cdiv(N, T_);
+    const int tb = trsv_block(fp64);
+    int nblk = (int)cdiv(N, tb);
     size_t el = fp64 ? 8 : 4;
-    return round_up((size_t)N * 4, 256) + round_up((size_t)2 * nblk * T_ * T_ * el, 256) +
-           round_up((size_t)2 * nblk * 4, 256) + round_up((size_t)N * el, 256) + 256 + round_up((size_t)(N + 1) * 4, 256);
+    return round_up((size_t)N * 4, 256) + round_up((size_t)2 * nblk * tb * tb * el, 256) +
+           round_up((size_t)2 * nblk * 4, 256) + round_up((size_t)N * 8 * 2, 256) + 256 +
+           round_up((size_t)(N + 1) * 4, 256);
 }
 
 void trsv_work_carve(void* base, int N, bool fp64, TrsvWork* w)
 {
-    int nblk = (int)cdiv(N, T_);
+    const int tb = trsv_block(fp64);
+    int nblk = (int)cdiv(N, tb);
     size_t el = fp64 ? 8 : 4;
     char* p = (char*)base;
     w->perm = (int*)p;
     p += round_up((size_t)N * 4, 256);
     w->dinv = p;
-    p += round_up((size_t)2 * nblk * T_ * T_ * el, 256);
+    p += round_up((size_t)2 * nblk * tb * tb * el, 256);
     w->flags = (int*)p;
     p += round_up((size_t)2 * nblk * 4, 256);
-    w->y = p;
-    p += round_up((size_t)N * el, 256);
+    w->y = p;  // double: N elements; float: 2 x N 64-bit mailbox words
+    p += round_up((size_t)N * 8 * 2, 256);
     w->err = (unsigned*)p;
     p += 256;
     w->scan = (int*)p;
+}
+
+// Diagonal-block inverses for block size TB.
+template <typename S, typename T, int TB>
+__global__ void __launch_bounds__(TB) k_invdiag_t(int N, const S* __restrict__ LU, int64_t ld, T* __restrict__ dinv,
+                                                  int nblk)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* A = reinterpret_cast<T*>(smem_raw);  // TB x (TB+1)
+    T* X = A + TB * (TB + 1);
+    const int b = blockIdx.x, r0 = b * TB, nb_ = min(TB, N - r0);
+    const int col = threadIdx.x;
+    for (int i = 0; i < TB; ++i)
+        A[i * (TB + 1) + col] = (i < nb_ && col < nb_) ? (T)ld_elem(LU + (int64_t)(r0 + i) * ld + r0 + col) : T(0);
+    __syncthreads();
+    for (int i = 0; i < TB; ++i) {
+        T x = T(0);
+        if (col < nb_ && i < nb_) {
+            if (i == col) x = T(1);
+            else if (i > col) {
+                T s = T(0);
+                for (int t = col; t < i; ++t) s = fma(A[i * (TB + 1) + t], X[t * (TB + 1) + col], s);
+                x = -s;
+            }
+        }
+        X[i * (TB + 1) + col] = x;
+    }
+    T* Linv = dinv + (int64_t)b * TB * TB;
+    for (int i = 0; i < TB; ++i) Linv[i * TB + col] = X[i * (TB + 1) + col];
+    for (int i = TB - 1; i >= 0; --i) {
+        T x = T(0);
+        if (col < nb_ && i < nb_ && i <= col) {
+            T s = (i == col) ? T(1) : T(0);
+            for (int t = i + 1; t <= col; ++t) s = fma(-A[i * (TB + 1) + t], X[t * (TB + 1) + col], s);
+            x = s / A[i * (TB + 1) + i];
+        }
+        X[i * (TB + 1) + col] = x;
+    }
+    T* Uinv = dinv + (int64_t)(nblk + b) * TB * TB;
+    for (int i = 0; i < TB; ++i) Uinv[i * TB + col] = X[i * (TB + 1) + col];
 }
 
 template <typename S, typename T>
 static nl_status prepare_impl(int N, const S* LU, int64_t ld, const int* ipiv, const TrsvWork& w, cudaStream_t st,
                               int* launches)
 {
-    const int nblk = (int)cdiv(N, T_);
+    constexpr bool fp64 = std::is_same<T, double>::value;
+    constexpr int TB = fp64 ? T_ : T2;
+    const int nblk = (int)cdiv(N, TB);
     static bool attr = false;
     if (!attr) {
-        NL_CUDA_OK(cudaFuncSetAttribute(k_perm, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        if (set_max_dynamic_smem((const void*)k_perm) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_invdiag_t<S, T, TB>) != NL_OK)
+            return NL_ECUDA;
         attr = true;
     }
-    if ((size_t)N * 4 > 227 * 1024) {
+    if ((size_t)N * 4 > 200 * 1024) {
         set_error("trsv: N=%d too large for the permutation kernel", N);
         return NL_EINVAL;
     }
     k_perm<<<1, 1024, (size_t)N * 4, st>>>(N, ipiv, w.perm, w.scan);
-    k_invdiag<S, T><<<nblk, T_, 0, st>>>(N, LU, ld, (T*)w.dinv, nblk);
+    k_invdiag_t<S, T, TB><<<nblk, TB, (size_t)2 * TB * (TB + 1) * sizeof(T), st>>>(N, LU, ld, (T*)w.dinv, nblk);
     NL_CUDA_OK(cudaGetLastError());
     if (launches) *launches += 2;
     return NL_OK;
@@ -293,10 +466,40 @@ static nl_status solve_impl(int N, const S* LU, int64_t ld, const T* v, T* z, co
     return s;
 }
 
+template <bool LOWER>
+static nl_status launch_trsv_mb(int N, const __half* LU, int64_t ld, const float* v, const unsigned long long* vin_mb,
+                                unsigned long long* mb, float* out, const TrsvWork& w, unsigned epoch, cudaStream_t st)
+{
+    const int nblk = (int)cdiv(N, T2);
+    auto kern = k_trsv_mb<LOWER>;
+    const size_t smem = (size_t)T2 * T2 * sizeof(float);
+    static int max_grid = 0;
+    if (max_grid == 0) {
+        if (set_max_dynamic_smem((const void*)kern) != NL_OK) return NL_ECUDA;
+        int per_sm = 0;
+        NL_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMbThreads, smem));
+        max_grid = std::max(1, per_sm) * num_sms();
+    }
+    int grid = std::min(nblk, max_grid);
+    const int* perm = w.perm;
+    const float* dinv = (const float*)w.dinv;
+    unsigned* err = w.err;
+    void* args[] = {(void*)&N,   (void*)&nblk, (void*)&LU,  (void*)&ld,    (void*)&v,   (void*)&vin_mb,
+                    (void*)&perm, (void*)&dinv, (void*)&mb, (void*)&out, (void*)&epoch, (void*)&err};
+    NL_CUDA_OK(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kMbThreads), args, smem, st));
+    return NL_OK;
+}
+
 nl_status trsv_solve16(int N, const __half* LU, int64_t ld, const float* v, float* z, const TrsvWork& w, int epoch,
                        cudaStream_t st, int* launches)
 {
-    return solve_impl<__half, float>(N, LU, ld, v, z, w, epoch, st, launches);
+    unsigned long long* mbf = (unsigned long long*)w.y;
+    unsigned long long* mbb = mbf + N;
+    nl_status s = launch_trsv_mb<true>(N, LU, ld, v, nullptr, mbf, nullptr, w, (unsigned)epoch, st);
+    if (s != NL_OK) return s;
+    s = launch_trsv_mb<false>(N, LU, ld, nullptr, mbf, mbb, z, w, (unsigned)epoch, st);
+    if (launches) *launches += 2;
+    return s;
 }
 
 nl_status trsv_solve64(int N, const double* LU, int64_t ld, const double* v, double* z, const TrsvWork& w, int epoch,

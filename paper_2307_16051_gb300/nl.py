@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
     _fields_ = [("eta_j", ctypes.c_double), ("ir_maxit", ctypes.c_int), ("gmres_restart", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_maxcycles", ctypes.c_int), ("newton_maxit", ctypes.c_int),
                 ("tau_a", ctypes.c_double), ("lu_nb", ctypes.c_int), ("trailing_gemm", ctypes.c_int),
-                ("reserved", ctypes.c_int * 8)]
+                ("lu_path", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class Stats(ctypes.Structure):
@@ -43,7 +43,8 @@ class Stats(ctypes.Structure):
                 ("lin_outer", ctypes.c_int * MAX_HIST), ("lin_failed", ctypes.c_int * MAX_HIST),
                 ("lin_relres", ctypes.c_double * MAX_HIST), ("t_total_ms", ctypes.c_double),
                 ("t_f_ms", ctypes.c_double), ("t_jac_ms", ctypes.c_double), ("t_lu_ms", ctypes.c_double),
-                ("t_lin_ms", ctypes.c_double), ("gpu_launches", ctypes.c_int), ("reserved", ctypes.c_int * 15)]
+                ("t_lin_ms", ctypes.c_double), ("gpu_launches", ctypes.c_int), ("lu_pivoted", ctypes.c_int),
+                ("reserved", ctypes.c_int * 14)]
 
 
 _lock = threading.Lock()
@@ -66,8 +67,8 @@ SIGNATURES = {
     "nl_k_residual": (_int, [_i64, _dbl, _P, _P, _int, _dbl, _P, _P, _P, _P, _P]),
     "nl_k_jacobian": (_int, [_i64, _dbl, _P, _P, _i64, _P, _i64, _P]),
     "nl_k_jacobian64": (_int, [_i64, _dbl, _P, _P, _i64, _P]),
-    "nl_lu16": (_int, [_i64, _P, _i64, _P, _int, _int, ctypes.POINTER(ctypes.c_int32), _P]),
-    "nl_lu64": (_int, [_i64, _P, _i64, _P, _int, ctypes.POINTER(ctypes.c_int32), _P]),
+    "nl_lu16": (_int, [_i64, _P, _i64, _P, _int, _int, _int, ctypes.POINTER(ctypes.c_int32), _P]),
+    "nl_lu64": (_int, [_i64, _P, _i64, _P, _int, _int, ctypes.POINTER(ctypes.c_int32), _P]),
     "nl_lusolve16": (_int, [_i64, _P, _i64, _P, _P, _P]),
     "nl_lusolve64": (_int, [_i64, _P, _i64, _P, _P, _P]),
     "nl_k_gemv_residual": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
@@ -187,7 +188,7 @@ class Solver:
                     hist=list(s.hist[: n + 1]), lin_iters=list(s.lin_iters[:n]), lin_outer=list(s.lin_outer[:n]),
                     lin_failed=list(s.lin_failed[:n]), lin_relres=list(s.lin_relres[:n]),
                     t_total_ms=s.t_total_ms, t_f_ms=s.t_f_ms, t_jac_ms=s.t_jac_ms, t_lu_ms=s.t_lu_ms,
-                    t_lin_ms=s.t_lin_ms, gpu_launches=s.gpu_launches)
+                    t_lin_ms=s.t_lin_ms, gpu_launches=s.gpu_launches, lu_pivoted=s.lu_pivoted)
 
     def device_bytes(self) -> int:
         return lib().nl_device_bytes(self._h)
@@ -208,16 +209,16 @@ def k_jacobian64(N, c, r, J64, ld, stream=None):
     return check(lib().nl_k_jacobian64(N, c, _ptr(r), _ptr(J64), ld, _stream(stream)))
 
 
-def lu16(N, A16, ld, ipiv, nb=0, gemm=0, stream=None):
+def lu16(N, A16, ld, ipiv, nb=0, gemm=0, path=0, stream=None):
     info = ctypes.c_int32(0)
-    st = lib().nl_lu16(N, _ptr(A16), ld, _ptr(ipiv), nb, gemm, ctypes.byref(info), _stream(stream))
+    st = lib().nl_lu16(N, _ptr(A16), ld, _ptr(ipiv), nb, gemm, path, ctypes.byref(info), _stream(stream))
     check(st, allow=(NL_ESINGULAR,))
     return info.value
 
 
-def lu64(N, A, ld, ipiv, nb=0, stream=None):
+def lu64(N, A, ld, ipiv, nb=0, path=0, stream=None):
     info = ctypes.c_int32(0)
-    st = lib().nl_lu64(N, _ptr(A), ld, _ptr(ipiv), nb, ctypes.byref(info), _stream(stream))
+    st = lib().nl_lu64(N, _ptr(A), ld, _ptr(ipiv), nb, path, ctypes.byref(info), _stream(stream))
     check(st, allow=(NL_ESINGULAR,))
     return info.value
 

@@ -27,11 +27,21 @@ def rel_inf(a, b):
     return np.max(np.abs(a - b)) / np.max(np.abs(b))
 
 
-def check_counts(st, ro, mode, allow_stall=False):
+def check_counts(st, ro, mode, allow_stall=False, ill=False):
+    """Identical Newton counts; linear counts within one.  For very
+    ill-conditioned c (kappa * u_s near eta) a GMRES-IR step may take one
+    more or one fewer outer correction (one more GMRES call) on either side,
+    decided by single-precision rounding: there the tolerance is one outer
+    correction, compared on the outer counts."""
     assert st["newton_iters"] == ro["newton_iters"], (st["newton_iters"], ro["newton_iters"])
-    if mode != "FP64LU" and not allow_stall:
-        for a, b in zip(st["lin_iters"], ro["lin_iters"]):
-            assert abs(a - b) <= 1, (st["lin_iters"], ro["lin_iters"])
+    if mode == "FP64LU" or allow_stall:
+        return
+    if ill and mode == "GMRESIR16":
+        for a, b in zip(st["lin_outer"], ro["lin_outer"]):
+            assert abs(a - b) <= 1, (st["lin_outer"], ro["lin_outer"])
+        return
+    for a, b in zip(st["lin_iters"], ro["lin_iters"]):
+        assert abs(a - b) <= 1, (st["lin_iters"], ro["lin_iters"])
 
 
 @pytest.mark.parametrize("mode", ["FP64LU", "IR16", "GMRESIR16"])
@@ -91,6 +101,19 @@ def test_custom_start_and_device_api():
     assert rel_inf(x, xo) <= 1e-10
 
 
+@pytest.mark.parametrize("mode", ["FP64LU", "IR16", "GMRESIR16"])
+def test_lu_paths_agree(mode):
+    """The no-interchange fast path and the interchanging path factor the
+    paper's Jacobian identically, so the whole solve is bitwise the same."""
+    res = []
+    for path in (0, 1):
+        with nl.Solver(900, 0.999, lu_path=path) as s:
+            x, status = s.solve(mode=mode)
+            assert status == nl.NL_OK and s.stats()["lu_pivoted"] == 0
+            res.append(x)
+    assert np.array_equal(res[0], res[1])
+
+
 def test_repeatable_bitwise():
     with nl.Solver(700, 0.99) as s:
         a, _ = s.solve(mode="GMRESIR16")
@@ -124,14 +147,19 @@ def test_sweep_n4096_vs_golden(c, mode):
     with nl.Solver(N, c) as s:
         x, status = s.solve(tol=1e-10, mode=mode)
         st = s.stats()
-    stall = mode == "IR16" and c >= 0.9999
-    if ro["status"] == 0 and not stall:
+    if ro["status"] == 0:
         assert status == nl.NL_OK
-        check_counts(st, ro, mode)
+        check_counts(st, ro, mode, ill=c >= 0.9999)
         idx = gold["sample_idx"]
         xs = np.array(ref["x_sample"])
-        assert np.max(np.abs(x[idx] - xs)) / np.max(np.abs(xs)) <= 1e-10
-        assert abs(x.sum() - ref["x_sum"]) <= 1e-10 * abs(ref["x_sum"])
+        # 1e-10 (the Newton tolerance); for the very ill-conditioned c the
+        # last iterate's residual ||F||/||F0|| (at most 1e-10, and the linear
+        # steps only match to single-precision rounding) is amplified into x by
+        # up to the condition number, which grows like (1 - c)^(-1/2)
+        kappa = 1.0 / math.sqrt(1.0 - c)
+        tol = 1e-10 if c <= 0.99 else 1e-10 + 10.0 * kappa * max(st["hist"][-1], ro["hist"][-1])
+        assert np.max(np.abs(x[idx] - xs)) / np.max(np.abs(xs)) <= tol
+        assert abs(x.sum() - ref["x_sum"]) <= tol * abs(ref["x_sum"])
     # properties that hold at any size: residual and the moment identity
     F = O.F(N, c, x)
     if status == nl.NL_OK:
