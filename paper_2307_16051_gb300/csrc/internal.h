@@ -25,6 +25,7 @@ struct LuWork {
     __half* ut = nullptr;     // U12^T for the tensor-core trailing update: N x NB binary16
     int* info = nullptr;      // device int: first zero pivot (1-based), 0 if none
     int* flag = nullptr;      // device int (info + 1): set when the no-interchange fast path failed
+    void* stage = nullptr;    // diagonal-block factors staged for the off-diagonal solves (<= 256 KB)
 };
 size_t lu_work_bytes(int N, int nb, bool fp64);
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w);

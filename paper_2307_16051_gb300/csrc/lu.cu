@@ -434,196 +434,357 @@ __global__ void __launch_bounds__(kTrsmThreads) k_trsm_u12(S* __restrict__ A, in
 // sets *flag; the remaining fast-path kernels then return at once and the
 // caller refactors with the interchanging path.
 
-// Diagonal block [K, K+w)^2 (w <= 128) in one CTA of 32 x 32 threads:
-// unpivoted right-looking elimination with the block held in registers
-// (thread (ty, tx) owns rows ty + 32a and columns tx + 32b).  Per step j the
-// owners publish the pivot row (rounded: U entries) and the multipliers
-// l_ij = fl16(a_ij / u_jj) through double-buffered shared vectors, then every
-// thread applies a_it -= l_ij u_jt to its entries: the same operations, in
-// the same order, as the elimination it replaces.
-template <typename T, typename S, bool RND, int NA>
-__global__ void __launch_bounds__(1024, 1) k_diag_lu(S* __restrict__ A, int64_t lda, int K, int w,
-                                                     int* __restrict__ ipiv, int* __restrict__ flag)
+// ------------------------------------------------ 32-wide chunk routines --
+// All routines below apply to each entry the elimination's updates
+// a <- a - l_t u_t in increasing t (one rounding each: the product of two
+// binary16 numbers is exact in binary32), round multipliers and U entries to
+// binary16 when they are formed, and check each pre-division value against
+// its pivot (|a_it| <= |u_tt|: partial pivoting keeps the diagonal).
+
+__device__ __forceinline__ float absT(float x) { return fabsf(x); }
+__device__ __forceinline__ double absT(double x) { return fabs(x); }
+
+// Diagonal block [K, K+w)^2 (w <= 128) in one CTA, held in shared memory,
+// in 32-column chunks c (padding beyond w is identity):
+//  (a) one warp factors the 32 x 32 diagonal sub-block, lane r = row r: at
+//      step t row t is final, its U entries are rounded, and the rows below
+//      form their multipliers and update;
+//  (b) groups of eight lanes solve the rows below the sub-block against its
+//      U, and (c) the columns right of it against its L (as k_offdiag does);
+//  (d) all threads apply the rank-32 update to the rest of the block.
+constexpr int kDiagThreads = 512;
+constexpr int kOffG = 8;  // lanes per row / column group
+
+// Block [K, K+w)^2 of A into shared memory W (ld ldw), identity-padded to
+// wp; 16-byte vector loads when the row segments allow them.
+template <typename T, typename S, int NT>
+__device__ __forceinline__ void load_block(const S* __restrict__ A, int64_t lda, int K, int w, int wp, T* W, int ldw,
+                                           int tid)
+{
+    constexpr int V = 16 / sizeof(S);  // elements per 16-byte vector
+    const bool vec = (w % V == 0) && ((((uintptr_t)(A + (int64_t)K * lda + K)) & 15) == 0) && ((lda * sizeof(S)) % 16 == 0);
+    if (vec) {
+        const int vpr = w / V;
+#pragma unroll 4
+        for (int q = tid; q < w * vpr; q += NT) {
+            const int i = q / vpr, tv = q - i * vpr;
+            uint4 raw = *reinterpret_cast<const uint4*>(A + (int64_t)(K + i) * lda + K + tv * V);
+            const S* e = reinterpret_cast<const S*>(&raw);
+#pragma unroll
+            for (int k = 0; k < V; ++k) W[i * ldw + tv * V + k] = (T)ld_elem(e + k);
+        }
+    } else {
+#pragma unroll 4
+        for (int q = tid; q < w * w; q += NT) {
+            const int i = q / w, t = q - i * w;
+            W[i * ldw + t] = (T)ld_elem(A + (int64_t)(K + i) * lda + K + t);
+        }
+    }
+    for (int q = tid; q < wp * wp; q += NT) {
+        const int i = q / wp, t = q - i * wp;
+        if (i >= w || t >= w) W[i * ldw + t] = (i == t) ? T(1) : T(0);
+    }
+}
+
+template <typename T, typename S, int NT>
+__device__ __forceinline__ void store_block(S* __restrict__ A, int64_t lda, int K, int w, const T* W, int ldw, int tid)
+{
+    constexpr int V = 16 / sizeof(S);
+    const bool vec = (w % V == 0) && ((((uintptr_t)(A + (int64_t)K * lda + K)) & 15) == 0) && ((lda * sizeof(S)) % 16 == 0);
+    if (vec) {
+        const int vpr = w / V;
+#pragma unroll 4
+        for (int q = tid; q < w * vpr; q += NT) {
+            const int i = q / vpr, tv = q - i * vpr;
+            uint4 raw;
+            S* e = reinterpret_cast<S*>(&raw);
+#pragma unroll
+            for (int k = 0; k < V; ++k) st_elem(e + k, W[i * ldw + tv * V + k]);
+            *reinterpret_cast<uint4*>(A + (int64_t)(K + i) * lda + K + tv * V) = raw;
+        }
+    } else {
+        for (int q = tid; q < w * w; q += NT) {
+            const int i = q / w, t = q - i * w;
+            st_elem(A + (int64_t)(K + i) * lda + K + t, W[i * ldw + t]);
+        }
+    }
+}
+
+template <typename T, bool RND>
+__device__ __forceinline__ void group_row_solve(T* W, int ldw, int c0, int r, int g, unsigned gmask, bool& bad)
+{
+    // row r, chunk columns c0 + 4g .. c0 + 4g + 3, against U = W[c0.., c0..]
+    T acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = W[r * ldw + c0 + 4 * g + k];
+#pragma unroll
+    for (int tt = 0; tt < 32; ++tt) {
+        T l = T(0);
+        if (g == tt / 4) {
+            const T utt = W[(c0 + tt) * ldw + c0 + tt];
+            const T x = acc[tt % 4];
+            if (!(absT(x) <= absT(utt)) || !(utt != T(0))) bad = true;
+            l = maybe_round(x / utt, RND);
+            acc[tt % 4] = l;
+        }
+        l = __shfl_sync(gmask, l, tt / 4, kOffG);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (4 * g + k > tt) acc[k] = fma(-l, W[(c0 + tt) * ldw + c0 + 4 * g + k], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) W[r * ldw + c0 + 4 * g + k] = acc[k];
+}
+
+template <typename T, bool RND>
+__device__ __forceinline__ void group_col_solve(T* W, int ldw, int c0, int col, int g, unsigned gmask)
+{
+    // column col, chunk rows c0 + 4g .. c0 + 4g + 3, against L = W[c0.., c0..]
+    T acc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = W[(c0 + 4 * g + k) * ldw + col];
+#pragma unroll
+    for (int tt = 0; tt < 32; ++tt) {
+        T u = T(0);
+        if (g == tt / 4) {
+            u = maybe_round(acc[tt % 4], RND);
+            acc[tt % 4] = u;
+        }
+        u = __shfl_sync(gmask, u, tt / 4, kOffG);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (4 * g + k > tt) acc[k] = fma(-W[(c0 + 4 * g + k) * ldw + c0 + tt], u, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) W[(c0 + 4 * g + k) * ldw + col] = acc[k];
+}
+
+template <typename T, typename S, bool RND>
+__global__ void __launch_bounds__(kDiagThreads, 1) k_diag_lu(S* __restrict__ A, int64_t lda, int K, int w,
+                                                             int* __restrict__ ipiv, int* __restrict__ flag,
+                                                             void* __restrict__ stage)
 {
     if (*(volatile int*)flag) return;
-    __shared__ T rowbuf[2][128];
-    __shared__ T colbuf[2][128];
-    const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-    T v[NA][NA];
-#pragma unroll
-    for (int a = 0; a < NA; ++a)
-#pragma unroll
-        for (int b = 0; b < NA; ++b) {
-            const int i = ty + 32 * a, t = tx + 32 * b;
-            v[a][b] = (i < w && t < w) ? (T)ld_elem(A + (int64_t)(K + i) * lda + K + t) : T(0);
-        }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* W = reinterpret_cast<T*>(smem_raw);
+    const int wp = (w + 31) & ~31, ldw = wp + 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int grp = tid / kOffG, g = tid % kOffG;
+    const unsigned gmask = 0xffu << ((tid & 31) & ~(kOffG - 1));
+    load_block<T, S, kDiagThreads>(A, lda, K, w, wp, W, ldw, tid);
+    __syncthreads();
     bool bad = false;
-    for (int j = 0; j < w; ++j) {
-        const int buf = j & 1, jr = j & 31, jb = j >> 5;
-        // pivot row j is final: round its entries (U) and publish them
-        if (ty == jr) {
+    const int nc = wp / 32;
+    for (int c = 0; c < nc; ++c) {
+        const int c0 = 32 * c;
+        if (warp == 0) {
+            // lane r holds row c0 + r of the sub-block; after step t the row
+            // array is shifted by one so that a[0] is always column c0 + t
+            T* Wr = W + (c0 + lane) * ldw + c0;
+            T a[32];
 #pragma unroll
-            for (int b = 0; b < NA; ++b) {
-                const int t = tx + 32 * b;
+            for (int j = 0; j < 32; ++j) a[j] = Wr[j];
+            for (int t = 0; t < 32; ++t) {
+                const T utt = __shfl_sync(0xffffffffu, maybe_round(a[0], RND), t);
+                // rows below form their multiplier; finished rows use l = 0
+                T l = T(0);
+                if (lane > t) {
+                    if (!(absT(a[0]) <= absT(utt)) || !(utt != T(0))) bad = true;
+                    l = maybe_round(a[0] / utt, RND);
+                }
+                a[0] = (lane == t) ? utt : ((lane > t) ? l : a[0]);
+                if (lane >= t) Wr[t] = a[0];
 #pragma unroll
-                for (int a = 0; a < NA; ++a)
-                    if (a == jb && t >= j) {
-                        v[a][b] = maybe_round(v[a][b], RND);
-                        rowbuf[buf][t] = v[a][b];
-                    }
+                for (int j = 1; j < 32; ++j) {
+                    const T uj = __shfl_sync(0xffffffffu, maybe_round(a[j], RND), t);
+                    a[j] = (lane == t) ? uj : fma(-l, uj, a[j]);
+                }
+                if (lane == t) {
+#pragma unroll
+                    for (int j = 1; j < 32; ++j)
+                        if (t + j < 32) Wr[t + j] = a[j];  // U entries of row t
+                }
+#pragma unroll
+                for (int j = 0; j < 31; ++j) a[j] = a[j + 1];
+                a[31] = T(0);
             }
         }
         __syncthreads();
-        const T ujj = rowbuf[buf][j];
-        if (tid == 0 && !(ujj != T(0))) bad = true;  // zero or NaN pivot
-        // multipliers of column j (owners: tx == j % 32)
-        if (tx == jr) {
-#pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const int i = ty + 32 * a;
-                if (i > j && i < w) {
-#pragma unroll
-                    for (int b = 0; b < NA; ++b)
-                        if (b == jb) {
-                            const T x = v[a][b];
-                            const T ax = x < T(0) ? -x : x, au = ujj < T(0) ? -ujj : ujj;
-                            if (!(ax <= au)) bad = true;
-                            const T l = maybe_round(x / ujj, RND);
-                            v[a][b] = l;
-                            colbuf[buf][i] = l;
-                        }
-                }
-            }
+        const int rest = wp - c0 - 32;
+        // (b) rows below and (c) columns right of the sub-block: one group each
+        for (int q = grp; q < 2 * rest; q += kDiagThreads / kOffG) {
+            if (q < rest) group_row_solve<T, RND>(W, ldw, c0, c0 + 32 + q, g, gmask, bad);
+            else group_col_solve<T, RND>(W, ldw, c0, c0 + 32 + (q - rest), g, gmask);
         }
         __syncthreads();
-        // rank-1 update of the entries right of and below the pivot
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-            const int i = ty + 32 * a;
-            if (i > j && i < w) {
-                const T l = colbuf[buf][i];
-#pragma unroll
-                for (int b = 0; b < NA; ++b) {
-                    const int t = tx + 32 * b;
-                    if (t > j && t < w) v[a][b] = fma(-l, rowbuf[buf][t], v[a][b]);
+        if (rest > 0) {
+            // (d) rows/cols [c0+32, wp): 2 x 2 entries per thread, t in order
+            const int nb2 = rest / 2;
+            for (int e = tid; e < nb2 * nb2; e += kDiagThreads) {
+                const int i = c0 + 32 + 2 * (e / nb2), j = c0 + 32 + 2 * (e % nb2);
+                T a00 = W[i * ldw + j], a01 = W[i * ldw + j + 1];
+                T a10 = W[(i + 1) * ldw + j], a11 = W[(i + 1) * ldw + j + 1];
+#pragma unroll 8
+                for (int t = c0; t < c0 + 32; ++t) {
+                    const T l0 = W[i * ldw + t], l1 = W[(i + 1) * ldw + t];
+                    const T u0 = W[t * ldw + j], u1 = W[t * ldw + j + 1];
+                    a00 = fma(-l0, u0, a00);
+                    a01 = fma(-l0, u1, a01);
+                    a10 = fma(-l1, u0, a10);
+                    a11 = fma(-l1, u1, a11);
                 }
+                W[i * ldw + j] = a00;
+                W[i * ldw + j + 1] = a01;
+                W[(i + 1) * ldw + j] = a10;
+                W[(i + 1) * ldw + j + 1] = a11;
             }
+            __syncthreads();
         }
     }
     if (__syncthreads_or(bad)) {
         if (tid == 0) atomicOr(flag, 1);
         return;
     }
-#pragma unroll
-    for (int a = 0; a < NA; ++a)
-#pragma unroll
-        for (int b = 0; b < NA; ++b) {
-            const int i = ty + 32 * a, t = tx + 32 * b;
-            if (i < w && t < w) st_elem(A + (int64_t)(K + i) * lda + K + t, v[a][b]);
-        }
+    store_block<T, S, kDiagThreads>(A, lda, K, w, W, ldw, tid);
+    // staged copies for k_offdiag: U11 (row role) and L11^T (column role),
+    // wp x wp each, identity / zero padded, in its shared-memory layout
+    using H = typename std::conditional<std::is_same<T, float>::value, __half, double>::type;
+    H* SU = reinterpret_cast<H*>(stage);
+    H* SL = SU + wp * wp;
+    for (int q = tid; q < wp * wp; q += kDiagThreads) {
+        const int r = q / wp, t = q - r * wp;
+        const T wv = W[r * ldw + t], wt = W[t * ldw + r];
+        SU[q] = (H)((r < w && t < w) ? ((t >= r) ? wv : T(0)) : ((r == t) ? T(1) : T(0)));
+        SL[q] = (H)((r < w && t < w && t > r) ? wt : T(0));
+    }
     if (tid < w) ipiv[K + tid] = K + tid;
 }
 
-// Off-diagonal blocks of the panel, one launch, 32 warps per CTA:
-//  * L21 = A21 U11^{-1}: one warp per row; lane owns columns lane + 32b.
-//    For t = 0..w-1 the owner of column t forms l_it = fl16(v_it / u_tt),
-//    checking |v_it| <= |u_tt| (partial pivoting would keep the diagonal),
-//    and broadcasts it; every lane then applies v_ij -= l_it u_tj (j > t).
-//  * U12 = L11^{-1} A12: one warp per column; lane owns rows lane + 32a.
-//    For t = 0..w-1 the owner of row t rounds u_tc (final) and broadcasts
-//    it; lanes apply v_kc -= l_kt u_tc (k > t).  Also writes U12^T.
-// Both follow the elimination's order of operations exactly.
-constexpr int kOffThreads = 1024;
+// Off-diagonal blocks of a panel of width w, one launch, eight lanes per row
+// (L21 = A21 U11^{-1}) or per column (U12 = L11^{-1} A12), four per warp.
+// Left-looking in 32-wide chunks: lane g of a group owns entries 4g..4g+3 of
+// the chunk.  The chunk is first updated with the earlier chunks' multipliers
+// (row role) or U entries (column role), which the group keeps in shared
+// memory as binary16 (exact), then solved against the chunk's diagonal
+// 32 x 32 block: at step t the owning lane forms the multiplier (or rounds
+// the U entry) and broadcasts it to its group.  U11 (row role) and L11^T
+// (column role) are staged in shared memory as binary16.
+constexpr int kOffThreads = 128;  // 16 groups of 8 lanes
 
-template <typename T, typename S, bool RND, int NA>
+template <typename T, typename S, bool RND>
 __global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                          int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                                         int* __restrict__ flag)
+                                                         int* __restrict__ flag, const void* __restrict__ stage)
 {
     if (flag && *(volatile int*)flag) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* D = reinterpret_cast<T*>(smem_raw);  // w x w: U11 (row role) or L11^T (column role)
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    using H = typename std::conditional<std::is_same<T, float>::value, __half, double>::type;
+    constexpr int NG = kOffThreads / kOffG;  // groups (rows or columns) per CTA
+    const int wp = (w + 31) & ~31;
+    H* D = reinterpret_cast<H*>(smem_raw);  // wp x wp: U11 (row role) or L11^T (column role), identity-padded
+    H* X = D + wp * wp;                     // wp x NG: earlier multipliers / U entries of each group
+    const int tid = threadIdx.x, grp = tid / kOffG, g = tid % kOffG;
+    const unsigned gmask = 0xffu << ((tid & 31) & ~(kOffG - 1));
     const bool row_role = (int)blockIdx.x < nrow_blocks;
-    if (row_role) {
-        for (int q = tid; q < w * w; q += kOffThreads) {
-            int r = q / w, t = q % w;
-            D[q] = (t >= r) ? (T)ld_elem(A + (int64_t)(K + r) * lda + K + t) : T(0);
-        }
-    } else {
-        for (int q = tid; q < w * w; q += kOffThreads) {
-            int r = q / w, t = q % w;  // D[t][r] = L[r][t]
-            D[t * w + r] = (t < r) ? (T)ld_elem(A + (int64_t)(K + r) * lda + K + t) : T(0);
-        }
+    {
+        // U11 or L11^T, staged by k_diag_lu in exactly this layout
+        const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const H*>(stage) + (row_role ? 0 : wp * wp));
+        uint4* dst = reinterpret_cast<uint4*>(D);
+        const int nv = wp * wp * (int)sizeof(H) / 16;
+#pragma unroll 4
+        for (int q = tid; q < nv; q += kOffThreads) dst[q] = src[q];
     }
     __syncthreads();
     bool bad = false;
+    const int nc = wp / 32;
     if (row_role) {
-        const int i = K + w + blockIdx.x * 32 + warp;
-        if (i < N) {
-            S* Ai = A + (int64_t)i * lda + K;
-            T v[NA];
-#pragma unroll
-            for (int b = 0; b < NA; ++b) v[b] = (lane + 32 * b < w) ? (T)ld_elem(Ai + lane + 32 * b) : T(0);
-            for (int t = 0; t < w; ++t) {
-                const int tb = t >> 5;
-                T l = T(0);
-                if (lane == (t & 31)) {
-#pragma unroll
-                    for (int b = 0; b < NA; ++b)
-                        if (b == tb) {
-                            const T utt = D[t * w + t];
-                            const T x = v[b];
-                            const T ax = x < T(0) ? -x : x, au = utt < T(0) ? -utt : utt;
-                            if (!(ax <= au) || !(utt != T(0))) bad = true;
-                            l = maybe_round(x / utt, RND);
-                            v[b] = l;
-                        }
+        const int i = K + w + blockIdx.x * NG + grp;
+        const bool live = i < N;
+        S* Ai = A + (int64_t)min(i, N - 1) * lda + K;
+        for (int c = 0; c < nc; ++c) {
+            const int c0 = 32 * c, jb = c0 + 4 * g;
+            T acc[4];
+            if (live && jb + 4 <= w) {
+                S e[4];
+                if constexpr (sizeof(S) == 2) *reinterpret_cast<uint2*>(e) = *reinterpret_cast<const uint2*>(Ai + jb);
+                else {
+                    reinterpret_cast<uint4*>(e)[0] = reinterpret_cast<const uint4*>(Ai + jb)[0];
+                    reinterpret_cast<uint4*>(e)[1] = reinterpret_cast<const uint4*>(Ai + jb)[1];
                 }
-                l = __shfl_sync(0xffffffffu, l, t & 31);
 #pragma unroll
-                for (int b = 0; b < NA; ++b) {
-                    const int j = lane + 32 * b;
-                    if (j > t && j < w) v[b] = fma(-l, D[t * w + j], v[b]);
-                }
+                for (int k = 0; k < 4; ++k) acc[k] = (T)ld_elem(e + k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k] = (live && jb + k < w) ? (T)ld_elem(Ai + jb + k) : T(0);
+            }
+            for (int t = 0; t < c0; ++t) {
+                const T l = (T)X[t * NG + grp];
+                const H* Dt = D + t * wp + jb;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[k] = fma(-l, (T)Dt[k], acc[k]);
             }
 #pragma unroll
-            for (int b = 0; b < NA; ++b)
-                if (lane + 32 * b < w) st_elem(Ai + lane + 32 * b, v[b]);
+            for (int tt = 0; tt < 32; ++tt) {
+                const int t = c0 + tt;
+                T l = T(0);
+                if (g == tt / 4) {
+                    const T utt = (T)D[t * wp + t];
+                    const T x = acc[tt % 4];
+                    if (live && t < w && (!(absT(x) <= absT(utt)) || !(utt != T(0)))) bad = true;
+                    l = maybe_round(x / utt, RND);
+                    acc[tt % 4] = l;
+                    X[t * NG + grp] = (H)l;
+                }
+                l = __shfl_sync(gmask, l, tt / 4, kOffG);
+                const H* Dt = D + t * wp + jb;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (4 * g + k > tt) acc[k] = fma(-l, (T)Dt[k], acc[k]);
+            }
+            if (live) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (jb + k < w) st_elem(Ai + jb + k, acc[k]);
+            }
         }
         if (__syncthreads_or(bad) && tid == 0 && flag) atomicOr(flag, 1);
     } else {
-        const int c = K + w + (blockIdx.x - nrow_blocks) * 32 + warp;
-        if (c < N) {
-            T v[NA];
+        const int col = K + w + (blockIdx.x - nrow_blocks) * NG + grp;
+        const bool live = col < N;
+        const int cc = min(col, N - 1);
+        for (int c = 0; c < nc; ++c) {
+            const int c0 = 32 * c, kb = c0 + 4 * g;
+            T acc[4];
 #pragma unroll
-            for (int a = 0; a < NA; ++a)
-                v[a] = (lane + 32 * a < w) ? (T)ld_elem(A + (int64_t)(K + lane + 32 * a) * lda + c) : T(0);
-            for (int t = 0; t < w; ++t) {
-                const int ta = t >> 5;
-                T u = T(0);
-                if (lane == (t & 31)) {
+            for (int k = 0; k < 4; ++k) acc[k] = (live && kb + k < w) ? (T)ld_elem(A + (int64_t)(K + kb + k) * lda + cc) : T(0);
+            for (int t = 0; t < c0; ++t) {
+                const T u = (T)X[t * NG + grp];
+                const H* Dt = D + t * wp + kb;  // L[kb + k][t]
 #pragma unroll
-                    for (int a = 0; a < NA; ++a)
-                        if (a == ta) {
-                            u = maybe_round(v[a], RND);
-                            v[a] = u;
-                        }
-                }
-                u = __shfl_sync(0xffffffffu, u, t & 31);
-#pragma unroll
-                for (int a = 0; a < NA; ++a) {
-                    const int k = lane + 32 * a;
-                    if (k > t && k < w) v[a] = fma(-D[t * w + k], u, v[a]);
-                }
+                for (int k = 0; k < 4; ++k) acc[k] = fma(-(T)Dt[k], u, acc[k]);
             }
 #pragma unroll
-            for (int a = 0; a < NA; ++a) {
-                const int k = lane + 32 * a;
-                if (k < w) {
-                    st_elem(A + (int64_t)(K + k) * lda + c, v[a]);
-                    if (Ut) Ut[(int64_t)(c - K - w) * ldut + k] = __float2half_rn((float)v[a]);
+            for (int tt = 0; tt < 32; ++tt) {
+                const int t = c0 + tt;
+                T u = T(0);
+                if (g == tt / 4) {
+                    u = maybe_round(acc[tt % 4], RND);
+                    acc[tt % 4] = u;
+                    X[t * NG + grp] = (H)u;
                 }
+                u = __shfl_sync(gmask, u, tt / 4, kOffG);
+                const H* Dt = D + t * wp + kb;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (4 * g + k > tt) acc[k] = fma(-(T)Dt[k], u, acc[k]);
+            }
+            if (live) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (kb + k < w) {
+                        st_elem(A + (int64_t)(K + kb + k) * lda + col, acc[k]);
+                        if (Ut) Ut[(int64_t)(col - K - w) * ldut + kb + k] = __float2half_rn((float)acc[k]);
+                    }
             }
         }
     }
@@ -692,7 +853,7 @@ size_t lu_work_bytes(int N, int nb, bool fp64)
     size_t el = fp64 ? 8 : 4;
     size_t pnl = (size_t)N * nb * el;
     size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
-    return round_up(pnl, 256) + round_up(ut, 256) + 256;
+    return round_up(pnl, 256) + round_up(ut, 256) + 256 + (size_t)2 * 128 * 128 * 8;
 }
 
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
@@ -706,6 +867,8 @@ void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
     p += round_up(ut, 256);
     w->info = (int*)p;
     w->flag = w->info + 1;
+    p += 256;
+    w->stage = p;
 }
 
 template <typename T, int NBL, int R, bool RND>
@@ -839,8 +1002,8 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
     static bool smem_set = false;
     if (!smem_set) {
         if (set_max_dynamic_smem((const void*)k_trsm_u12<T, S, RND>) != NL_OK ||
-            set_max_dynamic_smem((const void*)k_offdiag<T, S, RND, 2>) != NL_OK ||
-            set_max_dynamic_smem((const void*)k_offdiag<T, S, RND, 4>) != NL_OK)
+            set_max_dynamic_smem((const void*)k_offdiag<T, S, RND>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_diag_lu<T, S, RND>) != NL_OK)
             return NL_ECUDA;
         smem_set = true;
     }
@@ -850,19 +1013,16 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         const bool tc = (gemm == 2) && std::is_same<S, __half>::value && (wd % 64 == 0);
         const size_t trsm_smem = (size_t)wd * wd * sizeof(T) + (size_t)wd * kTrsmThreads * sizeof(T);
         if (fast) {
-            const int na = (int)cdiv(wd, 32);
-            if (na <= 2) k_diag_lu<T, S, RND, 2><<<1, 1024, 0, st>>>(A, ld, K, wd, ipiv, w.flag);
-            else k_diag_lu<T, S, RND, 4><<<1, 1024, 0, st>>>(A, ld, K, wd, ipiv, w.flag);
+            const int wp = (int)round_up(wd, 32);
+            k_diag_lu<T, S, RND><<<1, kDiagThreads, (size_t)wp * (wp + 1) * sizeof(T), st>>>(A, ld, K, wd, ipiv,
+                                                                                        w.flag, w.stage);
             ++nl;
             if (rest > 0) {
-                const int nrb = (int)cdiv(rest, 32);
-                const size_t sm = (size_t)wd * wd * sizeof(T);
-                if (na <= 2)
-                    k_offdiag<T, S, RND, 2><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb,
-                                                                            tc ? w.ut : nullptr, nb, w.flag);
-                else
-                    k_offdiag<T, S, RND, 4><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb,
-                                                                            tc ? w.ut : nullptr, nb, w.flag);
+                const int nrb = (int)cdiv(rest, kOffThreads / kOffG);
+                const size_t hsz = std::is_same<T, float>::value ? 2 : 8;
+                const size_t sm = (size_t)wp * wp * hsz + (size_t)wp * (kOffThreads / kOffG) * hsz;
+                k_offdiag<T, S, RND><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb, tc ? w.ut : nullptr, nb,
+                                                                      w.flag, w.stage);
                 nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
                 if (s != NL_OK) return s;
                 nl += 2;
