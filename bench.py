@@ -169,6 +169,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--lu-nb", type=int, default=0, help="LU outer block (0: library default)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
@@ -183,7 +184,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     hbm_peak, tc_peak, tc_sust, peak_kind = peaks()
-    solvers = {c: nl.Solver(N_BENCH, c) for c in SWEEP}
+    solvers = {c: nl.Solver(N_BENCH, c, lu_nb=args.lu_nb) for c in SWEEP}
     xdev = {c: torch.empty(N_BENCH, device=dev, dtype=torch.float64) for c in SWEEP}
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
 
