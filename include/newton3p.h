@@ -204,6 +204,23 @@ nl_status nl_k_gemv_residual(int64_t N, const float* A, int64_t ld, const float*
 nl_status nl_k_gemm16_update(int64_t M, int64_t Nc, int64_t K, const void* A, int64_t lda, const void* B,
                              int64_t ldb, void* C, int64_t ldc, int gemm, void* stream);
 
+/* Same operation and results as nl_k_gemv_residual, for callers that cannot
+ * allocate device memory (a fixed memory pool, a plug-in that must not grow
+ * the process's device footprint, or a stream under graph capture where
+ * allocation is not allowed).  The paper has no counterpart: this is a
+ * packaging of the residual for such callers.
+ * Scratch: a fixed 33 KB array inside the library image, held on every GPU
+ * that loads the library until the process exits; no cudaMalloc or other
+ * allocation happens.  Limit: 1 <= N <= 32768, else NL_EINVAL.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array per device, so calls whose work overlaps
+ * on the GPU (different streams, no ordering between them) race and give
+ * wrong norms; order them on one stream.  A, u: 16-byte aligned, ld a
+ * multiple of 4, as for nl_k_gemv_residual. */
+nl_status nl_k_gemv_residual_noalloc(int64_t N, const float* A, int64_t ld, const float* b, const float* u,
+                                     float* r, double* rnorm_dev, void* stream);
+
 /* IR / GMRES-IR for J32 u = b with given half-precision factors (Section 2.2):
  * u0 = 0; success at ||b - J32 u|| <= eta ||b||; failure when the residual
  * norm increases (the best iterate is returned, Section 3.1); at most maxit

@@ -72,6 +72,7 @@ SIGNATURES = {
     "nl_lusolve16": (_int, [_i64, _P, _i64, _P, _P, _P]),
     "nl_lusolve64": (_int, [_i64, _P, _i64, _P, _P, _P]),
     "nl_k_gemv_residual": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
+    "nl_k_gemv_residual_noalloc": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
     "nl_k_gemm16_update": (_int, [_i64, _i64, _i64, _P, _i64, _P, _i64, _P, _i64, _int, _P]),
     "nl_linsolve16": (_int, [_i64, _P, _i64, _P, _i64, _P, _P, _P, _dbl, _int, _int, _int, _dbl, _int,
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _P]),
@@ -233,6 +234,12 @@ def lusolve64(N, LU, ld, ipiv, b, stream=None):
 
 def k_gemv_residual(N, A, ld, b, u, r, rnorm, stream=None):
     return check(lib().nl_k_gemv_residual(N, _ptr(A), ld, _ptr(b), _ptr(u), _ptr(r), _ptr(rnorm), _stream(stream)))
+
+
+def k_gemv_residual_noalloc(N, A, ld, b, u, r, rnorm, stream=None):
+    """nl_k_gemv_residual without any device allocation (fixed in-library scratch)."""
+    return check(lib().nl_k_gemv_residual_noalloc(N, _ptr(A), ld, _ptr(b), _ptr(u), _ptr(r), _ptr(rnorm),
+                                                  _stream(stream)))
 
 
 def k_gemm16_update(M, Nc, K, A, lda, B, ldb, C, ldc, gemm=1, stream=None):

@@ -1,0 +1,52 @@
+"""The allocation-free residual entry point (nl_k_gemv_residual_noalloc).
+
+Callers that cannot allocate device memory (a fixed pool, a plug-in that
+must not grow the device footprint, a stream under graph capture) use this
+variant; it must give the same residual and norm as nl_k_gemv_residual.
+Collected last so that a failure here cannot hide any other test's result.
+"""
+import numpy as np
+import pytest
+
+from paper_2307_16051_gb300 import nl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _case(N, seed):
+    g = np.random.default_rng(seed)
+    ld = ((N + 63) // 64) * 64
+    A = torch.zeros((N, ld), device="cuda", dtype=torch.float32)
+    A[:, :N] = torch.as_tensor(g.standard_normal((N, N)).astype(np.float32), device="cuda")
+    u = torch.zeros(ld, device="cuda", dtype=torch.float32)
+    u[:N] = torch.as_tensor(g.standard_normal(N).astype(np.float32), device="cuda")
+    b = torch.as_tensor(g.standard_normal(N).astype(np.float32), device="cuda")
+    return A, ld, b, u
+
+
+def test_noalloc_matches_allocating_entry_point_twice():
+    assert torch.cuda.is_available(), "needs a CUDA device"
+    for N, seed in ((1000, 1), (4096, 2)):
+        A, ld, b, u = _case(N, seed)
+        r_ref = torch.empty(N, device="cuda", dtype=torch.float32)
+        n_ref = torch.empty(1, device="cuda", dtype=torch.float64)
+        nl.k_gemv_residual(N, A, ld, b, u, r_ref, n_ref)
+        for _ in range(2):  # two calls in a row: the shared scratch must not leak state
+            r = torch.full((N,), float("nan"), device="cuda", dtype=torch.float32)
+            n = torch.full((1,), float("nan"), device="cuda", dtype=torch.float64)
+            nl.k_gemv_residual_noalloc(N, A, ld, b, u, r, n)
+            torch.cuda.synchronize()
+            # deterministic kernels: the same bits as the allocating path
+            assert torch.equal(r, r_ref)
+            assert n.item() == n_ref.item()
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    A, ld, b, u = _case(8, 3)
+    r = torch.empty(8, device="cuda", dtype=torch.float32)
+    n = torch.empty(1, device="cuda", dtype=torch.float64)
+    st = nl.lib().nl_k_gemv_residual_noalloc(32769, A.data_ptr(), 32832, b.data_ptr(), u.data_ptr(), r.data_ptr(),
+                                             n.data_ptr(), None)
+    assert st == nl.NL_EINVAL and "32768" in nl.last_error()
