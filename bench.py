@@ -96,6 +96,58 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop/FMA x max SM clock
+
+
+def kernel_rooflines(nl, step, N, hbm_peak, tc_peak):
+    """Time each kernel class of one GMRES-IR16 sweep with CUDA events (the
+    library brackets every launch of the class on its stream) and set the
+    algorithmic work of one launch against its roofline."""
+    NB, T2 = 128, 128
+    out = {}
+    # algorithmic work per launch at N = 4096, nb = 128 (averaged over the 32 panels)
+    panels = [(K, min(NB, N - K)) for K in range(0, N, NB)]
+    diag_flop = sum(2.0 * w ** 3 / 3.0 for _, w in panels) / len(panels)
+    off = [(N - K - w, w) for K, w in panels if N - K - w > 0]
+    off_flop = sum(2.0 * 2 * r * w * w / 2.0 for r, w in off) / len(off)          # L21 and U12 solves
+    gemm_flop = sum(2.0 * r * r * w for r, w in off) / len(off)
+    nblk = (N + T2 - 1) // T2
+    trsv_bytes = (N * N / 2.0) * 2 + nblk * T2 * T2 * 4 + 3 * N * 4                 # fp16 triangle + diag inverses + vectors
+    gemv_bytes = 4.0 * N * N + 3 * 4.0 * N                                          # fp32 J and vectors
+    spec = {
+        "k_diag_lu": ("alu", diag_flop, FP32_PEAK_TFLOPS, "TFLOP/s", "derived fp32 FMA peak (152 SMs x 128 lanes x 2 x 2.07 GHz)"),
+        "k_offdiag": ("alu", off_flop, FP32_PEAK_TFLOPS, "TFLOP/s", "derived fp32 FMA peak"),
+        "k_tc_gemm": ("tensor", gemm_flop, tc_peak, "TFLOP/s", "measured bf16 dense (fp16 same rate)"),
+        "k_trsv_mb": ("hbm", trsv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
+        "k_gemv_residual": ("hbm", gemv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
+    }
+    for name, (bound, work, peak, unit, kind) in spec.items():
+        nl.kernel_timing(name)
+        step("GMRESIR16")
+        n, ms = nl.kernel_timing(None)
+        if n == 0:
+            continue
+        avg_s = ms / n / 1e3
+        scale = 1e12 if unit == "TFLOP/s" else 1e9
+        ach = work / avg_s / scale
+        out[name] = {"kernel": name, "bound": bound, "launches": n, "total_ms": ms, "avg_us": avg_s * 1e6,
+                     "work_per_launch": work, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+                     "traffic": None, "peak_kind": kind}
+    return out
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None."""
+    try:
+        for line in open(os.path.join(ROOT, "profiles", "ncu_traffic_per_launch.txt")):
+            p = line.split()
+            if len(p) == 2 and not line.startswith("#") and p[0] == kernel:
+                return int(p[1])
+    except OSError:
+        pass
+    return None
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -233,12 +285,16 @@ def main():
     lu_ms = sum(s["t_lu_ms"] for s in stats.values())
     n_lu = sum(s["newton_iters"] for s in stats.values())
     launches = sum(s["gpu_launches"] for s in stats.values())
+    kern = kernel_rooflines(nl, step, N_BENCH, hbm_peak, tc_peak)
+    dom = max(kern.values(), key=lambda k: k["total_ms"])
+    roofline = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
+    roofline["traffic"] = ncu_traffic(dom["kernel"]) if dom["kernel"] in ("k_diag_lu", "k_offdiag") else None
+    roofline.update({"kernel": dom["kernel"], "launches": dom["launches"], "avg_us": dom["avg_us"],
+                     "work_per_launch": dom["work_per_launch"], "peak_kind": dom["peak_kind"]})
     lu_flops = 2.0 * N_BENCH ** 3 / 3.0
-    achieved = lu_flops / (lu_ms / n_lu / 1e3) / 1e12 if n_lu else 0.0
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": tc_peak, "unit": "TFLOP/s",
-                "frac": achieved / tc_peak, "traffic": None,
-                "kernel": "binary16 LU (whole factorisation, all its kernels)",
-                "peak_kind": f"{peak_kind} bf16 dense (fp16 same rate)"}
+    lu_tf = lu_flops / (lu_ms / n_lu / 1e3) / 1e12 if n_lu else 0.0
+    roofline_lu = {"bound": "tensor", "achieved": lu_tf, "peak": tc_peak, "unit": "TFLOP/s", "frac": lu_tf / tc_peak,
+                   "note": "whole binary16 LU (2N^3/3 flop) over its device time per factorisation"}
     per_c = {str(c): {"newton": s["newton_iters"], "lin_iters": s["lin_iters"], "ms": s["t_total_ms"],
                       "final_rel_res": s["hist"][-1], "lu_ms": s["t_lu_ms"], "lin_ms": s["t_lin_ms"]}
              for c, s in stats.items()}
@@ -258,7 +314,7 @@ def main():
             "vs_baseline": None, "dtype": "f16/f32/f64", "data": "synthetic (the paper's H-equation, x0=ones)",
             "config": {"workload": WORKLOAD, "N": N_BENCH, "c": list(SWEEP), "mode": "GMRESIR16",
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
-            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "roofline": roofline, "roofline_lu": roofline_lu, "kernels": kern, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "per_c": per_c, **extra}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(n_lu)

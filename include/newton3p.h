@@ -129,6 +129,14 @@ void nl_destroy(nl_solver* s);
 /* Message of the last failing call on this thread ("" if none). */
 const char* nl_last_error(void);
 
+/* Per-kernel timing for measurement.  Returns the number of launches and the
+ * summed device time (CUDA events on each launch's stream) of the kernel
+ * class timed since the previous call, then starts timing `kernel_class`
+ * (NULL or "" stops timing).  Classes: "k_diag_lu", "k_offdiag",
+ * "k_tc_gemm", "k_trsv_mb", "k_gemv_residual".  Not thread-safe against
+ * concurrent solves on other threads.  Synchronises the recorded events. */
+nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* total_ms);
+
 /* Library version string. */
 const char* nl_version(void);
 

@@ -30,6 +30,11 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int num_sms();
 
+// Optional per-kernel-class timing (nl_kernel_timing): when enabled for a
+// class, every launch of it is bracketed by CUDA events on its stream.
+void prof_begin(const char* kernel_class, cudaStream_t st);
+void prof_end(const char* kernel_class, cudaStream_t st);
+
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum
 // minus the kernel's static shared memory.  Clears the runtime error state on
 // failure and reports it as NL_ECUDA.

@@ -284,7 +284,9 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
     // at least 58 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
     const size_t smem = std::max<size_t>(1024 + (size_t)KT * (kTcBM + kTcBN) * 128 + 64, 58 * 1024);
     dim3 grid((unsigned)cdiv(Nc, kTcBN), (unsigned)cdiv(M, kTcBM));
+    prof_begin("k_tc_gemm", st);
     k_tc_gemm<<<grid, kTcThreads, smem, st>>>(tmA, tmB, M, Nc, K, C, ldc, g_tc_err, flag);
+    prof_end("k_tc_gemm", st);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }

@@ -127,8 +127,10 @@ nl_status launch_gemv_residual(int N, const float* A, int64_t ld, const float* b
         set_error("gemv: A rows and u must be 16-byte aligned (ld multiple of 4)");
         return NL_EINVAL;
     }
+    prof_begin("k_gemv_residual", st);
     k_gemv_residual<<<(unsigned)cdiv(N, kGemvWarps), kGemvWarps * 32, 0, st>>>(N, A, ld, b, u, r, partial, counter,
                                                                               rnorm);
+    prof_end("k_gemv_residual", st);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }

@@ -1014,15 +1014,19 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         const size_t trsm_smem = (size_t)wd * wd * sizeof(T) + (size_t)wd * kTrsmThreads * sizeof(T);
         if (fast) {
             const int wp = (int)round_up(wd, 32);
+            prof_begin("k_diag_lu", st);
             k_diag_lu<T, S, RND><<<1, kDiagThreads, (size_t)wp * (wp + 1) * sizeof(T), st>>>(A, ld, K, wd, ipiv,
                                                                                         w.flag, w.stage);
+            prof_end("k_diag_lu", st);
             ++nl;
             if (rest > 0) {
                 const int nrb = (int)cdiv(rest, kOffThreads / kOffG);
                 const size_t hsz = std::is_same<T, float>::value ? 2 : 8;
                 const size_t sm = (size_t)wp * wp * hsz + (size_t)wp * (kOffThreads / kOffG) * hsz;
+                prof_begin("k_offdiag", st);
                 k_offdiag<T, S, RND><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb, tc ? w.ut : nullptr, nb,
                                                                       w.flag, w.stage);
+                prof_end("k_offdiag", st);
                 nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
                 if (s != NL_OK) return s;
                 nl += 2;

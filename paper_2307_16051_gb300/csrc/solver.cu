@@ -15,6 +15,8 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -43,6 +45,34 @@ int num_sms()
         if (n <= 0) n = 1;
     }
     return n;
+}
+
+// ---------------------------------------------------- per-kernel timing --
+struct KernelTiming {
+    std::mutex mu;
+    std::string cls;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    int open = -1;
+};
+static KernelTiming g_kt;
+
+void prof_begin(const char* kernel_class, cudaStream_t st)
+{
+    if (g_kt.cls.empty() || g_kt.cls != kernel_class) return;
+    std::lock_guard<std::mutex> lock(g_kt.mu);
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
+    cudaEventRecord(a, st);
+    g_kt.ev.push_back({a, b});
+    g_kt.open = (int)g_kt.ev.size() - 1;
+}
+
+void prof_end(const char* kernel_class, cudaStream_t st)
+{
+    if (g_kt.cls.empty() || g_kt.cls != kernel_class) return;
+    std::lock_guard<std::mutex> lock(g_kt.mu);
+    if (g_kt.open >= 0) cudaEventRecord(g_kt.ev[g_kt.open].second, st);
+    g_kt.open = -1;
 }
 
 int set_max_dynamic_smem(const void* func)
@@ -281,6 +311,28 @@ nl_status nl_config_default(nl_config* cfg)
 }
 
 const char* nl_last_error(void) { return get_error(); }
+
+nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* total_ms)
+{
+    std::lock_guard<std::mutex> lock(g_kt.mu);
+    double tot = 0.0;
+    int n = 0;
+    for (auto& p : g_kt.ev) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(p.second) == cudaSuccess && cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) {
+            tot += ms;
+            ++n;
+        }
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    g_kt.ev.clear();
+    g_kt.open = -1;
+    if (launches) *launches = n;
+    if (total_ms) *total_ms = tot;
+    g_kt.cls = kernel_class ? kernel_class : "";
+    return NL_OK;
+}
 const char* nl_version(void) { return "newton3p-gb300 0.1 (sm_103a)"; }
 
 nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)

@@ -486,7 +486,10 @@ static nl_status launch_trsv_mb(int N, const __half* LU, int64_t ld, const float
     unsigned* err = w.err;
     void* args[] = {(void*)&N,   (void*)&nblk, (void*)&LU,  (void*)&ld,    (void*)&v,   (void*)&vin_mb,
                     (void*)&perm, (void*)&dinv, (void*)&mb, (void*)&out, (void*)&epoch, (void*)&err};
-    NL_CUDA_OK(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kMbThreads), args, smem, st));
+    prof_begin("k_trsv_mb", st);
+    cudaError_t le = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kMbThreads), args, smem, st);
+    prof_end("k_trsv_mb", st);
+    NL_CUDA_OK(le);
     return NL_OK;
 }
 

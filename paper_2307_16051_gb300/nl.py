@@ -64,6 +64,7 @@ SIGNATURES = {
     "nl_destroy": (None, [_P]),
     "nl_last_error": (ctypes.c_char_p, []),
     "nl_version": (ctypes.c_char_p, []),
+    "nl_kernel_timing": (_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]),
     "nl_k_residual": (_int, [_i64, _dbl, _P, _P, _int, _dbl, _P, _P, _P, _P, _P]),
     "nl_k_jacobian": (_int, [_i64, _dbl, _P, _P, _i64, _P, _i64, _P]),
     "nl_k_jacobian64": (_int, [_i64, _dbl, _P, _P, _i64, _P]),
@@ -135,6 +136,14 @@ def config(**kw) -> Config:
     for k, v in kw.items():
         setattr(c, k, v)
     return c
+
+
+def kernel_timing(kernel_class=None):
+    """(launches, total_ms) of the class timed so far; then time `kernel_class`."""
+    cnt = ctypes.c_int(0)
+    ms = ctypes.c_double(0.0)
+    check(lib().nl_kernel_timing(kernel_class.encode() if kernel_class else None, ctypes.byref(cnt), ctypes.byref(ms)))
+    return cnt.value, ms.value
 
 
 class Solver:
