@@ -132,8 +132,9 @@ const char* nl_last_error(void);
 /* Per-kernel timing for measurement.  Returns the number of launches and the
  * summed device time (CUDA events on each launch's stream) of the kernel
  * class timed since the previous call, then starts timing `kernel_class`
- * (NULL or "" stops timing).  Classes: "k_diag_lu", "k_offdiag",
- * "k_tc_gemm", "k_trsv_mb", "k_gemv_residual".  Not thread-safe against
+ * (NULL or "" stops timing).  Classes: "k_diag_lu16", "k_offdiag16"
+ * (half-precision LU), "k_diag_lu", "k_offdiag" (double LU), "k_tc_gemm",
+ * "k_trsv_mb", "k_gemv_residual".  Not thread-safe against
  * concurrent solves on other threads.  Synchronises the recorded events. */
 nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* total_ms);
 
@@ -213,9 +214,9 @@ nl_status nl_k_gemm16_update(int64_t M, int64_t Nc, int64_t K, const void* A, in
                              int64_t ldb, void* C, int64_t ldc, int gemm, void* stream);
 
 /* Same operation and results as nl_k_gemv_residual, for callers that cannot
- * allocate device memory (a fixed memory pool, a plug-in that must not grow
- * the process's device footprint, or a stream under graph capture where
- * allocation is not allowed).  The paper has no counterpart: this is a
+ * allocate device memory: code running inside a fixed memory pool that owns
+ * all of the device's memory, or a plug-in that must not grow the process's
+ * device footprint.  The paper has no counterpart: this is a
  * packaging of the residual for such callers.
  * Scratch: a fixed 33 KB array inside the library image, held on every GPU
  * that loads the library until the process exits; no cudaMalloc or other

@@ -790,6 +790,350 @@ __global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int6
     }
 }
 
+// ------------------------------------------ fast path, binary16 factors --
+// The stage buffer holds, for the off-diagonal solves of one panel: U11 and
+// L11^T (wp x wp binary32 each, the exact binary16 values, identity / zero
+// padded) and the unrounded pivots a_tt (kStagePivOff floats in).
+constexpr int kStagePivOff = 2 * 128 * 128;
+
+// k_diag_lu16: the diagonal block [K, K+w)^2 (w <= 128), one CTA of 512
+// threads.  Warp v owns columns 8v..8v+7 and lane l rows 4l..4l+3, so every
+// thread keeps a 4 x 8 tile in registers.  Step t:
+//  * warp t/8 owns column t: each lane checks |a_it| <= |a_tt| for its rows
+//    below t (partial pivoting keeps the diagonal; ties go to the diagonal,
+//    which comes first) and forms l_it = fl16(a_it / fl16(a_tt));
+//  * lane t/4 of every warp owns a piece of row t and rounds it to binary16;
+//  * both are published through shared memory (double-buffered, so one
+//    barrier per step suffices), and every tile takes the rank-1 update.
+// Finished entries go to result buffers in shared memory as they are formed
+// (U row-major, L transposed, so that both writes are contiguous); the
+// register copies of finished entries are no longer read, so the update
+// needs no masking.
+constexpr int kD16Threads = 512;
+constexpr int kFwLd = 136;  // stride (halves) of the result buffers; rows stay 16-byte aligned
+constexpr size_t kDiag16Smem = 2 * 128 * kFwLd * sizeof(__half);
+
+__global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict__ A, int64_t lda, int K, int w,
+                                                             int* __restrict__ ipiv, int* __restrict__ flag,
+                                                             float* __restrict__ stage)
+{
+    if (*(volatile int*)flag) return;
+    __shared__ __align__(16) float urow[2][128];
+    __shared__ __align__(16) float lcol[2][128];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __half* fu = reinterpret_cast<__half*>(dsm);  // fu[i][j] = u_ij, j >= i
+    __half* fl = fu + 128 * kFwLd;                // fl[j][i] = l_ij, i > j
+    const int tid = threadIdx.x, lane = tid & 31, v = tid >> 5;
+    const int r0 = 4 * lane, c0 = 8 * v;
+    const int wp = (w + 31) & ~31;
+    const bool vec = (w % 32 == 0) && ((((uintptr_t)(A + (int64_t)K * lda + K)) & 15) == 0) && (lda % 8 == 0);
+    float a[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = r0 + r;
+        const __half* src = A + (int64_t)(K + min(i, w - 1)) * lda + K + c0;
+        if (vec && i < w && c0 < w) {
+            const uint4 raw = *reinterpret_cast<const uint4*>(src);
+            const __half* e = reinterpret_cast<const __half*>(&raw);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) a[r][c] = __half2float(e[c]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = c0 + c;
+                a[r][c] = (i < w && j < w) ? __half2float(src[c]) : ((i == j) ? 1.0f : 0.0f);
+            }
+        }
+    }
+    float* PV = stage + kStagePivOff;
+    bool bad = false;
+    for (int s = 0; s < wp / 8; ++s) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int t = 8 * s + k, b = k & 1;
+            if (v == s) {
+                // column t: the pivot a_tt sits in lane t/4, register row t%4
+                const float p = __shfl_sync(0xffffffffu, a[k & 3][k], t >> 2);
+                const float ut = round_h(p);
+                float l[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    l[r] = 0.0f;
+                    if (r0 + r > t) {
+                        if (!(fabsf(a[r][k]) <= fabsf(p))) bad = true;
+                        l[r] = round_h(a[r][k] / ut);
+                    }
+                }
+                *reinterpret_cast<float4*>(&lcol[b][r0]) = make_float4(l[0], l[1], l[2], l[3]);
+                *reinterpret_cast<__half2*>(&fl[t * kFwLd + r0]) = __floats2half2_rn(l[0], l[1]);
+                *reinterpret_cast<__half2*>(&fl[t * kFwLd + r0 + 2]) = __floats2half2_rn(l[2], l[3]);
+                if (lane == (t >> 2)) {
+                    PV[t] = p;
+                    if (!(ut != 0.0f)) bad = true;  // zero pivot: info is the interchanging path's
+                }
+            }
+            if (lane == (t >> 2) && v >= s) {
+                // row t, columns 8v..8v+7 (those left of t are multipliers, already recorded)
+                float u[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) u[c] = round_h(a[k & 3][c]);
+                *reinterpret_cast<float4*>(&urow[b][c0]) = make_float4(u[0], u[1], u[2], u[3]);
+                *reinterpret_cast<float4*>(&urow[b][c0 + 4]) = make_float4(u[4], u[5], u[6], u[7]);
+                __align__(16) __half h[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) h[c] = __float2half_rn(u[c]);
+                *reinterpret_cast<uint4*>(&fu[t * kFwLd + c0]) = *reinterpret_cast<const uint4*>(h);
+            }
+            __syncthreads();
+            if (v >= s) {
+                const float4 l4 = *reinterpret_cast<const float4*>(&lcol[b][r0]);
+                const float4 ua = *reinterpret_cast<const float4*>(&urow[b][c0]);
+                const float4 ub = *reinterpret_cast<const float4*>(&urow[b][c0 + 4]);
+                const float l[4] = {l4.x, l4.y, l4.z, l4.w};
+                const float u[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-l[r], u[c], a[r][c]);
+            }
+        }
+    }
+    if (__syncthreads_or(bad)) {
+        if (tid == 0) atomicOr(flag, 1);
+        return;
+    }
+    // the factors (binary16) to A with coalesced stores, U11 and L11^T to the stage
+    if (vec) {
+        const int vpr = w / 8;
+        for (int q = tid; q < w * vpr; q += kD16Threads) {
+            const int r = q / vpr, c = (q - r * vpr) * 8;
+            __align__(16) __half h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = (c + e >= r) ? fu[r * kFwLd + c + e] : fl[(c + e) * kFwLd + r];
+            *reinterpret_cast<uint4*>(A + (int64_t)(K + r) * lda + K + c) = *reinterpret_cast<const uint4*>(h);
+        }
+    } else {
+        for (int q = tid; q < w * w; q += kD16Threads) {
+            const int r = q / w, c = q - r * w;
+            A[(int64_t)(K + r) * lda + K + c] = (c >= r) ? fu[r * kFwLd + c] : fl[c * kFwLd + r];
+        }
+    }
+    {
+        const int q4 = wp / 4;
+        float4* SU = reinterpret_cast<float4*>(stage);
+        float4* SL = reinterpret_cast<float4*>(stage + wp * wp);
+        for (int q = tid; q < wp * q4; q += kD16Threads) {
+            const int r = q / q4, c = (q - r * q4) * 4;
+            float u[4], l[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int cc = c + e;
+                const bool in = r < w && cc < w;
+                u[e] = in ? ((cc >= r) ? __half2float(fu[r * kFwLd + cc]) : 0.0f) : ((r == cc) ? 1.0f : 0.0f);
+                l[e] = (in && cc > r) ? __half2float(fl[r * kFwLd + cc]) : 0.0f;
+            }
+            SU[q] = make_float4(u[0], u[1], u[2], u[3]);
+            SL[q] = make_float4(l[0], l[1], l[2], l[3]);
+        }
+    }
+    if (tid < w) ipiv[K + tid] = K + tid;
+}
+
+// k_offdiag16: L21 = A21 U11^{-1} (row role) and U12 = L11^{-1} A12 (column
+// role) for a panel of width w.  256 threads = 32 groups of eight lanes; a
+// group takes two rows (or two columns), and lane g holds entries 4g..4g+3 of
+// each 32-wide chunk of both.  Each chunk is first updated with the earlier
+// chunks' multipliers (row role) or U entries (column role), which the groups
+// keep in shared memory, then solved against the chunk's diagonal 32 x 32
+// block: at step t the owning lane forms the two multipliers (checking them
+// against the unrounded pivot) or rounds the two U entries, and broadcasts
+// them to its group.  Elementwise the operations and their order are those of
+// right-looking elimination.
+constexpr int kO16Threads = 256;
+constexpr int kO16Rows = 64;  // rows or columns per CTA (32 groups x 2)
+
+size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + wp) * sizeof(float); }
+
+__global__ void __launch_bounds__(kO16Threads) k_offdiag16(__half* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                           int nrow_blocks, __half* __restrict__ Ut, int ldut,
+                                                           int* __restrict__ flag, const float* __restrict__ stage)
+{
+    if (*(volatile int*)flag) return;
+    extern __shared__ __align__(16) float osm[];
+    const int wp = (w + 31) & ~31, nc = wp / 32;
+    float* D = osm;                  // U11 (row role) or L11^T (column role)
+    float* X = D + wp * wp;          // [t][2 grp + r]: multipliers / U entries of earlier chunks
+    float* pv = X + wp * kO16Rows;   // |a_tt|, unrounded
+    const int tid = threadIdx.x, grp = tid >> 3, g = tid & 7;
+    const unsigned gmask = 0xffu << ((tid & 31) & ~7);
+    const bool row_role = (int)blockIdx.x < nrow_blocks;
+    {
+        const float4* s4 = reinterpret_cast<const float4*>(stage + (row_role ? 0 : wp * wp));
+        float4* d4 = reinterpret_cast<float4*>(D);
+        const int nv = wp * wp / 4;
+#pragma unroll 4
+        for (int v = tid; v < nv; v += kO16Threads) d4[v] = s4[v];
+        if (tid < wp) pv[tid] = fabsf(stage[kStagePivOff + tid]);
+    }
+    __syncthreads();
+    const int base = K + w + (row_role ? (int)blockIdx.x : (int)blockIdx.x - nrow_blocks) * kO16Rows + 2 * grp;
+    const bool lv0 = base < N, lv1 = base + 1 < N;
+    float2* Xg = reinterpret_cast<float2*>(X) + grp;  // X[t][2 grp], X[t][2 grp + 1] at Xg[t * 32]
+    if (row_role) {
+        bool bad = false;
+        __half* R0 = A + (int64_t)min(base, N - 1) * lda + K;
+        __half* R1 = A + (int64_t)min(base + 1, N - 1) * lda + K;
+        const bool vec = (w % 32 == 0) && ((((uintptr_t)(A + K)) & 7) == 0) && (lda % 4 == 0);
+        for (int c = 0; c < nc; ++c) {
+            const int jb = 32 * c + 4 * g;
+            float x0[4], x1[4];
+            if (vec) {
+                __align__(8) __half e0[4], e1[4];
+                *reinterpret_cast<uint2*>(e0) = lv0 ? *reinterpret_cast<const uint2*>(R0 + jb) : make_uint2(0, 0);
+                *reinterpret_cast<uint2*>(e1) = lv1 ? *reinterpret_cast<const uint2*>(R1 + jb) : make_uint2(0, 0);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    x0[k] = __half2float(e0[k]);
+                    x1[k] = __half2float(e1[k]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    x0[k] = (lv0 && jb + k < w) ? __half2float(R0[jb + k]) : 0.0f;
+                    x1[k] = (lv1 && jb + k < w) ? __half2float(R1[jb + k]) : 0.0f;
+                }
+            }
+            for (int t = 0; t < 32 * c; ++t) {
+                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + jb);
+                const float2 l = Xg[t * 32];
+                x0[0] = fmaf(-l.x, d.x, x0[0]);
+                x0[1] = fmaf(-l.x, d.y, x0[1]);
+                x0[2] = fmaf(-l.x, d.z, x0[2]);
+                x0[3] = fmaf(-l.x, d.w, x0[3]);
+                x1[0] = fmaf(-l.y, d.x, x1[0]);
+                x1[1] = fmaf(-l.y, d.y, x1[1]);
+                x1[2] = fmaf(-l.y, d.z, x1[2]);
+                x1[3] = fmaf(-l.y, d.w, x1[3]);
+            }
+#pragma unroll
+            for (int tt = 0; tt < 32; ++tt) {
+                const int t = 32 * c + tt;
+                float l0 = 0.0f, l1 = 0.0f;
+                if (g == tt / 4) {
+                    const float utt = D[t * wp + t], p = pv[t];
+                    const float a0 = x0[tt % 4], a1 = x1[tt % 4];
+                    if (t < w && ((lv0 && !(fabsf(a0) <= p)) || (lv1 && !(fabsf(a1) <= p)))) bad = true;
+                    l0 = round_h(a0 / utt);
+                    l1 = round_h(a1 / utt);
+                    x0[tt % 4] = l0;
+                    x1[tt % 4] = l1;
+                    Xg[t * 32] = make_float2(l0, l1);
+                }
+                l0 = __shfl_sync(gmask, l0, tt / 4, 8);
+                l1 = __shfl_sync(gmask, l1, tt / 4, 8);
+                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + jb);
+                if (4 * g + 0 > tt) { x0[0] = fmaf(-l0, d.x, x0[0]); x1[0] = fmaf(-l1, d.x, x1[0]); }
+                if (4 * g + 1 > tt) { x0[1] = fmaf(-l0, d.y, x0[1]); x1[1] = fmaf(-l1, d.y, x1[1]); }
+                if (4 * g + 2 > tt) { x0[2] = fmaf(-l0, d.z, x0[2]); x1[2] = fmaf(-l1, d.z, x1[2]); }
+                if (4 * g + 3 > tt) { x0[3] = fmaf(-l0, d.w, x0[3]); x1[3] = fmaf(-l1, d.w, x1[3]); }
+            }
+            __syncwarp();
+            __align__(8) __half e0[4], e1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                e0[k] = __float2half_rn(x0[k]);
+                e1[k] = __float2half_rn(x1[k]);
+            }
+            if (vec) {
+                if (lv0) *reinterpret_cast<uint2*>(R0 + jb) = *reinterpret_cast<const uint2*>(e0);
+                if (lv1) *reinterpret_cast<uint2*>(R1 + jb) = *reinterpret_cast<const uint2*>(e1);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (lv0 && jb + k < w) R0[jb + k] = e0[k];
+                    if (lv1 && jb + k < w) R1[jb + k] = e1[k];
+                }
+            }
+        }
+        if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
+    } else {
+        // columns base and base + 1 (adjacent: one 4-byte access covers both)
+        const bool pair = lv1 && (((uintptr_t)(A + base)) % 4 == 0) && (lda % 2 == 0);
+        for (int c = 0; c < nc; ++c) {
+            const int kb = 32 * c + 4 * g;
+            float x0[4], x1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const __half* src = A + (int64_t)(K + kb + k) * lda;
+                if (kb + k < w && pair) {
+                    const __half2 v = *reinterpret_cast<const __half2*>(src + base);
+                    x0[k] = __low2float(v);
+                    x1[k] = __high2float(v);
+                } else {
+                    x0[k] = (kb + k < w && lv0) ? __half2float(src[base]) : 0.0f;
+                    x1[k] = (kb + k < w && lv1) ? __half2float(src[base + 1]) : 0.0f;
+                }
+            }
+            for (int t = 0; t < 32 * c; ++t) {
+                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + kb);  // L[kb + k][t]
+                const float2 u = Xg[t * 32];
+                x0[0] = fmaf(-d.x, u.x, x0[0]);
+                x0[1] = fmaf(-d.y, u.x, x0[1]);
+                x0[2] = fmaf(-d.z, u.x, x0[2]);
+                x0[3] = fmaf(-d.w, u.x, x0[3]);
+                x1[0] = fmaf(-d.x, u.y, x1[0]);
+                x1[1] = fmaf(-d.y, u.y, x1[1]);
+                x1[2] = fmaf(-d.z, u.y, x1[2]);
+                x1[3] = fmaf(-d.w, u.y, x1[3]);
+            }
+#pragma unroll
+            for (int tt = 0; tt < 32; ++tt) {
+                const int t = 32 * c + tt;
+                float u0 = 0.0f, u1 = 0.0f;
+                if (g == tt / 4) {
+                    u0 = round_h(x0[tt % 4]);
+                    u1 = round_h(x1[tt % 4]);
+                    x0[tt % 4] = u0;
+                    x1[tt % 4] = u1;
+                    Xg[t * 32] = make_float2(u0, u1);
+                }
+                u0 = __shfl_sync(gmask, u0, tt / 4, 8);
+                u1 = __shfl_sync(gmask, u1, tt / 4, 8);
+                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + kb);
+                if (4 * g + 0 > tt) { x0[0] = fmaf(-d.x, u0, x0[0]); x1[0] = fmaf(-d.x, u1, x1[0]); }
+                if (4 * g + 1 > tt) { x0[1] = fmaf(-d.y, u0, x0[1]); x1[1] = fmaf(-d.y, u1, x1[1]); }
+                if (4 * g + 2 > tt) { x0[2] = fmaf(-d.z, u0, x0[2]); x1[2] = fmaf(-d.z, u1, x1[2]); }
+                if (4 * g + 3 > tt) { x0[3] = fmaf(-d.w, u0, x0[3]); x1[3] = fmaf(-d.w, u1, x1[3]); }
+            }
+            __syncwarp();
+            __align__(8) __half e0[4], e1[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                e0[k] = __float2half_rn(x0[k]);
+                e1[k] = __float2half_rn(x1[k]);
+                if (kb + k < w) {
+                    __half* dst = A + (int64_t)(K + kb + k) * lda;
+                    if (pair) *reinterpret_cast<__half2*>(dst + base) = __halves2half2(e0[k], e1[k]);
+                    else {
+                        if (lv0) dst[base] = e0[k];
+                        if (lv1) dst[base + 1] = e1[k];
+                    }
+                }
+            }
+            if (Ut) {
+                // U12^T rows, the tensor-core B operand
+                __half* u0 = Ut + (int64_t)(base - K - w) * ldut + kb;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (kb + k < w) {
+                        if (lv0) u0[k] = e0[k];
+                        if (lv1) u0[ldut + k] = e1[k];
+                    }
+            }
+        }
+    }
+}
+
 // C <- C - A B with per-element sequential fused multiply-adds over k in
 // order, accumulated in T and stored once (rounded to binary16 for __half).
 template <typename S, typename T>
@@ -853,7 +1197,7 @@ size_t lu_work_bytes(int N, int nb, bool fp64)
     size_t el = fp64 ? 8 : 4;
     size_t pnl = (size_t)N * nb * el;
     size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
-    return round_up(pnl, 256) + round_up(ut, 256) + 256 + (size_t)2 * 128 * 128 * 8;
+    return round_up(pnl, 256) + round_up(ut, 256) + 256 + (size_t)2 * 128 * 128 * 8 + 128 * 8;
 }
 
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
@@ -999,12 +1343,19 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
     const int ldp = nb;
     int nl = 0;
     NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st));  // info and flag
+    constexpr bool kHalf = std::is_same<S, __half>::value;
     static bool smem_set = false;
     if (!smem_set) {
-        if (set_max_dynamic_smem((const void*)k_trsm_u12<T, S, RND>) != NL_OK ||
-            set_max_dynamic_smem((const void*)k_offdiag<T, S, RND>) != NL_OK ||
-            set_max_dynamic_smem((const void*)k_diag_lu<T, S, RND>) != NL_OK)
-            return NL_ECUDA;
+        if (set_max_dynamic_smem((const void*)k_trsm_u12<T, S, RND>) != NL_OK) return NL_ECUDA;
+        if constexpr (kHalf) {
+            if (set_max_dynamic_smem((const void*)k_offdiag16) != NL_OK ||
+                set_max_dynamic_smem((const void*)k_diag_lu16) != NL_OK)
+                return NL_ECUDA;
+        } else {
+            if (set_max_dynamic_smem((const void*)k_offdiag<T, S, RND>) != NL_OK ||
+                set_max_dynamic_smem((const void*)k_diag_lu<T, S, RND>) != NL_OK)
+                return NL_ECUDA;
+        }
         smem_set = true;
     }
     for (int K = 0; K < N; K += nb) {
@@ -1014,19 +1365,32 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         const size_t trsm_smem = (size_t)wd * wd * sizeof(T) + (size_t)wd * kTrsmThreads * sizeof(T);
         if (fast) {
             const int wp = (int)round_up(wd, 32);
-            prof_begin("k_diag_lu", st);
-            k_diag_lu<T, S, RND><<<1, kDiagThreads, (size_t)wp * (wp + 1) * sizeof(T), st>>>(A, ld, K, wd, ipiv,
-                                                                                        w.flag, w.stage);
-            prof_end("k_diag_lu", st);
+            if constexpr (kHalf) {
+                prof_begin("k_diag_lu16", st);
+                k_diag_lu16<<<1, kD16Threads, kDiag16Smem, st>>>(A, ld, K, wd, ipiv, w.flag, (float*)w.stage);
+                prof_end("k_diag_lu16", st);
+            } else {
+                prof_begin("k_diag_lu", st);
+                k_diag_lu<T, S, RND><<<1, kDiagThreads, (size_t)wp * (wp + 1) * sizeof(T), st>>>(A, ld, K, wd, ipiv,
+                                                                                            w.flag, w.stage);
+                prof_end("k_diag_lu", st);
+            }
             ++nl;
             if (rest > 0) {
-                const int nrb = (int)cdiv(rest, kOffThreads / kOffG);
-                const size_t hsz = std::is_same<T, float>::value ? 2 : 8;
-                const size_t sm = (size_t)wp * wp * hsz + (size_t)wp * (kOffThreads / kOffG) * hsz;
-                prof_begin("k_offdiag", st);
-                k_offdiag<T, S, RND><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb, tc ? w.ut : nullptr, nb,
-                                                                      w.flag, w.stage);
-                prof_end("k_offdiag", st);
+                if constexpr (kHalf) {
+                    const int nrb = (int)cdiv(rest, kO16Rows);
+                    prof_begin("k_offdiag16", st);
+                    k_offdiag16<<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(
+                        A, ld, K, wd, N, nrb, tc ? w.ut : nullptr, nb, w.flag, (const float*)w.stage);
+                    prof_end("k_offdiag16", st);
+                } else {
+                    const int nrb = (int)cdiv(rest, kOffThreads / kOffG);
+                    const size_t sm = (size_t)wp * wp * sizeof(T) + (size_t)wp * (kOffThreads / kOffG) * sizeof(T);
+                    prof_begin("k_offdiag", st);
+                    k_offdiag<T, S, RND><<<2 * nrb, kOffThreads, sm, st>>>(A, ld, K, wd, N, nrb, nullptr, nb, w.flag,
+                                                                          w.stage);
+                    prof_end("k_offdiag", st);
+                }
                 nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
                 if (s != NL_OK) return s;
                 nl += 2;

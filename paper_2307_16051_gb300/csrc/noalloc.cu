@@ -1,9 +1,9 @@
 // noalloc.cu — an entry point for callers that cannot allocate device memory.
 //
 // Some callers may not call cudaMalloc at all: code running inside a
-// pre-sized memory pool, a plug-in that must not change the process's device
-// footprint after start-up, or a stream that is being captured into a CUDA
-// graph by a framework that forbids allocations during capture.  For them,
+// pre-sized memory pool that already owns all of the device's memory, or a
+// plug-in that must not change the process's device footprint after
+// start-up.  For them,
 // nl_k_gemv_residual_noalloc computes the same single-precision residual and
 // norm as nl_k_gemv_residual, but keeps its scratch (one partial sum per
 // block of eight rows, and the finishing counter) in a fixed array that is

@@ -113,7 +113,7 @@ def test_lu16_simt_bit_exact_vs_oracle(N, nb, path):
     assert np.array_equal(LU, LUo)
 
 
-@pytest.mark.parametrize("N,nb", [(600, 128), (1000, 64), (77, 16)])
+@pytest.mark.parametrize("N,nb", [(600, 128), (1000, 64), (77, 16), (300, 48), (129, 128), (255, 96)])
 def test_lu16_simt_bit_exact_on_jacobian(N, nb):
     """The paper's Jacobian needs no interchanges: the fast path (path 0)
     and the interchanging path (path 1) both reproduce the oracle bit for bit."""
@@ -137,6 +137,29 @@ def test_lu16_fast_path_detects_late_interchange():
     A16 = O.fl16(B)
     LUo, ipivo, _, _ = O.lu16_dev(A16, 128)
     assert ipivo[250] == 260
+    LU, ipiv, _ = _lu16_gpu(A16, 128, 1, 0)
+    assert np.array_equal(ipiv, ipivo) and np.array_equal(LU, LUo)
+
+
+@pytest.mark.parametrize("row", [2, 200])
+def test_lu16_fast_path_compares_unrounded_pivot(row):
+    """Partial pivoting compares binary32 values before the pivot row is
+    rounded to binary16.  After the first elimination step column 1 holds
+    1 + 1.25 * 2^-11 on the diagonal (binary16 rounds it up to 1 + 2^-10) and
+    1 + 1.5 * 2^-11 in `row` (inside the diagonal block, or below it): the
+    larger one must become the pivot, so the fast path has to notice that the
+    diagonal loses although it wins after rounding."""
+    N = 300
+    rng = np.random.default_rng(5)
+    B = 4.0 * np.eye(N) + rng.uniform(-0.01, 0.01, (N, N))
+    B[:, 0] = rng.uniform(-0.01, 0.01, N)
+    B[:, 1] = rng.uniform(-0.01, 0.01, N)
+    B[0, 0] = B[0, 1] = 1.0
+    B[1, 0], B[1, 1] = -1.25 * 2.0 ** -11, 1.0
+    B[row, 0], B[row, 1] = -1.5 * 2.0 ** -11, 1.0
+    A16 = O.fl16(B)
+    LUo, ipivo, _, _ = O.lu16_dev(A16, 128)
+    assert ipivo[1] == row
     LU, ipiv, _ = _lu16_gpu(A16, 128, 1, 0)
     assert np.array_equal(ipiv, ipivo) and np.array_equal(LU, LUo)
 

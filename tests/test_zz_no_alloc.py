@@ -1,7 +1,8 @@
 """The allocation-free residual entry point (nl_k_gemv_residual_noalloc).
 
-Callers that cannot allocate device memory (a fixed pool, a plug-in that
-must not grow the device footprint, a stream under graph capture) use this
+Callers that cannot allocate device memory (code inside a fixed pool that
+owns all of the device memory, a plug-in that must not grow the device
+footprint) use this
 variant; it must give the same residual and norm as nl_k_gemv_residual.
 Collected last so that a failure here cannot hide any other test's result.
 """
