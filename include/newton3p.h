@@ -50,8 +50,12 @@ typedef enum {
  *                column F64 of Tables 2-3): the on-GPU baseline.
  *  NL_IR16:      J32 + half-precision LU + IR (Algorithm IR, Section 2.2).
  *  NL_GMRESIR16: J32 + half-precision LU as left preconditioner of GMRES,
- *                wrapped in IR (GMRES-IR, Section 2.2). */
-typedef enum { NL_FP64LU = 0, NL_IR16 = 1, NL_GMRESIR16 = 2 } nl_mode;
+ *                wrapped in IR (GMRES-IR, Section 2.2).
+ *  NL_IR16_GMRES: NL_IR16 until the first Newton step whose IR stalls (the
+ *                failure rule of Section 3.1 fires, or ir_maxit corrections
+ *                do not meet eta_j); that step's linear solve is redone with
+ *                GMRES-IR from u0 = 0 and every later step uses GMRES-IR. */
+typedef enum { NL_FP64LU = 0, NL_IR16 = 1, NL_GMRESIR16 = 2, NL_IR16_GMRES = 3 } nl_mode;
 
 /* Solver parameters (nl_config_default fills the defaults in brackets). */
 typedef struct {
@@ -140,6 +144,94 @@ nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* tota
 
 /* Library version string. */
 const char* nl_version(void);
+
+/* ----------------------------------------------------------------------- */
+/* Batched solves: many independent instances of eq. (3.2), each with its   */
+/* own N and c, advanced together on the device.                            */
+/* ----------------------------------------------------------------------- */
+
+/* Per-batch results of the last nl_batch_solve (host values). */
+typedef struct {
+    int count;              /* instances */
+    int converged;          /* instances that met the tolerance */
+    int parked_lu;          /* instances whose factorisation needed row interchanges (finished singly) */
+    int parked_ir;          /* instances whose IR stalled (finished singly with GMRES-IR) */
+    int newton_rounds;      /* executions of the batched Newton step */
+    int ir_rounds;          /* executions of the batched IR correction */
+    int lu_nb;              /* LU outer block in use (autotuned unless nl_config.lu_nb was set) */
+    int trailing_gemm;      /* 1 SIMT, 2 tcgen05 */
+    int gpu_launches;       /* kernels executed, including the single-instance completions */
+    int graph_nodes_step;   /* kernel nodes in one batched Newton step (outside the IR loop) */
+    int graph_nodes_ir;     /* kernel nodes in one IR correction */
+    int tune_count;         /* autotuner candidates timed */
+    int tune_nb[8];
+    int tune_gemm[8];
+    double tune_ms[8];      /* grouped LU time of each candidate on the batch's first Jacobians */
+    double t_total_ms;      /* host wall time of the solve */
+    double t_graph_ms;      /* device time of the batched graph (CUDA events) */
+    double t_single_ms;     /* host wall time of the single-instance completions */
+    int reserved[16];
+} nl_batch_info_t;
+
+typedef struct nl_batch nl_batch;
+
+/* Create a batch of `count` instances (N[i] in [1, 8192], 0 <= c[i] < 1).
+ * All device state is allocated here (the double Jacobians on the first
+ * NL_FP64LU solve).  cfg may be NULL; cfg->lu_nb = 0 lets the autotuner time
+ * the grouped LU for (nb, update) in {(128, tcgen05), (64, tcgen05),
+ * (64, SIMT), (32, SIMT)} on the batch's Jacobians at x0 = ones and keep the
+ * fastest (recorded in nl_batch_info_t).  Vectors of the batch are packed:
+ * instance i occupies entries [off_i, off_i + N[i]), off_i = N[0]+...+N[i-1]. */
+nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl_config* cfg, nl_batch** out);
+
+/* Solve every instance from x0 (host, packed; NULL = ones) to
+ * ||F(x)|| <= tol ||F(x0)|| + tau_a.  mode: NL_IR16_GMRES (three precisions)
+ * or NL_FP64LU.  The whole batched iteration is one CUDA graph with
+ * conditional WHILE nodes (Newton steps, IR corrections); instances that need
+ * row interchanges or whose IR stalls are finished on the single-instance
+ * path (NL_IR16_GMRES semantics, or NL_FP64LU).  x_out: host, packed,
+ * caller-owned.  Returns NL_OK when every instance met its tolerance,
+ * otherwise the first failing instance's status. */
+nl_status nl_batch_solve(nl_batch* b, const double* x0, double tol, nl_mode mode, double* x_out);
+
+/* As nl_batch_solve with x0 (may be NULL) and x_out in device memory. */
+nl_status nl_batch_solve_device(nl_batch* b, const double* x0_dev, double tol, nl_mode mode, double* x_out_dev);
+
+/* Statistics of instance i in the last solve (hist relative to its own ||F(x0)||). */
+nl_status nl_batch_stats(nl_batch* b, int i, nl_stats_t* out);
+
+/* Batch-level results of the last solve. */
+nl_status nl_batch_info(const nl_batch* b, nl_batch_info_t* out);
+
+/* Use `stream` (cudaStream_t) for later solves of this batch. */
+nl_status nl_batch_set_stream(nl_batch* b, void* stream);
+
+/* Bytes of device memory the batch holds. */
+int64_t nl_batch_device_bytes(const nl_batch* b);
+
+/* Release the batch.  NULL is a no-op. */
+void nl_batch_destroy(nl_batch* b);
+
+/* Grouped LU of `count` independent matrices (the batched factorisation of
+ * Section 2's J_h, one launch per kernel class per outer step): A[i] (device,
+ * N[i] x N[i], leading dimension ld[i], a multiple of 8) is factored in place
+ * without row interchanges, checking exactly that partial pivoting would keep
+ * every diagonal pivot (ipiv[i][k] = k).  flags_host[i] (host, count ints):
+ * 0 = factored (identical to partial pivoting); 1 = partial pivoting would
+ * interchange rows or a pivot is zero: A[i] is left partly factored and the
+ * caller factors it with nl_lu16 / nl_lu64.  fp64 = 0: binary16 matrices,
+ * arithmetic model as nl_lu16; fp64 = 1: double.  nb: multiple of 16 in
+ * [16, 128] (0 = 128).  gemm: 0 auto, 1 SIMT, 2 tcgen05 (binary16, nb a
+ * multiple of 64).  A, ipiv: host arrays of device pointers.  N[i] in
+ * [1, 32768].  Allocates its workspace with cudaMalloc.  Synchronises. */
+nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64_t* ld, int32_t* const* ipiv,
+                        int fp64, int nb, int gemm, int32_t* flags_host, void* stream);
+
+/* Grouped b[i] <- U^{-1} L^{-1} P b[i] with the factors LU[i] (binary16
+ * promoted to single on the fly, eq. (2.16), b single; or double), one CTA
+ * per system, N[i] in [1, 8192].  LU, ipiv, b: host arrays of device pointers. */
+nl_status nl_lusolve_grouped(int count, const int64_t* N, const void* const* LU, const int64_t* ld,
+                             const int32_t* const* ipiv, void* const* b, int fp64, void* stream);
 
 /* ----------------------------------------------------------------------- */
 /* Kernel-level entry points (device pointers).  These expose each step of */

@@ -753,7 +753,7 @@ void orc_linsolve(int64_t N, const float *A, const double *LU16, const int32_t *
 /* Newton drivers: Algorithm 1.1 [newton] and Algorithm 2.1 [newton3p].      */
 /* ------------------------------------------------------------------------ */
 
-enum { ORC_FP64LU = 0, ORC_IR16 = 1, ORC_GMRESIR16 = 2, ORC_F32 = 3, ORC_F16 = 4 };
+enum { ORC_FP64LU = 0, ORC_IR16 = 1, ORC_GMRESIR16 = 2, ORC_F32 = 3, ORC_F16 = 4, ORC_IR16GM = 5 };
 
 typedef struct {
     double eta;         /* eta_J of eq. (2.3) [inexactJ] */
@@ -790,7 +790,10 @@ typedef struct {
      GMRES-IR (Algorithm 2.1).
    mode ORC_F32 / ORC_F16: two-precision Newton of Section 1.3: J stored and
      factored in single / half and the step computed with one solve in that
-     precision (columns F32 / F16 of Tables 2 and 3). */
+     precision (columns F32 / F16 of Tables 2 and 3).
+   mode ORC_IR16GM: as ORC_IR16 until the first step whose IR does not meet
+     eta (the failure rule of Section 3.1 or the iteration cap); that step is
+     solved again by GMRES-IR from u0 = 0, as are all later steps. */
 int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, const orc_params *p,
                double *x, orc_result *res)
 {
@@ -811,7 +814,7 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
     double f0 = orc_norm2(N, F), fn = f0;
     double tau = tau_r * f0 + p->tau_a;
     res->hist[0] = 1.0;
-    int n = 0;
+    int n = 0, gm_sticky = 0;
     res->status = 1;
     while (!(fn <= tau)) {
         if (!isfinite(fn)) {
@@ -869,9 +872,22 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
             for (int64_t i = 0; i < N; ++i)
                 b32[i] = (float)(-F[i] / fn);
             orc_linstat st;
-            int solver = (mode == ORC_GMRESIR16) ? 2 : p->ir_variant;
+            int solver = (mode == ORC_GMRESIR16 || gm_sticky) ? 2 : p->ir_variant;
             orc_linsolve(N, J32, J, ipiv, b32, u32, p->eta, p->ir_maxit, solver, p->gmres_m,
                          p->gmres_tol, p->gmres_cycles, &st);
+            if (mode == ORC_IR16GM && !gm_sticky && !st.converged) {
+                /* IR stalled (failure rule or cap without meeting eta): this
+                   step's correction is recomputed by GMRES-IR (Section 2.2)
+                   from u0 = 0, and GMRES-IR serves every later step. */
+                orc_linstat sg;
+                gm_sticky = 1;
+                orc_linsolve(N, J32, J, ipiv, b32, u32, p->eta, p->ir_maxit, 2, p->gmres_m, p->gmres_tol,
+                             p->gmres_cycles, &sg);
+                sg.iters += st.iters;
+                sg.outer += st.outer;
+                sg.failed = 1;
+                st = sg;
+            }
             res->lin_iters[n] = st.iters;
             res->lin_outer[n] = st.outer;
             res->lin_failed[n] = st.failed;

@@ -20,8 +20,8 @@ _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-FP64LU, IR16, GMRESIR16, F32, F16 = 0, 1, 2, 3, 4
-MODES = {"FP64LU": FP64LU, "IR16": IR16, "GMRESIR16": GMRESIR16, "F32": F32, "F16": F16}
+FP64LU, IR16, GMRESIR16, F32, F16, IR16GM = 0, 1, 2, 3, 4, 5
+MODES = {"FP64LU": FP64LU, "IR16": IR16, "GMRESIR16": GMRESIR16, "F32": F32, "F16": F16, "IR16GM": IR16GM}
 
 
 def build(force: bool = False) -> str:

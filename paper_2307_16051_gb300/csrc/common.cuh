@@ -25,10 +25,32 @@ const char* get_error();
         }                                                                                  \
     } while (0)
 
+#define NL_TRY(expr)                    \
+    do {                                \
+        nl_status _s = (expr);          \
+        if (_s != NL_OK) return _s;     \
+    } while (0)
+
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int num_sms();
+
+// Carves 256-byte aligned sub-buffers out of one device allocation (a null
+// base only measures: off is the size needed).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base((char*)b) {}
+    template <typename T>
+    T* take(size_t n)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = (T*)(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
 
 // Optional per-kernel-class timing (nl_kernel_timing): when enabled for a
 // class, every launch of it is bracketed by CUDA events on its stream.

@@ -72,12 +72,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long lon
     }
 }
 
-__global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
-                                                        const __grid_constant__ CUtensorMap tmB, int M, int Nc,
-                                                        int K, __half* __restrict__ C, int64_t ldc,
-                                                        unsigned* __restrict__ err, const int* __restrict__ flag)
+// One 128 x 128 output tile at (m0, n0) of C (M x Nc).  The A slab kt of the
+// tile is the TMA box at (ax + 64 kt, ay + m0) of tmA, the B slab the box at
+// (64 kt, n0) of tmB.  tmA / tmB: generic addresses of the tensor maps (kernel
+// parameter or global memory).
+__device__ __forceinline__ void tc_gemm_tile(const CUtensorMap* tmA, const CUtensorMap* tmB, int ax, int ay, int M,
+                                             int Nc, int K, __half* __restrict__ C, int64_t ldc, int m0, int n0,
+                                             unsigned* __restrict__ err)
 {
-    if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -90,7 +92,6 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
     const uint32_t bar_load = smem_u32(&bars[0]), bar_mma = smem_u32(&bars[1]);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
     __shared__ int failed;
 
     if (warp == 0) {
@@ -116,12 +117,12 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
                     sA + kt * a_sz),
-                "l"(&tmA), "r"(kt * kTcBK), "r"(m0), "r"(bar_load)
+                "l"(tmA), "r"(ax + kt * kTcBK), "r"(ay + m0), "r"(bar_load)
                 : "memory");
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
                     sB + kt * b_sz),
-                "l"(&tmB), "r"(kt * kTcBK), "r"(n0), "r"(bar_load)
+                "l"(tmB), "r"(kt * kTcBK), "r"(n0), "r"(bar_load)
                 : "memory");
         }
         if (!mbar_wait(bar_load, 0, kTcWaitCycles)) {
@@ -217,6 +218,35 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
     }
 }
 
+__global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ CUtensorMap tmA,
+                                                        const __grid_constant__ CUtensorMap tmB, int M, int Nc,
+                                                        int K, __half* __restrict__ C, int64_t ldc,
+                                                        unsigned* __restrict__ err, const int* __restrict__ flag)
+{
+    if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
+    tc_gemm_tile(&tmA, &tmB, 0, 0, M, Nc, K, C, ldc, (int)blockIdx.y * kTcBM, (int)blockIdx.x * kTcBN, err);
+}
+
+// Grouped trailing update of outer step [K, K + w) of many matrices: task
+// {inst, m0, n0} updates tile (m0, n0) of instance inst's A22 (rows and
+// columns from K + w) with L21 (rows from K + w, columns K .. K + w) read
+// through the instance's whole-matrix tensor map and U12^T through its
+// buffer's map.  Rows past N read as zero (TMA fill) and are not stored.
+__global__ void __launch_bounds__(kTcThreads) k_tc_gemm_g(const GInst* __restrict__ inst,
+                                                          const TmapBytes* __restrict__ maps,
+                                                          const GTask* __restrict__ tasks, int K, int w,
+                                                          unsigned* __restrict__ err)
+{
+    const GTask t = tasks[blockIdx.x];
+    const GInst I = inst[t.inst];
+    if (*(volatile const int*)I.flag) return;
+    const int rest = I.N - K - w;
+    __half* A = reinterpret_cast<__half*>(I.A);
+    tc_gemm_tile(reinterpret_cast<const CUtensorMap*>(&maps[2 * t.inst]),
+                 reinterpret_cast<const CUtensorMap*>(&maps[2 * t.inst + 1]), K, K + w, rest, rest, w,
+                 A + (int64_t)(K + w) * I.ld + K + w, I.ld, t.a, t.b, err);
+}
+
 // ------------------------------------------------------------------- host --
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -243,8 +273,16 @@ bool tc_gemm_supported()
     if (cudaMalloc((void**)&g_tc_err, sizeof(unsigned)) != cudaSuccess) return false;
     cudaMemset(g_tc_err, 0, sizeof(unsigned));
     if (set_max_dynamic_smem((const void*)k_tc_gemm) != NL_OK) return false;
+    if (set_max_dynamic_smem((const void*)k_tc_gemm_g) != NL_OK) return false;
     g_tc_state = 1;
     return true;
+}
+
+static size_t tc_smem_bytes(int K)
+{
+    const int KT = K / kTcBK;
+    // at least 58 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
+    return std::max<size_t>(1024 + (size_t)KT * (kTcBM + kTcBN) * 128 + 64, 58 * 1024);
 }
 
 static bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t outer, uint64_t ld_elems,
@@ -280,12 +318,35 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         set_error("tcgen05 GEMM: cuTensorMapEncodeTiled failed");
         return NL_ECUDA;
     }
-    const int KT = K / kTcBK;
-    // at least 58 KB so that at most three CTAs (3 x 128 TMEM columns) share an SM
-    const size_t smem = std::max<size_t>(1024 + (size_t)KT * (kTcBM + kTcBN) * 128 + 64, 58 * 1024);
+    const size_t smem = tc_smem_bytes(K);
     dim3 grid((unsigned)cdiv(Nc, kTcBN), (unsigned)cdiv(M, kTcBM));
     prof_begin("k_tc_gemm", st);
     k_tc_gemm<<<grid, kTcThreads, smem, st>>>(tmA, tmB, M, Nc, K, C, ldc, g_tc_err, flag);
+    prof_end("k_tc_gemm", st);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+bool tc_encode_instance_maps(const __half* A, int N, int64_t ld, const __half* ut, int nb, TmapBytes* out2)
+{
+    static_assert(sizeof(TmapBytes) == sizeof(CUtensorMap), "tensor-map size");
+    if (!tc_gemm_supported()) return false;
+    return encode_2d(reinterpret_cast<CUtensorMap*>(&out2[0]), A, (uint64_t)N, (uint64_t)N, (uint64_t)ld, kTcBK,
+                     kTcBM) &&
+           encode_2d(reinterpret_cast<CUtensorMap*>(&out2[1]), ut, (uint64_t)nb, (uint64_t)round_up(N, 128),
+                     (uint64_t)nb, kTcBK, kTcBN);
+}
+
+nl_status tc_gemm16_grouped(const GInst* inst, const TmapBytes* maps, const GTask* tasks, int ntasks, int K, int w,
+                            cudaStream_t st)
+{
+    if (ntasks <= 0) return NL_OK;
+    if (!tc_gemm_supported() || w % kTcBK || w > 256) {
+        set_error("grouped tcgen05 GEMM: needs the tensor-core path and a panel width that is a multiple of 64");
+        return NL_EINVAL;
+    }
+    prof_begin("k_tc_gemm", st);
+    k_tc_gemm_g<<<(unsigned)ntasks, kTcThreads, tc_smem_bytes(w), st>>>(inst, maps, tasks, K, w, g_tc_err);
     prof_end("k_tc_gemm", st);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;

@@ -4,6 +4,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/newton3p.h"
 
 namespace nl {
@@ -40,6 +42,88 @@ nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast
                       int* launches);
 nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* B, int64_t ldb,
                         __half* C, int64_t ldc, int gemm, cudaStream_t st);
+
+// Grouped LU (many independent matrices, one launch per kernel class per
+// outer step).  The instance table lives in device memory.
+struct GInst {
+    void* A;        // binary16 or double matrix, row-major, leading dimension ld
+    int64_t ld;
+    int N;
+    int pad;
+    int* ipiv;      // N
+    int* flag;      // bit 0: the no-interchange fast path failed; bit 1: skip this matrix
+    void* stage;    // diagonal-block staging (lu_stage_bytes)
+    __half* ut;     // U12^T buffer for the tensor-core update: round_up(N, 128) x nb binary16
+};
+struct GTask {      // diag: {inst}; offdiag: {inst, block, row blocks}; gemm: {inst, m0, n0}
+    int inst, a, b, pad;
+};
+struct alignas(64) TmapBytes {  // an opaque CUtensorMap
+    unsigned char b[128];
+};
+// Per-step task lists of a grouped factorisation (device arrays, owned).
+struct GroupPlan {
+    int count = 0, nb = 128, gemm = 1, steps = 0;
+    bool fp64 = false;
+    std::vector<int> off, n;   // per step and class (3 * steps): offset into tasks and count
+    GTask* tasks = nullptr;    // device
+    TmapBytes* maps = nullptr; // device: 2 per instance (A and U12^T views), tensor-core update only
+    size_t bytes = 0;
+};
+size_t lu_stage_bytes();
+// Builds the plan for the instances (host copy of the device table, which must
+// already hold final pointers).  Allocates the device task and map arrays.
+nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, bool fp64, GroupPlan* plan);
+void lu_grouped_free(GroupPlan* plan);
+// One-time kernel attribute set-up (call before any stream capture).
+nl_status lu_grouped_setup();
+// Launches the whole factorisation (3 launches per outer step); stream-capturable.
+nl_status lu_grouped_factor(const GroupPlan& plan, const GInst* dev_inst, cudaStream_t st, int* launches);
+
+// Batched Newton (batch.cu): one instance of the H-equation per entry.
+enum : int {
+    BS_ACTIVE = 0,     // Newton continues
+    BS_CONVERGED = 1,  // ||F|| <= tau
+    BS_PARKED_LU = 2,  // the factorisation needs row interchanges: finished on the single-instance path
+    BS_PARKED_IR = 3,  // IR stalled: finished on the single-instance path with GMRES-IR
+    BS_NOTCONV = 4,    // Newton cap reached
+    BS_NUMERIC = 5     // non-finite residual
+};
+struct BInst {
+    int N, ld;         // ld: row stride of J32 and J (multiple of 64)
+    double c;
+    double* x[2];      // iterate buffers; BState::par selects the current one
+    double *F, *rr;
+    float* J32;
+    void* J;           // binary16 (three-precision) or double (FP64 mode) Jacobian, factored in place
+    int* ipiv;
+    int* flag;         // the grouped LU's flag word
+    float *b, *u, *r;  // single-precision IR vectors (ld entries)
+    double *b64, *u64; // double step (FP64 mode)
+    double* part;      // per-block partial sums of the norms
+    unsigned* cnt;     // [0] residual blocks done, [1] residual-GEMV blocks done
+    const double* x0;
+    double* xout;      // slice of the packed output
+};
+struct BState {
+    int status, it, par, lin_active;
+    int outer, lin_iters, failed, pad;
+    double fn0, fn, tau, nb, nr, prev, nr_new, pad2;
+};
+struct BTask {         // a block of rows of one instance
+    int inst, i0;
+};
+int residual_block_rows();  // rows per block of the grouped residual
+int gemv_block_rows();      // rows per block of the grouped residual GEMV
+// mode 0: F at x[0] (every instance); 1: x[par^1] = x[par] + fn u (single u), then F; 2: the same with u64.
+// Modes 1 and 2 skip instances that are not BS_ACTIVE.  The last block of an instance writes st.fn.
+nl_status launch_residual_g(const BInst* inst, BState* st, const BTask* tasks, int ntasks, int mode,
+                            const double* htab, cudaStream_t st_);
+// J32/J16 (fp64 = 0) or J64 (fp64 = 1) of the BS_ACTIVE instances; rows = total rows, row_off[count + 1].
+nl_status launch_jacobian_g(const BInst* inst, const BState* st, const int* row_off, int count, int rows,
+                            const double* htab, int fp64, cudaStream_t st_);
+// r = b - J32 u of instances with lin_active; the last block of an instance writes st.nr_new.
+nl_status launch_gemv_residual_g(const BInst* inst, BState* st, const BTask* tasks, int ntasks, cudaStream_t st_);
 
 // gemm_tc.cu: C = fl16(C - A * Bt^T), A M x K (lda), Bt Nc x K (ldbt), tcgen05 + TMA.
 bool tc_gemm_supported();
@@ -85,5 +169,11 @@ nl_status launch_arnoldi(int N, int64_t ldv, float* w, float* V, int j, double* 
 nl_status launch_gmres_update(int N, int64_t ldv, const float* V, double* ws, int m, int jcols, float* d,
                               cudaStream_t st);
 unsigned* tc_error_word();
+// Tensor maps of one grouped instance: the whole N x N binary16 matrix (ld)
+// and its U12^T buffer (round_up(N, 128) x nb), 64 x 128 boxes.
+bool tc_encode_instance_maps(const __half* A, int N, int64_t ld, const __half* ut, int nb, TmapBytes* out2);
+// Grouped trailing update of one outer step [K, K + w): tasks {inst, m0, n0}.
+nl_status tc_gemm16_grouped(const GInst* inst, const TmapBytes* maps, const GTask* tasks, int ntasks, int K, int w,
+                            cudaStream_t st);
 
 }  // namespace nl

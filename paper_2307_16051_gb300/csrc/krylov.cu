@@ -52,17 +52,13 @@ __device__ __forceinline__ DF df_add(DF a, DF b)
     return r;
 }
 
-__global__ void __launch_bounds__(kGemvWarps * 32)
-    k_gemv_residual(int N, const float* __restrict__ A, int64_t ld, const float* __restrict__ b,
-                    const float* __restrict__ u, float* __restrict__ r, double* __restrict__ partial,
-                    unsigned* __restrict__ counter, double* __restrict__ rnorm)
+// Row i of r = b - A u by one warp; returns r_i^2 in lane 0 (0 elsewhere).
+__device__ __forceinline__ double gemv_row(int N, const float* __restrict__ A, int64_t ld,
+                                           const float* __restrict__ b, const float* __restrict__ u,
+                                           float* __restrict__ r, int i, int lane)
 {
-    __shared__ double red[kGemvWarps];
-    __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int i = blockIdx.x * kGemvWarps + warp;
     double sq = 0.0;
-    if (i < N) {
+    {
         const float* Ai = A + (int64_t)i * ld;
         const int n4 = N >> 2;
         const float4* A4 = reinterpret_cast<const float4*>(Ai);
@@ -98,6 +94,19 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
             sq = (double)ri * (double)ri;
         }
     }
+    return sq;
+}
+
+__global__ void __launch_bounds__(kGemvWarps * 32)
+    k_gemv_residual(int N, const float* __restrict__ A, int64_t ld, const float* __restrict__ b,
+                    const float* __restrict__ u, float* __restrict__ r, double* __restrict__ partial,
+                    unsigned* __restrict__ counter, double* __restrict__ rnorm)
+{
+    __shared__ double red[kGemvWarps];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kGemvWarps + warp;
+    const double sq = (i < N) ? gemv_row(N, A, ld, b, u, r, i, lane) : 0.0;
     if (lane == 0) red[warp] = sq;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -119,6 +128,53 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
 }
 
 int gemv_partials(int N) { return (int)cdiv(N, kGemvWarps); }
+
+// Grouped residual r = b - J32 u: one block per task {instance, first row},
+// instances with an IR step in progress only; per-instance block partials
+// summed in block order by the instance's last block (into st.nr_new).
+__global__ void __launch_bounds__(kGemvWarps * 32)
+    k_gemv_residual_g(const BInst* __restrict__ inst, BState* __restrict__ st, const BTask* __restrict__ tasks)
+{
+    __shared__ double red[kGemvWarps];
+    __shared__ bool last;
+    const BTask tk = tasks[blockIdx.x];
+    const BInst& I = inst[tk.inst];
+    BState& S = st[tk.inst];
+    if (S.status != BS_ACTIVE || !S.lin_active) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int N = I.N, i = tk.i0 + warp;
+    const double sq = (i < N) ? gemv_row(N, I.J32, I.ld, I.b, I.u, I.r, i, lane) : 0.0;
+    if (lane == 0) red[warp] = sq;
+    __syncthreads();
+    const int blk = tk.i0 / kGemvWarps, nblk = (N + kGemvWarps - 1) / kGemvWarps;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kGemvWarps; ++q) t += red[q];
+        I.part[blk] = t;
+        __threadfence();
+        last = (atomicAdd(&I.cnt[1], 1u) == (unsigned)(nblk - 1));
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t = 0.0;
+        for (int q = 0; q < nblk; ++q) t += __ldcg(&I.part[q]);
+        S.nr_new = sqrt(t);
+        I.cnt[1] = 0u;
+    }
+}
+
+int gemv_block_rows() { return kGemvWarps; }
+
+nl_status launch_gemv_residual_g(const BInst* inst, BState* st, const BTask* tasks, int ntasks, cudaStream_t st_)
+{
+    if (ntasks <= 0) return NL_OK;
+    prof_begin("k_gemv_residual", st_);
+    k_gemv_residual_g<<<(unsigned)ntasks, kGemvWarps * 32, 0, st_>>>(inst, st, tasks);
+    prof_end("k_gemv_residual", st_);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
 
 nl_status launch_gemv_residual(int N, const float* A, int64_t ld, const float* b, const float* u, float* r,
                                double* partial, unsigned* counter, double* rnorm, cudaStream_t st)

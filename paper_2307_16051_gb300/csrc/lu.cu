@@ -560,7 +560,7 @@ __device__ __forceinline__ void group_col_solve(T* W, int ldw, int c0, int col, 
 }
 
 template <typename T, typename S, bool RND>
-__global__ void __launch_bounds__(kDiagThreads, 1) k_diag_lu(S* __restrict__ A, int64_t lda, int K, int w,
+__device__ __forceinline__ void diag_lu_body(S* __restrict__ A, int64_t lda, int K, int w,
                                                              int* __restrict__ ipiv, int* __restrict__ flag,
                                                              void* __restrict__ stage)
 {
@@ -660,6 +660,14 @@ __global__ void __launch_bounds__(kDiagThreads, 1) k_diag_lu(S* __restrict__ A, 
     if (tid < w) ipiv[K + tid] = K + tid;
 }
 
+template <typename T, typename S, bool RND>
+__global__ void __launch_bounds__(kDiagThreads, 1) k_diag_lu(S* __restrict__ A, int64_t lda, int K, int w,
+                                                             int* __restrict__ ipiv, int* __restrict__ flag,
+                                                             void* __restrict__ stage)
+{
+    diag_lu_body<T, S, RND>(A, lda, K, w, ipiv, flag, stage);
+}
+
 // Off-diagonal blocks of a panel of width w, one launch, eight lanes per row
 // (L21 = A21 U11^{-1}) or per column (U12 = L11^{-1} A12), four per warp.
 // Left-looking in 32-wide chunks: lane g of a group owns entries 4g..4g+3 of
@@ -672,9 +680,9 @@ __global__ void __launch_bounds__(kDiagThreads, 1) k_diag_lu(S* __restrict__ A, 
 constexpr int kOffThreads = 128;  // 16 groups of 8 lanes
 
 template <typename T, typename S, bool RND>
-__global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int64_t lda, int K, int w, int N,
+__device__ __forceinline__ void offdiag_body(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                          int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                                         int* __restrict__ flag, const void* __restrict__ stage)
+                                                         int* __restrict__ flag, const void* __restrict__ stage, int bid)
 {
     if (flag && *(volatile int*)flag) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -685,7 +693,7 @@ __global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int6
     H* X = D + wp * wp;                     // wp x NG: earlier multipliers / U entries of each group
     const int tid = threadIdx.x, grp = tid / kOffG, g = tid % kOffG;
     const unsigned gmask = 0xffu << ((tid & 31) & ~(kOffG - 1));
-    const bool row_role = (int)blockIdx.x < nrow_blocks;
+    const bool row_role = (int)bid < nrow_blocks;
     {
         // U11 or L11^T, staged by k_diag_lu in exactly this layout
         const uint4* src = reinterpret_cast<const uint4*>(reinterpret_cast<const H*>(stage) + (row_role ? 0 : wp * wp));
@@ -698,7 +706,7 @@ __global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int6
     bool bad = false;
     const int nc = wp / 32;
     if (row_role) {
-        const int i = K + w + blockIdx.x * NG + grp;
+        const int i = K + w + bid * NG + grp;
         const bool live = i < N;
         S* Ai = A + (int64_t)min(i, N - 1) * lda + K;
         for (int c = 0; c < nc; ++c) {
@@ -749,7 +757,7 @@ __global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int6
         }
         if (__syncthreads_or(bad) && tid == 0 && flag) atomicOr(flag, 1);
     } else {
-        const int col = K + w + (blockIdx.x - nrow_blocks) * NG + grp;
+        const int col = K + w + (bid - nrow_blocks) * NG + grp;
         const bool live = col < N;
         const int cc = min(col, N - 1);
         for (int c = 0; c < nc; ++c) {
@@ -790,6 +798,14 @@ __global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int6
     }
 }
 
+template <typename T, typename S, bool RND>
+__global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                         int nrow_blocks, __half* __restrict__ Ut, int ldut,
+                                                         int* __restrict__ flag, const void* __restrict__ stage)
+{
+    offdiag_body<T, S, RND>(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x);
+}
+
 // ------------------------------------------ fast path, binary16 factors --
 // The stage buffer holds, for the off-diagonal solves of one panel: U11 and
 // L11^T (wp x wp binary32 each, the exact binary16 values, identity / zero
@@ -813,7 +829,7 @@ constexpr int kD16Threads = 512;
 constexpr int kFwLd = 136;  // stride (halves) of the result buffers; rows stay 16-byte aligned
 constexpr size_t kDiag16Smem = 2 * 128 * kFwLd * sizeof(__half);
 
-__global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict__ A, int64_t lda, int K, int w,
+__device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t lda, int K, int w,
                                                              int* __restrict__ ipiv, int* __restrict__ flag,
                                                              float* __restrict__ stage)
 {
@@ -939,6 +955,13 @@ __global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict
     if (tid < w) ipiv[K + tid] = K + tid;
 }
 
+__global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict__ A, int64_t lda, int K, int w,
+                                                             int* __restrict__ ipiv, int* __restrict__ flag,
+                                                             float* __restrict__ stage)
+{
+    diag_lu16_body(A, lda, K, w, ipiv, flag, stage);
+}
+
 // k_offdiag16: L21 = A21 U11^{-1} (row role) and U12 = L11^{-1} A12 (column
 // role) for a panel of width w.  256 threads = 32 groups of eight lanes; a
 // group takes two rows (or two columns), and lane g holds entries 4g..4g+3 of
@@ -954,9 +977,9 @@ constexpr int kO16Rows = 64;  // rows or columns per CTA (32 groups x 2)
 
 size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + wp) * sizeof(float); }
 
-__global__ void __launch_bounds__(kO16Threads) k_offdiag16(__half* __restrict__ A, int64_t lda, int K, int w, int N,
+__device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t lda, int K, int w, int N,
                                                            int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                                           int* __restrict__ flag, const float* __restrict__ stage)
+                                                           int* __restrict__ flag, const float* __restrict__ stage, int bid)
 {
     if (*(volatile int*)flag) return;
     extern __shared__ __align__(16) float osm[];
@@ -966,7 +989,7 @@ __global__ void __launch_bounds__(kO16Threads) k_offdiag16(__half* __restrict__ 
     float* pv = X + wp * kO16Rows;   // |a_tt|, unrounded
     const int tid = threadIdx.x, grp = tid >> 3, g = tid & 7;
     const unsigned gmask = 0xffu << ((tid & 31) & ~7);
-    const bool row_role = (int)blockIdx.x < nrow_blocks;
+    const bool row_role = (int)bid < nrow_blocks;
     {
         const float4* s4 = reinterpret_cast<const float4*>(stage + (row_role ? 0 : wp * wp));
         float4* d4 = reinterpret_cast<float4*>(D);
@@ -976,7 +999,7 @@ __global__ void __launch_bounds__(kO16Threads) k_offdiag16(__half* __restrict__ 
         if (tid < wp) pv[tid] = fabsf(stage[kStagePivOff + tid]);
     }
     __syncthreads();
-    const int base = K + w + (row_role ? (int)blockIdx.x : (int)blockIdx.x - nrow_blocks) * kO16Rows + 2 * grp;
+    const int base = K + w + (row_role ? (int)bid : (int)bid - nrow_blocks) * kO16Rows + 2 * grp;
     const bool lv0 = base < N, lv1 = base + 1 < N;
     float2* Xg = reinterpret_cast<float2*>(X) + grp;  // X[t][2 grp], X[t][2 grp + 1] at Xg[t * 32]
     if (row_role) {
@@ -1134,19 +1157,25 @@ __global__ void __launch_bounds__(kO16Threads) k_offdiag16(__half* __restrict__ 
     }
 }
 
+__global__ void __launch_bounds__(kO16Threads) k_offdiag16(__half* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                           int nrow_blocks, __half* __restrict__ Ut, int ldut,
+                                                           int* __restrict__ flag, const float* __restrict__ stage)
+{
+    offdiag16_body(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x);
+}
+
 // C <- C - A B with per-element sequential fused multiply-adds over k in
 // order, accumulated in T and stored once (rounded to binary16 for __half).
 template <typename S, typename T>
-__global__ void __launch_bounds__(256) k_gemm_simt(int M, int Nc, int K, const S* __restrict__ A, int64_t lda,
+__device__ __forceinline__ void gemm_simt_body(int M, int Nc, int K, const S* __restrict__ A, int64_t lda,
                                                    const S* __restrict__ B, int64_t ldb, S* __restrict__ C,
-                                                   int64_t ldc, const int* __restrict__ flag)
+                                                   int64_t ldc, const int* __restrict__ flag, int m0, int n0)
 {
     if (flag && *(volatile const int*)flag) return;
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ T As[BK][BM + 1];
     __shared__ T Bs[BK][BN];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     T acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1188,6 +1217,14 @@ __global__ void __launch_bounds__(256) k_gemm_simt(int M, int Nc, int K, const S
             int i = m0 + ty + 16 * a, j = n0 + tx + 16 * b;
             if (i < M && j < Nc) st_elem(C + (int64_t)i * ldc + j, acc[a][b]);
         }
+}
+
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) k_gemm_simt(int M, int Nc, int K, const S* __restrict__ A, int64_t lda,
+                                                   const S* __restrict__ B, int64_t ldb, S* __restrict__ C,
+                                                   int64_t ldc, const int* __restrict__ flag)
+{
+    gemm_simt_body<S, T>(M, Nc, K, A, lda, B, ldb, C, ldc, flag, (int)blockIdx.y * 64, (int)blockIdx.x * 64);
 }
 
 // ------------------------------------------------------------------ host --
@@ -1449,6 +1486,212 @@ nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast
         return NL_EINVAL;
     }
     return lu_factor_impl<double, double, 8, false>(N, A, ld, ipiv, nb, 1, fast, w, st, launches);
+}
+
+}  // namespace nl
+
+// ================================================================ grouped ==
+// Many independent matrices of different N factored in lock step: outer step
+// k launches the diagonal-block kernel for every matrix with N > k nb, the
+// off-diagonal solves of all of them, and their trailing updates, each as one
+// launch over a precomputed task list (largest matrices first).  The kernels
+// are the single-matrix fast-path bodies; a matrix whose flag word is non-zero
+// (fast path failed, or marked to be skipped) does no work.  No interchanges:
+// a matrix that needs them is left with bit 0 of its flag set.
+namespace nl {
+
+size_t lu_stage_bytes() { return (size_t)2 * 128 * 128 * 8 + 128 * 8; }
+
+template <typename T, typename S, bool RND>
+__global__ void __launch_bounds__(kDiagThreads, 1) k_diag_lu_g(const GInst* __restrict__ inst,
+                                                               const GTask* __restrict__ tasks, int K, int nb)
+{
+    const GInst I = inst[tasks[blockIdx.x].inst];
+    diag_lu_body<T, S, RND>(reinterpret_cast<S*>(I.A), I.ld, K, min(nb, I.N - K), I.ipiv, I.flag, I.stage);
+}
+
+__global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16_g(const GInst* __restrict__ inst,
+                                                                const GTask* __restrict__ tasks, int K, int nb)
+{
+    const GInst I = inst[tasks[blockIdx.x].inst];
+    diag_lu16_body(reinterpret_cast<__half*>(I.A), I.ld, K, min(nb, I.N - K), I.ipiv, I.flag,
+                   reinterpret_cast<float*>(I.stage));
+}
+
+template <typename T, typename S, bool RND>
+__global__ void __launch_bounds__(kOffThreads) k_offdiag_g(const GInst* __restrict__ inst,
+                                                           const GTask* __restrict__ tasks, int K, int nb)
+{
+    const GTask t = tasks[blockIdx.x];
+    const GInst I = inst[t.inst];
+    offdiag_body<T, S, RND>(reinterpret_cast<S*>(I.A), I.ld, K, nb, I.N, t.b, nullptr, nb, I.flag, I.stage, t.a);
+}
+
+__global__ void __launch_bounds__(kO16Threads) k_offdiag16_g(const GInst* __restrict__ inst,
+                                                             const GTask* __restrict__ tasks, int K, int nb, int tc)
+{
+    const GTask t = tasks[blockIdx.x];
+    const GInst I = inst[t.inst];
+    offdiag16_body(reinterpret_cast<__half*>(I.A), I.ld, K, nb, I.N, t.b, tc ? I.ut : nullptr, nb, I.flag,
+                   reinterpret_cast<const float*>(I.stage), t.a);
+}
+
+template <typename S, typename T>
+__global__ void __launch_bounds__(256) k_gemm_simt_g(const GInst* __restrict__ inst, const GTask* __restrict__ tasks,
+                                                     int K, int w)
+{
+    const GTask t = tasks[blockIdx.x];
+    const GInst I = inst[t.inst];
+    const int rest = I.N - K - w;
+    S* A = reinterpret_cast<S*>(I.A);
+    const int64_t ld = I.ld;
+    gemm_simt_body<S, T>(rest, rest, w, A + (int64_t)(K + w) * ld + K, ld, A + (int64_t)K * ld + K + w, ld,
+                         A + (int64_t)(K + w) * ld + K + w, ld, I.flag, t.a, t.b);
+}
+
+nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, bool fp64, GroupPlan* plan)
+{
+    if (count < 1 || nb < 16 || nb > 128 || nb % 16) {
+        set_error("grouped LU: need count >= 1 and nb a multiple of 16 in [16, 128]");
+        return NL_EINVAL;
+    }
+    if (fp64) gemm = 1;
+    if (gemm == 2 && (nb % 64 || !tc_gemm_supported())) gemm = 1;
+    int nmax = 0;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, host_inst[i].N);
+    // largest matrices first in every task list
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return host_inst[a].N > host_inst[b].N; });
+    const int steps = (int)cdiv(nmax, nb);
+    const int rows_per_cta = fp64 ? kOffThreads / kOffG : kO16Rows;
+    const int tile = (gemm == 2) ? 128 : 64;
+    std::vector<GTask> tasks;
+    plan->off.assign(3 * steps, 0);
+    plan->n.assign(3 * steps, 0);
+    for (int k = 0; k < steps; ++k) {
+        const int K = k * nb;
+        plan->off[3 * k] = (int)tasks.size();
+        for (int i : order)
+            if (host_inst[i].N > K) tasks.push_back({i, 0, 0, 0});
+        plan->n[3 * k] = (int)tasks.size() - plan->off[3 * k];
+        plan->off[3 * k + 1] = (int)tasks.size();
+        for (int i : order) {
+            const int rest = host_inst[i].N - K - nb;
+            if (rest <= 0) continue;
+            const int nrb = (int)cdiv(rest, rows_per_cta);
+            for (int b = 0; b < 2 * nrb; ++b) tasks.push_back({i, b, nrb, 0});
+        }
+        plan->n[3 * k + 1] = (int)tasks.size() - plan->off[3 * k + 1];
+        plan->off[3 * k + 2] = (int)tasks.size();
+        for (int i : order) {
+            const int rest = host_inst[i].N - K - nb;
+            if (rest <= 0) continue;
+            const int nt = (int)cdiv(rest, tile);
+            for (int a = 0; a < nt; ++a)
+                for (int b = 0; b < nt; ++b) tasks.push_back({i, a * tile, b * tile, 0});
+        }
+        plan->n[3 * k + 2] = (int)tasks.size() - plan->off[3 * k + 2];
+    }
+    lu_grouped_free(plan);
+    plan->count = count;
+    plan->nb = nb;
+    plan->gemm = gemm;
+    plan->steps = steps;
+    plan->fp64 = fp64;
+    std::vector<TmapBytes> maps;
+    if (gemm == 2) {
+        maps.resize(2 * (size_t)count);
+        for (int i = 0; i < count; ++i)
+            if (host_inst[i].N > nb && !tc_encode_instance_maps(reinterpret_cast<const __half*>(host_inst[i].A), host_inst[i].N,
+                                         host_inst[i].ld, host_inst[i].ut, nb, &maps[2 * (size_t)i])) {
+                set_error("grouped LU: tensor-map encoding failed for matrix %d", i);
+                return NL_ECUDA;
+            }
+    }
+    const size_t tb = tasks.size() * sizeof(GTask), mb = maps.size() * sizeof(TmapBytes);
+    plan->bytes = round_up(tb, 256) + mb + 256;
+    void* p = nullptr;
+    NL_CUDA_OK(cudaMalloc(&p, plan->bytes));
+    plan->tasks = reinterpret_cast<GTask*>(p);
+    plan->maps = mb ? reinterpret_cast<TmapBytes*>((char*)p + round_up(tb, 256)) : nullptr;
+    if (tb) NL_CUDA_OK(cudaMemcpy(plan->tasks, tasks.data(), tb, cudaMemcpyHostToDevice));
+    if (mb) NL_CUDA_OK(cudaMemcpy(plan->maps, maps.data(), mb, cudaMemcpyHostToDevice));
+    return NL_OK;
+}
+
+void lu_grouped_free(GroupPlan* plan)
+{
+    if (plan->tasks) cudaFree(plan->tasks);
+    plan->tasks = nullptr;
+    plan->maps = nullptr;
+}
+
+nl_status lu_grouped_setup()
+{
+    static bool smem_set = false;
+    if (!smem_set) {
+        if (set_max_dynamic_smem((const void*)k_diag_lu16_g) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_offdiag16_g) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_diag_lu_g<double, double, false>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_offdiag_g<double, double, false>) != NL_OK)
+            return NL_ECUDA;
+        smem_set = true;
+    }
+    return NL_OK;
+}
+
+nl_status lu_grouped_factor(const GroupPlan& plan, const GInst* dev_inst, cudaStream_t st, int* launches)
+{
+    NL_TRY(lu_grouped_setup());
+    const int nb = plan.nb, wp = (int)round_up(nb, 32);
+    int nl = 0;
+    for (int k = 0; k < plan.steps; ++k) {
+        const int K = k * nb;
+        const GTask* td = plan.tasks + plan.off[3 * k];
+        const GTask* to = plan.tasks + plan.off[3 * k + 1];
+        const GTask* tg = plan.tasks + plan.off[3 * k + 2];
+        const int nd = plan.n[3 * k], no = plan.n[3 * k + 1], ng = plan.n[3 * k + 2];
+        if (plan.fp64) {
+            if (nd) {
+                prof_begin("k_diag_lu", st);
+                k_diag_lu_g<double, double, false><<<nd, kDiagThreads, (size_t)wp * (wp + 1) * 8, st>>>(dev_inst, td,
+                                                                                                      K, nb);
+                prof_end("k_diag_lu", st);
+            }
+            if (no) {
+                prof_begin("k_offdiag", st);
+                k_offdiag_g<double, double, false><<<no, kOffThreads,
+                                                     (size_t)wp * wp * 8 + (size_t)wp * (kOffThreads / kOffG) * 8,
+                                                     st>>>(dev_inst, to, K, nb);
+                prof_end("k_offdiag", st);
+            }
+            if (ng) k_gemm_simt_g<double, double><<<ng, 256, 0, st>>>(dev_inst, tg, K, nb);
+        } else {
+            if (nd) {
+                prof_begin("k_diag_lu16", st);
+                k_diag_lu16_g<<<nd, kD16Threads, kDiag16Smem, st>>>(dev_inst, td, K, nb);
+                prof_end("k_diag_lu16", st);
+            }
+            if (no) {
+                prof_begin("k_offdiag16", st);
+                k_offdiag16_g<<<no, kO16Threads, offdiag16_smem(wp), st>>>(dev_inst, to, K, nb, plan.gemm == 2);
+                prof_end("k_offdiag16", st);
+            }
+            if (ng) {
+                if (plan.gemm == 2) {
+                    nl_status s = tc_gemm16_grouped(dev_inst, plan.maps, tg, ng, K, nb, st);
+                    if (s != NL_OK) return s;
+                } else {
+                    k_gemm_simt_g<__half, float><<<ng, 256, 0, st>>>(dev_inst, tg, K, nb);
+                }
+            }
+        }
+        nl += (nd > 0) + (no > 0) + (ng > 0);
+        NL_CUDA_OK(cudaGetLastError());
+    }
+    if (launches) *launches += nl;
+    return NL_OK;
 }
 
 }  // namespace nl

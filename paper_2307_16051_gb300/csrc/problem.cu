@@ -15,19 +15,19 @@ namespace nl {
 // shared memory (x + scale*u for the chunk, and the h window it needs).
 constexpr int kFRows = 32, kFSlices = 8, kFChunk = 256;
 
+// Rows [i0, i0 + kFRows) of F at x + scale u (u may be NULL); returns the
+// block's sum of F_i^2 (valid in every thread).
 template <typename TU>
-__global__ void __launch_bounds__(kFRows* kFSlices)
-    k_residual(int N, double c, const double* __restrict__ x, const TU* __restrict__ u, double scale,
-               const double* __restrict__ htab, double* __restrict__ xout, double* __restrict__ F,
-               double* __restrict__ rr, double* __restrict__ partial, unsigned* __restrict__ counter,
-               double* __restrict__ fnorm)
+__device__ __forceinline__ double residual_rows(int N, double c, const double* __restrict__ x,
+                                                const TU* __restrict__ u, double scale,
+                                                const double* __restrict__ htab, double* __restrict__ xout,
+                                                double* __restrict__ F, double* __restrict__ rr, int i0)
 {
     __shared__ double xs[kFChunk];
     __shared__ double hw[kFChunk + kFRows];
     __shared__ double red[kFSlices][kFRows + 1];
-    __shared__ bool last;
+    __shared__ double bsum;
     const int r = threadIdx.x % kFRows, q = threadIdx.x / kFRows;
-    const int i0 = blockIdx.x * kFRows;
     const int i = i0 + r;
     double acc = 0.0;
     for (int j0 = 0; j0 < N; j0 += kFChunk) {
@@ -71,9 +71,22 @@ __global__ void __launch_bounds__(kFRows* kFSlices)
     if (q == 0) {
         double v = f2;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (r == 0) partial[blockIdx.x] = v;
+        if (r == 0) bsum = v;
     }
     __syncthreads();
+    return bsum;
+}
+
+template <typename TU>
+__global__ void __launch_bounds__(kFRows* kFSlices)
+    k_residual(int N, double c, const double* __restrict__ x, const TU* __restrict__ u, double scale,
+               const double* __restrict__ htab, double* __restrict__ xout, double* __restrict__ F,
+               double* __restrict__ rr, double* __restrict__ partial, unsigned* __restrict__ counter,
+               double* __restrict__ fnorm)
+{
+    __shared__ bool last;
+    const double v = residual_rows<TU>(N, c, x, u, scale, htab, xout, F, rr, blockIdx.x * kFRows);
+    if (threadIdx.x == 0) partial[blockIdx.x] = v;
     if (threadIdx.x == 0) {
         __threadfence();
         unsigned done = atomicAdd(counter, 1u);
@@ -118,6 +131,54 @@ nl_status launch_residual(int N, double c, const double* x, const void* u, int u
 }
 
 int residual_partials(int N) { return (int)cdiv(N, kFRows); }
+
+// Grouped residual: one block per task {instance, first row}.  Per-instance
+// block partials are summed in block order by the instance's last block.
+__global__ void __launch_bounds__(kFRows* kFSlices)
+    k_residual_g(const BInst* __restrict__ inst, BState* __restrict__ st, const BTask* __restrict__ tasks, int mode,
+                 const double* __restrict__ htab)
+{
+    __shared__ bool last;
+    const BTask tk = tasks[blockIdx.x];
+    const BInst& I = inst[tk.inst];
+    BState& S = st[tk.inst];
+    if (mode != 0 && S.status != BS_ACTIVE) return;
+    const int N = I.N;
+    const int par = (mode == 0) ? 0 : S.par;
+    const double* x = I.x[par];
+    double v;
+    if (mode == 0)
+        v = residual_rows<float>(N, I.c, x, nullptr, 0.0, htab, nullptr, I.F, I.rr, tk.i0);
+    else if (mode == 1)
+        v = residual_rows<float>(N, I.c, x, I.u, S.fn, htab, I.x[par ^ 1], I.F, I.rr, tk.i0);
+    else
+        v = residual_rows<double>(N, I.c, x, I.u64, S.fn, htab, I.x[par ^ 1], I.F, I.rr, tk.i0);
+    const int blk = tk.i0 / kFRows, nblk = (N + kFRows - 1) / kFRows;
+    if (threadIdx.x == 0) {
+        I.part[blk] = v;
+        __threadfence();
+        last = (atomicAdd(&I.cnt[0], 1u) == (unsigned)(nblk - 1));
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += __ldcg(&I.part[b]);
+        S.fn = sqrt(s);
+        I.cnt[0] = 0u;
+    }
+}
+
+int residual_block_rows() { return kFRows; }
+
+nl_status launch_residual_g(const BInst* inst, BState* st, const BTask* tasks, int ntasks, int mode,
+                            const double* htab, cudaStream_t st_)
+{
+    if (ntasks <= 0) return NL_OK;
+    k_residual_g<<<(unsigned)ntasks, kFRows * kFSlices, 0, st_>>>(inst, st, tasks, mode, htab);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
 
 // ------------------------------------------------------- K2: the Jacobian --
 // J_ij = delta_ij - w_i h[i+j],  w_i = c/(2N) r_i^2 (i + 1/2).  Each thread
@@ -191,6 +252,61 @@ nl_status launch_jacobian64(int N, double c, const double* rr, const double* hta
 {
     dim3 grid((unsigned)cdiv(ld, 256), (unsigned)N);
     k_jacobian64<<<grid, 256, 0, st>>>(N, c, rr, htab, J, ld);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+// Grouped Jacobian: one block per row of one instance (row_off gives the
+// instance's first global row), the same arithmetic as k_jacobian /
+// k_jacobian64.  Instances that are not BS_ACTIVE are skipped.
+__global__ void __launch_bounds__(256) k_jacobian_g(const BInst* __restrict__ inst, const BState* __restrict__ st,
+                                                    const int* __restrict__ row_off, int count,
+                                                    const double* __restrict__ htab, int fp64)
+{
+    const int g = blockIdx.x;
+    int lo = 0, hi = count - 1;  // last instance with row_off[k] <= g
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const BInst& I = inst[lo];
+    if (st[lo].status != BS_ACTIVE) return;
+    const int i = g - row_off[lo], N = I.N;
+    const double ri = I.rr[i];
+    if (fp64) {
+        const double w = I.c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5);
+        double* Ji = reinterpret_cast<double*>(I.J) + (int64_t)i * I.ld;
+        for (int j = threadIdx.x; j < I.ld; j += blockDim.x)
+            Ji[j] = (j < N) ? fma(-w, htab[i + j], (i == j) ? 1.0 : 0.0) : 0.0;
+        return;
+    }
+    const float w = (float)(I.c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5));
+    for (int j0 = threadIdx.x * kJCols; j0 < I.ld; j0 += blockDim.x * kJCols) {
+        float v[kJCols];
+#pragma unroll
+        for (int t = 0; t < kJCols; ++t) {
+            const int j = j0 + t;
+            float e = 0.0f;
+            if (j < N) e = fmaf(-w, (float)htab[i + j], (i == j) ? 1.0f : 0.0f);
+            v[t] = e;
+        }
+        float4* p = reinterpret_cast<float4*>(I.J32 + (int64_t)i * I.ld + j0);
+        p[0] = make_float4(v[0], v[1], v[2], v[3]);
+        p[1] = make_float4(v[4], v[5], v[6], v[7]);
+        __align__(16) __half h[kJCols];
+#pragma unroll
+        for (int t = 0; t < kJCols; ++t) h[t] = __float2half_rn(v[t]);
+        *reinterpret_cast<uint4*>(reinterpret_cast<__half*>(I.J) + (int64_t)i * I.ld + j0) =
+            *reinterpret_cast<uint4*>(h);
+    }
+}
+
+nl_status launch_jacobian_g(const BInst* inst, const BState* st, const int* row_off, int count, int rows,
+                            const double* htab, int fp64, cudaStream_t st_)
+{
+    if (rows <= 0) return NL_OK;
+    k_jacobian_g<<<(unsigned)rows, 256, 0, st_>>>(inst, st, row_off, count, htab, fp64);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }

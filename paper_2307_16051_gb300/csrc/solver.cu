@@ -59,6 +59,8 @@ static KernelTiming g_kt;
 void prof_begin(const char* kernel_class, cudaStream_t st)
 {
     if (g_kt.cls.empty() || g_kt.cls != kernel_class) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lock(g_kt.mu);
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return;
@@ -70,6 +72,8 @@ void prof_begin(const char* kernel_class, cudaStream_t st)
 void prof_end(const char* kernel_class, cudaStream_t st)
 {
     if (g_kt.cls.empty() || g_kt.cls != kernel_class) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
     std::lock_guard<std::mutex> lock(g_kt.mu);
     if (g_kt.open >= 0) cudaEventRecord(g_kt.ev[g_kt.open].second, st);
     g_kt.open = -1;
@@ -97,20 +101,6 @@ __global__ void k_fill64(int N, double v, double* x)
     if (i < N) x[i] = v;
 }
 
-// Carves aligned sub-buffers out of one device allocation.
-struct Carver {
-    char* base;
-    size_t off = 0;
-    explicit Carver(void* b) : base((char*)b) {}
-    template <typename T>
-    T* take(size_t n)
-    {
-        off = (off + 255) & ~(size_t)255;
-        T* p = (T*)(base + off);
-        off += n * sizeof(T);
-        return p;
-    }
-};
 
 struct LinBufs {
     float *r, *d, *t, *w, *ubest, *V;
@@ -145,12 +135,6 @@ struct Host {
         out[2] = pin[2];
     }
 };
-
-#define NL_TRY(expr)                    \
-    do {                                \
-        nl_status _s = (expr);          \
-        if (_s != NL_OK) return _s;     \
-    } while (0)
 
 // Left-preconditioned restarted GMRES(m) from d0 = 0 for M^{-1} A d = M^{-1} r.
 static nl_status gmres16(int N, const float* J32, int64_t ld32, const __half* LU, int64_t ld16, const TrsvWork& tw,
@@ -287,7 +271,7 @@ struct nl_solver {
     cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
-static bool valid_mode(int m) { return m == NL_FP64LU || m == NL_IR16 || m == NL_GMRESIR16; }
+static bool valid_mode(int m) { return m == NL_FP64LU || m == NL_IR16 || m == NL_GMRESIR16 || m == NL_IR16_GMRES; }
 
 extern "C" {
 
@@ -566,6 +550,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
     S.fnorm0 = f0;
     S.hist[0] = 1.0;
     int it = 0;
+    bool gm_sticky = false;  // NL_IR16_GMRES: GMRES-IR from the first stalled step on
     nl_status status = NL_ENOTCONV;
     while (!(fn <= tau)) {
         if (!std::isfinite(fn)) {
@@ -638,8 +623,20 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             ++launches;
             LinResult lr;
             NL_TRY(linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
-                              s->cfg.ir_maxit, mode == NL_GMRESIR16 ? 2 : 0, s->cfg.gmres_restart, s->cfg.gmres_tol,
-                              s->cfg.gmres_maxcycles, s->lb, H, &lr));
+                              s->cfg.ir_maxit, (mode == NL_GMRESIR16 || gm_sticky) ? 2 : 0, s->cfg.gmres_restart,
+                              s->cfg.gmres_tol, s->cfg.gmres_maxcycles, s->lb, H, &lr));
+            if (mode == NL_IR16_GMRES && !gm_sticky && !lr.converged) {
+                // IR stalled: redo this step with GMRES-IR, and keep it for the rest of the solve
+                gm_sticky = true;
+                LinResult lg;
+                NL_TRY(linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
+                                  s->cfg.ir_maxit, 2, s->cfg.gmres_restart, s->cfg.gmres_tol,
+                                  s->cfg.gmres_maxcycles, s->lb, H, &lg));
+                lg.iters += lr.iters;
+                lg.outer += lr.outer;
+                lg.failed = 1;
+                lr = lg;
+            }
             S.lin_iters[it] = lr.iters;
             S.lin_outer[it] = lr.outer;
             S.lin_failed[it] = lr.failed;

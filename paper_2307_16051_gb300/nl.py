@@ -18,8 +18,8 @@ from . import build as _build
 NL_OK, NL_EINVAL, NL_ENOMEM, NL_ENOTCONV, NL_ESINGULAR, NL_ENUMERIC, NL_ETIMEOUT, NL_ECUDA = range(8)
 STATUS_NAMES = ["NL_OK", "NL_EINVAL", "NL_ENOMEM", "NL_ENOTCONV", "NL_ESINGULAR", "NL_ENUMERIC", "NL_ETIMEOUT",
                 "NL_ECUDA"]
-NL_FP64LU, NL_IR16, NL_GMRESIR16 = 0, 1, 2
-MODES = {"FP64LU": NL_FP64LU, "IR16": NL_IR16, "GMRESIR16": NL_GMRESIR16}
+NL_FP64LU, NL_IR16, NL_GMRESIR16, NL_IR16_GMRES = 0, 1, 2, 3
+MODES = {"FP64LU": NL_FP64LU, "IR16": NL_IR16, "GMRESIR16": NL_GMRESIR16, "IR16_GMRES": NL_IR16_GMRES}
 MAX_HIST = 128
 
 
@@ -45,6 +45,16 @@ class Stats(ctypes.Structure):
                 ("t_f_ms", ctypes.c_double), ("t_jac_ms", ctypes.c_double), ("t_lu_ms", ctypes.c_double),
                 ("t_lin_ms", ctypes.c_double), ("gpu_launches", ctypes.c_int), ("lu_pivoted", ctypes.c_int),
                 ("reserved", ctypes.c_int * 14)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int), ("converged", ctypes.c_int), ("parked_lu", ctypes.c_int),
+                ("parked_ir", ctypes.c_int), ("newton_rounds", ctypes.c_int), ("ir_rounds", ctypes.c_int),
+                ("lu_nb", ctypes.c_int), ("trailing_gemm", ctypes.c_int), ("gpu_launches", ctypes.c_int),
+                ("graph_nodes_step", ctypes.c_int), ("graph_nodes_ir", ctypes.c_int), ("tune_count", ctypes.c_int),
+                ("tune_nb", ctypes.c_int * 8), ("tune_gemm", ctypes.c_int * 8), ("tune_ms", ctypes.c_double * 8),
+                ("t_total_ms", ctypes.c_double), ("t_graph_ms", ctypes.c_double), ("t_single_ms", ctypes.c_double),
+                ("reserved", ctypes.c_int * 16)]
 
 
 _lock = threading.Lock()
@@ -77,6 +87,16 @@ SIGNATURES = {
     "nl_k_gemm16_update": (_int, [_i64, _i64, _i64, _P, _i64, _P, _i64, _P, _i64, _int, _P]),
     "nl_linsolve16": (_int, [_i64, _P, _i64, _P, _i64, _P, _P, _P, _dbl, _int, _int, _int, _dbl, _int,
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _P]),
+    "nl_batch_create": (_int, [_int, _P, _P, ctypes.POINTER(Config), ctypes.POINTER(_P)]),
+    "nl_batch_solve": (_int, [_P, _P, _dbl, _int, _P]),
+    "nl_batch_solve_device": (_int, [_P, _P, _dbl, _int, _P]),
+    "nl_batch_stats": (_int, [_P, _int, ctypes.POINTER(Stats)]),
+    "nl_batch_info": (_int, [_P, ctypes.POINTER(BatchInfo)]),
+    "nl_batch_set_stream": (_int, [_P, _P]),
+    "nl_batch_device_bytes": (_i64, [_P]),
+    "nl_batch_destroy": (None, [_P]),
+    "nl_lu_grouped": (_int, [_int, _P, _P, _P, _P, _int, _int, _int, _P, _P]),
+    "nl_lusolve_grouped": (_int, [_int, _P, _P, _P, _P, _P, _int, _P]),
 }
 
 
@@ -204,6 +224,81 @@ class Solver:
         return lib().nl_device_bytes(self._h)
 
 
+def _stats_dict(s: Stats) -> dict:
+    n = s.newton_iters
+    return dict(status=s.status, mode=s.mode, newton_iters=n, lu_nb=s.lu_nb, fnorm0=s.fnorm0, fnorm=s.fnorm,
+                hist=list(s.hist[: n + 1]), lin_iters=list(s.lin_iters[:n]), lin_outer=list(s.lin_outer[:n]),
+                lin_failed=list(s.lin_failed[:n]), lin_relres=list(s.lin_relres[:n]),
+                t_total_ms=s.t_total_ms, gpu_launches=s.gpu_launches, lu_pivoted=s.lu_pivoted)
+
+
+class Batch:
+    """Owns one nl_batch handle: many (N, c) instances solved together."""
+
+    def __init__(self, Ns, cs, stream=None, **cfg):
+        self.N = np.ascontiguousarray(Ns, dtype=np.int64)
+        self.c = np.ascontiguousarray(cs, dtype=np.float64)
+        if self.N.shape != self.c.shape or self.N.ndim != 1:
+            raise ValueError("Ns and cs must be 1-D arrays of the same length")
+        self.count = int(self.N.size)
+        self.off = np.concatenate([[0], np.cumsum(self.N)]).astype(np.int64)
+        self._h = _P()
+        check(lib().nl_batch_create(self.count, self.N.ctypes.data, self.c.ctypes.data, ctypes.byref(config(**cfg)),
+                                    ctypes.byref(self._h)))
+        if stream is not None:
+            check(lib().nl_batch_set_stream(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            lib().nl_batch_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, tol=1e-10, mode="IR16_GMRES", x0=None):
+        """Host-memory solve (nl_batch_solve).  Returns (list of x, status)."""
+        x = np.empty(int(self.off[-1]))
+        x0p = None
+        if x0 is not None:
+            x0 = np.ascontiguousarray(x0, dtype=np.float64)
+            x0p = x0.ctypes.data
+        st = lib().nl_batch_solve(self._h, x0p, float(tol), MODES[mode] if isinstance(mode, str) else int(mode),
+                                  x.ctypes.data)
+        check(st, allow=(NL_ENOTCONV, NL_ENUMERIC, NL_ESINGULAR))
+        return [x[self.off[i]:self.off[i + 1]] for i in range(self.count)], st
+
+    def solve_device(self, x_out, tol=1e-10, mode="IR16_GMRES", x0=None):
+        st = lib().nl_batch_solve_device(self._h, _ptr(x0), float(tol),
+                                         MODES[mode] if isinstance(mode, str) else int(mode), _ptr(x_out))
+        return check(st, allow=(NL_ENOTCONV, NL_ENUMERIC, NL_ESINGULAR))
+
+    def stats(self, i: int) -> dict:
+        s = Stats()
+        check(lib().nl_batch_stats(self._h, int(i), ctypes.byref(s)))
+        return _stats_dict(s)
+
+    def info(self) -> dict:
+        b = BatchInfo()
+        check(lib().nl_batch_info(self._h, ctypes.byref(b)))
+        d = {k: getattr(b, k) for k, _ in BatchInfo._fields_ if k not in ("tune_nb", "tune_gemm", "tune_ms",
+                                                                         "reserved")}
+        d["tune"] = [(b.tune_nb[k], b.tune_gemm[k], b.tune_ms[k]) for k in range(b.tune_count)]
+        return d
+
+    def device_bytes(self) -> int:
+        return lib().nl_batch_device_bytes(self._h)
+
+
 # ---------------------------------------------------------------- kernels --
 
 def k_residual(N, c, x, F, r, fnorm, u=None, u_is_double=False, scale=0.0, x_out=None, stream=None):
@@ -262,3 +357,28 @@ def linsolve16(N, J32, ld32, LU16, ld16, ipiv, b, u, eta=1e-4, maxit=20, solver=
     check(lib().nl_linsolve16(N, _ptr(J32), ld32, _ptr(LU16), ld16, _ptr(ipiv), _ptr(b), _ptr(u), eta, maxit, solver,
                               m, gtol, gcycles, stats, ctypes.byref(rel), _stream(stream)))
     return dict(iters=stats[0], outer=stats[1], failed=stats[2], converged=stats[3], relres=rel.value)
+
+
+def lu_grouped(Ns, As, lds, ipivs, fp64=False, nb=0, gemm=0, stream=None):
+    """Grouped LU (nl_lu_grouped) of device matrices; returns the per-matrix flags."""
+    n = len(Ns)
+    Na = np.ascontiguousarray(Ns, dtype=np.int64)
+    lda = np.ascontiguousarray(lds, dtype=np.int64)
+    Ap = np.ascontiguousarray([_ptr(a) for a in As], dtype=np.uint64)
+    Pp = np.ascontiguousarray([_ptr(p) for p in ipivs], dtype=np.uint64)
+    flags = np.zeros(n, dtype=np.int32)
+    check(lib().nl_lu_grouped(n, Na.ctypes.data, Ap.ctypes.data, lda.ctypes.data, Pp.ctypes.data, int(fp64), nb, gemm,
+                              flags.ctypes.data, _stream(stream)))
+    return flags
+
+
+def lusolve_grouped(Ns, LUs, lds, ipivs, bs, fp64=False, stream=None):
+    """Grouped triangular solves (nl_lusolve_grouped), in place on the device vectors bs."""
+    n = len(Ns)
+    Na = np.ascontiguousarray(Ns, dtype=np.int64)
+    lda = np.ascontiguousarray(lds, dtype=np.int64)
+    Lp = np.ascontiguousarray([_ptr(a) for a in LUs], dtype=np.uint64)
+    Pp = np.ascontiguousarray([_ptr(p) for p in ipivs], dtype=np.uint64)
+    Bp = np.ascontiguousarray([_ptr(b) for b in bs], dtype=np.uint64)
+    return check(lib().nl_lusolve_grouped(n, Na.ctypes.data, Lp.ctypes.data, lda.ctypes.data, Pp.ctypes.data,
+                                          Bp.ctypes.data, int(fp64), _stream(stream)))

@@ -63,3 +63,27 @@ def test_no_device_is_an_error_not_a_fallback():
     assert nl.lib().nl_create(64, 0.5, None, nl.ctypes.byref(h)) == nl.NL_ECUDA
     with pytest.raises(nl.NLError):
         nl.Solver(64, 0.5)
+
+
+def test_batch_arguments_validated():
+    L = nl.lib()
+    h = nl._P()
+    import numpy as np
+    for Ns, cs in [([], []), ([0], [0.5]), ([8193], [0.5]), ([10, 20], [0.5, 1.0]), ([10], [-0.5])]:
+        N = np.ascontiguousarray(Ns, dtype=np.int64)
+        c = np.ascontiguousarray(cs, dtype=np.float64)
+        assert L.nl_batch_create(len(Ns), N.ctypes.data if len(Ns) else None, c.ctypes.data if len(cs) else None,
+                                 None, nl.ctypes.byref(h)) == nl.NL_EINVAL
+    assert L.nl_batch_solve(None, None, 1e-10, nl.NL_IR16_GMRES, None) == nl.NL_EINVAL
+    assert L.nl_batch_stats(None, 0, None) == nl.NL_EINVAL
+    assert L.nl_lu_grouped(0, None, None, None, None, 0, 0, 0, None, None) == nl.NL_EINVAL
+    assert L.nl_lusolve_grouped(0, None, None, None, None, None, 0, None) == nl.NL_EINVAL
+    L.nl_batch_destroy(None)
+
+
+def test_batch_no_device_is_an_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(nl.NLError):
+        nl.Batch([64, 100], [0.5, 0.9])

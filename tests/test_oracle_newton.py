@@ -166,3 +166,23 @@ def test_tables_full_size_n4096(table2, table3):
         _check_column(r["hist"], tab["F64"], len(tab["F64"]) - 1)
         _, r = O.newton(4096, c, "GMRESIR16", paper=True, tol=1e-9)
         _check_column(r["hist"], tab["IR-GM"], len(tab["IR-GM"]) - 2, last_rel=0.02)
+
+
+def test_ir16_gmres_fallback_rule():
+    """IR16 with GMRES-IR fallback (the batched path's mode): while IR meets
+    eta it is IR16 step for step; when the first step's IR cannot (one
+    correction towards eta = 1e-6), that step and every later one are
+    GMRES-IR solves from u0 = 0, so the iterates are exactly those of
+    GMRES-IR Newton, and the stalled step records the IR attempt."""
+    for c in (0.5, 0.99):
+        x1, r1 = O.newton(300, c, "IR16GM", tol=1e-10)
+        x2, r2 = O.newton(300, c, "IR16", tol=1e-10)
+        assert np.array_equal(x1, x2) and r1["hist"] == r2["hist"] and not any(r1["lin_failed"])
+    kw = dict(tol=1e-10, ir_maxit=1, eta=1e-6)
+    x1, r1 = O.newton(300, 0.99, "IR16GM", **kw)
+    x2, r2 = O.newton(300, 0.99, "GMRESIR16", **kw)
+    x3, r3 = O.newton(300, 0.99, "IR16", **kw)
+    assert np.array_equal(x1, x2) and r1["hist"] == r2["hist"]
+    assert r1["lin_failed"][0] == 1 and r1["lin_iters"][0] == r2["lin_iters"][0] + 1
+    assert r1["lin_iters"][1:] == r2["lin_iters"][1:]
+    assert not np.array_equal(x1, x3)
