@@ -9,6 +9,10 @@ value     : solves/s with x0/x in HBM (nl_solve_device), CUDA events.
 e2e       : solves/s through nl_solve with host buffers (copies included).
 baselines : the same sweep with FP64-LU Newton and with IR16 on the same GPU,
             and the CPU oracle on the host cores (a bounded sample).
+batched   : the 512-instance batch (one graph-captured batched solve), and
+            the same batch with FP64-LU Newton.
+serving   : the serving trace's first --serve-seconds seconds replayed in
+            real time through the request loop: p50/p99 latency, solves/s.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -148,6 +152,89 @@ def ncu_traffic(kernel):
     return None
 
 
+def bench_batched(nl, W, torch, dev, steps, warmup, tc_peak, fp64=True):
+    """The 512-instance batch (N log-uniform in [64, 2048], c uniform in
+    [0.1, 0.999], x0 = ones, seed 230716051): one graph-captured batched solve
+    per step, x in HBM; the same batch with FP64-LU Newton on the same GPU."""
+    inst = W.batch_instances()
+    Ns, cs = [n for n, _ in inst], [c for _, c in inst]
+    B = nl.Batch(Ns, cs)
+    tot = int(sum(Ns))
+    xout = torch.empty(tot, device=dev, dtype=torch.float64)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
+    for _ in range(max(1, warmup)):
+        B.solve_device(xout, tol=TOL, mode="IR16_GMRES")
+    ms = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = B.solve_device(xout, tol=TOL, mode="IR16_GMRES")
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    info = B.info()
+    lu_flop = sum(2.0 * n ** 3 / 3.0 for n in Ns)
+    best = min(info["tune"], key=lambda t: t[2]) if info["tune"] else None
+    out = {"workload": "512 instances, N log-uniform [64, 2048] (seed 230716051), c uniform [0.1, 0.999], x0=ones, "
+                       "IR16 with GMRES-IR16 fallback, eta 1e-4, to 1e-10",
+           "status": nl.STATUS_NAMES[st], "solves_per_s": len(Ns) / (statistics.median(ms) / 1e3),
+           "ms_per_batch": statistics.median(ms), "converged": info["converged"],
+           "parked_lu": info["parked_lu"], "parked_ir": info["parked_ir"], "newton_rounds": info["newton_rounds"],
+           "ir_rounds": info["ir_rounds"], "gpu_launches": info["gpu_launches"],
+           "graph": "one CUDA graph per solve: WHILE(Newton) { J, grouped LU, WHILE(IR) {...}, update }",
+           "autotune": [{"nb": t[0], "gemm": "tcgen05" if t[1] == 2 else "simt", "grouped_lu_ms": t[2]} for t in info["tune"]],
+           "lu_nb": info["lu_nb"], "trailing_gemm": "tcgen05" if info["trailing_gemm"] == 2 else "simt"}
+    if best:
+        tf = lu_flop / (best[2] / 1e3) / 1e12
+        out["grouped_lu"] = {"ms": best[2], "achieved": tf, "peak": tc_peak, "unit": "TFLOP/s", "frac": tf / tc_peak,
+                             "work": "sum of 2N^3/3 over the 512 Jacobians at x0"}
+    if fp64:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st64 = B.solve_device(xout, tol=TOL, mode="FP64LU")
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        i64 = B.info()
+        out["fp64lu"] = {"status": nl.STATUS_NAMES[st64], "solves_per_s": len(Ns) / (ms64 / 1e3), "ms_per_batch": ms64,
+                         "newton_rounds": i64["newton_rounds"]}
+        out["speedup_vs_fp64lu"] = ms64 / out["ms_per_batch"]
+    B.close()
+    return out
+
+
+def bench_serving(nl, W, seconds, mode="IR16_GMRES", drain_s=120.0, max_inflight=8):
+    """The serving trace (Poisson 200 req/s, N from {256, 1024, 4096, 16384}
+    with p = {.5, .3, .15, .05}, c uniform [.5, .9999], seed 16051), cut to
+    its first `seconds` seconds and replayed in real time."""
+    trace = W.serving_trace(duration_s=seconds)
+    with nl.Server(budget_bytes=96 << 30, max_inflight=max_inflight, mode=mode) as S:
+        ids = [S.submit(N, c, arrival_s=t) for t, N, c in trace]
+        S.start()
+        rc = S.drain(drain_s)
+        info = S.info()
+        per_n = {}
+        for rid, (t, N, c) in zip(ids, trace):
+            x, st, ri = S.result(rid, wait=False)
+            if ri["status"] == nl.NL_OK:
+                per_n.setdefault(N, []).append(ri["latency_ms"])
+    import numpy as np
+    out = {"workload": f"Poisson 200 req/s, first {seconds:g} s of the 60 s trace (seed 16051), N from "
+                       "{256,1024,4096,16384} p={.5,.3,.15,.05}, c uniform [.5,.9999], to 1e-10",
+           "mode": mode, "requests": len(trace), "completed": info["completed"], "failed": info["failed"],
+           "drained": rc == nl.NL_OK, "p50_ms": info["p50_ms"], "p99_ms": info["p99_ms"], "mean_ms": info["mean_ms"],
+           "solves_per_s": info["solves_per_s"], "span_s": info["span_s"], "inflight_peak": info["inflight_peak"],
+           "bytes_peak": info["bytes_peak"], "handles_created": info["handles_created"],
+           "per_N": {str(n): {"count": len(v), "p50_ms": float(np.percentile(v, 50)), "p99_ms": float(np.percentile(v, 99))}
+                     for n, v in sorted(per_n.items())},
+           "admission": f"device-memory footprint (budget 96 GiB), {max_inflight} slots, smallest N first with a "
+                        "250 ms starvation bound, high-priority streams for N <= 1024"}
+    return out
+
+
 def dist_init():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -222,6 +309,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--lu-nb", type=int, default=0, help="LU outer block (0: library default)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched workload")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="seconds of the serving trace to replay (0: skip serving)")
+    ap.add_argument("--serve-fp64-seconds", type=float, default=0.0,
+                    help="seconds of the serving trace to replay with FP64-LU Newton (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
@@ -316,6 +408,13 @@ def main():
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "roofline_lu": roofline_lu, "kernels": kern, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "per_c": per_c, **extra}
+    from paper_2307_16051_gb300 import workloads as W
+    if not args.no_batch:
+        line["batched"] = bench_batched(nl, W, torch, dev, args.steps, args.warmup, tc_peak, fp64=not args.no_fp64)
+    if args.serve_seconds > 0:
+        line["serving"] = bench_serving(nl, W, args.serve_seconds)
+    if args.serve_fp64_seconds > 0:
+        line["serving_fp64lu"] = bench_serving(nl, W, args.serve_fp64_seconds, mode="FP64LU", drain_s=60.0)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = oracle_sample(n_lu)
     if rank == 0:

@@ -130,6 +130,15 @@ int64_t nl_device_bytes(const nl_solver* s);
 /* Release the handle and its device memory.  NULL is a no-op. */
 void nl_destroy(nl_solver* s);
 
+/* Change the albedo c of an existing handle (its device state is reused; the
+ * next solve starts from its own x0).  0 <= c < 1. */
+nl_status nl_set_c(nl_solver* s, double c);
+
+/* Device bytes a handle for N needs in `mode` (NL_FP64LU adds the double
+ * Jacobian and its workspace), cfg as for nl_create (NULL = defaults).
+ * -1 on invalid arguments.  Used for admission by memory footprint. */
+int64_t nl_footprint_bytes(int64_t N, nl_mode mode, const nl_config* cfg);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* nl_last_error(void);
 
@@ -211,6 +220,86 @@ int64_t nl_batch_device_bytes(const nl_batch* b);
 
 /* Release the batch.  NULL is a no-op. */
 void nl_batch_destroy(nl_batch* b);
+
+/* ----------------------------------------------------------------------- */
+/* Serving: a request loop that admits solves of different N and c as      */
+/* device memory and execution slots free up, and runs them concurrently.  */
+/* ----------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t hbm_budget_bytes;  /* [64 GiB] device memory the server may hold (solver handles) */
+    int max_inflight;          /* [8] requests on the device at once (one worker thread and stream each) */
+    int mode;                  /* [NL_IR16_GMRES] nl_mode of every solve */
+    double tol;                /* [1e-10] tau_r of every solve */
+    int starve_ms;             /* [250] after the oldest waiting request has waited this long, no later
+                                  request is admitted before it */
+    int priority_n;            /* [1024] requests with N <= priority_n run on high-priority streams, so
+                                  that their short kernels are scheduled ahead of large factorisations */
+    int policy;                /* [1] admission order among arrived requests: 0 arrival order,
+                                  1 smallest N first (shortest solve first) */
+    nl_config solver;          /* solver parameters of every handle */
+    int reserved[8];
+} nl_server_config;
+
+/* Per-request results. */
+typedef struct {
+    int status;          /* nl_status of the solve; -1 while pending or running */
+    int N;
+    double c;
+    double t_arrive_s;   /* arrival, seconds after nl_server_start */
+    double t_admit_s;    /* admission (handle and slot granted) */
+    double t_done_s;     /* completion (x copied to the host) */
+    double latency_ms;   /* t_done - t_arrive */
+    int newton_iters;
+    int handle_reused;   /* 1 if the solve ran on a cached handle (no allocation) */
+    int reserved[6];
+} nl_request_info_t;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t bytes_held, bytes_peak;  /* device bytes of the handles the server holds (now, peak) */
+    int inflight_peak;               /* most requests on the device at once */
+    int handles_created, handles_evicted;
+    double p50_ms, p99_ms, mean_ms;  /* latency percentiles over completed requests */
+    double span_s;                   /* first arrival to last completion */
+    double solves_per_s;             /* completed / span_s */
+    int reserved[8];
+} nl_server_info_t;
+
+typedef struct nl_server nl_server;
+
+/* Defaults in brackets above (solver: nl_config_default). */
+nl_status nl_server_config_default(nl_server_config* cfg);
+
+/* Start a server (worker threads wait for nl_server_start).  The first call
+ * initialises the library's kernels on the current device. */
+nl_status nl_server_create(const nl_server_config* cfg, nl_server** out);
+
+/* Queue a request for the H-equation of size N and albedo c, arriving
+ * `arrival_s` seconds after nl_server_start (a negative value: now).  x0 =
+ * ones.  *id receives the request id.  Thread-safe. */
+nl_status nl_server_submit(nl_server* s, int64_t N, double c, double arrival_s, int64_t* id);
+
+/* Start the arrival clock and admission.  Requests are admitted in arrival
+ * order, skipping a request that does not fit in the memory budget for a
+ * later one that does (until the starvation bound); each runs on its own
+ * CUDA stream with its iterate, factors and Krylov basis on the device. */
+nl_status nl_server_start(nl_server* s);
+
+/* Result of request `id`.  wait != 0 blocks until it is done.  x_out (host,
+ * N doubles) and stats may be NULL.  Returns NL_EINVAL for an unknown id. */
+nl_status nl_server_result(nl_server* s, int64_t id, int wait, double* x_out, nl_stats_t* stats,
+                           nl_request_info_t* info);
+
+/* Wait until every submitted request is done (timeout_s <= 0: no limit);
+ * NL_ETIMEOUT if the limit passed first. */
+nl_status nl_server_drain(nl_server* s, double timeout_s);
+
+/* Counters and latency percentiles so far. */
+nl_status nl_server_info(nl_server* s, nl_server_info_t* out);
+
+/* Stop the workers (pending requests are dropped) and release all memory. */
+void nl_server_destroy(nl_server* s);
 
 /* Grouped LU of `count` independent matrices (the batched factorisation of
  * Section 2's J_h, one launch per kernel class per outer step): A[i] (device,

@@ -486,7 +486,7 @@ struct nl_batch {
     std::vector<int> ld;
     int nmax = 0, total_rows = 0;
     cudaStream_t st = nullptr, s1 = nullptr, s2 = nullptr;
-    bool own_streams = false;
+    bool own_streams = false, own_st = true;
     // device memory
     void* pool = nullptr;
     size_t pool_bytes = 0;
@@ -543,7 +543,7 @@ static void batch_free(nl_batch* B)
     if (B->pool) cudaFree(B->pool);
     if (B->pool64) cudaFree(B->pool64);
     if (B->own_streams) {
-        if (B->st) cudaStreamDestroy(B->st);
+        if (B->st && B->own_st) cudaStreamDestroy(B->st);
         if (B->s1) cudaStreamDestroy(B->s1);
         if (B->s2) cudaStreamDestroy(B->s2);
     }
@@ -1196,10 +1196,11 @@ nl_status nl_batch_set_stream(nl_batch* b, void* stream)
         set_error("nl_batch_set_stream: NULL handle");
         return NL_EINVAL;
     }
-    if (b->own_streams && b->st) {
+    if (b->own_st && b->st) {
         cudaStreamSynchronize(b->st);
         cudaStreamDestroy(b->st);
     }
+    b->own_st = false;
     b->st = (cudaStream_t)stream;
     return NL_OK;
 }

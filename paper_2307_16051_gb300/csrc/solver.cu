@@ -271,6 +271,49 @@ struct nl_solver {
     cudaEvent_t ev[2] = {nullptr, nullptr};
 };
 
+// Device bytes of one handle's main allocation (layout of nl_create).
+static size_t solver_bytes(int n, const nl_config& d)
+{
+    const int m = d.gmres_restart;
+    const int nb = d.lu_nb ? d.lu_nb : 128;
+    const int64_t ld = round_up(n, 64), ldv = ld;
+    const size_t npart = (size_t)std::max(residual_partials(n), gemv_partials(n)) + 64;
+    Carver cv(nullptr);
+    cv.take<double>(n);            // xa
+    cv.take<double>(n);            // xb
+    cv.take<double>(n);            // F
+    cv.take<double>(n);            // rr
+    cv.take<double>(2 * n);        // htab
+    cv.take<double>(npart);        // partial
+    cv.take<double>(16);           // dscal
+    cv.take<unsigned>(4);          // counter
+    cv.take<double>(gmres_ws_doubles(m));
+    cv.take<float>((size_t)n * ld);     // J32
+    cv.take<__half>((size_t)n * ld);    // J16
+    cv.take<int>(n);               // ipiv
+    cv.take<float>(ldv);           // b
+    cv.take<float>(ldv);           // u
+    for (int q = 0; q < 5; ++q) cv.take<float>(ldv);  // r d t w ubest
+    cv.take<float>((size_t)(m + 1) * ldv);            // V
+    cv.take<char>(lu_work_bytes(n, nb, false));
+    cv.take<char>(trsv_work_bytes(n, false));
+    return cv.off + 256;
+}
+
+// Device bytes of the double-precision mode's extra allocation.
+static size_t solver64_bytes(int n)
+{
+    const int64_t ld = round_up(n, 64);
+    Carver cv(nullptr);
+    cv.take<double>((size_t)n * ld);
+    cv.take<double>(n);
+    cv.take<double>(n);
+    cv.take<int>(n);
+    cv.take<char>(lu_work_bytes(n, 64, true));
+    cv.take<char>(trsv_work_bytes(n, true));
+    return cv.off + 256;
+}
+
 static bool valid_mode(int m) { return m == NL_FP64LU || m == NL_IR16 || m == NL_GMRESIR16 || m == NL_IR16_GMRES; }
 
 extern "C" {
@@ -352,30 +395,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     const int m = d.gmres_restart;
     const int64_t ldv = round_up(N, 64);
     const size_t npart = (size_t)std::max(residual_partials(n), gemv_partials(n)) + 64;
-    // sizes
-    size_t bytes = 0;
-    {
-        Carver cv(nullptr);
-        cv.take<double>(n);            // xa
-        cv.take<double>(n);            // xb
-        cv.take<double>(n);            // F
-        cv.take<double>(n);            // rr
-        cv.take<double>(2 * n);        // htab
-        cv.take<double>(npart);        // partial
-        cv.take<double>(16);           // dscal
-        cv.take<unsigned>(4);          // counter
-        cv.take<double>(gmres_ws_doubles(m));
-        cv.take<float>((size_t)n * s->ld);     // J32
-        cv.take<__half>((size_t)n * s->ld);    // J16
-        cv.take<int>(n);               // ipiv
-        cv.take<float>(ldv);           // b
-        cv.take<float>(ldv);           // u
-        for (int q = 0; q < 5; ++q) cv.take<float>(ldv);  // r d t w ubest
-        cv.take<float>((size_t)(m + 1) * ldv);            // V
-        cv.take<char>(lu_work_bytes(n, s->nb, false));
-        cv.take<char>(trsv_work_bytes(n, false));
-        bytes = cv.off + 256;
-    }
+    const size_t bytes = solver_bytes(n, d);
     if (cudaMalloc(&s->pool, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
@@ -440,6 +460,27 @@ nl_status nl_set_stream(nl_solver* s, void* stream)
 
 int64_t nl_device_bytes(const nl_solver* s) { return s ? (int64_t)(s->pool_bytes + s->pool64_bytes) : 0; }
 
+int64_t nl_footprint_bytes(int64_t N, nl_mode mode, const nl_config* cfg)
+{
+    if (N < 1 || N > 32768 || !valid_mode(mode)) return -1;
+    nl_config d;
+    nl_config_default(&d);
+    if (cfg) d = *cfg;
+    size_t b = solver_bytes((int)N, d);
+    if (mode == NL_FP64LU) b += solver64_bytes((int)N);
+    return (int64_t)b;
+}
+
+nl_status nl_set_c(nl_solver* s, double c)
+{
+    if (!s || !(c >= 0.0 && c < 1.0)) {
+        set_error("nl_set_c: need a handle and 0 <= c < 1");
+        return NL_EINVAL;
+    }
+    s->c = c;
+    return NL_OK;
+}
+
 void nl_destroy(nl_solver* s)
 {
     if (!s) return;
@@ -458,17 +499,7 @@ static nl_status ensure_fp64(nl_solver* s)
     if (s->pool64) return NL_OK;
     const int n = s->N;
     const int nb64 = 64;
-    size_t bytes;
-    {
-        Carver cv(nullptr);
-        cv.take<double>((size_t)n * s->ld);
-        cv.take<double>(n);
-        cv.take<double>(n);
-        cv.take<int>(n);
-        cv.take<char>(lu_work_bytes(n, nb64, true));
-        cv.take<char>(trsv_work_bytes(n, true));
-        bytes = cv.off + 256;
-    }
+    const size_t bytes = solver64_bytes(n);
     if (cudaMalloc(&s->pool64, bytes) != cudaSuccess) {
         cudaGetLastError();
         s->pool64 = nullptr;
@@ -503,7 +534,10 @@ static nl_status check_device_errors(nl_solver* s)
     NL_CUDA_OK(cudaStreamSynchronize(s->st));
     unsigned* tce = tc_error_word();
     unsigned e3 = 0;
-    if (tce) NL_CUDA_OK(cudaMemcpy(&e3, tce, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (tce) {
+        NL_CUDA_OK(cudaMemcpyAsync(&e3, tce, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+        NL_CUDA_OK(cudaStreamSynchronize(s->st));
+    }
     if (e[0] | e[1] | e3) {
         set_error("a device-side bounded wait gave up (error word 0x%x/0x%x/0x%x)", e[0], e[1], e3);
         cudaMemsetAsync(s->tw.err, 0, sizeof(unsigned), s->st);

@@ -57,6 +57,27 @@ class BatchInfo(ctypes.Structure):
                 ("reserved", ctypes.c_int * 16)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int), ("mode", ctypes.c_int),
+                ("tol", ctypes.c_double), ("starve_ms", ctypes.c_int), ("priority_n", ctypes.c_int),
+                ("policy", ctypes.c_int), ("solver", Config),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("N", ctypes.c_int), ("c", ctypes.c_double), ("t_arrive_s", ctypes.c_double),
+                ("t_admit_s", ctypes.c_double), ("t_done_s", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("newton_iters", ctypes.c_int), ("handle_reused", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("bytes_held", ctypes.c_int64), ("bytes_peak", ctypes.c_int64), ("inflight_peak", ctypes.c_int),
+                ("handles_created", ctypes.c_int), ("handles_evicted", ctypes.c_int), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double), ("span_s", ctypes.c_double),
+                ("solves_per_s", ctypes.c_double), ("reserved", ctypes.c_int * 8)]
+
+
 _lock = threading.Lock()
 _lib = None
 _P = ctypes.c_void_p
@@ -95,6 +116,16 @@ SIGNATURES = {
     "nl_batch_set_stream": (_int, [_P, _P]),
     "nl_batch_device_bytes": (_i64, [_P]),
     "nl_batch_destroy": (None, [_P]),
+    "nl_set_c": (_int, [_P, _dbl]),
+    "nl_footprint_bytes": (_i64, [_i64, _int, ctypes.POINTER(Config)]),
+    "nl_server_config_default": (_int, [ctypes.POINTER(ServerConfig)]),
+    "nl_server_create": (_int, [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)]),
+    "nl_server_submit": (_int, [_P, _i64, _dbl, _dbl, ctypes.POINTER(ctypes.c_int64)]),
+    "nl_server_start": (_int, [_P]),
+    "nl_server_result": (_int, [_P, _i64, _int, _P, ctypes.POINTER(Stats), ctypes.POINTER(RequestInfo)]),
+    "nl_server_drain": (_int, [_P, _dbl]),
+    "nl_server_info": (_int, [_P, ctypes.POINTER(ServerInfo)]),
+    "nl_server_destroy": (None, [_P]),
     "nl_lu_grouped": (_int, [_int, _P, _P, _P, _P, _int, _int, _int, _P, _P]),
     "nl_lusolve_grouped": (_int, [_int, _P, _P, _P, _P, _P, _int, _P]),
 }
@@ -382,3 +413,74 @@ def lusolve_grouped(Ns, LUs, lds, ipivs, bs, fp64=False, stream=None):
     Bp = np.ascontiguousarray([_ptr(b) for b in bs], dtype=np.uint64)
     return check(lib().nl_lusolve_grouped(n, Na.ctypes.data, Lp.ctypes.data, lda.ctypes.data, Pp.ctypes.data,
                                           Bp.ctypes.data, int(fp64), _stream(stream)))
+
+
+def footprint_bytes(N, mode="IR16_GMRES", **cfg) -> int:
+    return lib().nl_footprint_bytes(int(N), MODES[mode] if isinstance(mode, str) else int(mode),
+                                    ctypes.byref(config(**cfg)))
+
+
+class Server:
+    """Owns one nl_server: requests admitted by device-memory footprint and
+    solved concurrently on their own streams."""
+
+    def __init__(self, budget_bytes=64 << 30, max_inflight=8, mode="IR16_GMRES", tol=1e-10, starve_ms=250,
+                 priority_n=1024, policy=1, **cfg):
+        sc = ServerConfig()
+        check(lib().nl_server_config_default(ctypes.byref(sc)))
+        sc.hbm_budget_bytes = int(budget_bytes)
+        sc.max_inflight = int(max_inflight)
+        sc.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+        sc.tol = float(tol)
+        sc.starve_ms = int(starve_ms)
+        sc.priority_n = int(priority_n)
+        sc.policy = int(policy)
+        for k, v in cfg.items():
+            setattr(sc.solver, k, v)
+        self._h = _P()
+        check(lib().nl_server_create(ctypes.byref(sc), ctypes.byref(self._h)))
+        self.sizes = {}
+
+    def submit(self, N, c, arrival_s=-1.0) -> int:
+        rid = ctypes.c_int64(0)
+        check(lib().nl_server_submit(self._h, int(N), float(c), float(arrival_s), ctypes.byref(rid)))
+        self.sizes[rid.value] = int(N)
+        return rid.value
+
+    def start(self):
+        check(lib().nl_server_start(self._h))
+
+    def result(self, rid, wait=True):
+        """(x, stats dict, request info dict) of request rid."""
+        N = self.sizes[rid]
+        x = np.empty(N)
+        s = Stats()
+        ri = RequestInfo()
+        check(lib().nl_server_result(self._h, int(rid), int(wait), x.ctypes.data, ctypes.byref(s), ctypes.byref(ri)))
+        info = {k: getattr(ri, k) for k, _ in RequestInfo._fields_ if k != "reserved"}
+        return x, _stats_dict(s), info
+
+    def drain(self, timeout_s=0.0):
+        return check(lib().nl_server_drain(self._h, float(timeout_s)), allow=(NL_ETIMEOUT,))
+
+    def info(self) -> dict:
+        si = ServerInfo()
+        check(lib().nl_server_info(self._h, ctypes.byref(si)))
+        return {k: getattr(si, k) for k, _ in ServerInfo._fields_ if k != "reserved"}
+
+    def close(self):
+        if self._h:
+            lib().nl_server_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

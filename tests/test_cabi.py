@@ -87,3 +87,16 @@ def test_batch_no_device_is_an_error():
         pytest.skip("a GPU is present")
     with pytest.raises(nl.NLError):
         nl.Batch([64, 100], [0.5, 0.9])
+
+
+def test_server_no_device_is_an_error():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(nl.NLError):
+        nl.Server()
+    assert nl.lib().nl_server_submit(None, 64, 0.5, 0.0, None) == nl.NL_EINVAL
+    assert nl.lib().nl_server_create(None, None) == nl.NL_EINVAL
+    assert nl.footprint_bytes(1024) > 6 * 1024 * 1024
+    assert nl.footprint_bytes(1024, "FP64LU") > nl.footprint_bytes(1024) + 8 * 1024 * 1024
+    assert nl.lib().nl_footprint_bytes(0, 1, None) == -1
