@@ -13,6 +13,8 @@ batched   : the 512-instance batch (one graph-captured batched solve), and
             the same batch with FP64-LU Newton.
 serving   : the serving trace's first --serve-seconds seconds replayed in
             real time through the request loop: p50/p99 latency, solves/s.
+large     : one GMRES-IR16 solve at N = 32768, c = .99, autotuned panel width
+            (LU TFLOP/s, residual / triangular-solve GB/s).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -206,6 +208,65 @@ def bench_batched(nl, W, torch, dev, steps, warmup, tc_peak, fp64=True):
     return out
 
 
+def bench_large(nl, torch, dev, hbm_peak, tc_peak, N=32768, c=0.99, fp64=False):
+    """One GMRES-IR16 solve at N = 32768, c = .99 with the autotuned panel
+    width: time to 1e-10, the factorisation's TFLOP/s, and the residual GEMV
+    and triangular solves' GB/s (CUDA events on every launch)."""
+    s = nl.Solver(N, c, lu_nb=-1)
+    x = torch.empty(N, device=dev, dtype=torch.float64)
+    s.solve_device(x, tol=TOL, mode="GMRESIR16")  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    status = s.solve_device(x, tol=TOL, mode="GMRESIR16")
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = s.stats()
+    lu_flop = 2.0 * N ** 3 / 3.0
+    lu_ms = st["t_lu_ms"] / max(1, st["newton_iters"])
+    lu_tf = lu_flop / (lu_ms / 1e3) / 1e12
+    kern = {}
+    T2 = 128
+    nblk = (N + T2 - 1) // T2
+    work = {"k_gemv_residual": 4.0 * N * N + 12.0 * N,
+            "k_trsv_mb": (N * N / 2.0) * 2 + nblk * T2 * T2 * 4 + 12.0 * N,
+            "k_tc_gemm": None}
+    for name in ("k_gemv_residual", "k_trsv_mb", "k_tc_gemm"):
+        nl.kernel_timing(name)
+        s.solve_device(x, tol=TOL, mode="GMRESIR16")
+        n, kms = nl.kernel_timing(None)
+        if n:
+            k = {"launches": n, "total_ms": kms, "avg_us": kms / n * 1e3}
+            if work[name]:
+                gbs = work[name] / (kms / n / 1e3) / 1e9
+                k.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                          "work_per_launch": work[name]})
+            kern[name] = k
+    out = {"workload": f"H-equation N={N}, c={c}, x0=ones, GMRES-IR16 (restart 30, tol 1e-4), eta 1e-4, to 1e-10, "
+                       "panel width autotuned", "status": nl.STATUS_NAMES[status], "ms_to_solution": ms,
+           "newton": st["newton_iters"], "lin_iters": st["lin_iters"], "lu_nb": st["lu_nb"],
+           "autotune": [{"nb": nb, "lu_ms": t} for nb, t in st["lu_tune"]],
+           "lu": {"ms_per_factorisation": lu_ms, "achieved": lu_tf, "peak": tc_peak, "unit": "TFLOP/s",
+                  "frac": lu_tf / tc_peak, "work": "2N^3/3"},
+           "t_f_ms": st["t_f_ms"], "t_jac_ms": st["t_jac_ms"], "t_lu_ms": st["t_lu_ms"], "t_lin_ms": st["t_lin_ms"],
+           "kernels": kern, "final_rel_res": st["hist"][-1]}
+    s.close()
+    if fp64:
+        s64 = nl.Solver(N, c)
+        torch.cuda.synchronize()
+        e0.record()
+        st64 = s64.solve_device(x, tol=TOL, mode="FP64LU")
+        e1.record()
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        out["fp64lu"] = {"status": nl.STATUS_NAMES[st64], "ms_to_solution": ms64, "newton": s64.stats()["newton_iters"],
+                         "lu_ms_per_factorisation": s64.stats()["t_lu_ms"] / max(1, s64.stats()["newton_iters"])}
+        out["speedup_vs_fp64lu"] = ms64 / ms
+        s64.close()
+    return out
+
+
 def bench_serving(nl, W, seconds, mode="IR16_GMRES", drain_s=120.0, max_inflight=8):
     """The serving trace (Poisson 200 req/s, N from {256, 1024, 4096, 16384}
     with p = {.5, .3, .15, .05}, c uniform [.5, .9999], seed 16051), cut to
@@ -310,6 +371,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--lu-nb", type=int, default=0, help="LU outer block (0: library default)")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched workload")
+    ap.add_argument("--no-large", action="store_true", help="skip the N=32768 single solve")
+    ap.add_argument("--large-fp64", action="store_true", help="also time FP64-LU Newton at N=32768 (minutes)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="seconds of the serving trace to replay (0: skip serving)")
     ap.add_argument("--serve-fp64-seconds", type=float, default=0.0,
@@ -411,6 +474,8 @@ def main():
     from paper_2307_16051_gb300 import workloads as W
     if not args.no_batch:
         line["batched"] = bench_batched(nl, W, torch, dev, args.steps, args.warmup, tc_peak, fp64=not args.no_fp64)
+    if not args.no_large:
+        line["large"] = bench_large(nl, torch, dev, hbm_peak, tc_peak, fp64=args.large_fp64)
     if args.serve_seconds > 0:
         line["serving"] = bench_serving(nl, W, args.serve_seconds)
     if args.serve_fp64_seconds > 0:

@@ -66,8 +66,10 @@ typedef struct {
     int gmres_maxcycles; /* [10]  GMRES restart cycles per outer correction */
     int newton_maxit;    /* [30]  cap on Newton steps */
     double tau_a;        /* [0]   absolute tolerance tau_a of Algorithm 1.1 */
-    int lu_nb;           /* [0 = auto (128)] outer block of the LU (multiple of 16, <= 128); also its
-                            binary16 rounding period */
+    int lu_nb;           /* [0 = 128] outer block of the LU (multiple of 16, <= 128); also its binary16
+                            rounding period.  -1 = autotune at nl_create: the factorisation of the
+                            Jacobian at x0 = ones is timed for nb in {128, 96, 64, 32} (tcgen05 update
+                            for multiples of 64, SIMT otherwise) and the fastest is kept */
     int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update */
     int lu_path;         /* [0 = auto] no-interchange fast path with exact fallback; 1 = interchanging path only */
     int reserved[7];
@@ -92,7 +94,10 @@ typedef struct {
     double t_f_ms, t_jac_ms, t_lu_ms, t_lin_ms; /* device time per phase (CUDA events), summed */
     int gpu_launches;                 /* kernels launched by the solve */
     int lu_pivoted;                   /* factorisations that needed row interchanges (interchanging path) */
-    int reserved[14];
+    int lu_tune_count;                /* autotuner candidates timed at nl_create (lu_nb = -1), else 0 */
+    int lu_tune_nb[4];
+    float lu_tune_ms[4];              /* factorisation time of each candidate */
+    int reserved[5];
 } nl_stats_t;
 
 typedef struct nl_solver nl_solver;

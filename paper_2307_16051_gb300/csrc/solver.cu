@@ -269,13 +269,16 @@ struct nl_solver {
     int gemm = 2;
     nl_stats_t stats;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    int tune_count = 0;
+    int tune_nb[4] = {0, 0, 0, 0};
+    float tune_ms[4] = {0, 0, 0, 0};
 };
 
 // Device bytes of one handle's main allocation (layout of nl_create).
 static size_t solver_bytes(int n, const nl_config& d)
 {
     const int m = d.gmres_restart;
-    const int nb = d.lu_nb ? d.lu_nb : 128;
+    const int nb = d.lu_nb > 0 ? d.lu_nb : 128;  // the autotuner (-1) only ever lowers it
     const int64_t ld = round_up(n, 64), ldv = ld;
     const size_t npart = (size_t)std::max(residual_partials(n), gemv_partials(n)) + 64;
     Carver cv(nullptr);
@@ -312,6 +315,51 @@ static size_t solver64_bytes(int n)
     cv.take<char>(lu_work_bytes(n, 64, true));
     cv.take<char>(trsv_work_bytes(n, true));
     return cv.off + 256;
+}
+
+// lu_nb = -1: time the factorisation of the Jacobian at x0 = ones for each
+// candidate outer block (tcgen05 update where nb is a multiple of 64, SIMT
+// otherwise) and keep the fastest.  nb is also the binary16 rounding period.
+static nl_status autotune_lu(nl_solver* s)
+{
+    const int n = s->N;
+    const int cands[4] = {128, 96, 64, 32};
+    cudaStream_t st = s->st;
+    k_fill64<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, 1.0, s->xa);
+    NL_TRY(launch_residual(n, s->c, s->xa, nullptr, 0, 0.0, s->htab, nullptr, s->F, s->rr, s->partial, s->counter,
+                           s->dscal, st));
+    float best = 1e30f;
+    int bnb = 128, k = 0;
+    for (int nb : cands) {
+        if (nb > n && nb != 128) continue;
+        const int gemm = (nb % 64 == 0 && tc_gemm_supported()) ? 2 : 1;
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+            NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st));
+            lu_work_carve(s->luw.pnl, n, nb, false, &s->luw);
+            cudaEventRecord(s->ev[0], st);
+            NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, nb, gemm, true, s->luw, st, nullptr));
+            cudaEventRecord(s->ev[1], st);
+            NL_CUDA_OK(cudaEventSynchronize(s->ev[1]));
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, s->ev[0], s->ev[1]);
+            ms_best = std::min(ms_best, ms);
+        }
+        if (k < 4) {
+            s->tune_nb[k] = nb;
+            s->tune_ms[k] = ms_best;
+            ++k;
+        }
+        if (ms_best < best) {
+            best = ms_best;
+            bnb = nb;
+        }
+    }
+    s->tune_count = k;
+    s->nb = bnb;
+    s->gemm = (bnb % 64 == 0 && tc_gemm_supported()) ? (s->cfg.trailing_gemm ? s->cfg.trailing_gemm : 2) : 1;
+    lu_work_carve(s->luw.pnl, n, s->nb, false, &s->luw);
+    return NL_OK;
 }
 
 static bool valid_mode(int m) { return m == NL_FP64LU || m == NL_IR16 || m == NL_GMRESIR16 || m == NL_IR16_GMRES; }
@@ -374,7 +422,8 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     if (cfg) d = *cfg;
     if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 || d.lu_path < 0 ||
         d.lu_path > 1 ||
-        d.newton_maxit >= NL_MAX_HIST || (d.lu_nb && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16))) {
+        d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
+        d.lu_nb < -1) {
         set_error("nl_create: invalid configuration");
         return NL_EINVAL;
     }
@@ -387,7 +436,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->N = (int)N;
     s->c = c;
     s->cfg = d;
-    s->nb = d.lu_nb ? d.lu_nb : 128;
+    s->nb = d.lu_nb > 0 ? d.lu_nb : 128;  // the autotuner (lu_nb = -1) may lower it below; buffers fit 128
     s->gemm = d.trailing_gemm ? d.trailing_gemm : 2;
     if (s->gemm == 2 && (!tc_gemm_supported() || s->nb % 64)) s->gemm = 1;
     s->ld = round_up(N, 64);
@@ -444,6 +493,13 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         return NL_ECUDA;
     }
     memset(&s->stats, 0, sizeof(s->stats));
+    if (d.lu_nb < 0) {
+        nl_status ts = autotune_lu(s);
+        if (ts != NL_OK) {
+            nl_destroy(s);
+            return ts;
+        }
+    }
     *out = s;
     return NL_OK;
 }
@@ -558,6 +614,11 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
     memset(&S, 0, sizeof(S));
     S.mode = mode;
     S.lu_nb = (mode == NL_FP64LU) ? 64 : s->nb;
+    S.lu_tune_count = s->tune_count;
+    for (int k = 0; k < 4; ++k) {
+        S.lu_tune_nb[k] = s->tune_nb[k];
+        S.lu_tune_ms[k] = s->tune_ms[k];
+    }
     int launches = 0;
     Host H{s->pin, st, &launches};
     if (mode == NL_FP64LU) NL_TRY(ensure_fp64(s));

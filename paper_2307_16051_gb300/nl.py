@@ -44,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("lin_relres", ctypes.c_double * MAX_HIST), ("t_total_ms", ctypes.c_double),
                 ("t_f_ms", ctypes.c_double), ("t_jac_ms", ctypes.c_double), ("t_lu_ms", ctypes.c_double),
                 ("t_lin_ms", ctypes.c_double), ("gpu_launches", ctypes.c_int), ("lu_pivoted", ctypes.c_int),
-                ("reserved", ctypes.c_int * 14)]
+                ("lu_tune_count", ctypes.c_int), ("lu_tune_nb", ctypes.c_int * 4), ("lu_tune_ms", ctypes.c_float * 4),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class BatchInfo(ctypes.Structure):
@@ -249,7 +250,8 @@ class Solver:
                     hist=list(s.hist[: n + 1]), lin_iters=list(s.lin_iters[:n]), lin_outer=list(s.lin_outer[:n]),
                     lin_failed=list(s.lin_failed[:n]), lin_relres=list(s.lin_relres[:n]),
                     t_total_ms=s.t_total_ms, t_f_ms=s.t_f_ms, t_jac_ms=s.t_jac_ms, t_lu_ms=s.t_lu_ms,
-                    t_lin_ms=s.t_lin_ms, gpu_launches=s.gpu_launches, lu_pivoted=s.lu_pivoted)
+                    t_lin_ms=s.t_lin_ms, gpu_launches=s.gpu_launches, lu_pivoted=s.lu_pivoted,
+                    lu_tune=[(s.lu_tune_nb[k], s.lu_tune_ms[k]) for k in range(s.lu_tune_count)])
 
     def device_bytes(self) -> int:
         return lib().nl_device_bytes(self._h)

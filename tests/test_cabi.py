@@ -100,3 +100,6 @@ def test_server_no_device_is_an_error():
     assert nl.footprint_bytes(1024) > 6 * 1024 * 1024
     assert nl.footprint_bytes(1024, "FP64LU") > nl.footprint_bytes(1024) + 8 * 1024 * 1024
     assert nl.lib().nl_footprint_bytes(0, 1, None) == -1
+    # the autotuning setting (-1) sizes the handle for the largest panel width
+    for N in (1, 700, 4096):
+        assert nl.footprint_bytes(N, lu_nb=-1) == nl.footprint_bytes(N, lu_nb=128) >= nl.footprint_bytes(N, lu_nb=32)

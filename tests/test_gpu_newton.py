@@ -181,3 +181,37 @@ def test_large_n32768_gmresir():
     assert np.linalg.norm(F) <= 1e-10 * st["fnorm0"] * 1.0001
     m = c / (2 * N) * x.sum()
     assert abs(m - (1 - math.sqrt(1 - c))) <= 1e-10
+
+
+def test_autotuned_lu_nb_is_used_and_matches_oracle():
+    """lu_nb = -1: the handle times the factorisation for several outer
+    blocks, keeps the fastest, and the solve equals the oracle run with that
+    block (it is also the binary16 rounding period)."""
+    N, c = 700, 0.99
+    with nl.Solver(N, c, lu_nb=-1) as s:
+        x, status = s.solve(tol=1e-10, mode="GMRESIR16")
+        st = s.stats()
+    assert status == nl.NL_OK and len(st["lu_tune"]) >= 3
+    assert st["lu_nb"] == min(st["lu_tune"], key=lambda t: t[1])[0]
+    xo, ro = O.newton(N, c, "GMRESIR16", tol=1e-10, lu_nb=st["lu_nb"])
+    check_counts(st, ro, "GMRESIR16")
+    assert rel_inf(x, xo) <= 1e-10
+
+
+def test_large_single_solve_n32768():
+    """The large configuration (N = 32768, c = .99, GMRES-IR16, autotuned
+    panel width): beyond the oracle's reach, so checked by what holds at any
+    size: the oracle's double-precision F at the GPU's x meets the Newton
+    tolerance, and the exact discrete moment identity holds."""
+    N, c = 32768, 0.99
+    with nl.Solver(N, c, lu_nb=-1) as s:
+        x, status = s.solve(tol=1e-10, mode="GMRESIR16")
+        st = s.stats()
+    assert status == nl.NL_OK and st["lu_pivoted"] == 0
+    f0 = np.linalg.norm(O.F(N, c, np.ones(N)))
+    f = np.linalg.norm(O.F(N, c, x))
+    assert f <= 1e-10 * f0
+    m = c / (2 * N) * np.sum(x)
+    assert abs(m - (1 - math.sqrt(1 - c))) <= 1e-9 / math.sqrt(1 - c)
+    # the Newton count of the mesh-independent iteration (Section 3, Table 2's F64 column to 1e-10)
+    assert st["newton_iters"] == 6
