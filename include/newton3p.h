@@ -391,6 +391,13 @@ nl_status nl_lusolve64(int64_t N, const double* LU, int64_t ld, const int32_t* i
 nl_status nl_k_gemv_residual(int64_t N, const float* A, int64_t ld, const float* b, const float* u, float* r,
                              double* rnorm_dev, void* stream);
 
+/* out[i] = fl16(fl32(a[i] / b[i])) (device, n floats each): the multiplier
+ * rounding l = fl16(a / u) of the half-precision LU (Section 2), as the LU
+ * kernels compute it (a correctly rounded reciprocal, a product, and the IEEE
+ * division wherever the product lies within a few single-precision units of a
+ * binary16 rounding boundary).  For tests of that arithmetic. */
+nl_status nl_k_div_round16(int64_t n, const float* a, const float* b, float* out, void* stream);
+
 /* Trailing update of the half-precision LU:  C <- fl16(C - A B) with A M x K,
  * B K x Nc, C M x Nc binary16 row-major (lda, ldb, ldc), products accumulated
  * in single.  gemm: 1 SIMT (sequential fused multiply-adds over k),

@@ -76,6 +76,26 @@ constexpr long long kSpinLimit = 1LL << 24;
 
 __device__ __forceinline__ float round_h(float v) { return __half2float(__float2half_rn(v)); }
 
+// fl16(fl32(a / b)) given rb = __frcp_rn(b), without a division in the
+// common case.  q = fl32(a rb) is within about 2^-23 |a/b| of a/b, hence so is
+// fl32(a/b) (to 1.5 2^-23).  Rounding to binary16 is monotonic, so when the
+// two ends of [q (1 - 2^-20), q (1 + 2^-20)] round to the same binary16
+// value, every number in between does, fl32(a/b) included, and that value is
+// the answer.  Otherwise (a / b within a few single-precision units of a
+// binary16 rounding boundary, about one case in a thousand) the quotient is
+// formed by the IEEE division.  Exact for all inputs; NaN and infinity
+// propagate as with the division.
+__device__ __forceinline__ float div_round_h(float a, float b, float rb)
+{
+    const float q = __fmul_rn(a, rb);
+    const __half h = __float2half_rn(q);
+    const __half lo = __float2half_rn(__fmul_rn(q, 1.0f - 0x1p-20f));
+    const __half hi = __float2half_rn(__fmul_rn(q, 1.0f + 0x1p-20f));
+    if (__half_as_ushort(lo) == __half_as_ushort(hi) && __half_as_ushort(h) == __half_as_ushort(lo))
+        return __half2float(h);
+    return round_h(__fdiv_rn(a, b));
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {

@@ -813,42 +813,66 @@ __global__ void __launch_bounds__(kOffThreads) k_offdiag(S* __restrict__ A, int6
 constexpr int kStagePivOff = 2 * 128 * 128;
 
 // k_diag_lu16: the diagonal block [K, K+w)^2 (w <= 128), one CTA of 512
-// threads.  Warp v owns columns 8v..8v+7 and lane l rows 4l..4l+3, so every
-// thread keeps a 4 x 8 tile in registers.  Step t:
-//  * warp t/8 owns column t: each lane checks |a_it| <= |a_tt| for its rows
-//    below t (partial pivoting keeps the diagonal; ties go to the diagonal,
-//    which comes first) and forms l_it = fl16(a_it / fl16(a_tt));
-//  * lane t/4 of every warp owns a piece of row t and rounds it to binary16;
-//  * both are published through shared memory (double-buffered, so one
-//    barrier per step suffices), and every tile takes the rank-1 update.
-// Finished entries go to result buffers in shared memory as they are formed
-// (U row-major, L transposed, so that both writes are contiguous); the
-// register copies of finished entries are no longer read, so the update
-// needs no masking.
+// threads, as a column pipeline.  Warp v owns columns 8v..8v+7 and lane l rows
+// 4l..4l+3, so every thread keeps a 4 x 8 tile in registers.  Warp v first
+// applies, in order k = 0, 1, ..., 8v-1, the updates of the earlier warps'
+// columns as each column's multipliers appear in shared memory (a ready flag
+// per column), then factors its own eight columns: for column t the lanes
+// check |a_it| <= |a_tt| for their rows below t (partial pivoting keeps the
+// diagonal; ties go to the diagonal, which comes first), form
+// l_it = fl16(a_it / fl16(a_tt)), publish them, and update the warp's later
+// columns.  Row k's entries of a warp's columns are rounded to binary16 (U)
+// by that warp when it applies update k.  Every entry takes its updates in
+// increasing k, one binary32 fused multiply-add each, exactly as in
+// right-looking elimination; only the warps' schedule is pipelined, so the
+// critical path is one division and one hand-off per column instead of a
+// block-wide barrier per step.  Finished entries stay in the registers (U on
+// and above the diagonal, L below).  Every wait is bounded: a wait that gives
+// up marks the fast path failed, so the host refactors with interchanges.
+// (The hand-offs use CTA-scope release/acquire on the flags; a fence per
+// column and a clock-based wait cost 1.7x in time.)
 constexpr int kD16Threads = 512;
-constexpr int kFwLd = 136;  // stride (halves) of the result buffers; rows stay 16-byte aligned
-constexpr size_t kDiag16Smem = 2 * 128 * kFwLd * sizeof(__half);
+constexpr size_t kDiag16Smem = 128 * 128 * sizeof(float);
+constexpr int kDiagSpinLimit = 1 << 22;  // polls of a ready flag before a wait gives up
+
+// Column hand-off inside the CTA: the producer's lane 0 publishes a column
+// with a CTA-scope release store of its ready flag (shared memory); a
+// consumer's lane 0 polls it with CTA-scope acquire loads, at most
+// kDiagSpinLimit times.  (This exact loop shape matters: an equivalent
+// for-loop with the bound test first compiled to a 2.6x slower kernel.)
+__device__ __forceinline__ bool diag_wait(const int* f, int* failp)
+{
+    int it = 0;
+    while (true) {
+        int v;
+        asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(f)) : "memory");
+        if (v) return true;
+        if (*(volatile const int*)failp) return false;
+        if (++it > kDiagSpinLimit) { *(volatile int*)failp = 1; return false; }
+    }
+}
 
 __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t lda, int K, int w,
-                                                             int* __restrict__ ipiv, int* __restrict__ flag,
-                                                             float* __restrict__ stage)
+                                               int* __restrict__ ipiv, int* __restrict__ flag,
+                                               float* __restrict__ stage)
 {
     if (*(volatile int*)flag) return;
-    __shared__ __align__(16) float urow[2][128];
-    __shared__ __align__(16) float lcol[2][128];
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __half* fu = reinterpret_cast<__half*>(dsm);  // fu[i][j] = u_ij, j >= i
-    __half* fl = fu + 128 * kFwLd;                // fl[j][i] = l_ij, i > j
+    extern __shared__ __align__(16) float lsh[];  // lsh[t * 128 + i] = l_it (0 for i <= t)
+    __shared__ int rdy[128];
+    __shared__ int fail;
+    __shared__ float pvs[128];  // unrounded pivots, copied to the stage at the end
     const int tid = threadIdx.x, lane = tid & 31, v = tid >> 5;
-    const int r0 = 4 * lane, c0 = 8 * v;
+    const int r0 = 4 * lane, C0 = 8 * v;
     const int wp = (w + 31) & ~31;
-    const bool vec = (w % 32 == 0) && ((((uintptr_t)(A + (int64_t)K * lda + K)) & 15) == 0) && (lda % 8 == 0);
+    const bool vec = (w % 8 == 0) && ((((uintptr_t)(A + (int64_t)K * lda + K)) & 15) == 0) && (lda % 8 == 0);
+    if (tid < 128) rdy[tid] = 0;
+    if (tid == 0) fail = 0;
     float a[4][8];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int i = r0 + r;
-        const __half* src = A + (int64_t)(K + min(i, w - 1)) * lda + K + c0;
-        if (vec && i < w && c0 < w) {
+        const __half* src = A + (int64_t)(K + min(i, w - 1)) * lda + K + C0;
+        if (vec && i < w && C0 + 8 <= w) {
             const uint4 raw = *reinterpret_cast<const uint4*>(src);
             const __half* e = reinterpret_cast<const __half*>(&raw);
 #pragma unroll
@@ -856,104 +880,144 @@ __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t l
         } else {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
-                const int j = c0 + c;
+                const int j = C0 + c;
                 a[r][c] = (i < w && j < w) ? __half2float(src[c]) : ((i == j) ? 1.0f : 0.0f);
             }
         }
     }
+    __syncthreads();
     float* PV = stage + kStagePivOff;
-    bool bad = false;
-    for (int s = 0; s < wp / 8; ++s) {
+    bool bad = false, alive = true;
+    if (C0 < w) {
+        // the earlier warps' columns, in order
+        for (int k0 = 0; k0 < C0 && alive; k0 += 4) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int t = 8 * s + k, b = k & 1;
-            if (v == s) {
-                // column t: the pivot a_tt sits in lane t/4, register row t%4
-                const float p = __shfl_sync(0xffffffffu, a[k & 3][k], t >> 2);
-                const float ut = round_h(p);
-                float l[4];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    l[r] = 0.0f;
-                    if (r0 + r > t) {
-                        if (!(fabsf(a[r][k]) <= fabsf(p))) bad = true;
-                        l[r] = round_h(a[r][k] / ut);
-                    }
+            for (int kk = 0; kk < 4; ++kk) {
+                const int k = k0 + kk;  // row k is register row kk of lane k / 4
+                int ok = 1;
+                if (lane == 0) ok = diag_wait(&rdy[k], &fail);
+                __syncwarp();
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (!ok) {
+                    alive = false;
+                    break;
                 }
-                *reinterpret_cast<float4*>(&lcol[b][r0]) = make_float4(l[0], l[1], l[2], l[3]);
-                *reinterpret_cast<__half2*>(&fl[t * kFwLd + r0]) = __floats2half2_rn(l[0], l[1]);
-                *reinterpret_cast<__half2*>(&fl[t * kFwLd + r0 + 2]) = __floats2half2_rn(l[2], l[3]);
-                if (lane == (t >> 2)) {
-                    PV[t] = p;
-                    if (!(ut != 0.0f)) bad = true;  // zero pivot: info is the interchanging path's
-                }
-            }
-            if (lane == (t >> 2) && v >= s) {
-                // row t, columns 8v..8v+7 (those left of t are multipliers, already recorded)
+                const float4 l4 = *reinterpret_cast<const float4*>(&lsh[k * 128 + r0]);
+                const float lk[4] = {l4.x, l4.y, l4.z, l4.w};
                 float u[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) u[c] = round_h(a[k & 3][c]);
-                *reinterpret_cast<float4*>(&urow[b][c0]) = make_float4(u[0], u[1], u[2], u[3]);
-                *reinterpret_cast<float4*>(&urow[b][c0 + 4]) = make_float4(u[4], u[5], u[6], u[7]);
-                __align__(16) __half h[8];
+                for (int c = 0; c < 8; ++c) u[c] = round_h(__shfl_sync(0xffffffffu, a[kk][c], k >> 2));
+                if (lane == (k >> 2)) {
 #pragma unroll
-                for (int c = 0; c < 8; ++c) h[c] = __float2half_rn(u[c]);
-                *reinterpret_cast<uint4*>(&fu[t * kFwLd + c0]) = *reinterpret_cast<const uint4*>(h);
-            }
-            __syncthreads();
-            if (v >= s) {
-                const float4 l4 = *reinterpret_cast<const float4*>(&lcol[b][r0]);
-                const float4 ua = *reinterpret_cast<const float4*>(&urow[b][c0]);
-                const float4 ub = *reinterpret_cast<const float4*>(&urow[b][c0 + 4]);
-                const float l[4] = {l4.x, l4.y, l4.z, l4.w};
-                const float u[8] = {ua.x, ua.y, ua.z, ua.w, ub.x, ub.y, ub.z, ub.w};
+                    for (int c = 0; c < 8; ++c) a[kk][c] = u[c];
+                }
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
+                    if (r0 + r > k) {
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-l[r], u[c], a[r][c]);
+                        for (int c = 0; c < 8; ++c) a[r][c] = fmaf(-lk[r], u[c], a[r][c]);
+                    }
+            }
+        }
+        // this warp's own columns
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const int t = C0 + kk;
+            if (alive && t < w) {
+                const int src = t >> 2;  // row t is register row kk & 3 of lane t / 4
+                const float p = __shfl_sync(0xffffffffu, a[kk & 3][kk], src);
+                const float ut = round_h(p);
+                const float rut = __frcp_rn(ut);
+                float lv[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    lv[r] = 0.0f;
+                    if (r0 + r > t) {
+                        if (!(fabsf(a[r][kk]) <= fabsf(p))) bad = true;
+                        lv[r] = div_round_h(a[r][kk], ut, rut);
+                        a[r][kk] = lv[r];
+                    }
+                }
+                if (lane == src) {
+                    a[kk & 3][kk] = ut;
+                    pvs[t] = p;
+                    if (!(ut != 0.0f)) bad = true;  // zero pivot: info is the interchanging path's
+                }
+                *reinterpret_cast<float4*>(&lsh[t * 128 + r0]) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+                __syncwarp();
+                if (lane == 0) asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" :: "r"((unsigned)__cvta_generic_to_shared(&rdy[t])), "r"(1) : "memory");
+                float u[8];
+#pragma unroll
+                for (int c = kk + 1; c < 8; ++c) u[c] = round_h(__shfl_sync(0xffffffffu, a[kk & 3][c], src));
+                if (lane == src) {
+#pragma unroll
+                    for (int c = kk + 1; c < 8; ++c) a[kk & 3][c] = u[c];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r0 + r > t) {
+#pragma unroll
+                        for (int c = kk + 1; c < 8; ++c) a[r][c] = fmaf(-lv[r], u[c], a[r][c]);
+                    }
             }
         }
     }
+    if (!alive) bad = true;
     if (__syncthreads_or(bad)) {
         if (tid == 0) atomicOr(flag, 1);
         return;
     }
-    // the factors (binary16) to A with coalesced stores, U11 and L11^T to the stage
-    if (vec) {
-        const int vpr = w / 8;
-        for (int q = tid; q < w * vpr; q += kD16Threads) {
-            const int r = q / vpr, c = (q - r * vpr) * 8;
-            __align__(16) __half h[8];
+    // the factors (binary16) to A, U11 and L11^T (binary32, identity / zero padded to wp) to the stage
 #pragma unroll
-            for (int e = 0; e < 8; ++e) h[e] = (c + e >= r) ? fu[r * kFwLd + c + e] : fl[(c + e) * kFwLd + r];
-            *reinterpret_cast<uint4*>(A + (int64_t)(K + r) * lda + K + c) = *reinterpret_cast<const uint4*>(h);
-        }
-    } else {
-        for (int q = tid; q < w * w; q += kD16Threads) {
-            const int r = q / w, c = q - r * w;
-            A[(int64_t)(K + r) * lda + K + c] = (c >= r) ? fu[r * kFwLd + c] : fl[c * kFwLd + r];
-        }
-    }
-    {
-        const int q4 = wp / 4;
-        float4* SU = reinterpret_cast<float4*>(stage);
-        float4* SL = reinterpret_cast<float4*>(stage + wp * wp);
-        for (int q = tid; q < wp * q4; q += kD16Threads) {
-            const int r = q / q4, c = (q - r * q4) * 4;
-            float u[4], l[4];
+    for (int r = 0; r < 4; ++r) {
+        const int i = r0 + r;
+        if (i < w && C0 < w) {
+            __half* dst = A + (int64_t)(K + i) * lda + K + C0;
+            if (vec && C0 + 8 <= w) {
+                __align__(16) __half h[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int cc = c + e;
-                const bool in = r < w && cc < w;
-                u[e] = in ? ((cc >= r) ? __half2float(fu[r * kFwLd + cc]) : 0.0f) : ((r == cc) ? 1.0f : 0.0f);
-                l[e] = (in && cc > r) ? __half2float(fl[r * kFwLd + cc]) : 0.0f;
+                for (int c = 0; c < 8; ++c) h[c] = __float2half_rn(a[r][c]);
+                *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (C0 + c < w) dst[c] = __float2half_rn(a[r][c]);
             }
-            SU[q] = make_float4(u[0], u[1], u[2], u[3]);
-            SL[q] = make_float4(l[0], l[1], l[2], l[3]);
         }
     }
-    if (tid < w) ipiv[K + tid] = K + tid;
+    float* SU = stage;
+    float* SL = stage + wp * wp;
+    if (C0 < wp) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int i = r0 + r;
+            if (i >= wp) continue;
+            float uu[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int j = C0 + c;
+                uu[c] = (i < w && j < w) ? ((j >= i) ? a[r][c] : 0.0f) : ((i == j) ? 1.0f : 0.0f);
+            }
+            *reinterpret_cast<float4*>(&SU[i * wp + C0]) = make_float4(uu[0], uu[1], uu[2], uu[3]);
+            *reinterpret_cast<float4*>(&SU[i * wp + C0 + 4]) = make_float4(uu[4], uu[5], uu[6], uu[7]);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int j = C0 + c;
+            float ll[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = r0 + r;
+                ll[r] = (i < w && j < w && i > j) ? a[r][c] : 0.0f;
+            }
+            if (r0 < wp) *reinterpret_cast<float4*>(&SL[j * wp + r0]) = make_float4(ll[0], ll[1], ll[2], ll[3]);
+        }
+    }
+    if (tid < w) { ipiv[K + tid] = K + tid; PV[tid] = pvs[tid]; }
 }
+
+
+
 
 __global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict__ A, int64_t lda, int K, int w,
                                                              int* __restrict__ ipiv, int* __restrict__ flag,
@@ -975,7 +1039,7 @@ __global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict
 constexpr int kO16Threads = 256;
 constexpr int kO16Rows = 64;  // rows or columns per CTA (32 groups x 2)
 
-size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + wp) * sizeof(float); }
+size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + 2 * wp) * sizeof(float); }
 
 __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t lda, int K, int w, int N,
                                                            int nrow_blocks, __half* __restrict__ Ut, int ldut,
@@ -987,6 +1051,7 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
     float* D = osm;                  // U11 (row role) or L11^T (column role)
     float* X = D + wp * wp;          // [t][2 grp + r]: multipliers / U entries of earlier chunks
     float* pv = X + wp * kO16Rows;   // |a_tt|, unrounded
+    float* rinv = pv + wp;           // 1 / u_tt, correctly rounded (row role)
     const int tid = threadIdx.x, grp = tid >> 3, g = tid & 7;
     const unsigned gmask = 0xffu << ((tid & 31) & ~7);
     const bool row_role = (int)bid < nrow_blocks;
@@ -998,6 +1063,8 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
         for (int v = tid; v < nv; v += kO16Threads) d4[v] = s4[v];
         if (tid < wp) pv[tid] = fabsf(stage[kStagePivOff + tid]);
     }
+    __syncthreads();
+    if (row_role && tid < wp) rinv[tid] = __frcp_rn(D[tid * wp + tid]);
     __syncthreads();
     const int base = K + w + (row_role ? (int)bid : (int)bid - nrow_blocks) * kO16Rows + 2 * grp;
     const bool lv0 = base < N, lv1 = base + 1 < N;
@@ -1043,11 +1110,11 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
                 const int t = 32 * c + tt;
                 float l0 = 0.0f, l1 = 0.0f;
                 if (g == tt / 4) {
-                    const float utt = D[t * wp + t], p = pv[t];
+                    const float utt = D[t * wp + t], p = pv[t], ru = rinv[t];
                     const float a0 = x0[tt % 4], a1 = x1[tt % 4];
                     if (t < w && ((lv0 && !(fabsf(a0) <= p)) || (lv1 && !(fabsf(a1) <= p)))) bad = true;
-                    l0 = round_h(a0 / utt);
-                    l1 = round_h(a1 / utt);
+                    l0 = div_round_h(a0, utt, ru);
+                    l1 = div_round_h(a1, utt, ru);
                     x0[tt % 4] = l0;
                     x1[tt % 4] = l1;
                     Xg[t * 32] = make_float2(l0, l1);
@@ -1694,4 +1761,25 @@ nl_status lu_grouped_factor(const GroupPlan& plan, const GInst* dev_inst, cudaSt
     return NL_OK;
 }
 
+// The multiplier rounding of the binary16 LU, elementwise (for tests).
+__global__ void k_div_round16(int64_t n, const float* __restrict__ a, const float* __restrict__ b,
+                              float* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = div_round_h(a[i], b[i], __frcp_rn(b[i]));
+}
+
 }  // namespace nl
+
+extern "C" nl_status nl_k_div_round16(int64_t n, const float* a, const float* b, float* out, void* stream)
+{
+    using namespace nl;
+    if (n < 0 || (n > 0 && (!a || !b || !out))) {
+        set_error("nl_k_div_round16: bad argument");
+        return NL_EINVAL;
+    }
+    if (n == 0) return NL_OK;
+    k_div_round16<<<(unsigned)cdiv(n, 256), 256, 0, (cudaStream_t)stream>>>(n, a, b, out);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}

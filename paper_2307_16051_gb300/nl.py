@@ -106,6 +106,7 @@ SIGNATURES = {
     "nl_lusolve64": (_int, [_i64, _P, _i64, _P, _P, _P]),
     "nl_k_gemv_residual": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
     "nl_k_gemv_residual_noalloc": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
+    "nl_k_div_round16": (_int, [_i64, _P, _P, _P, _P]),
     "nl_k_gemm16_update": (_int, [_i64, _i64, _i64, _P, _i64, _P, _i64, _P, _i64, _int, _P]),
     "nl_linsolve16": (_int, [_i64, _P, _i64, _P, _i64, _P, _P, _P, _dbl, _int, _int, _int, _dbl, _int,
                              ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double), _P]),
@@ -486,3 +487,8 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+def k_div_round16(n, a, b, out, stream=None):
+    """out = fl16(fl32(a / b)) as the LU's multiplier rounding computes it."""
+    return check(lib().nl_k_div_round16(int(n), _ptr(a), _ptr(b), _ptr(out), _stream(stream)))

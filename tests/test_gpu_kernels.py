@@ -334,3 +334,33 @@ def test_linsolve16_matches_oracle(solver, N, c):
     got = ud.cpu().numpy()[:N].astype(np.float64)
     assert np.linalg.norm(got - uo) <= 10 * eta * np.linalg.norm(uo) * np.linalg.cond(J32.astype(np.float64))
     assert st["relres"] <= eta
+
+
+def test_multiplier_rounding_exact_vs_ieee():
+    """The LU forms l = fl16(a / u) from a correctly rounded reciprocal; it
+    must equal fl16 of the IEEE single-precision quotient for every input,
+    including quotients within a few single-precision units of a binary16
+    rounding boundary (the cases its exactness test sends to the division)."""
+    g = np.random.default_rng(12)
+    n = 1 << 20
+    # divisors: binary16 values (the rounded pivots), both signs, normal and subnormal
+    u16 = g.integers(1, 0x7C00, size=n).astype(np.uint16) | (g.integers(0, 2, size=n).astype(np.uint16) << 15)
+    u = u16.view(np.float16).astype(np.float32)
+    a = (g.uniform(-1.0, 1.0, size=n) * np.abs(u)).astype(np.float32)
+    # a quarter of the numerators aimed at binary16 midpoints: a ~ m u, nudged by a few units
+    k = n // 4
+    h = g.integers(0x0001, 0x7BFF, size=k).astype(np.uint16)
+    lo = h.view(np.float16).astype(np.float64)
+    hi = (h + 1).view(np.float16).astype(np.float64)
+    m = (lo + hi) / 2.0 * np.where(g.integers(0, 2, size=k) == 1, 1.0, -1.0)
+    aa = (m * u[:k].astype(np.float64)).astype(np.float32)
+    nudge = g.integers(-6, 7, size=k)
+    a[:k] = aa + nudge.astype(np.float32) * np.spacing(aa)
+    a[:16] = np.array([0.0, -0.0, 1.0, -1.0] * 4, dtype=np.float32)
+    ref32 = (a / u).astype(np.float32)  # IEEE single division (numpy)
+    ref = O.f16_bits_from_f32(ref32)
+    out = torch.empty(n, device=dev(), dtype=torch.float32)
+    nl.k_div_round16(n, T(a), T(u), out)
+    got = O.f16_bits_from_f32(out.cpu().numpy())
+    bad = np.nonzero(got != ref)[0]
+    assert bad.size == 0, (bad[:5], a[bad[:5]], u[bad[:5]])
