@@ -2,6 +2,8 @@
 GPU and print the solver statistics as JSON.
 
     python -m paper_2307_16051_gb300 --N 4096 --c 0.99 --mode GMRESIR16 --repeat 2
+    python -m paper_2307_16051_gb300 --batch 512 --repeat 2          # the batched workload
+    python -m paper_2307_16051_gb300 --serve-seconds 2               # the serving trace
 """
 import argparse
 import json
@@ -13,15 +15,40 @@ def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--N", type=int, default=4096)
     ap.add_argument("--c", type=float, default=0.99)
-    ap.add_argument("--mode", default="GMRESIR16", choices=sorted(nl.MODES))
+    ap.add_argument("--mode", default=None, choices=sorted(nl.MODES))
     ap.add_argument("--tol", type=float, default=1e-10)
     ap.add_argument("--repeat", type=int, default=1, help="solves on the same handle (the last one is reported)")
     ap.add_argument("--eta", type=float, default=1e-4)
     ap.add_argument("--lu-nb", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=0,
+                    help="solve the first BATCH instances of the batched workload (N log-uniform in [64, 2048], "
+                         "c uniform in [0.1, 0.999], seed 230716051) together")
+    ap.add_argument("--serve-seconds", type=float, default=0.0,
+                    help="replay the first SECONDS of the serving trace (Poisson 200/s) through the request loop")
     args = ap.parse_args()
+    if args.batch > 0:
+        from . import workloads as W
+        inst = W.batch_instances()[: args.batch]
+        with nl.Batch([n for n, _ in inst], [c for _, c in inst], eta_j=args.eta, lu_nb=args.lu_nb) as B:
+            for _ in range(max(1, args.repeat)):
+                xs, status = B.solve(tol=args.tol, mode=args.mode or "IR16_GMRES")
+            info = B.info()
+        info["status_name"] = nl.STATUS_NAMES[status]
+        print(json.dumps(info))
+        return
+    if args.serve_seconds > 0:
+        from . import workloads as W
+        trace = W.serving_trace(duration_s=args.serve_seconds)
+        with nl.Server(mode=args.mode or "IR16_GMRES", tol=args.tol) as S:
+            for t, N, c in trace:
+                S.submit(N, c, arrival_s=t)
+            S.start()
+            S.drain(600.0)
+            print(json.dumps(S.info()))
+        return
     with nl.Solver(args.N, args.c, eta_j=args.eta, lu_nb=args.lu_nb) as s:
         for _ in range(max(1, args.repeat)):
-            x, status = s.solve(tol=args.tol, mode=args.mode)
+            x, status = s.solve(tol=args.tol, mode=args.mode or "GMRESIR16")
         st = s.stats()
     st["status_name"] = nl.STATUS_NAMES[status]
     st["x_min"], st["x_max"] = float(x.min()), float(x.max())
