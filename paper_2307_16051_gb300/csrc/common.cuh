@@ -76,24 +76,54 @@ constexpr long long kSpinLimit = 1LL << 24;
 
 __device__ __forceinline__ float round_h(float v) { return __half2float(__float2half_rn(v)); }
 
-// fl16(fl32(a / b)) given rb = __frcp_rn(b), without a division in the
-// common case.  q = fl32(a rb) is within about 2^-23 |a/b| of a/b, hence so is
-// fl32(a/b) (to 1.5 2^-23).  Rounding to binary16 is monotonic, so when the
-// two ends of [q (1 - 2^-20), q (1 + 2^-20)] round to the same binary16
-// value, every number in between does, fl32(a/b) included, and that value is
-// the answer.  Otherwise (a / b within a few single-precision units of a
-// binary16 rounding boundary, about one case in a thousand) the quotient is
-// formed by the IEEE division.  Exact for all inputs; NaN and infinity
-// propagate as with the division.
+// fl16(fl32(a / b)) for a binary16 value b != 0 (held in a float) and
+// rb = __frcp_rn(b), with no division and no branch.
+//   q = fl32(a rb) is within 2^-22.9 |a/b| of a/b, hence so is fl32(a/b).
+//   h = fl16(q).  Let m be the binary16 rounding boundary (the midpoint of
+//   two adjacent binary16 values lo < hi) next to q on the side of q away
+//   from h.  If |q - m| > 2^-21 |q|, no boundary separates q from fl32(a/b)
+//   and h is the answer.  Otherwise the answer is decided exactly:
+//   e = |a| - m |b| is exact (m |b| has at most 23 significant bits, and
+//   Sterbenz's lemma applies), and fl32(|a/b|) > m iff e > up |b| / 2,
+//   < m iff e < -dn |b| / 2 (up, dn: the single-precision spacings above and
+//   below m; m has a zero last bit, so single-precision ties go to m), and
+//   = m otherwise, when binary16 rounding of the tie picks the even one of
+//   lo and hi.  The sign is that of q.  NaN and infinity follow q.
 __device__ __forceinline__ float div_round_h(float a, float b, float rb)
+{
+    const float q = __fmul_rn(a, rb);
+    const __half h = __float2half_rn(q);
+    const float aq = fabsf(q);
+    const unsigned hb = __half_as_ushort(h) & 0x7fffu;
+    const float ah = __half2float(__ushort_as_half((unsigned short)hb));
+    const unsigned nb = (aq > ah) ? hb + 1u : (hb ? hb - 1u : 0u);
+    const float nf = __half2float(__ushort_as_half((unsigned short)nb));
+    const float m = 0.5f * (ah + nf);
+    const bool near = (aq != 0.0f) && (fabsf(aq - m) <= aq * 0x1p-21f);
+    const float ab = fabsf(b);
+    const float e = __fmaf_rn(-m, ab, fabsf(a));
+    const unsigned mu = __float_as_uint(m);
+    const float up = __fsub_rn(__uint_as_float(mu + 1u), m);
+    const float dn = __fsub_rn(m, __uint_as_float(mu - 1u));
+    const float sup = 0.5f * up * ab, sdn = 0.5f * dn * ab;
+    const unsigned lob = min(hb, nb);
+    const float lo = fminf(ah, nf), hi = fmaxf(ah, nf);
+    const float exact = (e > sup) ? hi : ((-e > sdn) ? lo : ((lob & 1u) ? hi : lo));
+    return copysignf(near ? exact : ah, q);
+}
+
+// The common case of div_round_h alone: fl16(fl32(a rb)), and in *unsure
+// whether a binary16 rounding boundary lies within 2^-20 |q| of q (then the
+// caller must use div_round_h; when *unsure is false the result is exact, by
+// the same argument).
+__device__ __forceinline__ float div_round_h_fast(float a, float rb, bool* unsure)
 {
     const float q = __fmul_rn(a, rb);
     const __half h = __float2half_rn(q);
     const __half lo = __float2half_rn(__fmul_rn(q, 1.0f - 0x1p-20f));
     const __half hi = __float2half_rn(__fmul_rn(q, 1.0f + 0x1p-20f));
-    if (__half_as_ushort(lo) == __half_as_ushort(hi) && __half_as_ushort(h) == __half_as_ushort(lo))
-        return __half2float(h);
-    return round_h(__fdiv_rn(a, b));
+    *unsure = !(__half_as_ushort(lo) == __half_as_ushort(hi) && __half_as_ushort(h) == __half_as_ushort(lo));
+    return __half2float(h);
 }
 
 template <typename T>

@@ -929,13 +929,24 @@ __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t l
                 const float ut = round_h(p);
                 const float rut = __frcp_rn(ut);
                 float lv[4];
+                bool unsure = false;
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    lv[r] = 0.0f;
+                    bool u = false;
+                    lv[r] = div_round_h_fast(a[r][kk], rut, &u);
+                    unsure |= u && (r0 + r > t);
+                }
+                if (__any_sync(0xffffffffu, unsure)) {  // rare: decide the boundary cases exactly
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) lv[r] = div_round_h(a[r][kk], ut, rut);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
                     if (r0 + r > t) {
                         if (!(fabsf(a[r][kk]) <= fabsf(p))) bad = true;
-                        lv[r] = div_round_h(a[r][kk], ut, rut);
                         a[r][kk] = lv[r];
+                    } else {
+                        lv[r] = 0.0f;
                     }
                 }
                 if (lane == src) {
@@ -1027,34 +1038,37 @@ __global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict
 }
 
 // k_offdiag16: L21 = A21 U11^{-1} (row role) and U12 = L11^{-1} A12 (column
-// role) for a panel of width w.  256 threads = 32 groups of eight lanes; a
-// group takes two rows (or two columns), and lane g holds entries 4g..4g+3 of
-// each 32-wide chunk of both.  Each chunk is first updated with the earlier
-// chunks' multipliers (row role) or U entries (column role), which the groups
-// keep in shared memory, then solved against the chunk's diagonal 32 x 32
-// block: at step t the owning lane forms the two multipliers (checking them
-// against the unrounded pivot) or rounds the two U entries, and broadcasts
-// them to its group.  Elementwise the operations and their order are those of
-// right-looking elimination.
-constexpr int kO16Threads = 256;
-constexpr int kO16Rows = 64;  // rows or columns per CTA (32 groups x 2)
+// role) for a panel of width w, one thread per row (or column), 128 per CTA.
+// A thread takes its row in 32-wide chunks: the chunk is first updated with
+// the row's multipliers of the earlier chunks (kept in shared memory, one
+// column of X per thread), then solved against the chunk's diagonal 32 x 32
+// block of U11: at step t the thread checks its pre-division value against
+// the unrounded pivot, forms l = fl16(x_t / u_tt) and updates the rest of
+// the chunk.  The column role is the same with L11 and no division (U
+// entries rounded to binary16 as they are formed), and also writes U12^T for
+// the tensor-core update.  U11 / L11^T come from the stage as binary32 (exact
+// binary16 values) and are read by all threads at once (broadcast).  Every
+// entry takes its updates in increasing t, as in right-looking elimination;
+// with no shuffles or group hand-offs the per-step chain is one multiplier
+// formation and one fused multiply-add.
+constexpr int kO16Threads = 128;
+constexpr int kO16Rows = 128;  // rows or columns per CTA
 
 size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + 2 * wp) * sizeof(float); }
 
 __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t lda, int K, int w, int N,
-                                                           int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                                           int* __restrict__ flag, const float* __restrict__ stage, int bid)
+                                               int nrow_blocks, __half* __restrict__ Ut, int ldut,
+                                               int* __restrict__ flag, const float* __restrict__ stage, int bid)
 {
     if (*(volatile int*)flag) return;
     extern __shared__ __align__(16) float osm[];
     const int wp = (w + 31) & ~31, nc = wp / 32;
-    float* D = osm;                  // U11 (row role) or L11^T (column role)
-    float* X = D + wp * wp;          // [t][2 grp + r]: multipliers / U entries of earlier chunks
+    float* D = osm;                  // U11 (row role) or L11^T (column role), wp x wp
+    float* X = D + wp * wp;          // X[t * kO16Rows + tid]: this thread's multipliers / U entries
     float* pv = X + wp * kO16Rows;   // |a_tt|, unrounded
-    float* rinv = pv + wp;           // 1 / u_tt, correctly rounded (row role)
-    const int tid = threadIdx.x, grp = tid >> 3, g = tid & 7;
-    const unsigned gmask = 0xffu << ((tid & 31) & ~7);
-    const bool row_role = (int)bid < nrow_blocks;
+    float* rinv = pv + wp;           // 1 / u_tt, correctly rounded
+    const int tid = threadIdx.x;
+    const bool row_role = bid < nrow_blocks;
     {
         const float4* s4 = reinterpret_cast<const float4*>(stage + (row_role ? 0 : wp * wp));
         float4* d4 = reinterpret_cast<float4*>(D);
@@ -1066,159 +1080,125 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
     __syncthreads();
     if (row_role && tid < wp) rinv[tid] = __frcp_rn(D[tid * wp + tid]);
     __syncthreads();
-    const int base = K + w + (row_role ? (int)bid : (int)bid - nrow_blocks) * kO16Rows + 2 * grp;
-    const bool lv0 = base < N, lv1 = base + 1 < N;
-    float2* Xg = reinterpret_cast<float2*>(X) + grp;  // X[t][2 grp], X[t][2 grp + 1] at Xg[t * 32]
+    const int idx = K + w + (row_role ? bid : bid - nrow_blocks) * kO16Rows + tid;
+    const bool live = idx < N;
+    float* Xt = X + tid;
     if (row_role) {
         bool bad = false;
-        __half* R0 = A + (int64_t)min(base, N - 1) * lda + K;
-        __half* R1 = A + (int64_t)min(base + 1, N - 1) * lda + K;
-        const bool vec = (w % 32 == 0) && ((((uintptr_t)(A + K)) & 7) == 0) && (lda % 4 == 0);
+        __half* R = A + (int64_t)min(idx, N - 1) * lda + K;
+        const bool vec = (w % 32 == 0) && ((((uintptr_t)(A + K)) & 15) == 0) && (lda % 8 == 0);
         for (int c = 0; c < nc; ++c) {
-            const int jb = 32 * c + 4 * g;
-            float x0[4], x1[4];
-            if (vec) {
-                __align__(8) __half e0[4], e1[4];
-                *reinterpret_cast<uint2*>(e0) = lv0 ? *reinterpret_cast<const uint2*>(R0 + jb) : make_uint2(0, 0);
-                *reinterpret_cast<uint2*>(e1) = lv1 ? *reinterpret_cast<const uint2*>(R1 + jb) : make_uint2(0, 0);
+            const int j0 = 32 * c;
+            float x[32];
+            if (vec && live) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    x0[k] = __half2float(e0[k]);
-                    x1[k] = __half2float(e1[k]);
+                for (int q = 0; q < 4; ++q) {
+                    const uint4 raw = reinterpret_cast<const uint4*>(R + j0)[q];
+                    const __half* e = reinterpret_cast<const __half*>(&raw);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) x[8 * q + k] = __half2float(e[k]);
                 }
             } else {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    x0[k] = (lv0 && jb + k < w) ? __half2float(R0[jb + k]) : 0.0f;
-                    x1[k] = (lv1 && jb + k < w) ? __half2float(R1[jb + k]) : 0.0f;
-                }
+                for (int k = 0; k < 32; ++k) x[k] = (live && j0 + k < w) ? __half2float(R[j0 + k]) : 0.0f;
             }
-            for (int t = 0; t < 32 * c; ++t) {
-                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + jb);
-                const float2 l = Xg[t * 32];
-                x0[0] = fmaf(-l.x, d.x, x0[0]);
-                x0[1] = fmaf(-l.x, d.y, x0[1]);
-                x0[2] = fmaf(-l.x, d.z, x0[2]);
-                x0[3] = fmaf(-l.x, d.w, x0[3]);
-                x1[0] = fmaf(-l.y, d.x, x1[0]);
-                x1[1] = fmaf(-l.y, d.y, x1[1]);
-                x1[2] = fmaf(-l.y, d.z, x1[2]);
-                x1[3] = fmaf(-l.y, d.w, x1[3]);
+#pragma unroll 8
+            for (int t = 0; t < j0; ++t) {
+                const float l = Xt[t * kO16Rows];
+                const float4* Dt = reinterpret_cast<const float4*>(D + t * wp + j0);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 d = Dt[q];
+                    x[4 * q + 0] = fmaf(-l, d.x, x[4 * q + 0]);
+                    x[4 * q + 1] = fmaf(-l, d.y, x[4 * q + 1]);
+                    x[4 * q + 2] = fmaf(-l, d.z, x[4 * q + 2]);
+                    x[4 * q + 3] = fmaf(-l, d.w, x[4 * q + 3]);
+                }
             }
 #pragma unroll
             for (int tt = 0; tt < 32; ++tt) {
-                const int t = 32 * c + tt;
-                float l0 = 0.0f, l1 = 0.0f;
-                if (g == tt / 4) {
-                    const float utt = D[t * wp + t], p = pv[t], ru = rinv[t];
-                    const float a0 = x0[tt % 4], a1 = x1[tt % 4];
-                    if (t < w && ((lv0 && !(fabsf(a0) <= p)) || (lv1 && !(fabsf(a1) <= p)))) bad = true;
-                    l0 = div_round_h(a0, utt, ru);
-                    l1 = div_round_h(a1, utt, ru);
-                    x0[tt % 4] = l0;
-                    x1[tt % 4] = l1;
-                    Xg[t * 32] = make_float2(l0, l1);
-                }
-                l0 = __shfl_sync(gmask, l0, tt / 4, 8);
-                l1 = __shfl_sync(gmask, l1, tt / 4, 8);
-                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + jb);
-                if (4 * g + 0 > tt) { x0[0] = fmaf(-l0, d.x, x0[0]); x1[0] = fmaf(-l1, d.x, x1[0]); }
-                if (4 * g + 1 > tt) { x0[1] = fmaf(-l0, d.y, x0[1]); x1[1] = fmaf(-l1, d.y, x1[1]); }
-                if (4 * g + 2 > tt) { x0[2] = fmaf(-l0, d.z, x0[2]); x1[2] = fmaf(-l1, d.z, x1[2]); }
-                if (4 * g + 3 > tt) { x0[3] = fmaf(-l0, d.w, x0[3]); x1[3] = fmaf(-l1, d.w, x1[3]); }
-            }
-            __syncwarp();
-            __align__(8) __half e0[4], e1[4];
+                const int t = j0 + tt;
+                const float* Dt = D + t * wp + j0;
+                if (live && t < w && !(fabsf(x[tt]) <= pv[t])) bad = true;
+                const float l = div_round_h(x[tt], Dt[tt], rinv[t]);
+                x[tt] = l;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                e0[k] = __float2half_rn(x0[k]);
-                e1[k] = __float2half_rn(x1[k]);
+                for (int k = tt + 1; k < 32; ++k) x[k] = fmaf(-l, Dt[k], x[k]);
             }
-            if (vec) {
-                if (lv0) *reinterpret_cast<uint2*>(R0 + jb) = *reinterpret_cast<const uint2*>(e0);
-                if (lv1) *reinterpret_cast<uint2*>(R1 + jb) = *reinterpret_cast<const uint2*>(e1);
-            } else {
+            // the chunk's multipliers for the later chunks (no shared-memory stores inside
+            // the solve, so the loads of U11 can move ahead of the division chain)
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (lv0 && jb + k < w) R0[jb + k] = e0[k];
-                    if (lv1 && jb + k < w) R1[jb + k] = e1[k];
+            for (int tt = 0; tt < 32; ++tt) Xt[(j0 + tt) * kO16Rows] = x[tt];
+            if (live) {
+                if (vec) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        __align__(16) __half h[8];
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) h[k] = __float2half_rn(x[8 * q + k]);
+                        reinterpret_cast<uint4*>(R + j0)[q] = *reinterpret_cast<const uint4*>(h);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k)
+                        if (j0 + k < w) R[j0 + k] = __float2half_rn(x[k]);
                 }
             }
         }
         if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
     } else {
-        // columns base and base + 1 (adjacent: one 4-byte access covers both)
-        const bool pair = lv1 && (((uintptr_t)(A + base)) % 4 == 0) && (lda % 2 == 0);
+        const int col = min(idx, N - 1);
         for (int c = 0; c < nc; ++c) {
-            const int kb = 32 * c + 4 * g;
-            float x0[4], x1[4];
+            const int k0 = 32 * c;
+            float x[32];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const __half* src = A + (int64_t)(K + kb + k) * lda;
-                if (kb + k < w && pair) {
-                    const __half2 v = *reinterpret_cast<const __half2*>(src + base);
-                    x0[k] = __low2float(v);
-                    x1[k] = __high2float(v);
-                } else {
-                    x0[k] = (kb + k < w && lv0) ? __half2float(src[base]) : 0.0f;
-                    x1[k] = (kb + k < w && lv1) ? __half2float(src[base + 1]) : 0.0f;
+            for (int k = 0; k < 32; ++k)
+                x[k] = (live && k0 + k < w) ? __half2float(A[(int64_t)(K + k0 + k) * lda + col]) : 0.0f;
+#pragma unroll 8
+            for (int t = 0; t < k0; ++t) {
+                const float u = Xt[t * kO16Rows];
+                const float4* Dt = reinterpret_cast<const float4*>(D + t * wp + k0);  // L[k0 + k][t]
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 d = Dt[q];
+                    x[4 * q + 0] = fmaf(-d.x, u, x[4 * q + 0]);
+                    x[4 * q + 1] = fmaf(-d.y, u, x[4 * q + 1]);
+                    x[4 * q + 2] = fmaf(-d.z, u, x[4 * q + 2]);
+                    x[4 * q + 3] = fmaf(-d.w, u, x[4 * q + 3]);
                 }
-            }
-            for (int t = 0; t < 32 * c; ++t) {
-                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + kb);  // L[kb + k][t]
-                const float2 u = Xg[t * 32];
-                x0[0] = fmaf(-d.x, u.x, x0[0]);
-                x0[1] = fmaf(-d.y, u.x, x0[1]);
-                x0[2] = fmaf(-d.z, u.x, x0[2]);
-                x0[3] = fmaf(-d.w, u.x, x0[3]);
-                x1[0] = fmaf(-d.x, u.y, x1[0]);
-                x1[1] = fmaf(-d.y, u.y, x1[1]);
-                x1[2] = fmaf(-d.z, u.y, x1[2]);
-                x1[3] = fmaf(-d.w, u.y, x1[3]);
             }
 #pragma unroll
             for (int tt = 0; tt < 32; ++tt) {
-                const int t = 32 * c + tt;
-                float u0 = 0.0f, u1 = 0.0f;
-                if (g == tt / 4) {
-                    u0 = round_h(x0[tt % 4]);
-                    u1 = round_h(x1[tt % 4]);
-                    x0[tt % 4] = u0;
-                    x1[tt % 4] = u1;
-                    Xg[t * 32] = make_float2(u0, u1);
-                }
-                u0 = __shfl_sync(gmask, u0, tt / 4, 8);
-                u1 = __shfl_sync(gmask, u1, tt / 4, 8);
-                const float4 d = *reinterpret_cast<const float4*>(D + t * wp + kb);
-                if (4 * g + 0 > tt) { x0[0] = fmaf(-d.x, u0, x0[0]); x1[0] = fmaf(-d.x, u1, x1[0]); }
-                if (4 * g + 1 > tt) { x0[1] = fmaf(-d.y, u0, x0[1]); x1[1] = fmaf(-d.y, u1, x1[1]); }
-                if (4 * g + 2 > tt) { x0[2] = fmaf(-d.z, u0, x0[2]); x1[2] = fmaf(-d.z, u1, x1[2]); }
-                if (4 * g + 3 > tt) { x0[3] = fmaf(-d.w, u0, x0[3]); x1[3] = fmaf(-d.w, u1, x1[3]); }
-            }
-            __syncwarp();
-            __align__(8) __half e0[4], e1[4];
+                const int t = k0 + tt;
+                const float* Dt = D + t * wp + k0;
+                const float u = round_h(x[tt]);
+                x[tt] = u;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                e0[k] = __float2half_rn(x0[k]);
-                e1[k] = __float2half_rn(x1[k]);
-                if (kb + k < w) {
-                    __half* dst = A + (int64_t)(K + kb + k) * lda;
-                    if (pair) *reinterpret_cast<__half2*>(dst + base) = __halves2half2(e0[k], e1[k]);
-                    else {
-                        if (lv0) dst[base] = e0[k];
-                        if (lv1) dst[base + 1] = e1[k];
+                for (int k = tt + 1; k < 32; ++k) x[k] = fmaf(-Dt[k], u, x[k]);
+            }
+#pragma unroll
+            for (int tt = 0; tt < 32; ++tt) Xt[(k0 + tt) * kO16Rows] = x[tt];
+            if (live) {
+#pragma unroll
+                for (int k = 0; k < 32; ++k)
+                    if (k0 + k < w) A[(int64_t)(K + k0 + k) * lda + col] = __float2half_rn(x[k]);
+                if (Ut) {
+                    // U12^T row (the tensor-core B operand): 32 consecutive entries
+                    __half* u0 = Ut + (int64_t)(idx - K - w) * ldut + k0;
+                    if (k0 + 32 <= w && (ldut % 8 == 0) && ((((uintptr_t)Ut) & 15) == 0)) {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            __align__(16) __half h[8];
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) h[k] = __float2half_rn(x[8 * q + k]);
+                            reinterpret_cast<uint4*>(u0)[q] = *reinterpret_cast<const uint4*>(h);
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k)
+                            if (k0 + k < w) u0[k] = __float2half_rn(x[k]);
                     }
                 }
-            }
-            if (Ut) {
-                // U12^T rows, the tensor-core B operand
-                __half* u0 = Ut + (int64_t)(base - K - w) * ldut + kb;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (kb + k < w) {
-                        if (lv0) u0[k] = e0[k];
-                        if (lv1) u0[ldut + k] = e1[k];
-                    }
             }
         }
     }

@@ -349,7 +349,8 @@ def test_multiplier_rounding_exact_vs_ieee():
     a = (g.uniform(-1.0, 1.0, size=n) * np.abs(u)).astype(np.float32)
     # a quarter of the numerators aimed at binary16 midpoints: a ~ m u, nudged by a few units
     k = n // 4
-    h = g.integers(0x0001, 0x7BFF, size=k).astype(np.uint16)
+    h = g.integers(0x0000, 0x7BFF, size=k).astype(np.uint16)
+    h[: k // 4] = g.integers(0x0000, 0x0400, size=k // 4)  # binary16 subnormal boundaries, 2^-25 included
     lo = h.view(np.float16).astype(np.float64)
     hi = (h + 1).view(np.float16).astype(np.float64)
     m = (lo + hi) / 2.0 * np.where(g.integers(0, 2, size=k) == 1, 1.0, -1.0)
@@ -357,6 +358,10 @@ def test_multiplier_rounding_exact_vs_ieee():
     nudge = g.integers(-6, 7, size=k)
     a[:k] = aa + nudge.astype(np.float32) * np.spacing(aa)
     a[:16] = np.array([0.0, -0.0, 1.0, -1.0] * 4, dtype=np.float32)
+    # exact binary16 midpoints times u (ties at both precisions) and tiny quotients
+    a[16:32] = (np.float32(2.0 ** -25) * u[16:32]).astype(np.float32)
+    a[32:48] = (np.float32(0.5 * (1.0 + (1.0 - 2.0 ** -11))) * u[32:48]).astype(np.float32)
+    a[48:64] = (np.float32(2.0 ** -30) * u[48:64]).astype(np.float32)
     ref32 = (a / u).astype(np.float32)  # IEEE single division (numpy)
     ref = O.f16_bits_from_f32(ref32)
     out = torch.empty(n, device=dev(), dtype=torch.float32)
