@@ -191,7 +191,9 @@ typedef struct nl_batch nl_batch;
 
 /* Create a batch of `count` instances (N[i] in [1, 8192], 0 <= c[i] < 1).
  * All device state is allocated here (the double Jacobians on the first
- * NL_FP64LU solve).  cfg may be NULL; cfg->lu_nb = 0 lets the autotuner time
+ * NL_FP64LU solve).  cfg may be NULL; cfg->lu_path = 1 hands every instance to
+ * the single-instance interchanging path at its first step (the batch then
+ * factors nothing itself); cfg->lu_nb = 0 lets the autotuner time
  * the grouped LU for (nb, update) in {(128, tcgen05), (64, tcgen05),
  * (64, SIMT), (32, SIMT)} on the batch's Jacobians at x0 = ones and keep the
  * fastest (recorded in nl_batch_info_t).  Vectors of the batch are packed:

@@ -298,13 +298,13 @@ __global__ void k_b_cond(BCtl* __restrict__ ctl, int which, int reset, int cap, 
 // interchanges; form b = fl32(-F/||F||) (eq. (2.17)), r = b, u = 0,
 // ||b|| and the IR state (Algorithm IR, u0 = 0).
 __global__ void __launch_bounds__(256) k_b_rhs(const BInst* __restrict__ inst, BState* __restrict__ st, double eta,
-                                               int maxit, BCtl* __restrict__ ctl)
+                                               int maxit, int park_all, BCtl* __restrict__ ctl)
 {
     __shared__ double red[8];
     const BInst& I = inst[blockIdx.x];
     BState& S = st[blockIdx.x];
     if (S.status != BS_ACTIVE) return;
-    if (*(volatile int*)I.flag & 1) {
+    if (park_all || (*(volatile int*)I.flag & 1)) {
         if (threadIdx.x == 0) S.status = BS_PARKED_LU;
         return;
     }
@@ -333,12 +333,13 @@ __global__ void __launch_bounds__(256) k_b_rhs(const BInst* __restrict__ inst, B
     }
 }
 
-__global__ void __launch_bounds__(256) k_b_rhs64(const BInst* __restrict__ inst, BState* __restrict__ st)
+__global__ void __launch_bounds__(256) k_b_rhs64(const BInst* __restrict__ inst, BState* __restrict__ st,
+                                                 int park_all)
 {
     const BInst& I = inst[blockIdx.x];
     BState& S = st[blockIdx.x];
     if (S.status != BS_ACTIVE) return;
-    if (*(volatile int*)I.flag & 1) {
+    if (park_all || (*(volatile int*)I.flag & 1)) {
         if (threadIdx.x == 0) S.status = BS_PARKED_LU;
         return;
     }
@@ -618,7 +619,8 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
     nl_config_default(&d);
     if (cfg) d = *cfg;
     if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 ||
-        d.newton_maxit >= NL_MAX_HIST || (d.lu_nb && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16))) {
+        d.newton_maxit >= NL_MAX_HIST || (d.lu_nb && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
+        d.lu_path < 0 || d.lu_path > 1) {
         set_error("nl_batch_create: invalid configuration");
         return NL_EINVAL;
     }
@@ -908,9 +910,12 @@ static nl_status batch_build_graph(nl_batch* B, int fp64)
         // ---- Newton step body (s1)
         if ((s = launch_jacobian_g(inst, B->dst, B->row_off, count, B->total_rows, B->htab, fp64, s1)) != NL_OK) break;
         nodes_step = 1;
-        if ((s = lu_grouped_factor(plan, gin, s1, &nodes_step)) != NL_OK) break;
+        // lu_path = 1 (interchanging path only): the batch factors nothing itself and hands
+        // every instance to the single-instance path at its first step
+        const int park_all = (C.lu_path == 1) ? 1 : 0;
+        if (!park_all && (s = lu_grouped_factor(plan, gin, s1, &nodes_step)) != NL_OK) break;
         if (!fp64) {
-            k_b_rhs<<<count, 256, 0, s1>>>(inst, B->dst, C.eta_j, C.ir_maxit, B->ctl);
+            k_b_rhs<<<count, 256, 0, s1>>>(inst, B->dst, C.eta_j, C.ir_maxit, park_all, B->ctl);
             {
                 cudaStreamCaptureStatus cs;
                 cudaGraph_t cg;
@@ -933,7 +938,7 @@ static nl_status batch_build_graph(nl_batch* B, int fp64)
             if ((s = launch_residual_g(inst, B->dst, B->res_tasks, B->n_res, 1, B->htab, s1)) != NL_OK) break;
             nodes_step += 3;
         } else {
-            k_b_rhs64<<<count, 256, 0, s1>>>(inst, B->dst);
+            k_b_rhs64<<<count, 256, 0, s1>>>(inst, B->dst, park_all);
             k_b_trsv<double, double><<<count, kBtThreads, vec_smem, s1>>>(inst, B->dst, B->order);
             if ((s = launch_residual_g(inst, B->dst, B->res_tasks, B->n_res, 2, B->htab, s1)) != NL_OK) break;
             nodes_step += 3;

@@ -287,3 +287,20 @@ def test_batch_full_workload_512_instances():
     for k in np.argsort(Ns, kind="stable")[:5]:
         xo, ro = O.newton(Ns[k], cs[k], "IR16GM", tol=1e-10, lu_nb=nb)
         check_instance(stats[k], ro, xs[k], xo)
+
+
+@pytest.mark.parametrize("mode,omode", [("IR16_GMRES", "IR16GM"), ("FP64LU", "FP64LU")])
+def test_batch_instances_leaving_for_the_interchanging_path(mode, omode):
+    """lu_path = 1: every instance leaves the batch at its first step (as one
+    whose factorisation needs row interchanges does) and is finished on the
+    single-instance interchanging path; the results still follow the
+    oracle."""
+    Ns, cs = small_batch(6, seed=21, n_hi=300)
+    with nl.Batch(Ns, cs, lu_nb=64, lu_path=1) as B:
+        xs, status = B.solve(tol=1e-10, mode=mode)
+        info = B.info()
+        stats = [B.stats(i) for i in range(len(Ns))]
+    assert status == nl.NL_OK and info["parked_lu"] == len(Ns) and info["parked_ir"] == 0
+    for N, c, x, st in zip(Ns, cs, xs, stats):
+        xo, ro = O.newton(N, c, omode, tol=1e-10, lu_nb=64)
+        check_instance(st, ro, x, xo, lin=(mode != "FP64LU"))
