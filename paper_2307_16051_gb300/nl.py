@@ -226,9 +226,12 @@ class Solver:
     def __exit__(self, *a):
         self.close()
 
-    def solve(self, tol=1e-10, mode="GMRESIR16", x0=None):
-        """Host-memory solve (nl_solve).  Returns (x, status)."""
-        x = np.empty(self.N)
+    def solve(self, tol=1e-10, mode="GMRESIR16", x0=None, out=None):
+        """Host-memory solve (nl_solve).  Returns (x, status).  x0 and out may
+        be numpy arrays in pinned memory (float64, N)."""
+        x = np.empty(self.N) if out is None else out
+        if x.dtype != np.float64 or x.size != self.N or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("out must be a contiguous float64 array of length N")
         x0p = None
         if x0 is not None:
             x0 = np.ascontiguousarray(x0, dtype=np.float64)

@@ -113,3 +113,30 @@ def test_short_poisson_trace_latency_accounting():
             assert ri["latency_ms"] >= st["t_total_ms"] * 0.999
     assert info["completed"] == len(trace)
     assert 0 < info["p50_ms"] <= info["p99_ms"] and info["solves_per_s"] > 0
+
+
+def test_serving_trace_slice_full_sizes():
+    """The first 0.5 s of the serving workload itself (all four sizes, up to
+    N = 16384, replayed through the bench's server configuration): every
+    request converges; each result meets ||F(x)|| <= 1e-10 ||F(x0)|| under the
+    oracle's double-precision F and the exact moment identity; the small ones
+    match the oracle's Newton to 1e-10."""
+    import math
+    trace = W.serving_trace(duration_s=0.5)
+    assert {N for _, N, _ in trace} >= {256, 1024, 4096}
+    with nl.Server(budget_bytes=96 << 30, max_inflight=8) as S:
+        ids = [S.submit(N, c, arrival_s=t) for t, N, c in trace]
+        S.start()
+        assert S.drain(300.0) == nl.NL_OK
+        results = [S.result(r) for r in ids]
+    checked_oracle = 0
+    for (t, N, c), (x, st, ri) in zip(trace, results):
+        assert ri["status"] == nl.NL_OK
+        m = c / (2 * N) * np.sum(x)
+        assert abs(m - (1 - math.sqrt(1 - c))) <= 1e-9 / math.sqrt(1 - c)
+        f = np.linalg.norm(O.F(N, c, x)) / np.linalg.norm(O.F(N, c, np.ones(N)))
+        assert f <= 1e-10
+        if N == 256 and checked_oracle < 4:
+            xo, ro = O.newton(N, c, "IR16GM", tol=1e-10)
+            assert st["newton_iters"] == ro["newton_iters"] and rel_inf(x, xo) <= 1e-10
+            checked_oracle += 1
