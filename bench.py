@@ -124,6 +124,7 @@ def kernel_rooflines(nl, step, N, hbm_peak, tc_peak):
         "k_diag_lu16": ("alu", diag_flop, FP32_PEAK_TFLOPS, "TFLOP/s", "derived fp32 FMA peak (152 SMs x 128 lanes x 2 x 2.07 GHz)"),
         "k_offdiag16": ("alu", off_flop, FP32_PEAK_TFLOPS, "TFLOP/s", "derived fp32 FMA peak"),
         "k_tc_gemm": ("tensor", gemm_flop, tc_peak, "TFLOP/s", "measured bf16 dense (fp16 same rate)"),
+        "k_trsv_cl": ("hbm", trsv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
         "k_trsv_mb": ("hbm", trsv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
         "k_gemv_residual": ("hbm", gemv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
     }
@@ -230,9 +231,10 @@ def bench_large(nl, torch, dev, hbm_peak, tc_peak, N=32768, c=0.99, fp64=False):
     T2 = 128
     nblk = (N + T2 - 1) // T2
     work = {"k_gemv_residual": 4.0 * N * N + 12.0 * N,
+            "k_trsv_cl": (N * N / 2.0) * 2 + nblk * T2 * T2 * 4 + 12.0 * N,
             "k_trsv_mb": (N * N / 2.0) * 2 + nblk * T2 * T2 * 4 + 12.0 * N,
             "k_tc_gemm": None}
-    for name in ("k_gemv_residual", "k_trsv_mb", "k_tc_gemm"):
+    for name in ("k_gemv_residual", "k_trsv_cl", "k_trsv_mb", "k_tc_gemm"):
         nl.kernel_timing(name)
         s.solve_device(x, tol=TOL, mode="GMRESIR16")
         n, kms = nl.kernel_timing(None)

@@ -72,7 +72,11 @@ typedef struct {
                             for multiples of 64, SIMT otherwise) and the fastest is kept */
     int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update */
     int lu_path;         /* [0 = auto] no-interchange fast path with exact fallback; 1 = interchanging path only */
-    int reserved[7];
+    int trsv_cluster;    /* [0 = auto] half-precision triangular solves: one thread-block cluster per
+                            triangle of at most 16 CTAs (the largest of 16, 8, 4 the device can
+                            co-schedule); 4, 8 or 16 caps the cluster size; -1 = one launch of
+                            independent CTAs per triangle that hand solved entries over global memory */
+    int reserved[6];
 } nl_config;
 
 #define NL_MAX_HIST 128
@@ -152,7 +156,8 @@ const char* nl_last_error(void);
  * class timed since the previous call, then starts timing `kernel_class`
  * (NULL or "" stops timing).  Classes: "k_diag_lu16", "k_offdiag16"
  * (half-precision LU), "k_diag_lu", "k_offdiag" (double LU), "k_tc_gemm",
- * "k_trsv_mb", "k_gemv_residual".  Not thread-safe against
+ * "k_trsv_cl" (cluster triangular solve), "k_trsv_mb" (mailbox triangular
+ * solve), "k_gemv_residual".  Not thread-safe against
  * concurrent solves on other threads.  Synchronises the recorded events. */
 nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* total_ms);
 

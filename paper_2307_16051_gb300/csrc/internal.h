@@ -139,6 +139,7 @@ struct TrsvWork {
     void* y = nullptr;        // N elements: forward-solve result
     unsigned* err = nullptr;  // device error word
     int* scan = nullptr;      // scratch for the permutation build
+    int cluster = 0;          // half-precision solve: 0 = largest cluster available, -1 = mailbox kernel, else cap
 };
 size_t trsv_work_bytes(int N, bool fp64);
 void trsv_work_carve(void* base, int N, bool fp64, TrsvWork* w);

@@ -421,7 +421,8 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     nl_config_default(&d);
     if (cfg) d = *cfg;
     if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 || d.lu_path < 0 ||
-        d.lu_path > 1 ||
+        d.lu_path > 1 || !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 ||
+                           d.trsv_cluster == 8 || d.trsv_cluster == 16) ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
         d.lu_nb < -1) {
         set_error("nl_create: invalid configuration");
@@ -481,6 +482,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->lb.dscal = s->dscal + 4;
     lu_work_carve(cv.take<char>(lu_work_bytes(n, s->nb, false)), n, s->nb, false, &s->luw);
     trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &s->tw);
+    s->tw.cluster = d.trsv_cluster;
     if (cudaMallocHost((void**)&s->pin, 64) != cudaSuccess || cudaEventCreate(&s->ev[0]) != cudaSuccess ||
         cudaEventCreate(&s->ev[1]) != cudaSuccess) {
         cudaFree(s->pool);

@@ -22,6 +22,8 @@
 
 namespace nl {
 
+namespace cg = cooperative_groups;
+
 constexpr int T_ = kTrsvT;
 constexpr int kTrsvThreads = 256;           // 64 rows x 4 column quarters
 constexpr long long kWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
@@ -321,6 +323,206 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
     }
 }
 
+// ------------------------------------------------ cluster triangular solve --
+// One thread-block cluster of C CTAs (C <= 16) solves the whole triangle.
+// Block b of 128 rows belongs to CTA (step of b) mod C, which keeps the
+// running right-hand side of its blocks in shared memory.  The owner of step
+// s forms z_b = Dinv_b acc_b and stores z_b into every CTA's shared memory
+// with st.async, each store completing a transaction count on that CTA's
+// mbarrier for step s (one mbarrier per block, used once).  A CTA waits
+// only for the z it needs next; the owner of step s+1 first subtracts
+// L(b(s+1), b(s)) z_s, with the tile already in registers, then publishes
+// z_{b(s+1)} before it applies z_s to its other blocks, so the chain from
+// one block to the next is one shared-memory signal, one 128 x 32 update
+// per thread group and one 128 x 128 product with the inverse (also held
+// in registers).  Every row of the factor is read by exactly one CTA.
+// Shared vectors of 128 floats are padded to 132 (column c at c + c/32) so
+// the four column quarters fall in different banks.
+constexpr int kClThreads = 512;  // 128 rows x 4 column quarters of 32
+constexpr int kClPad = 132;
+constexpr int kClMaxSmem = 220 * 1024;
+constexpr long long kClWaitIters = 1LL << 24;
+
+// Dynamic shared memory: nblk mbarriers, then nblk + nown padded vectors.
+__host__ __device__ inline int trsv_cl_bar_bytes(int nblk) { return (nblk * 8 + 15) & ~15; }
+inline size_t trsv_cl_smem(int nblk, int nown)
+{
+    return (size_t)trsv_cl_bar_bytes(nblk) + (size_t)(nblk + nown) * kClPad * sizeof(float);
+}
+
+__device__ __forceinline__ uint32_t cl_smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t a, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cl_st_async(uint32_t addr, float v, uint32_t bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(bar)
+                 : "memory");
+}
+// Bounded wait for phase 0 of a local mbarrier; false after kClWaitIters polls.
+__device__ __forceinline__ bool cl_wait(uint32_t bar)
+{
+    for (long long it = 0; it < kClWaitIters; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Row i of the factor, columns c0 .. c0+31 (zeros outside the matrix).
+__device__ __forceinline__ void cl_load_tile(const __half* __restrict__ LU, int64_t ld, int N, int i, int c0,
+                                             bool vecld, uint4 (&t)[4])
+{
+    if (i < N && vecld && c0 + 32 <= N) {
+        const uint4* p = reinterpret_cast<const uint4*>(LU + (int64_t)i * ld + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) t[q] = p[q];
+    } else {
+        __half h[32];
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            h[k] = (i < N && c0 + k < N) ? LU[(int64_t)i * ld + c0 + k] : __float2half_rn(0.0f);
+        memcpy(t, h, 64);
+    }
+}
+__device__ __forceinline__ float cl_dot_tile(const uint4 (&t)[4], const float* __restrict__ z)
+{
+    float part = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const __half2* h2 = reinterpret_cast<const __half2*>(&t[q]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(h2[e]);
+            part = fmaf(f.x, z[8 * q + 2 * e], part);
+            part = fmaf(f.y, z[8 * q + 2 * e + 1], part);
+        }
+    }
+    return part;
+}
+
+template <bool LOWER>
+__global__ void __launch_bounds__(kClThreads, 1) k_trsv_cl(int N, int nblk, const __half* __restrict__ LU, int64_t ld,
+                                                       const float* __restrict__ v, const int* __restrict__ perm,
+                                                       const float* __restrict__ dinv, float* __restrict__ out,
+                                                       unsigned* __restrict__ err)
+{
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks();
+    const int rank = (int)cl.block_rank();
+    extern __shared__ __align__(16) unsigned char cl_raw[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(cl_raw);
+    float* yv = reinterpret_cast<float*>(cl_raw + trsv_cl_bar_bytes(nblk));  // solved blocks, padded
+    float* acc = yv + (size_t)nblk * kClPad;                                       // this CTA's blocks, padded
+    __shared__ int abort_cta;
+    const int tid = threadIdx.x, row = tid >> 2, qq = tid & 3;
+    const int prow = row + (row >> 5);  // padded position of this row
+    const float* Dinv = dinv + (LOWER ? 0 : (int64_t)nblk * T2 * T2);
+    const int nown = (nblk - rank + C - 1) / C;
+    const bool vecld = ((((uintptr_t)LU) & 15) == 0) && ((ld * 2) % 16 == 0);
+    auto blk = [&](int s) { return LOWER ? s : nblk - 1 - s; };
+    for (int j = 0; j < nown; ++j) {
+        const int bj = blk(rank + j * C);
+        for (int t = tid; t < T2; t += kClThreads) {
+            const int i = bj * T2 + t;
+            acc[j * kClPad + t + (t >> 5)] = (i < N) ? (LOWER ? v[perm[i]] : v[i]) : 0.0f;
+        }
+    }
+    if (tid == 0) {
+        abort_cta = 0;
+        for (int s = 0; s < nblk; ++s) {
+            const uint32_t a = cl_smem_u32(bar + s);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(T2 * 4) : "memory");
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cl.sync();  // barriers initialised and every CTA running before the first remote store
+
+    float4 dq[8];  // this thread's quarter of row `row` of the inverse of the next block it publishes
+    uint4 ct[4];   // its 32 factor entries of the next tile on its chain
+    auto load_D = [&](int b) {
+        const float4* D = reinterpret_cast<const float4*>(Dinv + (int64_t)b * T2 * T2 + row * T2 + qq * 32);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dq[k] = D[k];
+    };
+    // z_b = Dinv_b acc_b for the step s this CTA owns, stored into every CTA
+    auto publish = [&](int s) {
+        const int b = blk(s);
+        const float* a = acc + (s / C) * kClPad + qq * 33;
+        float sum = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            sum = fmaf(dq[k].x, a[4 * k], sum);
+            sum = fmaf(dq[k].y, a[4 * k + 1], sum);
+            sum = fmaf(dq[k].z, a[4 * k + 2], sum);
+            sum = fmaf(dq[k].w, a[4 * k + 3], sum);
+        }
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (qq == 0) {
+            const uint32_t ya = cl_smem_u32(yv + (size_t)b * kClPad + prow), ba = cl_smem_u32(bar + s);
+            for (int c = 0; c < C; ++c) cl_st_async(cl_mapa(ya, c), sum, cl_mapa(ba, c));
+            const int i = b * T2 + row;
+            if (i < N) out[i] = sum;
+        }
+        if (s + C < nblk) {
+            // inverse and chain tile for this CTA's next step s + C
+            load_D(blk(s + C));
+            cl_load_tile(LU, ld, N, blk(s + C) * T2 + row, blk(s + C - 1) * T2 + qq * 32, vecld, ct);
+        }
+    };
+    if (rank < nblk) load_D(blk(rank));
+    if (rank >= 1 && rank < nblk) cl_load_tile(LU, ld, N, blk(rank) * T2 + row, blk(rank - 1) * T2 + qq * 32, vecld, ct);
+    if (rank == 0) publish(0);
+    for (int s = 0; s < nblk; ++s) {
+        const int b = blk(s);
+        bool ok = false;
+        if (!*((volatile int*)&abort_cta)) {
+            ok = cl_wait(cl_smem_u32(bar + s));
+            if (!ok) {
+                abort_cta = 1;
+                atomicOr(err, (unsigned)ERR_TIMEOUT_TRSV);
+            }
+        }
+        const float* z = yv + (size_t)b * kClPad + qq * 33;
+        int j = (s < rank) ? 0 : (s - rank) / C + 1;  // this CTA's blocks solved after step s
+        if (j < nown && rank + j * C == s + 1) {
+            // next block on the chain: update with the tile already in registers, then publish it
+            const float part0 = ok ? cl_dot_tile(ct, z) : 0.0f;
+            float part = part0 + __shfl_xor_sync(0xffffffffu, part0, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            if (qq == 0) acc[j * kClPad + prow] -= part;
+            __syncthreads();
+            publish(s + 1);
+            ++j;
+        }
+        if (!ok) continue;
+        for (; j < nown; ++j) {
+            uint4 t[4];
+            cl_load_tile(LU, ld, N, blk(rank + j * C) * T2 + row, b * T2 + qq * 32, vecld, t);
+            float part = cl_dot_tile(t, z);
+            part += __shfl_xor_sync(0xffffffffu, part, 1);
+            part += __shfl_xor_sync(0xffffffffu, part, 2);
+            if (qq == 0) acc[j * kClPad + prow] -= part;
+        }
+    }
+    cl.sync();  // no CTA leaves before every CTA has passed all of its waits
+}
+
 // ------------------------------------------------------------------- host --
 
 static int trsv_block(bool fp64) { return fp64 ? T_ : T2; }
@@ -493,9 +695,94 @@ static nl_status launch_trsv_mb(int N, const __half* LU, int64_t ld, const float
     return NL_OK;
 }
 
+// Whether a cluster of C CTAs of the cluster triangular solve can be
+// co-scheduled on this device (cached per process; C in {4, 8, 16}).
+static bool trsv_cluster_ok(int C)
+{
+    static int avail[3] = {-1, -1, -1};
+    const int slot = C == 16 ? 2 : (C == 8 ? 1 : 0);
+    if (avail[slot] < 0) {
+        bool ok = true;
+        for (int low = 0; low < 2 && ok; ++low) {
+            const void* kern = low ? (const void*)k_trsv_cl<true> : (const void*)k_trsv_cl<false>;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kClMaxSmem) != cudaSuccess) {
+                ok = false;
+                break;
+            }
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(kClThreads);
+            cfg.dynamicSmemBytes = kClMaxSmem;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess || n < 1) ok = false;
+        }
+        cudaGetLastError();
+        avail[slot] = ok ? 1 : 0;
+    }
+    return avail[slot] == 1;
+}
+
+// Cluster size for nblk blocks under the request req (0 = largest available,
+// -1 = none, else the largest available <= req); 0 = use the mailbox solve.
+static int trsv_cluster_size(int nblk, int req)
+{
+    if (req < 0) return 0;
+    for (int C : {16, 8, 4})
+        if ((req == 0 || C <= req) && trsv_cluster_ok(C)) {
+            const int Cn = std::min(C, nblk);
+            if (trsv_cl_smem(nblk, (int)cdiv(nblk, Cn)) > (size_t)kClMaxSmem) return 0;
+            return Cn;
+        }
+    return 0;
+}
+
+template <bool LOWER>
+static nl_status launch_trsv_cl(int N, const __half* LU, int64_t ld, const float* v, float* out, const TrsvWork& w,
+                                int C, cudaStream_t st)
+{
+    const int nblk = (int)cdiv(N, T2);
+    const int nown = (int)cdiv(nblk, C);
+    const size_t smem = trsv_cl_smem(nblk, nown);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int* perm = w.perm;
+    const float* dinv = (const float*)w.dinv;
+    prof_begin("k_trsv_cl", st);
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_trsv_cl<LOWER>, N, nblk, LU, ld, v, perm, dinv, out, w.err);
+    prof_end("k_trsv_cl", st);
+    NL_CUDA_OK(le);
+    return NL_OK;
+}
+
 nl_status trsv_solve16(int N, const __half* LU, int64_t ld, const float* v, float* z, const TrsvWork& w, int epoch,
                        cudaStream_t st, int* launches)
 {
+    const int C = trsv_cluster_size((int)cdiv(N, T2), w.cluster);
+    if (C > 0) {
+        float* y = (float*)w.y;
+        nl_status s = launch_trsv_cl<true>(N, LU, ld, v, y, w, C, st);
+        if (s == NL_OK) s = launch_trsv_cl<false>(N, LU, ld, y, z, w, C, st);
+        if (launches) *launches += 2;
+        return s;
+    }
     unsigned long long* mbf = (unsigned long long*)w.y;
     unsigned long long* mbb = mbf + N;
     nl_status s = launch_trsv_mb<true>(N, LU, ld, v, nullptr, mbf, nullptr, w, (unsigned)epoch, st);

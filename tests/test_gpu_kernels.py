@@ -255,6 +255,37 @@ def test_lusolve16_matches_oracle_fly(N):
     assert np.linalg.norm(got - ref) <= 2e-5 * np.linalg.norm(ref)
 
 
+def synthetic_factors(N, seed):
+    """Binary16 factors with a known-stable solve: unit lower L and upper U
+    whose off-diagonal entries are uniform in (-2/N, 2/N) (so a skipped or
+    misplaced 128-column tile changes x by far more than the tolerance),
+    U's diagonal of magnitude in [1, 2] with random signs, and a random
+    valid pivot sequence ipiv[k] in [k, N)."""
+    rng = np.random.default_rng(seed)
+    LU = rng.uniform(-2.0 / N, 2.0 / N, size=(N, N))
+    d = rng.uniform(1.0, 2.0, size=N) * rng.choice([-1.0, 1.0], size=N)
+    LU[np.arange(N), np.arange(N)] = d
+    LU = LU.astype(np.float16).astype(np.float64)
+    ipiv = np.array([rng.integers(k, N) for k in range(N)], dtype=np.int32)
+    return LU, ipiv
+
+
+@pytest.mark.parametrize("N", [127, 128, 2049, 4096, 4097, 9000])
+def test_lusolve16_synthetic_factors(N):
+    """Both triangles over many 128-row blocks, with ragged last blocks and
+    more blocks than CTAs in one cluster (each CTA owns several blocks)."""
+    LUo, ipivo = synthetic_factors(N, 5000 + N)
+    b = W.random_vector(N, 6000 + N).astype(np.float32)
+    ref = O.lusolve_fly(LUo, ipivo, b).astype(np.float64)
+    ld = ((N + 63) // 64) * 64
+    LUd = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    LUd[:, :N] = T(LUo.astype(np.float16))
+    bd = T(b)
+    nl.lusolve16(N, LUd, ld, T(ipivo), bd)
+    got = bd.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 1e-5 * np.max(np.abs(ref)))
+
+
 @pytest.mark.parametrize("N,nb,diag", [(1, 16, False), (50, 16, False), (200, 64, False), (301, 64, False),
                                         (301, 64, True), (500, 128, True)])
 def test_lu64_and_solve_match_oracle(N, nb, diag):
