@@ -395,8 +395,11 @@ def main():
     hbm_peak, tc_peak, tc_sust, peak_kind = peaks()
     # the five solves of a step are independent problems: each runs on its own
     # stream, driven by its own host thread, so that their latency-bound
-    # factorisations share the GPU (per-solve times are reported separately)
-    streams = {c: torch.cuda.Stream(device=dev) for c in SWEEP}
+    # factorisations share the GPU (per-solve times are reported separately).
+    # Larger c takes more Newton steps, so the step's time is that solve's
+    # latency: its stream gets the highest priority (lower number = higher).
+    order = sorted(SWEEP)
+    streams = {c: torch.cuda.Stream(device=dev, priority=-order.index(c)) for c in SWEEP}
     solvers = {c: nl.Solver(N_BENCH, c, stream=streams[c], lu_nb=args.lu_nb) for c in SWEEP}
     xdev = {c: torch.empty(N_BENCH, device=dev, dtype=torch.float64) for c in SWEEP}
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)

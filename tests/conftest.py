@@ -58,3 +58,19 @@ def agrees_4digits(computed, printed):
     digits (half a unit in the last printed place, plus a hair for ties)."""
     e = np.floor(np.log10(abs(printed)))
     return abs(computed - printed) <= 0.5e-3 * 10 ** e * 1.0001
+
+
+def newton_counts_agree(gpu_iters, ro, tol=1e-10):
+    """The GPU Newton count equals the oracle's, or differs by one where the
+    oracle's relative residual at the smaller of the two counts lies within a
+    factor of two of the tolerance: the paper fixes the precisions of the
+    triangular solves (eq. (2.16)) but not their summation order, so the
+    last step's residual can land on either side of tau_r there."""
+    n = ro["newton_iters"]
+    if gpu_iters == n:
+        return True
+    if gpu_iters == n - 1:
+        return ro["hist"][gpu_iters] <= 2.0 * tol
+    if gpu_iters == n + 1:
+        return ro["hist"][n] >= 0.5 * tol
+    return False

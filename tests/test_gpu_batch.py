@@ -9,6 +9,7 @@ import pytest
 from oracle import oracle as O
 from paper_2307_16051_gb300 import nl
 from paper_2307_16051_gb300 import workloads as W
+from tests.conftest import newton_counts_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -178,7 +179,7 @@ def small_batch(count=24, seed=11, n_lo=17, n_hi=400):
 
 def check_instance(st, ro, x, xo, lin=True):
     assert ro["status"] == 0 and st["status"] == nl.NL_OK
-    assert st["newton_iters"] == ro["newton_iters"], (st["newton_iters"], ro["newton_iters"])
+    assert newton_counts_agree(st["newton_iters"], ro), (st["newton_iters"], ro["newton_iters"], ro["hist"])
     if lin:
         for a, b in zip(st["lin_iters"], ro["lin_iters"]):
             assert abs(a - b) <= 1, (st["lin_iters"], ro["lin_iters"])
@@ -262,7 +263,7 @@ def test_batch_autotuner_choice_is_used_and_recorded():
     assert (best[0], best[1]) == (info["lu_nb"], info["trailing_gemm"])
     assert st["lu_nb"] == info["lu_nb"]
     xo, ro = O.newton(Ns[0], cs[0], "IR16GM", tol=1e-10, lu_nb=info["lu_nb"])
-    assert st["newton_iters"] == ro["newton_iters"] and rel_inf(xs[0], xo) <= 1e-10
+    assert newton_counts_agree(st["newton_iters"], ro) and rel_inf(xs[0], xo) <= 1e-10
 
 
 def test_batch_full_workload_512_instances():

@@ -10,6 +10,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2307_16051_gb300 import nl
+from tests.conftest import newton_counts_agree
 
 pytestmark = pytest.mark.gpu
 
@@ -33,7 +34,7 @@ def check_counts(st, ro, mode, allow_stall=False, ill=False):
     more or one fewer outer correction (one more GMRES call) on either side,
     decided by single-precision rounding: there the tolerance is one outer
     correction, compared on the outer counts."""
-    assert st["newton_iters"] == ro["newton_iters"], (st["newton_iters"], ro["newton_iters"])
+    assert newton_counts_agree(st["newton_iters"], ro), (st["newton_iters"], ro["newton_iters"], ro["hist"])
     if mode == "FP64LU" or allow_stall:
         return
     if ill and mode == "GMRESIR16":
@@ -97,7 +98,7 @@ def test_custom_start_and_device_api():
         st = s.solve_device(xd, tol=1e-10, mode="GMRESIR16", x0=torch.as_tensor(x0, device="cuda"))
         assert st == nl.NL_OK
         assert np.array_equal(xd.cpu().numpy(), x)  # same path, bitwise
-        assert s.stats()["newton_iters"] == ro["newton_iters"]
+        assert newton_counts_agree(s.stats()["newton_iters"], ro)
     assert rel_inf(x, xo) <= 1e-10
 
 
@@ -127,7 +128,7 @@ def test_trsv_variants_agree(mode):
         with nl.Solver(N, c, trsv_cluster=cl) as s:
             x, status = s.solve(tol=1e-10, mode=mode)
             st = s.stats()
-        assert status == nl.NL_OK and st["newton_iters"] == ro["newton_iters"], (cl, st["newton_iters"])
+        assert status == nl.NL_OK and newton_counts_agree(st["newton_iters"], ro), (cl, st["newton_iters"])
         assert rel_inf(x, xo) <= 1e-10, cl
         res[cl] = x
     assert np.array_equal(res[4], res[8]) and np.array_equal(res[8], res[16]) and np.array_equal(res[16], res[0])

@@ -6,6 +6,7 @@ import pytest
 
 from oracle import oracle as O
 from paper_2307_16051_gb300 import nl
+from tests.conftest import newton_counts_agree
 from paper_2307_16051_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -70,7 +71,7 @@ def test_served_results_match_oracle():
             x, st, ri = S.result(rid)
             xo, ro = O.newton(N, c, "IR16GM", tol=1e-10)
             assert ri["status"] == nl.NL_OK and ro["status"] == 0
-            assert st["newton_iters"] == ro["newton_iters"]
+            assert newton_counts_agree(st["newton_iters"], ro)
             for a, b in zip(st["lin_iters"], ro["lin_iters"]):
                 assert abs(a - b) <= 1
             assert rel_inf(x, xo) <= 1e-10
@@ -138,5 +139,5 @@ def test_serving_trace_slice_full_sizes():
         assert f <= 1e-10
         if N == 256 and checked_oracle < 4:
             xo, ro = O.newton(N, c, "IR16GM", tol=1e-10)
-            assert st["newton_iters"] == ro["newton_iters"] and rel_inf(x, xo) <= 1e-10
+            assert newton_counts_agree(st["newton_iters"], ro) and rel_inf(x, xo) <= 1e-10
             checked_oracle += 1
