@@ -74,8 +74,9 @@ typedef struct {
     int lu_path;         /* [0 = auto] no-interchange fast path with exact fallback; 1 = interchanging path only */
     int trsv_cluster;    /* [0 = auto] half-precision triangular solves: one thread-block cluster per
                             triangle of at most 16 CTAs (the largest of 16, 8, 4 the device can
-                            co-schedule); 4, 8 or 16 caps the cluster size; -1 = one launch of
-                            independent CTAs per triangle that hand solved entries over global memory */
+                            co-schedule) for N <= 10240, else one launch of independent CTAs per
+                            triangle that hand solved entries over global memory; 4, 8 or 16 caps
+                            the cluster size (any N); -1 = always the global-memory hand-off */
     int reserved[6];
 } nl_config;
 
@@ -409,7 +410,10 @@ nl_status nl_k_div_round16(int64_t n, const float* a, const float* b, float* out
  * B K x Nc, C M x Nc binary16 row-major (lda, ldb, ldc), products accumulated
  * in single.  gemm: 1 SIMT (sequential fused multiply-adds over k),
  * 2 tcgen05 tensor cores (K a multiple of 64, lda/ldb/ldc multiples of 8,
- * pointers 16-byte aligned). */
+ * pointers 16-byte aligned; for K <= 128 the persistent kernel: one CTA per
+ * SM, TMA loads of A, B and C and TMA stores of C, loads and MMAs of one tile
+ * overlapping the epilogue of the previous one), 3 the same tensor-core
+ * arithmetic with one CTA per 128 x 128 tile (bitwise the same results as 2). */
 nl_status nl_k_gemm16_update(int64_t M, int64_t Nc, int64_t K, const void* A, int64_t lda, const void* B,
                              int64_t ldb, void* C, int64_t ldc, int gemm, void* stream);
 

@@ -227,6 +227,288 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
     tc_gemm_tile(&tmA, &tmB, 0, 0, M, Nc, K, C, ldc, (int)blockIdx.y * kTcBM, (int)blockIdx.x * kTcBN, err);
 }
 
+// ------------------------------------------------ persistent, pipelined --
+// The same update C <- fl16(C - A Bt^T) with one CTA per SM looping over the
+// output tiles (tile = blockIdx.x + i * gridDim.x) and four warp roles, each
+// stage of work double-buffered:
+//   warp 0 (one thread): TMA loads of the A and B slabs of tile i into
+//     operand stage i % 2 once the MMAs of tile i-2 are done with it;
+//   warp 1 (one thread): K/16 tcgen05.mma into TMEM accumulator i % 2 (128
+//     columns each) once the epilogue has read tile i-2's accumulator, then
+//     tcgen05.commit to "accumulator full" and to "operand stage free";
+//   warps 2-5: epilogue.  Each thread owns one tile row (its warp's TMEM
+//     lane quarter): tcgen05.ld of the accumulator row (then "accumulator
+//     free"), C from C buffer i % 3 (128-byte swizzle), fl16(C - acc)
+//     written back in place, a proxy fence and an arrival on "C written";
+//   warp 6 (one thread): the C tiles' traffic.  TMA load of C for tile i
+//     into buffer i % 3, and for each finished tile the TMA bulk store of its
+//     C buffer, whose completed read of the buffer frees it for tile i+3.
+// Loads, MMAs, epilogue and stores of consecutive tiles overlap, and all
+// global traffic is TMA (coalesced, asynchronous).  Per element the
+// arithmetic is the per-tile kernel's: the same K/16 MMAs in the same order,
+// then one subtraction and one rounding.  K <= 128 (two operand stages of
+// 64 KB and three C buffers of 32 KB, so two C tiles are in flight to and
+// from memory while the epilogue works on the third).  Every wait is bounded; a timeout marks
+// the CTA aborted, every role leaves its loop, in-flight copies and MMAs are
+// waited for (bounded), and tensor memory is released.
+constexpr int kPThreads = 224;
+constexpr uint32_t kPSlab = 128 * 128;  // bytes of one 128-row x 64-column binary16 slab
+constexpr uint32_t kPCBytes = 2 * kPSlab;  // one C tile: two 64-column boxes
+constexpr int kPCBuf = 3;
+
+static size_t p_smem_bytes(int KT) { return 1024 + 2 * (size_t)KT * 2 * kPSlab + kPCBuf * (size_t)kPCBytes + 128; }
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+__global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap tmA,
+                                                            const __grid_constant__ CUtensorMap tmB,
+                                                            const __grid_constant__ CUtensorMap tmC, int M, int Nc,
+                                                            int K, unsigned* __restrict__ err,
+                                                            const int* __restrict__ flag)
+{
+    if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* basep = smem_raw + (base - raw);
+    const int KT = K / kTcBK;
+    const uint32_t ab_bytes = (uint32_t)KT * 2 * kPSlab;
+    const uint32_t sAB = base, sCb = base + 2 * ab_bytes;  // operand stages, then C buffers
+    uint64_t* bars = reinterpret_cast<uint64_t*>(basep + 2 * ab_bytes + kPCBuf * kPCBytes);
+    // bars: ab_full[2], ab_empty[2], tfull[2], tempty[2], c_full[3] (8..10), c_done[3] (11..13);
+    // then the TMEM address
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
+    __shared__ int aborted;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_n = (Nc + kTcBN - 1) / kTcBN;
+    const int ntiles = tiles_n * ((M + kTcBM - 1) / kTcBM);
+    const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    auto bar = [&](int k) { return smem_u32(&bars[k]); };
+    auto fail = [&]() {
+        atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+        *(volatile int*)&aborted = 1;
+    };
+    auto tile_mn = [&](int it, int* m0, int* n0) {
+        const int tile = blockIdx.x + it * gridDim.x;
+        *m0 = (tile / tiles_n) * kTcBM;
+        *n0 = (tile % tiles_n) * kTcBN;
+    };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2u * kTcBN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (threadIdx.x == 32) {
+        aborted = 0;
+        for (int k = 0; k < 2; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(0 + k)));     // ab_full
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(2 + k)));     // ab_empty (MMA commit)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(4 + k)));     // tfull (MMA commit)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bar(6 + k)));   // tempty (epilogue)
+        }
+        for (int k = 0; k < kPCBuf; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(8 + k)));     // c_full (TMA)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bar(11 + k)));  // c_done (epilogue)
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
+                const int s = it & 1;
+                const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+                if (it >= 2 && !mbar_wait(bar(2 + s), ph ^ 1u, kTcWaitCycles)) {
+                    fail();
+                    break;
+                }
+                int m0, n0;
+                tile_mn(it, &m0, &n0);
+                const uint32_t sA = sAB + s * ab_bytes, sB = sA + KT * kPSlab;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)), "r"(ab_bytes)
+                             : "memory");
+                for (int kt = 0; kt < KT; ++kt) {
+                    tma_load_2d(sA + kt * kPSlab, &tmA, kt * kTcBK, m0, bar(s));
+                    tma_load_2d(sB + kt * kPSlab, &tmB, kt * kTcBK, n0, bar(s));
+                }
+                issued = it + 1;
+            }
+            // copies in flight land before the CTA's shared memory goes away
+            for (int it = (issued >= 2 ? issued - 2 : 0); it < issued; ++it)
+                mbar_wait(bar(it & 1), (uint32_t)(it >> 1) & 1u, kTcWaitCycles);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc();
+            int committed = 0;
+            for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
+                const int s = it & 1, b = it & 1;
+                const uint32_t ph = (uint32_t)(it >> 1) & 1u;
+                if (!mbar_wait(bar(s), ph, kTcWaitCycles) ||
+                    (it >= 2 && !mbar_wait(bar(6 + b), ph ^ 1u, kTcWaitCycles))) {
+                    fail();
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sA = sAB + s * ab_bytes, sB = sA + KT * kPSlab;
+                const uint32_t d = tmem + (uint32_t)(b * kTcBN);
+                for (int kt = 0; kt < KT; ++kt) {
+#pragma unroll
+                    for (int kk = 0; kk < kTcBK / 16; ++kk) {
+                        const uint64_t ad = sw128_desc(sA + kt * kPSlab + kk * 32);
+                        const uint64_t bd = sw128_desc(sB + kt * kPSlab + kk * 32);
+                        const uint32_t acc = (kt | kk) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 bar(4 + b))
+                             : "memory");
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 bar(2 + s))
+                             : "memory");
+                committed = it + 1;
+            }
+            if (committed > 0) {
+                // the last MMAs are complete before tensor memory is released
+                const int it = committed - 1;
+                mbar_wait(bar(4 + (it & 1)), (uint32_t)(it >> 1) & 1u, kTcWaitCycles);
+            }
+        }
+    } else if (warp == 6) {
+        if (lane == 0) {
+            // C traffic: loads for tiles 0..2, then per finished tile i its store
+            // and, once the store has read the buffer, the load for tile i+3
+            int loaded = 0;
+            for (int it = 0; it < kPCBuf && it < nmine; ++it) {
+                int m0, n0;
+                tile_mn(it, &m0, &n0);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(8 + it)),
+                             "r"(kPCBytes)
+                             : "memory");
+                for (int j = 0; j < 2; ++j) tma_load_2d(sCb + it * kPCBytes + j * kPSlab, &tmC, n0 + j * kTcBK, m0, bar(8 + it));
+                loaded = it + 1;
+            }
+            for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
+                const int s = it % kPCBuf;
+                const uint32_t ph = (uint32_t)(it / kPCBuf) & 1u;
+                if (!mbar_wait(bar(11 + s), ph, kTcWaitCycles)) {
+                    fail();
+                    break;
+                }
+                int m0, n0;
+                tile_mn(it, &m0, &n0);
+                for (int j = 0; j < 2; ++j)
+                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                     &tmC),
+                                 "r"(n0 + j * kTcBK), "r"(m0), "r"(sCb + s * kPCBytes + j * kPSlab)
+                                 : "memory");
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                if (it + kPCBuf < nmine) {
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                    tile_mn(it + kPCBuf, &m0, &n0);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(8 + s)),
+                                 "r"(kPCBytes)
+                                 : "memory");
+                    for (int j = 0; j < 2; ++j)
+                        tma_load_2d(sCb + s * kPCBytes + j * kPSlab, &tmC, n0 + j * kTcBK, m0, bar(8 + s));
+                    loaded = it + kPCBuf + 1;
+                }
+            }
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+            if (*(volatile int*)&aborted)
+                for (int it = (loaded >= kPCBuf ? loaded - kPCBuf : 0); it < loaded; ++it)
+                    mbar_wait(bar(8 + it % kPCBuf), (uint32_t)(it / kPCBuf) & 1u, kTcWaitCycles);
+        }
+    } else {
+        const int q = warp & 3;       // TMEM lane quarter of this warp (warps 2..5 -> 2, 3, 0, 1)
+        const int r = q * 32 + lane;  // tile row of this thread
+        const uint32_t swz = (uint32_t)(r & 7);
+        for (int it = 0; it < nmine; ++it) {
+            const int s = it % kPCBuf, b = it & 1;
+            const uint32_t ph = (uint32_t)(it >> 1) & 1u, phc = (uint32_t)(it / kPCBuf) & 1u;
+            const bool ok = !*(volatile int*)&aborted && mbar_wait(bar(4 + b), ph, kTcWaitCycles) &&
+                            mbar_wait(bar(8 + s), phc, kTcWaitCycles);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) fail();
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            uint8_t* cst = basep + 2 * ab_bytes + s * kPCBytes;  // C buffer it % 3
+#pragma unroll
+            for (int c = 0; c < kTcBN; c += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTcBN + c);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c + 32 == kTcBN) {
+                    // the whole accumulator row is in registers: the buffer may be reused
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    mbar_arrive(bar(6 + b));
+                }
+                // columns c .. c+31: box c / 64, 16-byte chunks (c % 64) / 8 .. + 3, swizzled by row
+                uint8_t* rowp = cst + (c / 64) * kPSlab + r * 128;
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const uint32_t chunk = (uint32_t)((c % 64) / 8 + h) ^ swz;
+                    uint4* p = reinterpret_cast<uint4*>(rowp + chunk * 16);
+                    const uint4 x = *p;
+                    uint32_t wds[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        __half2 h2;
+                        memcpy(&h2, &wds[e], 4);
+                        float2 f = __half22float2(h2);
+                        f.x -= __uint_as_float(v[h * 8 + 2 * e]);
+                        f.y -= __uint_as_float(v[h * 8 + 2 * e + 1]);
+                        h2 = __floats2half2_rn(f.x, f.y);
+                        memcpy(&wds[e], &h2, 4);
+                    }
+                    *p = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                }
+            }
+            // this row of the tile is written: visible to the TMA store, then signalled
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(bar(11 + s));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * kTcBN));
+    }
+}
+
 // Grouped trailing update of outer step [K, K + w) of many matrices: task
 // {inst, m0, n0} updates tile (m0, n0) of instance inst's A22 (rows and
 // columns from K + w) with L21 (rows from K + w, columns K .. K + w) read
@@ -274,6 +556,7 @@ bool tc_gemm_supported()
     cudaMemset(g_tc_err, 0, sizeof(unsigned));
     if (set_max_dynamic_smem((const void*)k_tc_gemm) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_g) != NL_OK) return false;
+    if (set_max_dynamic_smem((const void*)k_tc_gemm_p) != NL_OK) return false;
     g_tc_state = 1;
     return true;
 }
@@ -299,7 +582,7 @@ static bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t 
 }
 
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
-                           __half* C, int64_t ldc, cudaStream_t st, const int* flag)
+                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile)
 {
     if (M <= 0 || Nc <= 0) return NL_OK;
     if (!tc_gemm_supported()) {
@@ -317,6 +600,28 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         !encode_2d(&tmB, Bt, (uint64_t)K, (uint64_t)Nc, (uint64_t)ldbt, kTcBK, kTcBN)) {
         set_error("tcgen05 GEMM: cuTensorMapEncodeTiled failed");
         return NL_ECUDA;
+    }
+    if (!per_tile && K <= 2 * kTcBK) {
+        // persistent pipelined kernel: one CTA per SM (at most one per tile)
+        CUtensorMap tmC;
+        if (!encode_2d(&tmC, C, (uint64_t)Nc, (uint64_t)M, (uint64_t)ldc, kTcBK, kTcBM)) {
+            set_error("tcgen05 GEMM: cuTensorMapEncodeTiled failed (C)");
+            return NL_ECUDA;
+        }
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (nsm < 1) nsm = 1;
+        }
+        const long long ntiles = (long long)cdiv(Nc, kTcBN) * cdiv(M, kTcBM);
+        const unsigned grid = (unsigned)std::min<long long>(ntiles, nsm);
+        prof_begin("k_tc_gemm", st);
+        k_tc_gemm_p<<<grid, kPThreads, p_smem_bytes(K / kTcBK), st>>>(tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
+        prof_end("k_tc_gemm", st);
+        NL_CUDA_OK(cudaGetLastError());
+        return NL_OK;
     }
     const size_t smem = tc_smem_bytes(K);
     dim3 grid((unsigned)cdiv(Nc, kTcBN), (unsigned)cdiv(M, kTcBM));

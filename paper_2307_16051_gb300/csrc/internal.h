@@ -128,7 +128,7 @@ nl_status launch_gemv_residual_g(const BInst* inst, BState* st, const BTask* tas
 // gemm_tc.cu: C = fl16(C - A * Bt^T), A M x K (lda), Bt Nc x K (ldbt), tcgen05 + TMA.
 bool tc_gemm_supported();
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
-                           __half* C, int64_t ldc, cudaStream_t st, const int* flag);
+                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile = false);
 
 // trsv.cu: triangular solves with the factors.
 constexpr int kTrsvT = 64;  // diagonal block size

@@ -1392,12 +1392,12 @@ nl_status launch_transpose16(int R, int Cc, const __half* in, int64_t ldi, __hal
 nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* B, int64_t ldb, __half* C,
                         int64_t ldc, int gemm, cudaStream_t st)
 {
-    if (gemm == 2) {
+    if (gemm == 2 || gemm == 3) {
         // the tensor-core path takes B transposed (K-major): build it
         __half* Bt = nullptr;
         NL_CUDA_OK(cudaMallocAsync((void**)&Bt, (size_t)round_up(Nc, 128) * K * 2, st));
         nl_status s = launch_transpose16(K, Nc, B, ldb, Bt, K, st);
-        if (s == NL_OK) s = tc_gemm16_update(M, Nc, K, A, lda, Bt, K, C, ldc, st, nullptr);
+        if (s == NL_OK) s = tc_gemm16_update(M, Nc, K, A, lda, Bt, K, C, ldc, st, nullptr, gemm == 3);
         cudaFreeAsync(Bt, st);
         return s;
     }

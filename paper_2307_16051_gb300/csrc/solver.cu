@@ -1003,7 +1003,7 @@ nl_status nl_k_gemv_residual(int64_t N, const float* A, int64_t ld, const float*
 nl_status nl_k_gemm16_update(int64_t M, int64_t Nc, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                              void* C, int64_t ldc, int gemm, void* stream)
 {
-    if (M < 0 || Nc < 0 || K < 1 || !A || !B || !C || (gemm != 1 && gemm != 2)) {
+    if (M < 0 || Nc < 0 || K < 1 || !A || !B || !C || gemm < 1 || gemm > 3) {
         set_error("nl_k_gemm16_update: bad argument");
         return NL_EINVAL;
     }

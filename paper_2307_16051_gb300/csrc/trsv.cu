@@ -732,9 +732,14 @@ static bool trsv_cluster_ok(int C)
 
 // Cluster size for nblk blocks under the request req (0 = largest available,
 // -1 = none, else the largest available <= req); 0 = use the mailbox solve.
+// Automatic choice: the cluster's 16 SMs stream the whole factor, so beyond
+// 80 blocks (N > 10240) the mailbox solve over all SMs is faster (measured on
+// GB300: 197 vs 247 us at N = 8192, 379 vs 368 us at 12288, 676 vs 489 us at
+// 16384 per triangle).
+constexpr int kClAutoMaxBlocks = 80;
 static int trsv_cluster_size(int nblk, int req)
 {
-    if (req < 0) return 0;
+    if (req < 0 || (req == 0 && nblk > kClAutoMaxBlocks)) return 0;
     for (int C : {16, 8, 4})
         if ((req == 0 || C <= req) && trsv_cluster_ok(C)) {
             const int Cn = std::min(C, nblk);

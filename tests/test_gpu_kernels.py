@@ -208,7 +208,8 @@ def test_lu16_zero_column_reports_info():
 
 # ------------------------------------------------------------ GEMM update --
 
-@pytest.mark.parametrize("M,Nc,K", [(64, 64, 64), (300, 200, 128), (129, 1000, 256), (1, 5, 64)])
+@pytest.mark.parametrize("M,Nc,K", [(64, 64, 64), (300, 200, 128), (129, 1000, 256), (1, 5, 64), (2000, 2100, 128),
+                                    (3000, 2900, 64)])
 def test_gemm16_update(M, Nc, K):
     g = np.random.default_rng(M * 7 + Nc)
     A = g.uniform(-1, 1, (M, K)).astype(np.float16)
@@ -216,7 +217,7 @@ def test_gemm16_update(M, Nc, K):
     C = g.uniform(-4, 4, (M, Nc)).astype(np.float16)
     ld = lambda n: ((n + 63) // 64) * 64
     res = {}
-    for gemm in (1, 2):
+    for gemm in (1, 2, 3):
         Ad = torch.zeros((M, ld(K)), device=dev(), dtype=torch.float16)
         Bd = torch.zeros((K, ld(Nc)), device=dev(), dtype=torch.float16)
         Cd = torch.zeros((M, ld(Nc)), device=dev(), dtype=torch.float16)
@@ -235,6 +236,9 @@ def test_gemm16_update(M, Nc, K):
     exact = C.astype(np.float64) - A.astype(np.float64) @ B.astype(np.float64)
     tol = np.abs(exact) * 2.0 ** -10 + K * 2.0 ** -20 * 4
     assert np.all(np.abs(res[2].astype(np.float64) - exact) <= tol)
+    # the persistent pipelined kernel and the one-tile-per-CTA kernel issue the
+    # same MMAs and the same epilogue: bitwise the same
+    assert np.array_equal(res[2], res[3])
 
 
 # -------------------------------------------------------------- K4 / K7 --
