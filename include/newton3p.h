@@ -77,7 +77,11 @@ typedef struct {
                             co-schedule) for N <= 10240, else one launch of independent CTAs per
                             triangle that hand solved entries over global memory; 4, 8 or 16 caps
                             the cluster size (any N); -1 = always the global-memory hand-off */
-    int reserved[6];
+    int lu_stream;       /* [0 = auto] half-precision fast path: the diagonal block and the off-diagonal
+                            solves of a panel in one cooperative launch, the solves streaming one
+                            column behind the diagonal block (when its CTAs fit on the GPU at once);
+                            -1 = two launches per panel.  Bitwise the same factors either way */
+    int reserved[5];
 } nl_config;
 
 #define NL_MAX_HIST 128
@@ -374,7 +378,9 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
  * path: 0 = factor first without interchanges, checking exactly that partial
  * pivoting keeps every diagonal pivot, and refactor with interchanges from a
  * saved copy of A if not (same result either way); 1 = interchanging path
- * only.  Allocates its workspace (and the copy) with cudaMallocAsync on
+ * only; 2 = as 0 with the diagonal block and the off-diagonal solves of each
+ * panel in two launches instead of one streaming launch (same result).
+ * Allocates its workspace (and the copy) with cudaMallocAsync on
  * `stream`.  Synchronises the stream. */
 nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,
                   void* stream);

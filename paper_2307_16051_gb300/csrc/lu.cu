@@ -25,6 +25,7 @@
 // once per outer panel (when P is written back and when the trailing update
 // is stored).  With the SIMT trailing update this reproduces, operation for
 // operation, Gaussian elimination with that rounding schedule.
+#include <atomic>
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -852,9 +853,14 @@ __device__ __forceinline__ bool diag_wait(const int* f, int* failp)
     }
 }
 
+// PUB: also publish each finished column t to pub[t * 128 + i] as the 64-bit
+// word {epoch, value} (U above the diagonal, the unrounded pivot on it, the
+// multipliers below), for the streaming off-diagonal solves of k_panel16.
+template <bool PUB = false>
 __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t lda, int K, int w,
                                                int* __restrict__ ipiv, int* __restrict__ flag,
-                                               float* __restrict__ stage)
+                                               float* __restrict__ stage,
+                                               unsigned long long* __restrict__ pub = nullptr, unsigned epoch = 0)
 {
     if (*(volatile int*)flag) return;
     extern __shared__ __align__(16) float lsh[];  // lsh[t * 128 + i] = l_it (0 for i <= t)
@@ -957,6 +963,19 @@ __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t l
                 *reinterpret_cast<float4*>(&lsh[t * 128 + r0]) = make_float4(lv[0], lv[1], lv[2], lv[3]);
                 __syncwarp();
                 if (lane == 0) asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" :: "r"((unsigned)__cvta_generic_to_shared(&rdy[t])), "r"(1) : "memory");
+                if constexpr (PUB) {
+                    // column t is final: U entries (rounded) above the diagonal, p on it, l below
+                    unsigned long long wv[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int i = r0 + r;
+                        const float v = (i < t) ? a[r][kk] : ((i == t) ? p : lv[r]);
+                        wv[r] = ((unsigned long long)epoch << 32) | __float_as_uint(v);
+                    }
+                    unsigned long long* dst = pub + t * 128 + r0;
+                    asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(dst), "l"(wv[0]), "l"(wv[1]) : "memory");
+                    asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(dst + 2), "l"(wv[2]), "l"(wv[3]) : "memory");
+                }
                 float u[8];
 #pragma unroll
                 for (int c = kk + 1; c < 8; ++c) u[c] = round_h(__shfl_sync(0xffffffffu, a[kk & 3][c], src));
@@ -1035,6 +1054,271 @@ __global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict
                                                              float* __restrict__ stage)
 {
     diag_lu16_body(A, lda, K, w, ipiv, flag, stage);
+}
+
+// k_panel16: the diagonal block and the off-diagonal solves of one panel in
+// one cooperative launch.  CTA 0 factors the diagonal block (the column
+// pipeline above) and publishes every finished column t as {epoch, value}
+// words; the other CTAs stream behind it, one step per published column:
+//   row CTAs (256 rows of L21 each): row i at step t forms
+//     x_it - sum_{k<t} l_ik u_kt (the sum in increasing k, one fused
+//     multiply-add per term) from its own multipliers and U's column t, checks
+//     it against the unrounded pivot and forms l_it = fl16(x / u_tt);
+//   column CTAs (256 columns of U12 each): column j at step t forms
+//     u_tj = fl16(a_tj - sum_{k<t} l_tk u_kj) from its own U entries and row t
+//     of L11 (entry t of the published columns 0..t-1).
+// Every entry takes the same fused multiply-adds in the same order as in the
+// right-looking solves of k_offdiag16, so the results are bitwise those of
+// k_diag_lu16 followed by k_offdiag16; only the schedule differs (the
+// off-diagonal chains run one column behind the diagonal block instead of
+// after it).  A published word is its own ready flag (the epoch is unique per
+// launch and the buffer is cleared before each factorisation), so the
+// producer needs no fence.  Each CTA keeps its rows' (columns') 128 values in
+// shared memory; every wait is bounded and also gives up when the fast path
+// has been abandoned.  The launch is cooperative: all CTAs are co-resident.
+constexpr int kPnlThreads = 512;
+constexpr int kPnlRows = 256;   // at most this many rows (columns) per streaming CTA: one thread each
+constexpr int kPnlFetchW = 14;  // warps 14 and 15 fetch the published columns (even / odd t)
+constexpr int kPnlLd = 132;     // padded stride of the per-thread histories and the column cache (floats)
+constexpr size_t kPnlSmem = (size_t)kPnlRows * kPnlLd * 4 + (size_t)128 * kPnlLd * 4 + 128 * 8;
+constexpr long long kPnlSpin = 1LL << 22;
+
+// Fetch warp: copy published column t (all 128 entries, lane l: entries 4l..4l+3)
+// into the CTA's cache once its words carry this launch's epoch.  row_major:
+// cache[e * kPnlLd + t] (row e of the panel, column t), else cache[t * kPnlLd + e].
+__device__ __forceinline__ bool pnl_fetch(const unsigned long long* pub, int t, unsigned epoch, const int* flag,
+                                          float* cache, bool row_major, const int* gave_up)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long* q = pub + t * 128 + 4 * lane;
+    for (long long it = 0; it < kPnlSpin; ++it) {
+        unsigned long long v0, v1, v2, v3;
+        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(v0), "=l"(v1) : "l"(q) : "memory");
+        asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(v2), "=l"(v3) : "l"(q + 2) : "memory");
+        const bool ok = (unsigned)(v0 >> 32) == epoch && (unsigned)(v1 >> 32) == epoch &&
+                        (unsigned)(v2 >> 32) == epoch && (unsigned)(v3 >> 32) == epoch;
+        if (__all_sync(0xffffffffu, ok)) {
+            const float f[4] = {__uint_as_float((unsigned)v0), __uint_as_float((unsigned)v1),
+                                __uint_as_float((unsigned)v2), __uint_as_float((unsigned)v3)};
+            if (row_major) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) cache[(4 * lane + r) * kPnlLd + t] = f[r];
+            } else {
+                *reinterpret_cast<float4*>(cache + t * kPnlLd + 4 * lane) = make_float4(f[0], f[1], f[2], f[3]);
+            }
+            return true;
+        }
+        if ((it & 63) == 63 && (*(volatile const int*)flag || *(volatile const int*)gave_up)) return false;
+        __nanosleep(32);
+    }
+    return false;
+}
+
+__device__ __forceinline__ bool pnl_wait_ready(uint32_t bar, const int* gave_up)
+{
+    for (long long it = 0; it < kPnlSpin; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(bar)
+                     : "memory");
+        if (done) return true;
+        if (*(volatile const int*)gave_up) return false;
+    }
+    return false;
+}
+
+// Steps t .. t+NB-1 of one streaming row (column) at once: each history
+// value h[k], k < t, is loaded once for the NB dot products (shared-memory
+// traffic / NB), then the NB x NB tail in order.  Every entry still takes its
+// fused multiply-adds in increasing k.  c: the cache rows (ROWS: U's columns,
+// else L11's rows), c + j * kPnlLd the one for step t + j.
+template <bool ROWS, int NB>
+__device__ __forceinline__ void pnl_steps(float* __restrict__ h, const float* __restrict__ c, int t, bool* bad)
+{
+    float acc[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) acc[j] = h[t + j];
+    int k = 0;
+#pragma unroll 4
+    for (; k + 4 <= t; k += 4) {
+        const float4 l4 = *reinterpret_cast<const float4*>(h + k);
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const float4 c4 = *reinterpret_cast<const float4*>(c + j * kPnlLd + k);
+            acc[j] = fmaf(-l4.x, c4.x, acc[j]);
+            acc[j] = fmaf(-l4.y, c4.y, acc[j]);
+            acc[j] = fmaf(-l4.z, c4.z, acc[j]);
+            acc[j] = fmaf(-l4.w, c4.w, acc[j]);
+        }
+    }
+    for (; k < t; ++k) {
+        const float lk = h[k];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) acc[j] = fmaf(-lk, c[j * kPnlLd + k], acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+#pragma unroll
+        for (int jj = 0; jj < j; ++jj) acc[j] = fmaf(-h[t + jj], c[j * kPnlLd + t + jj], acc[j]);
+        if (ROWS) {
+            const float p = c[j * kPnlLd + t + j];
+            const float ut = round_h(p);
+            if (!(fabsf(acc[j]) <= fabsf(p))) *bad = true;
+            h[t + j] = div_round_h(acc[j], ut, __frcp_rn(ut));
+        } else {
+            h[t + j] = round_h(acc[j]);
+        }
+    }
+}
+
+__device__ __forceinline__ bool pnl_test_ready(uint32_t bar)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(done)
+                 : "r"(bar)
+                 : "memory");
+    return done != 0;
+}
+
+// One streaming CTA: ROWS = rows of L21 (cache = U's columns, cache[t][k] = u_kt,
+// entry t = the unrounded pivot), else columns of U12 (cache = L11 by rows,
+// cache[t][k] = l_tk).  Threads 0..255 each own one row (column) and its
+// 128-value history; warps 14 and 15 fetch the published columns; column t
+// is signalled through ready[t] (an mbarrier per column, used once).
+template <bool ROWS>
+__device__ __forceinline__ void panel16_stream(__half* __restrict__ A, int64_t lda, int K, int w, int N, int blk,
+                                               int rpc, __half* __restrict__ Ut, int ldut, int* __restrict__ flag,
+                                               const unsigned long long* __restrict__ pub, unsigned epoch,
+                                               unsigned* __restrict__ err)
+{
+    extern __shared__ __align__(16) float psm[];
+    float* H = psm;                          // H[r * kPnlLd + t]: a, replaced by l (rows) / u (columns) at step t
+    float* Cc = psm + kPnlRows * kPnlLd;     // the published columns
+    uint64_t* ready = reinterpret_cast<uint64_t*>(Cc + 128 * kPnlLd);
+    __shared__ int gave_up;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int idx = K + w + blk * rpc + tid;  // row (ROWS) or column of this thread
+    const bool mine = tid < rpc, live = mine && idx < N;
+    float* h = H + (mine ? tid : 0) * kPnlLd;
+    if (tid == 0) gave_up = 0;
+    if (tid < 128) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((unsigned)__cvta_generic_to_shared(&ready[tid])));
+    const bool vec = (w % 8 == 0) && (lda % 8 == 0) && ((((uintptr_t)(A + K)) & 15) == 0);
+    if (live) {
+        if (ROWS) {
+            const __half* R = A + (int64_t)idx * lda + K;
+            if (vec) {
+                for (int t = 0; t < w; t += 8) {
+                    const uint4 raw = *reinterpret_cast<const uint4*>(R + t);
+                    const __half* e = reinterpret_cast<const __half*>(&raw);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) h[t + q] = __half2float(e[q]);
+                }
+            } else {
+                for (int t = 0; t < w; ++t) h[t] = __half2float(R[t]);
+            }
+        } else {
+            for (int t = 0; t < w; ++t) h[t] = __half2float(A[(int64_t)(K + t) * lda + idx]);
+        }
+    }
+    __syncthreads();
+    bool bad = false;
+    if (warp >= kPnlFetchW) {
+        // fetchers: warp 14 the even columns, warp 15 the odd ones
+        const int f = warp - kPnlFetchW;
+        const int tmax = ROWS ? w : w - 1;  // the column CTAs never need the last column
+        for (int t = f; t < tmax; t += 2) {
+            if (!pnl_fetch(pub, t, epoch, flag, Cc, !ROWS, &gave_up)) {
+                *(volatile int*)&gave_up = 1;
+                break;
+            }
+            __syncwarp();
+            if ((tid & 31) == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((unsigned)__cvta_generic_to_shared(&ready[t]))
+                             : "memory");
+        }
+    } else if (mine) {
+        // rows need columns t..t+nb-1; columns need L11's rows t..t+nb-1, i.e. columns up to t+nb-2
+        const int lag = ROWS ? 0 : 1;
+        auto bar_of = [&](int col) { return (unsigned)__cvta_generic_to_shared(&ready[col]); };
+        for (int t = 0; t < w;) {
+            const int need = t - lag;
+            if (need >= 0 && !pnl_wait_ready(bar_of(need), &gave_up)) {
+                *(volatile int*)&gave_up = 1;
+                break;
+            }
+            // take up to four steps when their columns are already in (decided once per warp)
+            int nb = 1;
+            if ((threadIdx.x & 31) == 0)
+                while (nb < 4 && t + nb < w && (need + nb < 0 || pnl_test_ready(bar_of(need + nb)))) ++nb;
+            nb = __shfl_sync(0xffffffffu, nb, 0);
+            __syncwarp();  // lane 0's acquire of the extra columns orders the whole warp's reads
+            if (live) {
+                const float* c = Cc + t * kPnlLd;
+                switch (nb) {
+                case 4: pnl_steps<ROWS, 4>(h, c, t, &bad); break;
+                case 3: pnl_steps<ROWS, 3>(h, c, t, &bad); break;
+                case 2: pnl_steps<ROWS, 2>(h, c, t, &bad); break;
+                default: pnl_steps<ROWS, 1>(h, c, t, &bad); break;
+                }
+            }
+            t += nb;
+        }
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(flag, 1);
+    if (gave_up) {
+        if (tid == 0) {
+            // a timeout (not an abandoned fast path) is an error; either way the
+            // caller refactors with interchanges
+            if (!*(volatile const int*)flag) atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+            atomicOr(flag, 1);
+        }
+        return;
+    }
+    if (!live) return;
+    if (ROWS) {
+        __half* R = A + (int64_t)idx * lda + K;
+        if (vec) {
+            for (int t = 0; t < w; t += 8) {
+                __align__(16) __half e[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) e[q] = __float2half_rn(h[t + q]);
+                *reinterpret_cast<uint4*>(R + t) = *reinterpret_cast<const uint4*>(e);
+            }
+        } else {
+            for (int t = 0; t < w; ++t) R[t] = __float2half_rn(h[t]);
+        }
+    } else {
+        for (int t = 0; t < w; ++t) A[(int64_t)(K + t) * lda + idx] = __float2half_rn(h[t]);
+        if (Ut) {
+            __half* u0 = Ut + (int64_t)(idx - K - w) * ldut;
+            if ((w % 8 == 0) && (ldut % 8 == 0) && ((((uintptr_t)Ut) & 15) == 0)) {
+                for (int t = 0; t < w; t += 8) {
+                    __align__(16) __half e[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) e[q] = __float2half_rn(h[t + q]);
+                    *reinterpret_cast<uint4*>(u0 + t) = *reinterpret_cast<const uint4*>(e);
+                }
+            } else {
+                for (int t = 0; t < w; ++t) u0[t] = __float2half_rn(h[t]);
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPnlThreads, 1) k_panel16(__half* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                           int nrb, int rpc, int* __restrict__ ipiv, int* __restrict__ flag,
+                                                           float* __restrict__ stage, __half* __restrict__ Ut,
+                                                           int ldut, unsigned long long* __restrict__ pub,
+                                                           unsigned epoch, unsigned* __restrict__ err)
+{
+    if (blockIdx.x == 0)
+        diag_lu16_body<true>(A, lda, K, w, ipiv, flag, stage, pub, epoch);
+    else if ((int)blockIdx.x <= nrb)
+        panel16_stream<true>(A, lda, K, w, N, (int)blockIdx.x - 1, rpc, Ut, ldut, flag, pub, epoch, err);
+    else
+        panel16_stream<false>(A, lda, K, w, N, (int)blockIdx.x - 1 - nrb, rpc, Ut, ldut, flag, pub, epoch, err);
 }
 
 // k_offdiag16: L21 = A21 U11^{-1} (row role) and U12 = L11^{-1} A12 (column
@@ -1281,7 +1565,8 @@ size_t lu_work_bytes(int N, int nb, bool fp64)
     size_t el = fp64 ? 8 : 4;
     size_t pnl = (size_t)N * nb * el;
     size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
-    return round_up(pnl, 256) + round_up(ut, 256) + 256 + (size_t)2 * 128 * 128 * 8 + 128 * 8;
+    return round_up(pnl, 256) + round_up(ut, 256) + 256 + (size_t)2 * 128 * 128 * 8 + 128 * 8 +
+           (size_t)128 * 128 * 8;
 }
 
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
@@ -1297,6 +1582,8 @@ void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
     w->flag = w->info + 1;
     p += 256;
     w->stage = p;
+    p += (size_t)2 * 128 * 128 * 8 + 128 * 8;
+    w->pub = (unsigned long long*)p;
 }
 
 template <typename T, int NBL, int R, bool RND>
@@ -1419,6 +1706,65 @@ static nl_status trailing_update(int N, S* A, int64_t ld, int K, int wd, int nb,
     return launch_gemm_simt<S, T>(rest, rest, wd, L21, ld, U12, ld, A22, ld, st, flag);
 }
 
+// The streaming panel (k_panel16): one CTA for the diagonal block plus
+// ceil(rest / 256) CTAs for the rows of L21 and as many for the columns of
+// U12, all co-resident (cooperative launch); otherwise the two-launch path.
+static int panel16_max_ctas()
+{
+    static int cap = -1;
+    if (cap < 0) {
+        cap = 0;
+        int dev = 0, nsm = 0, coop = 0, per = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
+            set_max_dynamic_smem((const void*)k_panel16) == NL_OK &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_panel16, kPnlThreads, kPnlSmem) == cudaSuccess)
+            cap = per * nsm;
+        cudaGetLastError();
+    }
+    return cap;
+}
+
+// Rows (columns) per streaming CTA: 128 when the launch then fits on the GPU
+// (with 256 the full CTAs fall behind the diagonal block; 64 is no faster and
+// takes twice the SMs from concurrent solves), else 256; 0 when neither fits
+// (two launches instead).
+static int panel16_rows_per_cta(int rest)
+{
+    const int cap = panel16_max_ctas();
+    for (int rpc : {128, kPnlRows})
+        if (1 + 2 * (int)cdiv(rest, rpc) <= cap) return rpc;
+    return 0;
+}
+
+static std::atomic<unsigned> g_panel_epoch{0};
+
+static nl_status launch_panel16(__half* A, int64_t ld, int K, int wd, int N, int* ipiv, const LuWork& w, __half* Ut,
+                                int ldut, cudaStream_t st)
+{
+    const int rest = N - K - wd;
+    int rpc = panel16_rows_per_cta(rest);
+    int nrb = (int)cdiv(rest, rpc);
+    unsigned epoch = ++g_panel_epoch;
+    if (epoch == 0) epoch = ++g_panel_epoch;  // 0 is the cleared buffer's tag
+    int* flag = w.flag;
+    float* stage = (float*)w.stage;
+    unsigned long long* pub = w.pub;
+    unsigned* err = tc_error_word();
+    if (!err) err = (unsigned*)(w.info + 2);  // (a word of the info block nobody else uses)
+    int Kv = K, wv = wd, Nv = N, ldutv = ldut;
+    int64_t ldv = ld;
+    void* args[] = {(void*)&A, (void*)&ldv, (void*)&Kv, (void*)&wv, (void*)&Nv, (void*)&nrb, (void*)&rpc, (void*)&ipiv,
+                    (void*)&flag, (void*)&stage, (void*)&Ut, (void*)&ldutv, (void*)&pub, (void*)&epoch, (void*)&err};
+    prof_begin("k_panel16", st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_panel16, dim3(1 + 2 * nrb), dim3(kPnlThreads), args,
+                                                kPnlSmem, st);
+    prof_end("k_panel16", st);
+    NL_CUDA_OK(e);
+    return NL_OK;
+}
+
 template <typename T, typename S, int NBL, bool RND>
 static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int gemm, bool fast, const LuWork& w,
                                 cudaStream_t st, int* launches)
@@ -1442,6 +1788,7 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         }
         smem_set = true;
     }
+    bool pub_cleared = false;
     for (int K = 0; K < N; K += nb) {
         const int wd = std::min(nb, N - K), M = N - K;
         const int rest = N - K - wd;
@@ -1450,6 +1797,17 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         if (fast) {
             const int wp = (int)round_up(wd, 32);
             if constexpr (kHalf) {
+                if (rest > 0 && w.stream == 0 && panel16_rows_per_cta(rest) > 0) {
+                    if (!pub_cleared) {
+                        NL_CUDA_OK(cudaMemsetAsync(w.pub, 0, (size_t)128 * 128 * 8, st));
+                        pub_cleared = true;
+                    }
+                    NL_TRY(launch_panel16(A, ld, K, wd, N, ipiv, w, tc ? w.ut : nullptr, nb, st));
+                    nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
+                    if (s != NL_OK) return s;
+                    nl += 2;
+                    continue;
+                }
                 prof_begin("k_diag_lu16", st);
                 k_diag_lu16<<<1, kD16Threads, kDiag16Smem, st>>>(A, ld, K, wd, ipiv, w.flag, (float*)w.stage);
                 prof_end("k_diag_lu16", st);

@@ -423,6 +423,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 || d.lu_path < 0 ||
         d.lu_path > 1 || !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 ||
                            d.trsv_cluster == 8 || d.trsv_cluster == 16) ||
+        !(d.lu_stream == 0 || d.lu_stream == -1) ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
         d.lu_nb < -1) {
         set_error("nl_create: invalid configuration");
@@ -483,6 +484,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     lu_work_carve(cv.take<char>(lu_work_bytes(n, s->nb, false)), n, s->nb, false, &s->luw);
     trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &s->tw);
     s->tw.cluster = d.trsv_cluster;
+    s->luw.stream = d.lu_stream;
     if (cudaMallocHost((void**)&s->pin, 64) != cudaSuccess || cudaEventCreate(&s->ev[0]) != cudaSuccess ||
         cudaEventCreate(&s->ev[1]) != cudaSuccess) {
         cudaFree(s->pool);
@@ -869,6 +871,10 @@ static nl_status lu_entry(int64_t N, S* A, int64_t ld, int32_t* ipiv, int nb, in
     NL_CUDA_OK(cudaMallocAsync(&wk, lw + copy + 256, st));
     LuWork w;
     lu_work_carve(wk, n, nb, fp64, &w);
+    if (path == 2) {  // the fast path with two launches per panel (no streaming panel)
+        w.stream = -1;
+        path = 0;
+    }
     S* backup = (S*)((char*)wk + round_up(lw, 256));
     int iflag[2] = {0, 0};
     nl_status s = NL_OK;
@@ -913,7 +919,7 @@ extern "C" {
 nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,
                   void* stream)
 {
-    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2 || path < 0 || path > 1) {
+    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2 || path < 0 || path > 2) {
         set_error("nl_lu16: bad argument");
         return NL_EINVAL;
     }

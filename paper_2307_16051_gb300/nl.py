@@ -33,7 +33,8 @@ class Config(ctypes.Structure):
     _fields_ = [("eta_j", ctypes.c_double), ("ir_maxit", ctypes.c_int), ("gmres_restart", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_maxcycles", ctypes.c_int), ("newton_maxit", ctypes.c_int),
                 ("tau_a", ctypes.c_double), ("lu_nb", ctypes.c_int), ("trailing_gemm", ctypes.c_int),
-                ("lu_path", ctypes.c_int), ("trsv_cluster", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("lu_path", ctypes.c_int), ("trsv_cluster", ctypes.c_int), ("lu_stream", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class Stats(ctypes.Structure):

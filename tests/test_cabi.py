@@ -53,7 +53,8 @@ def test_invalid_arguments_rejected_before_device_use():
     assert L.nl_stats(None, None) == nl.NL_EINVAL
     assert "bad" in nl.last_error() or "NULL" in nl.last_error()
     L.nl_destroy(None)  # no-op
-    for bad in ({"trsv_cluster": 3}, {"trsv_cluster": -2}, {"trsv_cluster": 32}, {"lu_path": 2}):
+    for bad in ({"trsv_cluster": 3}, {"trsv_cluster": -2}, {"trsv_cluster": 32}, {"lu_path": 2}, {"lu_stream": 1},
+                {"lu_stream": -2}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
 
 

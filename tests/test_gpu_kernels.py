@@ -127,6 +127,24 @@ def test_lu16_simt_bit_exact_on_jacobian(N, nb):
         assert np.array_equal(ipiv, ipivo) and np.array_equal(LU, LUo), path
 
 
+@pytest.mark.parametrize("N,nb,gemm", [(1000, 128, 2), (4097, 128, 2), (700, 64, 1), (383, 96, 1)])
+def test_lu16_streaming_panel_equals_two_launches(N, nb, gemm):
+    """The streaming panel (one cooperative launch per panel, the off-diagonal
+    solves one column behind the diagonal block) and the two-launch panel do
+    the same fused multiply-adds in the same order: bitwise the same factors,
+    on the paper's Jacobian and on a matrix whose fast path fails late."""
+    c = 0.999
+    J16 = O.fl16(O.jacobian(N, c, np.ones(N)).astype(np.float32).astype(np.float64))
+    B, perm = W.pivot_forcing_matrix(min(N, 600), 17, margin=4.0)
+    B = B[np.argsort(perm)]
+    B[[B.shape[0] - 40, B.shape[0] - 30]] = B[[B.shape[0] - 30, B.shape[0] - 40]]
+    for M in (J16, O.fl16(B)):
+        res = [_lu16_gpu(M, nb, gemm, path) for path in (0, 2)]
+        assert np.array_equal(res[0][1], res[1][1])
+        assert np.array_equal(res[0][0], res[1][0])
+        assert res[0][2] == res[1][2]
+
+
 def test_lu16_fast_path_detects_late_interchange():
     """A matrix that needs exactly one interchange deep inside: the fast
     path must detect it and the result must equal the oracle's."""

@@ -134,6 +134,19 @@ def test_trsv_variants_agree(mode):
     assert np.array_equal(res[4], res[8]) and np.array_equal(res[8], res[16]) and np.array_equal(res[16], res[0])
 
 
+@pytest.mark.parametrize("mode", ["IR16", "GMRESIR16"])
+def test_streaming_panel_agrees(mode):
+    """One streaming launch per panel (lu_stream = 0) and two launches per
+    panel (-1) give the same factors, so the whole solve is bitwise the same."""
+    res = []
+    for st in (0, -1):
+        with nl.Solver(2100, 0.9999, lu_stream=st) as s:
+            x, status = s.solve(mode=mode)
+            assert status == nl.NL_OK
+            res.append(x)
+    assert np.array_equal(res[0], res[1])
+
+
 def test_repeatable_bitwise():
     with nl.Solver(700, 0.99) as s:
         a, _ = s.solve(mode="GMRESIR16")
