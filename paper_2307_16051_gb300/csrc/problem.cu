@@ -187,37 +187,42 @@ nl_status launch_residual_g(const BInst* inst, BState* st, const BTask* tasks, i
 // the single-rounded h[i+j] and the subtraction are one single-precision FMA.
 constexpr int kJCols = 8;
 
+// One CTA per 256 columns x 32 rows: the 287 Hankel entries the tile needs are
+// converted to single once into shared memory, and each row's factor
+// w_i = c/(2N) r_i^2 (i + 1/2) once per row; every thread then writes its
+// column of the 32 rows (coalesced rows of J32 and J16).  Per entry the value
+// is fma(-w_i, fl32(h_{i+j}), [i == j]), rounded once more for J16.
+constexpr int kJRows = 32;
 __global__ void __launch_bounds__(256) k_jacobian(int N, double c, const double* __restrict__ rr,
                                                   const double* __restrict__ htab, float* __restrict__ J32,
                                                   int64_t ld32, __half* __restrict__ J16, int64_t ld16,
                                                   int ldmax)
 {
-    const int i = blockIdx.y;
-    const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * kJCols;
-    if (j0 >= ldmax) return;
-    const double ri = rr[i];
-    const float w = (float)(c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5));
-    float v[kJCols];
-#pragma unroll
-    for (int t = 0; t < kJCols; ++t) {
-        int j = j0 + t;
-        float e = 0.0f;
-        if (j < N) {
-            float h = (float)htab[i + j];
-            e = fmaf(-w, h, (i == j) ? 1.0f : 0.0f);
+    __shared__ float hw[256 + kJRows];
+    __shared__ float wr[kJRows];
+    const int i0 = blockIdx.y * kJRows, j0 = blockIdx.x * 256;
+    for (int q = threadIdx.x; q < 256 + kJRows; q += 256) {
+        const int k = i0 + j0 + q;
+        hw[q] = (k < 2 * N - 1) ? (float)htab[k] : 0.0f;
+    }
+    if (threadIdx.x < kJRows) {
+        const int i = i0 + threadIdx.x;
+        float w = 0.0f;
+        if (i < N) {
+            const double ri = rr[i];
+            w = (float)(c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5));
         }
-        v[t] = e;
+        wr[threadIdx.x] = w;
     }
-    if (J32 && j0 < ld32) {
-        float4* p = reinterpret_cast<float4*>(J32 + (int64_t)i * ld32 + j0);
-        p[0] = make_float4(v[0], v[1], v[2], v[3]);
-        p[1] = make_float4(v[4], v[5], v[6], v[7]);
-    }
-    if (J16 && j0 < ld16) {
-        __align__(16) __half h[kJCols];
-#pragma unroll
-        for (int t = 0; t < kJCols; ++t) h[t] = __float2half_rn(v[t]);
-        *reinterpret_cast<uint4*>(J16 + (int64_t)i * ld16 + j0) = *reinterpret_cast<uint4*>(h);
+    __syncthreads();
+    const int j = j0 + threadIdx.x;
+    if (j >= ldmax) return;
+    const int rows = min(kJRows, N - i0);
+    for (int r = 0; r < rows; ++r) {
+        const int i = i0 + r;
+        const float e = (j < N) ? fmaf(-wr[r], hw[r + threadIdx.x], (i == j) ? 1.0f : 0.0f) : 0.0f;
+        if (J32 && j < ld32) J32[(int64_t)i * ld32 + j] = e;
+        if (J16 && j < ld16) J16[(int64_t)i * ld16 + j] = __float2half_rn(e);
     }
 }
 
@@ -229,7 +234,7 @@ nl_status launch_jacobian(int N, double c, const double* rr, const double* htab,
         return NL_EINVAL;
     }
     int ldmax = (int)std::max(J32 ? ld32 : 0, J16 ? ld16 : 0);
-    dim3 grid((unsigned)cdiv(cdiv(ldmax, kJCols), 256), (unsigned)N);
+    dim3 grid((unsigned)cdiv(ldmax, 256), (unsigned)cdiv(N, kJRows));
     k_jacobian<<<grid, 256, 0, st>>>(N, c, rr, htab, J32, ld32, J16, ld16, ldmax);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;

@@ -556,7 +556,32 @@ void trsv_work_carve(void* base, int N, bool fp64, TrsvWork* w)
     w->scan = (int*)p;
 }
 
-// Diagonal-block inverses for block size TB.
+// Diagonal-block inverses for block size TB, one thread per column, both
+// right-looking: once X's row t of the column is final, it is applied to every
+// later row, so the loop over rows has no dependence chain.  L (unit lower):
+// entry i of column c is -sum_{t=c}^{i-1} l_it x_t with the terms added in
+// increasing t, x_c = 1.  U: x_t = s_t / u_tt with s_i = [i == c] -
+// sum_{t>i} u_it x_t, the terms added in decreasing t.  Entries outside the
+// block (a ragged last block) are zero.
+// x[i] <- fma(a[i], y, x[i]) for rows i in [i0, i1) of one column (stride TB + 1);
+// rows in groups of four so the shared-memory loads run ahead of the stores.
+// fma(a, -y, x) is the same operation as fma(-a, y, x).
+template <typename T, int TB>
+__device__ __forceinline__ void axpy_col(const T* __restrict__ a, T* __restrict__ x, int i0, int i1, T y)
+{
+    constexpr int S = TB + 1;
+    int i = i0;
+    for (; i + 4 <= i1; i += 4) {
+        const T a0 = a[i * S], a1 = a[(i + 1) * S], a2 = a[(i + 2) * S], a3 = a[(i + 3) * S];
+        const T x0 = x[i * S], x1 = x[(i + 1) * S], x2 = x[(i + 2) * S], x3 = x[(i + 3) * S];
+        x[i * S] = fma(a0, y, x0);
+        x[(i + 1) * S] = fma(a1, y, x1);
+        x[(i + 2) * S] = fma(a2, y, x2);
+        x[(i + 3) * S] = fma(a3, y, x3);
+    }
+    for (; i < i1; ++i) x[i * S] = fma(a[i * S], y, x[i * S]);
+}
+
 template <typename S, typename T, int TB>
 __global__ void __launch_bounds__(TB) k_invdiag_t(int N, const S* __restrict__ LU, int64_t ld, T* __restrict__ dinv,
                                                   int nblk)
@@ -566,34 +591,111 @@ __global__ void __launch_bounds__(TB) k_invdiag_t(int N, const S* __restrict__ L
     T* X = A + TB * (TB + 1);
     const int b = blockIdx.x, r0 = b * TB, nb_ = min(TB, N - r0);
     const int col = threadIdx.x;
+    T* x = X + col;  // this thread's column: x[i * (TB + 1)]
     for (int i = 0; i < TB; ++i)
         A[i * (TB + 1) + col] = (i < nb_ && col < nb_) ? (T)ld_elem(LU + (int64_t)(r0 + i) * ld + r0 + col) : T(0);
+    for (int i = 0; i < TB; ++i) x[i * (TB + 1)] = T(0);
     __syncthreads();
-    for (int i = 0; i < TB; ++i) {
-        T x = T(0);
-        if (col < nb_ && i < nb_) {
-            if (i == col) x = T(1);
-            else if (i > col) {
-                T s = T(0);
-                for (int t = col; t < i; ++t) s = fma(A[i * (TB + 1) + t], X[t * (TB + 1) + col], s);
-                x = -s;
-            }
-        }
-        X[i * (TB + 1) + col] = x;
+    // L^{-1}
+    for (int t = 0; t < nb_; ++t) {
+        if (t < col || col >= nb_) continue;
+        const T xt = (t == col) ? T(1) : -x[t * (TB + 1)];
+        x[t * (TB + 1)] = xt;
+        axpy_col<T, TB>(A + t, x, t + 1, nb_, xt);
     }
     T* Linv = dinv + (int64_t)b * TB * TB;
-    for (int i = 0; i < TB; ++i) Linv[i * TB + col] = X[i * (TB + 1) + col];
-    for (int i = TB - 1; i >= 0; --i) {
-        T x = T(0);
-        if (col < nb_ && i < nb_ && i <= col) {
-            T s = (i == col) ? T(1) : T(0);
-            for (int t = i + 1; t <= col; ++t) s = fma(-A[i * (TB + 1) + t], X[t * (TB + 1) + col], s);
-            x = s / A[i * (TB + 1) + i];
-        }
-        X[i * (TB + 1) + col] = x;
+    for (int i = 0; i < TB; ++i) Linv[i * TB + col] = x[i * (TB + 1)];
+    // U^{-1}
+    for (int i = 0; i < TB; ++i) x[i * (TB + 1)] = (i == col && col < nb_) ? T(1) : T(0);
+    for (int t = nb_ - 1; t >= 0; --t) {
+        if (t > col || col >= nb_) continue;
+        const T xt = x[t * (TB + 1)] / A[t * (TB + 1) + t];
+        x[t * (TB + 1)] = xt;
+        axpy_col<T, TB>(A + t, x, 0, t, -xt);
     }
     T* Uinv = dinv + (int64_t)(nblk + b) * TB * TB;
-    for (int i = 0; i < TB; ++i) Uinv[i * TB + col] = X[i * (TB + 1) + col];
+    for (int i = 0; i < TB; ++i) Uinv[i * TB + col] = x[i * (TB + 1)];
+}
+
+// The binary16 factors' 128 x 128 diagonal-block inverses, the same
+// right-looking recurrences as k_invdiag_t with the column in registers:
+// four threads per column (lane = 4 x column-in-warp + quarter), thread q
+// holding rows 32q..32q+31.  At step t the thread holding row t finalises it
+// and passes x_t to the column's other three threads with one shuffle; every
+// thread then applies x_t to all 32 of its rows with the block's column t
+// (staged transposed in shared memory with the entries the step must not
+// touch — on and above the diagonal for L, on and below it for U — set to
+// zero, so the update needs no per-row test and leaves them unchanged).
+constexpr int kInvThreads = 512;
+constexpr int kInvS = 148;  // transposed column stride (floats): quarters 36 apart; 148 t mod 32 spreads the staging stores
+constexpr size_t kInvSmem = (size_t)T2 * kInvS * sizeof(float) + T2 * sizeof(float);
+
+template <bool UPPER>
+__device__ __forceinline__ void invdiag16_pass(const __half* __restrict__ LU, int64_t ld, float* __restrict__ D, int r0,
+                                               int nb_)
+{
+    extern __shared__ __align__(16) float inv_sm[];
+    float* At = inv_sm;             // At[t * kInvS + 36 q + r]: entry (32 q + r, t)
+    float* dg = inv_sm + T2 * kInvS;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int col = warp * 8 + (lane >> 2), q = lane & 3;
+    for (int e = tid; e < T2 * T2; e += kInvThreads) {
+        const int i = e / T2, t = e % T2;  // row i, column t of the block
+        float a = 0.0f;
+        if (i < nb_ && t < nb_) {
+            const float v = __half2float(LU[(int64_t)(r0 + i) * ld + r0 + t]);
+            if (UPPER ? (i < t) : (i > t)) a = UPPER ? -v : v;
+            if (i == t) dg[t] = v;
+        }
+        At[t * kInvS + 36 * (i >> 5) + (i & 31)] = a;
+    }
+    __syncthreads();
+    float acc[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc[r] = (UPPER && 32 * q + r == col && col < nb_) ? 1.0f : 0.0f;
+    for (int s = 0; s < T2 / 32; ++s) {
+        const int tq = UPPER ? 3 - s : s;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const int tt = UPPER ? 31 - k : k;
+            const int t = 32 * tq + tt;
+            float xt = 0.0f;
+            if (q == tq && col < nb_ && t < nb_) {
+                if (UPPER)
+                    xt = (t > col) ? 0.0f : acc[tt] / dg[t];
+                else
+                    xt = (t < col) ? 0.0f : ((t == col) ? 1.0f : -acc[tt]);
+                acc[tt] = xt;
+            }
+            xt = __shfl_sync(0xffffffffu, xt, (lane & ~3) | tq);
+            const float4* a4 = reinterpret_cast<const float4*>(At + t * kInvS + 36 * q);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const float4 v = a4[g];
+                acc[4 * g] = fmaf(v.x, xt, acc[4 * g]);
+                acc[4 * g + 1] = fmaf(v.y, xt, acc[4 * g + 1]);
+                acc[4 * g + 2] = fmaf(v.z, xt, acc[4 * g + 2]);
+                acc[4 * g + 3] = fmaf(v.w, xt, acc[4 * g + 3]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) D[(32 * q + r) * T2 + col] = acc[r];
+}
+
+// CTA b < nblk: L^{-1} of block b; CTA nblk + b: U^{-1} of block b (U's
+// entries are staged negated, so both updates are fma(a, x_t, acc)).
+__global__ void __launch_bounds__(kInvThreads) k_invdiag16(int N, const __half* __restrict__ LU, int64_t ld,
+                                                           float* __restrict__ dinv, int nblk)
+{
+    const bool upper = (int)blockIdx.x >= nblk;
+    const int b = upper ? (int)blockIdx.x - nblk : (int)blockIdx.x;
+    const int r0 = b * T2, nb_ = min(T2, N - r0);
+    float* D = dinv + (int64_t)blockIdx.x * T2 * T2;
+    if (upper)
+        invdiag16_pass<true>(LU, ld, D, r0, nb_);
+    else
+        invdiag16_pass<false>(LU, ld, D, r0, nb_);
 }
 
 template <typename S, typename T>
@@ -606,7 +708,8 @@ static nl_status prepare_impl(int N, const S* LU, int64_t ld, const int* ipiv, c
     static bool attr = false;
     if (!attr) {
         if (set_max_dynamic_smem((const void*)k_perm) != NL_OK ||
-            set_max_dynamic_smem((const void*)k_invdiag_t<S, T, TB>) != NL_OK)
+            set_max_dynamic_smem((const void*)k_invdiag_t<S, T, TB>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_invdiag16) != NL_OK)
             return NL_ECUDA;
         attr = true;
     }
@@ -615,7 +718,12 @@ static nl_status prepare_impl(int N, const S* LU, int64_t ld, const int* ipiv, c
         return NL_EINVAL;
     }
     k_perm<<<1, 1024, (size_t)N * 4, st>>>(N, ipiv, w.perm, w.scan);
-    k_invdiag_t<S, T, TB><<<nblk, TB, (size_t)2 * TB * (TB + 1) * sizeof(T), st>>>(N, LU, ld, (T*)w.dinv, nblk);
+    prof_begin("k_invdiag", st);
+    if constexpr (std::is_same<S, __half>::value && !fp64)
+        k_invdiag16<<<2 * nblk, kInvThreads, kInvSmem, st>>>(N, LU, ld, (float*)w.dinv, nblk);
+    else
+        k_invdiag_t<S, T, TB><<<nblk, TB, (size_t)2 * TB * (TB + 1) * sizeof(T), st>>>(N, LU, ld, (T*)w.dinv, nblk);
+    prof_end("k_invdiag", st);
     NL_CUDA_OK(cudaGetLastError());
     if (launches) *launches += 2;
     return NL_OK;
