@@ -374,6 +374,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--lu-nb", type=int, default=0, help="LU outer block (0: library default)")
+    ap.add_argument("--lu-stream", type=int, default=0,
+                    help="panel launch: 0 library default, 256 streaming CTAs of 256 rows, -1 two launches")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched workload")
     ap.add_argument("--no-large", action="store_true", help="skip the N=32768 single solve")
     ap.add_argument("--large-fp64", action="store_true", help="also time FP64-LU Newton at N=32768 (minutes)")
@@ -402,7 +404,7 @@ def main():
     # latency: its stream gets the highest priority (lower number = higher).
     order = sorted(SWEEP)
     streams = {c: torch.cuda.Stream(device=dev, priority=-order.index(c)) for c in SWEEP}
-    solvers = {c: nl.Solver(N_BENCH, c, stream=streams[c], lu_nb=args.lu_nb) for c in SWEEP}
+    solvers = {c: nl.Solver(N_BENCH, c, stream=streams[c], lu_nb=args.lu_nb, lu_stream=args.lu_stream) for c in SWEEP}
     xdev = {c: torch.empty(N_BENCH, device=dev, dtype=torch.float64) for c in SWEEP}
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
     import concurrent.futures as cf

@@ -79,8 +79,10 @@ typedef struct {
                             the cluster size (any N); -1 = always the global-memory hand-off */
     int lu_stream;       /* [0 = auto] half-precision fast path: the diagonal block and the off-diagonal
                             solves of a panel in one cooperative launch, the solves streaming one
-                            column behind the diagonal block (when its CTAs fit on the GPU at once);
-                            -1 = two launches per panel.  Bitwise the same factors either way */
+                            column behind the diagonal block (when its CTAs fit on the GPU at once),
+                            128 rows per CTA where possible; 256 = the same with 256 rows per CTA
+                            (half the SMs, for solves that share the GPU); -1 = two launches per
+                            panel.  Bitwise the same factors in every case */
     int reserved[5];
 } nl_config;
 

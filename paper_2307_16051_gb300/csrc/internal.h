@@ -29,7 +29,8 @@ struct LuWork {
     int* flag = nullptr;      // device int (info + 1): set when the no-interchange fast path failed
     void* stage = nullptr;    // diagonal-block factors staged for the off-diagonal solves (<= 256 KB)
     unsigned long long* pub = nullptr;  // 128 x 128 {epoch, value} words: columns published by k_panel16
-    int stream = 0;           // binary16 fast path: 0 = one streaming launch per panel when it fits, -1 = two launches
+    int stream = 0;           // binary16 fast path: 0 = one streaming launch per panel when it fits (128 rows per
+                              // CTA when possible), 256 = the same with 256 rows per CTA, -1 = two launches
 };
 size_t lu_work_bytes(int N, int nb, bool fp64);
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w);

@@ -1730,10 +1730,10 @@ static int panel16_max_ctas()
 // (with 256 the full CTAs fall behind the diagonal block; 64 is no faster and
 // takes twice the SMs from concurrent solves), else 256; 0 when neither fits
 // (two launches instead).
-static int panel16_rows_per_cta(int rest)
+static int panel16_rows_per_cta(int rest, int pref = 0)
 {
     const int cap = panel16_max_ctas();
-    for (int rpc : {128, kPnlRows})
+    for (int rpc : {pref == kPnlRows ? kPnlRows : 128, kPnlRows})
         if (1 + 2 * (int)cdiv(rest, rpc) <= cap) return rpc;
     return 0;
 }
@@ -1744,7 +1744,7 @@ static nl_status launch_panel16(__half* A, int64_t ld, int K, int wd, int N, int
                                 int ldut, cudaStream_t st)
 {
     const int rest = N - K - wd;
-    int rpc = panel16_rows_per_cta(rest);
+    int rpc = panel16_rows_per_cta(rest, w.stream);
     int nrb = (int)cdiv(rest, rpc);
     unsigned epoch = ++g_panel_epoch;
     if (epoch == 0) epoch = ++g_panel_epoch;  // 0 is the cleared buffer's tag
@@ -1797,7 +1797,7 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         if (fast) {
             const int wp = (int)round_up(wd, 32);
             if constexpr (kHalf) {
-                if (rest > 0 && w.stream == 0 && panel16_rows_per_cta(rest) > 0) {
+                if (rest > 0 && w.stream >= 0 && panel16_rows_per_cta(rest, w.stream) > 0) {
                     if (!pub_cleared) {
                         NL_CUDA_OK(cudaMemsetAsync(w.pub, 0, (size_t)128 * 128 * 8, st));
                         pub_cleared = true;

@@ -423,7 +423,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 || d.lu_path < 0 ||
         d.lu_path > 1 || !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 ||
                            d.trsv_cluster == 8 || d.trsv_cluster == 16) ||
-        !(d.lu_stream == 0 || d.lu_stream == -1) ||
+        !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
         d.lu_nb < -1) {
         set_error("nl_create: invalid configuration");

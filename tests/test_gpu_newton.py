@@ -139,12 +139,12 @@ def test_streaming_panel_agrees(mode):
     """One streaming launch per panel (lu_stream = 0) and two launches per
     panel (-1) give the same factors, so the whole solve is bitwise the same."""
     res = []
-    for st in (0, -1):
+    for st in (0, -1, 256):
         with nl.Solver(2100, 0.9999, lu_stream=st) as s:
             x, status = s.solve(mode=mode)
             assert status == nl.NL_OK
             res.append(x)
-    assert np.array_equal(res[0], res[1])
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
 
 
 def test_repeatable_bitwise():
