@@ -269,6 +269,7 @@ struct nl_solver {
     int gemm = 2;
     nl_stats_t stats;
     cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaEvent_t evp[6] = {};  // per-step phase timing (Jacobian, factorisation, linear solve), read once per step
     int tune_count = 0;
     int tune_nb[4] = {0, 0, 0, 0};
     float tune_ms[4] = {0, 0, 0, 0};
@@ -485,7 +486,9 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &s->tw);
     s->tw.cluster = d.trsv_cluster;
     s->luw.stream = d.lu_stream;
-    if (cudaMallocHost((void**)&s->pin, 64) != cudaSuccess || cudaEventCreate(&s->ev[0]) != cudaSuccess ||
+    bool evs_ok = true;
+    for (auto& e : s->evp) evs_ok = evs_ok && cudaEventCreate(&e) == cudaSuccess;
+    if (!evs_ok || cudaMallocHost((void**)&s->pin, 64) != cudaSuccess || cudaEventCreate(&s->ev[0]) != cudaSuccess ||
         cudaEventCreate(&s->ev[1]) != cudaSuccess) {
         cudaFree(s->pool);
         delete s;
@@ -551,6 +554,8 @@ void nl_destroy(nl_solver* s)
     if (s->pin) cudaFreeHost(s->pin);
     if (s->ev[0]) cudaEventDestroy(s->ev[0]);
     if (s->ev[1]) cudaEventDestroy(s->ev[1]);
+    for (auto& e : s->evp)
+        if (e) cudaEventDestroy(e);
     delete s;
 }
 
@@ -586,23 +591,38 @@ static float elapsed_ms(nl_solver* s)
     return ms;
 }
 
-static nl_status check_device_errors(nl_solver* s)
+static float pair_ms(cudaEvent_t a, cudaEvent_t b)
 {
-    unsigned e[2] = {0, 0};
-    cudaMemcpyAsync(&e[0], s->tw.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st);
-    if (s->tw64.err) cudaMemcpyAsync(&e[1], s->tw64.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st);
-    NL_CUDA_OK(cudaStreamSynchronize(s->st));
-    unsigned* tce = tc_error_word();
-    unsigned e3 = 0;
-    if (tce) {
-        NL_CUDA_OK(cudaMemcpyAsync(&e3, tce, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
-        NL_CUDA_OK(cudaStreamSynchronize(s->st));
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.0f;
     }
-    if (e[0] | e[1] | e3) {
-        set_error("a device-side bounded wait gave up (error word 0x%x/0x%x/0x%x)", e[0], e[1], e3);
+    return ms;
+}
+
+// The residual norm of the new iterate and the device error words in one
+// round trip; an error word set by a bounded wait that gave up is cleared and
+// reported as NL_ETIMEOUT.
+static nl_status read_step_end(nl_solver* s, const double* fn_dev, double* fn)
+{
+    char* p = reinterpret_cast<char*>(s->pin);
+    unsigned* tce = tc_error_word();
+    NL_CUDA_OK(cudaMemcpyAsync(p, fn_dev, sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    memset(p + 8, 0, 12);
+    NL_CUDA_OK(cudaMemcpyAsync(p + 8, s->tw.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    if (s->tw64.err) NL_CUDA_OK(cudaMemcpyAsync(p + 12, s->tw64.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    if (tce) NL_CUDA_OK(cudaMemcpyAsync(p + 16, tce, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    NL_CUDA_OK(cudaStreamSynchronize(s->st));
+    memcpy(fn, p, sizeof(double));
+    unsigned e[3];
+    memcpy(e, p + 8, sizeof(e));
+    if (e[0] | e[1] | e[2]) {
+        set_error("a device-side bounded wait gave up (error word 0x%x/0x%x/0x%x)", e[0], e[1], e[2]);
         cudaMemsetAsync(s->tw.err, 0, sizeof(unsigned), s->st);
         if (s->tw64.err) cudaMemsetAsync(s->tw64.err, 0, sizeof(unsigned), s->st);
         if (tce) cudaMemsetAsync(tce, 0, sizeof(unsigned), s->st);
+        cudaStreamSynchronize(s->st);
         return NL_ETIMEOUT;
     }
     return NL_OK;
@@ -658,17 +678,16 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             break;
         }
         if (it >= s->cfg.newton_maxit) break;
-        // Jacobian
-        cudaEventRecord(s->ev[0], st);
+        // Jacobian (the phases' times are read after the step's one synchronisation)
+        cudaEventRecord(s->evp[0], st);
         if (mode == NL_FP64LU)
             NL_TRY(launch_jacobian64(n, s->c, s->rr, s->htab, s->J64, s->ld, st));
         else
             NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st));
-        cudaEventRecord(s->ev[1], st);
+        cudaEventRecord(s->evp[1], st);
         ++launches;
-        S.t_jac_ms += elapsed_ms(s);
         // factorisation
-        cudaEventRecord(s->ev[0], st);
+        cudaEventRecord(s->evp[2], st);
         int info = 0, iflag[2] = {0, 0};
         const bool pivoted_only = s->cfg.lu_path == 1;
         if (mode == NL_FP64LU) {
@@ -685,8 +704,11 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             }
             NL_TRY(trsv_prepare64(n, s->J64, s->ld, s->ipiv64, s->tw64, st, &launches));
         } else {
+            // the fast path's outcome is read once, after the triangular solves' set-up
+            // has been queued behind it (redone below in the rare case of interchanges)
             NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, !pivoted_only, s->luw, st, &launches));
             NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
             NL_CUDA_OK(cudaStreamSynchronize(st));
             memcpy(iflag, s->pin, sizeof(iflag));
             if (iflag[1]) {
@@ -695,20 +717,19 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
                 NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
                 ++launches;
                 ++S.lu_pivoted;
+                NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
             }
-            NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
         }
-        cudaEventRecord(s->ev[1], st);
+        cudaEventRecord(s->evp[3], st);
         NL_CUDA_OK(cudaStreamSynchronize(st));
         memcpy(&info, s->pin, sizeof(int));
-        S.t_lu_ms += elapsed_ms(s);
         if (info != 0) {
             status = NL_ESINGULAR;
             set_error("zero pivot at column %d", info);
             break;
         }
         // linear solve for the scaled step
-        cudaEventRecord(s->ev[0], st);
+        cudaEventRecord(s->evp[4], st);
         const void* ustep;
         int u_is_double = 0;
         if (mode == NL_FP64LU) {
@@ -742,18 +763,19 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             S.lin_relres[it] = lr.relres;
             ustep = s->u;
         }
-        cudaEventRecord(s->ev[1], st);
-        // x_{n+1} = x_n + ||F|| u, fused with F(x_{n+1})
+        cudaEventRecord(s->evp[5], st);
+        // x_{n+1} = x_n + ||F|| u, fused with F(x_{n+1}); its norm and the device error
+        // words come back with the step's one synchronisation
         NL_TRY(launch_residual(n, s->c, x, ustep, u_is_double, fn, s->htab, xn, s->F, s->rr, s->partial, s->counter,
                                fn_dev, st));
         ++launches;
-        S.t_lin_ms += elapsed_ms(s);
-        cudaEventRecord(s->ev[0], st);
-        fn = H.read(fn_dev);
+        nl_status e = read_step_end(s, fn_dev, &fn);
+        S.t_jac_ms += pair_ms(s->evp[0], s->evp[1]);
+        S.t_lu_ms += pair_ms(s->evp[2], s->evp[3]);
+        S.t_lin_ms += pair_ms(s->evp[4], s->evp[5]);
         std::swap(x, xn);
         ++it;
         S.hist[it] = f0 > 0.0 ? fn / f0 : 0.0;
-        nl_status e = check_device_errors(s);
         if (e != NL_OK) return e;
     }
     if (fn <= tau) status = NL_OK;
