@@ -271,13 +271,29 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-__global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap tmA,
-                                                            const __grid_constant__ CUtensorMap tmB,
-                                                            const __grid_constant__ CUtensorMap tmC, int M, int Nc,
-                                                            int K, unsigned* __restrict__ err,
-                                                            const int* __restrict__ flag)
+// Where tile `it` of a persistent CTA reads and writes: the A slabs at
+// (ax + 64 kt, ay) of map a, the B slabs at (64 kt, by) of map b, the C tile's
+// two boxes at (cx + 64 j, cy) of map c; `store` is false for a matrix whose
+// factorisation has been abandoned (its tile is computed but not written).
+struct TileRef {
+    const CUtensorMap *a, *b, *c;
+    int ax, ay, by, cx, cy;
+    bool store;
+};
+
+// Single update: the maps are kernel parameters (tmA, tmB, tmC), tiles in
+// row-major order over the M x Nc output.  Grouped update: task t of the
+// step's list is {instance, m0, n0} of that instance's A22 (rows and columns
+// from K + w), read through the instance's whole-matrix map (A and C) and
+// its U12^T map (B); rows and columns past the instance's N read as zero and
+// are not stored.
+template <bool GROUPED>
+__device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                                   const CUtensorMap* tmC, int M, int Nc, int K,
+                                                   const GInst* __restrict__ ginst, const TmapBytes* __restrict__ gmaps,
+                                                   const GTask* __restrict__ gtasks, int ntasks, int gK, int gw,
+                                                   unsigned* __restrict__ err)
 {
-    if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;
@@ -292,17 +308,37 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
     __shared__ int aborted;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = (Nc + kTcBN - 1) / kTcBN;
-    const int ntiles = tiles_n * ((M + kTcBM - 1) / kTcBM);
+    const int ntiles = GROUPED ? ntasks : tiles_n * ((M + kTcBM - 1) / kTcBM);
     const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto bar = [&](int k) { return smem_u32(&bars[k]); };
     auto fail = [&]() {
         atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
         *(volatile int*)&aborted = 1;
     };
-    auto tile_mn = [&](int it, int* m0, int* n0) {
+    auto ref = [&](int it) {
         const int tile = blockIdx.x + it * gridDim.x;
-        *m0 = (tile / tiles_n) * kTcBM;
-        *n0 = (tile % tiles_n) * kTcBN;
+        TileRef r;
+        if constexpr (GROUPED) {
+            const GTask t = gtasks[tile];
+            r.a = r.c = reinterpret_cast<const CUtensorMap*>(&gmaps[2 * t.inst]);
+            r.b = reinterpret_cast<const CUtensorMap*>(&gmaps[2 * t.inst + 1]);
+            r.ax = gK;
+            r.ay = r.cy = gK + gw + t.a;
+            r.by = t.b;
+            r.cx = gK + gw + t.b;
+            r.store = *(volatile const int*)ginst[t.inst].flag == 0;
+        } else {
+            const int m0 = (tile / tiles_n) * kTcBM, n0 = (tile % tiles_n) * kTcBN;
+            r.a = tmA;
+            r.b = tmB;
+            r.c = tmC;
+            r.ax = 0;
+            r.ay = r.cy = m0;
+            r.by = n0;
+            r.cx = n0;
+            r.store = true;
+        }
+        return r;
     };
 
     if (warp == 0) {
@@ -339,14 +375,13 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
                     fail();
                     break;
                 }
-                int m0, n0;
-                tile_mn(it, &m0, &n0);
+                const TileRef r = ref(it);
                 const uint32_t sA = sAB + s * ab_bytes, sB = sA + KT * kPSlab;
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)), "r"(ab_bytes)
                              : "memory");
                 for (int kt = 0; kt < KT; ++kt) {
-                    tma_load_2d(sA + kt * kPSlab, &tmA, kt * kTcBK, m0, bar(s));
-                    tma_load_2d(sB + kt * kPSlab, &tmB, kt * kTcBK, n0, bar(s));
+                    tma_load_2d(sA + kt * kPSlab, r.a, r.ax + kt * kTcBK, r.ay, bar(s));
+                    tma_load_2d(sB + kt * kPSlab, r.b, kt * kTcBK, r.by, bar(s));
                 }
                 issued = it + 1;
             }
@@ -401,12 +436,12 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
             // and, once the store has read the buffer, the load for tile i+3
             int loaded = 0;
             for (int it = 0; it < kPCBuf && it < nmine; ++it) {
-                int m0, n0;
-                tile_mn(it, &m0, &n0);
+                const TileRef r = ref(it);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(8 + it)),
                              "r"(kPCBytes)
                              : "memory");
-                for (int j = 0; j < 2; ++j) tma_load_2d(sCb + it * kPCBytes + j * kPSlab, &tmC, n0 + j * kTcBK, m0, bar(8 + it));
+                for (int j = 0; j < 2; ++j)
+                    tma_load_2d(sCb + it * kPCBytes + j * kPSlab, r.c, r.cx + j * kTcBK, r.cy, bar(8 + it));
                 loaded = it + 1;
             }
             for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
@@ -416,22 +451,22 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
                     fail();
                     break;
                 }
-                int m0, n0;
-                tile_mn(it, &m0, &n0);
-                for (int j = 0; j < 2; ++j)
-                    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
-                                     &tmC),
-                                 "r"(n0 + j * kTcBK), "r"(m0), "r"(sCb + s * kPCBytes + j * kPSlab)
-                                 : "memory");
+                const TileRef r = ref(it);
+                if (r.store)
+                    for (int j = 0; j < 2; ++j)
+                        asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                                         r.c),
+                                     "r"(r.cx + j * kTcBK), "r"(r.cy), "r"(sCb + s * kPCBytes + j * kPSlab)
+                                     : "memory");
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 if (it + kPCBuf < nmine) {
                     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                    tile_mn(it + kPCBuf, &m0, &n0);
+                    const TileRef rn = ref(it + kPCBuf);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(8 + s)),
                                  "r"(kPCBytes)
                                  : "memory");
                     for (int j = 0; j < 2; ++j)
-                        tma_load_2d(sCb + s * kPCBytes + j * kPSlab, &tmC, n0 + j * kTcBK, m0, bar(8 + s));
+                        tma_load_2d(sCb + s * kPCBytes + j * kPSlab, rn.c, rn.cx + j * kTcBK, rn.cy, bar(8 + s));
                     loaded = it + kPCBuf + 1;
                 }
             }
@@ -509,6 +544,24 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
     }
 }
 
+__global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap tmA,
+                                                            const __grid_constant__ CUtensorMap tmB,
+                                                            const __grid_constant__ CUtensorMap tmC, int M, int Nc,
+                                                            int K, unsigned* __restrict__ err,
+                                                            const int* __restrict__ flag)
+{
+    if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
+    tc_gemm_persistent<false>(&tmA, &tmB, &tmC, M, Nc, K, nullptr, nullptr, nullptr, 0, 0, 0, err);
+}
+
+__global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_pg(const GInst* __restrict__ inst,
+                                                             const TmapBytes* __restrict__ maps,
+                                                             const GTask* __restrict__ tasks, int ntasks, int K, int w,
+                                                             unsigned* __restrict__ err)
+{
+    tc_gemm_persistent<true>(nullptr, nullptr, nullptr, 0, 0, w, inst, maps, tasks, ntasks, K, w, err);
+}
+
 // Grouped trailing update of outer step [K, K + w) of many matrices: task
 // {inst, m0, n0} updates tile (m0, n0) of instance inst's A22 (rows and
 // columns from K + w) with L21 (rows from K + w, columns K .. K + w) read
@@ -557,6 +610,7 @@ bool tc_gemm_supported()
     if (set_max_dynamic_smem((const void*)k_tc_gemm) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_g) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_p) != NL_OK) return false;
+    if (set_max_dynamic_smem((const void*)k_tc_gemm_pg) != NL_OK) return false;
     g_tc_state = 1;
     return true;
 }
@@ -651,7 +705,20 @@ nl_status tc_gemm16_grouped(const GInst* inst, const TmapBytes* maps, const GTas
         return NL_EINVAL;
     }
     prof_begin("k_tc_gemm", st);
-    k_tc_gemm_g<<<(unsigned)ntasks, kTcThreads, tc_smem_bytes(w), st>>>(inst, maps, tasks, K, w, g_tc_err);
+    if (w <= 2 * kTcBK) {
+        // persistent: one CTA per SM over the step's task list
+        static int nsm = 0;
+        if (!nsm) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (nsm < 1) nsm = 1;
+        }
+        const unsigned grid = (unsigned)std::min(ntasks, nsm);
+        k_tc_gemm_pg<<<grid, kPThreads, p_smem_bytes(w / kTcBK), st>>>(inst, maps, tasks, ntasks, K, w, g_tc_err);
+    } else {
+        k_tc_gemm_g<<<(unsigned)ntasks, kTcThreads, tc_smem_bytes(w), st>>>(inst, maps, tasks, K, w, g_tc_err);
+    }
     prof_end("k_tc_gemm", st);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
