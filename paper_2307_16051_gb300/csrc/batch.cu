@@ -430,10 +430,14 @@ __global__ void k_b_fill(int64_t n, double v, double* x)
     if (i < n) x[i] = v;
 }
 
-__global__ void k_htab_g(int n, double* htab)
+__global__ void k_htab_g(int n, double* htab, float* htab32)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) htab[k] = 1.0 / (double)(k + 1);
+    if (k < n) {
+        const double h = 1.0 / (double)(k + 1);
+        htab[k] = h;
+        htab32[k] = (float)h;
+    }
 }
 
 // --------------------------------------------------------------- host side --
@@ -508,6 +512,7 @@ struct nl_batch {
     int* row_off = nullptr;
     int* order = nullptr;
     double* htab = nullptr;
+    float* htab32 = nullptr;  // the same table rounded to single (the Jacobian's entries use it)
     double *x0 = nullptr, *xout = nullptr;
     double* hist = nullptr;
     int *lin_iters = nullptr, *lin_outer = nullptr, *lin_failed = nullptr;
@@ -574,7 +579,8 @@ static nl_status batch_autotune(nl_batch* B)
         float ms_best = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
             NL_CUDA_OK(cudaMemsetAsync(B->flags, 0, sizeof(int) * B->count, B->st));
-            NL_TRY(launch_jacobian_g(B->dinst, B->dst, B->row_off, B->count, B->total_rows, B->htab, 0, B->st));
+            NL_TRY(launch_jacobian_g(B->dinst, B->dst, B->row_off, B->count, B->total_rows, B->htab, B->htab32, 0,
+                                     B->st));
             cudaEventRecord(e0, B->st);
             s = lu_grouped_factor(pl, B->gin, B->st, nullptr);
             cudaEventRecord(e1, B->st);
@@ -693,6 +699,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         cv.take<int>(count + 1);
         cv.take<int>(count);
         cv.take<double>(2 * (size_t)B->nmax);
+        cv.take<float>(2 * (size_t)B->nmax);
         cv.take<double>(tot);  // x0
         cv.take<double>(tot);  // xout
         cv.take<double>((size_t)count * NL_MAX_HIST);
@@ -738,6 +745,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
     B->row_off = cv.take<int>(count + 1);
     B->order = cv.take<int>(count);
     B->htab = cv.take<double>(2 * (size_t)B->nmax);
+    B->htab32 = cv.take<float>(2 * (size_t)B->nmax);
     B->x0 = cv.take<double>(tot);
     B->xout = cv.take<double>(tot);
     B->hist = cv.take<double>((size_t)count * NL_MAX_HIST);
@@ -793,7 +801,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         batch_free(B);
         return NL_ECUDA;
     }
-    k_htab_g<<<(unsigned)cdiv(2 * (int64_t)B->nmax, 256), 256, 0, B->st>>>(2 * B->nmax - 1, B->htab);
+    k_htab_g<<<(unsigned)cdiv(2 * (int64_t)B->nmax, 256), 256, 0, B->st>>>(2 * B->nmax - 1, B->htab, B->htab32);
     // x0 = ones for the autotuner's Jacobians
     {
         std::vector<double> ones((size_t)tot, 1.0);
@@ -911,7 +919,9 @@ static nl_status batch_build_graph(nl_batch* B, int fp64)
         k_b_cond<<<1, 1, 0, s0>>>(B->ctl, 0, 1, C.newton_maxit, hN);
         if ((s = add_while_node(s0, s1, hN)) != NL_OK) break;
         // ---- Newton step body (s1)
-        if ((s = launch_jacobian_g(inst, B->dst, B->row_off, count, B->total_rows, B->htab, fp64, s1)) != NL_OK) break;
+        if ((s = launch_jacobian_g(inst, B->dst, B->row_off, count, B->total_rows, B->htab, B->htab32, fp64, s1)) !=
+            NL_OK)
+            break;
         nodes_step = 1;
         // lu_path = 1 (interchanging path only): the batch factors nothing itself and hands
         // every instance to the single-instance path at its first step

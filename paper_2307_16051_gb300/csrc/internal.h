@@ -124,7 +124,7 @@ nl_status launch_residual_g(const BInst* inst, BState* st, const BTask* tasks, i
                             const double* htab, cudaStream_t st_);
 // J32/J16 (fp64 = 0) or J64 (fp64 = 1) of the BS_ACTIVE instances; rows = total rows, row_off[count + 1].
 nl_status launch_jacobian_g(const BInst* inst, const BState* st, const int* row_off, int count, int rows,
-                            const double* htab, int fp64, cudaStream_t st_);
+                            const double* htab, const float* htab32, int fp64, cudaStream_t st_);
 // r = b - J32 u of instances with lin_active; the last block of an instance writes st.nr_new.
 nl_status launch_gemv_residual_g(const BInst* inst, BState* st, const BTask* tasks, int ntasks, cudaStream_t st_);
 

@@ -266,7 +266,8 @@ nl_status launch_jacobian64(int N, double c, const double* rr, const double* hta
 // k_jacobian64.  Instances that are not BS_ACTIVE are skipped.
 __global__ void __launch_bounds__(256) k_jacobian_g(const BInst* __restrict__ inst, const BState* __restrict__ st,
                                                     const int* __restrict__ row_off, int count,
-                                                    const double* __restrict__ htab, int fp64)
+                                                    const double* __restrict__ htab,
+                                                    const float* __restrict__ htab32, int fp64)
 {
     const int g = blockIdx.x;
     int lo = 0, hi = count - 1;  // last instance with row_off[k] <= g
@@ -286,14 +287,18 @@ __global__ void __launch_bounds__(256) k_jacobian_g(const BInst* __restrict__ in
             Ji[j] = (j < N) ? fma(-w, htab[i + j], (i == j) ? 1.0 : 0.0) : 0.0;
         return;
     }
-    const float w = (float)(I.c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5));
+    // the row factor once per row (double arithmetic), the Hankel entries from the single table
+    __shared__ float wsh;
+    if (threadIdx.x == 0) wsh = (float)(I.c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5));
+    __syncthreads();
+    const float w = wsh;
     for (int j0 = threadIdx.x * kJCols; j0 < I.ld; j0 += blockDim.x * kJCols) {
         float v[kJCols];
 #pragma unroll
         for (int t = 0; t < kJCols; ++t) {
             const int j = j0 + t;
             float e = 0.0f;
-            if (j < N) e = fmaf(-w, (float)htab[i + j], (i == j) ? 1.0f : 0.0f);
+            if (j < N) e = fmaf(-w, htab32[i + j], (i == j) ? 1.0f : 0.0f);
             v[t] = e;
         }
         float4* p = reinterpret_cast<float4*>(I.J32 + (int64_t)i * I.ld + j0);
@@ -308,10 +313,10 @@ __global__ void __launch_bounds__(256) k_jacobian_g(const BInst* __restrict__ in
 }
 
 nl_status launch_jacobian_g(const BInst* inst, const BState* st, const int* row_off, int count, int rows,
-                            const double* htab, int fp64, cudaStream_t st_)
+                            const double* htab, const float* htab32, int fp64, cudaStream_t st_)
 {
     if (rows <= 0) return NL_OK;
-    k_jacobian_g<<<(unsigned)rows, 256, 0, st_>>>(inst, st, row_off, count, htab, fp64);
+    k_jacobian_g<<<(unsigned)rows, 256, 0, st_>>>(inst, st, row_off, count, htab, htab32, fp64);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }
