@@ -1711,19 +1711,22 @@ static nl_status trailing_update(int N, S* A, int64_t ld, int K, int wd, int nb,
 // U12, all co-resident (cooperative launch); otherwise the two-launch path.
 static int panel16_max_ctas()
 {
-    static int cap = -1;
-    if (cap < 0) {
-        cap = 0;
+    // computed once; concurrent first callers compute the same value (never a transient 0)
+    static std::atomic<int> cap{-1};
+    int c = cap.load(std::memory_order_acquire);
+    if (c < 0) {
+        c = 0;
         int dev = 0, nsm = 0, coop = 0, per = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
             set_max_dynamic_smem((const void*)k_panel16) == NL_OK &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_panel16, kPnlThreads, kPnlSmem) == cudaSuccess)
-            cap = per * nsm;
+            c = per * nsm;
         cudaGetLastError();
+        cap.store(c, std::memory_order_release);
     }
-    return cap;
+    return c;
 }
 
 // Rows (columns) per streaming CTA: 128 when the launch then fits on the GPU
