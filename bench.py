@@ -489,6 +489,29 @@ def main():
     extra["ir16"] = {"ms_per_sweep": sum(msir), "per_c": {str(c): {"status": nl.STATUS_NAMES[s["status"]],
                                                                      "newton": s["newton_iters"], "ms": s["t_total_ms"]}
                                                             for c, s in stir.items()}}
+    # the paper's two-precision comparison columns (Section 1.3): one solve per step in the
+    # factorisation's precision, no refinement
+    def one_tp(c, mode):
+        try:
+            solvers[c].solve_device(xdev[c], tol=TOL, mode=mode)
+        except nl.NLError:
+            pass  # a non-finite residual or a zero pivot: the status is in the stats
+        return solvers[c].stats()
+
+    extra["two_precision"] = {}
+    for mode in ("F32", "F16"):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        futs = {c: pool.submit(one_tp, c, mode) for c in SWEEP}
+        stm = {c: f.result() for c, f in futs.items()}
+        e1.record()
+        torch.cuda.synchronize()
+        extra["two_precision"][mode] = {
+            "ms_per_sweep": e0.elapsed_time(e1),
+            "per_c": {str(c): {"status": nl.STATUS_NAMES[s["status"]], "newton": s["newton_iters"],
+                               "final_rel_res": s["hist"][-1], "ms": s["t_total_ms"]} for c, s in stm.items()}}
     extra["sequential"] = {"ms_per_sweep": ms_seq[0], "solves_per_s": len(SWEEP) / (ms_seq[0] / 1e3),
                            "note": "the same five solves one after another on one stream"}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,

@@ -54,8 +54,24 @@ typedef enum {
  *  NL_IR16_GMRES: NL_IR16 until the first Newton step whose IR stalls (the
  *                failure rule of Section 3.1 fires, or ir_maxit corrections
  *                do not meet eta_j); that step's linear solve is redone with
- *                GMRES-IR from u0 = 0 and every later step uses GMRES-IR. */
-typedef enum { NL_FP64LU = 0, NL_IR16 = 1, NL_GMRESIR16 = 2, NL_IR16_GMRES = 3 } nl_mode;
+ *                GMRES-IR from u0 = 0 and every later step uses GMRES-IR.
+ *  NL_F32, NL_F16: the two-precision Newton methods the paper compares
+ *                against (Section 1.3, columns F32 and F16 of Tables 2-3):
+ *                the Jacobian stored and factored in single (J32, binary32
+ *                LU with interchanges) or half (J16 = I_s^h(J32), the
+ *                binary16 LU of NL_IR16) precision, and the step computed
+ *                with ONE triangular-solve pair in that precision: binary32
+ *                for F32; for F16 the right side fl16(-F/||F||) and every
+ *                product and difference of both solves rounded to binary16.
+ *                No refinement, so F16 converges slowly (Section 1.3). */
+typedef enum {
+    NL_FP64LU = 0,
+    NL_IR16 = 1,
+    NL_GMRESIR16 = 2,
+    NL_IR16_GMRES = 3,
+    NL_F32 = 4,
+    NL_F16 = 5
+} nl_mode;
 
 /* Solver parameters (nl_config_default fills the defaults in brackets). */
 typedef struct {
@@ -117,8 +133,9 @@ typedef struct nl_solver nl_solver;
 nl_status nl_config_default(nl_config* cfg);
 
 /* Create a solver for the H-equation of size N and albedo c (Section 3).
- * Allocates all device state for all three modes except the double Jacobian
- * (allocated on the first NL_FP64LU solve).  N >= 1, 0 <= c < 1 (J(x*) is
+ * Allocates all device state for every mode except the double Jacobian
+ * (allocated on the first NL_FP64LU solve) and the single-precision solve's
+ * workspace (on the first NL_F32 solve).  N >= 1, 0 <= c < 1 (J(x*) is
  * singular at c = 1).  cfg may be NULL (defaults).  *out receives the handle,
  * owned by the caller until nl_destroy. */
 nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out);
@@ -248,7 +265,7 @@ void nl_batch_destroy(nl_batch* b);
 typedef struct {
     int64_t hbm_budget_bytes;  /* [64 GiB] device memory the server may hold (solver handles) */
     int max_inflight;          /* [8] requests on the device at once (one worker thread and stream each) */
-    int mode;                  /* [NL_IR16_GMRES] nl_mode of every solve */
+    int mode;                  /* [NL_IR16_GMRES] nl_mode of every solve, NL_FP64LU .. NL_IR16_GMRES */
     double tol;                /* [1e-10] tau_r of every solve */
     int starve_ms;             /* [250] after the oldest waiting request has waited this long, no later
                                   request is admitted before it */
@@ -401,6 +418,28 @@ nl_status nl_lusolve16(int64_t N, const void* LU16, int64_t ld, const int32_t* i
 
 /* b <- U^{-1} L^{-1} P b in double with the factors of nl_lu64. */
 nl_status nl_lusolve64(int64_t N, const double* LU, int64_t ld, const int32_t* ipiv, double* b, void* stream);
+
+/* Single-precision LU with partial pivoting of A (N x N binary32, in place;
+ * the F32 column of Section 1.3): binary32 storage and arithmetic (the
+ * updates as fused multiply-adds), always the interchanging path.  Layout,
+ * ipiv and info as nl_lu16.  nb: 0 = 128, else a multiple of 16 in
+ * [16, 128].  Allocates its workspace with cudaMallocAsync; synchronises
+ * the stream. */
+nl_status nl_lu32(int64_t N, float* A, int64_t ld, int32_t* ipiv, int nb, int32_t* info_host, void* stream);
+
+/* b <- U^{-1} L^{-1} P b in single with the factors of nl_lu32 (device, N
+ * floats).  Returns NL_ETIMEOUT if a bounded wait gave up.  Synchronises the
+ * stream. */
+nl_status nl_lusolve32(int64_t N, const float* LU, int64_t ld, const int32_t* ipiv, float* b, void* stream);
+
+/* b <- U^{-1} L^{-1} P b entirely in binary16 arithmetic with the factors of
+ * nl_lu16 (the F16 column of Section 1.3): b16 binary16 (device, N values,
+ * in place); the interchanges applied in order, then every product l_it x_t
+ * and every difference rounded to binary16 (round to nearest even), the
+ * forward solve taking row i's terms in increasing t, the backward solve in
+ * decreasing t, and x_t = fl16(s_t / u_tt).  One CTA; synchronises the
+ * stream. */
+nl_status nl_lusolve16h(int64_t N, const void* LU16, int64_t ld, const int32_t* ipiv, void* b16, void* stream);
 
 /* r = b - A u in single precision (Algorithm IR, residual line), A N x N
  * single row-major; *rnorm_dev = ||r||_2 (double, device). */

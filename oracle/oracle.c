@@ -494,8 +494,12 @@ void orc_lusolve_fly(int64_t N, const double *LU16, const int32_t *ipiv, float *
 }
 
 /* Both triangular solves entirely in binary16 arithmetic (the inner solve of
-   eq. (2.17) [nofly] and of eq. (2.19) [cheapir]).  b holds binary16 values
-   (as doubles), in place. */
+   eq. (2.17) [nofly] and of eq. (2.19) [cheapir], and the step of the F16
+   column, Section 1.3).  b holds binary16 values (as doubles), in place.
+   The paper fixes the precision of every operation, not the order of each
+   row's terms: the forward solve takes row i's terms in increasing t, the
+   backward solve in decreasing t (from the last column towards the
+   diagonal), the order of a column-oriented back substitution. */
 void orc_lusolve16(int64_t N, const double *LU16, const int32_t *ipiv, double *b)
 {
     apply_pivots_d(N, ipiv, b);
@@ -507,7 +511,7 @@ void orc_lusolve16(int64_t N, const double *LU16, const int32_t *ipiv, double *b
     }
     for (int64_t i = N - 1; i >= 0; --i) {
         double s = b[i];
-        for (int64_t t = i + 1; t < N; ++t)
+        for (int64_t t = N - 1; t > i; --t)
             s = orc_fl16(s - orc_fl16(LU16[i * N + t] * b[t]));
         b[i] = orc_fl16(s / LU16[i * N + i]);
     }
@@ -790,7 +794,9 @@ typedef struct {
      GMRES-IR (Algorithm 2.1).
    mode ORC_F32 / ORC_F16: two-precision Newton of Section 1.3: J stored and
      factored in single / half and the step computed with one solve in that
-     precision (columns F32 / F16 of Tables 2 and 3).
+     precision (columns F32 / F16 of Tables 2 and 3).  F16 factors
+     J_h = I_s^h(J) as the three-precision modes do (p->lu_nb selects the
+     arithmetic model) and solves in binary16 arithmetic.
    mode ORC_IR16GM: as ORC_IR16 until the first step whose IR does not meet
      eta (the failure rule of Section 3.1 or the iteration cap); that step is
      solved again by GMRES-IR from u0 = 0, as are all later steps. */
@@ -841,10 +847,15 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
             for (int64_t i = 0; i < N; ++i)
                 x[i] = x[i] + fn * (double)b32[i];
         } else if (mode == ORC_F16) {
+            /* J_h = I_s^h(J) from the single-precision Jacobian and the same
+               half-precision factorisation as the three-precision modes */
             int ovf = 0;
             for (size_t q = 0; q < NN; ++q)
-                J[q] = orc_fl16(J[q]);
-            res->lu_info[n] = orc_lu16(N, J, ipiv, &ovf);
+                J[q] = orc_fl16((double)(float)J[q]);
+            if (p->lu_nb > 0)
+                res->lu_info[n] = orc_lu16_dev(N, p->lu_nb, J, ipiv, &ovf);
+            else
+                res->lu_info[n] = orc_lu16(N, J, ipiv, &ovf);
             if (ovf) {
                 res->status = 3;
                 break;

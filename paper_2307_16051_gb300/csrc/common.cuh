@@ -161,10 +161,12 @@ __device__ __forceinline__ void st_release_gpu(int* p, int v)
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Element loads/stores for the two factor storage types.
+// Element loads/stores for the three factor storage types.
 __device__ __forceinline__ float ld_elem(const __half* p) { return __half2float(*p); }
+__device__ __forceinline__ float ld_elem(const float* p) { return *p; }
 __device__ __forceinline__ double ld_elem(const double* p) { return *p; }
 __device__ __forceinline__ void st_elem(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void st_elem(float* p, float v) { *p = v; }
 __device__ __forceinline__ void st_elem(double* p, double v) { *p = v; }
 
 }  // namespace nl

@@ -43,6 +43,9 @@ nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm,
                       cudaStream_t st, int* launches);
 nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast, const LuWork& w, cudaStream_t st,
                       int* launches);
+// Binary32 storage and arithmetic (F32 Newton), always with interchanges;
+// w carved for the single-precision panel (fp64 = false).
+nl_status lu32_factor(int N, float* A, int64_t ld, int* ipiv, int nb, const LuWork& w, cudaStream_t st, int* launches);
 nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* B, int64_t ldb,
                         __half* C, int64_t ldc, int gemm, cudaStream_t st);
 
@@ -155,6 +158,18 @@ nl_status trsv_solve16(int N, const __half* LU, int64_t ld, const float* v, floa
                        cudaStream_t st, int* launches);
 nl_status trsv_solve64(int N, const double* LU, int64_t ld, const double* v, double* z, const TrsvWork& w, int epoch,
                        cudaStream_t st, int* launches);
+// Single-precision factors (F32 Newton): the blocked solve of the double path
+// in binary32, so w is carved with the double layout (fp64 = true).
+nl_status trsv_prepare32(int N, const float* LU, int64_t ld, const int* ipiv, const TrsvWork& w, cudaStream_t st,
+                         int* launches);
+nl_status trsv_solve32(int N, const float* LU, int64_t ld, const float* v, float* z, const TrsvWork& w, int epoch,
+                       cudaStream_t st, int* launches);
+// Both triangular solves in binary16 arithmetic (F16 Newton): b = P v with
+// v = fl16(-F / *fnorm) when F is given, else v = vin (binary16); the result
+// goes to zout (binary16) and / or u (its values in binary32), either may be
+// null.  One CTA; N <= 32768.
+nl_status lusolve16h(int N, const __half* LU, int64_t ld, const int* ipiv, const double* F, const double* fnorm,
+                     const __half* vin, __half* zout, float* u, cudaStream_t st);
 
 // krylov.cu
 nl_status launch_gemv_residual(int N, const float* A, int64_t ld, const float* b, const float* u, float* r,

@@ -649,7 +649,7 @@ __device__ __forceinline__ void diag_lu_body(S* __restrict__ A, int64_t lda, int
     store_block<T, S, kDiagThreads>(A, lda, K, w, W, ldw, tid);
     // staged copies for k_offdiag: U11 (row role) and L11^T (column role),
     // wp x wp each, identity / zero padded, in its shared-memory layout
-    using H = typename std::conditional<std::is_same<T, float>::value, __half, double>::type;
+    using H = typename std::conditional<std::is_same<S, __half>::value, __half, T>::type;
     H* SU = reinterpret_cast<H*>(stage);
     H* SL = SU + wp * wp;
     for (int q = tid; q < wp * wp; q += kDiagThreads) {
@@ -687,7 +687,7 @@ __device__ __forceinline__ void offdiag_body(S* __restrict__ A, int64_t lda, int
 {
     if (flag && *(volatile int*)flag) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    using H = typename std::conditional<std::is_same<T, float>::value, __half, double>::type;
+    using H = typename std::conditional<std::is_same<S, __half>::value, __half, T>::type;
     constexpr int NG = kOffThreads / kOffG;  // groups (rows or columns) per CTA
     const int wp = (w + 31) & ~31;
     H* D = reinterpret_cast<H*>(smem_raw);  // wp x wp: U11 (row role) or L11^T (column role), identity-padded
@@ -1894,6 +1894,18 @@ nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast
         return NL_EINVAL;
     }
     return lu_factor_impl<double, double, 8, false>(N, A, ld, ipiv, nb, 1, fast, w, st, launches);
+}
+
+// The single-precision factorisation of the two-precision F32 Newton method
+// (Section 1.3): binary32 storage and arithmetic, always the interchanging
+// path (leaf panels with pivot search, row swaps, U12 solve, SIMT update).
+nl_status lu32_factor(int N, float* A, int64_t ld, int* ipiv, int nb, const LuWork& w, cudaStream_t st, int* launches)
+{
+    if (nb < 16 || nb > 128 || nb % 16) {
+        set_error("lu32: nb must be a multiple of 16 in [16, 128]");
+        return NL_EINVAL;
+    }
+    return lu_factor_impl<float, float, 16, false>(N, A, ld, ipiv, nb, 1, false, w, st, launches);
 }
 
 }  // namespace nl

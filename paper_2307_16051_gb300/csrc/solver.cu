@@ -248,6 +248,8 @@ struct nl_solver {
     size_t pool_bytes = 0;
     void* pool64 = nullptr;
     size_t pool64_bytes = 0;
+    void* pool32 = nullptr;  // F32 mode: the single-precision solve's workspace
+    size_t pool32_bytes = 0;
     double* pin = nullptr;
     // state
     double *xa = nullptr, *xb = nullptr, *F = nullptr, *rr = nullptr, *htab = nullptr, *partial = nullptr,
@@ -264,6 +266,7 @@ struct nl_solver {
     int* ipiv64 = nullptr;
     LuWork luw64;
     TrsvWork tw64;
+    TrsvWork tw32;
     int epoch = 0;
     int nb = 128;
     int gemm = 2;
@@ -363,7 +366,10 @@ static nl_status autotune_lu(nl_solver* s)
     return NL_OK;
 }
 
-static bool valid_mode(int m) { return m == NL_FP64LU || m == NL_IR16 || m == NL_GMRESIR16 || m == NL_IR16_GMRES; }
+static bool valid_mode(int m)
+{
+    return m == NL_FP64LU || m == NL_IR16 || m == NL_GMRESIR16 || m == NL_IR16_GMRES || m == NL_F32 || m == NL_F16;
+}
 
 extern "C" {
 
@@ -521,7 +527,10 @@ nl_status nl_set_stream(nl_solver* s, void* stream)
     return NL_OK;
 }
 
-int64_t nl_device_bytes(const nl_solver* s) { return s ? (int64_t)(s->pool_bytes + s->pool64_bytes) : 0; }
+int64_t nl_device_bytes(const nl_solver* s)
+{
+    return s ? (int64_t)(s->pool_bytes + s->pool64_bytes + s->pool32_bytes) : 0;
+}
 
 int64_t nl_footprint_bytes(int64_t N, nl_mode mode, const nl_config* cfg)
 {
@@ -531,6 +540,7 @@ int64_t nl_footprint_bytes(int64_t N, nl_mode mode, const nl_config* cfg)
     if (cfg) d = *cfg;
     size_t b = solver_bytes((int)N, d);
     if (mode == NL_FP64LU) b += solver64_bytes((int)N);
+    if (mode == NL_F32) b += trsv_work_bytes((int)N, true) + 256;
     return (int64_t)b;
 }
 
@@ -551,6 +561,7 @@ void nl_destroy(nl_solver* s)
     else cudaDeviceSynchronize();
     if (s->pool) cudaFree(s->pool);
     if (s->pool64) cudaFree(s->pool64);
+    if (s->pool32) cudaFree(s->pool32);
     if (s->pin) cudaFreeHost(s->pin);
     if (s->ev[0]) cudaEventDestroy(s->ev[0]);
     if (s->ev[1]) cudaEventDestroy(s->ev[1]);
@@ -583,6 +594,24 @@ static nl_status ensure_fp64(nl_solver* s)
     return NL_OK;
 }
 
+// F32 mode: the blocked single-precision solve uses the double layout of its
+// workspace (64-row blocks).
+static nl_status ensure_fp32(nl_solver* s)
+{
+    if (s->pool32) return NL_OK;
+    const size_t bytes = trsv_work_bytes(s->N, true);
+    if (cudaMalloc(&s->pool32, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->pool32 = nullptr;
+        set_error("single-precision solve: cudaMalloc of %zu bytes failed", bytes);
+        return NL_ENOMEM;
+    }
+    s->pool32_bytes = bytes;
+    cudaMemsetAsync(s->pool32, 0, bytes, s->st);
+    trsv_work_carve(s->pool32, s->N, true, &s->tw32);
+    return NL_OK;
+}
+
 static float elapsed_ms(nl_solver* s)
 {
     float ms = 0.0f;
@@ -609,18 +638,20 @@ static nl_status read_step_end(nl_solver* s, const double* fn_dev, double* fn)
     char* p = reinterpret_cast<char*>(s->pin);
     unsigned* tce = tc_error_word();
     NL_CUDA_OK(cudaMemcpyAsync(p, fn_dev, sizeof(double), cudaMemcpyDeviceToHost, s->st));
-    memset(p + 8, 0, 12);
+    memset(p + 8, 0, 16);
     NL_CUDA_OK(cudaMemcpyAsync(p + 8, s->tw.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
     if (s->tw64.err) NL_CUDA_OK(cudaMemcpyAsync(p + 12, s->tw64.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
     if (tce) NL_CUDA_OK(cudaMemcpyAsync(p + 16, tce, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
+    if (s->tw32.err) NL_CUDA_OK(cudaMemcpyAsync(p + 20, s->tw32.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s->st));
     NL_CUDA_OK(cudaStreamSynchronize(s->st));
     memcpy(fn, p, sizeof(double));
-    unsigned e[3];
+    unsigned e[4];
     memcpy(e, p + 8, sizeof(e));
-    if (e[0] | e[1] | e[2]) {
-        set_error("a device-side bounded wait gave up (error word 0x%x/0x%x/0x%x)", e[0], e[1], e[2]);
+    if (e[0] | e[1] | e[2] | e[3]) {
+        set_error("a device-side bounded wait gave up (error word 0x%x/0x%x/0x%x/0x%x)", e[0], e[1], e[2], e[3]);
         cudaMemsetAsync(s->tw.err, 0, sizeof(unsigned), s->st);
         if (s->tw64.err) cudaMemsetAsync(s->tw64.err, 0, sizeof(unsigned), s->st);
+        if (s->tw32.err) cudaMemsetAsync(s->tw32.err, 0, sizeof(unsigned), s->st);
         if (tce) cudaMemsetAsync(tce, 0, sizeof(unsigned), s->st);
         cudaStreamSynchronize(s->st);
         return NL_ETIMEOUT;
@@ -646,6 +677,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
     int launches = 0;
     Host H{s->pin, st, &launches};
     if (mode == NL_FP64LU) NL_TRY(ensure_fp64(s));
+    if (mode == NL_F32) NL_TRY(ensure_fp32(s));
 
     double* x = s->xa;
     double* xn = s->xb;
@@ -703,12 +735,17 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
                 ++S.lu_pivoted;
             }
             NL_TRY(trsv_prepare64(n, s->J64, s->ld, s->ipiv64, s->tw64, st, &launches));
+        } else if (mode == NL_F32) {
+            // two-precision Newton, F32: J32 factored in place in single precision
+            NL_TRY(lu32_factor(n, s->J32, s->ld, s->ipiv, s->nb, s->luw, st, &launches));
+            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+            NL_TRY(trsv_prepare32(n, s->J32, s->ld, s->ipiv, s->tw32, st, &launches));
         } else {
             // the fast path's outcome is read once, after the triangular solves' set-up
             // has been queued behind it (redone below in the rare case of interchanges)
             NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, !pivoted_only, s->luw, st, &launches));
             NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
-            NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
+            if (mode != NL_F16) NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
             NL_CUDA_OK(cudaStreamSynchronize(st));
             memcpy(iflag, s->pin, sizeof(iflag));
             if (iflag[1]) {
@@ -717,7 +754,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
                 NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
                 ++launches;
                 ++S.lu_pivoted;
-                NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
+                if (mode != NL_F16) NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
             }
         }
         cudaEventRecord(s->evp[3], st);
@@ -738,6 +775,17 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             ++launches;
             ustep = s->u64;
             u_is_double = 1;
+        } else if (mode == NL_F32) {
+            // one single-precision solve with the single-precision factors
+            NL_TRY(launch_scale_rhs32(n, s->F, fn_dev, s->b, st));
+            NL_TRY(trsv_solve32(n, s->J32, s->ld, s->b, s->u, s->tw32, ++s->epoch, st, &launches));
+            ++launches;
+            ustep = s->u;
+        } else if (mode == NL_F16) {
+            // one binary16-arithmetic solve of fl16(-F/||F||) with the binary16 factors
+            NL_TRY(lusolve16h(n, s->J16, s->ld, s->ipiv, s->F, fn_dev, nullptr, nullptr, s->u, st));
+            ++launches;
+            ustep = s->u;
         } else {
             NL_TRY(launch_scale_rhs32(n, s->F, fn_dev, s->b, st));
             ++launches;
@@ -961,6 +1009,30 @@ nl_status nl_lu64(int64_t N, double* A, int64_t ld, int32_t* ipiv, int nb, int p
     return lu_entry<double>(N, A, ld, ipiv, nb, 1, path, info_host, (cudaStream_t)stream, true);
 }
 
+nl_status nl_lu32(int64_t N, float* A, int64_t ld, int32_t* ipiv, int nb, int32_t* info_host, void* stream)
+{
+    if (nb == 0) nb = 128;
+    if (N < 1 || N > 32768 || !A || !ipiv || ld < N || nb < 16 || nb > 128 || nb % 16) {
+        set_error("nl_lu32: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    void* wk = nullptr;
+    NL_CUDA_OK(cudaMallocAsync(&wk, lu_work_bytes(n, nb, false) + 256, st));
+    LuWork w;
+    lu_work_carve(wk, n, nb, false, &w);
+    int info = 0;
+    nl_status s = lu32_factor(n, A, ld, ipiv, nb, w, st, nullptr);
+    if (s == NL_OK && cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        s = NL_ECUDA;
+    cudaFreeAsync(wk, st);
+    NL_CUDA_OK(cudaStreamSynchronize(st));
+    if (info_host) *info_host = info;
+    if (s == NL_OK && info) return NL_ESINGULAR;
+    return s;
+}
+
 }  // extern "C"
 
 template <typename S, typename T>
@@ -982,6 +1054,9 @@ static nl_status lusolve_entry(int64_t N, const S* LU, int64_t ld, const int32_t
     if constexpr (std::is_same<S, __half>::value) {
         s = trsv_prepare16(n, LU, ld, ipiv, w, st, nullptr);
         if (s == NL_OK) s = trsv_solve16(n, LU, ld, b, b, w, 1, st, nullptr);
+    } else if constexpr (std::is_same<S, float>::value) {
+        s = trsv_prepare32(n, LU, ld, ipiv, w, st, nullptr);
+        if (s == NL_OK) s = trsv_solve32(n, LU, ld, b, b, w, 1, st, nullptr);
     } else {
         s = trsv_prepare64(n, LU, ld, ipiv, w, st, nullptr);
         if (s == NL_OK) s = trsv_solve64(n, LU, ld, b, b, w, 1, st, nullptr);
@@ -1007,6 +1082,24 @@ nl_status nl_lusolve16(int64_t N, const void* LU16, int64_t ld, const int32_t* i
 nl_status nl_lusolve64(int64_t N, const double* LU, int64_t ld, const int32_t* ipiv, double* b, void* stream)
 {
     return lusolve_entry<double, double>(N, LU, ld, ipiv, b, stream, true);
+}
+
+nl_status nl_lusolve32(int64_t N, const float* LU, int64_t ld, const int32_t* ipiv, float* b, void* stream)
+{
+    return lusolve_entry<float, float>(N, LU, ld, ipiv, b, stream, true);  // the 64-row blocked layout
+}
+
+nl_status nl_lusolve16h(int64_t N, const void* LU16, int64_t ld, const int32_t* ipiv, void* b16, void* stream)
+{
+    if (N < 1 || N > 32768 || !LU16 || !ipiv || !b16 || ld < N) {
+        set_error("nl_lusolve16h: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    __half* b = (__half*)b16;
+    NL_TRY(lusolve16h((int)N, (const __half*)LU16, ld, ipiv, nullptr, nullptr, b, b, nullptr, st));
+    NL_CUDA_OK(cudaStreamSynchronize(st));
+    return NL_OK;
 }
 
 nl_status nl_k_gemv_residual(int64_t N, const float* A, int64_t ld, const float* b, const float* u, float* r,

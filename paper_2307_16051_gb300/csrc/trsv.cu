@@ -703,7 +703,7 @@ static nl_status prepare_impl(int N, const S* LU, int64_t ld, const int* ipiv, c
                               int* launches)
 {
     constexpr bool fp64 = std::is_same<T, double>::value;
-    constexpr int TB = fp64 ? T_ : T2;
+    constexpr int TB = std::is_same<S, __half>::value ? T2 : T_;  // the block size of the solve that follows
     const int nblk = (int)cdiv(N, TB);
     static bool attr = false;
     if (!attr) {
@@ -739,6 +739,12 @@ nl_status trsv_prepare64(int N, const double* LU, int64_t ld, const int* ipiv, c
                          int* launches)
 {
     return prepare_impl<double, double>(N, LU, ld, ipiv, w, st, launches);
+}
+
+nl_status trsv_prepare32(int N, const float* LU, int64_t ld, const int* ipiv, const TrsvWork& w, cudaStream_t st,
+                         int* launches)
+{
+    return prepare_impl<float, float>(N, LU, ld, ipiv, w, st, launches);
 }
 
 template <typename S, typename T, bool LOWER>
@@ -909,6 +915,95 @@ nl_status trsv_solve64(int N, const double* LU, int64_t ld, const double* v, dou
                        cudaStream_t st, int* launches)
 {
     return solve_impl<double, double>(N, LU, ld, v, z, w, epoch, st, launches);
+}
+
+nl_status trsv_solve32(int N, const float* LU, int64_t ld, const float* v, float* z, const TrsvWork& w, int epoch,
+                       cudaStream_t st, int* launches)
+{
+    return solve_impl<float, float>(N, LU, ld, v, z, w, epoch, st, launches);
+}
+
+// ------------------------------------------------- binary16 arithmetic --
+// Both triangular solves with every product and difference rounded to
+// binary16: the step of the two-precision F16 Newton method (Section 1.3),
+// computed in the precision of its factorisation.  Column-oriented in one
+// CTA: at step t the final entry x_t is applied to every later row (forward)
+// or earlier row (backward), so row i takes its updates in increasing t in
+// the forward solve and in decreasing t in the backward one.  The product of
+// two binary16 numbers is exact in binary32 and the difference of two is
+// exact in binary64, so each is rounded once, to binary16.  The backward
+// quotient is rounded to binary64 first; that gives the correctly rounded
+// binary16 quotient because 53 >= 2 * 11 + 2 (double rounding is innocuous
+// when the wider format has at least 2p + 2 bits, Figueroa 1995).
+constexpr int kH16Threads = 1024;
+
+__device__ __forceinline__ __half h16_sub_prod(__half b, __half l, __half x)
+{
+    const __half p = __float2half_rn(__half2float(l) * __half2float(x));
+    return __double2half((double)__half2float(b) - (double)__half2float(p));
+}
+
+__global__ void __launch_bounds__(kH16Threads) k_lusolve16h(int N, const __half* __restrict__ LU, int64_t ld,
+                                                           const int* __restrict__ ipiv,
+                                                           const double* __restrict__ F,
+                                                           const double* __restrict__ fnorm,
+                                                           const __half* vin, __half* zout, float* __restrict__ u)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __half* b = reinterpret_cast<__half*>(smem_raw);  // N entries
+    const int tid = threadIdx.x;
+    if (F) {
+        const double fn = *fnorm;
+        for (int i = tid; i < N; i += kH16Threads) b[i] = __double2half(-F[i] / fn);
+    } else {
+        for (int i = tid; i < N; i += kH16Threads) b[i] = vin[i];
+    }
+    __syncthreads();
+    if (tid == 0) {  // P b, the interchanges in factorisation order
+        for (int k = 0; k < N; ++k) {
+            const int p = ipiv[k];
+            if (p != k && (unsigned)p < (unsigned)N) {
+                const __half t = b[k];
+                b[k] = b[p];
+                b[p] = t;
+            }
+        }
+    }
+    __syncthreads();
+    for (int t = 0; t + 1 < N; ++t) {  // L y = P b, unit diagonal
+        const __half xt = b[t];
+        for (int i = t + 1 + tid; i < N; i += kH16Threads) b[i] = h16_sub_prod(b[i], LU[(int64_t)i * ld + t], xt);
+        __syncthreads();
+    }
+    for (int t = N - 1; t >= 0; --t) {  // U z = y
+        const __half xt =
+            __double2half((double)__half2float(b[t]) / (double)__half2float(LU[(int64_t)t * ld + t]));
+        if (tid == 0) {
+            if (zout) zout[t] = xt;
+            if (u) u[t] = __half2float(xt);
+        }
+        for (int i = tid; i < t; i += kH16Threads) b[i] = h16_sub_prod(b[i], LU[(int64_t)i * ld + t], xt);
+        __syncthreads();
+    }
+}
+
+nl_status lusolve16h(int N, const __half* LU, int64_t ld, const int* ipiv, const double* F, const double* fnorm,
+                     const __half* vin, __half* zout, float* u, cudaStream_t st)
+{
+    if (N < 1 || N > 32768 || !LU || !ipiv || ld < N || (F ? !fnorm : !vin)) {
+        set_error("binary16 solve: bad argument");
+        return NL_EINVAL;
+    }
+    static bool attr = false;
+    if (!attr) {
+        if (set_max_dynamic_smem((const void*)k_lusolve16h) != NL_OK) return NL_ECUDA;
+        attr = true;
+    }
+    prof_begin("k_lusolve16h", st);
+    k_lusolve16h<<<1, kH16Threads, (size_t)N * sizeof(__half), st>>>(N, LU, ld, ipiv, F, fnorm, vin, zout, u);
+    prof_end("k_lusolve16h", st);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
 }
 
 }  // namespace nl

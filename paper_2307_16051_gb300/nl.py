@@ -18,8 +18,9 @@ from . import build as _build
 NL_OK, NL_EINVAL, NL_ENOMEM, NL_ENOTCONV, NL_ESINGULAR, NL_ENUMERIC, NL_ETIMEOUT, NL_ECUDA = range(8)
 STATUS_NAMES = ["NL_OK", "NL_EINVAL", "NL_ENOMEM", "NL_ENOTCONV", "NL_ESINGULAR", "NL_ENUMERIC", "NL_ETIMEOUT",
                 "NL_ECUDA"]
-NL_FP64LU, NL_IR16, NL_GMRESIR16, NL_IR16_GMRES = 0, 1, 2, 3
-MODES = {"FP64LU": NL_FP64LU, "IR16": NL_IR16, "GMRESIR16": NL_GMRESIR16, "IR16_GMRES": NL_IR16_GMRES}
+NL_FP64LU, NL_IR16, NL_GMRESIR16, NL_IR16_GMRES, NL_F32, NL_F16 = 0, 1, 2, 3, 4, 5
+MODES = {"FP64LU": NL_FP64LU, "IR16": NL_IR16, "GMRESIR16": NL_GMRESIR16, "IR16_GMRES": NL_IR16_GMRES,
+         "F32": NL_F32, "F16": NL_F16}
 MAX_HIST = 128
 
 
@@ -105,6 +106,9 @@ SIGNATURES = {
     "nl_lu64": (_int, [_i64, _P, _i64, _P, _int, _int, ctypes.POINTER(ctypes.c_int32), _P]),
     "nl_lusolve16": (_int, [_i64, _P, _i64, _P, _P, _P]),
     "nl_lusolve64": (_int, [_i64, _P, _i64, _P, _P, _P]),
+    "nl_lu32": (_int, [_i64, _P, _i64, _P, _int, ctypes.POINTER(ctypes.c_int32), _P]),
+    "nl_lusolve32": (_int, [_i64, _P, _i64, _P, _P, _P]),
+    "nl_lusolve16h": (_int, [_i64, _P, _i64, _P, _P, _P]),
     "nl_k_gemv_residual": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
     "nl_k_gemv_residual_noalloc": (_int, [_i64, _P, _i64, _P, _P, _P, _P, _P]),
     "nl_k_div_round16": (_int, [_i64, _P, _P, _P, _P]),
@@ -372,6 +376,21 @@ def lusolve16(N, LU16, ld, ipiv, b, stream=None):
 
 def lusolve64(N, LU, ld, ipiv, b, stream=None):
     return check(lib().nl_lusolve64(N, _ptr(LU), ld, _ptr(ipiv), _ptr(b), _stream(stream)))
+
+
+def lu32(N, A, ld, ipiv, nb=0, stream=None):
+    info = ctypes.c_int32(0)
+    st = lib().nl_lu32(N, _ptr(A), ld, _ptr(ipiv), nb, ctypes.byref(info), _stream(stream))
+    check(st, allow=(NL_ESINGULAR,))
+    return info.value
+
+
+def lusolve32(N, LU, ld, ipiv, b, stream=None):
+    return check(lib().nl_lusolve32(N, _ptr(LU), ld, _ptr(ipiv), _ptr(b), _stream(stream)))
+
+
+def lusolve16h(N, LU16, ld, ipiv, b16, stream=None):
+    return check(lib().nl_lusolve16h(N, _ptr(LU16), ld, _ptr(ipiv), _ptr(b16), _stream(stream)))
 
 
 def k_gemv_residual(N, A, ld, b, u, r, rnorm, stream=None):

@@ -56,6 +56,13 @@ def test_invalid_arguments_rejected_before_device_use():
     for bad in ({"trsv_cluster": 3}, {"trsv_cluster": -2}, {"trsv_cluster": 32}, {"lu_path": 2}, {"lu_stream": 1},
                 {"lu_stream": -2}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
+    # the two-precision kernel entries check their arguments before any device call
+    assert L.nl_lu32(0, None, 0, None, 0, None, None) == nl.NL_EINVAL
+    assert L.nl_lu32(64, 1, 64, 1, 24, None, None) == nl.NL_EINVAL  # nb not a multiple of 16
+    assert L.nl_lusolve32(40000, 1, 40000, 1, 1, None) == nl.NL_EINVAL
+    assert L.nl_lusolve16h(64, 1, 32, 1, 1, None) == nl.NL_EINVAL  # ld < N
+    assert L.nl_lusolve16h(64, None, 64, 1, 1, None) == nl.NL_EINVAL
+    assert L.nl_solve(None, None, 1e-10, nl.NL_F16, None) == nl.NL_EINVAL
 
 
 def test_no_device_is_an_error_not_a_fallback():
@@ -103,6 +110,10 @@ def test_server_no_device_is_an_error():
     assert nl.footprint_bytes(1024) > 6 * 1024 * 1024
     assert nl.footprint_bytes(1024, "FP64LU") > nl.footprint_bytes(1024) + 8 * 1024 * 1024
     assert nl.lib().nl_footprint_bytes(0, 1, None) == -1
+    assert nl.lib().nl_footprint_bytes(64, 6, None) == -1  # no such mode
+    # F16 needs nothing beyond the handle; F32 adds the single-precision solve's workspace
+    assert nl.footprint_bytes(1024, "F16") == nl.footprint_bytes(1024, "IR16")
+    assert nl.footprint_bytes(1024, "F32") > nl.footprint_bytes(1024, "IR16")
     # the autotuning setting (-1) sizes the handle for the largest panel width
     for N in (1, 700, 4096):
         assert nl.footprint_bytes(N, lu_nb=-1) == nl.footprint_bytes(N, lu_nb=128) >= nl.footprint_bytes(N, lu_nb=32)

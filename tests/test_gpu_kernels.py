@@ -308,6 +308,81 @@ def test_lusolve16_synthetic_factors(N):
     assert np.all(np.abs(got - ref) <= 1e-5 * np.max(np.abs(ref)))
 
 
+# ------------------------------------------------- F32 / F16 columns --
+
+@pytest.mark.parametrize("N,nb", [(1, 16), (50, 16), (200, 64), (301, 128), (1000, 128)])
+def test_lu32_and_solve_match_oracle(N, nb):
+    """Single-precision LU with interchanges (the F32 column, Section 1.3).
+    A pivot-forcing matrix has one pivot sequence with a wide gap, so ipiv
+    must equal the oracle's exactly; the factors differ from the oracle's
+    only by the order and fusing of single-precision operations (measured
+    ~1.5e-6 of max|LU| at N = 1000; a misplaced term changes them by O(1)).
+    The solve is checked against the double solve of the same system."""
+    A, _ = W.pivot_forcing_matrix(N, 7000 + N)
+    A32 = A.astype(np.float32)
+    ld = ((N + 63) // 64) * 64
+    Ad = torch.zeros((N, ld), device=dev(), dtype=torch.float32)
+    Ad[:, :N] = T(A32)
+    ipiv = torch.empty(N, device=dev(), dtype=torch.int32)
+    info = nl.lu32(N, Ad, ld, ipiv, nb=nb)
+    LUo, ipivo, infoo = O.lu32(A32)
+    assert info == infoo == 0
+    assert np.array_equal(ipiv.cpu().numpy(), ipivo)
+    LU = Ad.cpu().numpy()[:, :N].astype(np.float64)
+    scale = np.max(np.abs(LUo))
+    assert np.max(np.abs(LU - LUo)) <= 2e-5 * scale
+    # partial pivoting: every multiplier at most 1 in magnitude
+    assert np.max(np.abs(np.tril(LU, -1)), initial=0.0) <= 1.0
+    b = W.random_vector(N, 8000 + N).astype(np.float32)
+    bd = T(b)
+    nl.lusolve32(N, Ad, ld, ipiv, bd)
+    LU64, ip64, _ = O.lu64(A32.astype(np.float64))
+    ref = O.lusolve64(LU64, ip64, b.astype(np.float64))
+    got = bd.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N", [127, 128, 2049, 4097, 9000])
+def test_lusolve32_synthetic_factors(N):
+    """The single-precision blocked solve over many 64-row blocks (more than
+    the cooperative grid's CTAs at 9000), ragged last blocks, against the
+    oracle's sequential single-precision solve."""
+    LUo, ipivo = synthetic_factors(N, 9000 + N)
+    b = W.random_vector(N, 9500 + N).astype(np.float32)
+    ref = O.lusolve32(LUo.astype(np.float32), ipivo, b).astype(np.float64)
+    ld = ((N + 63) // 64) * 64
+    LUd = torch.zeros((N, ld), device=dev(), dtype=torch.float32)
+    LUd[:, :N] = T(LUo.astype(np.float32))
+    bd = T(b)
+    nl.lusolve32(N, LUd, ld, T(ipivo), bd)
+    got = bd.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 1e-5 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("N,kind", [(1, "syn"), (5, "syn"), (127, "syn"), (1000, "syn"), (2049, "syn"),
+                                    (333, "lu16")])
+def test_lusolve16h_bit_exact(N, kind):
+    """Both triangular solves in binary16 arithmetic (the F16 step): every
+    product and difference rounded to binary16 in the oracle's order, so the
+    result is bitwise the oracle's."""
+    if kind == "syn":
+        LUo, ipivo = synthetic_factors(N, 10000 + N)
+    else:
+        A, _ = W.pivot_forcing_matrix(N, 10500 + N)
+        LUo, ipivo, info, ovf = O.lu16_dev(O.fl16(A), 64)
+        assert info == 0 and not ovf
+    b16 = O.fl16(W.random_vector(N, 11000 + N) / 4)
+    ref = O.lusolve16(LUo, ipivo, b16)
+    ld = ((N + 63) // 64) * 64
+    LUd = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    LUd[:, :N] = T(LUo.astype(np.float16))
+    bd = T(b16.astype(np.float16))
+    nl.lusolve16h(N, LUd, ld, T(ipivo.astype(np.int32)), bd)
+    got = bd.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(ref))
+    assert np.array_equal(got, ref)
+
+
 @pytest.mark.parametrize("N,nb,diag", [(1, 16, False), (50, 16, False), (200, 64, False), (301, 64, False),
                                         (301, 64, True), (500, 128, True)])
 def test_lu64_and_solve_match_oracle(N, nb, diag):

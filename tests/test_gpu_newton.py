@@ -168,6 +168,59 @@ def test_paper_mode_table2_columns_n1024(table2):
             assert agrees_4digits(h[n], p[n]), (mode, n, h[n], p[n])
 
 
+@pytest.mark.parametrize("N,c", [(1, 0.9), (100, 0.5), (517, 0.99), (1024, 0.9999)])
+def test_f32_two_precision_newton(N, c):
+    """F32 column (Section 1.3): J stored and factored in single precision,
+    one single-precision solve per step.  Newton counts as the oracle's F32
+    iteration, the same solution."""
+    with nl.Solver(N, c) as s:
+        x, status = s.solve(tol=1e-10, mode="F32")
+        st = s.stats()
+    xo, ro = O.newton(N, c, "F32", tol=1e-10)
+    assert status == nl.NL_OK and ro["status"] == 0
+    assert newton_counts_agree(st["newton_iters"], ro), (st["hist"], ro["hist"])
+    kappa = 1.0 / math.sqrt(1.0 - c)
+    tol = 1e-10 if c <= 0.99 else 1e-10 + 10.0 * kappa * max(st["hist"][-1], ro["hist"][-1])
+    assert rel_inf(x, xo) <= tol
+    assert np.linalg.norm(O.F(N, c, x)) <= 1e-10 * st["fnorm0"] * 1.0001
+
+
+def test_paper_mode_table2_f32_column_n1024(table2):
+    """The F32 column of the paper's Table 2 (c = .99): steps 1-4 to the
+    printed digits, the same number of steps."""
+    from tests.conftest import agrees_4digits
+    with nl.Solver(1024, 0.99, newton_maxit=10) as s:
+        s.solve(tol=1e-9, mode="F32")
+        h = s.stats()["hist"]
+    p = table2["F32"]
+    assert len(h) == len(p)
+    for n in range(1, 5):
+        assert agrees_4digits(h[n], p[n]), (n, h[n], p[n])
+
+
+@pytest.mark.parametrize("N,c", [(64, 0.9), (1024, 0.99)])
+def test_f16_two_precision_newton(N, c):
+    """F16 column (Section 1.3): J_h factored in half precision and ONE
+    binary16-arithmetic solve per step, no refinement.  The GPU factors are
+    the oracle's device-model factors of the same J_h, but J_h comes from
+    the single-precision Jacobian, which matches the oracle's only to a few
+    units of single precision, so the histories agree to a few digits, not
+    bitwise: each step's residual within a factor 2 of the oracle's, the
+    same count, and the slow (linear) convergence of the F16 column."""
+    with nl.Solver(N, c, newton_maxit=30) as s:
+        x, status = s.solve(tol=1e-9, mode="F16")
+        st = s.stats()
+    xo, ro = O.newton(N, c, "F16", tol=1e-9, newton_maxit=30)
+    h, ho = st["hist"], ro["hist"]
+    assert ro["status"] == 0 and status == nl.NL_OK
+    assert abs(len(h) - len(ho)) <= 1, (h, ho)
+    for n in range(1, min(len(h), len(ho))):
+        assert 0.5 <= h[n] / ho[n] <= 2.0, (n, h, ho)
+    _, r64 = O.newton(N, c, "FP64LU", tol=1e-9)
+    if c >= 0.99:
+        assert len(h) - 1 > r64["newton_iters"], (h, r64["hist"])
+
+
 @pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden sweep file not generated")
 @pytest.mark.parametrize("c", [0.5, 0.9, 0.99, 0.9999, 0.999999])
 @pytest.mark.parametrize("mode", ["FP64LU", "IR16", "GMRESIR16"])

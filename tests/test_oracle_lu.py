@@ -208,7 +208,9 @@ def test_lusolve_fly_bit_exact_vs_float32_machine():
 
 
 def test_lusolve16_bit_exact_vs_float16_machine():
-    """Inner solve of eqs. (2.17) and (2.19): all in binary16."""
+    """Inner solve of eqs. (2.17) and (2.19) and the F16 step: all in
+    binary16, the back substitution taking row i's terms from the last
+    column down."""
     n = 14
     A16 = O.fl16(W.random_matrix(n, 41))
     LU, ipiv, _, _ = O.lu16(A16)
@@ -222,7 +224,7 @@ def test_lusolve16_bit_exact_vs_float16_machine():
         y[i] = s
     for i in reversed(range(n)):
         s = y[i]
-        for t in range(i + 1, n):
+        for t in reversed(range(i + 1, n)):
             s = np.float16(s - np.float16(L16[i, t] * y[t]))
         y[i] = np.float16(s / L16[i, i])
     assert np.array_equal(O.lusolve16(LU, ipiv, b), y.astype(np.float64))
