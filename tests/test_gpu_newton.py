@@ -186,16 +186,23 @@ def test_f32_two_precision_newton(N, c):
 
 
 def test_paper_mode_table2_f32_column_n1024(table2):
-    """The F32 column of the paper's Table 2 (c = .99): steps 1-4 to the
-    printed digits, the same number of steps."""
-    from tests.conftest import agrees_4digits
+    """The F32 column of the paper's Table 2 (c = .99): the same number of
+    steps, steps 1-4 within one unit of the printed fourth digit.  Not half
+    a unit: the single-precision factorisation's summation order, which the
+    paper does not fix, moves the residuals in the seventh digit, and step 2
+    lies on a printing boundary (measured 3.9345006e-02 on the GPU, printed
+    3.934e-02).  The history also follows the oracle's F32 history (which
+    prints as the paper's) to 1e-3."""
     with nl.Solver(1024, 0.99, newton_maxit=10) as s:
         s.solve(tol=1e-9, mode="F32")
         h = s.stats()["hist"]
+    _, ro = O.newton(1024, 0.99, "F32", paper=True, tol=1e-9)
     p = table2["F32"]
-    assert len(h) == len(p)
+    assert len(h) == len(p) == len(ro["hist"])
     for n in range(1, 5):
-        assert agrees_4digits(h[n], p[n]), (n, h[n], p[n])
+        unit = 1e-3 * 10 ** np.floor(np.log10(p[n]))
+        assert abs(h[n] - p[n]) <= unit, (n, h[n], p[n])
+        assert abs(h[n] - ro["hist"][n]) <= 1e-3 * ro["hist"][n], (n, h[n], ro["hist"][n])
 
 
 @pytest.mark.parametrize("N,c", [(64, 0.9), (1024, 0.99)])
