@@ -99,7 +99,13 @@ typedef struct {
                             128 rows per CTA where possible; 256 = the same with 256 rows per CTA
                             (half the SMs, for solves that share the GPU); -1 = two launches per
                             panel.  Bitwise the same factors in every case */
-    int reserved[5];
+    int ir_variant;      /* [0] IR correction (NL_IR16, and the IR part of NL_IR16_GMRES): 0 = on the
+                            fly, d = U^{-1} L^{-1} r with the binary16 factors promoted to single
+                            (eq. (2.16) applied to IR); 1 = the scaled half-precision correction of
+                            eq. (2.19), d = ||r|| I_h^s(U^{-1} L^{-1} I_s^h(r/||r||)) with both
+                            triangular solves in binary16 arithmetic (as nl_lusolve16h).  The
+                            batched path accepts only 0 */
+    int reserved[4];
 } nl_config;
 
 #define NL_MAX_HIST 128

@@ -164,12 +164,16 @@ nl_status trsv_prepare32(int N, const float* LU, int64_t ld, const int* ipiv, co
                          int* launches);
 nl_status trsv_solve32(int N, const float* LU, int64_t ld, const float* v, float* z, const TrsvWork& w, int epoch,
                        cudaStream_t st, int* launches);
-// Both triangular solves in binary16 arithmetic (F16 Newton): b = P v with
-// v = fl16(-F / *fnorm) when F is given, else v = vin (binary16); the result
-// goes to zout (binary16) and / or u (its values in binary32), either may be
-// null.  One CTA; N <= 32768.
-nl_status lusolve16h(int N, const __half* LU, int64_t ld, const int* ipiv, const double* F, const double* fnorm,
-                     const __half* vin, __half* zout, float* u, cudaStream_t st);
+// Both triangular solves in binary16 arithmetic, z = U^{-1} L^{-1} P v, on
+//   v = fl16(-F / *nrm)  when F is given (the F16 Newton step, eq. (2.17)),
+//   v = fl16(r / rn)     when r is given, rn = fl32(*nrm) (eq. (2.19)),
+//   v = vin              otherwise (binary16).
+// P from perm (position -> original index, as trsv_prepare16 builds it) when
+// given, else from the interchanges ipiv.  The result goes to zout (binary16)
+// and / or u (binary32: z, or rn z when r is given); either may be null.
+// One CTA; N <= 32768.
+nl_status lusolve16h(int N, const __half* LU, int64_t ld, const int* ipiv, const int* perm, const double* F,
+                     const float* r, const double* nrm, const __half* vin, __half* zout, float* u, cudaStream_t st);
 
 // krylov.cu
 nl_status launch_gemv_residual(int N, const float* A, int64_t ld, const float* b, const float* u, float* r,

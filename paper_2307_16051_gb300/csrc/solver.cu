@@ -185,7 +185,8 @@ static nl_status gmres16(int N, const float* J32, int64_t ld32, const __half* LU
     return NL_OK;
 }
 
-// IR (solver 0) or GMRES-IR (solver 2) for J32 u = b, u0 = 0.
+// IR (solver 0: on-the-fly correction; solver 1: the scaled binary16 correction
+// of eq. (2.19)) or GMRES-IR (solver 2) for J32 u = b, u0 = 0.
 static nl_status linsolve16(int N, const float* J32, int64_t ld32, const __half* LU, int64_t ld16, const TrsvWork& tw,
                             int& epoch, const float* b, float* u, double eta, int maxit, int solver, int m,
                             double gtol, int gcycles, LinBufs& B, Host& H, LinResult* res)
@@ -209,6 +210,12 @@ static nl_status linsolve16(int N, const float* J32, int64_t ld32, const __half*
             int steps = 0;
             NL_TRY(gmres16(N, J32, ld32, LU, ld16, tw, epoch, B.r, B.d, m, gtol, gcycles, B, H, &steps));
             res->iters += steps;
+        } else if (solver == 1) {
+            // the norm of the current residual: of b before the first correction
+            const double* rnorm = res->outer == 0 ? B.dscal : B.dscal + 1;
+            NL_TRY(lusolve16h(N, LU, ld16, nullptr, tw.perm, nullptr, B.r, rnorm, nullptr, nullptr, B.d, st));
+            ++*H.launches;
+            res->iters += 1;
         } else {
             NL_TRY(trsv_solve16(N, LU, ld16, B.r, B.d, tw, ++epoch, st, H.launches));
             res->iters += 1;
@@ -430,7 +437,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     if (d.gmres_restart < 1 || d.gmres_restart > 62 || d.ir_maxit < 0 || d.newton_maxit < 0 || d.lu_path < 0 ||
         d.lu_path > 1 || !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 ||
                            d.trsv_cluster == 8 || d.trsv_cluster == 16) ||
-        !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) ||
+        !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant < 0 || d.ir_variant > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
         d.lu_nb < -1) {
         set_error("nl_create: invalid configuration");
@@ -783,7 +790,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             ustep = s->u;
         } else if (mode == NL_F16) {
             // one binary16-arithmetic solve of fl16(-F/||F||) with the binary16 factors
-            NL_TRY(lusolve16h(n, s->J16, s->ld, s->ipiv, s->F, fn_dev, nullptr, nullptr, s->u, st));
+            NL_TRY(lusolve16h(n, s->J16, s->ld, s->ipiv, nullptr, s->F, nullptr, fn_dev, nullptr, nullptr, s->u, st));
             ++launches;
             ustep = s->u;
         } else {
@@ -791,7 +798,8 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             ++launches;
             LinResult lr;
             NL_TRY(linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
-                              s->cfg.ir_maxit, (mode == NL_GMRESIR16 || gm_sticky) ? 2 : 0, s->cfg.gmres_restart,
+                              s->cfg.ir_maxit, (mode == NL_GMRESIR16 || gm_sticky) ? 2 : s->cfg.ir_variant,
+                              s->cfg.gmres_restart,
                               s->cfg.gmres_tol, s->cfg.gmres_maxcycles, s->lb, H, &lr));
             if (mode == NL_IR16_GMRES && !gm_sticky && !lr.converged) {
                 // IR stalled: redo this step with GMRES-IR, and keep it for the rest of the solve
@@ -1097,7 +1105,7 @@ nl_status nl_lusolve16h(int64_t N, const void* LU16, int64_t ld, const int32_t* 
     }
     cudaStream_t st = (cudaStream_t)stream;
     __half* b = (__half*)b16;
-    NL_TRY(lusolve16h((int)N, (const __half*)LU16, ld, ipiv, nullptr, nullptr, b, b, nullptr, st));
+    NL_TRY(lusolve16h((int)N, (const __half*)LU16, ld, ipiv, nullptr, nullptr, nullptr, nullptr, b, b, nullptr, st));
     NL_CUDA_OK(cudaStreamSynchronize(st));
     return NL_OK;
 }

@@ -943,23 +943,125 @@ __device__ __forceinline__ __half h16_sub_prod(__half b, __half l, __half x)
     return __double2half((double)__half2float(b) - (double)__half2float(p));
 }
 
+// Register-pipelined sweep for N <= 4096 (R <= 4 rows per thread, row
+// i = tid + k * 1024): the factor is read in chunks of eight columns, one
+// 16-byte load per row and chunk, issued a chunk ahead of its use, so the
+// loads overlap the previous chunk's eight barrier steps.  Same operations in
+// the same order as the scalar sweep.
+__device__ __forceinline__ __half h16_lane(const uint4& v, int s)
+{
+    const unsigned w = (s >> 1) == 0 ? v.x : (s >> 1) == 1 ? v.y : (s >> 1) == 2 ? v.z : v.w;
+    return __ushort_as_half((unsigned short)(w >> (16 * (s & 1))));
+}
+
+template <int R>
+__device__ __forceinline__ void h16_load_chunk(const __half* __restrict__ LU, int64_t ld, int N, int c, int tid,
+                                               uint4 (&v)[R])
+{
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int i = tid + k * kH16Threads;
+        v[k] = (i < N && c >= 0 && 8 * c < N) ? __ldg(reinterpret_cast<const uint4*>(LU + (int64_t)i * ld + 8 * c))
+                                              : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// u_tt for t in [8c, 8c + 8) (1 beyond N), packed as one 16-byte value.
+__device__ __forceinline__ uint4 h16_load_diag(const __half* __restrict__ LU, int64_t ld, int N, int c)
+{
+    unsigned w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int t0 = 8 * c + 2 * q, t1 = t0 + 1;
+        const unsigned short lo = (c >= 0 && t0 < N) ? __half_as_ushort(LU[(int64_t)t0 * ld + t0]) : (unsigned short)0x3c00;
+        const unsigned short hi = (c >= 0 && t1 < N) ? __half_as_ushort(LU[(int64_t)t1 * ld + t1]) : (unsigned short)0x3c00;
+        w[q] = (unsigned)lo | ((unsigned)hi << 16);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+template <int R>
+__device__ void lusolve16h_vec(int N, const __half* __restrict__ LU, int64_t ld, __half* b, __half* zout,
+                               float* __restrict__ u, float scale, int tid)
+{
+    const int nch = (N + 7) / 8;
+    uint4 cur[R], nxt[R];
+    h16_load_chunk<R>(LU, ld, N, 0, tid, cur);
+    for (int c = 0; c < nch; ++c) {  // L y = P b, unit diagonal
+        h16_load_chunk<R>(LU, ld, N, c + 1, tid, nxt);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int t = 8 * c + s;
+            if (t < N - 1) {
+                const __half xt = b[t];
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const int i = tid + k * kH16Threads;
+                    if (i > t && i < N) b[i] = h16_sub_prod(b[i], h16_lane(cur[k], s), xt);
+                }
+                __syncthreads();
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) cur[k] = nxt[k];
+    }
+    // the chunk's diagonal entries u_tt, packed eight binary16 to 16 bytes
+    uint4 dcur = h16_load_diag(LU, ld, N, nch - 1), dnxt;
+    h16_load_chunk<R>(LU, ld, N, nch - 1, tid, cur);
+    for (int c = nch - 1; c >= 0; --c) {  // U z = y
+        h16_load_chunk<R>(LU, ld, N, c - 1, tid, nxt);
+        dnxt = h16_load_diag(LU, ld, N, c - 1);
+#pragma unroll
+        for (int s = 7; s >= 0; --s) {
+            const int t = 8 * c + s;
+            if (t < N) {
+                const __half xt =
+                    __double2half((double)__half2float(b[t]) / (double)__half2float(h16_lane(dcur, s)));
+                if (tid == 0) {
+                    if (zout) zout[t] = xt;
+                    if (u) u[t] = scale * __half2float(xt);
+                }
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const int i = tid + k * kH16Threads;
+                    if (i < t) b[i] = h16_sub_prod(b[i], h16_lane(cur[k], s), xt);
+                }
+                __syncthreads();
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) cur[k] = nxt[k];
+        dcur = dnxt;
+    }
+}
+
 __global__ void __launch_bounds__(kH16Threads) k_lusolve16h(int N, const __half* __restrict__ LU, int64_t ld,
-                                                           const int* __restrict__ ipiv,
-                                                           const double* __restrict__ F,
-                                                           const double* __restrict__ fnorm,
-                                                           const __half* vin, __half* zout, float* __restrict__ u)
+                                                           const int* __restrict__ ipiv, const int* __restrict__ perm,
+                                                           const double* __restrict__ F, const float* __restrict__ r,
+                                                           const double* __restrict__ nrm, const __half* vin,
+                                                           __half* zout, float* __restrict__ u)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __half* b = reinterpret_cast<__half*>(smem_raw);  // N entries
     const int tid = threadIdx.x;
+    float scale = 1.0f;
     if (F) {
-        const double fn = *fnorm;
-        for (int i = tid; i < N; i += kH16Threads) b[i] = __double2half(-F[i] / fn);
+        const double fn = *nrm;
+        for (int i = tid; i < N; i += kH16Threads) {
+            const int j = perm ? perm[i] : i;
+            b[i] = __double2half(-F[j] / fn);
+        }
+    } else if (r) {
+        scale = (float)*nrm;
+        for (int i = tid; i < N; i += kH16Threads) {
+            const int j = perm ? perm[i] : i;
+            b[i] = __float2half_rn(r[j] / scale);
+        }
     } else {
-        for (int i = tid; i < N; i += kH16Threads) b[i] = vin[i];
+        for (int i = tid; i < N; i += kH16Threads) b[i] = vin[perm ? perm[i] : i];
     }
     __syncthreads();
-    if (tid == 0) {  // P b, the interchanges in factorisation order
+    if (!perm && tid == 0) {  // P b, the interchanges in factorisation order
         for (int k = 0; k < N; ++k) {
             const int p = ipiv[k];
             if (p != k && (unsigned)p < (unsigned)N) {
@@ -970,6 +1072,14 @@ __global__ void __launch_bounds__(kH16Threads) k_lusolve16h(int N, const __half*
         }
     }
     __syncthreads();
+    const bool vec = N <= 4 * kH16Threads && (ld % 8) == 0 && (((uintptr_t)LU) & 15) == 0;
+    if (vec) {
+        const int R = (N + kH16Threads - 1) / kH16Threads;
+        if (R == 1) lusolve16h_vec<1>(N, LU, ld, b, zout, u, scale, tid);
+        else if (R == 2) lusolve16h_vec<2>(N, LU, ld, b, zout, u, scale, tid);
+        else lusolve16h_vec<4>(N, LU, ld, b, zout, u, scale, tid);
+        return;
+    }
     for (int t = 0; t + 1 < N; ++t) {  // L y = P b, unit diagonal
         const __half xt = b[t];
         for (int i = t + 1 + tid; i < N; i += kH16Threads) b[i] = h16_sub_prod(b[i], LU[(int64_t)i * ld + t], xt);
@@ -980,17 +1090,17 @@ __global__ void __launch_bounds__(kH16Threads) k_lusolve16h(int N, const __half*
             __double2half((double)__half2float(b[t]) / (double)__half2float(LU[(int64_t)t * ld + t]));
         if (tid == 0) {
             if (zout) zout[t] = xt;
-            if (u) u[t] = __half2float(xt);
+            if (u) u[t] = scale * __half2float(xt);
         }
         for (int i = tid; i < t; i += kH16Threads) b[i] = h16_sub_prod(b[i], LU[(int64_t)i * ld + t], xt);
         __syncthreads();
     }
 }
 
-nl_status lusolve16h(int N, const __half* LU, int64_t ld, const int* ipiv, const double* F, const double* fnorm,
-                     const __half* vin, __half* zout, float* u, cudaStream_t st)
+nl_status lusolve16h(int N, const __half* LU, int64_t ld, const int* ipiv, const int* perm, const double* F,
+                     const float* r, const double* nrm, const __half* vin, __half* zout, float* u, cudaStream_t st)
 {
-    if (N < 1 || N > 32768 || !LU || !ipiv || ld < N || (F ? !fnorm : !vin)) {
+    if (N < 1 || N > 32768 || !LU || !(ipiv || perm) || ld < N || ((F || r) ? !nrm : !vin)) {
         set_error("binary16 solve: bad argument");
         return NL_EINVAL;
     }
@@ -1000,7 +1110,7 @@ nl_status lusolve16h(int N, const __half* LU, int64_t ld, const int* ipiv, const
         attr = true;
     }
     prof_begin("k_lusolve16h", st);
-    k_lusolve16h<<<1, kH16Threads, (size_t)N * sizeof(__half), st>>>(N, LU, ld, ipiv, F, fnorm, vin, zout, u);
+    k_lusolve16h<<<1, kH16Threads, (size_t)N * sizeof(__half), st>>>(N, LU, ld, ipiv, perm, F, r, nrm, vin, zout, u);
     prof_end("k_lusolve16h", st);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;

@@ -54,7 +54,7 @@ def test_invalid_arguments_rejected_before_device_use():
     assert "bad" in nl.last_error() or "NULL" in nl.last_error()
     L.nl_destroy(None)  # no-op
     for bad in ({"trsv_cluster": 3}, {"trsv_cluster": -2}, {"trsv_cluster": 32}, {"lu_path": 2}, {"lu_stream": 1},
-                {"lu_stream": -2}):
+                {"lu_stream": -2}, {"ir_variant": 2}, {"ir_variant": -1}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
     # the two-precision kernel entries check their arguments before any device call
     assert L.nl_lu32(0, None, 0, None, 0, None, None) == nl.NL_EINVAL
@@ -84,6 +84,11 @@ def test_batch_arguments_validated():
         c = np.ascontiguousarray(cs, dtype=np.float64)
         assert L.nl_batch_create(len(Ns), N.ctypes.data if len(Ns) else None, c.ctypes.data if len(cs) else None,
                                  None, nl.ctypes.byref(h)) == nl.NL_EINVAL
+    # the batched path solves with the on-the-fly correction only
+    N = np.ascontiguousarray([64], dtype=np.int64)
+    c = np.ascontiguousarray([0.5], dtype=np.float64)
+    assert L.nl_batch_create(1, N.ctypes.data, c.ctypes.data, nl.ctypes.byref(nl.config(ir_variant=1)),
+                             nl.ctypes.byref(h)) == nl.NL_EINVAL
     assert L.nl_batch_solve(None, None, 1e-10, nl.NL_IR16_GMRES, None) == nl.NL_EINVAL
     assert L.nl_batch_stats(None, 0, None) == nl.NL_EINVAL
     assert L.nl_lu_grouped(0, None, None, None, None, 0, 0, 0, None, None) == nl.NL_EINVAL

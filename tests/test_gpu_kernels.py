@@ -359,12 +359,17 @@ def test_lusolve32_synthetic_factors(N):
     assert np.all(np.abs(got - ref) <= 1e-5 * np.max(np.abs(ref)))
 
 
-@pytest.mark.parametrize("N,kind", [(1, "syn"), (5, "syn"), (127, "syn"), (1000, "syn"), (2049, "syn"),
-                                    (333, "lu16")])
-def test_lusolve16h_bit_exact(N, kind):
-    """Both triangular solves in binary16 arithmetic (the F16 step): every
-    product and difference rounded to binary16 in the oracle's order, so the
-    result is bitwise the oracle's."""
+@pytest.mark.parametrize("N,kind,ld_mode", [(1, "syn", 64), (5, "syn", 64), (127, "syn", 64), (1000, "syn", 64),
+                                            (2049, "syn", 64), (3000, "syn", 64), (4096, "syn", 64),
+                                            (333, "lu16", 64), (1001, "syn", 1), (4097, "syn", 64),
+                                            (9000, "syn", 64)])
+def test_lusolve16h_bit_exact(N, kind, ld_mode):
+    """Both triangular solves in binary16 arithmetic (the F16 step and the
+    correction of eq. (2.19)): every product and difference rounded to
+    binary16 in the oracle's order, so the result is bitwise the oracle's.
+    N <= 4096 with ld a multiple of 8 takes the register-pipelined sweep
+    (1, 2 and 4 rows per thread); ld = N odd (1001) and N > 4096 the scalar
+    one."""
     if kind == "syn":
         LUo, ipivo = synthetic_factors(N, 10000 + N)
     else:
@@ -373,7 +378,7 @@ def test_lusolve16h_bit_exact(N, kind):
         assert info == 0 and not ovf
     b16 = O.fl16(W.random_vector(N, 11000 + N) / 4)
     ref = O.lusolve16(LUo, ipivo, b16)
-    ld = ((N + 63) // 64) * 64
+    ld = ((N + ld_mode - 1) // ld_mode) * ld_mode
     LUd = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
     LUd[:, :N] = T(LUo.astype(np.float16))
     bd = T(b16.astype(np.float16))

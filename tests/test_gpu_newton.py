@@ -205,6 +205,27 @@ def test_paper_mode_table2_f32_column_n1024(table2):
         assert abs(h[n] - ro["hist"][n]) <= 1e-3 * ro["hist"][n], (n, h[n], ro["hist"][n])
 
 
+@pytest.mark.parametrize("N,c", [(127, 0.5), (512, 0.9), (1000, 0.99), (1024, 0.9999)])
+def test_ir16_scaled_half_correction(N, c):
+    """IR with the scaled binary16 correction of eq. (2.19) (ir_variant = 1):
+    Newton counts as the oracle's, linear counts within one, the same
+    solution; and, as Section 2.3 expects for all but the most
+    ill-conditioned problems, the same Newton counts as IR with the
+    on-the-fly correction."""
+    with nl.Solver(N, c, ir_variant=1) as s:
+        x, status = s.solve(tol=1e-10, mode="IR16")
+        st = s.stats()
+    xo, ro = O.newton(N, c, "IR16", tol=1e-10, ir_variant=1)
+    assert status == nl.NL_OK and ro["status"] == 0
+    check_counts(st, ro, "IR16")
+    kappa = 1.0 / math.sqrt(1.0 - c)
+    tol = 1e-10 if c <= 0.99 else 1e-10 + 10.0 * kappa * max(st["hist"][-1], ro["hist"][-1])
+    assert rel_inf(x, xo) <= tol
+    with nl.Solver(N, c) as s:
+        s.solve(tol=1e-10, mode="IR16")
+        assert s.stats()["newton_iters"] == st["newton_iters"]
+
+
 @pytest.mark.parametrize("N,c", [(64, 0.9), (1024, 0.99)])
 def test_f16_two_precision_newton(N, c):
     """F16 column (Section 1.3): J_h factored in half precision and ONE

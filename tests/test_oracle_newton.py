@@ -173,6 +173,23 @@ def test_fp16_newton_device_factorisation_still_linear():
     assert all(h[k + 1] / h[k] > 1e-3 for k in range(1, len(h) - 1))
 
 
+def test_scaled_half_correction_same_newton_counts():
+    """Section 2.3: IR with the scaled binary16 correction of eq. (2.19) and
+    IR with the on-the-fly correction give the same nonlinear iteration for
+    all but the most ill-conditioned problems; the binary16 correction is
+    less accurate, so it needs at least as many linear corrections."""
+    for c in (0.5, 0.9, 0.99, 0.9999):
+        _, r0 = O.newton(512, c, "IR16", tol=1e-10, ir_variant=0)
+        _, r1 = O.newton(512, c, "IR16", tol=1e-10, ir_variant=1)
+        assert r0["status"] == r1["status"] == 0
+        assert r0["newton_iters"] == r1["newton_iters"], c
+        assert sum(r1["lin_iters"]) >= sum(r0["lin_iters"]), c
+    # the most ill-conditioned end of the sweep: the binary16 correction stalls
+    _, r0 = O.newton(1024, 0.999999, "IR16", tol=1e-10, ir_variant=0)
+    _, r1 = O.newton(1024, 0.999999, "IR16", tol=1e-10, ir_variant=1)
+    assert r0["status"] == 0 and r1["newton_iters"] > r0["newton_iters"]
+
+
 def test_table2_f32_column_n1024(table2):
     """F32 column (Section 1.3, J stored and factored in single, one
     single-precision solve): the printed history of Table 2, steps 1-4 to
