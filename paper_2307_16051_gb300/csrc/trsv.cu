@@ -930,17 +930,24 @@ nl_status trsv_solve32(int N, const float* LU, int64_t ld, const float* v, float
 // CTA: at step t the final entry x_t is applied to every later row (forward)
 // or earlier row (backward), so row i takes its updates in increasing t in
 // the forward solve and in decreasing t in the backward one.  The product of
-// two binary16 numbers is exact in binary32 and the difference of two is
-// exact in binary64, so each is rounded once, to binary16.  The backward
-// quotient is rounded to binary64 first; that gives the correctly rounded
-// binary16 quotient because 53 >= 2 * 11 + 2 (double rounding is innocuous
-// when the wider format has at least 2p + 2 bits, Figueroa 1995).
+// two binary16 numbers is exact in binary32 and is rounded once, to binary16;
+// the difference and the backward quotient are formed in binary32 (IEEE
+// round to nearest) and then rounded to binary16, which gives the correctly
+// rounded binary16 result because 24 >= 2 * 11 + 2 (rounding twice is
+// innocuous when the wider format has at least 2p + 2 bits, Figueroa 1995).
+// All in single precision: binary64 here would run on the SM's few FP64
+// units and dominate the sweep.
 constexpr int kH16Threads = 1024;
 
 __device__ __forceinline__ __half h16_sub_prod(__half b, __half l, __half x)
 {
-    const __half p = __float2half_rn(__half2float(l) * __half2float(x));
-    return __double2half((double)__half2float(b) - (double)__half2float(p));
+    const float p = __half2float(__float2half_rn(__half2float(l) * __half2float(x)));
+    return __float2half_rn(__half2float(b) - p);
+}
+
+__device__ __forceinline__ __half h16_div(__half a, __half b)
+{
+    return __float2half_rn(__fdiv_rn(__half2float(a), __half2float(b)));
 }
 
 // Register-pipelined sweep for N <= 4096 (R <= 4 rows per thread, row
@@ -1015,8 +1022,7 @@ __device__ void lusolve16h_vec(int N, const __half* __restrict__ LU, int64_t ld,
         for (int s = 7; s >= 0; --s) {
             const int t = 8 * c + s;
             if (t < N) {
-                const __half xt =
-                    __double2half((double)__half2float(b[t]) / (double)__half2float(h16_lane(dcur, s)));
+                const __half xt = h16_div(b[t], h16_lane(dcur, s));
                 if (tid == 0) {
                     if (zout) zout[t] = xt;
                     if (u) u[t] = scale * __half2float(xt);
@@ -1086,8 +1092,7 @@ __global__ void __launch_bounds__(kH16Threads) k_lusolve16h(int N, const __half*
         __syncthreads();
     }
     for (int t = N - 1; t >= 0; --t) {  // U z = y
-        const __half xt =
-            __double2half((double)__half2float(b[t]) / (double)__half2float(LU[(int64_t)t * ld + t]));
+        const __half xt = h16_div(b[t], LU[(int64_t)t * ld + t]);
         if (tid == 0) {
             if (zout) zout[t] = xt;
             if (u) u[t] = scale * __half2float(xt);
