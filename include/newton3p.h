@@ -105,7 +105,13 @@ typedef struct {
                             eq. (2.19), d = ||r|| I_h^s(U^{-1} L^{-1} I_s^h(r/||r||)) with both
                             triangular solves in binary16 arithmetic (as nl_lusolve16h).  The
                             batched path accepts only 0 */
-    int reserved[4];
+    int gmres_factors32; /* [0] GMRES-IR preconditioner: 0 = the binary16 factors promoted to single on the
+                            fly (eq. (2.16)); 1 = a single-precision copy of the binary16 factors made
+                            once per factorisation (Section 2.3: one more N x N copy, no interchange
+                            of precision inside the solves; the same values, so the same
+                            preconditioner up to the solves' summation order).  The batched path
+                            accepts only 0 */
+    int reserved[3];
 } nl_config;
 
 #define NL_MAX_HIST 128

@@ -164,6 +164,8 @@ nl_status trsv_prepare32(int N, const float* LU, int64_t ld, const int* ipiv, co
                          int* launches);
 nl_status trsv_solve32(int N, const float* LU, int64_t ld, const float* v, float* z, const TrsvWork& w, int epoch,
                        cudaStream_t st, int* launches);
+// B = A (N x N binary16 promoted to binary32, exact).
+nl_status launch_promote16(int N, const __half* A, int64_t lda, float* B, int64_t ldb, cudaStream_t st);
 // Both triangular solves in binary16 arithmetic, z = U^{-1} L^{-1} P v, on
 //   v = fl16(-F / *nrm)  when F is given (the F16 Newton step, eq. (2.17)),
 //   v = fl16(r / rn)     when r is given, rn = fl32(*nrm) (eq. (2.19)),

@@ -109,7 +109,19 @@ struct LinBufs {
     double* partial;
     unsigned* counter;
     double* dscal;  // device scalars: [0] norm(b), [1] residual norm
+    // GMRES-IR preconditioner with a single-precision copy of the factors (null: on the fly)
+    const float* LU32 = nullptr;
+    const TrsvWork* tw32 = nullptr;
 };
+
+// M^{-1} v for GMRES-IR: the binary16 factors promoted on the fly, or their
+// single-precision copy.
+static nl_status precond_apply(int N, const __half* LU, int64_t ld16, const TrsvWork& tw, int& epoch, const float* v,
+                               float* z, const LinBufs& B, cudaStream_t st, int* launches)
+{
+    if (B.LU32) return trsv_solve32(N, B.LU32, ld16, v, z, *B.tw32, ++epoch, st, launches);
+    return trsv_solve16(N, LU, ld16, v, z, tw, ++epoch, st, launches);
+}
 
 struct LinResult {
     int iters = 0, outer = 0, failed = 0, converged = 0;
@@ -153,7 +165,7 @@ static nl_status gmres16(int N, const float* J32, int64_t ld32, const __half* LU
             NL_TRY(launch_gemv_residual(N, J32, ld32, r, d, B.t, B.partial, B.counter, nullptr, st));
             ++*H.launches;
         }
-        NL_TRY(trsv_solve16(N, LU, ld16, B.t, B.w, tw, ++epoch, st, H.launches));
+        NL_TRY(precond_apply(N, LU, ld16, tw, epoch, B.t, B.w, B, st, H.launches));
         NL_TRY(launch_gmres_start(N, B.w, B.V, B.gws, m, st));
         ++*H.launches;
         double sc[3];
@@ -166,7 +178,7 @@ static nl_status gmres16(int N, const float* J32, int64_t ld32, const __half* LU
         for (int j = 0; j < m; ++j) {
             NL_TRY(launch_gemv_residual(N, J32, ld32, nullptr, B.V + (int64_t)j * B.ldv, B.t, B.partial, B.counter,
                                         nullptr, st));
-            NL_TRY(trsv_solve16(N, LU, ld16, B.t, B.w, tw, ++epoch, st, H.launches));
+            NL_TRY(precond_apply(N, LU, ld16, tw, epoch, B.t, B.w, B, st, H.launches));
             NL_TRY(launch_arnoldi(N, B.ldv, B.w, B.V, j, B.gws, m, st));
             *H.launches += 2;
             H.read2(B.gws + so, sc);
@@ -255,8 +267,11 @@ struct nl_solver {
     size_t pool_bytes = 0;
     void* pool64 = nullptr;
     size_t pool64_bytes = 0;
-    void* pool32 = nullptr;  // F32 mode: the single-precision solve's workspace
+    void* pool32 = nullptr;  // F32 mode and single-precision GMRES-IR factors: the single-precision solve's workspace
     size_t pool32_bytes = 0;
+    void* poolc = nullptr;   // single-precision copy of the binary16 factors (gmres_factors32)
+    size_t poolc_bytes = 0;
+    float* LU32c = nullptr;
     double* pin = nullptr;
     // state
     double *xa = nullptr, *xb = nullptr, *F = nullptr, *rr = nullptr, *htab = nullptr, *partial = nullptr,
@@ -438,6 +453,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         d.lu_path > 1 || !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 ||
                            d.trsv_cluster == 8 || d.trsv_cluster == 16) ||
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant < 0 || d.ir_variant > 1 ||
+        d.gmres_factors32 < 0 || d.gmres_factors32 > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
         d.lu_nb < -1) {
         set_error("nl_create: invalid configuration");
@@ -536,7 +552,7 @@ nl_status nl_set_stream(nl_solver* s, void* stream)
 
 int64_t nl_device_bytes(const nl_solver* s)
 {
-    return s ? (int64_t)(s->pool_bytes + s->pool64_bytes + s->pool32_bytes) : 0;
+    return s ? (int64_t)(s->pool_bytes + s->pool64_bytes + s->pool32_bytes + s->poolc_bytes) : 0;
 }
 
 int64_t nl_footprint_bytes(int64_t N, nl_mode mode, const nl_config* cfg)
@@ -547,7 +563,9 @@ int64_t nl_footprint_bytes(int64_t N, nl_mode mode, const nl_config* cfg)
     if (cfg) d = *cfg;
     size_t b = solver_bytes((int)N, d);
     if (mode == NL_FP64LU) b += solver64_bytes((int)N);
-    if (mode == NL_F32) b += trsv_work_bytes((int)N, true) + 256;
+    const bool f32fac = d.gmres_factors32 && (mode == NL_GMRESIR16 || mode == NL_IR16_GMRES);
+    if (mode == NL_F32 || f32fac) b += trsv_work_bytes((int)N, true) + 256;
+    if (f32fac) b += (size_t)N * round_up((int)N, 64) * sizeof(float) + 256;
     return (int64_t)b;
 }
 
@@ -569,6 +587,7 @@ void nl_destroy(nl_solver* s)
     if (s->pool) cudaFree(s->pool);
     if (s->pool64) cudaFree(s->pool64);
     if (s->pool32) cudaFree(s->pool32);
+    if (s->poolc) cudaFree(s->poolc);
     if (s->pin) cudaFreeHost(s->pin);
     if (s->ev[0]) cudaEventDestroy(s->ev[0]);
     if (s->ev[1]) cudaEventDestroy(s->ev[1]);
@@ -616,6 +635,23 @@ static nl_status ensure_fp32(nl_solver* s)
     s->pool32_bytes = bytes;
     cudaMemsetAsync(s->pool32, 0, bytes, s->st);
     trsv_work_carve(s->pool32, s->N, true, &s->tw32);
+    return NL_OK;
+}
+
+// gmres_factors32: the single-precision copy of the binary16 factors.
+static nl_status ensure_factors32(nl_solver* s)
+{
+    NL_TRY(ensure_fp32(s));
+    if (s->poolc) return NL_OK;
+    const size_t bytes = (size_t)s->N * s->ld * sizeof(float);
+    if (cudaMalloc(&s->poolc, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->poolc = nullptr;
+        set_error("single-precision factor copy: cudaMalloc of %zu bytes failed", bytes);
+        return NL_ENOMEM;
+    }
+    s->poolc_bytes = bytes;
+    s->LU32c = (float*)s->poolc;
     return NL_OK;
 }
 
@@ -685,6 +721,10 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
     Host H{s->pin, st, &launches};
     if (mode == NL_FP64LU) NL_TRY(ensure_fp64(s));
     if (mode == NL_F32) NL_TRY(ensure_fp32(s));
+    const bool f32fac = s->cfg.gmres_factors32 && (mode == NL_GMRESIR16 || mode == NL_IR16_GMRES);
+    if (f32fac) NL_TRY(ensure_factors32(s));
+    s->lb.LU32 = f32fac ? s->LU32c : nullptr;
+    s->lb.tw32 = f32fac ? &s->tw32 : nullptr;
 
     double* x = s->xa;
     double* xn = s->xb;
@@ -762,6 +802,11 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
                 ++launches;
                 ++S.lu_pivoted;
                 if (mode != NL_F16) NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
+            }
+            if (f32fac) {
+                NL_TRY(launch_promote16(n, s->J16, s->ld, s->LU32c, s->ld, st));
+                NL_TRY(trsv_prepare32(n, s->LU32c, s->ld, s->ipiv, s->tw32, st, &launches));
+                ++launches;
             }
         }
         cudaEventRecord(s->evp[3], st);

@@ -923,6 +923,24 @@ nl_status trsv_solve32(int N, const float* LU, int64_t ld, const float* v, float
     return solve_impl<float, float>(N, LU, ld, v, z, w, epoch, st, launches);
 }
 
+// The binary16 factors promoted to a single-precision copy (exact), for the
+// GMRES-IR preconditioner that solves with single-precision factors.
+__global__ void __launch_bounds__(256) k_promote16(int N, const __half* __restrict__ A, int64_t lda,
+                                                   float* __restrict__ B, int64_t ldb)
+{
+    const int64_t i = blockIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < N; j += gridDim.x * blockDim.x)
+        B[i * ldb + j] = __half2float(A[i * lda + j]);
+}
+
+nl_status launch_promote16(int N, const __half* A, int64_t lda, float* B, int64_t ldb, cudaStream_t st)
+{
+    if (N < 1 || N > 32768) return NL_EINVAL;
+    k_promote16<<<dim3((unsigned)std::min<int64_t>(cdiv(N, 256), 8), (unsigned)N), 256, 0, st>>>(N, A, lda, B, ldb);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
 // ------------------------------------------------- binary16 arithmetic --
 // Both triangular solves with every product and difference rounded to
 // binary16: the step of the two-precision F16 Newton method (Section 1.3),

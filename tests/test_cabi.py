@@ -54,7 +54,8 @@ def test_invalid_arguments_rejected_before_device_use():
     assert "bad" in nl.last_error() or "NULL" in nl.last_error()
     L.nl_destroy(None)  # no-op
     for bad in ({"trsv_cluster": 3}, {"trsv_cluster": -2}, {"trsv_cluster": 32}, {"lu_path": 2}, {"lu_stream": 1},
-                {"lu_stream": -2}, {"ir_variant": 2}, {"ir_variant": -1}):
+                {"lu_stream": -2}, {"ir_variant": 2}, {"ir_variant": -1}, {"gmres_factors32": 2},
+                {"gmres_factors32": -1}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
     # the two-precision kernel entries check their arguments before any device call
     assert L.nl_lu32(0, None, 0, None, 0, None, None) == nl.NL_EINVAL
@@ -89,6 +90,8 @@ def test_batch_arguments_validated():
     c = np.ascontiguousarray([0.5], dtype=np.float64)
     assert L.nl_batch_create(1, N.ctypes.data, c.ctypes.data, nl.ctypes.byref(nl.config(ir_variant=1)),
                              nl.ctypes.byref(h)) == nl.NL_EINVAL
+    assert L.nl_batch_create(1, N.ctypes.data, c.ctypes.data, nl.ctypes.byref(nl.config(gmres_factors32=1)),
+                             nl.ctypes.byref(h)) == nl.NL_EINVAL
     assert L.nl_batch_solve(None, None, 1e-10, nl.NL_IR16_GMRES, None) == nl.NL_EINVAL
     assert L.nl_batch_stats(None, 0, None) == nl.NL_EINVAL
     assert L.nl_lu_grouped(0, None, None, None, None, 0, 0, 0, None, None) == nl.NL_EINVAL
@@ -119,6 +122,9 @@ def test_server_no_device_is_an_error():
     # F16 needs nothing beyond the handle; F32 adds the single-precision solve's workspace
     assert nl.footprint_bytes(1024, "F16") == nl.footprint_bytes(1024, "IR16")
     assert nl.footprint_bytes(1024, "F32") > nl.footprint_bytes(1024, "IR16")
+    # the single-precision factor copy: 4 N ld bytes more, and only for the GMRES-IR modes
+    assert nl.footprint_bytes(1024, "GMRESIR16", gmres_factors32=1) >= nl.footprint_bytes(1024, "GMRESIR16") + 4 * 1024 * 1024
+    assert nl.footprint_bytes(1024, "IR16", gmres_factors32=1) == nl.footprint_bytes(1024, "IR16")
     # the autotuning setting (-1) sizes the handle for the largest panel width
     for N in (1, 700, 4096):
         assert nl.footprint_bytes(N, lu_nb=-1) == nl.footprint_bytes(N, lu_nb=128) >= nl.footprint_bytes(N, lu_nb=32)

@@ -226,6 +226,35 @@ def test_ir16_scaled_half_correction(N, c):
         assert s.stats()["newton_iters"] == st["newton_iters"]
 
 
+@pytest.mark.parametrize("N,c,mode", [(512, 0.9, "GMRESIR16"), (1000, 0.99, "GMRESIR16"),
+                                      (1024, 0.9999, "GMRESIR16"), (700, 0.99, "IR16_GMRES")])
+def test_gmresir_single_precision_factor_copy(N, c, mode):
+    """GMRES-IR preconditioned with a single-precision copy of the binary16
+    factors (Section 2.3, gmres_factors32 = 1): the same values as the
+    on-the-fly promotion, applied by the blocked single-precision solve in
+    another summation order.  Newton counts as the oracle's, linear counts
+    within one, the same solution, and the same Newton counts as with the
+    on-the-fly preconditioner."""
+    # IR16_GMRES: one IR correction cannot reach eta = 1e-6, so the first step
+    # falls back to GMRES-IR and every later step uses it
+    cfg, ocfg = ({"eta_j": 1e-6, "ir_maxit": 1}, {"eta": 1e-6, "ir_maxit": 1}) if mode == "IR16_GMRES" else ({}, {})
+    with nl.Solver(N, c, gmres_factors32=1, **cfg) as s:
+        x, status = s.solve(tol=1e-10, mode=mode)
+        st = s.stats()
+    om = "IR16GM" if mode == "IR16_GMRES" else mode
+    xo, ro = O.newton(N, c, om, tol=1e-10, **ocfg)
+    if mode == "IR16_GMRES":
+        assert st["lin_failed"][0] == 1 and ro["lin_failed"][0] == 1
+    assert status == nl.NL_OK and ro["status"] == 0
+    check_counts(st, ro, "GMRESIR16", ill=c >= 0.9999)
+    kappa = 1.0 / math.sqrt(1.0 - c)
+    tol = 1e-10 if c <= 0.99 else 1e-10 + 10.0 * kappa * max(st["hist"][-1], ro["hist"][-1])
+    assert rel_inf(x, xo) <= tol
+    with nl.Solver(N, c, **cfg) as s:
+        s.solve(tol=1e-10, mode=mode)
+        assert s.stats()["newton_iters"] == st["newton_iters"]
+
+
 @pytest.mark.parametrize("N,c", [(64, 0.9), (1024, 0.99)])
 def test_f16_two_precision_newton(N, c):
     """F16 column (Section 1.3): J_h factored in half precision and ONE
