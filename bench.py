@@ -542,6 +542,21 @@ def main():
                                    "lin_iters": s["lin_iters"], "ms": s["t_total_ms"], "lin_ms": s["t_lin_ms"]}
                           for c, s in stc.items()}}
 
+    # the binary16-arithmetic solve pair of the F16 step: a chain of 2N barrier steps in one CTA
+    try:
+        nl.kernel_timing("k_lusolve16h")
+        one_tp(SWEEP[0], "F16")
+        n16, ms16 = nl.kernel_timing(None)
+        if n16:
+            us = ms16 / n16 * 1e3
+            fbytes = 2.0 * N_BENCH * N_BENCH  # both binary16 triangles
+            extra["two_precision"]["F16"]["k_lusolve16h"] = {
+                "launches": n16, "avg_us": us, "bound": "latency", "ns_per_barrier_step": us * 1e3 / (2 * N_BENCH),
+                "factor_bytes_per_launch": fbytes, "achieved_GBps": fbytes / (us * 1e-6) / 1e9,
+                "frac_of_hbm": fbytes / (us * 1e-6) / 1e9 / hbm_peak}
+    except nl.NLError as e:
+        extra["two_precision"]["F16"]["k_lusolve16h"] = {"error": str(e)}
+
     # interprecision ablation (Section 2.3): IR16 with the scaled binary16 correction of eq. (2.19)
     # against the on-the-fly correction of the "ir16" sweep above
     extra["ir16_scaled_half"] = alt_sweep("IR16", ir_variant=1)

@@ -190,10 +190,13 @@ const char* nl_last_error(void);
 /* Per-kernel timing for measurement.  Returns the number of launches and the
  * summed device time (CUDA events on each launch's stream) of the kernel
  * class timed since the previous call, then starts timing `kernel_class`
- * (NULL or "" stops timing).  Classes: "k_diag_lu16", "k_offdiag16"
- * (half-precision LU), "k_diag_lu", "k_offdiag" (double LU), "k_tc_gemm",
- * "k_trsv_cl" (cluster triangular solve), "k_trsv_mb" (mailbox triangular
- * solve), "k_gemv_residual".  Not thread-safe against
+ * (NULL or "" stops timing).  Classes: "k_panel16" (streaming panel),
+ * "k_diag_lu16", "k_offdiag16" (half-precision LU, two-launch panel),
+ * "k_diag_lu", "k_offdiag" (double LU), "k_tc_gemm" (tensor-core trailing
+ * update), "k_invdiag" (diagonal-block inverses), "k_trsv_cl" (cluster
+ * triangular solve), "k_trsv_mb" (mailbox triangular solve),
+ * "k_lusolve16h" (binary16-arithmetic solve), "k_gemv_residual".  Not
+ * thread-safe against
  * concurrent solves on other threads.  Synchronises the recorded events. */
 nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* total_ms);
 
