@@ -125,7 +125,8 @@ typedef struct {
     double fnorm0;                    /* ||F(x0)||_2 */
     double fnorm;                     /* ||F(x_final)||_2 */
     double hist[NL_MAX_HIST];         /* ||F(x_n)|| / ||F(x_0)||, n = 0..newton_iters */
-    int lin_iters[NL_MAX_HIST];       /* per Newton step: IR corrections or GMRES Arnoldi steps */
+    int lin_iters[NL_MAX_HIST];       /* per Newton step: IR corrections or GMRES Arnoldi steps
+                                         (0 for the direct solves of NL_FP64LU, NL_F32, NL_F16) */
     int lin_outer[NL_MAX_HIST];       /* per Newton step: IR / GMRES-IR outer corrections */
     int lin_failed[NL_MAX_HIST];      /* per Newton step: IR failure rule fired (Section 3.1) */
     double lin_relres[NL_MAX_HIST];   /* per Newton step: final ||J32 u - b|| / ||b|| */
@@ -180,7 +181,9 @@ void nl_destroy(nl_solver* s);
 nl_status nl_set_c(nl_solver* s, double c);
 
 /* Device bytes a handle for N needs in `mode` (NL_FP64LU adds the double
- * Jacobian and its workspace), cfg as for nl_create (NULL = defaults).
+ * Jacobian and its workspace, NL_F32 the single-precision solve's workspace,
+ * gmres_factors32 with a GMRES-IR mode that workspace and the single-precision
+ * factor copy), cfg as for nl_create (NULL = defaults).
  * -1 on invalid arguments.  Used for admission by memory footprint. */
 int64_t nl_footprint_bytes(int64_t N, nl_mode mode, const nl_config* cfg);
 
