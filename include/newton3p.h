@@ -111,7 +111,12 @@ typedef struct {
                             of precision inside the solves; the same values, so the same
                             preconditioner up to the solves' summation order).  The batched path
                             accepts only 0 */
-    int reserved[3];
+    int lu16_arith;      /* [0] arithmetic of the half-precision factorisation: 0 = binary32 arithmetic on
+                            binary16 storage (lu_nb above); 1 = every operation rounded to binary16
+                            (the arithmetic behind the paper's F16 column): right-looking partial
+                            pivoting, one grid-wide step per column, slow (as nl_lu16 path 3).  The
+                            batched path accepts only 0 */
+    int reserved[2];
 } nl_config;
 
 #define NL_MAX_HIST 128
@@ -416,7 +421,12 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
  * pivoting keeps every diagonal pivot, and refactor with interchanges from a
  * saved copy of A if not (same result either way); 1 = interchanging path
  * only; 2 = as 0 with the diagonal block and the off-diagonal solves of each
- * panel in two launches instead of one streaming launch (same result).
+ * panel in two launches instead of one streaming launch (same result);
+ * 3 = every operation rounded to binary16 instead (l_ik = fl16(a_ik/a_kk),
+ * a_ij <- fl16(a_ij - fl16(l_ik a_kj)) in increasing k, the first row of
+ * largest |a_ik| as pivot): the arithmetic of the paper's F16 column; nb and
+ * gemm are ignored, and *info_host is also set (to -1) after a binary16
+ * overflow, returned as NL_ENUMERIC.
  * Allocates its workspace (and the copy) with cudaMallocAsync on
  * `stream`.  Synchronises the stream. */
 nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,

@@ -630,7 +630,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 || d.trsv_cluster == 8 ||
           d.trsv_cluster == 16) ||
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant != 0 ||
-        d.gmres_factors32 != 0) {
+        d.gmres_factors32 != 0 || d.lu16_arith != 0) {
         set_error("nl_batch_create: invalid configuration");
         return NL_EINVAL;
     }

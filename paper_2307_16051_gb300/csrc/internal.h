@@ -46,6 +46,11 @@ nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast
 // Binary32 storage and arithmetic (F32 Newton), always with interchanges;
 // w carved for the single-precision panel (fp64 = false).
 nl_status lu32_factor(int N, float* A, int64_t ld, int* ipiv, int nb, const LuWork& w, cudaStream_t st, int* launches);
+// Every operation rounded to binary16 (the F16 column's arithmetic), partial
+// pivoting, one cooperative launch.  Asynchronous: w.info[0] = first zero
+// pivot (1-based) or 0, w.info[1] != 0 after a binary16 overflow; a barrier
+// that gave up sets the tensor-core error word (or w.info[2]).
+nl_status lu16_factor_arith(int N, __half* A, int64_t ld, int* ipiv, const LuWork& w, cudaStream_t st);
 nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* B, int64_t ldb,
                         __half* C, int64_t ldc, int gemm, cudaStream_t st);
 

@@ -1908,6 +1908,188 @@ nl_status lu32_factor(int N, float* A, int64_t ld, int* ipiv, int nb, const LuWo
     return lu_factor_impl<float, float, 16, false>(N, A, ld, ipiv, nb, 1, false, w, st, launches);
 }
 
+// ------------------------------------------------ binary16 arithmetic LU --
+// Partial-pivot LU with every operation rounded to binary16, the arithmetic
+// of the paper's F16 column (Section 1.3): at step k the pivot is the first
+// row of largest |a_ik| (i >= k), rows k and p are swapped whole,
+// l_ik = fl16(a_ik / a_kk) and a_ij <- fl16(a_ij - fl16(l_ik a_kj)) for
+// i, j > k, so every entry takes its updates in increasing k.  One
+// cooperative launch, one CTA per SM: a warp updates one row at a time, the
+// next column's pivot candidates are formed during the update, and each step
+// ends at a bounded grid barrier (one more after a row swap).  The product of
+// two binary16 numbers is exact in binary32; the difference and the quotient
+// are formed in binary32 and rounded once more, to binary16, which is the
+// correctly rounded result (24 >= 2 * 11 + 2).  Matrix reads bypass L1
+// (other SMs write the rows between barriers).
+constexpr int kHaThreads = 512;
+constexpr int kHaWarps = kHaThreads / 32;
+
+__device__ __forceinline__ float h16r(float v) { return __half2float(__float2half_rn(v)); }
+
+// {|a| bits, ~i}: the largest packed value is the first row of largest |a|.
+__device__ __forceinline__ unsigned long long ha_pack(float a, int i)
+{
+    return ((unsigned long long)__float_as_uint(fabsf(a)) << 32) | (unsigned long long)(~(unsigned)i);
+}
+
+__device__ __forceinline__ unsigned long long ha_block_max(unsigned long long v, unsigned long long* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    __syncthreads();  // red is reused across calls
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    v = 0;
+#pragma unroll
+    for (int q = 0; q < kHaWarps; ++q) v = red[q] > v ? red[q] : v;
+    return v;
+}
+
+// Grid barrier over co-resident CTAs: bar[0] counts arrivals, bar[1] is the
+// generation (both zero at launch).  Bounded: false after recording a timeout,
+// or when another CTA recorded an error.
+__device__ bool ha_grid_sync(unsigned* bar, unsigned& gen, unsigned* err)
+{
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicAdd(&bar[1], 1u);
+        } else {
+            long long spins = 0;
+            while ((unsigned)ld_acquire_gpu((const int*)&bar[1]) == gen) {
+                if (*(volatile unsigned*)err) {
+                    ok = 0;
+                    break;
+                }
+                if (++spins > kSpinLimit) {
+                    atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        ++gen;
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(kHaThreads, 1) k_lu16_arith(__half* __restrict__ A, int64_t lda, int N,
+                                                              int* __restrict__ ipiv, int* __restrict__ info,
+                                                              unsigned* __restrict__ bar,
+                                                              unsigned long long* __restrict__ cand,
+                                                              unsigned* __restrict__ err)
+{
+    __shared__ unsigned long long red[kHaWarps];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int G = gridDim.x;
+    const int gw = blockIdx.x * kHaWarps + (tid >> 5), nw = G * kHaWarps;  // this warp, all warps
+    unsigned gen = 0;
+    // pivot candidates of column 0
+    unsigned long long nb = 0;
+    if (lane == 0)
+        for (int i = gw; i < N; i += nw) {
+            const unsigned long long c = ha_pack(__half2float(__ldcg(A + (int64_t)i * lda)), i);
+            nb = c > nb ? c : nb;
+        }
+    nb = ha_block_max(nb, red);
+    if (tid == 0) cand[blockIdx.x] = nb;
+    if (!ha_grid_sync(bar, gen, err)) return;
+    for (int k = 0; k < N; ++k) {
+        unsigned long long b = 0;
+        for (int g = tid; g < G; g += kHaThreads) {
+            const unsigned long long c = __ldcg(cand + (k & 1) * G + g);
+            b = c > b ? c : b;
+        }
+        b = ha_block_max(b, red);
+        const int p = (int)(~(unsigned)(b & 0xffffffffull));
+        if (blockIdx.x == 0 && tid == 0) ipiv[k] = p;
+        if (p != k && p > k && p < N) {  // swap rows k and p whole
+            __half* Rk = A + (int64_t)k * lda;
+            __half* Rp = A + (int64_t)p * lda;
+            for (int j = blockIdx.x * kHaThreads + tid; j < N; j += G * kHaThreads) {
+                const __half t = __ldcg(Rk + j);
+                Rk[j] = __ldcg(Rp + j);
+                Rp[j] = t;
+            }
+            if (!ha_grid_sync(bar, gen, err)) return;
+        }
+        const __half* Rk = A + (int64_t)k * lda;
+        const float akk = __half2float(__ldcg(Rk + k));
+        if (akk == 0.0f && blockIdx.x == 0 && tid == 0) atomicCAS(info, 0, k + 1);
+        if (k == N - 1) break;
+        nb = 0;
+        if (akk == 0.0f) {  // no elimination at this step; the next column's candidates as they stand
+            if (lane == 0)
+                for (int i = k + 1 + gw; i < N; i += nw) {
+                    const unsigned long long c = ha_pack(__half2float(__ldcg(A + (int64_t)i * lda + k + 1)), i);
+                    nb = c > nb ? c : nb;
+                }
+        } else {
+            bool inf = false;
+            for (int i = k + 1 + gw; i < N; i += nw) {
+                __half* Ri = A + (int64_t)i * lda;
+                const float l = h16r(__fdiv_rn(__half2float(__ldcg(Ri + k)), akk));
+                __syncwarp();  // every lane has read a_ik before lane 0 overwrites it
+                if (lane == 0) Ri[k] = __float2half_rn(l);
+                for (int j = k + 1 + lane; j < N; j += 32) {
+                    const float pr = h16r(l * __half2float(__ldcg(Rk + j)));
+                    const float v = h16r(__half2float(__ldcg(Ri + j)) - pr);
+                    Ri[j] = __float2half_rn(v);
+                    inf |= isinf(v);
+                    if (j == k + 1) {
+                        const unsigned long long c = ha_pack(v, i);
+                        nb = c > nb ? c : nb;
+                    }
+                }
+            }
+            if (inf) atomicOr(info + 1, 1);
+        }
+        nb = ha_block_max(nb, red);
+        if (tid == 0) cand[((k + 1) & 1) * G + blockIdx.x] = nb;
+        if (!ha_grid_sync(bar, gen, err)) return;
+    }
+}
+
+nl_status lu16_factor_arith(int N, __half* A, int64_t ld, int* ipiv, const LuWork& w, cudaStream_t st)
+{
+    static std::atomic<int> grid_cache{0};
+    int grid = grid_cache.load();
+    if (grid == 0) {
+        int per_sm = 0;
+        NL_CUDA_OK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lu16_arith, kHaThreads, 0));
+        if (per_sm < 1) {
+            set_error("binary16-arithmetic LU: the kernel does not fit on an SM");
+            return NL_ECUDA;
+        }
+        grid = std::min(num_sms(), 128 * 128 / 2);  // one CTA per SM; two candidate rows per CTA fit in pub
+        grid_cache.store(grid);
+    }
+    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 6 * sizeof(int), st));  // info, overflow, (err), barrier count and generation
+    unsigned* err = tc_error_word();
+    if (!err) err = (unsigned*)(w.info + 2);
+    unsigned* bar = (unsigned*)(w.info + 4);
+    int* info = w.info;
+    unsigned long long* cand = w.pub;
+    int Nv = N;
+    int64_t ldv = ld;
+    void* args[] = {(void*)&A, (void*)&ldv, (void*)&Nv, (void*)&ipiv, (void*)&info, (void*)&bar, (void*)&cand,
+                    (void*)&err};
+    NL_CUDA_OK(cudaLaunchCooperativeKernel((const void*)k_lu16_arith, dim3(grid), dim3(kHaThreads), args, 0, st));
+    return NL_OK;
+}
+
 }  // namespace nl
 
 // ================================================================ grouped ==

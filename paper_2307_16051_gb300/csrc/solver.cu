@@ -453,7 +453,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         d.lu_path > 1 || !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 ||
                            d.trsv_cluster == 8 || d.trsv_cluster == 16) ||
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant < 0 || d.ir_variant > 1 ||
-        d.gmres_factors32 < 0 || d.gmres_factors32 > 1 ||
+        d.gmres_factors32 < 0 || d.gmres_factors32 > 1 || d.lu16_arith < 0 || d.lu16_arith > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
         d.lu_nb < -1) {
         set_error("nl_create: invalid configuration");
@@ -782,6 +782,24 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
                 ++S.lu_pivoted;
             }
             NL_TRY(trsv_prepare64(n, s->J64, s->ld, s->ipiv64, s->tw64, st, &launches));
+        } else if (s->cfg.lu16_arith && mode != NL_F32) {
+            // every operation of the factorisation rounded to binary16 (interchanges included)
+            NL_TRY(lu16_factor_arith(n, s->J16, s->ld, s->ipiv, s->luw, st));
+            ++launches;
+            NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            if (mode != NL_F16) NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
+            if (f32fac) {
+                NL_TRY(launch_promote16(n, s->J16, s->ld, s->LU32c, s->ld, st));
+                NL_TRY(trsv_prepare32(n, s->LU32c, s->ld, s->ipiv, s->tw32, st, &launches));
+                ++launches;
+            }
+            NL_CUDA_OK(cudaStreamSynchronize(st));
+            memcpy(iflag, s->pin, sizeof(iflag));
+            if (iflag[1]) {
+                status = NL_ENUMERIC;
+                set_error("binary16 overflow in the factorisation");
+                break;
+            }
         } else if (mode == NL_F32) {
             // two-precision Newton, F32: J32 factored in place in single precision
             NL_TRY(lu32_factor(n, s->J32, s->ld, s->ipiv, s->nb, s->luw, st, &launches));
@@ -1037,15 +1055,48 @@ static nl_status lu_entry(int64_t N, S* A, int64_t ld, int32_t* ipiv, int nb, in
     return s;
 }
 
+// nl_lu16 path 3: the binary16-arithmetic factorisation.
+static nl_status lu16_arith_entry(int n, __half* A, int64_t ld, int32_t* ipiv, int32_t* info_host, cudaStream_t st)
+{
+    void* wk = nullptr;
+    NL_CUDA_OK(cudaMallocAsync(&wk, lu_work_bytes(n, 128, false) + 256, st));
+    LuWork w;
+    lu_work_carve(wk, n, 128, false, &w);
+    int iflag[2] = {0, 0};
+    nl_status s = lu16_factor_arith(n, A, ld, ipiv, w, st);
+    if (s == NL_OK && cudaMemcpyAsync(iflag, w.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        s = NL_ECUDA;
+    unsigned e = 0;
+    unsigned* tce = tc_error_word();
+    unsigned* err = tce ? tce : (unsigned*)(w.info + 2);
+    if (s == NL_OK && cudaMemcpyAsync(&e, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        s = NL_ECUDA;
+    cudaFreeAsync(wk, st);
+    NL_CUDA_OK(cudaStreamSynchronize(st));
+    if (s != NL_OK) return s;
+    if (e) {
+        if (tce) cudaMemset(tce, 0, sizeof(unsigned));
+        set_error("binary16-arithmetic LU: a grid barrier gave up");
+        return NL_ETIMEOUT;
+    }
+    if (info_host) *info_host = iflag[1] ? -1 : iflag[0];
+    if (iflag[1]) {
+        set_error("binary16-arithmetic LU: overflow to infinity");
+        return NL_ENUMERIC;
+    }
+    return iflag[0] ? NL_ESINGULAR : NL_OK;
+}
+
 extern "C" {
 
 nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,
                   void* stream)
 {
-    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2 || path < 0 || path > 2) {
+    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2 || path < 0 || path > 3) {
         set_error("nl_lu16: bad argument");
         return NL_EINVAL;
     }
+    if (path == 3) return lu16_arith_entry((int)N, (__half*)A16, ld, ipiv, info_host, (cudaStream_t)stream);
     if (nb == 0) nb = 128;
     if (gemm == 0) gemm = 2;
     if (gemm == 2 && (nb % 64 || !tc_gemm_supported())) gemm = 1;

@@ -35,7 +35,8 @@ class Config(ctypes.Structure):
                 ("gmres_tol", ctypes.c_double), ("gmres_maxcycles", ctypes.c_int), ("newton_maxit", ctypes.c_int),
                 ("tau_a", ctypes.c_double), ("lu_nb", ctypes.c_int), ("trailing_gemm", ctypes.c_int),
                 ("lu_path", ctypes.c_int), ("trsv_cluster", ctypes.c_int), ("lu_stream", ctypes.c_int),
-                ("ir_variant", ctypes.c_int), ("gmres_factors32", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("ir_variant", ctypes.c_int), ("gmres_factors32", ctypes.c_int), ("lu16_arith", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Stats(ctypes.Structure):

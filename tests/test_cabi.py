@@ -55,7 +55,7 @@ def test_invalid_arguments_rejected_before_device_use():
     L.nl_destroy(None)  # no-op
     for bad in ({"trsv_cluster": 3}, {"trsv_cluster": -2}, {"trsv_cluster": 32}, {"lu_path": 2}, {"lu_stream": 1},
                 {"lu_stream": -2}, {"ir_variant": 2}, {"ir_variant": -1}, {"gmres_factors32": 2},
-                {"gmres_factors32": -1}):
+                {"gmres_factors32": -1}, {"lu16_arith": 2}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
     # the two-precision kernel entries check their arguments before any device call
     assert L.nl_lu32(0, None, 0, None, 0, None, None) == nl.NL_EINVAL
@@ -91,6 +91,8 @@ def test_batch_arguments_validated():
     assert L.nl_batch_create(1, N.ctypes.data, c.ctypes.data, nl.ctypes.byref(nl.config(ir_variant=1)),
                              nl.ctypes.byref(h)) == nl.NL_EINVAL
     assert L.nl_batch_create(1, N.ctypes.data, c.ctypes.data, nl.ctypes.byref(nl.config(gmres_factors32=1)),
+                             nl.ctypes.byref(h)) == nl.NL_EINVAL
+    assert L.nl_batch_create(1, N.ctypes.data, c.ctypes.data, nl.ctypes.byref(nl.config(lu16_arith=1)),
                              nl.ctypes.byref(h)) == nl.NL_EINVAL
     assert L.nl_batch_solve(None, None, 1e-10, nl.NL_IR16_GMRES, None) == nl.NL_EINVAL
     assert L.nl_batch_stats(None, 0, None) == nl.NL_EINVAL

@@ -308,6 +308,32 @@ def test_lusolve16_synthetic_factors(N):
     assert np.all(np.abs(got - ref) <= 1e-5 * np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("N,kind", [(1, "rand"), (2, "rand"), (7, "rand"), (100, "rand"), (333, "rand"),
+                                    (600, "piv"), (50, "sing"), (1000, "rand")])
+def test_lu16_binary16_arithmetic_bit_exact(N, kind):
+    """nl_lu16 path 3: every operation rounded to binary16 (the arithmetic of
+    the F16 column), partial pivoting with whole-row swaps: pivots, factors
+    and info bitwise the oracle's binary16 LU.  A Gaussian matrix swaps rows
+    at most steps; "sing" has a zero column (info = 11, that step skipped)."""
+    if kind == "piv":
+        A = W.pivot_forcing_matrix(N, 12000 + N)[0]
+    else:
+        A = W.random_matrix(N, 12000 + N)
+        if kind == "sing":
+            A[:, 10] = 0.0
+    A16 = O.fl16(A)
+    LUo, ipivo, infoo, ovfo = O.lu16(A16)
+    assert not ovfo
+    ld = ((N + 63) // 64) * 64
+    Ad = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    Ad[:, :N] = T(A16.astype(np.float16))
+    ipiv = torch.empty(N, device=dev(), dtype=torch.int32)
+    info = nl.lu16(N, Ad, ld, ipiv, path=3)
+    assert info == infoo == (11 if kind == "sing" else 0)
+    assert np.array_equal(ipiv.cpu().numpy(), ipivo)
+    assert np.array_equal(Ad.cpu().numpy()[:, :N].astype(np.float64), LUo)
+
+
 # ------------------------------------------------- F32 / F16 columns --
 
 @pytest.mark.parametrize("N,nb", [(1, 16), (50, 16), (200, 64), (301, 128), (1000, 128)])

@@ -255,6 +255,39 @@ def test_gmresir_single_precision_factor_copy(N, c, mode):
         assert s.stats()["newton_iters"] == st["newton_iters"]
 
 
+def test_paper_mode_table2_f16_column_n4096(table2):
+    """The F16 column of the paper's Table 2 at its own size (N = 4096,
+    c = .99) with the factorisation in binary16 arithmetic (lu16_arith = 1)
+    and the binary16-arithmetic solve: ten steps without converging, steps
+    1-3 within one unit of the printed fourth digit, steps 4-10 within 10%
+    (the oracle with the same arithmetic gives the same)."""
+    with nl.Solver(4096, 0.99, newton_maxit=10, lu16_arith=1) as s:
+        _, status = s.solve(tol=1e-9, mode="F16")
+        h = s.stats()["hist"]
+    p = table2["F16"]
+    assert status == nl.NL_ENOTCONV and len(h) == len(p) == 11, h
+    for n in range(1, 4):
+        unit = 1e-3 * 10 ** np.floor(np.log10(p[n]))
+        assert abs(h[n] - p[n]) <= unit, (n, h[n], p[n])
+    for n in range(4, 11):
+        assert abs(h[n] - p[n]) <= 0.10 * p[n], (n, h[n], p[n])
+
+
+@pytest.mark.parametrize("mode", ["IR16", "GMRESIR16"])
+def test_binary16_arithmetic_factorisation_three_precision(mode):
+    """The three-precision modes with the factorisation in binary16 arithmetic
+    (lu16_arith = 1 on the GPU, lu_nb = 0 in the oracle): Newton counts as
+    the oracle's, linear counts within one, the same solution."""
+    N, c = 512, 0.99
+    with nl.Solver(N, c, lu16_arith=1) as s:
+        x, status = s.solve(tol=1e-10, mode=mode)
+        st = s.stats()
+    xo, ro = O.newton(N, c, mode, tol=1e-10, lu_nb=0)
+    assert status == nl.NL_OK and ro["status"] == 0
+    check_counts(st, ro, mode)
+    assert rel_inf(x, xo) <= 1e-10
+
+
 @pytest.mark.parametrize("N,c", [(64, 0.9), (1024, 0.99)])
 def test_f16_two_precision_newton(N, c):
     """F16 column (Section 1.3): J_h factored in half precision and ONE
