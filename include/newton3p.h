@@ -114,8 +114,10 @@ typedef struct {
     int lu16_arith;      /* [0] arithmetic of the half-precision factorisation: 0 = binary32 arithmetic on
                             binary16 storage (lu_nb above); 1 = every operation rounded to binary16
                             (the arithmetic behind the paper's F16 column): right-looking partial
-                            pivoting, one grid-wide step per column, slow (as nl_lu16 path 3).  The
-                            batched path accepts only 0 */
+                            pivoting, one grid-wide step per column, slow (as nl_lu16 path 3); one
+                            cooperative launch with a CTA on every SM, so it is meant for solves that
+                            have the GPU to themselves (its barriers are bounded: NL_ETIMEOUT, not a
+                            hang, if its CTAs cannot all run).  The batched path accepts only 0 */
     int reserved[2];
 } nl_config;
 
