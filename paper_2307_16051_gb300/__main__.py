@@ -2,6 +2,7 @@
 GPU and print the solver statistics as JSON.
 
     python -m paper_2307_16051_gb300 --N 4096 --c 0.99 --mode GMRESIR16 --repeat 2
+    python -m paper_2307_16051_gb300 --N 4096 --c 0.99 --mode F16 --lu16-arith 1 --newton-maxit 10 --tol 1e-9
     python -m paper_2307_16051_gb300 --batch 512 --repeat 2          # the batched workload
     python -m paper_2307_16051_gb300 --serve-seconds 2               # the serving trace
 """
@@ -20,6 +21,13 @@ def main():
     ap.add_argument("--repeat", type=int, default=1, help="solves on the same handle (the last one is reported)")
     ap.add_argument("--eta", type=float, default=1e-4)
     ap.add_argument("--lu-nb", type=int, default=0)
+    ap.add_argument("--newton-maxit", type=int, default=30)
+    ap.add_argument("--ir-variant", type=int, default=0, choices=[0, 1],
+                    help="1: IR with the scaled binary16 correction of eq. (2.19)")
+    ap.add_argument("--gmres-factors32", type=int, default=0, choices=[0, 1],
+                    help="1: GMRES-IR preconditioned with a single-precision copy of the factors")
+    ap.add_argument("--lu16-arith", type=int, default=0, choices=[0, 1],
+                    help="1: the half-precision factorisation with every operation in binary16")
     ap.add_argument("--batch", type=int, default=0,
                     help="solve the first BATCH instances of the batched workload (N log-uniform in [64, 2048], "
                          "c uniform in [0.1, 0.999], seed 230716051) together")
@@ -46,7 +54,8 @@ def main():
             S.drain(600.0)
             print(json.dumps(S.info()))
         return
-    with nl.Solver(args.N, args.c, eta_j=args.eta, lu_nb=args.lu_nb) as s:
+    with nl.Solver(args.N, args.c, eta_j=args.eta, lu_nb=args.lu_nb, newton_maxit=args.newton_maxit,
+                   ir_variant=args.ir_variant, gmres_factors32=args.gmres_factors32, lu16_arith=args.lu16_arith) as s:
         for _ in range(max(1, args.repeat)):
             x, status = s.solve(tol=args.tol, mode=args.mode or "GMRESIR16")
         st = s.stats()
