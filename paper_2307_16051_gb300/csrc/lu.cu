@@ -1923,6 +1923,7 @@ nl_status lu32_factor(int N, float* A, int64_t ld, int* ipiv, int nb, const LuWo
 // (other SMs write the rows between barriers).
 constexpr int kHaThreads = 512;
 constexpr int kHaWarps = kHaThreads / 32;
+constexpr int kHaU = 8;  // row entries per lane per batch of loads
 
 __device__ __forceinline__ float h16r(float v) { return __half2float(__float2half_rn(v)); }
 
@@ -2043,14 +2044,29 @@ __global__ void __launch_bounds__(kHaThreads, 1) k_lu16_arith(__half* __restrict
                 const float l = h16r(__fdiv_rn(__half2float(__ldcg(Ri + k)), akk));
                 __syncwarp();  // every lane has read a_ik before lane 0 overwrites it
                 if (lane == 0) Ri[k] = __float2half_rn(l);
-                for (int j = k + 1 + lane; j < N; j += 32) {
-                    const float pr = h16r(l * __half2float(__ldcg(Rk + j)));
-                    const float v = h16r(__half2float(__ldcg(Ri + j)) - pr);
-                    Ri[j] = __float2half_rn(v);
-                    inf |= isinf(v);
-                    if (j == k + 1) {
-                        const unsigned long long c = ha_pack(v, i);
-                        nb = c > nb ? c : nb;
+                // kHaU entries per lane: all loads issued before the stores (the rows may alias
+                // as far as the compiler knows), the same operations per entry
+                for (int j0 = k + 1; j0 < N; j0 += 32 * kHaU) {
+                    __half rk[kHaU], ri[kHaU];
+#pragma unroll
+                    for (int u = 0; u < kHaU; ++u) {
+                        const int j = j0 + u * 32 + lane;
+                        rk[u] = j < N ? __ldcg(Rk + j) : __ushort_as_half((unsigned short)0);
+                        ri[u] = j < N ? __ldcg(Ri + j) : __ushort_as_half((unsigned short)0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < kHaU; ++u) {
+                        const int j = j0 + u * 32 + lane;
+                        if (j < N) {
+                            const float pr = h16r(l * __half2float(rk[u]));
+                            const float v = h16r(__half2float(ri[u]) - pr);
+                            Ri[j] = __float2half_rn(v);
+                            inf |= isinf(v);
+                            if (j == k + 1) {
+                                const unsigned long long c = ha_pack(v, i);
+                                nb = c > nb ? c : nb;
+                            }
+                        }
                     }
                 }
             }
