@@ -7,14 +7,19 @@ inner tolerance 1e-4, eta = 1e-4): five Newton solves per step.
 
 value     : solves/s with x0/x in HBM (nl_solve_device), CUDA events.
 e2e       : solves/s through nl_solve with host buffers (copies included).
+per_c     : per c, the counts, and each result's error against the oracle's
+            FP64-LU solution (tests/golden/sweep_n4096_x.npy, oracle-written).
 baselines : the same sweep with FP64-LU Newton and with IR16 on the same GPU,
-            and the CPU oracle on the host cores (a bounded sample).
+            and the CPU oracle on the host cores (the whole sweep, measured).
+ablations : the section 2.3 variants and the scaling into the binary16 range.
 batched   : the 512-instance batch (one graph-captured batched solve), and
             the same batch with FP64-LU Newton.
 serving   : the serving trace's first --serve-seconds seconds replayed in
-            real time through the request loop: p50/p99 latency, solves/s.
-large     : one GMRES-IR16 solve at N = 32768, c = .99, autotuned panel width
-            (LU TFLOP/s, residual / triangular-solve GB/s).
+            real time through the request loop: p50/p99 latency, solves/s;
+            FP64-LU Newton served over the same window.
+large     : GMRES-IR16 at N = 32768, c = .99, autotuned panel width (median of
+            three solves; LU TFLOP/s, residual / triangular-solve GB/s), the
+            scaled variant, and FP64-LU Newton on the same GPU.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -211,20 +216,25 @@ def bench_batched(nl, W, torch, dev, steps, warmup, tc_peak, fp64=True):
     return out
 
 
-def bench_large(nl, torch, dev, hbm_peak, tc_peak, N=32768, c=0.99, fp64=False):
-    """One GMRES-IR16 solve at N = 32768, c = .99 with the autotuned panel
-    width: time to 1e-10, the factorisation's TFLOP/s, and the residual GEMV
-    and triangular solves' GB/s (CUDA events on every launch)."""
+def bench_large(nl, torch, dev, hbm_peak, tc_peak, N=32768, c=0.99, fp64=True, reps=3):
+    """GMRES-IR16 solves at N = 32768, c = .99 with the autotuned panel
+    width: time to 1e-10 (the median of `reps` solves after a warm-up), the
+    factorisation's TFLOP/s, and the residual GEMV and triangular solves'
+    GB/s (CUDA events on every launch); the same solve with the scaling into
+    the binary16 range; and FP64-LU Newton on the same GPU (one solve)."""
     s = nl.Solver(N, c, lu_nb=-1)
     x = torch.empty(N, device=dev, dtype=torch.float64)
     s.solve_device(x, tol=TOL, mode="GMRESIR16")  # warm-up
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    status = s.solve_device(x, tol=TOL, mode="GMRESIR16")
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        status = s.solve_device(x, tol=TOL, mode="GMRESIR16")
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
     st = s.stats()
     lu_flop = 2.0 * N ** 3 / 3.0
     lu_ms = st["t_lu_ms"] / max(1, st["newton_iters"])
@@ -249,13 +259,30 @@ def bench_large(nl, torch, dev, hbm_peak, tc_peak, N=32768, c=0.99, fp64=False):
             kern[name] = k
     out = {"workload": f"H-equation N={N}, c={c}, x0=ones, GMRES-IR16 (restart 30, tol 1e-4), eta 1e-4, to 1e-10, "
                        "panel width autotuned", "status": nl.STATUS_NAMES[status], "ms_to_solution": ms,
+           "ms_solves": times, "timing": f"median of {reps} solves after one warm-up solve",
            "newton": st["newton_iters"], "lin_iters": st["lin_iters"], "lu_nb": st["lu_nb"],
            "autotune": [{"nb": nb, "lu_ms": t} for nb, t in st["lu_tune"]],
            "lu": {"ms_per_factorisation": lu_ms, "achieved": lu_tf, "peak": tc_peak, "unit": "TFLOP/s",
                   "frac": lu_tf / tc_peak, "work": "2N^3/3"},
            "t_f_ms": st["t_f_ms"], "t_jac_ms": st["t_jac_ms"], "t_lu_ms": st["t_lu_ms"], "t_lin_ms": st["t_lin_ms"],
            "kernels": kern, "final_rel_res": st["hist"][-1]}
+    xg = x.cpu().numpy()
     s.close()
+    # the scaled factorisation (scale_fp16 = 1): one warm-up, one timed solve
+    with nl.Solver(N, c, lu_nb=-1, scale_fp16=1) as ss:
+        ss.solve_device(x, tol=TOL, mode="GMRESIR16")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sst = ss.solve_device(x, tol=TOL, mode="GMRESIR16")
+        e1.record()
+        torch.cuda.synchronize()
+        S2 = ss.stats()
+        out["scaled"] = {"status": nl.STATUS_NAMES[sst], "ms_to_solution": e0.elapsed_time(e1),
+                         "newton": S2["newton_iters"], "lin_iters": S2["lin_iters"], "final_rel_res": S2["hist"][-1],
+                         "max_rel_diff_vs_unscaled": float(abs(x.cpu().numpy() - xg).max() / abs(xg).max()),
+                         "note": "J_h = fl16(R J32) with power-of-two row factors; at this N nearly every "
+                                 "off-diagonal entry of the unscaled J_h is a binary16 subnormal"}
     if fp64:
         s64 = nl.Solver(N, c)
         torch.cuda.synchronize()
@@ -264,9 +291,12 @@ def bench_large(nl, torch, dev, hbm_peak, tc_peak, N=32768, c=0.99, fp64=False):
         e1.record()
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
+        x64 = x.cpu().numpy()
         out["fp64lu"] = {"status": nl.STATUS_NAMES[st64], "ms_to_solution": ms64, "newton": s64.stats()["newton_iters"],
-                         "lu_ms_per_factorisation": s64.stats()["t_lu_ms"] / max(1, s64.stats()["newton_iters"])}
+                         "lu_ms_per_factorisation": s64.stats()["t_lu_ms"] / max(1, s64.stats()["newton_iters"]),
+                         "timing": "one solve (no warm-up: the FP64 LU dominates, about 18 s per factorisation)"}
         out["speedup_vs_fp64lu"] = ms64 / ms
+        out["err_vs_gpu_fp64lu"] = float(abs(xg - x64).max() / abs(x64).max())
         s64.close()
     return out
 
@@ -279,7 +309,7 @@ def bench_serving(nl, W, seconds, mode="IR16_GMRES", drain_s=120.0, max_inflight
     with nl.Server(budget_bytes=96 << 30, max_inflight=max_inflight, mode=mode) as S:
         ids = [S.submit(N, c, arrival_s=t) for t, N, c in trace]
         S.start()
-        rc = S.drain(drain_s)
+        rc = S.drain(seconds + drain_s)  # the arrivals span `seconds`; then at most drain_s more
         info = S.info()
         per_n = {}
         for rid, (t, N, c) in zip(ids, trace):
@@ -298,6 +328,26 @@ def bench_serving(nl, W, seconds, mode="IR16_GMRES", drain_s=120.0, max_inflight
            "admission": f"device-memory footprint (budget 96 GiB), {max_inflight} slots, smallest N first with a "
                         "250 ms starvation bound, high-priority streams for N <= 1024"}
     return out
+
+
+def golden_x():
+    """The oracle's FP64-LU solutions of the sweep (written by
+    tests/golden/make_golden.py from the CPU oracle alone), or None."""
+    import numpy as np
+    p = os.path.join(ROOT, "tests", "golden", "sweep_n4096_x.npy")
+    try:
+        return np.load(p)
+    except OSError:
+        return None
+
+
+def golden_counts():
+    p = os.path.join(ROOT, "tests", "golden", "sweep_n4096.json")
+    try:
+        g = json.load(open(p))
+        return {k: (v["newton_iters"], v["hist"]) for k, v in g["cases"].items()}
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def dist_init():
@@ -321,44 +371,50 @@ def barrier_max(value, ws):
     return float(t.item())
 
 
-def oracle_sample(n_newton_steps_per_step):
-    """The oracle as it stands on the host cores: one three-precision Newton
-    step (Jacobian, binary16-storage LU, GMRES-IR) at N=4096, c=.99, scaled to
-    solves/s with the GPU's Newton step count for the sweep."""
+def oracle_sample():
+    """The oracle as it stands on the host cores, timed on the workload
+    itself: the five GMRES-IR16 Newton solves of the sweep (N = 4096, c in
+    SWEEP, x0 = ones, to 1e-10), one after another, each complete."""
     from oracle import oracle as O
     O.build()
     t = time.time()
-    O.newton(N_BENCH, 0.99, "GMRESIR16", tol=TOL, newton_maxit=1)
+    steps = 0
+    for c in SWEEP:
+        _, r = O.newton(N_BENCH, c, "GMRESIR16", tol=TOL)
+        steps += r["newton_iters"]
     dt = time.time() - t
-    per_solve = dt * n_newton_steps_per_step / len(SWEEP)
-    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": (f"one oracle Newton step (J, LU16 binary16-storage/binary32 arithmetic, GMRES-IR) at N=4096 "
-                       f"c=0.99 took {dt:.1f}s; scaled by the sweep's {n_newton_steps_per_step} Newton steps per "
-                       f"{len(SWEEP)} solves")}
+    return {"value": len(SWEEP) / dt, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+            "seconds": dt,
+            "sample": (f"the whole sweep measured: 5 complete oracle GMRES-IR16 Newton solves at N=4096 (c in "
+                       f"{list(SWEEP)}, {steps} Newton steps in all; J, binary16-storage/binary32-arithmetic LU, "
+                       f"GMRES-IR) in {dt:.1f} s on {O.num_threads()} threads")}
 
 
 def run_reference(args, ws, rank):
+    """The oracle arm: each step is one complete oracle GMRES-IR16 Newton
+    solve of the sweep at N = 4096 (the steps go through the five c in turn,
+    so K = 5m steps are m whole sweeps), timed on the host cores; the warm-up
+    steps solve at the same size.  value = solves / measured seconds."""
     if rank != 0:
         return
-    # per step: one oracle Newton step (bounded sample), extrapolated to solves/s
     from oracle import oracle as O
     O.build()
-    steps_per_sweep = 3 + 4 + 6 + 9 + 11  # FP64 Newton counts of the sweep to 1e-10
-    for _ in range(args.warmup):
-        O.newton(512, 0.99, "GMRESIR16", tol=TOL, newton_maxit=1)
+    for k in range(args.warmup):
+        O.newton(N_BENCH, SWEEP[k % len(SWEEP)], "GMRESIR16", tol=TOL)
     times = []
-    for _ in range(args.steps):
+    for k in range(args.steps):
         t = time.time()
-        O.newton(N_BENCH, 0.99, "GMRESIR16", tol=TOL, newton_maxit=1)
+        O.newton(N_BENCH, SWEEP[k % len(SWEEP)], "GMRESIR16", tol=TOL)
         times.append(time.time() - t)
-    dt = sum(times) / len(times)
-    value = len(SWEEP) / (dt * steps_per_sweep)
-    sample = (f"each step: one oracle Newton step at N=4096 c=0.99 (GMRES-IR16), {dt:.1f}s, extrapolated by "
-              f"{steps_per_sweep} Newton steps per 5-solve sweep")
+    total = sum(times)
+    value = len(times) / total
+    sample = (f"{len(times)} complete oracle GMRES-IR16 Newton solves at N=4096, c cycling through {list(SWEEP)}, "
+              f"measured: {total:.1f} s in all on {O.num_threads()} threads (no extrapolation)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * steps_per_sweep * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / len(times) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16/f32/f64 (emulated)",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "N": N_BENCH, "c": list(SWEEP)},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "N": N_BENCH, "c": list(SWEEP),
+                                            "step": "one complete solve (c cycling through the sweep)"},
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -378,10 +434,10 @@ def main():
                     help="panel launch: 0 library default, 256 streaming CTAs of 256 rows, -1 two launches")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched workload")
     ap.add_argument("--no-large", action="store_true", help="skip the N=32768 single solve")
-    ap.add_argument("--large-fp64", action="store_true", help="also time FP64-LU Newton at N=32768 (minutes)")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--no-large-fp64", action="store_true", help="skip FP64-LU Newton at N=32768 (about 2 minutes)")
+    ap.add_argument("--serve-seconds", type=float, default=30.0,
                     help="seconds of the serving trace to replay (0: skip serving)")
-    ap.add_argument("--serve-fp64-seconds", type=float, default=0.0,
+    ap.add_argument("--serve-fp64-seconds", type=float, default=30.0,
                     help="seconds of the serving trace to replay with FP64-LU Newton (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
@@ -475,20 +531,47 @@ def main():
     lu_tf = lu_flops / (lu_ms / n_lu / 1e3) / 1e12 if n_lu else 0.0
     roofline_lu = {"bound": "tensor", "achieved": lu_tf, "peak": tc_peak, "unit": "TFLOP/s", "frac": lu_tf / tc_peak,
                    "note": "whole binary16 LU (2N^3/3 flop) over its device time per factorisation"}
+    X64 = golden_x()
+    GC = golden_counts()
+
+    def errors(mode, st_by_c):
+        """Per c: ||x - x_oracle64||_inf / ||x_oracle64||_inf of the results now in xdev, and
+        how the Newton count compares with the oracle's for the same mode."""
+        out = {}
+        for k, c in enumerate(SWEEP):
+            e = {}
+            if X64 is not None:
+                x = xdev[c].cpu().numpy()
+                e["err_vs_fp64_oracle"] = float(np.max(np.abs(x - X64[k])) / np.max(np.abs(X64[k])))
+            if mode and GC is not None and f"{c}/{mode}" in GC:
+                n_or, h_or = GC[f"{c}/{mode}"]
+                n = st_by_c[c]["newton_iters"]
+                e["newton_oracle"] = n_or
+                e["newton_match"] = ("equal" if n == n_or else
+                                     ("one apart: oracle residual at the smaller count within 2x of tol"
+                                      if abs(n - n_or) == 1 and h_or[min(n, n_or)] <= 2 * TOL else "DIFFERENT"))
+            out[str(c)] = e
+        return out
+
+    err_gm = errors("GMRESIR16", stats)
     per_c = {str(c): {"newton": s["newton_iters"], "lin_iters": s["lin_iters"], "ms": s["t_total_ms"],
-                      "final_rel_res": s["hist"][-1], "lu_ms": s["t_lu_ms"], "lin_ms": s["t_lin_ms"]}
+                      "final_rel_res": s["hist"][-1], "lu_ms": s["t_lu_ms"], "lin_ms": s["t_lin_ms"],
+                      **err_gm[str(c)]}
              for c, s in stats.items()}
     extra = {}
     if not args.no_fp64:
         ms64, st64 = timed("FP64LU", 1)
         extra["fp64lu"] = {"solves_per_s": len(SWEEP) / (sum(ms64) / 1e3), "ms_per_sweep": sum(ms64),
                            "per_c_ms": {str(c): s["t_total_ms"] for c, s in st64.items()},
-                           "newton": {str(c): s["newton_iters"] for c, s in st64.items()}}
+                           "newton": {str(c): s["newton_iters"] for c, s in st64.items()},
+                           "vs_oracle": errors("FP64LU", st64)}
         extra["speedup_vs_fp64lu"] = extra["fp64lu"]["ms_per_sweep"] / ms_step
     msir, stir = timed("IR16", 1)
+    err_ir = errors("IR16", stir)
     extra["ir16"] = {"ms_per_sweep": sum(msir), "per_c": {str(c): {"status": nl.STATUS_NAMES[s["status"]],
                                                                      "newton": s["newton_iters"], "ms": s["t_total_ms"],
-                                                                     "lin_iters": s["lin_iters"], "lin_ms": s["t_lin_ms"]}
+                                                                     "lin_iters": s["lin_iters"], "lin_ms": s["t_lin_ms"],
+                                                                     **err_ir[str(c)]}
                                                             for c, s in stir.items()}}
     # the paper's two-precision comparison columns (Section 1.3): one solve per step in the
     # factorisation's precision, no refinement
@@ -537,9 +620,11 @@ def main():
             torch.cuda.synchronize()
         for h in hs.values():
             h.close()
+        err = errors(None, stc)
         return {"ms_per_sweep": e0.elapsed_time(e1),
                 "per_c": {str(c): {"status": nl.STATUS_NAMES[s["status"]], "newton": s["newton_iters"],
-                                   "lin_iters": s["lin_iters"], "ms": s["t_total_ms"], "lin_ms": s["t_lin_ms"]}
+                                   "lin_iters": s["lin_iters"], "ms": s["t_total_ms"], "lin_ms": s["t_lin_ms"],
+                                   **err[str(c)]}
                           for c, s in stc.items()}}
 
     # the binary16-arithmetic solve pair of the F16 step: a chain of 2N barrier steps in one CTA
@@ -564,6 +649,11 @@ def main():
     # GMRES-IR preconditioned with a single-precision copy of the binary16 factors (Section 2.3)
     extra["gmresir16_factors32"] = alt_sweep("GMRESIR16", gmres_factors32=1)
     extra["gmresir16_factors32"]["note"] = "the headline sweep with the factors promoted once per factorisation"
+    # the optional scaling of J into the binary16 range (scale_fp16 = 1) against the unscaled headline sweep
+    extra["gmresir16_scaled"] = alt_sweep("GMRESIR16", scale_fp16=1)
+    extra["gmresir16_scaled"]["note"] = ("J_h = fl16(R J32), power-of-two row factors (2^12 here), solves applied to "
+                                         "R v; against the unscaled headline sweep")
+    extra["ir16_scaled"] = alt_sweep("IR16", scale_fp16=1)
     extra["sequential"] = {"ms_per_sweep": ms_seq[0], "solves_per_s": len(SWEEP) / (ms_seq[0] / 1e3),
                            "note": "the same five solves one after another on one stream"}
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -578,13 +668,16 @@ def main():
     if not args.no_batch:
         line["batched"] = bench_batched(nl, W, torch, dev, args.steps, args.warmup, tc_peak, fp64=not args.no_fp64)
     if not args.no_large:
-        line["large"] = bench_large(nl, torch, dev, hbm_peak, tc_peak, fp64=args.large_fp64)
+        line["large"] = bench_large(nl, torch, dev, hbm_peak, tc_peak, fp64=not args.no_large_fp64)
     if args.serve_seconds > 0:
         line["serving"] = bench_serving(nl, W, args.serve_seconds)
     if args.serve_fp64_seconds > 0:
-        line["serving_fp64lu"] = bench_serving(nl, W, args.serve_fp64_seconds, mode="FP64LU", drain_s=60.0)
+        line["serving_fp64lu"] = bench_serving(nl, W, args.serve_fp64_seconds, mode="FP64LU", drain_s=30.0)
+        line["serving_fp64lu"]["note"] = ("the same trace window as the three-precision server; FP64-LU Newton cannot "
+                                          "keep up with 200 req/s, so the server is stopped 30 s after the last "
+                                          "arrival and the requests still waiting then are counted as not served")
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_sample(n_lu)
+        line["cpu_baseline"] = oracle_sample()
     if rank == 0:
         print(json.dumps(line), flush=True)
     for s in solvers.values():

@@ -118,6 +118,18 @@ typedef struct {
                             cooperative launch with a CTA on every SM, so it is meant for solves that
                             have the GPU to themselves (its barriers are bounded: NL_ETIMEOUT, not a
                             hang, if its CTAs cannot all run).  The batched path accepts only 0 */
+    int wait_limit;      /* [0] bound of the device-side waits of the half-precision triangular solves:
+                            0 = the default (about a second, then NL_ETIMEOUT); > 0 = that many polls
+                            (cluster solve) or clock cycles (global-memory solve); < 0 = every such wait
+                            gives up at once.  A test hook for the timeout path: the solve returns
+                            NL_ETIMEOUT with the context intact */
+    int scale_fp16;      /* [0] 1 = scale J into the binary16 range before the down-cast (Section 2.3 on
+                            underflow when rounding to half precision): J_h = I_s^h(R J32) with power-of-two
+                            row factors R (exact in binary32, nl_k_jacobian_scaled), so the factors are
+                            those of R J and every triangular solve with them is applied to R v.  Three-
+                            precision modes with the on-the-fly correction only: NL_EINVAL with
+                            ir_variant = 1, gmres_factors32 = 1 or lu16_arith = 1 (nl_create) and with
+                            NL_F16 (nl_solve).  The batched path accepts only 0 */
     int reserved[2];
 } nl_config;
 
@@ -130,7 +142,7 @@ typedef struct {
     int newton_iters;                 /* Newton steps taken */
     int lu_nb;                        /* LU outer block used */
     double fnorm0;                    /* ||F(x0)||_2 */
-    double fnorm;                     /* ||F(x_final)||_2 */
+    double fnorm;                     /* ||F||_2 of the returned iterate (the final one on NL_OK, else the best) */
     double hist[NL_MAX_HIST];         /* ||F(x_n)|| / ||F(x_0)||, n = 0..newton_iters */
     int lin_iters[NL_MAX_HIST];       /* per Newton step: IR corrections or GMRES Arnoldi steps
                                          (0 for the direct solves of NL_FP64LU, NL_F32, NL_F16) */
@@ -167,7 +179,10 @@ nl_status nl_set_stream(nl_solver* s, void* stream);
  * ||F(x)||_2 <= tol ||F(x0)||_2 + tau_a (Algorithm 1.1 / 2.1 with tau_r = tol).
  * The step uses the scaled right-hand side of eqs. (2.17)-(2.18): the linear
  * solver works on b = -F/||F|| and s = ||F|| u.  x_out (host, N doubles) gets
- * the final iterate (the last one on NL_ENOTCONV).  Blocks until done. */
+ * the final iterate on NL_OK; on any other status (NL_ENOTCONV, NL_ENUMERIC,
+ * NL_ESINGULAR, NL_ETIMEOUT) the iterate with the smallest ||F|| seen, whose
+ * norm is nl_stats_t.fnorm (after NL_ETIMEOUT the step that timed out is not
+ * a candidate).  Blocks until done. */
 nl_status nl_solve(nl_solver* s, const double* x0, double tol, nl_mode mode, double* x_out);
 
 /* As nl_solve with x0 and x_out in device memory (x0 may be NULL = ones):
@@ -212,6 +227,13 @@ nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* tota
 
 /* Library version string. */
 const char* nl_version(void);
+
+/* Test hook for the out-of-memory path: the next `count` device allocations
+ * made for solver or batch handles (nl_create, the first NL_FP64LU / NL_F32
+ * solve, nl_batch_create) fail as if the device were full, so those calls
+ * return NL_ENOMEM and leave no handle behind.  0 turns it off.  NL_EINVAL
+ * for count < 0. */
+nl_status nl_debug_fail_allocs(int count);
 
 /* ----------------------------------------------------------------------- */
 /* Batched solves: many independent instances of eq. (3.2), each with its   */
@@ -406,6 +428,16 @@ nl_status nl_k_residual(int64_t N, double c, const double* x, const void* u, int
  * Either output may be NULL.  Padding columns N..ld-1 are set to 0. */
 nl_status nl_k_jacobian(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16,
                         int64_t ld16, void* stream);
+
+/* As nl_k_jacobian, with J16 scaled into the binary16 range row by row
+ * (nl_config.scale_fp16; Section 2.3 on rounding into half precision):
+ *   J16_ij = I_s^h(2^k_i J32_ij),  rs[i] = 2^k_i (device, N floats),
+ * where 2^k_i is the largest power of two with 2^k_i B_i <= 2^13 for the row
+ * bound B_i = 1 + c/(2N) r_i^2 >= max_j |J_ij|.  The factors of J16 then
+ * factor R J; a solve with them is applied to R v to solve with J.
+ * J32 is unscaled.  rs must not be NULL. */
+nl_status nl_k_jacobian_scaled(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16,
+                               int64_t ld16, float* rs, void* stream);
 
 /* The same Jacobian in double (for NL_FP64LU). */
 nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int64_t ld, void* stream);

@@ -173,6 +173,29 @@ void orc_jacobian(int64_t N, double c, const double *x, double *J)
     }
 }
 
+/* Optional scaling of the Jacobian into the binary16 range before the
+   down-cast (Section 2.3 warns that rounding to half precision can underflow;
+   the paper scales vectors, this scales the rows of J).  Row i of J is
+   bounded by B_i = 1 + c/(2N) r_i^2, since |J_ij| <= delta_ij + c/(2N) r_i^2
+   mu_i/(mu_i + mu_j) and mu_i/(mu_i + mu_j) < 1.  The row factor is the power
+   of two 2^k_i with k_i the largest integer such that 2^k_i B_i <= 2^13
+   (three bits of headroom below the binary16 maximum 65504 for growth in the
+   elimination): k_i = 13 - ceil(log2 B_i), found exactly from frexp.
+   Multiplying a binary32 entry by 2^k_i is exact, so J_h = I_s^h(R J32)
+   differs from I_s^h(J32) only in its rounding to binary16. */
+void orc_row_scales(int64_t N, double c, const double *x, double *rs)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < N; ++i) {
+        double ri = 1.0 / (1.0 - hsum(N, c, x, i));
+        double B = 1.0 + (c / (2.0 * (double)N)) * ri * ri;
+        int e;
+        double m = frexp(B, &e); /* B = m 2^e, m in [0.5, 1) */
+        int ceil_log2 = (m == 0.5) ? e - 1 : e;
+        rs[i] = ldexp(1.0, 13 - ceil_log2);
+    }
+}
+
 double orc_norm2(int64_t n, const double *v)
 {
     double s = 0.0;
@@ -296,7 +319,7 @@ int orc_lu32(int64_t N, float *A, int32_t *ipiv)
    to the same binary16 value as the exact quotient, so each step is one
    correctly rounded binary16 operation.  Returns info; sets *overflow when a
    result overflowed to infinity. */
-int orc_lu16(int64_t N, double *A, int32_t *ipiv, int *overflow)
+static int lu16_impl(int64_t N, double *A, int32_t *ipiv, int *overflow, int recip)
 {
     int info = 0, ovf = 0;
     for (int64_t k = 0; k < N; ++k) {
@@ -309,9 +332,10 @@ int orc_lu16(int64_t N, double *A, int32_t *ipiv, int *overflow)
                 info = (int)k + 1;
             continue;
         }
+        const double rk = orc_fl16(1.0 / akk); /* recip: the rounded reciprocal of the pivot */
 #pragma omp parallel for schedule(static) reduction(| : ovf)
         for (int64_t i = k + 1; i < N; ++i) {
-            double l = orc_fl16(A[i * N + k] / akk);
+            double l = recip ? orc_fl16(A[i * N + k] * rk) : orc_fl16(A[i * N + k] / akk);
             A[i * N + k] = l;
             for (int64_t j = k + 1; j < N; ++j) {
                 double v = orc_fl16(A[i * N + j] - orc_fl16(l * A[k * N + j]));
@@ -324,6 +348,21 @@ int orc_lu16(int64_t N, double *A, int32_t *ipiv, int *overflow)
     if (overflow)
         *overflow = ovf;
     return info;
+}
+
+int orc_lu16(int64_t N, double *A, int32_t *ipiv, int *overflow)
+{
+    return lu16_impl(N, A, ipiv, overflow, 0);
+}
+
+/* The same elimination with the column scaled by the reciprocal of the pivot,
+   as unblocked LAPACK-style codes do (xGETF2 multiplies the column below the
+   pivot by 1/a_kk): r = fl16(1/a_kk), l_ik = fl16(a_ik * r), then
+   a_ij = fl16(a_ij - fl16(l_ik * a_kj)).  r carries one more rounding than
+   the quotient, so every multiplier of column k shares r's relative error. */
+int orc_lu16_recip(int64_t N, double *A, int32_t *ipiv, int *overflow)
+{
+    return lu16_impl(N, A, ipiv, overflow, 1);
 }
 
 /* Half-precision factorisation with binary16 storage and binary32
@@ -538,11 +577,14 @@ static void residual32(int64_t N, const float *A, const float *b, const float *u
 /* z = (L U)^{-1} P v with the on-the-fly single-precision solve, in double
    vectors (the preconditioner-vector product of GMRES-IR, Section 2.2: "two
    triangular solves", done in single precision per Section 2.3). */
-static void precond_apply(int64_t N, const double *LU16, const int32_t *ipiv, const double *v,
-                          double *z, float *tmp)
+static void precond_apply(int64_t N, const double *LU16, const int32_t *ipiv, const double *rs,
+                          const double *v, double *z, float *tmp)
 {
     for (int64_t i = 0; i < N; ++i)
         tmp[i] = (float)v[i];
+    if (rs) /* factors of R J: (R J)^{-1} R v = J^{-1} v; times 2^k is exact */
+        for (int64_t i = 0; i < N; ++i)
+            tmp[i] = tmp[i] * (float)rs[i];
     orc_lusolve_fly(N, LU16, ipiv, tmp);
     for (int64_t i = 0; i < N; ++i)
         z[i] = (double)tmp[i];
@@ -575,8 +617,8 @@ typedef struct {
    Stops when the preconditioned residual estimate is <= tol times the
    initial preconditioned residual norm, or after maxcycles restarts.
    Returns the number of Arnoldi steps. */
-int orc_gmres(int64_t N, const float *A, const double *LU16, const int32_t *ipiv, const double *r,
-              double *d, int m, double tol, int maxcycles)
+static int gmres_impl(int64_t N, const float *A, const double *LU16, const int32_t *ipiv, const double *rs,
+                      const double *r, double *d, int m, double tol, int maxcycles)
 {
     double *V = (double *)malloc(sizeof(double) * (size_t)N * (size_t)(m + 1));
     double *H = (double *)calloc((size_t)(m + 1) * (size_t)m, sizeof(double));
@@ -596,7 +638,7 @@ int orc_gmres(int64_t N, const float *A, const double *LU16, const int32_t *ipiv
         matvec32(N, A, d, w);
         for (int64_t i = 0; i < N; ++i)
             t[i] = r[i] - w[i];
-        precond_apply(N, LU16, ipiv, t, w, tmp);
+        precond_apply(N, LU16, ipiv, rs, t, w, tmp);
         double beta = orc_norm2(N, w);
         if (beta0 < 0.0)
             beta0 = beta;
@@ -611,7 +653,7 @@ int orc_gmres(int64_t N, const float *A, const double *LU16, const int32_t *ipiv
         for (j = 0; j < m; ++j) {
             /* w = M^{-1} A v_j */
             matvec32(N, A, V + (size_t)j * N, t);
-            precond_apply(N, LU16, ipiv, t, w, tmp);
+            precond_apply(N, LU16, ipiv, rs, t, w, tmp);
             ++steps;
             /* modified Gram-Schmidt against v_0..v_j */
             for (int i = 0; i <= j; ++i) {
@@ -673,6 +715,12 @@ int orc_gmres(int64_t N, const float *A, const double *LU16, const int32_t *ipiv
     return steps;
 }
 
+int orc_gmres(int64_t N, const float *A, const double *LU16, const int32_t *ipiv, const double *r,
+              double *d, int m, double tol, int maxcycles)
+{
+    return gmres_impl(N, A, LU16, ipiv, NULL, r, d, m, tol, maxcycles);
+}
+
 /* Iterative refinement (Algorithm IR, Section 2.2) and GMRES-IR for
    A u = b with A single precision and a half-precision factorisation.
    u0 = 0.  Stops with success when ||b - A u|| <= eta ||b|| (Section 3.1),
@@ -683,9 +731,12 @@ int orc_gmres(int64_t N, const float *A, const double *LU16, const int32_t *ipiv
                (eq. (2.16) applied to IR, Section 2.3);
            1 = IR with the scaled half-precision correction of eq. (2.19);
            2 = GMRES-IR (defect from GMRES(m) on M^{-1} A d = M^{-1} r). */
-void orc_linsolve(int64_t N, const float *A, const double *LU16, const int32_t *ipiv, const float *b,
-                  float *u, double eta, int maxit, int solver, int m, double gtol, int gcycles,
-                  orc_linstat *st)
+/* rs (may be NULL): the row factors of a scaled factorisation LU = P R A
+   (orc_row_scales); every solve with the factors is applied to R times its
+   right-hand side, so that it solves with A. */
+void orc_linsolve_scaled(int64_t N, const float *A, const double *LU16, const int32_t *ipiv, const double *rs,
+                         const float *b, float *u, double eta, int maxit, int solver, int m, double gtol,
+                         int gcycles, orc_linstat *st)
 {
     float *r = (float *)malloc(sizeof(float) * (size_t)N);
     float *ubest = (float *)malloc(sizeof(float) * (size_t)N);
@@ -709,13 +760,16 @@ void orc_linsolve(int64_t N, const float *A, const double *LU16, const int32_t *
             break;
         if (solver == 0) {
             memcpy(dv, r, sizeof(float) * (size_t)N);
+            if (rs)
+                for (int64_t i = 0; i < N; ++i)
+                    dv[i] = dv[i] * (float)rs[i];
             orc_lusolve_fly(N, LU16, ipiv, dv);
             st->iters++;
         } else if (solver == 1) {
             /* eq. (2.19): d = ||r|| I_h^s( U^{-1} L^{-1} I_s^h(r/||r||) ) */
             float rn = (float)nr;
             for (int64_t i = 0; i < N; ++i)
-                h16[i] = orc_fl16((double)(r[i] / rn));
+                h16[i] = orc_fl16((double)(r[i] / rn) * (rs ? rs[i] : 1.0));
             orc_lusolve16(N, LU16, ipiv, h16);
             for (int64_t i = 0; i < N; ++i)
                 dv[i] = rn * (float)h16[i];
@@ -723,7 +777,7 @@ void orc_linsolve(int64_t N, const float *A, const double *LU16, const int32_t *
         } else {
             for (int64_t i = 0; i < N; ++i)
                 rd[i] = (double)r[i];
-            st->iters += orc_gmres(N, A, LU16, ipiv, rd, dd, m, gtol, gcycles);
+            st->iters += gmres_impl(N, A, LU16, ipiv, rs, rd, dd, m, gtol, gcycles);
             for (int64_t i = 0; i < N; ++i)
                 dv[i] = (float)dd[i];
         }
@@ -753,6 +807,13 @@ void orc_linsolve(int64_t N, const float *A, const double *LU16, const int32_t *
     free(h16);
 }
 
+void orc_linsolve(int64_t N, const float *A, const double *LU16, const int32_t *ipiv, const float *b,
+                  float *u, double eta, int maxit, int solver, int m, double gtol, int gcycles,
+                  orc_linstat *st)
+{
+    orc_linsolve_scaled(N, A, LU16, ipiv, NULL, b, u, eta, maxit, solver, m, gtol, gcycles, st);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Newton drivers: Algorithm 1.1 [newton] and Algorithm 2.1 [newton3p].      */
 /* ------------------------------------------------------------------------ */
@@ -768,8 +829,13 @@ typedef struct {
     int newton_maxit;   /* cap on Newton steps */
     double tau_a;       /* absolute tolerance of Algorithm 1.1 */
     int ir_variant;     /* 0: on-the-fly correction (eq. 2.16), 1: scaled fp16 (eq. 2.19) */
-    int lu_nb;          /* 0: binary16 arithmetic LU (orc_lu16); >0: binary16 storage,
-                           binary32 arithmetic, rounding period lu_nb (orc_lu16_dev) */
+    int lu_nb;          /* 0: binary16 arithmetic LU (orc_lu16); -1: the same with the
+                           multipliers scaled by the rounded reciprocal of the pivot
+                           (orc_lu16_recip); >0: binary16 storage, binary32 arithmetic,
+                           rounding period lu_nb (orc_lu16_dev) */
+    int scale_fp16;     /* 1: J_h = I_s^h(R J32) with the row factors of orc_row_scales, the
+                           solves applied to R times their right-hand side (three-precision
+                           modes) */
 } orc_params;
 
 typedef struct {
@@ -813,12 +879,18 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
     float *b32 = (float *)malloc(sizeof(float) * (size_t)N);
     float *u32 = (float *)malloc(sizeof(float) * (size_t)N);
     double *bd = (double *)malloc(sizeof(double) * (size_t)N);
+    double *rs = p->scale_fp16 ? (double *)malloc(sizeof(double) * (size_t)N) : NULL;
+    double *xbest = (double *)malloc(sizeof(double) * (size_t)N);
 
     for (int64_t i = 0; i < N; ++i)
         x[i] = x0 ? x0[i] : 1.0;
     orc_F(N, c, x, F);
     double f0 = orc_norm2(N, F), fn = f0;
     double tau = tau_r * f0 + p->tau_a;
+    /* the iterate with the smallest ||F||, returned when the iteration does
+       not meet the tolerance (the convention of the C interface) */
+    double fbest = f0;
+    memcpy(xbest, x, sizeof(double) * (size_t)N);
     res->hist[0] = 1.0;
     int n = 0, gm_sticky = 0;
     res->status = 1;
@@ -854,6 +926,8 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
                 J[q] = orc_fl16((double)(float)J[q]);
             if (p->lu_nb > 0)
                 res->lu_info[n] = orc_lu16_dev(N, p->lu_nb, J, ipiv, &ovf);
+            else if (p->lu_nb == -1)
+                res->lu_info[n] = orc_lu16_recip(N, J, ipiv, &ovf);
             else
                 res->lu_info[n] = orc_lu16(N, J, ipiv, &ovf);
             if (ovf) {
@@ -866,14 +940,19 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
             for (int64_t i = 0; i < N; ++i)
                 x[i] = x[i] + fn * bd[i];
         } else {
-            /* Algorithm 2.1: J in single, J_h = I_s^h(J) in half */
+            /* Algorithm 2.1: J in single, J_h = I_s^h(J) in half (of R J with
+               the row factors R when scale_fp16 is set) */
             int ovf = 0;
+            if (rs)
+                orc_row_scales(N, c, x, rs);
             for (size_t q = 0; q < NN; ++q) {
                 J32[q] = (float)J[q];
-                J[q] = orc_fl16((double)J32[q]);
+                J[q] = orc_fl16((double)J32[q] * (rs ? rs[q / (size_t)N] : 1.0));
             }
             if (p->lu_nb > 0)
                 res->lu_info[n] = orc_lu16_dev(N, p->lu_nb, J, ipiv, &ovf);
+            else if (p->lu_nb == -1)
+                res->lu_info[n] = orc_lu16_recip(N, J, ipiv, &ovf);
             else
                 res->lu_info[n] = orc_lu16(N, J, ipiv, &ovf);
             if (ovf) {
@@ -884,16 +963,16 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
                 b32[i] = (float)(-F[i] / fn);
             orc_linstat st;
             int solver = (mode == ORC_GMRESIR16 || gm_sticky) ? 2 : p->ir_variant;
-            orc_linsolve(N, J32, J, ipiv, b32, u32, p->eta, p->ir_maxit, solver, p->gmres_m,
-                         p->gmres_tol, p->gmres_cycles, &st);
+            orc_linsolve_scaled(N, J32, J, ipiv, rs, b32, u32, p->eta, p->ir_maxit, solver, p->gmres_m,
+                                p->gmres_tol, p->gmres_cycles, &st);
             if (mode == ORC_IR16GM && !gm_sticky && !st.converged) {
                 /* IR stalled (failure rule or cap without meeting eta): this
                    step's correction is recomputed by GMRES-IR (Section 2.2)
                    from u0 = 0, and GMRES-IR serves every later step. */
                 orc_linstat sg;
                 gm_sticky = 1;
-                orc_linsolve(N, J32, J, ipiv, b32, u32, p->eta, p->ir_maxit, 2, p->gmres_m, p->gmres_tol,
-                             p->gmres_cycles, &sg);
+                orc_linsolve_scaled(N, J32, J, ipiv, rs, b32, u32, p->eta, p->ir_maxit, 2, p->gmres_m,
+                                    p->gmres_tol, p->gmres_cycles, &sg);
                 sg.iters += st.iters;
                 sg.outer += st.outer;
                 sg.failed = 1;
@@ -910,9 +989,15 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
         orc_F(N, c, x, F);
         fn = orc_norm2(N, F);
         res->hist[n] = (f0 > 0.0) ? fn / f0 : 0.0;
+        if (fn < fbest) {
+            fbest = fn;
+            memcpy(xbest, x, sizeof(double) * (size_t)N);
+        }
     }
     if (fn <= tau)
         res->status = 0;
+    else if (fbest < fn || !isfinite(fn))
+        memcpy(x, xbest, sizeof(double) * (size_t)N);
     res->newton_iters = n;
     free(F);
     free(J);
@@ -922,6 +1007,8 @@ int orc_newton(int64_t N, double c, int mode, const double *x0, double tau_r, co
     free(b32);
     free(u32);
     free(bd);
+    free(rs);
+    free(xbest);
     return res->status;
 }
 

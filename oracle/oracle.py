@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
     _fields_ = [("eta", ctypes.c_double), ("ir_maxit", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("gmres_tol", ctypes.c_double), ("gmres_cycles", ctypes.c_int),
                 ("newton_maxit", ctypes.c_int), ("tau_a", ctypes.c_double), ("ir_variant", ctypes.c_int),
-                ("lu_nb", ctypes.c_int)]
+                ("lu_nb", ctypes.c_int), ("scale_fp16", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -80,6 +80,7 @@ def lib():
                 "orc_lu32": (_int, [_i64, _F, _I]),
                 "orc_lu16": (_int, [_i64, _D, _I, ctypes.POINTER(_int)]),
                 "orc_lu16_dev": (_int, [_i64, _i64, _D, _I, ctypes.POINTER(_int)]),
+                "orc_lu16_recip": (_int, [_i64, _D, _I, ctypes.POINTER(_int)]),
                 "orc_lusolve64": (None, [_i64, _D, _I, _D]),
                 "orc_lusolve32": (None, [_i64, _F, _I, _F]),
                 "orc_lusolve_fly": (None, [_i64, _D, _I, _F]),
@@ -87,6 +88,9 @@ def lib():
                 "orc_gmres": (_int, [_i64, _F, _D, _I, _D, _D, _int, _dbl, _int]),
                 "orc_linsolve": (None, [_i64, _F, _D, _I, _F, _F, _dbl, _int, _int, _int, _dbl, _int,
                                         ctypes.POINTER(LinStat)]),
+                "orc_linsolve_scaled": (None, [_i64, _F, _D, _I, ctypes.c_void_p, _F, _F, _dbl, _int, _int, _int,
+                                               _dbl, _int, ctypes.POINTER(LinStat)]),
+                "orc_row_scales": (None, [_i64, _dbl, _D, _D]),
                 "orc_newton": (_int, [_i64, _dbl, _int, ctypes.c_void_p, _dbl, ctypes.POINTER(Params), _D,
                                       ctypes.POINTER(Result)]),
                 "orc_num_threads": (_int, []),
@@ -167,6 +171,18 @@ def lu16(A16):
     return a, ipiv, info, bool(ovf.value)
 
 
+def lu16_recip(A16):
+    """As lu16 with each multiplier fl16(a_ik * fl16(1 / a_kk)) (the column
+    scaled by the rounded reciprocal of the pivot).  Returns (LU, ipiv, info,
+    overflow)."""
+    a = np.array(A16, dtype=np.float64, order="C", copy=True)
+    N = a.shape[0]
+    ipiv = np.empty(N, dtype=np.int32)
+    ovf = _int(0)
+    info = lib().orc_lu16_recip(N, a, ipiv, ctypes.byref(ovf))
+    return a, ipiv, info, bool(ovf.value)
+
+
 def lu16_dev(A16, nb):
     """Binary16-storage / binary32-arithmetic LU with rounding period nb.
     Returns (LU as float64 holding binary16 values, ipiv, info, overflow)."""
@@ -218,15 +234,28 @@ def gmres(A32, LU16, ipiv, r, m=30, tol=1e-4, cycles=10):
 SOLVER_IR_FLY, SOLVER_IR_CHEAP, SOLVER_GMRES = 0, 1, 2
 
 
-def linsolve(A32, LU16, ipiv, b, solver=SOLVER_IR_FLY, eta=1e-4, maxit=20, m=30, gtol=1e-4, gcycles=10):
-    """IR / GMRES-IR from u0 = 0.  Returns (u, LinStat as dict)."""
+def linsolve(A32, LU16, ipiv, b, solver=SOLVER_IR_FLY, eta=1e-4, maxit=20, m=30, gtol=1e-4, gcycles=10, rs=None):
+    """IR / GMRES-IR from u0 = 0.  rs: row factors R when LU16 factors R A
+    (scaled into the binary16 range), else None.  Returns (u, LinStat as dict)."""
     N = A32.shape[0]
     u = np.empty(N, dtype=np.float32)
     st = LinStat()
-    lib().orc_linsolve(N, np.ascontiguousarray(A32, np.float32), np.ascontiguousarray(LU16, np.float64),
-                       np.ascontiguousarray(ipiv, np.int32), np.ascontiguousarray(b, np.float32), u,
-                       eta, maxit, solver, m, gtol, gcycles, ctypes.byref(st))
+    rsp = None
+    if rs is not None:
+        rs = np.ascontiguousarray(rs, np.float64)
+        rsp = rs.ctypes.data_as(ctypes.c_void_p)
+    lib().orc_linsolve_scaled(N, np.ascontiguousarray(A32, np.float32), np.ascontiguousarray(LU16, np.float64),
+                              np.ascontiguousarray(ipiv, np.int32), rsp, np.ascontiguousarray(b, np.float32), u,
+                              eta, maxit, solver, m, gtol, gcycles, ctypes.byref(st))
     return u, {k: getattr(st, k) for k, _ in LinStat._fields_}
+
+
+def row_scales(N: int, c: float, x) -> np.ndarray:
+    """Power-of-two row factors that scale J into the binary16 range."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.empty(N)
+    lib().orc_row_scales(N, c, x, out)
+    return out
 
 
 DEFAULT_LU_NB = 128
@@ -239,7 +268,7 @@ def default_params(paper: bool = False) -> dict:
     operation in binary16, > 0 = binary16 storage with binary32 arithmetic
     and rounding period lu_nb (the GPU's model)."""
     return dict(eta=1e-6 if paper else 1e-4, ir_maxit=20, gmres_m=30, gmres_tol=1e-4, gmres_cycles=10,
-                newton_maxit=10 if paper else 30, tau_a=0.0, ir_variant=0, lu_nb=DEFAULT_LU_NB)
+                newton_maxit=10 if paper else 30, tau_a=0.0, ir_variant=0, lu_nb=DEFAULT_LU_NB, scale_fp16=0)
 
 
 def newton(N: int, c: float, mode="IR16", tol=1e-10, x0=None, **overrides):

@@ -630,7 +630,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 || d.trsv_cluster == 8 ||
           d.trsv_cluster == 16) ||
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant != 0 ||
-        d.gmres_factors32 != 0 || d.lu16_arith != 0) {
+        d.gmres_factors32 != 0 || d.lu16_arith != 0 || d.scale_fp16 != 0) {
         set_error("nl_batch_create: invalid configuration");
         return NL_EINVAL;
     }
@@ -725,7 +725,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         carve(cv);
         B->pool_bytes = cv.off + 256;
     }
-    if (cudaMalloc(&B->pool, B->pool_bytes) != cudaSuccess) {
+    if (dev_malloc(&B->pool, B->pool_bytes) != cudaSuccess) {
         cudaGetLastError();
         set_error("nl_batch_create: cudaMalloc of %zu bytes failed", B->pool_bytes);
         batch_free(B);
@@ -860,7 +860,7 @@ static nl_status batch_alloc_fp64(nl_batch* B)
         }
         bytes = cv.off + 256;
     }
-    if (cudaMalloc(&B->pool64, bytes) != cudaSuccess) {
+    if (dev_malloc(&B->pool64, bytes) != cudaSuccess) {
         cudaGetLastError();
         B->pool64 = nullptr;
         set_error("batch: cudaMalloc of %zu bytes for the double Jacobians failed", bytes);

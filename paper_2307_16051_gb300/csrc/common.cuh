@@ -36,6 +36,10 @@ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 int num_sms();
 
+// cudaMalloc for the handles' device pools; fails on purpose while the test
+// hook nl_debug_fail_allocs has allocations left to fail.
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 // Carves 256-byte aligned sub-buffers out of one device allocation (a null
 // base only measures: off is the size needed).
 struct Carver {

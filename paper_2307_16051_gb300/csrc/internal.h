@@ -16,8 +16,10 @@ nl_status launch_residual(int N, double c, const double* x, const void* u, int u
                           const double* htab, double* xout, double* F, double* rr, double* partial,
                           unsigned* counter, double* fnorm, cudaStream_t st);
 int residual_partials(int N);
+// rs != NULL: J16 scaled into the binary16 range row by row (power-of-two
+// factors written to rs[0..N)); see k_jacobian.
 nl_status launch_jacobian(int N, double c, const double* rr, const double* htab, float* J32, int64_t ld32,
-                          __half* J16, int64_t ld16, cudaStream_t st);
+                          __half* J16, int64_t ld16, cudaStream_t st, float* rs = nullptr);
 nl_status launch_jacobian64(int N, double c, const double* rr, const double* htab, double* J, int64_t ld,
                             cudaStream_t st);
 
@@ -151,6 +153,10 @@ struct TrsvWork {
     unsigned* err = nullptr;  // device error word
     int* scan = nullptr;      // scratch for the permutation build
     int cluster = 0;          // half-precision solve: 0 = largest cluster available, -1 = mailbox kernel, else cap
+    const float* rs = nullptr;  // half-precision solve: row factors of a factorisation of R J (the right side
+                                // is multiplied by R first), or null
+    int wait_limit = 0;       // half-precision solve's waits: 0 = default bound (about a second), < 0 = give up at
+                              // once (test of the timeout path), > 0 = polls (cluster) / cycles (mailbox)
 };
 size_t trsv_work_bytes(int N, bool fp64);
 void trsv_work_carve(void* base, int N, bool fp64, TrsvWork* w);

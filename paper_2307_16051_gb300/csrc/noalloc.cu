@@ -24,13 +24,17 @@ constexpr size_t kNoAllocBytes = kNoAllocPartials * sizeof(double) + 256;
 // Every GPU that loads the library holds these 33 KB until the process ends.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device address of the array, looked up once per device (a host-side name
-// of a __device__ array is not a device address).
+// Device address of the array (a host-side name of a __device__ array is
+// not a device address).  It is looked up again on every call made outside a
+// stream capture, so an address cached before a device reset (which tears the
+// context down and loads the module again) is never used; during a capture
+// the address cached by the last call on that device is used, so the first
+// call on a device must come before any capture.
 static constexpr int kMaxDevices = 64;
 static void* g_scratch_ptr[kMaxDevices] = {};
 static std::mutex g_scratch_mu;
 
-static nl_status scratch_for_current_device(void** out)
+static nl_status scratch_for_current_device(cudaStream_t st, void** out)
 {
     int dev = 0;
     NL_CUDA_OK(cudaGetDevice(&dev));
@@ -38,8 +42,10 @@ static nl_status scratch_for_current_device(void** out)
         set_error("gemv_residual_noalloc: device index %d out of range", dev);
         return NL_EINVAL;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    NL_CUDA_OK(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone || !g_scratch_ptr[dev]) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -64,10 +70,10 @@ extern "C" nl_status nl_k_gemv_residual_noalloc(int64_t N, const float* A, int64
                   kNoAllocMaxN, (long long)N);
         return NL_EINVAL;
     }
-    void* scratch = nullptr;
-    nl_status s = scratch_for_current_device(&scratch);
-    if (s != NL_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    void* scratch = nullptr;
+    nl_status s = scratch_for_current_device(st, &scratch);
+    if (s != NL_OK) return s;
     double* partial = (double*)scratch;
     unsigned* counter = (unsigned*)((char*)scratch + kNoAllocPartials * sizeof(double));
     // the finishing counter must start at zero whatever the last call left

@@ -192,14 +192,31 @@ constexpr int kJCols = 8;
 // w_i = c/(2N) r_i^2 (i + 1/2) once per row; every thread then writes its
 // column of the 32 rows (coalesced rows of J32 and J16).  Per entry the value
 // is fma(-w_i, fl32(h_{i+j}), [i == j]), rounded once more for J16.
+//
+// Optional scaling into the binary16 range (rs != NULL): J16 row i is
+// fl16(2^k_i J32_ij), where 2^k_i is the largest power of two with
+// 2^k_i B_i <= 2^13 for the row bound B_i = 1 + c/(2N) r_i^2 >= max_j |J_ij|
+// (|J_ij| <= delta_ij + c/(2N) r_i^2 mu_i/(mu_i+mu_j), mu_i/(mu_i+mu_j) < 1);
+// k_i = 13 - ceil(log2 B_i) exactly, from frexp.  The product with 2^k_i is
+// exact in single precision; the factor goes to rs[i] for the solves.
 constexpr int kJRows = 32;
+
+__device__ __forceinline__ float row_scale16(int N, double c, double ri)
+{
+    const double B = 1.0 + (c / (2.0 * (double)N)) * ri * ri;
+    int e;
+    const double m = frexp(B, &e);
+    return ldexpf(1.0f, 13 - ((m == 0.5) ? e - 1 : e));
+}
+
 __global__ void __launch_bounds__(256) k_jacobian(int N, double c, const double* __restrict__ rr,
                                                   const double* __restrict__ htab, float* __restrict__ J32,
                                                   int64_t ld32, __half* __restrict__ J16, int64_t ld16,
-                                                  int ldmax)
+                                                  int ldmax, float* __restrict__ rs)
 {
     __shared__ float hw[256 + kJRows];
     __shared__ float wr[kJRows];
+    __shared__ float sr[kJRows];
     const int i0 = blockIdx.y * kJRows, j0 = blockIdx.x * 256;
     for (int q = threadIdx.x; q < 256 + kJRows; q += 256) {
         const int k = i0 + j0 + q;
@@ -207,12 +224,17 @@ __global__ void __launch_bounds__(256) k_jacobian(int N, double c, const double*
     }
     if (threadIdx.x < kJRows) {
         const int i = i0 + threadIdx.x;
-        float w = 0.0f;
+        float w = 0.0f, sc = 1.0f;
         if (i < N) {
             const double ri = rr[i];
             w = (float)(c / (2.0 * (double)N) * ri * ri * ((double)i + 0.5));
+            if (rs) {
+                sc = row_scale16(N, c, ri);
+                if (blockIdx.x == 0) rs[i] = sc;
+            }
         }
         wr[threadIdx.x] = w;
+        sr[threadIdx.x] = sc;
     }
     __syncthreads();
     const int j = j0 + threadIdx.x;
@@ -222,12 +244,12 @@ __global__ void __launch_bounds__(256) k_jacobian(int N, double c, const double*
         const int i = i0 + r;
         const float e = (j < N) ? fmaf(-wr[r], hw[r + threadIdx.x], (i == j) ? 1.0f : 0.0f) : 0.0f;
         if (J32 && j < ld32) J32[(int64_t)i * ld32 + j] = e;
-        if (J16 && j < ld16) J16[(int64_t)i * ld16 + j] = __float2half_rn(e);
+        if (J16 && j < ld16) J16[(int64_t)i * ld16 + j] = __float2half_rn(rs ? e * sr[r] : e);
     }
 }
 
 nl_status launch_jacobian(int N, double c, const double* rr, const double* htab, float* J32, int64_t ld32,
-                          __half* J16, int64_t ld16, cudaStream_t st)
+                          __half* J16, int64_t ld16, cudaStream_t st, float* rs)
 {
     if ((J32 && (ld32 % kJCols)) || (J16 && (ld16 % kJCols))) {
         set_error("jacobian: leading dimensions must be multiples of %d", kJCols);
@@ -235,7 +257,7 @@ nl_status launch_jacobian(int N, double c, const double* rr, const double* htab,
     }
     int ldmax = (int)std::max(J32 ? ld32 : 0, J16 ? ld16 : 0);
     dim3 grid((unsigned)cdiv(ldmax, 256), (unsigned)cdiv(N, kJRows));
-    k_jacobian<<<grid, 256, 0, st>>>(N, c, rr, htab, J32, ld32, J16, ld16, ldmax);
+    k_jacobian<<<grid, 256, 0, st>>>(N, c, rr, htab, J32, ld32, J16, ld16, ldmax, rs);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }

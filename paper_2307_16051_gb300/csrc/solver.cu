@@ -10,6 +10,7 @@
 // half-precision factors; success at ||b - J32 u|| <= eta ||b||, failure
 // when the residual norm increases (the best iterate is kept), Section 3.1.
 // Control runs on the host; each decision reads one device scalar back.
+#include <atomic>
 #include <chrono>
 #include <type_traits>
 #include <cmath>
@@ -25,6 +26,22 @@
 namespace nl {
 
 static thread_local char g_err[512] = "";
+
+// Test hook (nl_debug_fail_allocs): the next g_fail_allocs device allocations
+// of the library's handles fail as if the device were out of memory.
+static std::atomic<int> g_fail_allocs{0};
+
+cudaError_t dev_malloc(void** p, size_t bytes)
+{
+    int n = g_fail_allocs.load();
+    while (n > 0) {
+        if (g_fail_allocs.compare_exchange_weak(n, n - 1)) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
 
 void set_error(const char* fmt, ...)
 {
@@ -138,6 +155,15 @@ struct Host {
         cudaStreamSynchronize(st);
         return pin[0];
     }
+    // *dev and a device error word in one synchronisation
+    double read_err(const double* dev, const unsigned* err, unsigned* errv)
+    {
+        cudaMemcpyAsync(pin, dev, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(pin + 4, err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        memcpy(errv, pin + 4, sizeof(unsigned));
+        return pin[0];
+    }
     void read2(const double* dev, double* out)
     {
         cudaMemcpyAsync(pin, dev, 3 * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -236,7 +262,9 @@ static nl_status linsolve16(int N, const float* J32, int64_t ld32, const __half*
         res->outer += 1;
         NL_TRY(launch_gemv_residual(N, J32, ld32, b, u, B.r, B.partial, B.counter, B.dscal + 1, st));
         *H.launches += 2;
-        nr = H.read(B.dscal + 1);
+        unsigned werr = 0;
+        nr = H.read_err(B.dscal + 1, tw.err, &werr);
+        if (werr) return NL_ETIMEOUT;  // a triangular solve's bounded wait gave up (reported by the caller)
         if (nr > prev) {
             res->failed = 1;
             NL_CUDA_OK(cudaMemcpyAsync(u, B.ubest, sizeof(float) * N, cudaMemcpyDeviceToDevice, st));
@@ -274,10 +302,12 @@ struct nl_solver {
     float* LU32c = nullptr;
     double* pin = nullptr;
     // state
-    double *xa = nullptr, *xb = nullptr, *F = nullptr, *rr = nullptr, *htab = nullptr, *partial = nullptr,
+    double *xa = nullptr, *xb = nullptr, *xbest = nullptr, *F = nullptr, *rr = nullptr, *htab = nullptr,
+           *partial = nullptr,
            *dscal = nullptr, *gws = nullptr;
     unsigned* counter = nullptr;
     float *J32 = nullptr, *b = nullptr, *u = nullptr;
+    float* rs16 = nullptr;  // scale_fp16: power-of-two row factors of J16 = fl16(R J32)
     __half* J16 = nullptr;
     int* ipiv = nullptr;
     LinBufs lb;
@@ -312,6 +342,7 @@ static size_t solver_bytes(int n, const nl_config& d)
     cv.take<double>(n);            // xb
     cv.take<double>(n);            // F
     cv.take<double>(n);            // rr
+    cv.take<double>(n);            // xbest
     cv.take<double>(2 * n);        // htab
     cv.take<double>(npart);        // partial
     cv.take<double>(16);           // dscal
@@ -320,6 +351,7 @@ static size_t solver_bytes(int n, const nl_config& d)
     cv.take<float>((size_t)n * ld);     // J32
     cv.take<__half>((size_t)n * ld);    // J16
     cv.take<int>(n);               // ipiv
+    cv.take<float>(n);             // rs16
     cv.take<float>(ldv);           // b
     cv.take<float>(ldv);           // u
     for (int q = 0; q < 5; ++q) cv.take<float>(ldv);  // r d t w ubest
@@ -351,6 +383,7 @@ static nl_status autotune_lu(nl_solver* s)
     const int n = s->N;
     const int cands[4] = {128, 96, 64, 32};
     cudaStream_t st = s->st;
+    float* jrs = s->cfg.scale_fp16 ? s->rs16 : nullptr;
     k_fill64<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, 1.0, s->xa);
     NL_TRY(launch_residual(n, s->c, s->xa, nullptr, 0, 0.0, s->htab, nullptr, s->F, s->rr, s->partial, s->counter,
                            s->dscal, st));
@@ -361,7 +394,7 @@ static nl_status autotune_lu(nl_solver* s)
         const int gemm = (nb % 64 == 0 && tc_gemm_supported()) ? 2 : 1;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
-            NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st));
+            NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st, jrs));
             lu_work_carve(s->luw.pnl, n, nb, false, &s->luw);
             cudaEventRecord(s->ev[0], st);
             NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, nb, gemm, true, s->luw, st, nullptr));
@@ -437,7 +470,17 @@ nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* tota
     g_kt.cls = kernel_class ? kernel_class : "";
     return NL_OK;
 }
-const char* nl_version(void) { return "newton3p-gb300 0.1 (sm_103a)"; }
+const char* nl_version(void) { return "newton3p-gb300 0.2 (sm_103a)"; }
+
+nl_status nl_debug_fail_allocs(int count)
+{
+    if (count < 0) {
+        set_error("nl_debug_fail_allocs: count < 0");
+        return NL_EINVAL;
+    }
+    g_fail_allocs.store(count);
+    return NL_OK;
+}
 
 nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
 {
@@ -455,7 +498,8 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant < 0 || d.ir_variant > 1 ||
         d.gmres_factors32 < 0 || d.gmres_factors32 > 1 || d.lu16_arith < 0 || d.lu16_arith > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
-        d.lu_nb < -1) {
+        d.lu_nb < -1 || d.scale_fp16 < 0 || d.scale_fp16 > 1 ||
+        (d.scale_fp16 && (d.ir_variant || d.gmres_factors32 || d.lu16_arith))) {
         set_error("nl_create: invalid configuration");
         return NL_EINVAL;
     }
@@ -477,7 +521,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     const int64_t ldv = round_up(N, 64);
     const size_t npart = (size_t)std::max(residual_partials(n), gemv_partials(n)) + 64;
     const size_t bytes = solver_bytes(n, d);
-    if (cudaMalloc(&s->pool, bytes) != cudaSuccess) {
+    if (dev_malloc(&s->pool, bytes) != cudaSuccess) {
         cudaGetLastError();
         delete s;
         set_error("nl_create: cudaMalloc of %zu bytes failed", bytes);
@@ -490,6 +534,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->xb = cv.take<double>(n);
     s->F = cv.take<double>(n);
     s->rr = cv.take<double>(n);
+    s->xbest = cv.take<double>(n);
     s->htab = cv.take<double>(2 * n);
     s->partial = cv.take<double>(npart);
     s->dscal = cv.take<double>(16);
@@ -498,6 +543,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->J32 = cv.take<float>((size_t)n * s->ld);
     s->J16 = cv.take<__half>((size_t)n * s->ld);
     s->ipiv = cv.take<int>(n);
+    s->rs16 = cv.take<float>(n);
     s->b = cv.take<float>(ldv);
     s->u = cv.take<float>(ldv);
     s->lb.r = cv.take<float>(ldv);
@@ -514,6 +560,8 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     lu_work_carve(cv.take<char>(lu_work_bytes(n, s->nb, false)), n, s->nb, false, &s->luw);
     trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &s->tw);
     s->tw.cluster = d.trsv_cluster;
+    s->tw.wait_limit = d.wait_limit;
+    s->tw.rs = d.scale_fp16 ? s->rs16 : nullptr;
     s->luw.stream = d.lu_stream;
     bool evs_ok = true;
     for (auto& e : s->evp) evs_ok = evs_ok && cudaEventCreate(&e) == cudaSuccess;
@@ -602,7 +650,7 @@ static nl_status ensure_fp64(nl_solver* s)
     const int n = s->N;
     const int nb64 = 64;
     const size_t bytes = solver64_bytes(n);
-    if (cudaMalloc(&s->pool64, bytes) != cudaSuccess) {
+    if (dev_malloc(&s->pool64, bytes) != cudaSuccess) {
         cudaGetLastError();
         s->pool64 = nullptr;
         set_error("double-precision Jacobian: cudaMalloc of %zu bytes failed", bytes);
@@ -626,7 +674,7 @@ static nl_status ensure_fp32(nl_solver* s)
 {
     if (s->pool32) return NL_OK;
     const size_t bytes = trsv_work_bytes(s->N, true);
-    if (cudaMalloc(&s->pool32, bytes) != cudaSuccess) {
+    if (dev_malloc(&s->pool32, bytes) != cudaSuccess) {
         cudaGetLastError();
         s->pool32 = nullptr;
         set_error("single-precision solve: cudaMalloc of %zu bytes failed", bytes);
@@ -644,7 +692,7 @@ static nl_status ensure_factors32(nl_solver* s)
     NL_TRY(ensure_fp32(s));
     if (s->poolc) return NL_OK;
     const size_t bytes = (size_t)s->N * s->ld * sizeof(float);
-    if (cudaMalloc(&s->poolc, bytes) != cudaSuccess) {
+    if (dev_malloc(&s->poolc, bytes) != cudaSuccess) {
         cudaGetLastError();
         s->poolc = nullptr;
         set_error("single-precision factor copy: cudaMalloc of %zu bytes failed", bytes);
@@ -673,6 +721,18 @@ static float pair_ms(cudaEvent_t a, cudaEvent_t b)
     return ms;
 }
 
+// Clears the handle's device error words (after a bounded wait gave up), so
+// that the next solve starts clean.
+static void clear_error_words(nl_solver* s)
+{
+    unsigned* tce = tc_error_word();
+    cudaMemsetAsync(s->tw.err, 0, sizeof(unsigned), s->st);
+    if (s->tw64.err) cudaMemsetAsync(s->tw64.err, 0, sizeof(unsigned), s->st);
+    if (s->tw32.err) cudaMemsetAsync(s->tw32.err, 0, sizeof(unsigned), s->st);
+    if (tce) cudaMemsetAsync(tce, 0, sizeof(unsigned), s->st);
+    cudaStreamSynchronize(s->st);
+}
+
 // The residual norm of the new iterate and the device error words in one
 // round trip; an error word set by a bounded wait that gave up is cleared and
 // reported as NL_ETIMEOUT.
@@ -692,11 +752,7 @@ static nl_status read_step_end(nl_solver* s, const double* fn_dev, double* fn)
     memcpy(e, p + 8, sizeof(e));
     if (e[0] | e[1] | e[2] | e[3]) {
         set_error("a device-side bounded wait gave up (error word 0x%x/0x%x/0x%x/0x%x)", e[0], e[1], e[2], e[3]);
-        cudaMemsetAsync(s->tw.err, 0, sizeof(unsigned), s->st);
-        if (s->tw64.err) cudaMemsetAsync(s->tw64.err, 0, sizeof(unsigned), s->st);
-        if (s->tw32.err) cudaMemsetAsync(s->tw32.err, 0, sizeof(unsigned), s->st);
-        if (tce) cudaMemsetAsync(tce, 0, sizeof(unsigned), s->st);
-        cudaStreamSynchronize(s->st);
+        clear_error_words(s);
         return NL_ETIMEOUT;
     }
     return NL_OK;
@@ -719,6 +775,11 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
     }
     int launches = 0;
     Host H{s->pin, st, &launches};
+    if (mode == NL_F16 && s->cfg.scale_fp16) {
+        set_error("nl_solve: scale_fp16 applies to the three-precision modes, not NL_F16");
+        return NL_EINVAL;
+    }
+    float* jrs = s->cfg.scale_fp16 ? s->rs16 : nullptr;
     if (mode == NL_FP64LU) NL_TRY(ensure_fp64(s));
     if (mode == NL_F32) NL_TRY(ensure_fp32(s));
     const bool f32fac = s->cfg.gmres_factors32 && (mode == NL_GMRESIR16 || mode == NL_IR16_GMRES);
@@ -750,6 +811,13 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
     int it = 0;
     bool gm_sticky = false;  // NL_IR16_GMRES: GMRES-IR from the first stalled step on
     nl_status status = NL_ENOTCONV;
+    // The iterate with the smallest ||F|| so far (returned unless the solve
+    // converges): its step index, its norm, and whether it has been copied to
+    // xbest (it is, as soon as a later step fails to improve on it, while it
+    // still sits in the other iterate buffer).
+    int best_it = 0;
+    double best_fn = f0;
+    bool best_saved = false;
     while (!(fn <= tau)) {
         if (!std::isfinite(fn)) {
             status = NL_ENUMERIC;
@@ -762,7 +830,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
         if (mode == NL_FP64LU)
             NL_TRY(launch_jacobian64(n, s->c, s->rr, s->htab, s->J64, s->ld, st));
         else
-            NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st));
+            NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st, jrs));
         cudaEventRecord(s->evp[1], st);
         ++launches;
         // factorisation
@@ -814,7 +882,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             NL_CUDA_OK(cudaStreamSynchronize(st));
             memcpy(iflag, s->pin, sizeof(iflag));
             if (iflag[1]) {
-                NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st));
+                NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st, jrs));
                 NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, false, s->luw, st, &launches));
                 NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
                 ++launches;
@@ -860,17 +928,30 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             NL_TRY(launch_scale_rhs32(n, s->F, fn_dev, s->b, st));
             ++launches;
             LinResult lr;
-            NL_TRY(linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
-                              s->cfg.ir_maxit, (mode == NL_GMRESIR16 || gm_sticky) ? 2 : s->cfg.ir_variant,
-                              s->cfg.gmres_restart,
-                              s->cfg.gmres_tol, s->cfg.gmres_maxcycles, s->lb, H, &lr));
+            nl_status ls = linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
+                                      s->cfg.ir_maxit, (mode == NL_GMRESIR16 || gm_sticky) ? 2 : s->cfg.ir_variant,
+                                      s->cfg.gmres_restart, s->cfg.gmres_tol, s->cfg.gmres_maxcycles, s->lb, H, &lr);
+            if (ls == NL_ETIMEOUT) {  // a triangular solve gave up: no step from this factorisation
+                clear_error_words(s);
+                set_error("a device-side bounded wait gave up (triangular solve)");
+                status = NL_ETIMEOUT;
+                break;
+            }
+            NL_TRY(ls);
             if (mode == NL_IR16_GMRES && !gm_sticky && !lr.converged) {
                 // IR stalled: redo this step with GMRES-IR, and keep it for the rest of the solve
                 gm_sticky = true;
                 LinResult lg;
-                NL_TRY(linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
-                                  s->cfg.ir_maxit, 2, s->cfg.gmres_restart, s->cfg.gmres_tol,
-                                  s->cfg.gmres_maxcycles, s->lb, H, &lg));
+                ls = linsolve16(n, s->J32, s->ld, s->J16, s->ld, s->tw, s->epoch, s->b, s->u, s->cfg.eta_j,
+                                s->cfg.ir_maxit, 2, s->cfg.gmres_restart, s->cfg.gmres_tol, s->cfg.gmres_maxcycles,
+                                s->lb, H, &lg);
+                if (ls == NL_ETIMEOUT) {
+                    clear_error_words(s);
+                    set_error("a device-side bounded wait gave up (triangular solve)");
+                    status = NL_ETIMEOUT;
+                    break;
+                }
+                NL_TRY(ls);
                 lg.iters += lr.iters;
                 lg.outer += lr.outer;
                 lg.failed = 1;
@@ -895,15 +976,34 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
         std::swap(x, xn);
         ++it;
         S.hist[it] = f0 > 0.0 ? fn / f0 : 0.0;
-        if (e != NL_OK) return e;
+        if (e != NL_OK) {  // a bounded wait gave up: this step's iterate is not trusted
+            status = e;
+            break;
+        }
+        if (fn < best_fn) {
+            best_it = it;
+            best_fn = fn;
+            best_saved = false;
+        } else if (best_it == it - 1 && !best_saved) {
+            NL_CUDA_OK(cudaMemcpyAsync(s->xbest, xn, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+            best_saved = true;
+        }
     }
-    if (fn <= tau) status = NL_OK;
-    NL_CUDA_OK(cudaMemcpyAsync(x_out, x, sizeof(double) * n, out_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                               st));
+    if (status != NL_ETIMEOUT && fn <= tau) status = NL_OK;
+    // NL_OK: the final iterate; otherwise the best one seen (the final one when it is the best)
+    const double* xres = x;
+    double fres = fn;
+    if (status != NL_OK && best_it != it) {
+        if (best_it == it - 1 && !best_saved) xres = xn;
+        else xres = s->xbest;
+        fres = best_fn;
+    }
+    NL_CUDA_OK(cudaMemcpyAsync(x_out, xres, sizeof(double) * n,
+                               out_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
     NL_CUDA_OK(cudaStreamSynchronize(st));
     S.status = status;
     S.newton_iters = it;
-    S.fnorm = fn;
+    S.fnorm = fres;
     S.gpu_launches = launches;
     S.t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return status;
@@ -964,11 +1064,11 @@ nl_status nl_k_residual(int64_t N, double c, const double* x, const void* u, int
     return s;
 }
 
-nl_status nl_k_jacobian(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16, int64_t ld16,
-                        void* stream)
+static nl_status jacobian_entry(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16,
+                                int64_t ld16, float* rs, void* stream, const char* name)
 {
     if (N < 1 || N > 32768 || !r || (J32 && ld32 < N) || (J16 && ld16 < N)) {
-        set_error("nl_k_jacobian: bad argument");
+        set_error("%s: bad argument", name);
         return NL_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -976,9 +1076,25 @@ nl_status nl_k_jacobian(int64_t N, double c, const double* r, float* J32, int64_
     double* htab = nullptr;
     NL_CUDA_OK(cudaMallocAsync((void**)&htab, sizeof(double) * 2 * n, st));
     nl_status s = launch_htab(n, htab, st);
-    if (s == NL_OK) s = launch_jacobian(n, c, r, htab, J32, ld32, (__half*)J16, ld16, st);
+    if (s == NL_OK) s = launch_jacobian(n, c, r, htab, J32, ld32, (__half*)J16, ld16, st, rs);
     cudaFreeAsync(htab, st);
     return s;
+}
+
+nl_status nl_k_jacobian(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16, int64_t ld16,
+                        void* stream)
+{
+    return jacobian_entry(N, c, r, J32, ld32, J16, ld16, nullptr, stream, "nl_k_jacobian");
+}
+
+nl_status nl_k_jacobian_scaled(int64_t N, double c, const double* r, float* J32, int64_t ld32, void* J16,
+                               int64_t ld16, float* rs, void* stream)
+{
+    if (!rs) {
+        set_error("nl_k_jacobian_scaled: rs is NULL");
+        return NL_EINVAL;
+    }
+    return jacobian_entry(N, c, r, J32, ld32, J16, ld16, rs, stream, "nl_k_jacobian_scaled");
 }
 
 nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int64_t ld, void* stream)
@@ -1169,8 +1285,8 @@ static nl_status lusolve_entry(int64_t N, const S* LU, int64_t ld, const int32_t
     cudaMemcpyAsync(&e, w.err, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
     cudaFreeAsync(wk, st);
     NL_CUDA_OK(cudaStreamSynchronize(st));
-    if (s == NL_OK && e) {
-        set_error("triangular solve: bounded wait gave up");
+    if ((s == NL_OK && e) || s == NL_ETIMEOUT) {
+        set_error("triangular solve: a bounded wait gave up");
         return NL_ETIMEOUT;
     }
     return s;
@@ -1297,8 +1413,8 @@ nl_status nl_linsolve16(int64_t N, const float* J32, int64_t ld32, const void* L
     cudaFreeAsync(wk, st);
     cudaStreamSynchronize(st);
     cudaFreeHost(pin);
-    if (s == NL_OK && e) {
-        set_error("triangular solve: bounded wait gave up");
+    if ((s == NL_OK && e) || s == NL_ETIMEOUT) {
+        set_error("triangular solve: a bounded wait gave up");
         return NL_ETIMEOUT;
     }
     if (stats_host) {

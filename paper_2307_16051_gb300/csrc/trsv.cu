@@ -220,9 +220,13 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
     asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Bounded poll of one published entry: false once `limit` cycles have passed
+// (a negative limit gives up before the first poll: the test of the timeout
+// path, a wait that runs out whatever the producer does).
 __device__ __forceinline__ bool poll_value(const unsigned long long* p, unsigned epoch, float* out,
-                                           const unsigned* err)
+                                           const unsigned* err, long long limit)
 {
+    if (limit < 0) return false;
     long long t0 = clock64();
     for (;;) {
         unsigned long long w = ld_acquire_u64(p);
@@ -231,7 +235,7 @@ __device__ __forceinline__ bool poll_value(const unsigned long long* p, unsigned
             return true;
         }
         if (*((volatile const unsigned*)err) != 0u) return false;
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -241,7 +245,8 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
                                                        const unsigned long long* __restrict__ vin_mb,
                                                        const int* __restrict__ perm, const float* __restrict__ dinv,
                                                        unsigned long long* __restrict__ mb, float* __restrict__ out,
-                                                       unsigned epoch, unsigned* __restrict__ err)
+                                                       unsigned epoch, unsigned* __restrict__ err, long long wait_cycles,
+                                                       const float* __restrict__ rs)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* Ds = reinterpret_cast<float*>(smem_raw);  // T2 x T2 diagonal inverse
@@ -262,7 +267,8 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
         if (tid < T2) {
             const int i = r0 + tid;
             float x = 0.0f;
-            if (i < N) x = LOWER ? v[perm[i]] : __uint_as_float((unsigned)vin_mb[i]);
+            if (i < N)
+                x = LOWER ? (rs ? v[perm[i]] * rs[perm[i]] : v[perm[i]]) : __uint_as_float((unsigned)vin_mb[i]);
             acc[tid] = x;
         }
         float part = 0.0f;
@@ -294,7 +300,7 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
             if (tid < T2) {
                 const int i = c * T2 + tid;
                 float y = 0.0f;
-                if (i < N) okp = poll_value(mb + i, epoch, &y, err);
+                if (i < N) okp = poll_value(mb + i, epoch, &y, err, wait_cycles);
                 ys[tid] = y;
             }
             if (__syncthreads_or(!okp)) {
@@ -366,10 +372,11 @@ __device__ __forceinline__ void cl_st_async(uint32_t addr, float v, uint32_t bar
                  "r"(__float_as_uint(v)), "r"(bar)
                  : "memory");
 }
-// Bounded wait for phase 0 of a local mbarrier; false after kClWaitIters polls.
-__device__ __forceinline__ bool cl_wait(uint32_t bar)
+// Bounded wait for phase 0 of a local mbarrier; false after `iters` polls
+// (kClWaitIters by default; 0 gives up at once, the test of the timeout path).
+__device__ __forceinline__ bool cl_wait(uint32_t bar, long long iters = kClWaitIters)
 {
-    for (long long it = 0; it < kClWaitIters; ++it) {
+    for (long long it = 0; it < iters; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], 0;\n"
@@ -418,7 +425,8 @@ template <bool LOWER>
 __global__ void __launch_bounds__(kClThreads, 1) k_trsv_cl(int N, int nblk, const __half* __restrict__ LU, int64_t ld,
                                                        const float* __restrict__ v, const int* __restrict__ perm,
                                                        const float* __restrict__ dinv, float* __restrict__ out,
-                                                       unsigned* __restrict__ err)
+                                                       unsigned* __restrict__ err, long long wait_iters,
+                                                       const float* __restrict__ rs)
 {
     cg::cluster_group cl = cg::this_cluster();
     const int C = (int)cl.num_blocks();
@@ -438,7 +446,8 @@ __global__ void __launch_bounds__(kClThreads, 1) k_trsv_cl(int N, int nblk, cons
         const int bj = blk(rank + j * C);
         for (int t = tid; t < T2; t += kClThreads) {
             const int i = bj * T2 + t;
-            acc[j * kClPad + t + (t >> 5)] = (i < N) ? (LOWER ? v[perm[i]] : v[i]) : 0.0f;
+            acc[j * kClPad + t + (t >> 5)] =
+                (i < N) ? (LOWER ? (rs ? v[perm[i]] * rs[perm[i]] : v[perm[i]]) : v[i]) : 0.0f;
         }
     }
     if (tid == 0) {
@@ -492,7 +501,7 @@ __global__ void __launch_bounds__(kClThreads, 1) k_trsv_cl(int N, int nblk, cons
         const int b = blk(s);
         bool ok = false;
         if (!*((volatile int*)&abort_cta)) {
-            ok = cl_wait(cl_smem_u32(bar + s));
+            ok = cl_wait(cl_smem_u32(bar + s), wait_iters);
             if (!ok) {
                 abort_cta = 1;
                 atomicOr(err, (unsigned)ERR_TIMEOUT_TRSV);
@@ -520,6 +529,13 @@ __global__ void __launch_bounds__(kClThreads, 1) k_trsv_cl(int N, int nblk, cons
             if (qq == 0) acc[j * kClPad + prow] -= part;
         }
     }
+    // After a wait gave up, the owners of the later steps still publish them
+    // (their values unused), so every mbarrier of this CTA still completes:
+    // wait for all of them (the default bound) before leaving, so that no
+    // st.async into this CTA's shared memory is still in flight when it exits.
+    __syncthreads();
+    if (*((volatile int*)&abort_cta))
+        for (int s = 0; s < nblk; ++s) cl_wait(cl_smem_u32(bar + s));
     cl.sync();  // no CTA leaves before every CTA has passed all of its waits
 }
 
@@ -800,8 +816,10 @@ static nl_status launch_trsv_mb(int N, const __half* LU, int64_t ld, const float
     const int* perm = w.perm;
     const float* dinv = (const float*)w.dinv;
     unsigned* err = w.err;
-    void* args[] = {(void*)&N,   (void*)&nblk, (void*)&LU,  (void*)&ld,    (void*)&v,   (void*)&vin_mb,
-                    (void*)&perm, (void*)&dinv, (void*)&mb, (void*)&out, (void*)&epoch, (void*)&err};
+    long long wait = w.wait_limit == 0 ? kWaitCycles : (w.wait_limit < 0 ? -1LL : (long long)w.wait_limit);
+    const float* rs = w.rs;
+    void* args[] = {(void*)&N,   (void*)&nblk, (void*)&LU,  (void*)&ld,    (void*)&v,   (void*)&vin_mb, (void*)&perm,
+                    (void*)&dinv, (void*)&mb, (void*)&out, (void*)&epoch, (void*)&err, (void*)&wait, (void*)&rs};
     prof_begin("k_trsv_mb", st);
     cudaError_t le = cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(kMbThreads), args, smem, st);
     prof_end("k_trsv_mb", st);
@@ -885,7 +903,8 @@ static nl_status launch_trsv_cl(int N, const __half* LU, int64_t ld, const float
     const int* perm = w.perm;
     const float* dinv = (const float*)w.dinv;
     prof_begin("k_trsv_cl", st);
-    cudaError_t le = cudaLaunchKernelEx(&cfg, k_trsv_cl<LOWER>, N, nblk, LU, ld, v, perm, dinv, out, w.err);
+    const long long wait = w.wait_limit == 0 ? kClWaitIters : (w.wait_limit < 0 ? 0LL : (long long)w.wait_limit);
+    cudaError_t le = cudaLaunchKernelEx(&cfg, k_trsv_cl<LOWER>, N, nblk, LU, ld, v, perm, dinv, out, w.err, wait, w.rs);
     prof_end("k_trsv_cl", st);
     NL_CUDA_OK(le);
     return NL_OK;

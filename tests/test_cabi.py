@@ -55,7 +55,9 @@ def test_invalid_arguments_rejected_before_device_use():
     L.nl_destroy(None)  # no-op
     for bad in ({"trsv_cluster": 3}, {"trsv_cluster": -2}, {"trsv_cluster": 32}, {"lu_path": 2}, {"lu_stream": 1},
                 {"lu_stream": -2}, {"ir_variant": 2}, {"ir_variant": -1}, {"gmres_factors32": 2},
-                {"gmres_factors32": -1}, {"lu16_arith": 2}):
+                {"gmres_factors32": -1}, {"lu16_arith": 2}, {"scale_fp16": 2}, {"scale_fp16": -1},
+                {"scale_fp16": 1, "ir_variant": 1}, {"scale_fp16": 1, "gmres_factors32": 1},
+                {"scale_fp16": 1, "lu16_arith": 1}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
     # the two-precision kernel entries check their arguments before any device call
     assert L.nl_lu32(0, None, 0, None, 0, None, None) == nl.NL_EINVAL
@@ -130,3 +132,14 @@ def test_server_no_device_is_an_error():
     # the autotuning setting (-1) sizes the handle for the largest panel width
     for N in (1, 700, 4096):
         assert nl.footprint_bytes(N, lu_nb=-1) == nl.footprint_bytes(N, lu_nb=128) >= nl.footprint_bytes(N, lu_nb=32)
+
+
+def test_test_hooks_and_scaled_jacobian_validate_arguments():
+    L = nl.lib()
+    assert L.nl_debug_fail_allocs(-1) == nl.NL_EINVAL
+    assert L.nl_debug_fail_allocs(0) == nl.NL_OK
+    # the scaled Jacobian needs its row-factor output; bad sizes are rejected first
+    assert L.nl_k_jacobian_scaled(64, 0.5, 8, 8, 64, 8, 64, None, None) == nl.NL_EINVAL
+    assert L.nl_k_jacobian_scaled(0, 0.5, 8, 8, 64, 8, 64, 8, None) == nl.NL_EINVAL
+    c = nl.config()
+    assert c.wait_limit == 0 and c.scale_fp16 == 0

@@ -16,6 +16,8 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sweep_n4096.json")
+GOLDEN_X = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sweep_n4096_x.npy")
+SWEEP = (0.5, 0.9, 0.99, 0.9999, 0.999999)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -311,31 +313,33 @@ def test_f16_two_precision_newton(N, c):
         assert len(h) - 1 > r64["newton_iters"], (h, r64["hist"])
 
 
-@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="golden sweep file not generated")
-@pytest.mark.parametrize("c", [0.5, 0.9, 0.99, 0.9999, 0.999999])
+@pytest.mark.skipif(not (os.path.exists(GOLDEN) and os.path.exists(GOLDEN_X)), reason="golden sweep files missing")
+@pytest.mark.parametrize("c", list(SWEEP))
 @pytest.mark.parametrize("mode", ["FP64LU", "IR16", "GMRESIR16"])
 def test_sweep_n4096_vs_golden(c, mode):
-    """Conditioning sweep at N = 4096 against stored oracle results."""
+    """Conditioning sweep at N = 4096 against stored oracle results: the
+    counts, and the GPU solution element by element against the oracle's
+    whole FP64-LU solution."""
     gold = json.load(open(GOLDEN))
     N = gold["N"]
     ro = gold["cases"][f"{c}/{mode}"]
-    ref = gold["cases"][f"{c}/FP64LU"]
+    x64 = np.load(GOLDEN_X)[SWEEP.index(c)]
     with nl.Solver(N, c) as s:
         x, status = s.solve(tol=1e-10, mode=mode)
         st = s.stats()
-    if ro["status"] == 0:
-        assert status == nl.NL_OK
-        check_counts(st, ro, mode, ill=c >= 0.9999)
-        idx = gold["sample_idx"]
-        xs = np.array(ref["x_sample"])
-        # 1e-10 (the Newton tolerance); for the very ill-conditioned c the
-        # last iterate's residual ||F||/||F0|| (at most 1e-10, and the linear
-        # steps only match to single-precision rounding) is amplified into x by
-        # up to the condition number, which grows like (1 - c)^(-1/2)
-        kappa = 1.0 / math.sqrt(1.0 - c)
-        tol = 1e-10 if c <= 0.99 else 1e-10 + 10.0 * kappa * max(st["hist"][-1], ro["hist"][-1])
-        assert np.max(np.abs(x[idx] - xs)) / np.max(np.abs(xs)) <= tol
-        assert abs(x.sum() - ref["x_sum"]) <= tol * abs(ref["x_sum"])
+    assert ro["status"] == 0 and status == nl.NL_OK
+    check_counts(st, ro, mode, ill=c >= 0.9999)
+    err = rel_inf(x, x64)
+    branch = "equal" if st["newton_iters"] == ro["newton_iters"] else "one apart (oracle at the tolerance)"
+    print(f"N=4096 c={c} {mode}: newton {st['newton_iters']} (oracle {ro['newton_iters']}, {branch}), "
+          f"||x - x_oracle64||_inf/||x_oracle64||_inf = {err:.2e}")
+    # 1e-10 (the Newton tolerance) for every c <= .99.  For c >= .9999 the
+    # last iterate's residual ||F||/||F0|| (at most 1e-10) is amplified into x
+    # by up to the condition number, which grows like (1 - c)^(-1/2): there the
+    # bound is 10 kappa times the larger final residual.
+    kappa = 1.0 / math.sqrt(1.0 - c)
+    tol = 1e-10 if c <= 0.99 else 1e-10 + 10.0 * kappa * max(st["hist"][-1], ro["hist"][-1])
+    assert err <= tol
     # properties that hold at any size: residual and the moment identity
     F = O.F(N, c, x)
     if status == nl.NL_OK:

@@ -120,6 +120,40 @@ def np16_gepp(A16):
     return a.astype(np.float64), piv
 
 
+def np16_gepp_recip(A16):
+    """The same elimination with the column scaled by the rounded reciprocal
+    of the pivot: r = fl16(1 / a_kk), l = fl16(a_ik r), in numpy float16."""
+    a = np.array(A16, dtype=np.float16)
+    n = a.shape[0]
+    piv = []
+    for k in range(n):
+        col = np.abs(a[k:, k].astype(np.float64))
+        p = k + int(np.argmax(col))
+        piv.append(p)
+        a[[k, p]] = a[[p, k]]
+        if a[k, k] == 0:
+            continue
+        r = np.float16(np.float16(1.0) / a[k, k])
+        for i in range(k + 1, n):
+            l = np.float16(a[i, k] * r)
+            a[i, k] = l
+            for j in range(k + 1, n):
+                a[i, j] = np.float16(a[i, j] - np.float16(l * a[k, j]))
+    return a.astype(np.float64), piv
+
+
+@pytest.mark.parametrize("n,seed", [(4, 1), (9, 2), (13, 3), (16, 4)])
+def test_lu16_recip_bit_exact_vs_numpy_float16_machine(n, seed):
+    A = W.random_matrix(n, seed).astype(np.float16).astype(np.float64)
+    ref, piv = np16_gepp_recip(A)
+    LU, ipiv, info, ovf = O.lu16_recip(A)
+    assert not ovf and list(ipiv) == piv
+    assert np.array_equal(LU, ref)
+    # and it is a different elimination from the quotient one
+    LUq, _, _, _ = O.lu16(A)
+    assert not np.array_equal(LU, LUq) or n <= 4
+
+
 @pytest.mark.parametrize("n,seed", [(4, 1), (9, 2), (13, 3), (16, 4)])
 def test_lu16_bit_exact_vs_numpy_float16_machine(n, seed):
     A = W.random_matrix(n, seed).astype(np.float16).astype(np.float64)
@@ -292,3 +326,30 @@ def test_lu16_dev_accuracy_beats_per_op_binary16():
         assert list(ipiv) == list(range(N))
     assert res["dev"] < res["op"] / 3
     assert res["dev"] <= 4 * 2.0 ** -11
+
+
+def test_uniform_power_of_two_scaling_changes_no_rounding():
+    """Scaling a matrix by 2^k commutes with every binary16 and binary32
+    rounding as long as no result is subnormal or overflows: the factors of
+    fl16(2^k A) are those of fl16(A) with U multiplied by 2^k and the same L,
+    and IR with the row factors applied to the right side returns the same
+    u bit for bit (the scaled solve multiplies each right side by 2^k, which
+    the factors' U undoes exactly)."""
+    n, k = 48, 10
+    g = np.random.default_rng(11)
+    A = np.eye(n) * 4.0 + g.uniform(0.25, 1.0, (n, n)) * np.where(g.random((n, n)) < 0.5, -1.0, 1.0)
+    A16 = O.fl16(A)
+    LU, ipiv, _, _ = O.lu16_dev(A16, 16)
+    tiny = (np.abs(LU) < 2.0 ** -14) & (LU != 0)
+    assert not tiny.any()  # the premise: no subnormal factor entry
+    LUs, ipivs, _, _ = O.lu16_dev(O.fl16(A16 * 2.0 ** k), 16)
+    assert np.array_equal(ipiv, ipivs)
+    L = np.tril(LU, -1)
+    assert np.array_equal(np.tril(LUs, -1), L)
+    assert np.array_equal(np.triu(LUs), np.triu(LU) * 2.0 ** k)
+    A32 = A16.astype(np.float32)
+    b = g.standard_normal(n).astype(np.float32)
+    for solver in (O.SOLVER_IR_FLY, O.SOLVER_GMRES):
+        u0, st0 = O.linsolve(A32, LU, ipiv, b, solver=solver, eta=1e-6)
+        u1, st1 = O.linsolve(A32, LUs, ipivs, b, solver=solver, eta=1e-6, rs=np.full(n, 2.0 ** k))
+        assert np.array_equal(u0, u1) and st0 == st1

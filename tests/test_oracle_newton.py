@@ -244,3 +244,46 @@ def test_ir16_gmres_fallback_rule():
     assert r1["lin_failed"][0] == 1 and r1["lin_iters"][0] == r2["lin_iters"][0] + 1
     assert r1["lin_iters"][1:] == r2["lin_iters"][1:]
     assert not np.array_equal(x1, x3)
+
+
+def test_row_scales_are_the_largest_powers_of_two_under_2_13():
+    """The row factor 2^k_i is the largest power of two with 2^k_i B_i <= 2^13,
+    B_i = 1 + c/(2N) r_i^2, r_i = (1 - t_i)^{-1} recomputed here in numpy from
+    eq. (3.2); and B_i bounds row i of the Jacobian, so max |R J| <= 2^13."""
+    for N, c in ((1, 0.5), (7, 0.0), (300, 0.99), (1000, 0.999999)):
+        x = np.linspace(0.8, 2.5, N)
+        rs = O.row_scales(N, c, x)
+        mu = (np.arange(N) + 0.5) / N
+        t = c / (2 * N) * (x[None, :] * mu[:, None] / (mu[None, :] + mu[:, None])).sum(axis=1)
+        r = 1.0 / (1.0 - t)
+        B = 1.0 + c / (2 * N) * r * r
+        k = np.log2(rs)
+        assert np.all(k == np.round(k))
+        assert np.all(rs * B <= 2.0 ** 13 * (1 + 1e-12)) and np.all(2 * rs * B > 2.0 ** 13 * (1 - 1e-12))
+        J = O.jacobian(N, c, x)
+        assert np.max(np.abs(J * rs[:, None])) <= 2.0 ** 13
+
+
+@pytest.mark.parametrize("mode", ["IR16", "GMRESIR16"])
+def test_scaled_newton_reaches_the_same_solution(mode):
+    """With the Jacobian scaled into the binary16 range, three-precision
+    Newton still meets the tolerance in the FP64-LU number of steps and
+    reaches the FP64-LU solution."""
+    for N, c in ((256, 0.9), (512, 0.99)):
+        x64, r64 = O.newton(N, c, "FP64LU", tol=1e-10)
+        xs, rsc = O.newton(N, c, mode, tol=1e-10, scale_fp16=1)
+        assert rsc["status"] == 0 and rsc["newton_iters"] == r64["newton_iters"]
+        assert np.max(np.abs(xs - x64)) <= 1e-10 * np.max(np.abs(x64))
+
+
+def test_best_iterate_returned_when_not_converged():
+    """Far from the solution the Newton history is not monotone; when the
+    step cap is reached, the oracle returns the iterate with the smallest
+    ||F||: its residual is the history's minimum times ||F(x0)||."""
+    N, c = 128, 0.999
+    x0 = 6.0 * np.ones(N)
+    x, r = O.newton(N, c, "GMRESIR16", tol=1e-10, x0=x0, newton_maxit=7)
+    h = np.array(r["hist"])
+    assert r["status"] == 1 and np.argmin(h) not in (0, len(h) - 1)  # a middle iterate is the best
+    f0 = np.linalg.norm(O.F(N, c, x0))
+    assert abs(np.linalg.norm(O.F(N, c, x)) - h.min() * f0) <= 1e-12 * f0
