@@ -170,6 +170,34 @@ def test_paper_mode_table2_columns_n1024(table2):
             assert agrees_4digits(h[n], p[n]), (mode, n, h[n], p[n])
 
 
+def test_paper_mode_table3_ir3216_stall_n4096(table3):
+    """Table 3's IR 32-16 column on the GPU (N = 4096, c = .9999, eta_J =
+    1e-6), in the reading that reproduces it: IR with the scaled binary16
+    correction of eq. (2.19) on the binary16-storage / binary32-arithmetic
+    factorisation.  IR follows the F64 history for five steps (1-3 within
+    one printed unit, 4-5 within 0.1%), then its failure rule fires at every
+    step and Newton stalls near 5e-4 (steps 6-8 within a factor 1.5 of the
+    printed values); GMRES-IR on the same factorisation converges."""
+    p = table3["IR32-16"]
+    with nl.Solver(4096, 0.9999, eta_j=1e-6, newton_maxit=8, ir_variant=1) as s:
+        _, status = s.solve(tol=1e-9, mode="IR16")
+        st = s.stats()
+    h = st["hist"]
+    assert status == nl.NL_ENOTCONV and len(h) == 9, h
+    for n in (1, 2, 3):
+        unit = 1e-3 * 10 ** np.floor(np.log10(p[n]))
+        assert abs(h[n] - p[n]) <= unit, (n, h[n], p[n])
+    for n in (4, 5):
+        assert abs(h[n] - p[n]) <= 1e-3 * p[n], (n, h[n], p[n])
+    assert not any(st["lin_failed"][:5]) and all(st["lin_failed"][5:8]), st["lin_failed"]
+    for n in (6, 7, 8):
+        assert p[n] / 1.5 <= h[n] <= 1.5 * p[n], (n, h[n], p[n])
+    print("GPU IR 32-16 history (eq. (2.19)):", ["%.3e" % v for v in h], "failed:", st["lin_failed"])
+    with nl.Solver(4096, 0.9999, eta_j=1e-6, newton_maxit=10) as s:
+        _, status = s.solve(tol=1e-9, mode="GMRESIR16")
+        assert status == nl.NL_OK and s.stats()["newton_iters"] == len(table3["IR-GM"]) - 1
+
+
 @pytest.mark.parametrize("N,c", [(1, 0.9), (100, 0.5), (517, 0.99), (1024, 0.9999)])
 def test_f32_two_precision_newton(N, c):
     """F32 column (Section 1.3): J stored and factored in single precision,
