@@ -130,7 +130,13 @@ typedef struct {
                             precision modes with the on-the-fly correction only: NL_EINVAL with
                             ir_variant = 1, gmres_factors32 = 1 or lu16_arith = 1 (nl_create) and with
                             NL_F16 (nl_solve).  The batched path accepts only 0 */
-    int reserved[2];
+    int fft_f;           /* [0 = auto] evaluation of F (Section 3: O(N log N) with an FFT): 1 = FFT
+                            convolution in double (nl_k_residual_fft: four launches, rounding-level
+                            differences from the direct sum); -1 = the direct double sum over the Hankel
+                            table (N^2 products); 0 = the FFT for N >= 4096, where it is the faster one
+                            (45 against 61 us at N = 4096, 70 us against 2.1 ms at N = 32768), the direct
+                            sum below */
+    int reserved[1];
 } nl_config;
 
 #define NL_MAX_HIST 128
@@ -220,7 +226,9 @@ const char* nl_last_error(void);
  * "k_diag_lu", "k_offdiag" (double LU), "k_tc_gemm" (tensor-core trailing
  * update), "k_invdiag" (diagonal-block inverses), "k_trsv_cl" (cluster
  * triangular solve), "k_trsv_mb" (mailbox triangular solve),
- * "k_lusolve16h" (binary16-arithmetic solve), "k_gemv_residual".  Not
+ * "k_lusolve16h" (binary16-arithmetic solve), "k_gemv_residual",
+ * "k_residual" (F by the direct sum), "k_fft" (F by the FFT: its four
+ * launches together).  Not
  * thread-safe against
  * concurrent solves on other threads.  Synchronises the recorded events. */
 nl_status nl_kernel_timing(const char* kernel_class, int* launches, double* total_ms);
@@ -420,6 +428,20 @@ nl_status nl_lusolve_grouped(int count, const int64_t* N, const void* const* LU,
 nl_status nl_k_residual(int64_t N, double c, const double* x, const void* u, int u_is_double,
                         double fnorm_scale, double* x_out, double* F, double* r, double* fnorm_dev,
                         void* stream);
+
+/* The same residual, fused update and norm as nl_k_residual, with the sum of
+ * eq. (3.2) evaluated in O(N log N) (Section 3): with z_m = x_(N-1-m) the sum
+ * y_i = sum_j x_j h[i+j], h[k] = 1/(k+1), is the convolution (h * z)[i+N-1],
+ * computed as a circular convolution of length L (the power of two >=
+ * max(4, 2N)) by hand-written double-precision FFTs (four-step split into two
+ * passes of radix-2 Stockham transforms in shared memory, twiddles from
+ * sincospi).  Results differ from nl_k_residual by rounding only (about
+ * 1e-14 relative to max|x| at N = 4096).  Allocates its workspace (16 L
+ * doubles) with cudaMallocAsync; the transform of h is recomputed per call
+ * (a solver handle keeps it). */
+nl_status nl_k_residual_fft(int64_t N, double c, const double* x, const void* u, int u_is_double,
+                            double fnorm_scale, double* x_out, double* F, double* r, double* fnorm_dev,
+                            void* stream);
 
 /* Analytic Jacobian of eq. (3.2) at x, given r from nl_k_residual:
  *   J_ij = delta_ij - (c/(2N)) r_i^2 mu_i/(mu_i+mu_j)   (Sections 1.1, 3),

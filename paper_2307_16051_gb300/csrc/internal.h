@@ -16,6 +16,24 @@ nl_status launch_residual(int N, double c, const double* x, const void* u, int u
                           const double* htab, double* xout, double* F, double* rr, double* partial,
                           unsigned* counter, double* fnorm, cudaStream_t st);
 int residual_partials(int N);
+
+// fft.cu: the residual of eq. (3.2) through a length-L FFT convolution (L the
+// power of two >= max(4, 2N), split L = L1 L2 for the two passes).
+struct FftPlan {
+    int N = 0, L = 0, L1 = 0, L2 = 0;
+    double2* tw = nullptr;   // L twiddles exp(-2 pi i k / L)
+    double2* Hh = nullptr;   // transform of h[k] = 1/(k+1), k < 2N-1, zero-padded
+    double2* Y = nullptr;    // work: L
+    double2* V = nullptr;    // work: L
+    double* part = nullptr;  // L1 per-block partial sums of F_i^2
+    unsigned* cnt = nullptr; // finishing counter (zero between calls)
+};
+size_t fft_work_bytes(int N);
+void fft_work_carve(void* base, int N, FftPlan* p);
+nl_status fft_prepare(const FftPlan& p, cudaStream_t st);  // twiddles and Hh (once per plan)
+// As launch_residual (same outputs, norm deterministic), O(N log N).
+nl_status launch_residual_fft(const FftPlan& p, double c, const double* x, const void* u, int u_is_double,
+                              double scale, double* xout, double* F, double* rr, double* fnorm, cudaStream_t st);
 // rs != NULL: J16 scaled into the binary16 range row by row (power-of-two
 // factors written to rs[0..N)); see k_jacobian.
 nl_status launch_jacobian(int N, double c, const double* rr, const double* htab, float* J32, int64_t ld32,

@@ -120,12 +120,14 @@ nl_status launch_residual(int N, double c, const double* x, const void* u, int u
                           unsigned* counter, double* fnorm, cudaStream_t st)
 {
     unsigned grid = (unsigned)cdiv(N, kFRows);
+    prof_begin("k_residual", st);
     if (u_is_double)
         k_residual<double><<<grid, kFRows * kFSlices, 0, st>>>(N, c, x, (const double*)u, scale, htab, xout, F,
                                                                rr, partial, counter, fnorm);
     else
         k_residual<float><<<grid, kFRows * kFSlices, 0, st>>>(N, c, x, (const float*)u, scale, htab, xout, F,
                                                               rr, partial, counter, fnorm);
+    prof_end("k_residual", st);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }

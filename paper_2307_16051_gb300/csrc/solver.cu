@@ -308,6 +308,8 @@ struct nl_solver {
     unsigned* counter = nullptr;
     float *J32 = nullptr, *b = nullptr, *u = nullptr;
     float* rs16 = nullptr;  // scale_fp16: power-of-two row factors of J16 = fl16(R J32)
+    bool use_fft = false;   // F through the FFT convolution (fft_f)
+    FftPlan fft;
     __half* J16 = nullptr;
     int* ipiv = nullptr;
     LinBufs lb;
@@ -329,6 +331,12 @@ struct nl_solver {
     int tune_nb[4] = {0, 0, 0, 0};
     float tune_ms[4] = {0, 0, 0, 0};
 };
+
+// Whether F is evaluated through the FFT convolution (nl_config.fft_f).  The
+// automatic choice takes it from N = 4096, where its four launches (about
+// 45 us) beat the direct sum (61 us at N = 4096, 2.1 ms at N = 32768, GB300).
+constexpr int kFftAutoMinN = 4096;
+static bool uses_fft(int n, const nl_config& d) { return d.fft_f == 1 || (d.fft_f == 0 && n >= kFftAutoMinN); }
 
 // Device bytes of one handle's main allocation (layout of nl_create).
 static size_t solver_bytes(int n, const nl_config& d)
@@ -358,6 +366,7 @@ static size_t solver_bytes(int n, const nl_config& d)
     cv.take<float>((size_t)(m + 1) * ldv);            // V
     cv.take<char>(lu_work_bytes(n, nb, false));
     cv.take<char>(trsv_work_bytes(n, false));
+    if (uses_fft(n, d)) cv.take<char>(fft_work_bytes(n));
     return cv.off + 256;
 }
 
@@ -375,6 +384,15 @@ static size_t solver64_bytes(int n)
     return cv.off + 256;
 }
 
+// F(x + scale u) (u may be NULL), r and ||F||: direct sum or FFT convolution.
+static nl_status eval_F(nl_solver* s, const double* x, const void* u, int u_is_double, double scale, double* xout,
+                        double* fnorm_dev, cudaStream_t st)
+{
+    if (s->use_fft) return launch_residual_fft(s->fft, s->c, x, u, u_is_double, scale, xout, s->F, s->rr, fnorm_dev, st);
+    return launch_residual(s->N, s->c, x, u, u_is_double, scale, s->htab, xout, s->F, s->rr, s->partial, s->counter,
+                           fnorm_dev, st);
+}
+
 // lu_nb = -1: time the factorisation of the Jacobian at x0 = ones for each
 // candidate outer block (tcgen05 update where nb is a multiple of 64, SIMT
 // otherwise) and keep the fastest.  nb is also the binary16 rounding period.
@@ -385,8 +403,7 @@ static nl_status autotune_lu(nl_solver* s)
     cudaStream_t st = s->st;
     float* jrs = s->cfg.scale_fp16 ? s->rs16 : nullptr;
     k_fill64<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, 1.0, s->xa);
-    NL_TRY(launch_residual(n, s->c, s->xa, nullptr, 0, 0.0, s->htab, nullptr, s->F, s->rr, s->partial, s->counter,
-                           s->dscal, st));
+    NL_TRY(eval_F(s, s->xa, nullptr, 0, 0.0, nullptr, s->dscal, st));
     float best = 1e30f;
     int bnb = 128, k = 0;
     for (int nb : cands) {
@@ -498,7 +515,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant < 0 || d.ir_variant > 1 ||
         d.gmres_factors32 < 0 || d.gmres_factors32 > 1 || d.lu16_arith < 0 || d.lu16_arith > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
-        d.lu_nb < -1 || d.scale_fp16 < 0 || d.scale_fp16 > 1 ||
+        d.lu_nb < -1 || d.scale_fp16 < 0 || d.scale_fp16 > 1 || d.fft_f < -1 || d.fft_f > 1 ||
         (d.scale_fp16 && (d.ir_variant || d.gmres_factors32 || d.lu16_arith))) {
         set_error("nl_create: invalid configuration");
         return NL_EINVAL;
@@ -559,6 +576,8 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->lb.dscal = s->dscal + 4;
     lu_work_carve(cv.take<char>(lu_work_bytes(n, s->nb, false)), n, s->nb, false, &s->luw);
     trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &s->tw);
+    s->use_fft = uses_fft(n, d);
+    if (s->use_fft) fft_work_carve(cv.take<char>(fft_work_bytes(n)), n, &s->fft);
     s->tw.cluster = d.trsv_cluster;
     s->tw.wait_limit = d.wait_limit;
     s->tw.rs = d.scale_fp16 ? s->rs16 : nullptr;
@@ -572,7 +591,8 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         set_error("nl_create: host/event allocation failed");
         return NL_ENOMEM;
     }
-    if (launch_htab(n, s->htab, s->st) != NL_OK || cudaStreamSynchronize(s->st) != cudaSuccess) {
+    if (launch_htab(n, s->htab, s->st) != NL_OK || (s->use_fft && fft_prepare(s->fft, s->st) != NL_OK) ||
+        cudaStreamSynchronize(s->st) != cudaSuccess) {
         nl_destroy(s);
         return NL_ECUDA;
     }
@@ -798,8 +818,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
     }
     double* fn_dev = s->dscal;
     cudaEventRecord(s->ev[0], st);
-    NL_TRY(launch_residual(n, s->c, x, nullptr, 0, 0.0, s->htab, nullptr, s->F, s->rr, s->partial, s->counter, fn_dev,
-                           st));
+    NL_TRY(eval_F(s, x, nullptr, 0, 0.0, nullptr, fn_dev, st));
     cudaEventRecord(s->ev[1], st);
     ++launches;
     const double f0 = H.read(fn_dev);
@@ -966,8 +985,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
         cudaEventRecord(s->evp[5], st);
         // x_{n+1} = x_n + ||F|| u, fused with F(x_{n+1}); its norm and the device error
         // words come back with the step's one synchronisation
-        NL_TRY(launch_residual(n, s->c, x, ustep, u_is_double, fn, s->htab, xn, s->F, s->rr, s->partial, s->counter,
-                               fn_dev, st));
+        NL_TRY(eval_F(s, x, ustep, u_is_double, fn, xn, fn_dev, st));
         ++launches;
         nl_status e = read_step_end(s, fn_dev, &fn);
         S.t_jac_ms += pair_ms(s->evp[0], s->evp[1]);
@@ -1061,6 +1079,25 @@ nl_status nl_k_residual(int64_t N, double c, const double* x, const void* u, int
     if (s == NL_OK)
         s = launch_residual(n, c, x, u, u_is_double, fnorm_scale, htab, x_out, F, r, partial, counter, fnorm_dev, st);
     cudaFreeAsync(htab, st);
+    return s;
+}
+
+nl_status nl_k_residual_fft(int64_t N, double c, const double* x, const void* u, int u_is_double,
+                            double fnorm_scale, double* x_out, double* F, double* r, double* fnorm_dev, void* stream)
+{
+    if (N < 1 || N > 32768 || !x || !F || !r || !fnorm_dev || (u && !x_out) || (x_out && x_out == x)) {
+        set_error("nl_k_residual_fft: bad argument");
+        return NL_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = (int)N;
+    void* wk = nullptr;
+    NL_CUDA_OK(cudaMallocAsync(&wk, fft_work_bytes(n), st));
+    FftPlan p;
+    fft_work_carve(wk, n, &p);
+    nl_status s = fft_prepare(p, st);
+    if (s == NL_OK) s = launch_residual_fft(p, c, x, u, u_is_double, fnorm_scale, x_out, F, r, fnorm_dev, st);
+    cudaFreeAsync(wk, st);
     return s;
 }
 

@@ -36,7 +36,8 @@ class Config(ctypes.Structure):
                 ("tau_a", ctypes.c_double), ("lu_nb", ctypes.c_int), ("trailing_gemm", ctypes.c_int),
                 ("lu_path", ctypes.c_int), ("trsv_cluster", ctypes.c_int), ("lu_stream", ctypes.c_int),
                 ("ir_variant", ctypes.c_int), ("gmres_factors32", ctypes.c_int), ("lu16_arith", ctypes.c_int),
-                ("wait_limit", ctypes.c_int), ("scale_fp16", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("wait_limit", ctypes.c_int), ("scale_fp16", ctypes.c_int), ("fft_f", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class Stats(ctypes.Structure):
@@ -103,6 +104,7 @@ SIGNATURES = {
     "nl_debug_fail_allocs": (_int, [_int]),
     "nl_k_residual": (_int, [_i64, _dbl, _P, _P, _int, _dbl, _P, _P, _P, _P, _P]),
     "nl_k_jacobian": (_int, [_i64, _dbl, _P, _P, _i64, _P, _i64, _P]),
+    "nl_k_residual_fft": (_int, [_i64, _dbl, _P, _P, _int, _dbl, _P, _P, _P, _P, _P]),
     "nl_k_jacobian_scaled": (_int, [_i64, _dbl, _P, _P, _i64, _P, _i64, _P, _P]),
     "nl_k_jacobian64": (_int, [_i64, _dbl, _P, _P, _i64, _P]),
     "nl_lu16": (_int, [_i64, _P, _i64, _P, _int, _int, _int, ctypes.POINTER(ctypes.c_int32), _P]),
@@ -353,6 +355,11 @@ def k_residual(N, c, x, F, r, fnorm, u=None, u_is_double=False, scale=0.0, x_out
 
 def k_jacobian(N, c, r, J32, ld32, J16, ld16, stream=None):
     return check(lib().nl_k_jacobian(N, c, _ptr(r), _ptr(J32), ld32, _ptr(J16), ld16, _stream(stream)))
+
+
+def k_residual_fft(N, c, x, F, r, fnorm, u=None, u_is_double=False, scale=0.0, x_out=None, stream=None):
+    return check(lib().nl_k_residual_fft(N, c, _ptr(x), _ptr(u), int(u_is_double), float(scale), _ptr(x_out),
+                                         _ptr(F), _ptr(r), _ptr(fnorm), _stream(stream)))
 
 
 def k_jacobian_scaled(N, c, r, J32, ld32, J16, ld16, rs, stream=None):

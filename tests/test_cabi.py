@@ -57,7 +57,7 @@ def test_invalid_arguments_rejected_before_device_use():
                 {"lu_stream": -2}, {"ir_variant": 2}, {"ir_variant": -1}, {"gmres_factors32": 2},
                 {"gmres_factors32": -1}, {"lu16_arith": 2}, {"scale_fp16": 2}, {"scale_fp16": -1},
                 {"scale_fp16": 1, "ir_variant": 1}, {"scale_fp16": 1, "gmres_factors32": 1},
-                {"scale_fp16": 1, "lu16_arith": 1}):
+                {"scale_fp16": 1, "lu16_arith": 1}, {"fft_f": 2}, {"fft_f": -2}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
     # the two-precision kernel entries check their arguments before any device call
     assert L.nl_lu32(0, None, 0, None, 0, None, None) == nl.NL_EINVAL
@@ -142,4 +142,4 @@ def test_test_hooks_and_scaled_jacobian_validate_arguments():
     assert L.nl_k_jacobian_scaled(64, 0.5, 8, 8, 64, 8, 64, None, None) == nl.NL_EINVAL
     assert L.nl_k_jacobian_scaled(0, 0.5, 8, 8, 64, 8, 64, 8, None) == nl.NL_EINVAL
     c = nl.config()
-    assert c.wait_limit == 0 and c.scale_fp16 == 0
+    assert c.wait_limit == 0 and c.scale_fp16 == 0 and c.fft_f == 0
