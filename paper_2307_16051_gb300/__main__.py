@@ -28,6 +28,10 @@ def main():
                     help="1: GMRES-IR preconditioned with a single-precision copy of the factors")
     ap.add_argument("--lu16-arith", type=int, default=0, choices=[0, 1],
                     help="1: the half-precision factorisation with every operation in binary16")
+    ap.add_argument("--scale-fp16", type=int, default=0, choices=[0, 1],
+                    help="1: J scaled into the binary16 range (power-of-two row factors) before the down-cast")
+    ap.add_argument("--fft-f", type=int, default=0, choices=[-1, 0, 1],
+                    help="F by the FFT convolution (1), the direct sum (-1), or the automatic choice (0)")
     ap.add_argument("--batch", type=int, default=0,
                     help="solve the first BATCH instances of the batched workload (N log-uniform in [64, 2048], "
                          "c uniform in [0.1, 0.999], seed 230716051) together")
@@ -55,7 +59,8 @@ def main():
             print(json.dumps(S.info()))
         return
     with nl.Solver(args.N, args.c, eta_j=args.eta, lu_nb=args.lu_nb, newton_maxit=args.newton_maxit,
-                   ir_variant=args.ir_variant, gmres_factors32=args.gmres_factors32, lu16_arith=args.lu16_arith) as s:
+                   ir_variant=args.ir_variant, gmres_factors32=args.gmres_factors32, lu16_arith=args.lu16_arith,
+                   scale_fp16=args.scale_fp16, fft_f=args.fft_f) as s:
         for _ in range(max(1, args.repeat)):
             x, status = s.solve(tol=args.tol, mode=args.mode or "GMRESIR16")
         st = s.stats()
