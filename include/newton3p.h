@@ -82,10 +82,15 @@ typedef struct {
     int gmres_maxcycles; /* [10]  GMRES restart cycles per outer correction */
     int newton_maxit;    /* [30]  cap on Newton steps */
     double tau_a;        /* [0]   absolute tolerance tau_a of Algorithm 1.1 */
-    int lu_nb;           /* [0 = 128] outer block of the LU (multiple of 16, <= 128); also its binary16
-                            rounding period.  -1 = autotune at nl_create: the factorisation of the
-                            Jacobian at x0 = ones is timed for nb in {128, 96, 64, 32} (tcgen05 update
-                            for multiples of 64, SIMT otherwise) and the fastest is kept */
+    int lu_nb;           /* [0 = 128] outer block of the LU, also its binary16 rounding period: a multiple
+                            of 16 up to 128 (one level of blocking), or 256, 384 or 512 (two levels: inner
+                            panels of 128 carried in single precision, and one tensor-core update of
+                            depth lu_nb of the rest of the matrix per outer block, so the trailing matrix
+                            is read and written once per lu_nb columns; when partial pivoting needs
+                            interchanges the factorisation is redone with 128).  -1 = autotune at
+                            nl_create: the factorisation of the Jacobian at x0 = ones is timed for nb in
+                            {512, 256, 128, 64} (the two-level ones when N >= 2 nb) and the fastest is
+                            kept */
     int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update */
     int lu_path;         /* [0 = auto] no-interchange fast path with exact fallback; 1 = interchanging path only */
     int trsv_cluster;    /* [0 = auto] half-precision triangular solves: one thread-block cluster per
@@ -472,7 +477,9 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
  * Section 2 says only that J_h is factored in half precision).
  * ipiv (device, N int32): LAPACK-style 0-based interchanges.  *info_host: 0,
  * or k+1 for the first exactly-zero pivot k (then NL_ESINGULAR).  nb: 0 = 128,
- * else a multiple of 16 in [16, 128].  gemm: 0 auto, 1 SIMT, 2 tcgen05.
+ * else a multiple of 16 in [16, 128], or 256, 384, 512 for the two-level
+ * factorisation (nl_config.lu_nb; its workspace includes a single-precision
+ * copy of the matrix).  gemm: 0 auto, 1 SIMT, 2 tcgen05.
  * path: 0 = factor first without interchanges, checking exactly that partial
  * pivoting keeps every diagonal pivot, and refactor with interchanges from a
  * saved copy of A if not (same result either way); 1 = interchanging path
@@ -540,11 +547,13 @@ nl_status nl_k_div_round16(int64_t n, const float* a, const float* b, float* out
 /* Trailing update of the half-precision LU:  C <- fl16(C - A B) with A M x K,
  * B K x Nc, C M x Nc binary16 row-major (lda, ldb, ldc), products accumulated
  * in single.  gemm: 1 SIMT (sequential fused multiply-adds over k),
- * 2 tcgen05 tensor cores (K a multiple of 64, lda/ldb/ldc multiples of 8,
- * pointers 16-byte aligned; for K <= 128 the persistent kernel: one CTA per
- * SM, TMA loads of A, B and C and TMA stores of C, loads and MMAs of one tile
- * overlapping the epilogue of the previous one), 3 the same tensor-core
- * arithmetic with one CTA per 128 x 128 tile (bitwise the same results as 2). */
+ * 2 tcgen05 tensor cores (K a multiple of 64 up to 1024, lda/ldb/ldc multiples
+ * of 8, pointers 16-byte aligned; the persistent kernel: one CTA per SM, TMA
+ * loads of A, B and C and TMA stores of C, the K extent streamed through a
+ * four-slot ring of 64-wide operand slabs while C stays in tensor memory, so
+ * C is read and written once whatever K; loads and MMAs of one tile overlap
+ * the epilogue of the previous one), 3 the same tensor-core arithmetic with
+ * one CTA per 128 x 128 tile and K <= 256 (bitwise the same results as 2). */
 nl_status nl_k_gemm16_update(int64_t M, int64_t Nc, int64_t K, const void* A, int64_t lda, const void* B,
                              int64_t ldb, void* C, int64_t ldc, int gemm, void* stream);
 

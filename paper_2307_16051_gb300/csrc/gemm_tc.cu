@@ -10,7 +10,8 @@
 //     accumulator and commits them to a second mbarrier;
 //   * all four warps read their 32 TMEM lanes (tcgen05.ld 32x32b) and apply
 //     C = fl16(C - acc) in the epilogue.
-// K <= 256 (the LU's outer block), so the whole K extent is staged at once.
+// K <= 256, so the whole K extent is staged at once (the persistent kernel
+// below streams any K).
 // Each wait is bounded; on timeout the CTA records the error, waits (again
 // bounded) for its own copies, releases its tensor memory and returns.
 // No cluster multicast: every CTA loads its own tiles.
@@ -246,17 +247,22 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
 // Loads, MMAs, epilogue and stores of consecutive tiles overlap, and all
 // global traffic is TMA (coalesced, asynchronous).  Per element the
 // arithmetic is the per-tile kernel's: the same K/16 MMAs in the same order,
-// then one subtraction and one rounding.  K <= 128 (two operand stages of
-// 64 KB and three C buffers of 32 KB, so two C tiles are in flight to and
-// from memory while the epilogue works on the third).  Every wait is bounded; a timeout marks
+// then one subtraction and one rounding.  The operands stream through a ring
+// of four slots of one 64-wide K slab of A and of B each (32 KB), so K is any
+// multiple of 64 up to kPMaxK: C stays in the tensor-memory accumulator for
+// the whole K extent and is read and written once per update, whatever K
+// (the LU's outer block).  Three C buffers of 32 KB keep two C tiles in flight
+// to and from memory while the epilogue works on the third.  Every wait is bounded; a timeout marks
 // the CTA aborted, every role leaves its loop, in-flight copies and MMAs are
 // waited for (bounded), and tensor memory is released.
 constexpr int kPThreads = 224;
 constexpr uint32_t kPSlab = 128 * 128;  // bytes of one 128-row x 64-column binary16 slab
 constexpr uint32_t kPCBytes = 2 * kPSlab;  // one C tile: two 64-column boxes
 constexpr int kPCBuf = 3;
+constexpr int kPRing = 4;                  // operand slots, each an A slab and a B slab (K = 64)
+constexpr int kPMaxK = 1024;               // largest K of one update
 
-static size_t p_smem_bytes(int KT) { return 1024 + 2 * (size_t)KT * 2 * kPSlab + kPCBuf * (size_t)kPCBytes + 128; }
+static size_t p_smem_bytes() { return 1024 + (size_t)kPRing * 2 * kPSlab + kPCBuf * (size_t)kPCBytes + 256; }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 {
@@ -299,12 +305,14 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* basep = smem_raw + (base - raw);
     const int KT = K / kTcBK;
-    const uint32_t ab_bytes = (uint32_t)KT * 2 * kPSlab;
-    const uint32_t sAB = base, sCb = base + 2 * ab_bytes;  // operand stages, then C buffers
-    uint64_t* bars = reinterpret_cast<uint64_t*>(basep + 2 * ab_bytes + kPCBuf * kPCBytes);
-    // bars: ab_full[2], ab_empty[2], tfull[2], tempty[2], c_full[3] (8..10), c_done[3] (11..13);
-    // then the TMEM address
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 14);
+    const uint32_t ring_bytes = (uint32_t)kPRing * 2 * kPSlab;
+    const uint32_t sAB = base, sCb = base + ring_bytes;  // operand slots, then C buffers
+    uint64_t* bars = reinterpret_cast<uint64_t*>(basep + ring_bytes + kPCBuf * kPCBytes);
+    // bars: slot_full[4] (0..3), slot_empty[4] (4..7), tfull[2] (8, 9), tempty[2] (10, 11),
+    // c_full[3] (12..14), c_done[3] (15..17); then the TMEM address
+    constexpr int bFULL = 0, bEMPTY = kPRing, bTFULL = 2 * kPRing, bTEMPTY = 2 * kPRing + 2,
+                  bCFULL = 2 * kPRing + 4, bCDONE = 2 * kPRing + 4 + kPCBuf;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + bCDONE + kPCBuf);
     __shared__ int aborted;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = (Nc + kTcBN - 1) / kTcBN;
@@ -348,15 +356,17 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     }
     if (threadIdx.x == 32) {
         aborted = 0;
+        for (int k = 0; k < kPRing; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(bFULL + k)));     // slot full (TMA)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(bEMPTY + k)));    // slot free (MMA commit)
+        }
         for (int k = 0; k < 2; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(0 + k)));     // ab_full
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(2 + k)));     // ab_empty (MMA commit)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(4 + k)));     // tfull (MMA commit)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bar(6 + k)));   // tempty (epilogue)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(bTFULL + k)));    // tfull (MMA commit)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bar(bTEMPTY + k))); // tempty (epilogue)
         }
         for (int k = 0; k < kPCBuf; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(8 + k)));     // c_full (TMA)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bar(11 + k)));  // c_done (epilogue)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar(bCFULL + k)));    // c_full (TMA)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(bar(bCDONE + k)));  // c_done (epilogue)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -367,68 +377,80 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
-                const int s = it & 1;
-                const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-                if (it >= 2 && !mbar_wait(bar(2 + s), ph ^ 1u, kTcWaitCycles)) {
-                    fail();
-                    break;
-                }
+            // producer: slab g (tile it, K slab kt; g = it KT + kt) into slot g % kPRing once the
+            // MMAs of slab g - kPRing are done with it
+            long long g = 0;
+            bool ok = true;
+            for (int it = 0; it < nmine && ok && !*(volatile int*)&aborted; ++it) {
                 const TileRef r = ref(it);
-                const uint32_t sA = sAB + s * ab_bytes, sB = sA + KT * kPSlab;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(s)), "r"(ab_bytes)
-                             : "memory");
-                for (int kt = 0; kt < KT; ++kt) {
-                    tma_load_2d(sA + kt * kPSlab, r.a, r.ax + kt * kTcBK, r.ay, bar(s));
-                    tma_load_2d(sB + kt * kPSlab, r.b, kt * kTcBK, r.by, bar(s));
+                for (int kt = 0; kt < KT; ++kt, ++g) {
+                    const int s = (int)(g % kPRing);
+                    const uint32_t ph = (uint32_t)(g / kPRing) & 1u;
+                    if (g >= kPRing && !mbar_wait(bar(bEMPTY + s), ph ^ 1u, kTcWaitCycles)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t sA = sAB + (uint32_t)s * 2 * kPSlab, sB = sA + kPSlab;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(bFULL + s)),
+                                 "r"(2 * kPSlab)
+                                 : "memory");
+                    tma_load_2d(sA, r.a, r.ax + kt * kTcBK, r.ay, bar(bFULL + s));
+                    tma_load_2d(sB, r.b, kt * kTcBK, r.by, bar(bFULL + s));
                 }
-                issued = it + 1;
             }
             // copies in flight land before the CTA's shared memory goes away
-            for (int it = (issued >= 2 ? issued - 2 : 0); it < issued; ++it)
-                mbar_wait(bar(it & 1), (uint32_t)(it >> 1) & 1u, kTcWaitCycles);
+            for (long long j = (g >= kPRing ? g - kPRing : 0); j < g; ++j)
+                mbar_wait(bar(bFULL + (int)(j % kPRing)), (uint32_t)(j / kPRing) & 1u, kTcWaitCycles);
         }
     } else if (warp == 1) {
         if (lane == 0) {
+            // MMA issuer: tile it accumulates its KT slabs into accumulator it % 2, each slab's
+            // MMAs committed to its slot's "free" barrier, the tile's to "accumulator full"
             const uint32_t idesc = tc_idesc();
-            int committed = 0;
-            for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
-                const int s = it & 1, b = it & 1;
-                const uint32_t ph = (uint32_t)(it >> 1) & 1u;
-                if (!mbar_wait(bar(s), ph, kTcWaitCycles) ||
-                    (it >= 2 && !mbar_wait(bar(6 + b), ph ^ 1u, kTcWaitCycles))) {
+            long long g = 0;
+            bool ok = true;
+            for (int it = 0; it < nmine && ok && !*(volatile int*)&aborted; ++it) {
+                const int b = it & 1;
+                const uint32_t pht = (uint32_t)(it >> 1) & 1u;
+                if (it >= 2 && !mbar_wait(bar(bTEMPTY + b), pht ^ 1u, kTcWaitCycles)) {
                     fail();
                     break;
                 }
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sA = sAB + s * ab_bytes, sB = sA + KT * kPSlab;
                 const uint32_t d = tmem + (uint32_t)(b * kTcBN);
-                for (int kt = 0; kt < KT; ++kt) {
+                for (int kt = 0; kt < KT; ++kt, ++g) {
+                    const int s = (int)(g % kPRing);
+                    const uint32_t ph = (uint32_t)(g / kPRing) & 1u;
+                    if (!mbar_wait(bar(bFULL + s), ph, kTcWaitCycles)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sA = sAB + (uint32_t)s * 2 * kPSlab, sB = sA + kPSlab;
 #pragma unroll
                     for (int kk = 0; kk < kTcBK / 16; ++kk) {
-                        const uint64_t ad = sw128_desc(sA + kt * kPSlab + kk * 32);
-                        const uint64_t bd = sw128_desc(sB + kt * kPSlab + kk * 32);
+                        const uint64_t ad = sw128_desc(sA + kk * 32);
+                        const uint64_t bd = sw128_desc(sB + kk * 32);
                         const uint32_t acc = (kt | kk) ? 1u : 0u;
                         asm volatile(
                             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
                             "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
                     }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     bar(bEMPTY + s))
+                                 : "memory");
                 }
+                if (!ok) break;
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 bar(4 + b))
+                                 bar(bTFULL + b))
                              : "memory");
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                                 bar(2 + s))
-                             : "memory");
-                committed = it + 1;
             }
-            if (committed > 0) {
-                // the last MMAs are complete before tensor memory is released
-                const int it = committed - 1;
-                mbar_wait(bar(4 + (it & 1)), (uint32_t)(it >> 1) & 1u, kTcWaitCycles);
-            }
+            // every issued MMA is complete (the last commit covers all earlier ones) before
+            // tensor memory is released
+            if (g > 0)
+                mbar_wait(bar(bEMPTY + (int)((g - 1) % kPRing)), (uint32_t)((g - 1) / kPRing) & 1u, kTcWaitCycles);
         }
     } else if (warp == 6) {
         if (lane == 0) {
@@ -437,17 +459,17 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
             int loaded = 0;
             for (int it = 0; it < kPCBuf && it < nmine; ++it) {
                 const TileRef r = ref(it);
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(8 + it)),
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(bCFULL + it)),
                              "r"(kPCBytes)
                              : "memory");
                 for (int j = 0; j < 2; ++j)
-                    tma_load_2d(sCb + it * kPCBytes + j * kPSlab, r.c, r.cx + j * kTcBK, r.cy, bar(8 + it));
+                    tma_load_2d(sCb + it * kPCBytes + j * kPSlab, r.c, r.cx + j * kTcBK, r.cy, bar(bCFULL + it));
                 loaded = it + 1;
             }
             for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
                 const int s = it % kPCBuf;
                 const uint32_t ph = (uint32_t)(it / kPCBuf) & 1u;
-                if (!mbar_wait(bar(11 + s), ph, kTcWaitCycles)) {
+                if (!mbar_wait(bar(bCDONE + s), ph, kTcWaitCycles)) {
                     fail();
                     break;
                 }
@@ -462,18 +484,18 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                 if (it + kPCBuf < nmine) {
                     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                     const TileRef rn = ref(it + kPCBuf);
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(8 + s)),
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(bCFULL + s)),
                                  "r"(kPCBytes)
                                  : "memory");
                     for (int j = 0; j < 2; ++j)
-                        tma_load_2d(sCb + s * kPCBytes + j * kPSlab, rn.c, rn.cx + j * kTcBK, rn.cy, bar(8 + s));
+                        tma_load_2d(sCb + s * kPCBytes + j * kPSlab, rn.c, rn.cx + j * kTcBK, rn.cy, bar(bCFULL + s));
                     loaded = it + kPCBuf + 1;
                 }
             }
             asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
             if (*(volatile int*)&aborted)
                 for (int it = (loaded >= kPCBuf ? loaded - kPCBuf : 0); it < loaded; ++it)
-                    mbar_wait(bar(8 + it % kPCBuf), (uint32_t)(it / kPCBuf) & 1u, kTcWaitCycles);
+                    mbar_wait(bar(bCFULL + it % kPCBuf), (uint32_t)(it / kPCBuf) & 1u, kTcWaitCycles);
         }
     } else {
         const int q = warp & 3;       // TMEM lane quarter of this warp (warps 2..5 -> 2, 3, 0, 1)
@@ -482,14 +504,14 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
         for (int it = 0; it < nmine; ++it) {
             const int s = it % kPCBuf, b = it & 1;
             const uint32_t ph = (uint32_t)(it >> 1) & 1u, phc = (uint32_t)(it / kPCBuf) & 1u;
-            const bool ok = !*(volatile int*)&aborted && mbar_wait(bar(4 + b), ph, kTcWaitCycles) &&
-                            mbar_wait(bar(8 + s), phc, kTcWaitCycles);
+            const bool ok = !*(volatile int*)&aborted && mbar_wait(bar(bTFULL + b), ph, kTcWaitCycles) &&
+                            mbar_wait(bar(bCFULL + s), phc, kTcWaitCycles);
             if (!__all_sync(0xffffffffu, ok)) {
                 if (lane == 0) fail();
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint8_t* cst = basep + 2 * ab_bytes + s * kPCBytes;  // C buffer it % 3
+            uint8_t* cst = basep + ring_bytes + s * kPCBytes;  // C buffer it % 3
 #pragma unroll
             for (int c = 0; c < kTcBN; c += 32) {
                 uint32_t v[32];
@@ -508,7 +530,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                 if (c + 32 == kTcBN) {
                     // the whole accumulator row is in registers: the buffer may be reused
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    mbar_arrive(bar(6 + b));
+                    mbar_arrive(bar(bTEMPTY + b));
                 }
                 // columns c .. c+31: box c / 64, 16-byte chunks (c % 64) / 8 .. + 3, swizzled by row
                 uint8_t* rowp = cst + (c / 64) * kPSlab + r * 128;
@@ -533,7 +555,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
             }
             // this row of the tile is written: visible to the TMA store, then signalled
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_arrive(bar(11 + s));
+            mbar_arrive(bar(bCDONE + s));
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -643,10 +665,10 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         set_error("tcgen05 GEMM: needs an sm_100-family device and the tensor-map driver entry point");
         return NL_ECUDA;
     }
-    if (K % kTcBK || K > 256 || (lda % 8) || (ldbt % 8) || (ldc % 8) || ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) ||
-        ((uintptr_t)C & 15)) {
-        set_error("tcgen05 GEMM: K must be a multiple of 64 (<= 256), leading dimensions multiples of 8, "
-                  "pointers 16-byte aligned");
+    if (K % kTcBK || K < kTcBK || K > kPMaxK || (per_tile && K > 256) || (lda % 8) || (ldbt % 8) || (ldc % 8) ||
+        ((uintptr_t)A & 15) || ((uintptr_t)Bt & 15) || ((uintptr_t)C & 15)) {
+        set_error("tcgen05 GEMM: K must be a multiple of 64 (<= 1024; <= 256 one tile per CTA), leading dimensions "
+                  "multiples of 8, pointers 16-byte aligned");
         return NL_EINVAL;
     }
     CUtensorMap tmA, tmB;
@@ -655,7 +677,7 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         set_error("tcgen05 GEMM: cuTensorMapEncodeTiled failed");
         return NL_ECUDA;
     }
-    if (!per_tile && K <= 2 * kTcBK) {
+    if (!per_tile) {
         // persistent pipelined kernel: one CTA per SM (at most one per tile)
         CUtensorMap tmC;
         if (!encode_2d(&tmC, C, (uint64_t)Nc, (uint64_t)M, (uint64_t)ldc, kTcBK, kTcBM)) {
@@ -672,7 +694,7 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         const long long ntiles = (long long)cdiv(Nc, kTcBN) * cdiv(M, kTcBM);
         const unsigned grid = (unsigned)std::min<long long>(ntiles, nsm);
         prof_begin("k_tc_gemm", st);
-        k_tc_gemm_p<<<grid, kPThreads, p_smem_bytes(K / kTcBK), st>>>(tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
+        k_tc_gemm_p<<<grid, kPThreads, p_smem_bytes(), st>>>(tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
         prof_end("k_tc_gemm", st);
         NL_CUDA_OK(cudaGetLastError());
         return NL_OK;
@@ -715,7 +737,7 @@ nl_status tc_gemm16_grouped(const GInst* inst, const TmapBytes* maps, const GTas
             if (nsm < 1) nsm = 1;
         }
         const unsigned grid = (unsigned)std::min(ntasks, nsm);
-        k_tc_gemm_pg<<<grid, kPThreads, p_smem_bytes(w / kTcBK), st>>>(inst, maps, tasks, ntasks, K, w, g_tc_err);
+        k_tc_gemm_pg<<<grid, kPThreads, p_smem_bytes(), st>>>(inst, maps, tasks, ntasks, K, w, g_tc_err);
     } else {
         k_tc_gemm_g<<<(unsigned)ntasks, kTcThreads, tc_smem_bytes(w), st>>>(inst, maps, tasks, K, w, g_tc_err);
     }

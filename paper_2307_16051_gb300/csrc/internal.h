@@ -51,6 +51,9 @@ struct LuWork {
     unsigned long long* pub = nullptr;  // 128 x 128 {epoch, value} words: columns published by k_panel16
     int stream = 0;           // binary16 fast path: 0 = one streaming launch per panel when it fits (128 rows per
                               // CTA when possible), 256 = the same with 256 rows per CTA, -1 = two launches
+    float* p32 = nullptr;     // two-level LU (outer block > 128): single-precision shadow of the matrix, N x ldp32,
+                              // of which the current outer block's row and column strips are used
+    int64_t ldp32 = 0;
 };
 size_t lu_work_bytes(int N, int nb, bool fp64);
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w);
@@ -59,6 +62,9 @@ void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w);
 // partial pivoting would keep the diagonal; the result equals partial pivoting
 // when *flag stays 0, otherwise A is left partly factored and the caller
 // restores A and calls again with fast = false.
+// nb: a multiple of 16 up to 128 (one level), or 256, 384, 512 (two levels,
+// fast path; lu16_nb_valid).
+bool lu16_nb_valid(int nb);
 nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm, bool fast, const LuWork& w,
                       cudaStream_t st, int* launches);
 nl_status lu64_factor(int N, double* A, int64_t ld, int* ipiv, int nb, bool fast, const LuWork& w, cudaStream_t st,

@@ -853,11 +853,39 @@ __device__ __forceinline__ bool diag_wait(const int* f, int* failp)
     }
 }
 
+// Eight consecutive entries (16-byte aligned) as binary32, and back: binary16
+// storage (the factorised matrix) rounds on store; binary32 storage (the
+// single-precision shadow of an outer block, two-level LU) keeps the value.
+__device__ __forceinline__ void load8(const __half* p, float* v)
+{
+    const uint4 raw = *reinterpret_cast<const uint4*>(p);
+    const __half* e = reinterpret_cast<const __half*>(&raw);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = __half2float(e[c]);
+}
+__device__ __forceinline__ void load8(const float* p, float* v)
+{
+    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void store8(__half* p, const float* v)
+{
+    __align__(16) __half h[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) h[c] = __float2half_rn(v[c]);
+    *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(h);
+}
+__device__ __forceinline__ void store8(float* p, const float* v)
+{
+    reinterpret_cast<float4*>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+    reinterpret_cast<float4*>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+
 // PUB: also publish each finished column t to pub[t * 128 + i] as the 64-bit
 // word {epoch, value} (U above the diagonal, the unrounded pivot on it, the
 // multipliers below), for the streaming off-diagonal solves of k_panel16.
-template <bool PUB = false>
-__device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t lda, int K, int w,
+template <bool PUB = false, typename S = __half>
+__device__ __forceinline__ void diag_lu16_body(S* __restrict__ A, int64_t lda, int K, int w,
                                                int* __restrict__ ipiv, int* __restrict__ flag,
                                                float* __restrict__ stage,
                                                unsigned long long* __restrict__ pub = nullptr, unsigned epoch = 0)
@@ -877,17 +905,14 @@ __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t l
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const int i = r0 + r;
-        const __half* src = A + (int64_t)(K + min(i, w - 1)) * lda + K + C0;
+        const S* src = A + (int64_t)(K + min(i, w - 1)) * lda + K + C0;
         if (vec && i < w && C0 + 8 <= w) {
-            const uint4 raw = *reinterpret_cast<const uint4*>(src);
-            const __half* e = reinterpret_cast<const __half*>(&raw);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) a[r][c] = __half2float(e[c]);
+            load8(src, a[r]);
         } else {
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 const int j = C0 + c;
-                a[r][c] = (i < w && j < w) ? __half2float(src[c]) : ((i == j) ? 1.0f : 0.0f);
+                a[r][c] = (i < w && j < w) ? ld_elem(src + c) : ((i == j) ? 1.0f : 0.0f);
             }
         }
     }
@@ -1002,16 +1027,13 @@ __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t l
     for (int r = 0; r < 4; ++r) {
         const int i = r0 + r;
         if (i < w && C0 < w) {
-            __half* dst = A + (int64_t)(K + i) * lda + K + C0;
+            S* dst = A + (int64_t)(K + i) * lda + K + C0;
             if (vec && C0 + 8 <= w) {
-                __align__(16) __half h[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) h[c] = __float2half_rn(a[r][c]);
-                *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<const uint4*>(h);
+                store8(dst, a[r]);
             } else {
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
-                    if (C0 + c < w) dst[c] = __float2half_rn(a[r][c]);
+                    if (C0 + c < w) st_elem(dst + c, a[r][c]);
             }
         }
     }
@@ -1049,11 +1071,12 @@ __device__ __forceinline__ void diag_lu16_body(__half* __restrict__ A, int64_t l
 
 
 
-__global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(__half* __restrict__ A, int64_t lda, int K, int w,
+template <typename S>
+__global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(S* __restrict__ A, int64_t lda, int K, int w,
                                                              int* __restrict__ ipiv, int* __restrict__ flag,
                                                              float* __restrict__ stage)
 {
-    diag_lu16_body(A, lda, K, w, ipiv, flag, stage);
+    diag_lu16_body<false, S>(A, lda, K, w, ipiv, flag, stage);
 }
 
 // k_panel16: the diagonal block and the off-diagonal solves of one panel in
@@ -1187,11 +1210,11 @@ __device__ __forceinline__ bool pnl_test_ready(uint32_t bar)
 // cache[t][k] = l_tk).  Threads 0..255 each own one row (column) and its
 // 128-value history; warps 14 and 15 fetch the published columns; column t
 // is signalled through ready[t] (an mbarrier per column, used once).
-template <bool ROWS>
-__device__ __forceinline__ void panel16_stream(__half* __restrict__ A, int64_t lda, int K, int w, int N, int blk,
-                                               int rpc, __half* __restrict__ Ut, int ldut, int* __restrict__ flag,
-                                               const unsigned long long* __restrict__ pub, unsigned epoch,
-                                               unsigned* __restrict__ err)
+template <bool ROWS, typename S = __half>
+__device__ __forceinline__ void panel16_stream(S* __restrict__ A, int64_t lda, int K, int w, int N, int blk,
+                                               int rpc, __half* __restrict__ Ut, int ldut, int ut_col0, int ut_k0,
+                                               int* __restrict__ flag, const unsigned long long* __restrict__ pub,
+                                               unsigned epoch, unsigned* __restrict__ err)
 {
     extern __shared__ __align__(16) float psm[];
     float* H = psm;                          // H[r * kPnlLd + t]: a, replaced by l (rows) / u (columns) at step t
@@ -1207,19 +1230,14 @@ __device__ __forceinline__ void panel16_stream(__half* __restrict__ A, int64_t l
     const bool vec = (w % 8 == 0) && (lda % 8 == 0) && ((((uintptr_t)(A + K)) & 15) == 0);
     if (live) {
         if (ROWS) {
-            const __half* R = A + (int64_t)idx * lda + K;
+            const S* R = A + (int64_t)idx * lda + K;
             if (vec) {
-                for (int t = 0; t < w; t += 8) {
-                    const uint4 raw = *reinterpret_cast<const uint4*>(R + t);
-                    const __half* e = reinterpret_cast<const __half*>(&raw);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) h[t + q] = __half2float(e[q]);
-                }
+                for (int t = 0; t < w; t += 8) load8(R + t, h + t);
             } else {
-                for (int t = 0; t < w; ++t) h[t] = __half2float(R[t]);
+                for (int t = 0; t < w; ++t) h[t] = ld_elem(R + t);
             }
         } else {
-            for (int t = 0; t < w; ++t) h[t] = __half2float(A[(int64_t)(K + t) * lda + idx]);
+            for (int t = 0; t < w; ++t) h[t] = ld_elem(A + (int64_t)(K + t) * lda + idx);
         }
     }
     __syncthreads();
@@ -1278,22 +1296,19 @@ __device__ __forceinline__ void panel16_stream(__half* __restrict__ A, int64_t l
     }
     if (!live) return;
     if (ROWS) {
-        __half* R = A + (int64_t)idx * lda + K;
+        S* R = A + (int64_t)idx * lda + K;
         if (vec) {
-            for (int t = 0; t < w; t += 8) {
-                __align__(16) __half e[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) e[q] = __float2half_rn(h[t + q]);
-                *reinterpret_cast<uint4*>(R + t) = *reinterpret_cast<const uint4*>(e);
-            }
+            for (int t = 0; t < w; t += 8) store8(R + t, h + t);
         } else {
-            for (int t = 0; t < w; ++t) R[t] = __float2half_rn(h[t]);
+            for (int t = 0; t < w; ++t) st_elem(R + t, h[t]);
         }
     } else {
-        for (int t = 0; t < w; ++t) A[(int64_t)(K + t) * lda + idx] = __float2half_rn(h[t]);
-        if (Ut) {
-            __half* u0 = Ut + (int64_t)(idx - K - w) * ldut;
-            if ((w % 8 == 0) && (ldut % 8 == 0) && ((((uintptr_t)Ut) & 15) == 0)) {
+        for (int t = 0; t < w; ++t) st_elem(A + (int64_t)(K + t) * lda + idx, h[t]);
+        // U12^T for the tensor-core update: row idx - ut_col0, columns ut_k0 .. ut_k0 + w - 1
+        // (columns left of ut_col0 are not part of that update)
+        if (Ut && idx >= ut_col0) {
+            __half* u0 = Ut + (int64_t)(idx - ut_col0) * ldut + ut_k0;
+            if ((w % 8 == 0) && (ldut % 8 == 0) && (ut_k0 % 8 == 0) && ((((uintptr_t)Ut) & 15) == 0)) {
                 for (int t = 0; t < w; t += 8) {
                     __align__(16) __half e[8];
 #pragma unroll
@@ -1307,18 +1322,25 @@ __device__ __forceinline__ void panel16_stream(__half* __restrict__ A, int64_t l
     }
 }
 
-__global__ void __launch_bounds__(kPnlThreads, 1) k_panel16(__half* __restrict__ A, int64_t lda, int K, int w, int N,
+// S: the storage the panel is read from and written to: the binary16 matrix,
+// or (two-level LU) its single-precision shadow over the current outer block.
+// Ut: U12^T in binary16 for the columns from ut_col0 (at K offset ut_k0).
+template <typename S>
+__global__ void __launch_bounds__(kPnlThreads, 1) k_panel16(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                            int nrb, int rpc, int* __restrict__ ipiv, int* __restrict__ flag,
                                                            float* __restrict__ stage, __half* __restrict__ Ut,
-                                                           int ldut, unsigned long long* __restrict__ pub,
-                                                           unsigned epoch, unsigned* __restrict__ err)
+                                                           int ldut, int ut_col0, int ut_k0,
+                                                           unsigned long long* __restrict__ pub, unsigned epoch,
+                                                           unsigned* __restrict__ err)
 {
     if (blockIdx.x == 0)
-        diag_lu16_body<true>(A, lda, K, w, ipiv, flag, stage, pub, epoch);
+        diag_lu16_body<true, S>(A, lda, K, w, ipiv, flag, stage, pub, epoch);
     else if ((int)blockIdx.x <= nrb)
-        panel16_stream<true>(A, lda, K, w, N, (int)blockIdx.x - 1, rpc, Ut, ldut, flag, pub, epoch, err);
+        panel16_stream<true, S>(A, lda, K, w, N, (int)blockIdx.x - 1, rpc, Ut, ldut, ut_col0, ut_k0, flag, pub, epoch,
+                                err);
     else
-        panel16_stream<false>(A, lda, K, w, N, (int)blockIdx.x - 1 - nrb, rpc, Ut, ldut, flag, pub, epoch, err);
+        panel16_stream<false, S>(A, lda, K, w, N, (int)blockIdx.x - 1 - nrb, rpc, Ut, ldut, ut_col0, ut_k0, flag, pub,
+                                 epoch, err);
 }
 
 // k_offdiag16: L21 = A21 U11^{-1} (row role) and U12 = L11^{-1} A12 (column
@@ -1340,10 +1362,13 @@ constexpr int kO16Rows = 128;  // rows or columns per CTA
 
 size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + 2 * wp) * sizeof(float); }
 
-__device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t lda, int K, int w, int N,
+template <typename S = __half>
+__device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                               int* __restrict__ flag, const float* __restrict__ stage, int bid)
+                                               int* __restrict__ flag, const float* __restrict__ stage, int bid,
+                                               int ut_col0 = -1, int ut_k0 = 0)
 {
+    if (ut_col0 < 0) ut_col0 = K + w;
     if (*(volatile int*)flag) return;
     extern __shared__ __align__(16) float osm[];
     const int wp = (w + 31) & ~31, nc = wp / 32;
@@ -1369,22 +1394,17 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
     float* Xt = X + tid;
     if (row_role) {
         bool bad = false;
-        __half* R = A + (int64_t)min(idx, N - 1) * lda + K;
+        S* R = A + (int64_t)min(idx, N - 1) * lda + K;
         const bool vec = (w % 32 == 0) && ((((uintptr_t)(A + K)) & 15) == 0) && (lda % 8 == 0);
         for (int c = 0; c < nc; ++c) {
             const int j0 = 32 * c;
             float x[32];
             if (vec && live) {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint4 raw = reinterpret_cast<const uint4*>(R + j0)[q];
-                    const __half* e = reinterpret_cast<const __half*>(&raw);
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) x[8 * q + k] = __half2float(e[k]);
-                }
+                for (int q = 0; q < 4; ++q) load8(R + j0 + 8 * q, x + 8 * q);
             } else {
 #pragma unroll
-                for (int k = 0; k < 32; ++k) x[k] = (live && j0 + k < w) ? __half2float(R[j0 + k]) : 0.0f;
+                for (int k = 0; k < 32; ++k) x[k] = (live && j0 + k < w) ? ld_elem(R + j0 + k) : 0.0f;
             }
 #pragma unroll 8
             for (int t = 0; t < j0; ++t) {
@@ -1416,16 +1436,11 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
             if (live) {
                 if (vec) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        __align__(16) __half h[8];
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) h[k] = __float2half_rn(x[8 * q + k]);
-                        reinterpret_cast<uint4*>(R + j0)[q] = *reinterpret_cast<const uint4*>(h);
-                    }
+                    for (int q = 0; q < 4; ++q) store8(R + j0 + 8 * q, x + 8 * q);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 32; ++k)
-                        if (j0 + k < w) R[j0 + k] = __float2half_rn(x[k]);
+                        if (j0 + k < w) st_elem(R + j0 + k, x[k]);
                 }
             }
         }
@@ -1437,7 +1452,7 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
             float x[32];
 #pragma unroll
             for (int k = 0; k < 32; ++k)
-                x[k] = (live && k0 + k < w) ? __half2float(A[(int64_t)(K + k0 + k) * lda + col]) : 0.0f;
+                x[k] = (live && k0 + k < w) ? ld_elem(A + (int64_t)(K + k0 + k) * lda + col) : 0.0f;
 #pragma unroll 8
             for (int t = 0; t < k0; ++t) {
                 const float u = Xt[t * kO16Rows];
@@ -1465,11 +1480,11 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
             if (live) {
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
-                    if (k0 + k < w) A[(int64_t)(K + k0 + k) * lda + col] = __float2half_rn(x[k]);
-                if (Ut) {
+                    if (k0 + k < w) st_elem(A + (int64_t)(K + k0 + k) * lda + col, x[k]);
+                if (Ut && idx >= ut_col0) {
                     // U12^T row (the tensor-core B operand): 32 consecutive entries
-                    __half* u0 = Ut + (int64_t)(idx - K - w) * ldut + k0;
-                    if (k0 + 32 <= w && (ldut % 8 == 0) && ((((uintptr_t)Ut) & 15) == 0)) {
+                    __half* u0 = Ut + (int64_t)(idx - ut_col0) * ldut + ut_k0 + k0;
+                    if (k0 + 32 <= w && (ldut % 8 == 0) && (ut_k0 % 8 == 0) && ((((uintptr_t)Ut) & 15) == 0)) {
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
                             __align__(16) __half h[8];
@@ -1488,11 +1503,13 @@ __device__ __forceinline__ void offdiag16_body(__half* __restrict__ A, int64_t l
     }
 }
 
-__global__ void __launch_bounds__(kO16Threads) k_offdiag16(__half* __restrict__ A, int64_t lda, int K, int w, int N,
+template <typename S>
+__global__ void __launch_bounds__(kO16Threads) k_offdiag16(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                            int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                                           int* __restrict__ flag, const float* __restrict__ stage)
+                                                           int* __restrict__ flag, const float* __restrict__ stage,
+                                                           int ut_col0, int ut_k0)
 {
-    offdiag16_body(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x);
+    offdiag16_body<S>(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x, ut_col0, ut_k0);
 }
 
 // C <- C - A B with per-element sequential fused multiply-adds over k in
@@ -1560,13 +1577,18 @@ __global__ void __launch_bounds__(256) k_gemm_simt(int M, int Nc, int K, const S
 
 // ------------------------------------------------------------------ host --
 
+// Workspace layout: the interchanging path's working panel (N x min(nb, 128)),
+// U12^T for the tensor-core update (N x nb binary16), info/flag words, the
+// diagonal-block stage, the published columns, and for an outer block above
+// 128 (two-level LU, binary16 only) the single-precision shadow N x ld.
 size_t lu_work_bytes(int N, int nb, bool fp64)
 {
     size_t el = fp64 ? 8 : 4;
-    size_t pnl = (size_t)N * nb * el;
+    size_t pnl = (size_t)N * std::min(nb, 128) * el;
     size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
+    size_t shadow = (!fp64 && nb > 128) ? (size_t)N * round_up(N, 64) * 4 + 256 : 0;
     return round_up(pnl, 256) + round_up(ut, 256) + 256 + (size_t)2 * 128 * 128 * 8 + 128 * 8 +
-           (size_t)128 * 128 * 8;
+           round_up((size_t)128 * 128 * 8, 256) + shadow;
 }
 
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
@@ -1574,7 +1596,7 @@ void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
     char* p = (char*)base;
     size_t el = fp64 ? 8 : 4;
     w->pnl = p;
-    p += round_up((size_t)N * nb * el, 256);
+    p += round_up((size_t)N * std::min(nb, 128) * el, 256);
     size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
     w->ut = fp64 ? nullptr : (__half*)p;
     p += round_up(ut, 256);
@@ -1584,6 +1606,14 @@ void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
     w->stage = p;
     p += (size_t)2 * 128 * 128 * 8 + 128 * 8;
     w->pub = (unsigned long long*)p;
+    p += round_up((size_t)128 * 128 * 8, 256);
+    if (!fp64 && nb > 128) {
+        w->p32 = (float*)p;
+        w->ldp32 = round_up(N, 64);
+    } else {
+        w->p32 = nullptr;
+        w->ldp32 = 0;
+    }
 }
 
 template <typename T, int NBL, int R, bool RND>
@@ -1720,8 +1750,9 @@ static int panel16_max_ctas()
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
-            set_max_dynamic_smem((const void*)k_panel16) == NL_OK &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_panel16, kPnlThreads, kPnlSmem) == cudaSuccess)
+            set_max_dynamic_smem((const void*)k_panel16<__half>) == NL_OK &&
+            set_max_dynamic_smem((const void*)k_panel16<float>) == NL_OK &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_panel16<__half>, kPnlThreads, kPnlSmem) == cudaSuccess)
             c = per * nsm;
         cudaGetLastError();
         cap.store(c, std::memory_order_release);
@@ -1743,9 +1774,11 @@ static int panel16_rows_per_cta(int rest, int pref = 0)
 
 static std::atomic<unsigned> g_panel_epoch{0};
 
-static nl_status launch_panel16(__half* A, int64_t ld, int K, int wd, int N, int* ipiv, const LuWork& w, __half* Ut,
-                                int ldut, cudaStream_t st)
+template <typename S>
+static nl_status launch_panel16(S* A, int64_t ld, int K, int wd, int N, int* ipiv, const LuWork& w, __half* Ut,
+                                int ldut, cudaStream_t st, int ut_col0 = -1, int ut_k0 = 0)
 {
+    if (ut_col0 < 0) ut_col0 = K + wd;
     const int rest = N - K - wd;
     int rpc = panel16_rows_per_cta(rest, w.stream);
     int nrb = (int)cdiv(rest, rpc);
@@ -1756,12 +1789,13 @@ static nl_status launch_panel16(__half* A, int64_t ld, int K, int wd, int N, int
     unsigned long long* pub = w.pub;
     unsigned* err = tc_error_word();
     if (!err) err = (unsigned*)(w.info + 2);  // (a word of the info block nobody else uses)
-    int Kv = K, wv = wd, Nv = N, ldutv = ldut;
+    int Kv = K, wv = wd, Nv = N, ldutv = ldut, uc0 = ut_col0, uk0 = ut_k0;
     int64_t ldv = ld;
-    void* args[] = {(void*)&A, (void*)&ldv, (void*)&Kv, (void*)&wv, (void*)&Nv, (void*)&nrb, (void*)&rpc, (void*)&ipiv,
-                    (void*)&flag, (void*)&stage, (void*)&Ut, (void*)&ldutv, (void*)&pub, (void*)&epoch, (void*)&err};
+    void* args[] = {(void*)&A,     (void*)&ldv,  (void*)&Kv,    (void*)&wv,   (void*)&Nv,  (void*)&nrb,
+                    (void*)&rpc,   (void*)&ipiv, (void*)&flag,  (void*)&stage, (void*)&Ut, (void*)&ldutv,
+                    (void*)&uc0,   (void*)&uk0,  (void*)&pub,   (void*)&epoch, (void*)&err};
     prof_begin("k_panel16", st);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_panel16, dim3(1 + 2 * nrb), dim3(kPnlThreads), args,
+    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_panel16<S>, dim3(1 + 2 * nrb), dim3(kPnlThreads), args,
                                                 kPnlSmem, st);
     prof_end("k_panel16", st);
     NL_CUDA_OK(e);
@@ -1781,8 +1815,10 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
     if (!smem_set) {
         if (set_max_dynamic_smem((const void*)k_trsm_u12<T, S, RND>) != NL_OK) return NL_ECUDA;
         if constexpr (kHalf) {
-            if (set_max_dynamic_smem((const void*)k_offdiag16) != NL_OK ||
-                set_max_dynamic_smem((const void*)k_diag_lu16) != NL_OK)
+            if (set_max_dynamic_smem((const void*)k_offdiag16<__half>) != NL_OK ||
+                set_max_dynamic_smem((const void*)k_offdiag16<float>) != NL_OK ||
+                set_max_dynamic_smem((const void*)k_diag_lu16<__half>) != NL_OK ||
+                set_max_dynamic_smem((const void*)k_diag_lu16<float>) != NL_OK)
                 return NL_ECUDA;
         } else {
             if (set_max_dynamic_smem((const void*)k_offdiag<T, S, RND>) != NL_OK ||
@@ -1812,7 +1848,7 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
                     continue;
                 }
                 prof_begin("k_diag_lu16", st);
-                k_diag_lu16<<<1, kD16Threads, kDiag16Smem, st>>>(A, ld, K, wd, ipiv, w.flag, (float*)w.stage);
+                k_diag_lu16<__half><<<1, kD16Threads, kDiag16Smem, st>>>(A, ld, K, wd, ipiv, w.flag, (float*)w.stage);
                 prof_end("k_diag_lu16", st);
             } else {
                 prof_begin("k_diag_lu", st);
@@ -1825,8 +1861,8 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
                 if constexpr (kHalf) {
                     const int nrb = (int)cdiv(rest, kO16Rows);
                     prof_begin("k_offdiag16", st);
-                    k_offdiag16<<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(
-                        A, ld, K, wd, N, nrb, tc ? w.ut : nullptr, nb, w.flag, (const float*)w.stage);
+                    k_offdiag16<__half><<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(
+                        A, ld, K, wd, N, nrb, tc ? w.ut : nullptr, nb, w.flag, (const float*)w.stage, -1, 0);
                     prof_end("k_offdiag16", st);
                 } else {
                     const int nrb = (int)cdiv(rest, kOffThreads / kOffG);
@@ -1875,14 +1911,161 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
     return NL_OK;
 }
 
+// ------------------------------------------------------ two-level LU --
+// Outer block W (a multiple of 128 up to 512), inner panels of 128, for the
+// binary16 fast path: the arithmetic of rounding period W, i.e. the oracle's
+// binary16-storage / binary32-arithmetic elimination with nb = W.  Per outer
+// block [K0, K0 + W):
+//   * its row and column strips (rows K0.. x columns K0..K0+W-1, and rows
+//     K0..K0+W-1 x the columns right of it) are copied to a single-precision
+//     shadow P;
+//   * each inner panel is factored on P by the streaming panel (or the two
+//     launches) exactly as the one-level path factors A: multipliers and U
+//     entries rounded to binary16 as they are formed, U12^T of the columns
+//     right of the outer block written in binary16 for the update below;
+//   * the inner panel's update is applied in single precision, unrounded, to
+//     the rest of the two strips only (one fused multiply-add per term in
+//     increasing k: the oracle's sequence exactly);
+//   * the strips go back to A (their entries are now binary16 values), and
+//     the rest of the matrix receives one update of depth W,
+//     A22 <- fl16(A22 - L21 U12), on the tensor cores (K streamed through the
+//     persistent kernel's operand ring) or SIMT.
+// So the trailing matrix is read and written once per W columns instead of
+// once per 128.
+template <bool TO32>
+__global__ void __launch_bounds__(256) k_strip_copy(__half* __restrict__ A, int64_t lda, float* __restrict__ P,
+                                                    int64_t ldp, int r0, int c0, int ncols)
+{
+    const int i = r0 + blockIdx.y;
+    const int j = c0 + (blockIdx.x * 256 + threadIdx.x) * 8;
+    if (j >= c0 + ncols) return;
+    __half* a = A + (int64_t)i * lda + j;
+    float* q = P + (int64_t)i * ldp + j;
+    const int n = min(8, c0 + ncols - j);
+    if (n == 8 && ((((uintptr_t)a) & 15) == 0) && ((((uintptr_t)q) & 15) == 0)) {
+        float v[8];
+        if (TO32) {
+            load8(a, v);
+            store8(q, v);
+        } else {
+            load8(q, v);
+            store8(a, v);
+        }
+    } else {
+        for (int e = 0; e < n; ++e) {
+            if (TO32) q[e] = __half2float(a[e]);
+            else a[e] = __float2half_rn(q[e]);
+        }
+    }
+}
+
+template <bool TO32>
+static nl_status copy_block(__half* A, int64_t lda, float* P, int64_t ldp, int r0, int c0, int nrows, int ncols,
+                            cudaStream_t st)
+{
+    if (nrows <= 0 || ncols <= 0) return NL_OK;
+    for (int y0 = 0; y0 < nrows; y0 += 65535) {
+        const int ny = std::min(65535, nrows - y0);
+        k_strip_copy<TO32><<<dim3((unsigned)cdiv(ncols, 256 * 8), (unsigned)ny), 256, 0, st>>>(A, lda, P, ldp, r0 + y0,
+                                                                                              c0, ncols);
+    }
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+static nl_status lu16_factor_2lvl(int N, __half* A, int64_t ld, int* ipiv, int W, int gemm, const LuWork& w,
+                                  cudaStream_t st, int* launches)
+{
+    float* P = w.p32;
+    const int64_t ldp = w.ldp32;
+    if (!P) {
+        set_error("lu16: an outer block above 128 needs the single-precision shadow workspace");
+        return NL_EINVAL;
+    }
+    int nl = 0;
+    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st));
+    NL_CUDA_OK(cudaMemsetAsync(w.pub, 0, (size_t)128 * 128 * 8, st));
+    static bool smem_set = false;
+    if (!smem_set) {
+        if (set_max_dynamic_smem((const void*)k_offdiag16<float>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_diag_lu16<float>) != NL_OK)
+            return NL_ECUDA;
+        smem_set = true;
+    }
+    for (int K0 = 0; K0 < N; K0 += W) {
+        const int Wd = std::min(W, N - K0), far = N - K0 - Wd, C1 = K0 + Wd;
+        const bool tc = gemm == 2 && tc_gemm_supported() && (Wd % 64 == 0);
+        NL_TRY(copy_block<true>(A, ld, P, ldp, K0, K0, N - K0, Wd, st));
+        NL_TRY(copy_block<true>(A, ld, P, ldp, K0, C1, Wd, far, st));
+        nl += 2;
+        for (int p0 = 0; p0 < Wd; p0 += 128) {
+            const int K = K0 + p0, wd = std::min(128, Wd - p0), rest = N - K - wd;
+            __half* ut = (tc && far > 0) ? w.ut : nullptr;
+            if (rest > 0 && w.stream >= 0 && panel16_rows_per_cta(rest, w.stream) > 0) {
+                NL_TRY(launch_panel16<float>(P, ldp, K, wd, N, ipiv, w, ut, W, st, C1, p0));
+                ++nl;
+            } else {
+                prof_begin("k_diag_lu16", st);
+                k_diag_lu16<float><<<1, kD16Threads, kDiag16Smem, st>>>(P, ldp, K, wd, ipiv, w.flag, (float*)w.stage);
+                prof_end("k_diag_lu16", st);
+                ++nl;
+                if (rest > 0) {
+                    const int nrb = (int)cdiv(rest, kO16Rows);
+                    const int wp = (int)round_up(wd, 32);
+                    prof_begin("k_offdiag16", st);
+                    k_offdiag16<float><<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(
+                        P, ldp, K, wd, N, nrb, ut, W, w.flag, (const float*)w.stage, C1, p0);
+                    prof_end("k_offdiag16", st);
+                    ++nl;
+                }
+            }
+            // this inner panel's update on the rest of the two strips, unrounded
+            const int right = C1 - K - wd;  // strip columns right of the inner panel
+            if (rest > 0 && right > 0) {
+                NL_TRY((launch_gemm_simt<float, float>(rest, right, wd, P + (K + wd) * ldp + K, ldp, P + K * ldp + K + wd,
+                                                      ldp, P + (K + wd) * ldp + K + wd, ldp, st, w.flag)));
+                ++nl;
+            }
+            const int below = C1 - K - wd;  // rows of the outer block below the inner panel
+            if (far > 0 && below > 0) {
+                NL_TRY((launch_gemm_simt<float, float>(below, far, wd, P + (K + wd) * ldp + K, ldp, P + K * ldp + C1, ldp,
+                                                      P + (K + wd) * ldp + C1, ldp, st, w.flag)));
+                ++nl;
+            }
+        }
+        NL_TRY(copy_block<false>(A, ld, P, ldp, K0, K0, N - K0, Wd, st));
+        NL_TRY(copy_block<false>(A, ld, P, ldp, K0, C1, Wd, far, st));
+        nl += 2;
+        if (far > 0) {
+            __half* L21 = A + (int64_t)C1 * ld + K0;
+            __half* A22 = A + (int64_t)C1 * ld + C1;
+            if (tc) NL_TRY(tc_gemm16_update(far, far, Wd, L21, ld, w.ut, W, A22, ld, st, w.flag));
+            else NL_TRY((launch_gemm_simt<__half, float>(far, far, Wd, L21, ld, A + (int64_t)K0 * ld + C1, ld, A22,
+                                                        ld, st, w.flag)));
+            ++nl;
+        }
+        NL_CUDA_OK(cudaGetLastError());
+    }
+    if (launches) *launches += nl;
+    return NL_OK;
+}
+
+// Outer block nb: a multiple of 16 up to 128 (one level), or 256, 384, 512
+// (two levels, fast path only; the interchanging path factors with 128).
+bool lu16_nb_valid(int nb) { return (nb >= 16 && nb <= 128 && nb % 16 == 0) || nb == 256 || nb == 384 || nb == 512; }
+
 nl_status lu16_factor(int N, __half* A, int64_t ld, int* ipiv, int nb, int gemm, bool fast, const LuWork& w,
                       cudaStream_t st, int* launches)
 {
-    if (nb < 16 || nb > 128 || nb % 16) {
-        set_error("lu16: nb must be a multiple of 16 in [16, 128]");
+    if (!lu16_nb_valid(nb)) {
+        set_error("lu16: nb must be a multiple of 16 in [16, 128], or 256, 384 or 512");
         return NL_EINVAL;
     }
     if (gemm == 2 && !tc_gemm_supported()) gemm = 1;
+    if (nb > 128) {
+        if (fast) return lu16_factor_2lvl(N, A, ld, ipiv, nb, gemm, w, st, launches);
+        nb = 128;  // the interchanging path (partial pivoting needs row swaps): one level
+    }
     return lu_factor_impl<float, __half, 16, true>(N, A, ld, ipiv, nb, gemm, fast, w, st, launches);
 }
 

@@ -332,6 +332,10 @@ struct nl_solver {
     float tune_ms[4] = {0, 0, 0, 0};
 };
 
+// Outer block the handle's LU workspace is sized for: the configured one, or
+// the largest autotuner candidate.
+static int lu_nb_alloc(const nl_config& d) { return d.lu_nb == -1 ? 512 : (d.lu_nb > 0 ? d.lu_nb : 128); }
+
 // Whether F is evaluated through the FFT convolution (nl_config.fft_f).  The
 // automatic choice takes it from N = 4096, where its four launches (about
 // 45 us) beat the direct sum (61 us at N = 4096, 2.1 ms at N = 32768, GB300).
@@ -342,7 +346,7 @@ static bool uses_fft(int n, const nl_config& d) { return d.fft_f == 1 || (d.fft_
 static size_t solver_bytes(int n, const nl_config& d)
 {
     const int m = d.gmres_restart;
-    const int nb = d.lu_nb > 0 ? d.lu_nb : 128;  // the autotuner (-1) only ever lowers it
+    const int nb = lu_nb_alloc(d);
     const int64_t ld = round_up(n, 64), ldv = ld;
     const size_t npart = (size_t)std::max(residual_partials(n), gemv_partials(n)) + 64;
     Carver cv(nullptr);
@@ -399,7 +403,8 @@ static nl_status eval_F(nl_solver* s, const double* x, const void* u, int u_is_d
 static nl_status autotune_lu(nl_solver* s)
 {
     const int n = s->N;
-    const int cands[4] = {128, 96, 64, 32};
+    // one-level 64 and 128, two-level 256 and 512 (all with the tensor-core update)
+    const int cands[4] = {512, 256, 128, 64};
     cudaStream_t st = s->st;
     float* jrs = s->cfg.scale_fp16 ? s->rs16 : nullptr;
     k_fill64<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, 1.0, s->xa);
@@ -407,7 +412,8 @@ static nl_status autotune_lu(nl_solver* s)
     float best = 1e30f;
     int bnb = 128, k = 0;
     for (int nb : cands) {
-        if (nb > n && nb != 128) continue;
+        if (nb > 128 && 2 * nb > n) continue;  // two levels need at least two outer blocks
+        if (nb < 128 && nb > n) continue;
         const int gemm = (nb % 64 == 0 && tc_gemm_supported()) ? 2 : 1;
         float ms_best = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
@@ -514,7 +520,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
                            d.trsv_cluster == 8 || d.trsv_cluster == 16) ||
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant < 0 || d.ir_variant > 1 ||
         d.gmres_factors32 < 0 || d.gmres_factors32 > 1 || d.lu16_arith < 0 || d.lu16_arith > 1 ||
-        d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && (d.lu_nb < 16 || d.lu_nb > 128 || d.lu_nb % 16)) ||
+        d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && !lu16_nb_valid(d.lu_nb)) ||
         d.lu_nb < -1 || d.scale_fp16 < 0 || d.scale_fp16 > 1 || d.fft_f < -1 || d.fft_f > 1 ||
         (d.scale_fp16 && (d.ir_variant || d.gmres_factors32 || d.lu16_arith))) {
         set_error("nl_create: invalid configuration");
@@ -529,7 +535,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->N = (int)N;
     s->c = c;
     s->cfg = d;
-    s->nb = d.lu_nb > 0 ? d.lu_nb : 128;  // the autotuner (lu_nb = -1) may lower it below; buffers fit 128
+    s->nb = d.lu_nb > 0 ? d.lu_nb : 128;  // the autotuner (lu_nb = -1) may change it; buffers fit lu_nb_alloc
     s->gemm = d.trailing_gemm ? d.trailing_gemm : 2;
     if (s->gemm == 2 && (!tc_gemm_supported() || s->nb % 64)) s->gemm = 1;
     s->ld = round_up(N, 64);
@@ -574,7 +580,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->lb.partial = s->partial;
     s->lb.counter = s->counter;
     s->lb.dscal = s->dscal + 4;
-    lu_work_carve(cv.take<char>(lu_work_bytes(n, s->nb, false)), n, s->nb, false, &s->luw);
+    lu_work_carve(cv.take<char>(lu_work_bytes(n, lu_nb_alloc(d), false)), n, s->nb, false, &s->luw);
     trsv_work_carve(cv.take<char>(trsv_work_bytes(n, false)), n, false, &s->tw);
     s->use_fft = uses_fft(n, d);
     if (s->use_fft) fft_work_carve(cv.take<char>(fft_work_bytes(n)), n, &s->fft);
@@ -889,7 +895,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
             }
         } else if (mode == NL_F32) {
             // two-precision Newton, F32: J32 factored in place in single precision
-            NL_TRY(lu32_factor(n, s->J32, s->ld, s->ipiv, s->nb, s->luw, st, &launches));
+            NL_TRY(lu32_factor(n, s->J32, s->ld, s->ipiv, std::min(s->nb, 128), s->luw, st, &launches));
             NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, sizeof(int), cudaMemcpyDeviceToHost, st));
             NL_TRY(trsv_prepare32(n, s->J32, s->ld, s->ipiv, s->tw32, st, &launches));
         } else {
@@ -1251,6 +1257,10 @@ nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int g
     }
     if (path == 3) return lu16_arith_entry((int)N, (__half*)A16, ld, ipiv, info_host, (cudaStream_t)stream);
     if (nb == 0) nb = 128;
+    if (!lu16_nb_valid(nb)) {
+        set_error("nl_lu16: nb must be a multiple of 16 in [16, 128], or 256, 384 or 512");
+        return NL_EINVAL;
+    }
     if (gemm == 0) gemm = 2;
     if (gemm == 2 && (nb % 64 || !tc_gemm_supported())) gemm = 1;
     return lu_entry<__half>(N, (__half*)A16, ld, ipiv, nb, gemm, path, info_host, (cudaStream_t)stream, false);

@@ -391,6 +391,20 @@ def test_large_n32768_gmresir():
     assert abs(m - (1 - math.sqrt(1 - c))) <= 1e-10
 
 
+@pytest.mark.parametrize("N,nb,mode", [(1100, 256, "GMRESIR16"), (2048, 512, "GMRESIR16"), (1500, 384, "IR16")])
+def test_two_level_lu_newton_matches_oracle(N, nb, mode):
+    """Newton with the two-level factorisation (lu_nb > 128): Newton counts
+    and solution of the oracle run with the same rounding period."""
+    c = 0.99
+    with nl.Solver(N, c, lu_nb=nb) as s:
+        x, status = s.solve(tol=1e-10, mode=mode)
+        st = s.stats()
+    xo, ro = O.newton(N, c, mode, tol=1e-10, lu_nb=nb)
+    assert status == nl.NL_OK and st["lu_nb"] == nb
+    check_counts(st, ro, mode)
+    assert rel_inf(x, xo) <= 1e-10
+
+
 def test_autotuned_lu_nb_is_used_and_matches_oracle():
     """lu_nb = -1: the handle times the factorisation for several outer
     blocks, keeps the fastest, and the solve equals the oracle run with that
