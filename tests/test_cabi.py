@@ -129,9 +129,12 @@ def test_server_no_device_is_an_error():
     # the single-precision factor copy: 4 N ld bytes more, and only for the GMRES-IR modes
     assert nl.footprint_bytes(1024, "GMRESIR16", gmres_factors32=1) >= nl.footprint_bytes(1024, "GMRESIR16") + 4 * 1024 * 1024
     assert nl.footprint_bytes(1024, "IR16", gmres_factors32=1) == nl.footprint_bytes(1024, "IR16")
-    # the autotuning setting (-1) sizes the handle for the largest panel width
+    # the autotuning setting (-1) sizes the handle for its largest candidate (the two-level
+    # outer block 512, with its single-precision shadow of the matrix)
     for N in (1, 700, 4096):
-        assert nl.footprint_bytes(N, lu_nb=-1) == nl.footprint_bytes(N, lu_nb=128) >= nl.footprint_bytes(N, lu_nb=32)
+        assert nl.footprint_bytes(N, lu_nb=-1) == nl.footprint_bytes(N, lu_nb=512) > nl.footprint_bytes(N, lu_nb=128)
+        assert nl.footprint_bytes(N, lu_nb=128) >= nl.footprint_bytes(N, lu_nb=32)
+        assert nl.footprint_bytes(N, lu_nb=512) >= nl.footprint_bytes(N, lu_nb=128) + 4 * N * N
 
 
 def test_test_hooks_and_scaled_jacobian_validate_arguments():
