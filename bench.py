@@ -162,6 +162,10 @@ def ncu_traffic(kernel):
     return None
 
 
+GROUPED_KIND = {1: "simt, 3 launches per outer step", 2: "tcgen05, 3 launches per outer step",
+                3: "one persistent launch, 64x64 simt tiles", 4: "one persistent launch, 128x64 simt tiles"}
+
+
 def bench_batched(nl, W, torch, dev, steps, warmup, tc_peak, fp64=True):
     """The 512-instance batch (N log-uniform in [64, 2048], c uniform in
     [0.1, 0.999], x0 = ones, seed 230716051): one graph-captured batched solve
@@ -186,7 +190,6 @@ def bench_batched(nl, W, torch, dev, steps, warmup, tc_peak, fp64=True):
         ms.append(e0.elapsed_time(e1))
     info = B.info()
     lu_flop = sum(2.0 * n ** 3 / 3.0 for n in Ns)
-    best = min(info["tune"], key=lambda t: t[2]) if info["tune"] else None
     out = {"workload": "512 instances, N log-uniform [64, 2048] (seed 230716051), c uniform [0.1, 0.999], x0=ones, "
                        "IR16 with GMRES-IR16 fallback, eta 1e-4, to 1e-10",
            "status": nl.STATUS_NAMES[st], "solves_per_s": len(Ns) / (statistics.median(ms) / 1e3),
@@ -194,12 +197,17 @@ def bench_batched(nl, W, torch, dev, steps, warmup, tc_peak, fp64=True):
            "parked_lu": info["parked_lu"], "parked_ir": info["parked_ir"], "newton_rounds": info["newton_rounds"],
            "ir_rounds": info["ir_rounds"], "gpu_launches": info["gpu_launches"],
            "graph": "one CUDA graph per solve: WHILE(Newton) { J, grouped LU, WHILE(IR) {...}, update }",
-           "autotune": [{"nb": t[0], "gemm": "tcgen05" if t[1] == 2 else "simt", "grouped_lu_ms": t[2]} for t in info["tune"]],
-           "lu_nb": info["lu_nb"], "trailing_gemm": "tcgen05" if info["trailing_gemm"] == 2 else "simt"}
-    if best:
-        tf = lu_flop / (best[2] / 1e3) / 1e12
-        out["grouped_lu"] = {"ms": best[2], "achieved": tf, "peak": tc_peak, "unit": "TFLOP/s", "frac": tf / tc_peak,
-                             "work": "sum of 2N^3/3 over the 512 Jacobians at x0"}
+           "autotune": [{"bucket_nmax": info["buckets"][t[3]]["nmax"], "nb": t[0], "gemm": GROUPED_KIND[t[1]],
+                         "bucket_lu_ms": t[2]} for t in info["tune"]],
+           "buckets": [{"nmax": b["nmax"], "count": b["count"], "nb": b["nb"], "gemm": GROUPED_KIND[b["gemm"]],
+                        "from_table": bool(b["cached"])} for b in info["buckets"]],
+           "lu_nb": info["lu_nb"], "trailing_gemm": GROUPED_KIND[info["trailing_gemm"]]}
+    if info["lu16_ms"] > 0:
+        tf = lu_flop / (info["lu16_ms"] / 1e3) / 1e12
+        out["grouped_lu"] = {"ms": info["lu16_ms"], "achieved": tf, "peak": tc_peak, "unit": "TFLOP/s",
+                             "frac": tf / tc_peak,
+                             "work": "sum of 2N^3/3 over the 512 Jacobians at x0; every N bucket's grouped LU "
+                                     "side by side on its own stream, CUDA events around the whole"}
     if fp64:
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -91,7 +91,9 @@ typedef struct {
                             nl_create: the factorisation of the Jacobian at x0 = ones is timed for nb in
                             {512, 256, 128, 64} (the two-level ones when N >= 2 nb) and the fastest is
                             kept */
-    int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update */
+    int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update;
+                            batches only (nl_batch_create): 3 / 4 = the grouped LU as one persistent
+                            launch with 64 x 64 / 128 x 64 SIMT update tiles (nb <= 64) */
     int lu_path;         /* [0 = auto] no-interchange fast path with exact fallback; 1 = interchanging path only */
     int trsv_cluster;    /* [0 = auto] half-precision triangular solves: one thread-block cluster per
                             triangle of at most 16 CTAs (the largest of 16, 8, 4 the device can
@@ -253,6 +255,8 @@ nl_status nl_debug_fail_allocs(int count);
 /* own N and c, advanced together on the device.                            */
 /* ----------------------------------------------------------------------- */
 
+#define NL_BATCH_MAX_TUNE 48
+
 /* Per-batch results of the last nl_batch_solve (host values). */
 typedef struct {
     int count;              /* instances */
@@ -261,15 +265,25 @@ typedef struct {
     int parked_ir;          /* instances whose IR stalled (finished singly with GMRES-IR) */
     int newton_rounds;      /* executions of the batched Newton step */
     int ir_rounds;          /* executions of the batched IR correction */
-    int lu_nb;              /* LU outer block in use (autotuned unless nl_config.lu_nb was set) */
-    int trailing_gemm;      /* 1 SIMT, 2 tcgen05 */
+    int lu_nb;              /* LU outer block of the bucket that holds the largest instance */
+    int trailing_gemm;      /* that bucket's update: 1 SIMT, 2 tcgen05 (three launches per outer step);
+                               3 / 4 one persistent launch, 64 x 64 / 128 x 64 SIMT update tiles */
     int gpu_launches;       /* kernels executed, including the single-instance completions */
     int graph_nodes_step;   /* kernel nodes in one batched Newton step (outside the IR loop) */
     int graph_nodes_ir;     /* kernel nodes in one IR correction */
-    int tune_count;         /* autotuner candidates timed */
-    int tune_nb[8];
-    int tune_gemm[8];
-    double tune_ms[8];      /* grouped LU time of each candidate on the batch's first Jacobians */
+    int tune_count;         /* autotuner candidates timed (all buckets) */
+    int tune_bucket[NL_BATCH_MAX_TUNE];  /* the bucket each candidate was timed on */
+    int tune_nb[NL_BATCH_MAX_TUNE];
+    int tune_gemm[NL_BATCH_MAX_TUNE];
+    double tune_ms[NL_BATCH_MAX_TUNE];   /* grouped LU time of the candidate on its bucket's first Jacobians */
+    int nbuckets;           /* N buckets of the binary16 grouped LU, factored side by side */
+    int bucket_nmax[8];     /* bucket b: bucket_nmax[b-1] < N <= bucket_nmax[b] (powers of two from 128) */
+    int bucket_count[8];    /* instances in the bucket */
+    int bucket_nb[8];       /* its outer block (the rounding period of its instances' factorisations) */
+    int bucket_gemm[8];     /* its update / launch form, as trailing_gemm */
+    int bucket_cached[8];   /* 1: the choice was read from the tuning table (NL_LU_TUNE_FILE) */
+    double lu16_ms;         /* device time of one whole binary16 grouped LU of the batch (every bucket,
+                               side by side) on the Jacobians at x0 = ones, best of 3 at creation */
     double t_total_ms;      /* host wall time of the solve */
     double t_graph_ms;      /* device time of the batched graph (CUDA events) */
     double t_single_ms;     /* host wall time of the single-instance completions */
@@ -282,10 +296,20 @@ typedef struct nl_batch nl_batch;
  * All device state is allocated here (the double Jacobians on the first
  * NL_FP64LU solve).  cfg may be NULL; cfg->lu_path = 1 hands every instance to
  * the single-instance interchanging path at its first step (the batch then
- * factors nothing itself); cfg->lu_nb = 0 lets the autotuner time
- * the grouped LU for (nb, update) in {(128, tcgen05), (64, tcgen05),
- * (64, SIMT), (32, SIMT)} on the batch's Jacobians at x0 = ones and keep the
- * fastest (recorded in nl_batch_info_t).  Vectors of the batch are packed:
+ * factors nothing itself).  The instances are grouped by N into buckets
+ * (N <= 128, 129..256, ..., 4097..8192); each bucket's binary16 grouped LU
+ * runs on its own stream, side by side with the others, with its own outer
+ * block nb (the rounding period of its instances' factorisations) and update.
+ * cfg->lu_nb != 0 gives every bucket that nb (and cfg->trailing_gemm);
+ * cfg->lu_nb = 0 lets the autotuner time each bucket alone, on the batch's
+ * Jacobians at x0 = ones, for (nb, update) in {(128, tcgen05), (64, tcgen05),
+ * (64, persistent 64x64), (64, persistent 128x64), (32, persistent 64x64),
+ * (32, persistent 128x64)} and keep the fastest (recorded in
+ * nl_batch_info_t).  When the environment variable NL_LU_TUNE_FILE names a
+ * file, the choices are kept there as JSON (one entry per device, SM count,
+ * bucket range and instance count rounded up to a power of two), read by
+ * later batches instead of timing, and written after tuning (a file that
+ * cannot be read or written only costs the timing).  Vectors of the batch are packed:
  * instance i occupies entries [off_i, off_i + N[i]), off_i = N[0]+...+N[i-1]. */
 nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl_config* cfg, nl_batch** out);
 
@@ -407,8 +431,14 @@ void nl_server_destroy(nl_server* s);
  * caller factors it with nl_lu16 / nl_lu64.  fp64 = 0: binary16 matrices,
  * arithmetic model as nl_lu16; fp64 = 1: double.  nb: multiple of 16 in
  * [16, 128] (0 = 128).  gemm: 0 auto, 1 SIMT, 2 tcgen05 (binary16, nb a
- * multiple of 64).  A, ipiv: host arrays of device pointers.  N[i] in
- * [1, 32768].  Allocates its workspace with cudaMalloc.  Synchronises. */
+ * multiple of 64), 3 / 4: the whole factorisation as ONE persistent launch
+ * (binary16, nb <= 64): CTAs take diagonal, off-diagonal and update tasks
+ * from a device queue and wait (bounded) on per-matrix progress words; the
+ * update tiles are 64 x 64 (3) or 128 x 64 (4) with the SIMT update's
+ * arithmetic, so the factors are bitwise those of gemm = 1.  A wait that
+ * gives up returns NL_ETIMEOUT.  A, ipiv: host arrays of device pointers.
+ * N[i] in [1, 32768].  Allocates its workspace with cudaMalloc.
+ * Synchronises. */
 nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64_t* ld, int32_t* const* ipiv,
                         int fp64, int nb, int gemm, int32_t* flags_host, void* stream);
 

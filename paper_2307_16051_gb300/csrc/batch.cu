@@ -25,7 +25,11 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -35,6 +39,10 @@ namespace nl {
 
 constexpr int kBtThreads = 512;  // grouped triangular solve: one CTA per instance
 constexpr int kBMaxN = 8192;     // batch instances keep their vector in shared memory
+// Instances are grouped by N into buckets (N <= 128, 129..256, ..., 4097..8192),
+// each factored by its own grouped LU on its own stream.
+constexpr int kBMaxBuckets = 7;
+constexpr int kBucketNmax[kBMaxBuckets] = {128, 256, 512, 1024, 2048, 4096, 8192};
 
 struct BCtl {
     int lin_count, act_count, ir_round, newton_round;
@@ -517,8 +525,19 @@ struct nl_batch {
     double* hist = nullptr;
     int *lin_iters = nullptr, *lin_outer = nullptr, *lin_failed = nullptr;
     double* lin_relres = nullptr;
-    GroupPlan plan16, plan64;
-    int nb = 128, gemm = 2;
+    GroupPlan plan64;
+    int nb = 128, gemm = 2;       // the choice of the bucket that holds the largest instance
+    // N buckets of the binary16 grouped LU, factored side by side on their own streams,
+    // each with its own outer block and update (autotuned per bucket)
+    int nbk = 0;
+    int bk_nmax[kBMaxBuckets] = {}, bk_count[kBMaxBuckets] = {}, bk_nb[kBMaxBuckets] = {},
+        bk_gemm[kBMaxBuckets] = {}, bk_cached[kBMaxBuckets] = {}, bk_id[kBMaxBuckets] = {};
+    std::vector<int> bk_of;                     // bucket of each instance
+    std::vector<std::vector<GInst>> bk_hgin;    // host copies of the bucket tables
+    GInst* bk_gin[kBMaxBuckets] = {};           // device bucket tables (in the pool)
+    GroupPlan bk_plan[kBMaxBuckets];
+    cudaStream_t bk_st[kBMaxBuckets] = {};
+    cudaEvent_t bk_ev[kBMaxBuckets] = {}, ev_fork = nullptr;
     // graphs (built on first use per mode)
     cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int nodes_init = 0, nodes_newton[2] = {0, 0}, nodes_ir = 0;
@@ -526,7 +545,7 @@ struct nl_batch {
     std::vector<nl_stats_t> stats;
     nl_batch_info_t info;
     // autotuning record
-    std::vector<int> tune_nb, tune_gemm;
+    std::vector<int> tune_nb, tune_gemm, tune_bucket;
     std::vector<double> tune_ms;
     // last solve
     std::vector<BState> hstate;
@@ -544,7 +563,12 @@ static void batch_free(nl_batch* B)
     if (B->st) cudaStreamSynchronize(B->st);
     for (int m = 0; m < 2; ++m)
         if (B->exec[m]) cudaGraphExecDestroy(B->exec[m]);
-    lu_grouped_free(&B->plan16);
+    for (int b = 0; b < kBMaxBuckets; ++b) {
+        lu_grouped_free(&B->bk_plan[b]);
+        if (B->bk_st[b]) cudaStreamDestroy(B->bk_st[b]);
+        if (B->bk_ev[b]) cudaEventDestroy(B->bk_ev[b]);
+    }
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
     lu_grouped_free(&B->plan64);
     if (B->pool) cudaFree(B->pool);
     if (B->pool64) cudaFree(B->pool64);
@@ -556,58 +580,198 @@ static void batch_free(nl_batch* B)
     delete B;
 }
 
-// Times the grouped binary16 LU on the batch's initial Jacobians for each
-// candidate (outer block, trailing update) and keeps the fastest.
-static nl_status batch_autotune(nl_batch* B)
+// The binary16 grouped-LU plan of bucket b for outer block nb and update g
+// (1 SIMT and 2 tcgen05, three launches per outer step; 3 / 4 one persistent
+// launch with 64 x 64 / 128 x 64 SIMT update tiles).
+static nl_status batch_plan16(nl_batch* B, int b, int nb, int g, GroupPlan* pl)
 {
-    const int cands[4][2] = {{128, 2}, {64, 2}, {64, 1}, {32, 1}};
-    const bool tc = tc_gemm_supported();
+    const int n = B->bk_count[b];
+    const GInst* h = B->bk_hgin[b].data();
+    if (g >= 3) return lu_grouped_plan(n, h, nb, 1, false, pl, 1, g == 3 ? 64 : 128);
+    return lu_grouped_plan(n, h, nb, g, false, pl);
+}
+
+// The binary16 grouped LU of every bucket: one bucket on the given stream, or
+// a fork to the buckets' streams and a join back (stream-capturable).
+static nl_status batch_lu16(nl_batch* B, cudaStream_t st, int* launches)
+{
+    if (B->nbk == 1) return lu_grouped_factor(B->bk_plan[0], B->bk_gin[0], st, launches);
+    NL_CUDA_OK(cudaEventRecord(B->ev_fork, st));
+    for (int b = 0; b < B->nbk; ++b) {
+        NL_CUDA_OK(cudaStreamWaitEvent(B->bk_st[b], B->ev_fork, 0));
+        NL_TRY(lu_grouped_factor(B->bk_plan[b], B->bk_gin[b], B->bk_st[b], launches));
+        NL_CUDA_OK(cudaEventRecord(B->bk_ev[b], B->bk_st[b]));
+        NL_CUDA_OK(cudaStreamWaitEvent(st, B->bk_ev[b], 0));
+    }
+    return NL_OK;
+}
+
+// Device time of one whole grouped LU (all buckets) on the Jacobians at
+// x0 = ones, best of three.
+static nl_status batch_time_lu16(nl_batch* B, double* ms_out)
+{
     cudaEvent_t e0, e1;
     NL_CUDA_OK(cudaEventCreate(&e0));
     NL_CUDA_OK(cudaEventCreate(&e1));
-    double best = 1e300;
-    int bnb = 128, bg = tc ? 2 : 1;
-    // F and J at x0 = ones for every instance
     k_b_init<<<B->count, 256, 0, B->st>>>(B->dinst, B->dst);
-    NL_TRY(launch_residual_g(B->dinst, B->dst, B->res_tasks, B->n_res, 0, B->htab, B->st));
-    for (const auto& cnd : cands) {
-        const int nb = cnd[0], g = cnd[1];
-        if (g == 2 && !tc) continue;
-        GroupPlan pl;
-        nl_status s = lu_grouped_plan(B->count, B->hgin.data(), nb, g, false, &pl);
-        if (s != NL_OK) return s;
-        float ms_best = 1e30f;
-        for (int rep = 0; rep < 2; ++rep) {
-            NL_CUDA_OK(cudaMemsetAsync(B->flags, 0, sizeof(int) * B->count, B->st));
-            NL_TRY(launch_jacobian_g(B->dinst, B->dst, B->row_off, B->count, B->total_rows, B->htab, B->htab32, 0,
-                                     B->st));
-            cudaEventRecord(e0, B->st);
-            s = lu_grouped_factor(pl, B->gin, B->st, nullptr);
-            cudaEventRecord(e1, B->st);
-            if (s != NL_OK) {
-                lu_grouped_free(&pl);
-                return s;
-            }
-            NL_CUDA_OK(cudaEventSynchronize(e1));
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms_best = std::min(ms_best, ms);
-        }
-        lu_grouped_free(&pl);
-        B->tune_nb.push_back(nb);
-        B->tune_gemm.push_back(g);
-        B->tune_ms.push_back(ms_best);
-        if (ms_best < best) {
-            best = ms_best;
-            bnb = nb;
-            bg = g;
-        }
+    nl_status s = launch_residual_g(B->dinst, B->dst, B->res_tasks, B->n_res, 0, B->htab, B->st);
+    float best = 1e30f;
+    for (int rep = 0; rep < 3 && s == NL_OK; ++rep) {
+        if (cudaMemsetAsync(B->flags, 0, sizeof(int) * B->count, B->st) != cudaSuccess) s = NL_ECUDA;
+        if (s == NL_OK)
+            s = launch_jacobian_g(B->dinst, B->dst, B->row_off, B->count, B->total_rows, B->htab, B->htab32, 0,
+                                  B->st);
+        if (s != NL_OK) break;
+        cudaEventRecord(e0, B->st);
+        s = batch_lu16(B, B->st, nullptr);
+        cudaEventRecord(e1, B->st);
+        if (s == NL_OK && cudaEventSynchronize(e1) != cudaSuccess) s = NL_ECUDA;
+        float ms = 0.0f;
+        if (s == NL_OK) cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    B->nb = bnb;
-    B->gemm = bg;
-    return NL_OK;
+    *ms_out = s == NL_OK ? best : 0.0;
+    return s;
+}
+
+// ---- the tuning table: a JSON file (path in the environment variable
+// NL_LU_TUNE_FILE) that keeps each bucket's choice between processes, one
+// entry per line:  "<key>": {"nb": 64, "gemm": 2, "ms": 1.234}
+// keyed by device, SM count, bucket range and instance count (next power of two).
+static std::string tune_key(const nl_batch* B, int b)
+{
+    int dev = 0, nsm = num_sms();
+    cudaGetDevice(&dev);
+    cudaDeviceProp pr;
+    std::string name = cudaGetDeviceProperties(&pr, dev) == cudaSuccess ? pr.name : "unknown";
+    for (char& ch : name)
+        if (ch == '"' || ch == '\\' || ch == '\n') ch = '_';
+    int cp = 1;
+    while (cp < B->bk_count[b]) cp *= 2;
+    const int id = B->bk_id[b], lo = id ? kBucketNmax[id - 1] + 1 : 1;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|sm%d|N%d-%d|count%d", name.c_str(), nsm, lo, kBucketNmax[id], cp);
+    return buf;
+}
+
+struct TuneEntry {
+    int nb = 0, gemm = 0;
+    double ms = 0.0;
+};
+
+static std::map<std::string, TuneEntry> tune_read(const char* path)
+{
+    std::map<std::string, TuneEntry> m;
+    FILE* f = path ? fopen(path, "r") : nullptr;
+    if (!f) return m;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        const char* q0 = strchr(line, '"');
+        const char* q1 = q0 ? strchr(q0 + 1, '"') : nullptr;
+        const char* body = q1 ? strstr(q1, "{\"nb\":") : nullptr;
+        TuneEntry e;
+        if (body && sscanf(body, "{\"nb\": %d, \"gemm\": %d, \"ms\": %lf", &e.nb, &e.gemm, &e.ms) == 3)
+            m[std::string(q0 + 1, q1)] = e;
+    }
+    fclose(f);
+    return m;
+}
+
+static bool tune_write(const char* path, const std::map<std::string, TuneEntry>& m)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\n\"format\": \"binary16 grouped-LU tuning table, one entry per N bucket\",\n\"entries\": {\n");
+    size_t k = 0;
+    for (const auto& kv : m)
+        fprintf(f, "  \"%s\": {\"nb\": %d, \"gemm\": %d, \"ms\": %.6f}%s\n", kv.first.c_str(), kv.second.nb,
+                kv.second.gemm, kv.second.ms, ++k < m.size() ? "," : "");
+    fprintf(f, "}\n}\n");
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+static bool tune_valid(int nb, int g)
+{
+    if (nb < 16 || nb > 128 || nb % 16 || g < 1 || g > 4) return false;
+    if (g == 2) return nb % 64 == 0 && tc_gemm_supported();
+    if (g >= 3) return nb <= 64 && tc_gemm_supported();
+    return true;
+}
+
+// Times the grouped binary16 LU of each bucket alone on the batch's initial
+// Jacobians for each candidate (outer block, update / launch form) and keeps
+// the fastest; a bucket found in the tuning table takes the stored choice.
+static nl_status batch_autotune(nl_batch* B)
+{
+    const int cands[6][2] = {{128, 2}, {64, 2}, {64, 3}, {64, 4}, {32, 3}, {32, 4}};
+    const bool tc = tc_gemm_supported();
+    const char* path = getenv("NL_LU_TUNE_FILE");
+    if (path && !*path) path = nullptr;
+    std::map<std::string, TuneEntry> table = tune_read(path);
+    bool dirty = false;
+    cudaEvent_t e0, e1;
+    NL_CUDA_OK(cudaEventCreate(&e0));
+    NL_CUDA_OK(cudaEventCreate(&e1));
+    // F and J at x0 = ones for every instance
+    k_b_init<<<B->count, 256, 0, B->st>>>(B->dinst, B->dst);
+    NL_TRY(launch_residual_g(B->dinst, B->dst, B->res_tasks, B->n_res, 0, B->htab, B->st));
+    nl_status s = NL_OK;
+    for (int b = 0; b < B->nbk && s == NL_OK; ++b) {
+        const std::string key = tune_key(B, b);
+        auto it = table.find(key);
+        if (it != table.end() && tune_valid(it->second.nb, it->second.gemm)) {
+            B->bk_nb[b] = it->second.nb;
+            B->bk_gemm[b] = it->second.gemm;
+            B->bk_cached[b] = 1;
+            continue;
+        }
+        double best = 1e300;
+        int bnb = 128, bg = tc ? 2 : 1;
+        for (const auto& cnd : cands) {
+            const int nb = cnd[0], g = cnd[1];
+            if (g >= 2 && !tc) continue;
+            GroupPlan pl;
+            if ((s = batch_plan16(B, b, nb, g, &pl)) != NL_OK) break;
+            float ms_best = 1e30f;
+            for (int rep = 0; rep < 2 && s == NL_OK; ++rep) {
+                if (cudaMemsetAsync(B->flags, 0, sizeof(int) * B->count, B->st) != cudaSuccess) s = NL_ECUDA;
+                if (s == NL_OK)
+                    s = launch_jacobian_g(B->dinst, B->dst, B->row_off, B->count, B->total_rows, B->htab, B->htab32,
+                                          0, B->st);
+                if (s != NL_OK) break;
+                cudaEventRecord(e0, B->st);
+                s = lu_grouped_factor(pl, B->bk_gin[b], B->st, nullptr);
+                cudaEventRecord(e1, B->st);
+                if (s == NL_OK && cudaEventSynchronize(e1) != cudaSuccess) s = NL_ECUDA;
+                float ms = 0.0f;
+                if (s == NL_OK) cudaEventElapsedTime(&ms, e0, e1);
+                ms_best = std::min(ms_best, ms);
+            }
+            lu_grouped_free(&pl);
+            if (s != NL_OK) break;
+            B->tune_bucket.push_back(b);
+            B->tune_nb.push_back(nb);
+            B->tune_gemm.push_back(g);
+            B->tune_ms.push_back(ms_best);
+            if (ms_best < best) {
+                best = ms_best;
+                bnb = nb;
+                bg = g;
+            }
+        }
+        B->bk_nb[b] = bnb;
+        B->bk_gemm[b] = bg;
+        table[key] = TuneEntry{bnb, bg, best};
+        dirty = true;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s == NL_OK && dirty && path) tune_write(path, table);  // best effort: an unwritable table only costs tuning
+    return s;
 }
 
 static nl_status batch_alloc_fp64(nl_batch* B);
@@ -630,6 +794,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 || d.trsv_cluster == 8 ||
           d.trsv_cluster == 16) ||
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant != 0 ||
+        d.trailing_gemm < 0 || d.trailing_gemm > 4 ||
         d.gmres_factors32 != 0 || d.lu16_arith != 0 || d.scale_fp16 != 0) {
         set_error("nl_batch_create: invalid configuration");
         return NL_EINVAL;
@@ -691,6 +856,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         cv.take<BInst>(count);
         cv.take<GInst>(count);
         cv.take<GInst>(count);
+        cv.take<GInst>(count);  // bucket tables
         cv.take<BState>(count);
         cv.take<BCtl>(1);
         cv.take<BParams>(1);
@@ -736,6 +902,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
     B->dinst = cv.take<BInst>(count);
     B->gin = cv.take<GInst>(count);
     B->gin64 = cv.take<GInst>(count);
+    GInst* bk_base = cv.take<GInst>(count);
     B->dst = cv.take<BState>(count);
     B->ctl = cv.take<BCtl>(1);
     B->prm = cv.take<BParams>(1);
@@ -792,6 +959,55 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         G.stage = stage;
         G.ut = ut;
     }
+    // N buckets: bucket tables in instance order, one stream and event each
+    {
+        int cnt[kBMaxBuckets] = {}, idx[kBMaxBuckets];
+        std::vector<int> raw(count);
+        for (int i = 0; i < count; ++i) {
+            int b = 0;
+            while (B->N[i] > kBucketNmax[b]) ++b;
+            raw[i] = b;
+            cnt[b] += 1;
+        }
+        B->nbk = 0;
+        for (int b = 0; b < kBMaxBuckets; ++b) {
+            idx[b] = -1;
+            if (!cnt[b]) continue;
+            idx[b] = B->nbk;
+            B->bk_id[B->nbk] = b;
+            B->bk_nmax[B->nbk] = kBucketNmax[b];
+            B->bk_count[B->nbk] = cnt[b];
+            B->nbk += 1;
+        }
+        B->bk_of.resize(count);
+        B->bk_hgin.assign(B->nbk, {});
+        for (int i = 0; i < count; ++i) {
+            B->bk_of[i] = idx[raw[i]];
+            B->bk_hgin[B->bk_of[i]].push_back(B->hgin[i]);
+        }
+        size_t o = 0;
+        for (int b = 0; b < B->nbk; ++b) {
+            B->bk_gin[b] = bk_base + o;
+            if (cudaMemcpy(B->bk_gin[b], B->bk_hgin[b].data(), sizeof(GInst) * B->bk_count[b],
+                           cudaMemcpyHostToDevice) != cudaSuccess) {
+                set_error("nl_batch_create: table upload failed");
+                batch_free(B);
+                return NL_ECUDA;
+            }
+            o += B->bk_count[b];
+        }
+        if (B->nbk > 1) {
+            bool ok = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+            for (int b = 0; b < B->nbk && ok; ++b)
+                ok = cudaStreamCreateWithFlags(&B->bk_st[b], cudaStreamNonBlocking) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&B->bk_ev[b], cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) {
+                set_error("nl_batch_create: stream creation failed");
+                batch_free(B);
+                return NL_ECUDA;
+            }
+        }
+    }
     if (cudaMemcpy(B->dinst, B->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(B->gin, B->hgin.data(), sizeof(GInst) * count, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(B->res_tasks, rt.data(), sizeof(BTask) * rt.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -814,13 +1030,21 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
     }
     nl_status s = NL_OK;
     if (d.lu_nb) {
-        B->nb = d.lu_nb;
-        B->gemm = d.trailing_gemm ? d.trailing_gemm : 2;
-        if (B->gemm == 2 && (B->nb % 64 || !tc_gemm_supported())) B->gemm = 1;
+        int g = d.trailing_gemm ? d.trailing_gemm : 2;
+        if (g == 2 && (d.lu_nb % 64 || !tc_gemm_supported())) g = 1;
+        if (g >= 3 && (d.lu_nb > 64 || !tc_gemm_supported())) g = 1;
+        for (int b = 0; b < B->nbk; ++b) {
+            B->bk_nb[b] = d.lu_nb;
+            B->bk_gemm[b] = g;
+        }
     } else {
         s = batch_autotune(B);
     }
-    if (s == NL_OK) s = lu_grouped_plan(count, B->hgin.data(), B->nb, B->gemm, false, &B->plan16);
+    for (int b = 0; b < B->nbk && s == NL_OK; ++b) s = batch_plan16(B, b, B->bk_nb[b], B->bk_gemm[b], &B->bk_plan[b]);
+    B->nb = B->bk_nb[B->nbk - 1];
+    B->gemm = B->bk_gemm[B->nbk - 1];
+    double lu16_ms = 0.0;
+    if (s == NL_OK) s = batch_time_lu16(B, &lu16_ms);
     if (s == NL_OK && cudaStreamSynchronize(B->st) != cudaSuccess) {
         set_error("nl_batch_create: %s", cudaGetErrorString(cudaGetLastError()));
         s = NL_ECUDA;
@@ -831,11 +1055,21 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
     }
     B->stats.resize(count);
     memset(&B->info, 0, sizeof(B->info));
-    B->info.tune_count = (int)std::min<size_t>(8, B->tune_nb.size());
+    B->info.tune_count = (int)std::min<size_t>(NL_BATCH_MAX_TUNE, B->tune_nb.size());
     for (int k = 0; k < B->info.tune_count; ++k) {
+        B->info.tune_bucket[k] = B->tune_bucket[k];
         B->info.tune_nb[k] = B->tune_nb[k];
         B->info.tune_gemm[k] = B->tune_gemm[k];
         B->info.tune_ms[k] = B->tune_ms[k];
+    }
+    B->info.lu16_ms = lu16_ms;
+    B->info.nbuckets = B->nbk;
+    for (int b = 0; b < B->nbk; ++b) {
+        B->info.bucket_nmax[b] = B->bk_nmax[b];
+        B->info.bucket_count[b] = B->bk_count[b];
+        B->info.bucket_nb[b] = B->bk_nb[b];
+        B->info.bucket_gemm[b] = B->bk_gemm[b];
+        B->info.bucket_cached[b] = B->bk_cached[b];
     }
     B->info.lu_nb = B->nb;
     B->info.trailing_gemm = B->gemm;
@@ -892,8 +1126,7 @@ static nl_status batch_build_graph(nl_batch* B, int fp64)
     const int count = B->count;
     const nl_config& C = B->cfg;
     const BInst* inst = fp64 ? B->dinst64 : B->dinst;
-    const GroupPlan& plan = fp64 ? B->plan64 : B->plan16;
-    const GInst* gin = fp64 ? B->gin64 : B->gin;
+    const GInst* gin64 = B->gin64;
     BParams* prm = B->prm;
     cudaStream_t s0 = B->st, s1 = B->s1, s2 = B->s2;
     const size_t vec_smem = (size_t)round_up(B->nmax, 32) * (fp64 ? 8 : 4);
@@ -927,7 +1160,10 @@ static nl_status batch_build_graph(nl_batch* B, int fp64)
         // lu_path = 1 (interchanging path only): the batch factors nothing itself and hands
         // every instance to the single-instance path at its first step
         const int park_all = (C.lu_path == 1) ? 1 : 0;
-        if (!park_all && (s = lu_grouped_factor(plan, gin, s1, &nodes_step)) != NL_OK) break;
+        if (!park_all) {
+            s = fp64 ? lu_grouped_factor(B->plan64, gin64, s1, &nodes_step) : batch_lu16(B, s1, &nodes_step);
+            if (s != NL_OK) break;
+        }
         if (!fp64) {
             k_b_rhs<<<count, 256, 0, s1>>>(inst, B->dst, C.eta_j, C.ir_maxit, park_all, B->ctl);
             {
@@ -1049,7 +1285,7 @@ static nl_status batch_solve_impl(nl_batch* B, const double* x0, bool x0_host, d
         if (tce) NL_CUDA_OK(cudaMemcpy(&e, tce, sizeof(unsigned), cudaMemcpyDeviceToHost));
         if (e) {
             cudaMemset(tce, 0, sizeof(unsigned));
-            set_error("batch: a tensor-core update's bounded wait gave up");
+            set_error("batch: a bounded device wait of the grouped LU gave up");
             return NL_ETIMEOUT;
         }
     }
@@ -1081,8 +1317,11 @@ static nl_status batch_solve_impl(nl_batch* B, const double* x0, bool x0_host, d
             nl_config cf = B->cfg;
             cf.tau_a = S.tau;
             if (!fp64) {
-                cf.lu_nb = B->nb;  // the same factorisation (rounding period) as the batch
-                cf.trailing_gemm = B->gemm;
+                // the same factorisation (rounding period) as the instance's bucket; the persistent
+                // launch's arithmetic is the SIMT update's
+                const int b = B->bk_of[i];
+                cf.lu_nb = B->bk_nb[b];
+                cf.trailing_gemm = B->bk_gemm[b] >= 3 ? 1 : B->bk_gemm[b];
             }
             cf.newton_maxit = std::max(0, B->cfg.newton_maxit - S.it);
             nl_solver* sv = nullptr;
@@ -1127,7 +1366,7 @@ static nl_status batch_fetch_stats(nl_batch* B)
         nl_stats_t& o = B->stats[i];
         memset(&o, 0, sizeof(o));
         o.mode = B->last_fp64 ? NL_FP64LU : NL_IR16_GMRES;
-        o.lu_nb = B->last_fp64 ? 64 : B->nb;
+        o.lu_nb = B->last_fp64 ? 64 : B->bk_nb[B->bk_of[i]];
         o.fnorm0 = S.fn0;
         o.fnorm = S.fn;
         o.status = status_of(S.status);
@@ -1232,7 +1471,7 @@ nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64
                         int fp64, int nb, int gemm, int32_t* flags_host, void* stream)
 {
     set_error("");
-    if (count < 1 || !N || !A || !ld || !ipiv || !flags_host || gemm < 0 || gemm > 2) {
+    if (count < 1 || !N || !A || !ld || !ipiv || !flags_host || gemm < 0 || gemm > 4) {
         set_error("nl_lu_grouped: bad argument");
         return NL_EINVAL;
     }
@@ -1278,7 +1517,10 @@ nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64
         set_error("nl_lu_grouped: upload failed");
         s = NL_ECUDA;
     }
-    if (s == NL_OK) s = lu_grouped_plan(count, hg.data(), nb, gemm, fp64 != 0, &plan);
+    if (s == NL_OK) {
+        if (gemm >= 3) s = lu_grouped_plan(count, hg.data(), nb, 1, fp64 != 0, &plan, 1, gemm == 3 ? 64 : 128);
+        else s = lu_grouped_plan(count, hg.data(), nb, gemm, fp64 != 0, &plan);
+    }
     if (s == NL_OK) s = lu_grouped_factor(plan, dg, st, nullptr);
     if (s == NL_OK && cudaStreamSynchronize(st) != cudaSuccess) {
         set_error("nl_lu_grouped: %s", cudaGetErrorString(cudaGetLastError()));
@@ -1294,7 +1536,7 @@ nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64
         unsigned e = 0;
         if (tce && cudaMemcpy(&e, tce, sizeof(unsigned), cudaMemcpyDeviceToHost) == cudaSuccess && e) {
             cudaMemset(tce, 0, sizeof(unsigned));
-            set_error("nl_lu_grouped: a tensor-core update's bounded wait gave up");
+            set_error("nl_lu_grouped: a bounded device wait gave up");
             return NL_ETIMEOUT;
         }
         for (int i = 0; i < count; ++i) flags_host[i] = hf[i] & 1;

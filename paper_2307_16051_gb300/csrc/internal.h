@@ -99,22 +99,32 @@ struct alignas(64) TmapBytes {  // an opaque CUtensorMap
     unsigned char b[128];
 };
 // Per-step task lists of a grouped factorisation (device arrays, owned).
+struct PTask;
 struct GroupPlan {
     int count = 0, nb = 128, gemm = 1, steps = 0;
     bool fp64 = false;
+    int kind = 0;              // 0: three launches per outer step; 1: one persistent launch (task queue)
+    int tm = 64;               // kind 1: update tile rows (64 or 128; 64 columns)
     std::vector<int> off, n;   // per step and class (3 * steps): offset into tasks and count
     GTask* tasks = nullptr;    // device
     TmapBytes* maps = nullptr; // device: 2 per instance (A and U12^T views), tensor-core update only
+    PTask* ptasks = nullptr;   // kind 1: the queue (device)
+    int nptasks = 0, grid = 0;
+    int* ctl = nullptr;        // kind 1: next-task counter, progress words, task counters (zeroed per launch)
     size_t bytes = 0;
 };
 size_t lu_stage_bytes();
 // Builds the plan for the instances (host copy of the device table, which must
 // already hold final pointers).  Allocates the device task and map arrays.
-nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, bool fp64, GroupPlan* plan);
+// kind 1 (one persistent launch over a device task queue) needs the binary16
+// factorisation, the SIMT update (gemm 1) and nb <= 64; tm is its update tile height.
+nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, bool fp64, GroupPlan* plan,
+                          int kind = 0, int tm = 64);
 void lu_grouped_free(GroupPlan* plan);
 // One-time kernel attribute set-up (call before any stream capture).
 nl_status lu_grouped_setup();
-// Launches the whole factorisation (3 launches per outer step); stream-capturable.
+// Launches the whole factorisation (kind 0: 3 launches per outer step; kind 1: a
+// memset and one launch); stream-capturable.
 nl_status lu_grouped_factor(const GroupPlan& plan, const GInst* dev_inst, cudaStream_t st, int* launches);
 
 // Batched Newton (batch.cu): one instance of the H-equation per entry.

@@ -1360,23 +1360,26 @@ __global__ void __launch_bounds__(kPnlThreads, 1) k_panel16(S* __restrict__ A, i
 constexpr int kO16Threads = 128;
 constexpr int kO16Rows = 128;  // rows or columns per CTA
 
-size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + 2 * wp) * sizeof(float); }
+__host__ __device__ size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + 2 * wp) * sizeof(float); }
 
 template <typename S = __half>
 __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                               int* __restrict__ flag, const float* __restrict__ stage, int bid,
-                                               int ut_col0 = -1, int ut_k0 = 0)
+                                               int* __restrict__ flag, const float* stage, int bid,
+                                               int ut_col0 = -1, int ut_k0 = 0, int tid_in = -1,
+                                               float* smem = nullptr)
 {
     if (ut_col0 < 0) ut_col0 = K + w;
-    if (*(volatile int*)flag) return;
+    if (tid_in < 0 && *(volatile int*)flag) return;  // (a group of a larger CTA: its caller checked)
     extern __shared__ __align__(16) float osm[];
     const int wp = (w + 31) & ~31, nc = wp / 32;
-    float* D = osm;                  // U11 (row role) or L11^T (column role), wp x wp
+    // tid_in / smem: a group of 128 threads of a larger CTA and its own shared region (the
+    // persistent grouped factorisation runs four such groups side by side)
+    float* D = smem ? smem : osm;    // U11 (row role) or L11^T (column role), wp x wp
     float* X = D + wp * wp;          // X[t * kO16Rows + tid]: this thread's multipliers / U entries
     float* pv = X + wp * kO16Rows;   // |a_tt|, unrounded
     float* rinv = pv + wp;           // 1 / u_tt, correctly rounded
-    const int tid = threadIdx.x;
+    const int tid = tid_in >= 0 ? tid_in : (int)threadIdx.x;
     const bool row_role = bid < nrow_blocks;
     {
         const float4* s4 = reinterpret_cast<const float4*>(stage + (row_role ? 0 : wp * wp));
@@ -2350,10 +2353,260 @@ __global__ void __launch_bounds__(256) k_gemm_simt_g(const GInst* __restrict__ i
                          A + (int64_t)(K + w) * ld + K + w, ld, I.flag, t.a, t.b);
 }
 
-nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, bool fp64, GroupPlan* plan)
+// ------------------------------------------- persistent grouped LU --
+// The whole grouped factorisation in one launch: CTAs (one per SM) take tasks
+// from a device queue in order (an atomic counter) and each task waits, with
+// a bounded poll, for the progress word of its matrix:
+//   diag(i, k)      needs phase 3k   (matrix i's update of step k-1 done),
+//   offdiag(i, k)   needs phase 3k+1 (its diagonal block factored),
+//   update(i, k)    needs phase 3k+2 (all its off-diagonal solves done);
+// the last task of each phase advances the word (release).  The queue lists
+// step k's diagonal tasks, then its off-diagonal tasks, then its update
+// tiles, step by step, so every task's dependencies come earlier in the queue
+// and were taken by CTAs that are running: no co-residency is needed and the
+// launch can be captured in a graph.  A CTA of 512 threads runs a diagonal
+// block (diag_lu16_body), four off-diagonal blocks of one role side by side
+// (four groups of 128 threads, each with its own shared region; padding
+// groups get blocks past the matrix and store nothing), or one update tile of
+// TM x 64 with sequential single-precision fused multiply-adds over k and one
+// rounding to binary16: the arithmetic of the three-launch SIMT path, so the
+// factors are bitwise those of the single-matrix LU with the SIMT update.
+// A matrix whose fast path failed (flag set) skips its work but its tasks
+// still advance its progress word; a wait that gives up records the error
+// and its CTA skips the work the same way, so nothing waits forever.
+constexpr int kPgThreads = 512;
+constexpr long long kPgSpin = 1LL << 24;
+
+struct PTask {
+    int inst, kind, step, a, b, n, pad0, pad1;  // kind 0 diag; 1 off-diagonal quad (a first block, b blocks in it,
+                                                // n = 1 row role / 0 column role); 2 update tile (a = m0, b = n0)
+};
+
+__device__ __forceinline__ bool pg_wait(const int* p, int need, unsigned* err)
+{
+    long long it = 0;
+    while (ld_acquire_gpu(p) < need) {
+        if (*(volatile unsigned*)err) return false;
+        if (++it > kPgSpin) {
+            atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// C[m0.., n0..] (TM x 64) <- fl16(C - A B) over K, 512 threads: thread (ty, tx) =
+// (tid / 16, tid % 16) owns rows ty + 32 a and columns tx + 16 b; every entry takes
+// its K products in increasing k, one fused multiply-add each.  The operands are
+// written by other CTAs of the same launch, so they are read through plain
+// (coherent) loads, never the read-only path.
+template <int TM>
+__device__ __forceinline__ void pg_gemm_tile(int M, int Nc, int K, const __half* A, int64_t lda, const __half* B,
+                                             int64_t ldb, __half* C, int64_t ldc, int m0, int n0, float* sm)
+{
+    constexpr int BK = 16, RA = TM / 32;
+    float* As = sm;                    // [BK][TM + 1]
+    float* Bs = sm + BK * (TM + 1);    // [BK][64]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    float acc[RA][4];
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = m0 + ty + 32 * a, j = n0 + tx + 16 * b;
+            acc[a][b] = (i < M && j < Nc) ? __half2float(C[(int64_t)i * ldc + j]) : 0.0f;
+        }
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        __syncthreads();
+        for (int q = tid; q < TM * BK; q += kPgThreads) {
+            const int r = q / BK, kk = q % BK, i = m0 + r, k = k0 + kk;
+            As[kk * (TM + 1) + r] = (i < M && k < K) ? __half2float(A[(int64_t)i * lda + k]) : 0.0f;
+        }
+        for (int q = tid; q < BK * 64; q += kPgThreads) {
+            const int kk = q / 64, x = q % 64, k = k0 + kk, j = n0 + x;
+            Bs[kk * 64 + x] = (k < K && j < Nc) ? __half2float(B[(int64_t)k * ldb + j]) : 0.0f;
+        }
+        __syncthreads();
+        const int kmax = min(BK, K - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            float av[RA], bv[4];
+#pragma unroll
+            for (int a = 0; a < RA; ++a) av[a] = As[kk * (TM + 1) + ty + 32 * a];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) bv[b] = Bs[kk * 64 + tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < RA; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(-av[a], bv[b], acc[a][b]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < RA; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int i = m0 + ty + 32 * a, j = n0 + tx + 16 * b;
+            if (i < M && j < Nc) C[(int64_t)i * ldc + j] = __float2half_rn(acc[a][b]);
+        }
+}
+
+// ctl: [0] the queue's next task, [1 .. count] progress words, [1 + count .. 1 + 2 count)
+// per-matrix task counters (all zero at launch).
+__global__ void __launch_bounds__(kPgThreads, 1) k_lu_grouped_p(const GInst* __restrict__ inst,
+                                                                const PTask* __restrict__ tasks, int ntasks, int nb,
+                                                                int tm, int* __restrict__ ctl, int count,
+                                                                unsigned* __restrict__ err)
+{
+    extern __shared__ __align__(16) float pgsm[];
+    __shared__ int tix, go;
+    int* next = ctl;
+    int* prog = ctl + 1;
+    int* cnt = ctl + 1 + count;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) tix = atomicAdd(next, 1);
+        __syncthreads();
+        const int t = tix;
+        if (t >= ntasks) break;
+        const PTask T = tasks[t];
+        const GInst I = inst[T.inst];
+        const int K = T.step * nb, w = min(nb, I.N - K), rest = I.N - K - w;
+        __half* A = reinterpret_cast<__half*>(I.A);
+        if (threadIdx.x == 0) {
+            const bool ok = pg_wait(&prog[T.inst], 3 * T.step + T.kind, err);
+            go = (ok && *(volatile const int*)I.flag == 0) ? 1 : 0;  // one read of the flag for the whole CTA
+        }
+        __syncthreads();
+        if (T.kind == 0) {
+            if (go) diag_lu16_body<false, __half>(A, I.ld, K, w, I.ipiv, I.flag, reinterpret_cast<float*>(I.stage));
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release_gpu(&prog[T.inst], rest > 0 ? 3 * T.step + 1 : 3 * T.step + 3);
+            }
+        } else if (T.kind == 1) {
+            const int wp = (w + 31) & ~31;
+            const int q = threadIdx.x >> 7, b = T.a + q;
+            const int fl = (int)(offdiag16_smem(wp) / sizeof(float));
+            if (go)
+                offdiag16_body<__half>(A, I.ld, K, w, I.N, T.n ? (1 << 20) : 0, nullptr, 0, I.flag,
+                                       reinterpret_cast<const float*>(I.stage), b, -1, 0, threadIdx.x & 127,
+                                       pgsm + q * fl);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const int total = 2 * ((rest + kO16Rows - 1) / kO16Rows);
+                if (atomicAdd(&cnt[T.inst], T.b) + T.b == total) {
+                    cnt[T.inst] = 0;
+                    __threadfence();
+                    st_release_gpu(&prog[T.inst], 3 * T.step + 2);
+                }
+            }
+        } else {
+            if (go) {
+                const __half* L21 = A + (int64_t)(K + w) * I.ld + K;
+                const __half* U12 = A + (int64_t)K * I.ld + K + w;
+                __half* C = A + (int64_t)(K + w) * I.ld + K + w;
+                if (tm == 128) pg_gemm_tile<128>(rest, rest, w, L21, I.ld, U12, I.ld, C, I.ld, T.a, T.b, pgsm);
+                else pg_gemm_tile<64>(rest, rest, w, L21, I.ld, U12, I.ld, C, I.ld, T.a, T.b, pgsm);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const int total = ((rest + tm - 1) / tm) * ((rest + 63) / 64);
+                if (atomicAdd(&cnt[T.inst], 1) + 1 == total) {
+                    cnt[T.inst] = 0;
+                    __threadfence();
+                    st_release_gpu(&prog[T.inst], 3 * T.step + 3);
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_zero_ints(int* __restrict__ p, int n)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+}
+
+static size_t pg_smem_bytes(int nb)
+{
+    const int wp = (int)round_up(nb, 32);
+    size_t b = std::max<size_t>(kDiag16Smem, 4 * offdiag16_smem(wp));
+    b = std::max<size_t>(b, (size_t)(16 * (128 + 1) + 16 * 64) * sizeof(float));
+    return b;
+}
+
+// The persistent launch's queue: for every outer step, the diagonal tasks, the
+// off-diagonal quads (row role, then column role), then the update tiles,
+// largest matrices first.
+static nl_status lu_grouped_plan_p(int count, const GInst* host_inst, int nb, int tm, GroupPlan* plan)
+{
+    int nmax = 0;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, host_inst[i].N);
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return host_inst[a].N > host_inst[b].N; });
+    const int steps = (int)cdiv(nmax, nb);
+    std::vector<PTask> q;
+    for (int k = 0; k < steps; ++k) {
+        const int K = k * nb;
+        for (int i : order)
+            if (host_inst[i].N > K) q.push_back({i, 0, k, 0, 0, 0, 0, 0});
+        for (int role = 1; role >= 0; --role)
+            for (int i : order) {
+                const int rest = host_inst[i].N - K - nb;
+                if (rest <= 0) continue;
+                const int nblk = (int)cdiv(rest, kO16Rows);
+                for (int a = 0; a < nblk; a += 4) q.push_back({i, 1, k, a, std::min(4, nblk - a), role, 0, 0});
+            }
+        for (int i : order) {
+            const int rest = host_inst[i].N - K - nb;
+            if (rest <= 0) continue;
+            for (int m0 = 0; m0 < rest; m0 += tm)
+                for (int n0 = 0; n0 < rest; n0 += 64) q.push_back({i, 2, k, m0, n0, 0, 0, 0});
+        }
+    }
+    lu_grouped_free(plan);
+    plan->count = count;
+    plan->nb = nb;
+    plan->gemm = 1;
+    plan->steps = steps;
+    plan->fp64 = false;
+    plan->kind = 1;
+    plan->tm = tm;
+    plan->off.clear();
+    plan->n.clear();
+    plan->nptasks = (int)q.size();
+    plan->grid = std::max(1, std::min(plan->nptasks, num_sms()));
+    const size_t qb = q.size() * sizeof(PTask), cb = (size_t)(1 + 2 * count) * sizeof(int);
+    plan->bytes = round_up(qb, 256) + round_up(cb, 256);
+    void* p = nullptr;
+    NL_CUDA_OK(cudaMalloc(&p, plan->bytes));
+    plan->tasks = reinterpret_cast<GTask*>(p);  // the allocation's base (freed through it)
+    plan->ptasks = reinterpret_cast<PTask*>(p);
+    plan->ctl = reinterpret_cast<int*>((char*)p + round_up(qb, 256));
+    if (qb) NL_CUDA_OK(cudaMemcpy(plan->ptasks, q.data(), qb, cudaMemcpyHostToDevice));
+    return NL_OK;
+}
+
+nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, bool fp64, GroupPlan* plan, int kind,
+                          int tm)
 {
     if (count < 1 || nb < 16 || nb > 128 || nb % 16) {
         set_error("grouped LU: need count >= 1 and nb a multiple of 16 in [16, 128]");
+        return NL_EINVAL;
+    }
+    if (kind == 1) {
+        if (fp64 || gemm != 1 || nb > 64 || !(tm == 64 || tm == 128) || !tc_gemm_supported() || !tc_error_word()) {
+            set_error("grouped LU: the persistent launch needs the binary16 LU, the SIMT update, nb <= 64, "
+                      "tile height 64 or 128");
+            return NL_EINVAL;
+        }
+        return lu_grouped_plan_p(count, host_inst, nb, tm, plan);
+    }
+    if (kind != 0) {
+        set_error("grouped LU: unknown kind %d", kind);
         return NL_EINVAL;
     }
     if (fp64) gemm = 1;
@@ -2426,6 +2679,10 @@ void lu_grouped_free(GroupPlan* plan)
     if (plan->tasks) cudaFree(plan->tasks);
     plan->tasks = nullptr;
     plan->maps = nullptr;
+    plan->ptasks = nullptr;
+    plan->ctl = nullptr;
+    plan->nptasks = 0;
+    plan->kind = 0;
 }
 
 nl_status lu_grouped_setup()
@@ -2435,7 +2692,8 @@ nl_status lu_grouped_setup()
         if (set_max_dynamic_smem((const void*)k_diag_lu16_g) != NL_OK ||
             set_max_dynamic_smem((const void*)k_offdiag16_g) != NL_OK ||
             set_max_dynamic_smem((const void*)k_diag_lu_g<double, double, false>) != NL_OK ||
-            set_max_dynamic_smem((const void*)k_offdiag_g<double, double, false>) != NL_OK)
+            set_max_dynamic_smem((const void*)k_offdiag_g<double, double, false>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_lu_grouped_p) != NL_OK)
             return NL_ECUDA;
         smem_set = true;
     }
@@ -2446,6 +2704,16 @@ nl_status lu_grouped_factor(const GroupPlan& plan, const GInst* dev_inst, cudaSt
 {
     NL_TRY(lu_grouped_setup());
     const int nb = plan.nb, wp = (int)round_up(nb, 32);
+    if (plan.kind == 1) {
+        k_zero_ints<<<1, 256, 0, st>>>(plan.ctl, 1 + 2 * plan.count);  // a kernel node: legal in conditional bodies
+        prof_begin("k_lu_grouped_p", st);
+        k_lu_grouped_p<<<plan.grid, kPgThreads, pg_smem_bytes(nb), st>>>(
+            dev_inst, plan.ptasks, plan.nptasks, nb, plan.tm, plan.ctl, plan.count, tc_error_word());
+        prof_end("k_lu_grouped_p", st);
+        NL_CUDA_OK(cudaGetLastError());
+        if (launches) *launches += 2;
+        return NL_OK;
+    }
     int nl = 0;
     for (int k = 0; k < plan.steps; ++k) {
         const int K = k * nb;

@@ -522,6 +522,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         d.gmres_factors32 < 0 || d.gmres_factors32 > 1 || d.lu16_arith < 0 || d.lu16_arith > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && !lu16_nb_valid(d.lu_nb)) ||
         d.lu_nb < -1 || d.scale_fp16 < 0 || d.scale_fp16 > 1 || d.fft_f < -1 || d.fft_f > 1 ||
+        d.trailing_gemm < 0 || d.trailing_gemm > 2 ||
         (d.scale_fp16 && (d.ir_variant || d.gmres_factors32 || d.lu16_arith))) {
         set_error("nl_create: invalid configuration");
         return NL_EINVAL;

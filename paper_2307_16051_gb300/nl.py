@@ -52,12 +52,19 @@ class Stats(ctypes.Structure):
                 ("reserved", ctypes.c_int * 5)]
 
 
+BATCH_MAX_TUNE = 48  # NL_BATCH_MAX_TUNE
+
+
 class BatchInfo(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int), ("converged", ctypes.c_int), ("parked_lu", ctypes.c_int),
                 ("parked_ir", ctypes.c_int), ("newton_rounds", ctypes.c_int), ("ir_rounds", ctypes.c_int),
                 ("lu_nb", ctypes.c_int), ("trailing_gemm", ctypes.c_int), ("gpu_launches", ctypes.c_int),
                 ("graph_nodes_step", ctypes.c_int), ("graph_nodes_ir", ctypes.c_int), ("tune_count", ctypes.c_int),
-                ("tune_nb", ctypes.c_int * 8), ("tune_gemm", ctypes.c_int * 8), ("tune_ms", ctypes.c_double * 8),
+                ("tune_bucket", ctypes.c_int * BATCH_MAX_TUNE), ("tune_nb", ctypes.c_int * BATCH_MAX_TUNE),
+                ("tune_gemm", ctypes.c_int * BATCH_MAX_TUNE), ("tune_ms", ctypes.c_double * BATCH_MAX_TUNE),
+                ("nbuckets", ctypes.c_int), ("bucket_nmax", ctypes.c_int * 8), ("bucket_count", ctypes.c_int * 8),
+                ("bucket_nb", ctypes.c_int * 8), ("bucket_gemm", ctypes.c_int * 8), ("bucket_cached", ctypes.c_int * 8),
+                ("lu16_ms", ctypes.c_double),
                 ("t_total_ms", ctypes.c_double), ("t_graph_ms", ctypes.c_double), ("t_single_ms", ctypes.c_double),
                 ("reserved", ctypes.c_int * 16)]
 
@@ -337,9 +344,12 @@ class Batch:
     def info(self) -> dict:
         b = BatchInfo()
         check(lib().nl_batch_info(self._h, ctypes.byref(b)))
-        d = {k: getattr(b, k) for k, _ in BatchInfo._fields_ if k not in ("tune_nb", "tune_gemm", "tune_ms",
-                                                                         "reserved")}
-        d["tune"] = [(b.tune_nb[k], b.tune_gemm[k], b.tune_ms[k]) for k in range(b.tune_count)]
+        d = {k: getattr(b, k) for k, _ in BatchInfo._fields_ if not k.startswith(("tune_", "bucket_", "reserved"))}
+        d["tune_count"] = b.tune_count
+        # (nb, gemm, ms, bucket) of every timed candidate
+        d["tune"] = [(b.tune_nb[k], b.tune_gemm[k], b.tune_ms[k], b.tune_bucket[k]) for k in range(b.tune_count)]
+        d["buckets"] = [{"nmax": b.bucket_nmax[k], "count": b.bucket_count[k], "nb": b.bucket_nb[k],
+                         "gemm": b.bucket_gemm[k], "cached": b.bucket_cached[k]} for k in range(b.nbuckets)]
         return d
 
     def device_bytes(self) -> int:

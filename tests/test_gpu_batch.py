@@ -1,6 +1,7 @@
 """Batched path (grouped LU, grouped triangular solves, graph-captured
 Newton over many instances) against the single-instance CUDA path and the
 CPU oracle, through the C ABI."""
+import json
 import math
 
 import numpy as np
@@ -99,6 +100,61 @@ def test_lu_grouped_simt_bit_exact_vs_oracle(nb):
         assert info == 0 and not ovf
         assert np.array_equal(ip, ipo)
         assert np.array_equal(LU, LUo)
+
+
+@pytest.mark.parametrize("nb,gemm", [(64, 3), (64, 4), (32, 3), (48, 4), (16, 3)])
+def test_lu_grouped_persistent_identical_to_single(nb, gemm):
+    """One persistent launch over a device task queue (gemm 3 / 4: 64 x 64 /
+    128 x 64 update tiles): factors and pivots bit-for-bit those of the
+    single-matrix LU with the SIMT update at the same nb, on the sizes of the
+    three-launch test plus one that spans many tiles and several
+    off-diagonal quads (N = 1500)."""
+    sizes = SIZES + [1500]
+    mats = [jacobian16(N, 0.5 + 0.049 * k, 300 + k) for k, N in enumerate(sizes)]
+    out, flags = lu_grouped(mats, nb, gemm)
+    assert not flags.any()
+    for M, (LU, ip) in zip(mats, out):
+        N = M.shape[0]
+        LUs, ips = lu_single(M, ((N + 63) // 64) * 64, nb, 1)
+        assert np.array_equal(ip, np.arange(N)) and np.array_equal(ips, ip)
+        assert np.array_equal(LU, LUs), N
+
+
+def test_lu_grouped_persistent_many_matrices_vs_oracle():
+    """Many more queue tasks than CTAs (60 matrices, N log-uniform in
+    [20, 900]): every matrix equals the oracle's binary16-storage /
+    binary32-arithmetic elimination with rounding period nb, exactly."""
+    g = np.random.default_rng(11)
+    Ns = [int(round(math.exp(v))) for v in g.uniform(math.log(20), math.log(900), 60)]
+    mats = [jacobian16(N, float(g.uniform(0.1, 0.999)), 500 + k) for k, N in enumerate(Ns)]
+    out, flags = lu_grouped(mats, 32, 4)
+    assert not flags.any()
+    for M, (LU, ip) in zip(mats, out):
+        LUo, ipo, info, ovf = O.lu16_dev(M, 32)
+        assert info == 0 and not ovf
+        assert np.array_equal(ip, ipo) and np.array_equal(LU, LUo)
+
+
+def test_lu_grouped_persistent_flags_and_neighbours():
+    """In the persistent launch a matrix that needs interchanges is flagged,
+    its remaining tasks skip their work but still advance its progress word
+    (nothing waits on it), and its neighbours are factored as alone."""
+    P, _ = W.pivot_forcing_matrix(150, 3)
+    mats = [jacobian16(90, 0.9, 1), O.fl16(P), jacobian16(700, 0.99, 2), O.fl16(W.pivot_forcing_matrix(70, 4)[0])]
+    out, flags = lu_grouped(mats, 64, 3)
+    assert list(flags) == [0, 1, 0, 1]
+    for k in (0, 2):
+        N = mats[k].shape[0]
+        LUs, ips = lu_single(mats[k], ((N + 63) // 64) * 64, 64, 1)
+        assert np.array_equal(out[k][0], LUs) and np.array_equal(out[k][1], ips)
+
+
+def test_lu_grouped_persistent_rejects_unsupported():
+    """The persistent launch takes binary16, nb <= 64 only."""
+    A = padded16(jacobian16(100, 0.5, 1), 128)
+    ip = torch.empty(100, dtype=torch.int32, device=dev())
+    with pytest.raises(RuntimeError):
+        nl.lu_grouped([100], [A], [128], [ip], nb=128, gemm=3)
 
 
 def test_lu_grouped_flags_matrices_that_need_interchanges():
@@ -249,21 +305,72 @@ def test_batch_edge_instances_and_repeat():
         assert rel_inf(x, xo) <= 1e-10
 
 
-def test_batch_autotuner_choice_is_used_and_recorded():
+def test_batch_autotuner_per_bucket_choice_is_used_and_recorded(tmp_path, monkeypatch):
+    """Each N bucket is timed alone for every candidate and takes its fastest;
+    every instance's factorisation (stats lu_nb) is its bucket's; the choices
+    are written to the tuning table (NL_LU_TUNE_FILE, JSON) and a second
+    batch reads them instead of timing, with bit-identical results."""
     Ns, cs = small_batch(10, seed=9)
+    path = tmp_path / "tune.json"
+    monkeypatch.setenv("NL_LU_TUNE_FILE", str(path))
     with nl.Batch(Ns, cs) as B:
         info0 = B.info()
         xs, status = B.solve(tol=1e-10)
-        info = B.info()
-        st = B.stats(0)
+        sts = [B.stats(i) for i in range(len(Ns))]
     assert status == nl.NL_OK
-    cands = {(t[0], t[1]) for t in info0["tune"]}
-    assert len(info0["tune"]) >= 2 and (info["lu_nb"], info["trailing_gemm"]) in cands
-    best = min(info0["tune"], key=lambda t: t[2])
-    assert (best[0], best[1]) == (info["lu_nb"], info["trailing_gemm"])
-    assert st["lu_nb"] == info["lu_nb"]
-    xo, ro = O.newton(Ns[0], cs[0], "IR16GM", tol=1e-10, lu_nb=info["lu_nb"])
-    assert newton_counts_agree(st["newton_iters"], ro) and rel_inf(xs[0], xo) <= 1e-10
+    bks = info0["buckets"]
+    assert len(bks) >= 2 and sum(b["count"] for b in bks) == len(Ns)
+    for k, b in enumerate(bks):
+        cands = [t for t in info0["tune"] if t[3] == k]
+        assert len(cands) >= 2 and not b["cached"]
+        best = min(cands, key=lambda t: t[2])
+        assert (best[0], best[1]) == (b["nb"], b["gemm"])
+    bounds = [b["nmax"] for b in bks]
+    for i, N in enumerate(Ns):
+        k = next(j for j, m in enumerate(bounds) if N <= m)
+        assert sts[i]["lu_nb"] == bks[k]["nb"]
+    assert (info0["lu_nb"], info0["trailing_gemm"]) == (bks[-1]["nb"], bks[-1]["gemm"])
+    xo, ro = O.newton(Ns[0], cs[0], "IR16GM", tol=1e-10, lu_nb=sts[0]["lu_nb"])
+    assert newton_counts_agree(sts[0]["newton_iters"], ro) and rel_inf(xs[0], xo) <= 1e-10
+    table = json.loads(path.read_text())["entries"]
+    assert len(table) == len(bks)
+    with nl.Batch(Ns, cs) as B2:
+        info1 = B2.info()
+        xs2, _ = B2.solve(tol=1e-10)
+    assert info1["tune_count"] == 0 and all(b["cached"] for b in info1["buckets"])
+    assert [(b["nb"], b["gemm"]) for b in info1["buckets"]] == [(b["nb"], b["gemm"]) for b in bks]
+    for a, b in zip(xs, xs2):
+        assert np.array_equal(a, b)
+
+
+def test_batch_tuning_table_unreadable_is_ignored(tmp_path, monkeypatch):
+    """A tuning table that is not ours (or holds choices this device cannot
+    run) is ignored: the batch times its buckets and overwrites it."""
+    path = tmp_path / "tune.json"
+    path.write_text('{"entries": {"x": {"nb": 999, "gemm": 7, "ms": 1.0}}}\nnot json at all\n')
+    monkeypatch.setenv("NL_LU_TUNE_FILE", str(path))
+    Ns, cs = small_batch(4, seed=2)
+    with nl.Batch(Ns, cs) as B:
+        info = B.info()
+        _, status = B.solve(tol=1e-10)
+    assert status == nl.NL_OK and info["tune_count"] >= 2 and not any(b["cached"] for b in info["buckets"])
+    assert len(json.loads(path.read_text())["entries"]) >= 1
+
+
+@pytest.mark.parametrize("gemm", [3, 4])
+def test_batch_persistent_grouped_lu_in_graph_equals_simt(gemm):
+    """The persistent grouped-LU launch inside the batch graph (conditional
+    WHILE body, buckets side by side): every instance's iterate bit for bit
+    that of the three-launch SIMT grouped LU at the same nb."""
+    Ns, cs = small_batch(12, seed=21)
+    with nl.Batch(Ns, cs, lu_nb=64, trailing_gemm=1) as B1:
+        x1, s1 = B1.solve(tol=1e-10)
+    with nl.Batch(Ns, cs, lu_nb=64, trailing_gemm=gemm) as B2:
+        x2, s2 = B2.solve(tol=1e-10)
+        info = B2.info()
+    assert s1 == s2 == nl.NL_OK and all(b["gemm"] == gemm for b in info["buckets"])
+    for a, b in zip(x1, x2):
+        assert np.array_equal(a, b)
 
 
 def test_batch_full_workload_512_instances():
