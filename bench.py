@@ -163,7 +163,8 @@ def ncu_traffic(kernel):
 
 
 GROUPED_KIND = {1: "simt, 3 launches per outer step", 2: "tcgen05, 3 launches per outer step",
-                3: "one persistent launch, 64x64 simt tiles", 4: "one persistent launch, 128x64 simt tiles"}
+                3: "one persistent launch, 64x64 simt tiles", 4: "one persistent launch, 128x64 simt tiles",
+                5: "one persistent launch, 128x128 tcgen05 tiles"}
 
 
 def bench_batched(nl, W, torch, dev, steps, warmup, tc_peak, fp64=True):

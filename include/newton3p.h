@@ -93,7 +93,8 @@ typedef struct {
                             kept */
     int trailing_gemm;   /* [0 = auto] 1 = SIMT fp32-FMA trailing update, 2 = tcgen05 tensor-core update;
                             batches only (nl_batch_create): 3 / 4 = the grouped LU as one persistent
-                            launch with 64 x 64 / 128 x 64 SIMT update tiles (nb <= 64) */
+                            launch with 64 x 64 / 128 x 64 SIMT update tiles (nb <= 64), 5 = one
+                            persistent launch with 128 x 128 tcgen05 update tiles (nb = 64) */
     int lu_path;         /* [0 = auto] no-interchange fast path with exact fallback; 1 = interchanging path only */
     int trsv_cluster;    /* [0 = auto] half-precision triangular solves: one thread-block cluster per
                             triangle of at most 16 CTAs (the largest of 16, 8, 4 the device can
@@ -267,7 +268,8 @@ typedef struct {
     int ir_rounds;          /* executions of the batched IR correction */
     int lu_nb;              /* LU outer block of the bucket that holds the largest instance */
     int trailing_gemm;      /* that bucket's update: 1 SIMT, 2 tcgen05 (three launches per outer step);
-                               3 / 4 one persistent launch, 64 x 64 / 128 x 64 SIMT update tiles */
+                               3 / 4 one persistent launch, 64 x 64 / 128 x 64 SIMT update tiles;
+                               5 one persistent launch, 128 x 128 tcgen05 update tiles */
     int gpu_launches;       /* kernels executed, including the single-instance completions */
     int graph_nodes_step;   /* kernel nodes in one batched Newton step (outside the IR loop) */
     int graph_nodes_ir;     /* kernel nodes in one IR correction */
@@ -303,8 +305,9 @@ typedef struct nl_batch nl_batch;
  * cfg->lu_nb != 0 gives every bucket that nb (and cfg->trailing_gemm);
  * cfg->lu_nb = 0 lets the autotuner time each bucket alone, on the batch's
  * Jacobians at x0 = ones, for (nb, update) in {(128, tcgen05), (64, tcgen05),
- * (64, persistent 64x64), (64, persistent 128x64), (32, persistent 64x64),
- * (32, persistent 128x64)} and keep the fastest (recorded in
+ * (64, persistent tcgen05 128x128), (64, persistent SIMT 64x64), (64,
+ * persistent SIMT 128x64), (32, persistent SIMT 64x64), (32, persistent SIMT
+ * 128x64)} and keep the fastest (recorded in
  * nl_batch_info_t).  When the environment variable NL_LU_TUNE_FILE names a
  * file, the choices are kept there as JSON (one entry per device, SM count,
  * bucket range and instance count rounded up to a power of two), read by
@@ -431,16 +434,27 @@ void nl_server_destroy(nl_server* s);
  * caller factors it with nl_lu16 / nl_lu64.  fp64 = 0: binary16 matrices,
  * arithmetic model as nl_lu16; fp64 = 1: double.  nb: multiple of 16 in
  * [16, 128] (0 = 128).  gemm: 0 auto, 1 SIMT, 2 tcgen05 (binary16, nb a
- * multiple of 64), 3 / 4: the whole factorisation as ONE persistent launch
- * (binary16, nb <= 64): CTAs take diagonal, off-diagonal and update tasks
- * from a device queue and wait (bounded) on per-matrix progress words; the
- * update tiles are 64 x 64 (3) or 128 x 64 (4) with the SIMT update's
- * arithmetic, so the factors are bitwise those of gemm = 1.  A wait that
- * gives up returns NL_ETIMEOUT.  A, ipiv: host arrays of device pointers.
+ * multiple of 64), 3 / 4 / 5: the whole factorisation as ONE persistent
+ * launch (binary16, nb <= 64): CTAs take diagonal, off-diagonal and update
+ * tasks from a device queue and wait (bounded) on per-matrix progress words;
+ * the update tiles are 64 x 64 (3) or 128 x 64 (4) with the SIMT update's
+ * arithmetic (factors bitwise those of gemm = 1), or 128 x 128 tcgen05 tiles
+ * (5, nb = 64; factors bitwise those of gemm = 2).  A wait that gives up
+ * returns NL_ETIMEOUT.  A, ipiv: host arrays of device pointers.
  * N[i] in [1, 32768].  Allocates its workspace with cudaMalloc.
  * Synchronises. */
 nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64_t* ld, int32_t* const* ipiv,
                         int fp64, int nb, int gemm, int32_t* flags_host, void* stream);
+
+/* Per-task timing of the persistent grouped LU (nl_lu_grouped gemm 3 / 4 /
+ * 5, batches with trailing_gemm 3 / 4 / 5), for measurement.  Returns in out9
+ * (host, 9 doubles; may be NULL), for the task kinds diagonal block,
+ * off-diagonal quad and update tile in that order, the tasks run and the
+ * microseconds (SM clock cycles / the device's clock rate) summed over them
+ * waiting for dependencies and working, since the previous call; then clears
+ * the sums and switches the timing on (enable != 0) or off.  Synchronises the
+ * device. */
+nl_status nl_debug_grouped_task_times(int enable, double* out9);
 
 /* Grouped b[i] <- U^{-1} L^{-1} P b[i] with the factors LU[i] (binary16
  * promoted to single on the fly, eq. (2.16), b single; or double), one CTA

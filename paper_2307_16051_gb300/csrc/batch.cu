@@ -582,11 +582,13 @@ static void batch_free(nl_batch* B)
 
 // The binary16 grouped-LU plan of bucket b for outer block nb and update g
 // (1 SIMT and 2 tcgen05, three launches per outer step; 3 / 4 one persistent
-// launch with 64 x 64 / 128 x 64 SIMT update tiles).
+// launch with 64 x 64 / 128 x 64 SIMT update tiles, 5 one persistent launch
+// with 128 x 128 tcgen05 update tiles).
 static nl_status batch_plan16(nl_batch* B, int b, int nb, int g, GroupPlan* pl)
 {
     const int n = B->bk_count[b];
     const GInst* h = B->bk_hgin[b].data();
+    if (g == 5) return lu_grouped_plan(n, h, nb, 2, false, pl, 1, 128);
     if (g >= 3) return lu_grouped_plan(n, h, nb, 1, false, pl, 1, g == 3 ? 64 : 128);
     return lu_grouped_plan(n, h, nb, g, false, pl);
 }
@@ -696,8 +698,9 @@ static bool tune_write(const char* path, const std::map<std::string, TuneEntry>&
 
 static bool tune_valid(int nb, int g)
 {
-    if (nb < 16 || nb > 128 || nb % 16 || g < 1 || g > 4) return false;
+    if (nb < 16 || nb > 128 || nb % 16 || g < 1 || g > 5) return false;
     if (g == 2) return nb % 64 == 0 && tc_gemm_supported();
+    if (g == 5) return nb == 64 && tc_gemm_supported();
     if (g >= 3) return nb <= 64 && tc_gemm_supported();
     return true;
 }
@@ -707,7 +710,7 @@ static bool tune_valid(int nb, int g)
 // the fastest; a bucket found in the tuning table takes the stored choice.
 static nl_status batch_autotune(nl_batch* B)
 {
-    const int cands[6][2] = {{128, 2}, {64, 2}, {64, 3}, {64, 4}, {32, 3}, {32, 4}};
+    const int cands[7][2] = {{128, 2}, {64, 2}, {64, 5}, {64, 3}, {64, 4}, {32, 3}, {32, 4}};
     const bool tc = tc_gemm_supported();
     const char* path = getenv("NL_LU_TUNE_FILE");
     if (path && !*path) path = nullptr;
@@ -794,7 +797,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         !(d.trsv_cluster == -1 || d.trsv_cluster == 0 || d.trsv_cluster == 4 || d.trsv_cluster == 8 ||
           d.trsv_cluster == 16) ||
         !(d.lu_stream == 0 || d.lu_stream == -1 || d.lu_stream == 256) || d.ir_variant != 0 ||
-        d.trailing_gemm < 0 || d.trailing_gemm > 4 ||
+        d.trailing_gemm < 0 || d.trailing_gemm > 5 ||
         d.gmres_factors32 != 0 || d.lu16_arith != 0 || d.scale_fp16 != 0) {
         set_error("nl_batch_create: invalid configuration");
         return NL_EINVAL;
@@ -1033,6 +1036,7 @@ nl_status nl_batch_create(int count, const int64_t* N, const double* c, const nl
         int g = d.trailing_gemm ? d.trailing_gemm : 2;
         if (g == 2 && (d.lu_nb % 64 || !tc_gemm_supported())) g = 1;
         if (g >= 3 && (d.lu_nb > 64 || !tc_gemm_supported())) g = 1;
+        if (g == 5 && d.lu_nb != 64) g = 1;
         for (int b = 0; b < B->nbk; ++b) {
             B->bk_nb[b] = d.lu_nb;
             B->bk_gemm[b] = g;
@@ -1321,7 +1325,7 @@ static nl_status batch_solve_impl(nl_batch* B, const double* x0, bool x0_host, d
                 // launch's arithmetic is the SIMT update's
                 const int b = B->bk_of[i];
                 cf.lu_nb = B->bk_nb[b];
-                cf.trailing_gemm = B->bk_gemm[b] >= 3 ? 1 : B->bk_gemm[b];
+                cf.trailing_gemm = B->bk_gemm[b] == 5 ? 2 : (B->bk_gemm[b] >= 3 ? 1 : B->bk_gemm[b]);
             }
             cf.newton_maxit = std::max(0, B->cfg.newton_maxit - S.it);
             nl_solver* sv = nullptr;
@@ -1471,7 +1475,7 @@ nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64
                         int fp64, int nb, int gemm, int32_t* flags_host, void* stream)
 {
     set_error("");
-    if (count < 1 || !N || !A || !ld || !ipiv || !flags_host || gemm < 0 || gemm > 4) {
+    if (count < 1 || !N || !A || !ld || !ipiv || !flags_host || gemm < 0 || gemm > 5) {
         set_error("nl_lu_grouped: bad argument");
         return NL_EINVAL;
     }
@@ -1518,7 +1522,8 @@ nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64
         s = NL_ECUDA;
     }
     if (s == NL_OK) {
-        if (gemm >= 3) s = lu_grouped_plan(count, hg.data(), nb, 1, fp64 != 0, &plan, 1, gemm == 3 ? 64 : 128);
+        if (gemm == 5) s = lu_grouped_plan(count, hg.data(), nb, 2, fp64 != 0, &plan, 1, 128);
+        else if (gemm >= 3) s = lu_grouped_plan(count, hg.data(), nb, 1, fp64 != 0, &plan, 1, gemm == 3 ? 64 : 128);
         else s = lu_grouped_plan(count, hg.data(), nb, gemm, fp64 != 0, &plan);
     }
     if (s == NL_OK) s = lu_grouped_factor(plan, dg, st, nullptr);

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace nl {
 
@@ -29,49 +30,7 @@ constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 64;
 constexpr int kTcThreads = 128;
 constexpr long long kTcWaitCycles = 2000000000LL;
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p)
-{
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor for a K-major operand slab written by TMA
-// with 128-byte swizzle: 8-row x 128-byte swizzle atoms stacked every 1024 B.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);      // start address
-    d |= (uint64_t)(16u >> 4) << 16;              // leading-dimension byte offset (unused for this layout)
-    d |= (uint64_t)(1024u >> 4) << 32;            // stride-dimension byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                       // descriptor version for tcgen05
-    d |= (uint64_t)2 << 61;                       // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor: kind::f16, A = B = binary16, D = binary32, both
-// operands K-major, M = 128, N = kTcBN.
-__host__ __device__ constexpr uint32_t tc_idesc()
-{
-    return (1u << 4)                        // D format: f32
-           | (0u << 7) | (0u << 10)         // A, B format: f16
-           | (0u << 15) | (0u << 16)        // A, B K-major
-           | ((uint32_t)(kTcBN >> 3) << 17)  // N / 8
-           | ((uint32_t)(kTcBM >> 4) << 24); // M / 16
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit)
-{
-    long long t0 = clock64();
-    uint32_t done = 0;
-    while (true) {
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(phase)
-            : "memory");
-        if (done) return true;
-        if (clock64() - t0 > limit) return false;
-    }
-}
+__host__ __device__ constexpr uint32_t tc_idesc() { return tc_idesc_mn(kTcBM, kTcBN); }
 
 // One 128 x 128 output tile at (m0, n0) of C (M x Nc).  The A slab kt of the
 // tile is the TMA box at (ax + 64 kt, ay + m0) of tmA, the B slab the box at
@@ -263,19 +222,6 @@ constexpr int kPRing = 4;                  // operand slots, each an A slab and 
 constexpr int kPMaxK = 1024;               // largest K of one update
 
 static size_t p_smem_bytes() { return 1024 + (size_t)kPRing * 2 * kPSlab + kPCBuf * (size_t)kPCBytes + 256; }
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
 
 // Where tile `it` of a persistent CTA reads and writes: the A slabs at
 // (ax + 64 kt, ay) of map a, the B slabs at (64 kt, by) of map b, the C tile's

@@ -104,7 +104,7 @@ struct GroupPlan {
     int count = 0, nb = 128, gemm = 1, steps = 0;
     bool fp64 = false;
     int kind = 0;              // 0: three launches per outer step; 1: one persistent launch (task queue)
-    int tm = 64;               // kind 1: update tile rows (64 or 128; 64 columns)
+    int tm = 64, tn = 64;      // kind 1: update tile (SIMT: tm x 64, tm 64 or 128; tcgen05: 128 x 128)
     std::vector<int> off, n;   // per step and class (3 * steps): offset into tasks and count
     GTask* tasks = nullptr;    // device
     TmapBytes* maps = nullptr; // device: 2 per instance (A and U12^T views), tensor-core update only
@@ -117,7 +117,8 @@ size_t lu_stage_bytes();
 // Builds the plan for the instances (host copy of the device table, which must
 // already hold final pointers).  Allocates the device task and map arrays.
 // kind 1 (one persistent launch over a device task queue) needs the binary16
-// factorisation, the SIMT update (gemm 1) and nb <= 64; tm is its update tile height.
+// factorisation and nb <= 64: gemm 1 SIMT update tiles of tm x 64, gemm 2
+// tcgen05 tiles of 128 x 128 (nb = 64).
 nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, bool fp64, GroupPlan* plan,
                           int kind = 0, int tm = 64);
 void lu_grouped_free(GroupPlan* plan);

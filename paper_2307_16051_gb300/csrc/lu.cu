@@ -30,10 +30,12 @@
 
 #include <algorithm>
 #include <climits>
+#include <queue>
 #include <type_traits>
 
 #include "common.cuh"
 #include "internal.h"
+#include "tcgen05.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -2377,15 +2379,30 @@ __global__ void __launch_bounds__(256) k_gemm_simt_g(const GInst* __restrict__ i
 constexpr int kPgThreads = 512;
 constexpr long long kPgSpin = 1LL << 24;
 
-struct PTask {
-    int inst, kind, step, a, b, n, pad0, pad1;  // kind 0 diag; 1 off-diagonal quad (a first block, b blocks in it,
-                                                // n = 1 row role / 0 column role); 2 update tile (a = m0, b = n0)
+// A queue entry carries its matrix's pointers (one 80-byte record, fetched
+// ahead with cp.async while the previous task runs).
+struct alignas(16) PTask {
+    void* A;
+    int* ipiv;
+    int* flag;
+    void* stage;
+    __half* ut;
+    int ld, N;
+    int inst, kind, step, a, b, n;  // kind 0 diag; 1 off-diagonal quad (a first block, b blocks in it,
+                                    // n = 1 row role / 0 column role); 2 update tile (a = m0, b = n0)
 };
+static_assert(sizeof(PTask) == 80, "queue entries are five 16-byte chunks");
 
-__device__ __forceinline__ bool pg_wait(const int* p, int need, unsigned* err)
+// progress word: the phase reached, with kPgFail once the matrix's flag is set
+// (folded in by the task that completes each phase, so a waiting task learns
+// both from its one acquire load)
+constexpr int kPgFail = 1 << 30;
+
+__device__ __forceinline__ bool pg_wait(const int* p, int need, unsigned* err, int* val)
 {
     long long it = 0;
-    while (ld_acquire_gpu(p) < need) {
+    int v;
+    while (((v = ld_acquire_gpu(p)) & ~kPgFail) < need) {
         if (*(volatile unsigned*)err) return false;
         if (++it > kPgSpin) {
             atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
@@ -2393,7 +2410,28 @@ __device__ __forceinline__ bool pg_wait(const int* p, int need, unsigned* err)
         }
         __nanosleep(64);
     }
+    *val = v;
     return true;
+}
+
+__device__ __forceinline__ int atom_add_acq_rel_gpu(int* p, int v)
+{
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// thread 0: queue entry t (if any) into a shared slot, asynchronously
+__device__ __forceinline__ void pg_fetch(const PTask* tasks, int t, int ntasks, PTask* slot)
+{
+    if (t < ntasks) {
+        const char* src = reinterpret_cast<const char*>(tasks + t);
+        const uint32_t dst = smem_u32(slot);
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * q), "l"(src + 16 * q) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
 // C[m0.., n0..] (TM x 64) <- fl16(C - A B) over K, 512 threads: thread (ty, tx) =
@@ -2450,83 +2488,277 @@ __device__ __forceinline__ void pg_gemm_tile(int M, int Nc, int K, const __half*
         }
 }
 
+constexpr long long kPgTcWait = 2000000000LL;  // cycles: bounded mbarrier waits of the tcgen05 tiles
+
+// One 128 x 128 update tile on the tensor cores (TC kernels): thread 0 loads the
+// 64-wide A slab (L21 rows, through the matrix's tensor map) and B slab (U12^T
+// rows, through its U12^T map) with TMA, issues the four K = 16 tcgen05.mma of
+// the slab into the CTA's 128-column TMEM accumulator and commits them; each of
+// the 16 warps then reads its 32 lanes x 32 columns (warp w: lanes 32 (w % 4),
+// columns 32 (w / 4)) and writes C = fl16(C - acc).  The per-element arithmetic
+// is the trailing-update kernels' (same MMAs in the same order, one
+// subtraction, one rounding).  `uses` counts the tiles issued by this CTA (the
+// mbarrier phases); a wait that gives up marks the CTA dead: its later tiles
+// store nothing and it never touches its barriers again.
+__device__ __forceinline__ void pg_tc_tile(__half* A, int64_t ld, const TmapBytes* __restrict__ maps, int inst, int K, int w,
+                                           int rest, int m0, int n0, bool run, uint32_t tmem, uint32_t& uses,
+                                           uint64_t* tbar, int* dead, float* pgsm, unsigned* err)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t raw = smem_u32(pgsm), base = (raw + 1023u) & ~1023u;
+    const uint32_t sA = base, sB = base + 128 * 128;
+    const uint32_t bl = smem_u32(&tbar[0]), bm = smem_u32(&tbar[1]);
+    const uint32_t ph = uses & 1u;
+    // this CTA's earlier generic writes to the shared region, before the TMA writes into it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    run = run && !*(volatile int*)dead;  // CTA-uniform: written by thread 0 only, read after a barrier
+    if (run && threadIdx.x == 0) {
+        const CUtensorMap* ma = reinterpret_cast<const CUtensorMap*>(&maps[2 * inst]);
+        const CUtensorMap* mb = reinterpret_cast<const CUtensorMap*>(&maps[2 * inst + 1]);
+        asm volatile("fence.proxy.async.global;" ::: "memory");  // the acquired operands, for the async proxy
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bl), "r"(2u * 128 * 128)
+                     : "memory");
+        tma_load_2d(sA, ma, K, K + w + m0, bl);
+        tma_load_2d(sB, mb, 0, n0, bl);
+        if (!mbar_wait(bl, ph, kPgTcWait)) {
+            atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+            *(volatile int*)dead = 1;
+            mbar_wait(bl, ph, kPgTcWait);  // let copies in flight land
+        } else {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            constexpr uint32_t idesc = tc_idesc_mn(128, 128);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const uint64_t ad = sw128_desc(sA + kk * 32), bd = sw128_desc(sB + kk * 32);
+                const uint32_t acc = kk ? 1u : 0u;
+                asm volatile(
+                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bm)
+                         : "memory");
+        }
+    }
+    // the epilogue's C segment does not depend on the MMAs: load it while they run
+    const int q = warp & 3, cg = warp >> 2;
+    const int row = m0 + q * 32 + lane, col0 = n0 + cg * 32;
+    __half* Crow = A + (int64_t)(K + w + min(row, rest - 1)) * ld + K + w;
+    const bool full = run && row < rest && col0 + 32 <= rest;
+    uint4 cpre[4];
+    if (full) {
+        const uint4* p = reinterpret_cast<const uint4*>(Crow + col0);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cpre[v] = p[v];
+    }
+    __syncthreads();
+    bool good = run && !*(volatile int*)dead;  // CTA-uniform (a failed load wait set it)
+    const bool waited = good ? mbar_wait(bm, ph, kPgTcWait) : true;
+    if (__syncthreads_or(!waited)) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+            *(volatile int*)dead = 1;
+            mbar_wait(bm, ph, kPgTcWait);  // let the MMAs in flight finish
+        }
+        good = false;
+    }
+    if (run) uses += 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (good) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cg * 32);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (full) {
+            uint4* p = reinterpret_cast<uint4*>(Crow + col0);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                uint32_t wds[4] = {cpre[v].x, cpre[v].y, cpre[v].z, cpre[v].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    __half2 h2;
+                    memcpy(&h2, &wds[e], 4);
+                    float2 f = __half22float2(h2);
+                    f.x -= __uint_as_float(r[v * 8 + 2 * e]);
+                    f.y -= __uint_as_float(r[v * 8 + 2 * e + 1]);
+                    h2 = __floats2half2_rn(f.x, f.y);
+                    memcpy(&wds[e], &h2, 4);
+                }
+                p[v] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+            }
+        } else if (run && row < rest) {
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                if (col0 + e < rest)
+                    Crow[col0 + e] = __float2half_rn(__half2float(Crow[col0 + e]) - __uint_as_float(r[e]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
 // ctl: [0] the queue's next task, [1 .. count] progress words, [1 + count .. 1 + 2 count)
-// per-matrix task counters (all zero at launch).
-__global__ void __launch_bounds__(kPgThreads, 1) k_lu_grouped_p(const GInst* __restrict__ inst,
-                                                                const PTask* __restrict__ tasks, int ntasks, int nb,
-                                                                int tm, int* __restrict__ ctl, int count,
-                                                                unsigned* __restrict__ err)
+// per-matrix task counters (set by k_pg_init before each launch).  TC: update tiles of
+// 128 x 128 on the tensor cores (nb = 64, U12^T written by the column-role solves,
+// tensor maps in `maps`); otherwise tm x 64 SIMT tiles.  Thread 0 takes the next queue
+// index while it waits for the current task's dependencies and fetches that entry with
+// cp.async while the task runs; a phase is handed on with an acquire-release count and
+// a release store of the progress word.
+template <bool TC>
+__global__ void __launch_bounds__(kPgThreads, 1) k_lu_grouped_p(const PTask* __restrict__ tasks, int ntasks, int nb,
+                                                                int tm, int tn, const TmapBytes* __restrict__ maps,
+                                                                int* __restrict__ ctl, int count,
+                                                                unsigned* __restrict__ err,
+                                                                unsigned long long* __restrict__ tstat)
 {
     extern __shared__ __align__(16) float pgsm[];
-    __shared__ int tix, go;
+    __shared__ PTask qbuf[2];
+    __shared__ int qidx[2], go, dead;
+    __shared__ __align__(8) uint64_t tbar[2];  // TC: operands landed, MMAs done
+    __shared__ uint32_t tslot;
     int* next = ctl;
     int* prog = ctl + 1;
     int* cnt = ctl + 1 + count;
+    uint32_t tmem = 0, uses = 0;
+    if constexpr (TC) {
+        if ((threadIdx.x >> 5) == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                         "r"(128u));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        if (threadIdx.x == 32) {
+            dead = 0;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tbar[0])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tbar[1])));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem = tslot;
+    }
+    if (threadIdx.x == 0) {
+        const int t0 = atomicAdd(next, 1);
+        qidx[0] = t0;
+        pg_fetch(tasks, t0, ntasks, &qbuf[0]);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    int slot = 0;
     for (;;) {
         __syncthreads();
-        if (threadIdx.x == 0) tix = atomicAdd(next, 1);
-        __syncthreads();
-        const int t = tix;
+        const int t = qidx[slot];
         if (t >= ntasks) break;
-        const PTask T = tasks[t];
-        const GInst I = inst[T.inst];
-        const int K = T.step * nb, w = min(nb, I.N - K), rest = I.N - K - w;
-        __half* A = reinterpret_cast<__half*>(I.A);
+        const PTask& T = qbuf[slot];  // stays put while the task runs (the prefetch fills the other slot)
+        const int K = T.step * nb, w = min(nb, T.N - K), rest = T.N - K - w;
+        __half* A = reinterpret_cast<__half*>(T.A);
+        long long c0 = 0, c1 = 0;  // task timing (tstat): start, dependencies met
         if (threadIdx.x == 0) {
-            const bool ok = pg_wait(&prog[T.inst], 3 * T.step + T.kind, err);
-            go = (ok && *(volatile const int*)I.flag == 0) ? 1 : 0;  // one read of the flag for the whole CTA
+            c0 = clock64();
+            const int tnext = atomicAdd(next, 1);  // its latency overlaps the wait below
+            int v = 0;
+            const bool ok = pg_wait(&prog[T.inst], 3 * T.step + T.kind, err, &v);
+            c1 = clock64();
+            go = (ok && !(v & kPgFail)) ? 1 : 0;
+            qidx[slot ^ 1] = tnext;
+            pg_fetch(tasks, tnext, ntasks, &qbuf[slot ^ 1]);  // lands while this task runs
         }
         __syncthreads();
+        int* done_word = nullptr;  // thread 0: the counter this task adds to, and by how much
+        int add = 0, total = 0, phase = 0;
         if (T.kind == 0) {
-            if (go) diag_lu16_body<false, __half>(A, I.ld, K, w, I.ipiv, I.flag, reinterpret_cast<float*>(I.stage));
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                st_release_gpu(&prog[T.inst], rest > 0 ? 3 * T.step + 1 : 3 * T.step + 3);
-            }
+            if (go) diag_lu16_body<false, __half>(A, T.ld, K, w, T.ipiv, T.flag, reinterpret_cast<float*>(T.stage));
+            phase = rest > 0 ? 3 * T.step + 1 : 3 * T.step + 3;
         } else if (T.kind == 1) {
             const int wp = (w + 31) & ~31;
             const int q = threadIdx.x >> 7, b = T.a + q;
             const int fl = (int)(offdiag16_smem(wp) / sizeof(float));
             if (go)
-                offdiag16_body<__half>(A, I.ld, K, w, I.N, T.n ? (1 << 20) : 0, nullptr, 0, I.flag,
-                                       reinterpret_cast<const float*>(I.stage), b, -1, 0, threadIdx.x & 127,
+                offdiag16_body<__half>(A, T.ld, K, w, T.N, T.n ? (1 << 20) : 0, TC ? T.ut : nullptr, nb, T.flag,
+                                       reinterpret_cast<const float*>(T.stage), b, -1, 0, threadIdx.x & 127,
                                        pgsm + q * fl);
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                const int total = 2 * ((rest + kO16Rows - 1) / kO16Rows);
-                if (atomicAdd(&cnt[T.inst], T.b) + T.b == total) {
-                    cnt[T.inst] = 0;
-                    __threadfence();
-                    st_release_gpu(&prog[T.inst], 3 * T.step + 2);
-                }
-            }
+            done_word = &cnt[T.inst];
+            add = T.b;
+            total = 2 * ((rest + kO16Rows - 1) / kO16Rows);
+            phase = 3 * T.step + 2;
         } else {
-            if (go) {
-                const __half* L21 = A + (int64_t)(K + w) * I.ld + K;
-                const __half* U12 = A + (int64_t)K * I.ld + K + w;
-                __half* C = A + (int64_t)(K + w) * I.ld + K + w;
-                if (tm == 128) pg_gemm_tile<128>(rest, rest, w, L21, I.ld, U12, I.ld, C, I.ld, T.a, T.b, pgsm);
-                else pg_gemm_tile<64>(rest, rest, w, L21, I.ld, U12, I.ld, C, I.ld, T.a, T.b, pgsm);
+            if constexpr (TC) {
+                pg_tc_tile(A, T.ld, maps, T.inst, K, w, rest, T.a, T.b, go != 0, tmem, uses, tbar, &dead, pgsm, err);
+            } else if (go) {
+                const __half* L21 = A + (int64_t)(K + w) * T.ld + K;
+                const __half* U12 = A + (int64_t)K * T.ld + K + w;
+                __half* C = A + (int64_t)(K + w) * T.ld + K + w;
+                if (tm == 128) pg_gemm_tile<128>(rest, rest, w, L21, T.ld, U12, T.ld, C, T.ld, T.a, T.b, pgsm);
+                else pg_gemm_tile<64>(rest, rest, w, L21, T.ld, U12, T.ld, C, T.ld, T.a, T.b, pgsm);
             }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                const int total = ((rest + tm - 1) / tm) * ((rest + 63) / 64);
-                if (atomicAdd(&cnt[T.inst], 1) + 1 == total) {
-                    cnt[T.inst] = 0;
-                    __threadfence();
-                    st_release_gpu(&prog[T.inst], 3 * T.step + 3);
-                }
+            done_word = &cnt[T.inst];
+            add = 1;
+            total = ((rest + tm - 1) / tm) * ((rest + tn - 1) / tn);
+            phase = 3 * T.step + 3;
+        }
+        // TC: the off-diagonal solves' generic writes (L21 rows and U12^T, the tiles' TMA
+        // operands) ordered before the TMA reads of them; the diagonal blocks and the
+        // tiles' C are read by generic loads only
+        if constexpr (TC)
+            if (T.kind == 1) asm volatile("fence.proxy.async.global;" ::: "memory");
+        if (threadIdx.x == 0) asm volatile("cp.async.wait_all;" ::: "memory");  // the next entry has landed
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // the CTA's writes are ordered before thread 0's release by the barrier
+            bool last = true;
+            if (done_word) {
+                last = atom_add_acq_rel_gpu(done_word, add) + add == total;
+                if (last) *done_word = 0;
             }
+            if (last) st_release_gpu(&prog[T.inst], phase | (*(volatile const int*)T.flag ? kPgFail : 0));
+            if (tstat) {  // per kind: tasks, cycles waiting for dependencies, cycles working
+                const long long c2 = clock64();
+                atomicAdd(&tstat[3 * T.kind], 1ull);
+                atomicAdd(&tstat[3 * T.kind + 1], (unsigned long long)(c1 - c0));
+                atomicAdd(&tstat[3 * T.kind + 2], (unsigned long long)(c2 - c1));
+            }
+        }
+        slot ^= 1;
+    }
+    if constexpr (TC) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
         }
     }
 }
 
-__global__ void k_zero_ints(int* __restrict__ p, int n)
+// Per-task timing of the persistent launch (off unless switched on): per task
+// kind, the tasks run, the cycles spent waiting for their dependencies and the
+// cycles spent on them (thread 0's clock64 from dependencies met to hand-off).
+__device__ unsigned long long g_pg_tstat[9];
+static std::atomic<bool> g_pg_tstat_on{false};
+
+static unsigned long long* pg_task_stats_ptr()
 {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+    if (!g_pg_tstat_on.load()) return nullptr;
+    void* p = nullptr;
+    return cudaGetSymbolAddress(&p, g_pg_tstat) == cudaSuccess ? static_cast<unsigned long long*>(p) : nullptr;
+}
+
+// Before each launch: the queue counter and task counters zeroed, each progress
+// word 0 with kPgFail for a matrix whose flag is already set (skipped).
+__global__ void k_pg_init(int* __restrict__ ctl, int count, const GInst* __restrict__ inst)
+{
+    for (int i = threadIdx.x; i < 1 + 2 * count; i += blockDim.x) {
+        int v = 0;
+        if (i >= 1 && i <= count && *(volatile const int*)inst[i - 1].flag) v = kPgFail;
+        ctl[i] = v;
+    }
 }
 
 static size_t pg_smem_bytes(int nb)
@@ -2534,59 +2766,171 @@ static size_t pg_smem_bytes(int nb)
     const int wp = (int)round_up(nb, 32);
     size_t b = std::max<size_t>(kDiag16Smem, 4 * offdiag16_smem(wp));
     b = std::max<size_t>(b, (size_t)(16 * (128 + 1) + 16 * 64) * sizeof(float));
+    b = std::max<size_t>(b, 1024 + 2 * 128 * 128);  // the tcgen05 tile's A and B slabs, 1024-byte aligned
     return b;
 }
 
-// The persistent launch's queue: for every outer step, the diagonal tasks, the
-// off-diagonal quads (row role, then column role), then the update tiles,
-// largest matrices first.
-static nl_status lu_grouped_plan_p(int count, const GInst* host_inst, int nb, int tm, GroupPlan* plan)
+// The persistent launch's queue order: a list schedule simulated on the host
+// with a cost model (microseconds per task on one CTA).  `workers` CTAs; the
+// tasks of a matrix's next phase become ready when its current phase is done
+// (diagonal block -> off-diagonal quads -> update tiles -> next diagonal
+// block); a free CTA takes the ready task whose matrix has the most outer
+// steps left (the longest remaining chain), a diagonal block before quads
+// before tiles, then in generation order.  The queue lists the tasks by
+// simulated start, so every task's dependencies come earlier in it, and the
+// long chains of the largest matrices advance while the others fill the gaps.
+static std::vector<PTask> lu_grouped_schedule(int count, const GInst* host_inst, int nb, int tm, int tn, bool tc,
+                                              int workers)
 {
-    int nmax = 0;
-    for (int i = 0; i < count; ++i) nmax = std::max(nmax, host_inst[i].N);
-    std::vector<int> order(count);
-    for (int i = 0; i < count; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return host_inst[a].N > host_inst[b].N; });
-    const int steps = (int)cdiv(nmax, nb);
-    std::vector<PTask> q;
-    for (int k = 0; k < steps; ++k) {
-        const int K = k * nb;
-        for (int i : order)
-            if (host_inst[i].N > K) q.push_back({i, 0, k, 0, 0, 0, 0, 0});
-        for (int role = 1; role >= 0; --role)
-            for (int i : order) {
-                const int rest = host_inst[i].N - K - nb;
-                if (rest <= 0) continue;
-                const int nblk = (int)cdiv(rest, kO16Rows);
-                for (int a = 0; a < nblk; a += 4) q.push_back({i, 1, k, a, std::min(4, nblk - a), role, 0, 0});
-            }
-        for (int i : order) {
-            const int rest = host_inst[i].N - K - nb;
-            if (rest <= 0) continue;
+    struct Ready {
+        int rem, kind;
+        long long seq;
+        PTask t;
+        bool operator<(const Ready& o) const  // max-heap: most steps left, then kind, then earliest
+        {
+            if (rem != o.rem) return rem < o.rem;
+            if (kind != o.kind) return kind > o.kind;
+            return seq > o.seq;
+        }
+    };
+    struct Busy {
+        double end;
+        int inst;
+        bool operator<(const Busy& o) const { return end > o.end; }  // min-heap on finish time
+    };
+    std::vector<int> steps(count), step(count, 0), left(count, 0);
+    std::priority_queue<Ready> ready;
+    std::priority_queue<Busy> busy;
+    long long seq = 0;
+    size_t total = 0;
+    for (int i = 0; i < count; ++i) steps[i] = (int)cdiv(host_inst[i].N, nb);
+    // per-task times measured on a GB300 for w = 64 (clock64 around each task of the
+    // 512-instance workload): diagonal block ~30 us, off-diagonal quad ~25 us, tile
+    // ~6 us (tcgen05 128 x 128), ~15 us (SIMT 128 x 64), ~8 us (SIMT 64 x 64)
+    auto dur = [&](int kind, int w) {
+        const double f = (double)w / 64.0;
+        if (kind == 0) return 0.47 * w;
+        if (kind == 1) return 3.0 + 22.0 * f * f;
+        return tc ? 6.0 : (tm == 128 ? 15.0 : 8.0) * f;
+    };
+    std::vector<double> tdur;  // per generated task, indexed by its seq
+    auto mk = [&](int i, int kind, int k, int a, int b, int n) {
+        const GInst& G = host_inst[i];
+        PTask t;
+        t.A = G.A;
+        t.ipiv = G.ipiv;
+        t.flag = G.flag;
+        t.stage = G.stage;
+        t.ut = G.ut;
+        t.ld = (int)G.ld;
+        t.N = G.N;
+        t.inst = i;
+        t.kind = kind;
+        t.step = k;
+        t.a = a;
+        t.b = b;
+        t.n = n;
+        return t;
+    };
+    // phase `kind` of matrix i's current step becomes ready
+    auto release = [&](int i, int kind) {
+        const int k = step[i], K = k * nb, w = std::min(nb, host_inst[i].N - K), rest = host_inst[i].N - K - w;
+        const int rem = steps[i] - k;
+        auto push = [&](PTask t) {
+            ready.push({rem, kind, seq++, t});
+            tdur.push_back(dur(kind, w));
+            left[i] += 1;
+            total += 1;
+        };
+        if (kind == 0) {
+            push(mk(i, 0, k, 0, 0, 0));
+        } else if (kind == 1) {
+            const int nblk = (int)cdiv(rest, kO16Rows);
+            for (int role = 1; role >= 0; --role)
+                for (int a = 0; a < nblk; a += 4) push(mk(i, 1, k, a, std::min(4, nblk - a), role));
+        } else {
             for (int m0 = 0; m0 < rest; m0 += tm)
-                for (int n0 = 0; n0 < rest; n0 += 64) q.push_back({i, 2, k, m0, n0, 0, 0, 0});
+                for (int n0 = 0; n0 < rest; n0 += tn) push(mk(i, 2, k, m0, n0, 0));
+        }
+    };
+    for (int i = 0; i < count; ++i) release(i, 0);
+    std::vector<PTask> q;
+    double t = 0.0;
+    int idle = std::max(1, workers);
+    while (!ready.empty() || !busy.empty()) {
+        while (idle > 0 && !ready.empty()) {
+            const Ready r = ready.top();
+            ready.pop();
+            q.push_back(r.t);
+            busy.push({t + tdur[(size_t)r.seq], r.t.inst + count * r.t.kind});
+            idle -= 1;
+        }
+        if (busy.empty()) break;
+        const Busy b = busy.top();
+        busy.pop();
+        t = b.end;
+        idle += 1;
+        const int i = b.inst % count, kind = b.inst / count;
+        if (--left[i] > 0) continue;
+        // matrix i's phase `kind` is done
+        const int K = step[i] * nb, rest = host_inst[i].N - K - std::min(nb, host_inst[i].N - K);
+        if (kind == 0) {
+            if (rest > 0) release(i, 1);
+        } else if (kind == 1) {
+            release(i, 2);
+        } else {
+            step[i] += 1;
+            release(i, 0);
         }
     }
+    return q;
+}
+
+// The persistent launch's queue (see lu_grouped_schedule).
+static nl_status lu_grouped_plan_p(int count, const GInst* host_inst, int nb, int gemm, int tm, GroupPlan* plan)
+{
+    const int tn = gemm == 2 ? 128 : 64;
+    if (gemm == 2) tm = 128;
+    int nmax = 0;
+    for (int i = 0; i < count; ++i) nmax = std::max(nmax, host_inst[i].N);
+    const int steps = (int)cdiv(nmax, nb);
+    const int workers = num_sms();
+    std::vector<PTask> q = lu_grouped_schedule(count, host_inst, nb, tm, tn, gemm == 2, workers);
     lu_grouped_free(plan);
     plan->count = count;
     plan->nb = nb;
-    plan->gemm = 1;
+    plan->gemm = gemm;
     plan->steps = steps;
     plan->fp64 = false;
     plan->kind = 1;
     plan->tm = tm;
+    plan->tn = tn;
     plan->off.clear();
     plan->n.clear();
     plan->nptasks = (int)q.size();
     plan->grid = std::max(1, std::min(plan->nptasks, num_sms()));
+    std::vector<TmapBytes> maps;
+    if (gemm == 2) {
+        maps.resize(2 * (size_t)count);
+        for (int i = 0; i < count; ++i)
+            if (host_inst[i].N > nb && !tc_encode_instance_maps(reinterpret_cast<const __half*>(host_inst[i].A),
+                                                                host_inst[i].N, host_inst[i].ld, host_inst[i].ut, nb,
+                                                                &maps[2 * (size_t)i])) {
+                set_error("grouped LU: tensor-map encoding failed for matrix %d", i);
+                return NL_ECUDA;
+            }
+    }
     const size_t qb = q.size() * sizeof(PTask), cb = (size_t)(1 + 2 * count) * sizeof(int);
-    plan->bytes = round_up(qb, 256) + round_up(cb, 256);
+    const size_t mb = maps.size() * sizeof(TmapBytes);
+    plan->bytes = round_up(qb, 256) + round_up(cb, 256) + mb;
     void* p = nullptr;
     NL_CUDA_OK(cudaMalloc(&p, plan->bytes));
     plan->tasks = reinterpret_cast<GTask*>(p);  // the allocation's base (freed through it)
     plan->ptasks = reinterpret_cast<PTask*>(p);
     plan->ctl = reinterpret_cast<int*>((char*)p + round_up(qb, 256));
+    plan->maps = mb ? reinterpret_cast<TmapBytes*>((char*)p + round_up(qb, 256) + round_up(cb, 256)) : nullptr;
     if (qb) NL_CUDA_OK(cudaMemcpy(plan->ptasks, q.data(), qb, cudaMemcpyHostToDevice));
+    if (mb) NL_CUDA_OK(cudaMemcpy(plan->maps, maps.data(), mb, cudaMemcpyHostToDevice));
     return NL_OK;
 }
 
@@ -2598,12 +2942,13 @@ nl_status lu_grouped_plan(int count, const GInst* host_inst, int nb, int gemm, b
         return NL_EINVAL;
     }
     if (kind == 1) {
-        if (fp64 || gemm != 1 || nb > 64 || !(tm == 64 || tm == 128) || !tc_gemm_supported() || !tc_error_word()) {
-            set_error("grouped LU: the persistent launch needs the binary16 LU, the SIMT update, nb <= 64, "
-                      "tile height 64 or 128");
+        if (fp64 || !(gemm == 1 || gemm == 2) || nb > 64 || (gemm == 2 && nb != 64) || !(tm == 64 || tm == 128) ||
+            !tc_gemm_supported() || !tc_error_word()) {
+            set_error("grouped LU: the persistent launch needs the binary16 LU, nb <= 64 (nb = 64 with the "
+                      "tensor-core update), SIMT tile height 64 or 128");
             return NL_EINVAL;
         }
-        return lu_grouped_plan_p(count, host_inst, nb, tm, plan);
+        return lu_grouped_plan_p(count, host_inst, nb, gemm, tm, plan);
     }
     if (kind != 0) {
         set_error("grouped LU: unknown kind %d", kind);
@@ -2693,7 +3038,8 @@ nl_status lu_grouped_setup()
             set_max_dynamic_smem((const void*)k_offdiag16_g) != NL_OK ||
             set_max_dynamic_smem((const void*)k_diag_lu_g<double, double, false>) != NL_OK ||
             set_max_dynamic_smem((const void*)k_offdiag_g<double, double, false>) != NL_OK ||
-            set_max_dynamic_smem((const void*)k_lu_grouped_p) != NL_OK)
+            set_max_dynamic_smem((const void*)k_lu_grouped_p<false>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_lu_grouped_p<true>) != NL_OK)
             return NL_ECUDA;
         smem_set = true;
     }
@@ -2705,10 +3051,17 @@ nl_status lu_grouped_factor(const GroupPlan& plan, const GInst* dev_inst, cudaSt
     NL_TRY(lu_grouped_setup());
     const int nb = plan.nb, wp = (int)round_up(nb, 32);
     if (plan.kind == 1) {
-        k_zero_ints<<<1, 256, 0, st>>>(plan.ctl, 1 + 2 * plan.count);  // a kernel node: legal in conditional bodies
+        k_pg_init<<<1, 256, 0, st>>>(plan.ctl, plan.count, dev_inst);  // a kernel node: legal in conditional bodies
         prof_begin("k_lu_grouped_p", st);
-        k_lu_grouped_p<<<plan.grid, kPgThreads, pg_smem_bytes(nb), st>>>(
-            dev_inst, plan.ptasks, plan.nptasks, nb, plan.tm, plan.ctl, plan.count, tc_error_word());
+        unsigned long long* ts = pg_task_stats_ptr();
+        if (plan.gemm == 2)
+            k_lu_grouped_p<true><<<plan.grid, kPgThreads, pg_smem_bytes(nb), st>>>(
+                plan.ptasks, plan.nptasks, nb, plan.tm, plan.tn, plan.maps, plan.ctl, plan.count, tc_error_word(),
+                ts);
+        else
+            k_lu_grouped_p<false><<<plan.grid, kPgThreads, pg_smem_bytes(nb), st>>>(
+                plan.ptasks, plan.nptasks, nb, plan.tm, plan.tn, nullptr, plan.ctl, plan.count, tc_error_word(),
+                ts);
         prof_end("k_lu_grouped_p", st);
         NL_CUDA_OK(cudaGetLastError());
         if (launches) *launches += 2;
@@ -2783,5 +3136,26 @@ extern "C" nl_status nl_k_div_round16(int64_t n, const float* a, const float* b,
     if (n == 0) return NL_OK;
     k_div_round16<<<(unsigned)cdiv(n, 256), 256, 0, (cudaStream_t)stream>>>(n, a, b, out);
     NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
+extern "C" nl_status nl_debug_grouped_task_times(int enable, double* out9)
+{
+    using namespace nl;
+    unsigned long long v[9] = {};
+    NL_CUDA_OK(cudaDeviceSynchronize());
+    NL_CUDA_OK(cudaMemcpyFromSymbol(v, g_pg_tstat, sizeof(v)));
+    const unsigned long long z[9] = {};
+    NL_CUDA_OK(cudaMemcpyToSymbol(g_pg_tstat, z, sizeof(z)));
+    int dev = 0, khz = 0;
+    NL_CUDA_OK(cudaGetDevice(&dev));
+    NL_CUDA_OK(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+    if (out9)
+        for (int k = 0; k < 3; ++k) {
+            out9[3 * k] = (double)v[3 * k];
+            out9[3 * k + 1] = khz > 0 ? (double)v[3 * k + 1] / (khz * 1e-3) : 0.0;  // cycles -> microseconds
+            out9[3 * k + 2] = khz > 0 ? (double)v[3 * k + 2] / (khz * 1e-3) : 0.0;
+        }
+    g_pg_tstat_on.store(enable != 0);
     return NL_OK;
 }

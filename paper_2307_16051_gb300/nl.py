@@ -146,6 +146,7 @@ SIGNATURES = {
     "nl_server_info": (_int, [_P, ctypes.POINTER(ServerInfo)]),
     "nl_server_destroy": (None, [_P]),
     "nl_lu_grouped": (_int, [_int, _P, _P, _P, _P, _int, _int, _int, _P, _P]),
+    "nl_debug_grouped_task_times": (_int, [_int, _P]),
     "nl_lusolve_grouped": (_int, [_int, _P, _P, _P, _P, _P, _int, _P]),
 }
 
@@ -438,6 +439,19 @@ def linsolve16(N, J32, ld32, LU16, ld16, ipiv, b, u, eta=1e-4, maxit=20, solver=
     check(lib().nl_linsolve16(N, _ptr(J32), ld32, _ptr(LU16), ld16, _ptr(ipiv), _ptr(b), _ptr(u), eta, maxit, solver,
                               m, gtol, gcycles, stats, ctypes.byref(rel), _stream(stream)))
     return dict(iters=stats[0], outer=stats[1], failed=stats[2], converged=stats[3], relres=rel.value)
+
+
+def grouped_task_times(enable=True) -> dict:
+    """Per-task timing of the persistent grouped LU since the previous call
+    (nl_debug_grouped_task_times); then switch it on or off."""
+    out = (ctypes.c_double * 9)()
+    check(lib().nl_debug_grouped_task_times(int(enable), ctypes.cast(out, _P)))
+    res = {}
+    for k, name in enumerate(("diag", "quad", "tile")):
+        n = out[3 * k]
+        res[name] = {"tasks": int(n), "wait_us": out[3 * k + 1] / n if n else 0.0,
+                     "work_us": out[3 * k + 2] / n if n else 0.0}
+    return res
 
 
 def lu_grouped(Ns, As, lds, ipivs, fp64=False, nb=0, gemm=0, stream=None):

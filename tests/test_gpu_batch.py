@@ -120,6 +120,71 @@ def test_lu_grouped_persistent_identical_to_single(nb, gemm):
         assert np.array_equal(LU, LUs), N
 
 
+@pytest.mark.parametrize("ref_kind", ["single", "grouped"])
+def test_lu_grouped_persistent_tcgen05_identical(ref_kind):
+    """The persistent launch with 128 x 128 tcgen05 update tiles (gemm 5,
+    nb = 64): factors and pivots bit for bit those of the single-matrix LU
+    with the tensor-core update at nb = 64, and of the three-launch grouped
+    tcgen05 path."""
+    sizes = SIZES + [1500, 700]
+    mats = [jacobian16(N, 0.5 + 0.049 * k, 700 + k) for k, N in enumerate(sizes)]
+    out, flags = lu_grouped(mats, 64, 5)
+    assert not flags.any()
+    if ref_kind == "grouped":
+        ref, rflags = lu_grouped(mats, 64, 2)
+        assert not rflags.any()
+    for k, (M, (LU, ip)) in enumerate(zip(mats, out)):
+        N = M.shape[0]
+        LUs, ips = lu_single(M, ((N + 63) // 64) * 64, 64, 2) if ref_kind == "single" else ref[k]
+        assert np.array_equal(ip, np.arange(N)) and np.array_equal(ips, ip)
+        assert np.array_equal(LU, LUs), N
+
+
+def test_lu_grouped_persistent_tcgen05_many_matrices_vs_oracle():
+    """Many matrices through the tcgen05 persistent launch: the same pivots as
+    the oracle's elimination (rounding period 64) and the tensor-core update's
+    rule against it: within 8 binary16 roundings (relative to the entry, or to
+    2^-11 of the largest pivot), at least 95% of entries identical."""
+    g = np.random.default_rng(13)
+    Ns = [int(round(math.exp(v))) for v in g.uniform(math.log(20), math.log(900), 40)]
+    mats = [jacobian16(N, float(g.uniform(0.1, 0.999)), 900 + k) for k, N in enumerate(Ns)]
+    out, flags = lu_grouped(mats, 64, 5)
+    assert not flags.any()
+    same = total = 0
+    for M, (LU, ip) in zip(mats, out):
+        LUo, ipo, info, ovf = O.lu16_dev(M, 64)
+        assert info == 0 and not ovf and np.array_equal(ip, ipo)
+        scale = np.maximum(np.abs(LUo), np.abs(np.diag(LUo)).max() * 2.0 ** -11)
+        assert np.max(np.abs(LU - LUo) / scale) <= 8 * 2.0 ** -11
+        same += int(np.sum(LU == LUo))
+        total += LU.size
+    assert same >= 0.95 * total, same / total
+
+
+def test_lu_grouped_persistent_task_times():
+    """nl_debug_grouped_task_times: with timing on, every task of the queue is
+    counted once per kind (diagonal blocks, off-diagonal quads, 128 x 128
+    tiles) with positive work time; with timing off nothing is counted."""
+    Ns = [70, 300, 1000]
+    mats = [jacobian16(N, 0.9, 40 + N) for N in Ns]
+    nl.grouped_task_times(True)
+    lu_grouped(mats, 64, 5)
+    t = nl.grouped_task_times(False)
+    nd = nq = nt = 0
+    for N in Ns:
+        for k in range(-(-N // 64)):
+            nd += 1
+            rest = N - 64 * k - min(64, N - 64 * k)
+            if rest > 0:
+                nq += 2 * (-(-(-(-rest // 128)) // 4))
+                nt += (-(-rest // 128)) ** 2
+    assert (t["diag"]["tasks"], t["quad"]["tasks"], t["tile"]["tasks"]) == (nd, nq, nt)
+    assert all(t[k]["work_us"] > 0 for k in ("diag", "quad", "tile"))
+    lu_grouped(mats, 64, 5)
+    t2 = nl.grouped_task_times(False)
+    assert all(t2[k]["tasks"] == 0 for k in ("diag", "quad", "tile"))
+
+
 def test_lu_grouped_persistent_many_matrices_vs_oracle():
     """Many more queue tasks than CTAs (60 matrices, N log-uniform in
     [20, 900]): every matrix equals the oracle's binary16-storage /
@@ -357,13 +422,14 @@ def test_batch_tuning_table_unreadable_is_ignored(tmp_path, monkeypatch):
     assert len(json.loads(path.read_text())["entries"]) >= 1
 
 
-@pytest.mark.parametrize("gemm", [3, 4])
-def test_batch_persistent_grouped_lu_in_graph_equals_simt(gemm):
+@pytest.mark.parametrize("gemm,ref", [(3, 1), (4, 1), (5, 2)])
+def test_batch_persistent_grouped_lu_in_graph_equals_three_launch(gemm, ref):
     """The persistent grouped-LU launch inside the batch graph (conditional
     WHILE body, buckets side by side): every instance's iterate bit for bit
-    that of the three-launch SIMT grouped LU at the same nb."""
+    that of the three-launch grouped LU with the same update arithmetic
+    (SIMT for 3 / 4, tcgen05 for 5) at the same nb."""
     Ns, cs = small_batch(12, seed=21)
-    with nl.Batch(Ns, cs, lu_nb=64, trailing_gemm=1) as B1:
+    with nl.Batch(Ns, cs, lu_nb=64, trailing_gemm=ref) as B1:
         x1, s1 = B1.solve(tol=1e-10)
     with nl.Batch(Ns, cs, lu_nb=64, trailing_gemm=gemm) as B2:
         x2, s2 = B2.solve(tol=1e-10)
