@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -551,7 +552,8 @@ def main():
             e = {}
             if X64 is not None:
                 x = xdev[c].cpu().numpy()
-                e["err_vs_fp64_oracle"] = float(np.max(np.abs(x - X64[k])) / np.max(np.abs(X64[k])))
+                err = float(np.max(np.abs(x - X64[k])) / np.max(np.abs(X64[k])))
+                e["err_vs_fp64_oracle"] = err if math.isfinite(err) else None  # (a diverged comparison column)
             if mode and GC is not None and f"{c}/{mode}" in GC:
                 n_or, h_or = GC[f"{c}/{mode}"]
                 n = st_by_c[c]["newton_iters"]
@@ -601,10 +603,12 @@ def main():
         stm = {c: f.result() for c, f in futs.items()}
         e1.record()
         torch.cuda.synchronize()
+        err_tp = errors(None, stm)  # the error against the FP64 oracle is stated for every column
         extra["two_precision"][mode] = {
             "ms_per_sweep": e0.elapsed_time(e1),
             "per_c": {str(c): {"status": nl.STATUS_NAMES[s["status"]], "newton": s["newton_iters"],
-                               "final_rel_res": s["hist"][-1], "ms": s["t_total_ms"]} for c, s in stm.items()}}
+                               "final_rel_res": s["hist"][-1], "ms": s["t_total_ms"], **err_tp[str(c)]}
+                      for c, s in stm.items()}}
     def alt_sweep(mode, **cfg):
         """The sweep with other handles (another configuration) on the same streams: one untimed
         pass, one timed."""
