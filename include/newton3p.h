@@ -231,7 +231,9 @@ const char* nl_last_error(void);
  * class timed since the previous call, then starts timing `kernel_class`
  * (NULL or "" stops timing).  Classes: "k_panel16" (streaming panel),
  * "k_diag_lu16", "k_offdiag16" (half-precision LU, two-launch panel),
- * "k_diag_lu", "k_offdiag" (double LU), "k_tc_gemm" (tensor-core trailing
+ * "k_diag_lu", "k_offdiag" (double LU), "k_tc_update32" (the two-level
+ * LU's tensor-core inner updates), "k_lu_grouped_p" (the persistent grouped
+ * LU), "k_tc_gemm" (tensor-core trailing
  * update), "k_invdiag" (diagonal-block inverses), "k_trsv_cl" (cluster
  * triangular solve), "k_trsv_mb" (mailbox triangular solve),
  * "k_lusolve16h" (binary16-arithmetic solve), "k_gemv_residual",
@@ -466,6 +468,17 @@ nl_status nl_lusolve_grouped(int count, const int64_t* N, const void* const* LU,
 /* Kernel-level entry points (device pointers).  These expose each step of */
 /* the hot path on its own, for tests and for callers with their own loop.  */
 /* ----------------------------------------------------------------------- */
+
+/* C <- C - A B on the tensor cores (tcgen05 kind::f16, binary32 accumulation
+ * in tensor memory, one binary32 rounding per entry of C), the two-level
+ * factorisation's inner update on its single-precision shadow (Section 2:
+ * the elimination of J_h with binary16 multipliers and U entries, kept in
+ * binary32 between roundings): C is M x Nc binary32, A is M x K and B is
+ * K x Nc binary32 whose entries are binary16 values (other values are rounded
+ * to binary16 on the way in); row-major device arrays, K <= 128, any M, Nc.
+ * Rows and columns outside M x Nc are not touched. */
+nl_status nl_k_update32(int64_t M, int64_t Nc, int64_t K, const float* A, int64_t lda, const float* B,
+                        int64_t ldb, float* C, int64_t ldc, void* stream);
 
 /* Residual of eq. (3.2) with the fused Newton update (Algorithm 1.1, last two
  * lines):  x_out = x + fnorm_scale * u  (u NULL: x_out = x), then

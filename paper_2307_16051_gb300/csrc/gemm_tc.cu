@@ -19,6 +19,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 
 #include "common.cuh"
 #include "internal.h"
@@ -664,6 +665,204 @@ bool tc_encode_instance_maps(const __half* A, int N, int64_t ld, const __half* u
                      (uint64_t)nb, kTcBK, kTcBN);
 }
 
+// ------------------------------------------ single-precision C update --
+// C <- C - A B for binary32 C and binary32 operands whose values are binary16
+// numbers (the two-level LU's inner updates on its single-precision shadow:
+// multipliers and U entries are rounded to binary16 when they are formed),
+// K <= 128.  One CTA of 256 threads per 128 x 128 tile: the threads convert
+// the operands to binary16 (exact) into 128-byte-swizzled K-major slabs (the
+// layout a TMA load with 128-byte swizzle writes: 16-byte chunk c of row r at
+// (r / 8) * 1024 + (r % 8) * 128 + ((c ^ (r % 8)) * 16)), zero beyond M, N and
+// K; thread 0 issues the ceil(K / 16) tcgen05.mma of kind::f16 into a
+// 128-column TMEM accumulator; each thread then applies C = C - acc to 64
+// entries of one row (its C segment loaded while the MMAs run).  Per entry the K products are summed by the tensor cores and applied
+// with one binary32 rounding (the SIMT update rounds after each product), the
+// tensor-core update's rounding.  The wait is bounded; on timeout the CTA
+// records the error, waits (bounded) for its MMAs, skips the update, and
+// releases its tensor memory.
+constexpr int kUfThreads = 256;
+constexpr uint32_t kUfSlab = 128 * 128;  // bytes: 128 rows x 64 binary16
+static size_t uf_smem_bytes() { return 1024 + 4 * (size_t)kUfSlab + 64; }
+
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk)
+{
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ uint4 pack8_h(const float* v)
+{
+    uint4 u;
+    __half2 h;
+    h = __floats2half2_rn(v[0], v[1]);
+    memcpy(&u.x, &h, 4);
+    h = __floats2half2_rn(v[2], v[3]);
+    memcpy(&u.y, &h, 4);
+    h = __floats2half2_rn(v[4], v[5]);
+    memcpy(&u.z, &h, 4);
+    h = __floats2half2_rn(v[6], v[7]);
+    memcpy(&u.w, &h, 4);
+    return u;
+}
+
+__global__ void __launch_bounds__(kUfThreads) k_tc_update_f32(int M, int Nc, int K, const float* __restrict__ A,
+                                                              int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                                              float* __restrict__ C, int64_t ldc,
+                                                              unsigned* __restrict__ err, const int* __restrict__ flag)
+{
+    if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    uint8_t* basep = smem_raw + (base - raw);
+    const uint32_t sA = base, sB = base + 2 * kUfSlab;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(basep + 4 * kUfSlab);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = (int)blockIdx.y * 128, n0 = (int)blockIdx.x * 128;
+    const int KT = (K + 63) / 64, nq = 8 * KT;  // slabs and 16-byte chunks per row
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(128u));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const bool avec = (lda % 4 == 0) && ((((uintptr_t)A) & 15) == 0);
+#pragma unroll 4
+    for (int idx = tid; idx < 128 * nq; idx += kUfThreads) {
+        const int r = idx / nq, q = idx % nq, k0 = 8 * q, i = m0 + r;
+        float v[8];
+        if (avec && i < M && k0 + 8 <= K) {
+            const float4* p = reinterpret_cast<const float4*>(A + (int64_t)i * lda + k0);
+            const float4 a = __ldg(p), b = __ldg(p + 1);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = (i < M && k0 + e < K) ? __ldg(A + (int64_t)i * lda + k0 + e) : 0.0f;
+        }
+        const uint4 u = pack8_h(v);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sA + (q >> 3) * kUfSlab + sw128_off(r, q & 7)),
+                     "r"(u.x), "r"(u.y), "r"(u.z), "r"(u.w)
+                     : "memory");
+    }
+    // B as N x K (K-major): row n holds column n0 + n of B; consecutive threads read consecutive columns
+#pragma unroll 4
+    for (int idx = tid; idx < 128 * nq; idx += kUfThreads) {
+        const int n = idx & 127, q = idx >> 7, k0 = 8 * q, j = n0 + n;
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (j < Nc && k0 + e < K) ? __ldg(B + (int64_t)(k0 + e) * ldb + j) : 0.0f;
+        const uint4 u = pack8_h(v);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sB + (q >> 3) * kUfSlab + sw128_off(n, q & 7)),
+                     "r"(u.x), "r"(u.y), "r"(u.z), "r"(u.w)
+                     : "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the slabs, for the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot, bar = smem_u32(&bars[0]);
+    if (tid == 0) {
+        const uint32_t idesc = tc_idesc_mn(128, 128);
+        const int ks = (K + 15) / 16;
+        for (int s2 = 0; s2 < ks; ++s2) {
+            const uint32_t off = (uint32_t)(s2 >> 2) * kUfSlab + (uint32_t)(s2 & 3) * 32;
+            const uint64_t ad = sw128_desc(sA + off), bd = sw128_desc(sB + off);
+            const uint32_t acc = s2 ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
+    }
+    // warp w: TMEM lanes (rows) 32 (w % 4) .. +31, columns 64 (w / 4) .. +63.  The C
+    // segment does not depend on the MMAs: load it while they run.
+    const int row = m0 + (warp & 3) * 32 + lane, cbase = (warp >> 2) * 64;
+    float* Crow = C + (int64_t)min(row, M - 1) * ldc + n0 + cbase;
+    const bool cfull = row < M && n0 + cbase + 64 <= Nc && (ldc % 4 == 0) && ((((uintptr_t)Crow) & 15) == 0);
+    float4 cpre[16];
+    if (cfull) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) cpre[q] = reinterpret_cast<const float4*>(Crow)[q];
+    }
+    bool ok = mbar_wait(bar, 0, kTcWaitCycles);
+    if (!ok) {
+        atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
+        mbar_wait(bar, 0, kTcWaitCycles);  // let the MMAs in flight finish
+    }
+    ok = !__syncthreads_or(!ok);  // CTA-uniform: the TMEM loads below are warp-collective
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t r[32];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(cbase + 32 * h);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (cfull) {
+                float4* p4 = reinterpret_cast<float4*>(Crow + 32 * h);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4 x = cpre[8 * h + q];
+                    x.x -= __uint_as_float(r[4 * q]);
+                    x.y -= __uint_as_float(r[4 * q + 1]);
+                    x.z -= __uint_as_float(r[4 * q + 2]);
+                    x.w -= __uint_as_float(r[4 * q + 3]);
+                    p4[q] = x;
+                }
+            } else if (row < M) {
+                const int j0 = n0 + cbase + 32 * h;
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    if (j0 + e < Nc) Crow[32 * h + e] -= __uint_as_float(r[e]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128u));
+    }
+}
+
+nl_status tc_update_f32(int M, int Nc, int K, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                        int64_t ldc, cudaStream_t st, const int* flag)
+{
+    if (M <= 0 || Nc <= 0 || K <= 0) return NL_OK;
+    if (!tc_gemm_supported()) {
+        set_error("tcgen05 update: needs an sm_100-family device");
+        return NL_ECUDA;
+    }
+    if (K > 128) {
+        set_error("tcgen05 update: K must be at most 128");
+        return NL_EINVAL;
+    }
+    static bool smem_set = false;
+    if (!smem_set) {
+        if (set_max_dynamic_smem((const void*)k_tc_update_f32) != NL_OK) return NL_ECUDA;
+        smem_set = true;
+    }
+    const dim3 grid((unsigned)cdiv(Nc, 128), (unsigned)cdiv(M, 128));
+    prof_begin("k_tc_update32", st);
+    k_tc_update_f32<<<grid, kUfThreads, uf_smem_bytes(), st>>>(M, Nc, K, A, lda, B, ldb, C, ldc, g_tc_err, flag);
+    prof_end("k_tc_update32", st);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
+}
+
 nl_status tc_gemm16_grouped(const GInst* inst, const TmapBytes* maps, const GTask* tasks, int ntasks, int K, int w,
                             cudaStream_t st)
 {
@@ -696,3 +895,16 @@ nl_status tc_gemm16_grouped(const GInst* inst, const TmapBytes* maps, const GTas
 unsigned* tc_error_word() { return g_tc_err; }
 
 }  // namespace nl
+
+extern "C" nl_status nl_k_update32(int64_t M, int64_t Nc, int64_t K, const float* A, int64_t lda, const float* B,
+                                   int64_t ldb, float* C, int64_t ldc, void* stream)
+{
+    using namespace nl;
+    set_error("");
+    if (M < 0 || Nc < 0 || K < 0 || K > 128 || M > INT32_MAX || Nc > INT32_MAX ||
+        (M > 0 && Nc > 0 && K > 0 && (!A || !B || !C || lda < K || ldb < Nc || ldc < Nc))) {
+        set_error("nl_k_update32: bad argument (K <= 128, leading dimensions at least the row lengths)");
+        return NL_EINVAL;
+    }
+    return tc_update_f32((int)M, (int)Nc, (int)K, A, lda, B, ldb, C, ldc, (cudaStream_t)stream, nullptr);
+}

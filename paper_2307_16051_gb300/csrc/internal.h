@@ -175,6 +175,10 @@ nl_status launch_gemv_residual_g(const BInst* inst, BState* st, const BTask* tas
 
 // gemm_tc.cu: C = fl16(C - A * Bt^T), A M x K (lda), Bt Nc x K (ldbt), tcgen05 + TMA.
 bool tc_gemm_supported();
+// C <- C - A B on the tensor cores for binary32 C and binary32 operands holding
+// binary16 values (the two-level LU's inner updates), K <= 128, any M, Nc.
+nl_status tc_update_f32(int M, int Nc, int K, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                        int64_t ldc, cudaStream_t st, const int* flag);
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
                            __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile = false);
 

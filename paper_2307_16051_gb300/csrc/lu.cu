@@ -1929,8 +1929,11 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
 //     entries rounded to binary16 as they are formed, U12^T of the columns
 //     right of the outer block written in binary16 for the update below;
 //   * the inner panel's update is applied in single precision, unrounded, to
-//     the rest of the two strips only (one fused multiply-add per term in
-//     increasing k: the oracle's sequence exactly);
+//     the rest of the two strips only: with the SIMT update one fused
+//     multiply-add per term in increasing k (the oracle's sequence exactly);
+//     with the tensor-core update on the tcgen05 kernel for binary32 C (the
+//     operands are binary16 values, so the K products are exact and their
+//     sum is applied with one binary32 rounding);
 //   * the strips go back to A (their entries are now binary16 values), and
 //     the rest of the matrix receives one update of depth W,
 //     A22 <- fl16(A22 - L21 U12), on the tensor cores (K streamed through the
@@ -2024,17 +2027,26 @@ static nl_status lu16_factor_2lvl(int N, __half* A, int64_t ld, int* ipiv, int W
                     ++nl;
                 }
             }
-            // this inner panel's update on the rest of the two strips, unrounded
+            // this inner panel's update on the rest of the two strips, unrounded (single
+            // precision): SIMT fused multiply-adds in order k (the oracle's arithmetic), or
+            // with the tensor-core update the tcgen05 kernel for binary32 C
+            const bool tci = gemm == 2 && tc_gemm_supported();
             const int right = C1 - K - wd;  // strip columns right of the inner panel
             if (rest > 0 && right > 0) {
-                NL_TRY((launch_gemm_simt<float, float>(rest, right, wd, P + (K + wd) * ldp + K, ldp, P + K * ldp + K + wd,
-                                                      ldp, P + (K + wd) * ldp + K + wd, ldp, st, w.flag)));
+                const float* L21 = P + (K + wd) * ldp + K;
+                const float* U12 = P + K * ldp + K + wd;
+                float* C22 = P + (K + wd) * ldp + K + wd;
+                if (tci) NL_TRY(tc_update_f32(rest, right, wd, L21, ldp, U12, ldp, C22, ldp, st, w.flag));
+                else NL_TRY((launch_gemm_simt<float, float>(rest, right, wd, L21, ldp, U12, ldp, C22, ldp, st, w.flag)));
                 ++nl;
             }
             const int below = C1 - K - wd;  // rows of the outer block below the inner panel
             if (far > 0 && below > 0) {
-                NL_TRY((launch_gemm_simt<float, float>(below, far, wd, P + (K + wd) * ldp + K, ldp, P + K * ldp + C1, ldp,
-                                                      P + (K + wd) * ldp + C1, ldp, st, w.flag)));
+                const float* L21 = P + (K + wd) * ldp + K;
+                const float* U12 = P + K * ldp + C1;
+                float* C22 = P + (K + wd) * ldp + C1;
+                if (tci) NL_TRY(tc_update_f32(below, far, wd, L21, ldp, U12, ldp, C22, ldp, st, w.flag));
+                else NL_TRY((launch_gemm_simt<float, float>(below, far, wd, L21, ldp, U12, ldp, C22, ldp, st, w.flag)));
                 ++nl;
             }
         }

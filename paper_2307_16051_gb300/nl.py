@@ -147,6 +147,7 @@ SIGNATURES = {
     "nl_server_destroy": (None, [_P]),
     "nl_lu_grouped": (_int, [_int, _P, _P, _P, _P, _int, _int, _int, _P, _P]),
     "nl_debug_grouped_task_times": (_int, [_int, _P]),
+    "nl_k_update32": (_int, [_i64, _i64, _i64, _P, _i64, _P, _i64, _P, _i64, _P]),
     "nl_lusolve_grouped": (_int, [_int, _P, _P, _P, _P, _P, _int, _P]),
 }
 
@@ -430,6 +431,10 @@ def k_gemv_residual_noalloc(N, A, ld, b, u, r, rnorm, stream=None):
 
 def k_gemm16_update(M, Nc, K, A, lda, B, ldb, C, ldc, gemm=1, stream=None):
     return check(lib().nl_k_gemm16_update(M, Nc, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, gemm, _stream(stream)))
+
+
+def k_update32(M, Nc, K, A, lda, B, ldb, C, ldc, stream=None):
+    return check(lib().nl_k_update32(M, Nc, K, _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, _stream(stream)))
 
 
 def linsolve16(N, J32, ld32, LU16, ld16, ipiv, b, u, eta=1e-4, maxit=20, solver=0, m=30, gtol=1e-4, gcycles=10,

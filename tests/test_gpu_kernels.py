@@ -273,6 +273,57 @@ def test_lu16_zero_column_reports_info():
 
 # ------------------------------------------------------------ GEMM update --
 
+@pytest.mark.parametrize("M,Nc,K", [(128, 128, 128), (300, 200, 128), (129, 1000, 88), (1, 5, 16), (2000, 2100, 128),
+                                    (257, 130, 64), (77, 3000, 1), (4000, 384, 128)])
+def test_update32_tensor_core(M, Nc, K):
+    """nl_k_update32 (the two-level LU's inner update on the tensor cores):
+    C <- C - A B for binary32 C and binary16-valued A, B.  The products are
+    exact, so the result is the exact C - A B up to the tensor cores' binary32
+    summation and one rounding: within (K + 2) 2^-23 (|C| + |A| |B|) of the
+    double-precision value.  Entries outside M x Nc (the leading dimensions'
+    padding) are untouched, and a second call gives the same bits."""
+    g = np.random.default_rng(M * 13 + Nc + K)
+    A = g.uniform(-1, 1, (M, K)).astype(np.float16).astype(np.float32)
+    B = g.uniform(-1, 1, (K, Nc)).astype(np.float16).astype(np.float32)
+    C = g.uniform(-4, 4, (M, Nc)).astype(np.float32)
+    lda, ldb, ldc = K + 5, Nc + 3, Nc + 7  # odd strides: the scalar load paths
+    Ad = torch.full((M, lda), 7.0, device=dev(), dtype=torch.float32)
+    Bd = torch.full((K, ldb), 7.0, device=dev(), dtype=torch.float32)
+    Cd = torch.full((M + 1, ldc), -3.0, device=dev(), dtype=torch.float32)
+    Ad[:, :K] = T(A)
+    Bd[:, :Nc] = T(B)
+    Cd[:M, :Nc] = T(C)
+    C0 = Cd.clone()
+    nl.k_update32(M, Nc, K, Ad, lda, Bd, ldb, Cd, ldc)
+    out = Cd.cpu().numpy()
+    exact = C.astype(np.float64) - A.astype(np.float64) @ B.astype(np.float64)
+    bound = (K + 2) * 2.0 ** -23 * (np.abs(C) + np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64))
+    assert np.all(np.abs(out[:M, :Nc] - exact) <= bound)
+    assert np.array_equal(out[:M, Nc:], C0.cpu().numpy()[:M, Nc:]) and np.all(out[M] == -3.0)
+    Cd2 = C0.clone()
+    nl.k_update32(M, Nc, K, Ad, lda, Bd, ldb, Cd2, ldc)
+    assert np.array_equal(Cd2.cpu().numpy(), out)
+
+
+def test_update32_aligned_strides_match_scalar_paths():
+    """The vector (16-byte) load and store paths give the bits of the scalar
+    ones (the same values in the same order)."""
+    M, Nc, K = 640, 512, 128
+    g = np.random.default_rng(5)
+    A = g.uniform(-1, 1, (M, K)).astype(np.float16).astype(np.float32)
+    B = g.uniform(-1, 1, (K, Nc)).astype(np.float16).astype(np.float32)
+    C = g.uniform(-4, 4, (M, Nc)).astype(np.float32)
+    outs = []
+    for pad in (0, 1):
+        Ad = torch.zeros((M, K + pad), device=dev(), dtype=torch.float32)
+        Bd = torch.zeros((K, Nc + pad), device=dev(), dtype=torch.float32)
+        Cd = torch.zeros((M, Nc + pad), device=dev(), dtype=torch.float32)
+        Ad[:, :K], Bd[:, :Nc], Cd[:, :Nc] = T(A), T(B), T(C)
+        nl.k_update32(M, Nc, K, Ad, K + pad, Bd, Nc + pad, Cd, Nc + pad)
+        outs.append(Cd.cpu().numpy()[:, :Nc])
+    assert np.array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("M,Nc,K", [(64, 64, 64), (300, 200, 128), (129, 1000, 256), (1, 5, 64), (2000, 2100, 128),
                                     (3000, 2900, 64), (700, 900, 512), (300, 129, 1024), (1100, 1300, 384)])
 def test_gemm16_update(M, Nc, K):
