@@ -209,15 +209,18 @@ __global__ void __launch_bounds__(kTrsvThreads) k_trsv(int N, int nblk, const S*
 constexpr int T2 = 128;
 constexpr int kMbThreads = 256;  // 128 rows x 2 halves of 64 columns
 
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p)
+// A published word carries its own readiness (the epoch) and its value, and a
+// consumer reads nothing else the producer wrote, so relaxed GPU-scope accesses
+// suffice (no acquire / release, hence no cache invalidation per poll).
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p)
 {
     unsigned long long v;
-    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v)
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // Bounded poll of one published entry: false once `limit` cycles have passed
@@ -229,7 +232,7 @@ __device__ __forceinline__ bool poll_value(const unsigned long long* p, unsigned
     if (limit < 0) return false;
     long long t0 = clock64();
     for (;;) {
-        unsigned long long w = ld_acquire_u64(p);
+        unsigned long long w = ld_relaxed_u64(p);
         if ((unsigned)(w >> 32) == epoch) {
             *out = __uint_as_float((unsigned)w);
             return true;
@@ -274,17 +277,15 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
         float part = 0.0f;
         const __half* Lrow = LU + (int64_t)min(row, N - 1) * ld;
         const int cnt = LOWER ? b : nblk - 1 - b;
-        for (int s = 0; s < cnt; ++s) {
-            const int c = LOWER ? s : nblk - 1 - s;
-            // prefetch this thread's 64 entries of tile (b, c)
+        // this thread's 64 entries of tile (b, c), loaded one tile ahead of their use
+        auto fetch = [&](int c, __half2* dst) {
             const int cb = c * T2 + h * 64;
-            __half2 lv[32];
             if (row < N && cb + 64 <= N && (((uintptr_t)(Lrow + cb)) & 15) == 0) {
                 const uint4* p4 = reinterpret_cast<const uint4*>(Lrow + cb);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
-                    uint4 u = p4[q];
-                    memcpy(&lv[4 * q], &u, 16);
+                    uint4 u = __ldcs(p4 + q);  // streamed once: do not keep it in the caches
+                    memcpy(&dst[4 * q], &u, 16);
                 }
             } else {
 #pragma unroll
@@ -292,9 +293,15 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
                     int c0 = cb + 2 * q;
                     float a0 = (row < N && c0 < N) ? __half2float(Lrow[c0]) : 0.0f;
                     float a1 = (row < N && c0 + 1 < N) ? __half2float(Lrow[c0 + 1]) : 0.0f;
-                    lv[q] = __floats2half2_rn(a0, a1);
+                    dst[q] = __floats2half2_rn(a0, a1);
                 }
             }
+        };
+        __half2 lv[32], nx[32];
+        if (cnt > 0) fetch(LOWER ? 0 : nblk - 1, lv);
+        for (int s = 0; s < cnt; ++s) {
+            const int c = LOWER ? s : nblk - 1 - s;
+            if (s + 1 < cnt) fetch(LOWER ? s + 1 : nblk - 2 - s, nx);
             __syncthreads();  // ys of the previous tile no longer in use
             bool okp = true;
             if (tid < T2) {
@@ -313,6 +320,8 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
                 part = fmaf(f.x, ys[h * 64 + 2 * q], part);
                 part = fmaf(f.y, ys[h * 64 + 2 * q + 1], part);
             }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) lv[q] = nx[q];
         }
         part += __shfl_xor_sync(0xffffffffu, part, 1);
         __syncthreads();
@@ -324,7 +333,7 @@ __global__ void __launch_bounds__(kMbThreads) k_trsv_mb(int N, int nblk, const _
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);
         if (h == 0 && row < N) {
             if (out) out[row] = sum;
-            st_release_u64(mb + row, ((unsigned long long)epoch << 32) | __float_as_uint(sum));
+            st_relaxed_u64(mb + row, ((unsigned long long)epoch << 32) | __float_as_uint(sum));
         }
     }
 }
