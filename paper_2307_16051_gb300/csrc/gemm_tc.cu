@@ -742,10 +742,8 @@ __global__ void __launch_bounds__(kUfThreads) k_tc_update_f32(int M, int Nc, int
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[e] = (i < M && k0 + e < K) ? __ldg(A + (int64_t)i * lda + k0 + e) : 0.0f;
         }
-        const uint4 u = pack8_h(v);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sA + (q >> 3) * kUfSlab + sw128_off(r, q & 7)),
-                     "r"(u.x), "r"(u.y), "r"(u.z), "r"(u.w)
-                     : "memory");
+        // a plain shared store (no asm barrier), so the loads of later chunks can be issued ahead
+        *reinterpret_cast<uint4*>(basep + (q >> 3) * kUfSlab + sw128_off(r, q & 7)) = pack8_h(v);
     }
     // B as N x K (K-major): row n holds column n0 + n of B; consecutive threads read consecutive columns
 #pragma unroll 4
@@ -754,10 +752,7 @@ __global__ void __launch_bounds__(kUfThreads) k_tc_update_f32(int M, int Nc, int
         float v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) v[e] = (j < Nc && k0 + e < K) ? __ldg(B + (int64_t)(k0 + e) * ldb + j) : 0.0f;
-        const uint4 u = pack8_h(v);
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(sB + (q >> 3) * kUfSlab + sw128_off(n, q & 7)),
-                     "r"(u.x), "r"(u.y), "r"(u.z), "r"(u.w)
-                     : "memory");
+        *reinterpret_cast<uint4*>(basep + 2 * kUfSlab + (q >> 3) * kUfSlab + sw128_off(n, q & 7)) = pack8_h(v);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // the slabs, for the tensor cores
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -45,7 +45,9 @@ nl_status launch_jacobian64(int N, double c, const double* rr, const double* hta
 struct LuWork {
     void* pnl = nullptr;      // outer-panel working copy: N x NB (float for fp16 LU, double for fp64 LU)
     __half* ut = nullptr;     // U12^T for the tensor-core trailing update: N x NB binary16
-    int* info = nullptr;      // device int: first zero pivot (1-based), 0 if none
+    int* info = nullptr;      // device int: first zero pivot (1-based), 0 if none; the 256-byte info block
+                              // also holds the flag (+1), an error word (+2), the binary16-arithmetic LU's
+                              // barrier (+4, +5) and the streaming panel's role ticket (bytes 32..39)
     int* flag = nullptr;      // device int (info + 1): set when the no-interchange fast path failed
     void* stage = nullptr;    // diagonal-block factors staged for the off-diagonal solves (<= 256 KB)
     unsigned long long* pub = nullptr;  // 128 x 128 {epoch, value} words: columns published by k_panel16

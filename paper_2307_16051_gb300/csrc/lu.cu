@@ -1082,9 +1082,9 @@ __global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(S* __restrict__ A,
 }
 
 // k_panel16: the diagonal block and the off-diagonal solves of one panel in
-// one cooperative launch.  CTA 0 factors the diagonal block (the column
-// pipeline above) and publishes every finished column t as {epoch, value}
-// words; the other CTAs stream behind it, one step per published column:
+// one launch.  One CTA factors the diagonal block (the column pipeline above)
+// and publishes every finished column t as {epoch, value} words; the other
+// CTAs stream behind it, one step per published column:
 //   row CTAs (256 rows of L21 each): row i at step t forms
 //     x_it - sum_{k<t} l_ik u_kt (the sum in increasing k, one fused
 //     multiply-add per term) from its own multipliers and U's column t, checks
@@ -1100,7 +1100,8 @@ __global__ void __launch_bounds__(kD16Threads, 1) k_diag_lu16(S* __restrict__ A,
 // launch and the buffer is cleared before each factorisation), so the
 // producer needs no fence.  Each CTA keeps its rows' (columns') 128 values in
 // shared memory; every wait is bounded and also gives up when the fast path
-// has been abandoned.  The launch is cooperative: all CTAs are co-resident.
+// has been abandoned.  The CTAs' roles follow the order they start in (see
+// k_panel16), so no co-residency is needed.
 constexpr int kPnlThreads = 512;
 constexpr int kPnlRows = 256;   // at most this many rows (columns) per streaming CTA: one thread each
 constexpr int kPnlFetchW = 14;  // warps 14 and 15 fetch the published columns (even / odd t)
@@ -1327,22 +1328,49 @@ __device__ __forceinline__ void panel16_stream(S* __restrict__ A, int64_t lda, i
 // S: the storage the panel is read from and written to: the binary16 matrix,
 // or (two-level LU) its single-precision shadow over the current outer block.
 // Ut: U12^T in binary16 for the columns from ut_col0 (at K offset ut_k0).
+// Roles are handed out in the order the CTAs start (a ticket word {epoch,
+// count}, reset by the first CTA of each launch): ticket 0 factors the
+// diagonal block and publishes its columns, tickets 1..nrb stream rows, the
+// rest stream columns.  A CTA only ever waits on the diagonal CTA, which took
+// its ticket before any waiting CTA existed and so is running: the launch
+// needs no co-residency, and its CTAs may run in several waves (the later ones
+// find every column already published).
 template <typename S>
 __global__ void __launch_bounds__(kPnlThreads, 1) k_panel16(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                            int nrb, int rpc, int* __restrict__ ipiv, int* __restrict__ flag,
                                                            float* __restrict__ stage, __half* __restrict__ Ut,
                                                            int ldut, int ut_col0, int ut_k0,
                                                            unsigned long long* __restrict__ pub, unsigned epoch,
-                                                           unsigned* __restrict__ err)
+                                                           unsigned* __restrict__ err,
+                                                           unsigned long long* __restrict__ ticket)
 {
-    if (blockIdx.x == 0)
+    __shared__ int role;
+    if (threadIdx.x == 0) {
+        unsigned long long old = *(volatile unsigned long long*)ticket;
+        int t = 0;
+        for (;;) {
+            unsigned long long want;
+            if ((unsigned)(old >> 32) != epoch) {
+                want = ((unsigned long long)epoch << 32) | 1ull;  // the launch's first CTA
+                t = 0;
+            } else {
+                t = (int)(unsigned)old;
+                want = old + 1ull;
+            }
+            const unsigned long long prev = atomicCAS(ticket, old, want);
+            if (prev == old) break;
+            old = prev;
+        }
+        role = t;
+    }
+    __syncthreads();
+    const int r = role;
+    if (r == 0)
         diag_lu16_body<true, S>(A, lda, K, w, ipiv, flag, stage, pub, epoch);
-    else if ((int)blockIdx.x <= nrb)
-        panel16_stream<true, S>(A, lda, K, w, N, (int)blockIdx.x - 1, rpc, Ut, ldut, ut_col0, ut_k0, flag, pub, epoch,
-                                err);
+    else if (r <= nrb)
+        panel16_stream<true, S>(A, lda, K, w, N, r - 1, rpc, Ut, ldut, ut_col0, ut_k0, flag, pub, epoch, err);
     else
-        panel16_stream<false, S>(A, lda, K, w, N, (int)blockIdx.x - 1 - nrb, rpc, Ut, ldut, ut_col0, ut_k0, flag, pub,
-                                 epoch, err);
+        panel16_stream<false, S>(A, lda, K, w, N, r - 1 - nrb, rpc, Ut, ldut, ut_col0, ut_k0, flag, pub, epoch, err);
 }
 
 // k_offdiag16: L21 = A21 U11^{-1} (row role) and U12 = L11^{-1} A12 (column
@@ -1742,8 +1770,9 @@ static nl_status trailing_update(int N, S* A, int64_t ld, int K, int wd, int nb,
 }
 
 // The streaming panel (k_panel16): one CTA for the diagonal block plus
-// ceil(rest / 256) CTAs for the rows of L21 and as many for the columns of
-// U12, all co-resident (cooperative launch); otherwise the two-launch path.
+// ceil(rest / rpc) CTAs for the rows of L21 and as many for the columns of
+// U12 (rpc = 128 while they all fit on the device at once, else 256), when
+// they fit in one wave; otherwise the two-launch path.
 static int panel16_max_ctas()
 {
     // computed once; concurrent first callers compute the same value (never a transient 0)
@@ -1751,10 +1780,9 @@ static int panel16_max_ctas()
     int c = cap.load(std::memory_order_acquire);
     if (c < 0) {
         c = 0;
-        int dev = 0, nsm = 0, coop = 0, per = 0;
+        int dev = 0, nsm = 0, per = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
-            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop &&
             set_max_dynamic_smem((const void*)k_panel16<__half>) == NL_OK &&
             set_max_dynamic_smem((const void*)k_panel16<float>) == NL_OK &&
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_panel16<__half>, kPnlThreads, kPnlSmem) == cudaSuccess)
@@ -1771,6 +1799,9 @@ static int panel16_max_ctas()
 // (two launches instead).
 static int panel16_rows_per_cta(int rest, int pref = 0)
 {
+    // 128 rows per CTA while every CTA fits at once (more CTAs in the chain's shadow), else
+    // 256; beyond what fits in one wave the two launches are faster (measured on GB300 at
+    // N = 32768: 173 us per streamed panel in two waves against 150 us for the two launches)
     const int cap = panel16_max_ctas();
     for (int rpc : {pref == kPnlRows ? kPnlRows : 128, kPnlRows})
         if (1 + 2 * (int)cdiv(rest, rpc) <= cap) return rpc;
@@ -1794,16 +1825,12 @@ static nl_status launch_panel16(S* A, int64_t ld, int K, int wd, int N, int* ipi
     unsigned long long* pub = w.pub;
     unsigned* err = tc_error_word();
     if (!err) err = (unsigned*)(w.info + 2);  // (a word of the info block nobody else uses)
-    int Kv = K, wv = wd, Nv = N, ldutv = ldut, uc0 = ut_col0, uk0 = ut_k0;
-    int64_t ldv = ld;
-    void* args[] = {(void*)&A,     (void*)&ldv,  (void*)&Kv,    (void*)&wv,   (void*)&Nv,  (void*)&nrb,
-                    (void*)&rpc,   (void*)&ipiv, (void*)&flag,  (void*)&stage, (void*)&Ut, (void*)&ldutv,
-                    (void*)&uc0,   (void*)&uk0,  (void*)&pub,   (void*)&epoch, (void*)&err};
+    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(w.info + 8);  // bytes 32..39 of the info block
     prof_begin("k_panel16", st);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_panel16<S>, dim3(1 + 2 * nrb), dim3(kPnlThreads), args,
-                                                kPnlSmem, st);
+    k_panel16<S><<<1 + 2 * nrb, kPnlThreads, kPnlSmem, st>>>(A, ld, K, wd, N, nrb, rpc, ipiv, flag, stage, Ut, ldut,
+                                                            ut_col0, ut_k0, pub, epoch, err, ticket);
     prof_end("k_panel16", st);
-    NL_CUDA_OK(e);
+    NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
 }
 
@@ -1814,7 +1841,7 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
     T* P = (T*)w.pnl;
     const int ldp = nb;
     int nl = 0;
-    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st));  // info and flag
+    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 10 * sizeof(int), st));  // info, flag, ..., the panel's role ticket
     constexpr bool kHalf = std::is_same<S, __half>::value;
     static bool smem_set = false;
     if (!smem_set) {
@@ -1991,7 +2018,7 @@ static nl_status lu16_factor_2lvl(int N, __half* A, int64_t ld, int* ipiv, int W
         return NL_EINVAL;
     }
     int nl = 0;
-    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 2 * sizeof(int), st));
+    NL_CUDA_OK(cudaMemsetAsync(w.info, 0, 10 * sizeof(int), st));  // info, flag, ..., the panel's role ticket
     NL_CUDA_OK(cudaMemsetAsync(w.pub, 0, (size_t)128 * 128 * 8, st));
     static bool smem_set = false;
     if (!smem_set) {
