@@ -47,7 +47,7 @@ struct LuWork {
     __half* ut = nullptr;     // U12^T for the tensor-core trailing update: N x NB binary16
     int* info = nullptr;      // device int: first zero pivot (1-based), 0 if none; the 256-byte info block
                               // also holds the flag (+1), an error word (+2), the binary16-arithmetic LU's
-                              // barrier (+4, +5) and the streaming panel's role ticket (bytes 32..39)
+                              // barrier (+4, +5) and the streaming panel's two role counters (+8, +9)
     int* flag = nullptr;      // device int (info + 1): set when the no-interchange fast path failed
     void* stage = nullptr;    // diagonal-block factors staged for the off-diagonal solves (<= 256 KB)
     unsigned long long* pub = nullptr;  // 128 x 128 {epoch, value} words: columns published by k_panel16

@@ -1328,39 +1328,27 @@ __device__ __forceinline__ void panel16_stream(S* __restrict__ A, int64_t lda, i
 // S: the storage the panel is read from and written to: the binary16 matrix,
 // or (two-level LU) its single-precision shadow over the current outer block.
 // Ut: U12^T in binary16 for the columns from ut_col0 (at K offset ut_k0).
-// Roles are handed out in the order the CTAs start (a ticket word {epoch,
-// count}, reset by the first CTA of each launch): ticket 0 factors the
-// diagonal block and publishes its columns, tickets 1..nrb stream rows, the
-// rest stream columns.  A CTA only ever waits on the diagonal CTA, which took
-// its ticket before any waiting CTA existed and so is running: the launch
-// needs no co-residency, and its CTAs may run in several waves (the later ones
-// find every column already published).
+// Roles are handed out in the order the CTAs start (an atomic ticket; panel p
+// of a factorisation counts in word p % 2, its first CTA clears the other word
+// and its last one its own; both are cleared when the factorisation starts): ticket 0
+// factors the diagonal block and publishes its columns, tickets 1..nrb stream
+// rows, the rest stream columns.  A CTA only ever waits on the diagonal CTA,
+// which took its ticket before any waiting CTA existed and so is running: the
+// launch needs no co-residency.
 template <typename S>
 __global__ void __launch_bounds__(kPnlThreads, 1) k_panel16(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                            int nrb, int rpc, int* __restrict__ ipiv, int* __restrict__ flag,
                                                            float* __restrict__ stage, __half* __restrict__ Ut,
                                                            int ldut, int ut_col0, int ut_k0,
                                                            unsigned long long* __restrict__ pub, unsigned epoch,
-                                                           unsigned* __restrict__ err,
-                                                           unsigned long long* __restrict__ ticket)
+                                                           unsigned* __restrict__ err, int* __restrict__ tickets,
+                                                           int slot)
 {
     __shared__ int role;
     if (threadIdx.x == 0) {
-        unsigned long long old = *(volatile unsigned long long*)ticket;
-        int t = 0;
-        for (;;) {
-            unsigned long long want;
-            if ((unsigned)(old >> 32) != epoch) {
-                want = ((unsigned long long)epoch << 32) | 1ull;  // the launch's first CTA
-                t = 0;
-            } else {
-                t = (int)(unsigned)old;
-                want = old + 1ull;
-            }
-            const unsigned long long prev = atomicCAS(ticket, old, want);
-            if (prev == old) break;
-            old = prev;
-        }
+        const int t = atomicAdd(&tickets[slot], 1);
+        if (t == 0) tickets[slot ^ 1] = 0;                // for the next panel (launched after this one ends)
+        if (t == (int)gridDim.x - 1) tickets[slot] = 0;  // every ticket is taken: this launch's word is free
         role = t;
     }
     __syncthreads();
@@ -1390,9 +1378,14 @@ __global__ void __launch_bounds__(kPnlThreads, 1) k_panel16(S* __restrict__ A, i
 constexpr int kO16Threads = 128;
 constexpr int kO16Rows = 128;  // rows or columns per CTA
 
-__host__ __device__ size_t offdiag16_smem(int wp) { return ((size_t)wp * wp + (size_t)wp * kO16Rows + 2 * wp) * sizeof(float); }
+// R: rows (columns) per CTA, one thread each: 128, or 256 for wide launches of
+// 128-column panels (twice the warps per SM at one CTA per SM)
+__host__ __device__ size_t offdiag16_smem(int wp, int R = kO16Rows)
+{
+    return ((size_t)wp * wp + (size_t)wp * R + 2 * wp) * sizeof(float);
+}
 
-template <typename S = __half>
+template <typename S = __half, int ROWS = kO16Rows>
 __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                int nrow_blocks, __half* __restrict__ Ut, int ldut,
                                                int* __restrict__ flag, const float* stage, int bid,
@@ -1406,8 +1399,8 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
     // tid_in / smem: a group of 128 threads of a larger CTA and its own shared region (the
     // persistent grouped factorisation runs four such groups side by side)
     float* D = smem ? smem : osm;    // U11 (row role) or L11^T (column role), wp x wp
-    float* X = D + wp * wp;          // X[t * kO16Rows + tid]: this thread's multipliers / U entries
-    float* pv = X + wp * kO16Rows;   // |a_tt|, unrounded
+    float* X = D + wp * wp;          // X[t * ROWS + tid]: this thread's multipliers / U entries
+    float* pv = X + wp * ROWS;          // |a_tt|, unrounded
     float* rinv = pv + wp;           // 1 / u_tt, correctly rounded
     const int tid = tid_in >= 0 ? tid_in : (int)threadIdx.x;
     const bool row_role = bid < nrow_blocks;
@@ -1416,13 +1409,13 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
         float4* d4 = reinterpret_cast<float4*>(D);
         const int nv = wp * wp / 4;
 #pragma unroll 4
-        for (int v = tid; v < nv; v += kO16Threads) d4[v] = s4[v];
+        for (int v = tid; v < nv; v += ROWS) d4[v] = s4[v];
         if (tid < wp) pv[tid] = fabsf(stage[kStagePivOff + tid]);
     }
     __syncthreads();
     if (row_role && tid < wp) rinv[tid] = __frcp_rn(D[tid * wp + tid]);
     __syncthreads();
-    const int idx = K + w + (row_role ? bid : bid - nrow_blocks) * kO16Rows + tid;
+    const int idx = K + w + (row_role ? bid : bid - nrow_blocks) * ROWS + tid;
     const bool live = idx < N;
     float* Xt = X + tid;
     if (row_role) {
@@ -1441,7 +1434,7 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
             }
 #pragma unroll 8
             for (int t = 0; t < j0; ++t) {
-                const float l = Xt[t * kO16Rows];
+                const float l = Xt[t * ROWS];
                 const float4* Dt = reinterpret_cast<const float4*>(D + t * wp + j0);
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
@@ -1465,7 +1458,7 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
             // the chunk's multipliers for the later chunks (no shared-memory stores inside
             // the solve, so the loads of U11 can move ahead of the division chain)
 #pragma unroll
-            for (int tt = 0; tt < 32; ++tt) Xt[(j0 + tt) * kO16Rows] = x[tt];
+            for (int tt = 0; tt < 32; ++tt) Xt[(j0 + tt) * ROWS] = x[tt];
             if (live) {
                 if (vec) {
 #pragma unroll
@@ -1488,7 +1481,7 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
                 x[k] = (live && k0 + k < w) ? ld_elem(A + (int64_t)(K + k0 + k) * lda + col) : 0.0f;
 #pragma unroll 8
             for (int t = 0; t < k0; ++t) {
-                const float u = Xt[t * kO16Rows];
+                const float u = Xt[t * ROWS];
                 const float4* Dt = reinterpret_cast<const float4*>(D + t * wp + k0);  // L[k0 + k][t]
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
@@ -1509,7 +1502,7 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
                 for (int k = tt + 1; k < 32; ++k) x[k] = fmaf(-Dt[k], u, x[k]);
             }
 #pragma unroll
-            for (int tt = 0; tt < 32; ++tt) Xt[(k0 + tt) * kO16Rows] = x[tt];
+            for (int tt = 0; tt < 32; ++tt) Xt[(k0 + tt) * ROWS] = x[tt];
             if (live) {
 #pragma unroll
                 for (int k = 0; k < 32; ++k)
@@ -1536,13 +1529,38 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
     }
 }
 
-template <typename S>
-__global__ void __launch_bounds__(kO16Threads) k_offdiag16(S* __restrict__ A, int64_t lda, int K, int w, int N,
-                                                           int nrow_blocks, __half* __restrict__ Ut, int ldut,
-                                                           int* __restrict__ flag, const float* __restrict__ stage,
-                                                           int ut_col0, int ut_k0)
+template <typename S, int ROWS = kO16Rows>
+__global__ void __launch_bounds__(ROWS) k_offdiag16(S* __restrict__ A, int64_t lda, int K, int w, int N,
+                                                 int nrow_blocks, __half* __restrict__ Ut, int ldut,
+                                                 int* __restrict__ flag, const float* __restrict__ stage,
+                                                 int ut_col0, int ut_k0)
 {
-    offdiag16_body<S>(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x, ut_col0, ut_k0);
+    offdiag16_body<S, ROWS>(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x, ut_col0, ut_k0);
+}
+
+// The off-diagonal solves of one panel: 128 rows (columns) per CTA, or 256 for a
+// panel of 128 columns whose 128-row CTAs would not all fit at once (one CTA per
+// SM either way at that width, so twice the warps per SM).  Bitwise the same
+// results: every row (column) is solved by one thread in the same order.
+template <typename S>
+static nl_status launch_offdiag16(S* A, int64_t ld, int K, int wd, int N, __half* ut, int ldut, int* flag,
+                                  const float* stage, int ut_col0, int ut_k0, cudaStream_t st)
+{
+    const int rest = N - K - wd, wp = (int)round_up(wd, 32);
+    const bool wide = wp > 64 && 2 * (int)cdiv(rest, kO16Rows) > num_sms();
+    prof_begin("k_offdiag16", st);
+    if (wide) {
+        const int nrb = (int)cdiv(rest, 256);
+        k_offdiag16<S, 256><<<2 * nrb, 256, offdiag16_smem(wp, 256), st>>>(A, ld, K, wd, N, nrb, ut, ldut, flag, stage,
+                                                                         ut_col0, ut_k0);
+    } else {
+        const int nrb = (int)cdiv(rest, kO16Rows);
+        k_offdiag16<S><<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(A, ld, K, wd, N, nrb, ut, ldut, flag, stage,
+                                                                        ut_col0, ut_k0);
+    }
+    prof_end("k_offdiag16", st);
+    NL_CUDA_OK(cudaGetLastError());
+    return NL_OK;
 }
 
 // C <- C - A B with per-element sequential fused multiply-adds over k in
@@ -1812,7 +1830,7 @@ static std::atomic<unsigned> g_panel_epoch{0};
 
 template <typename S>
 static nl_status launch_panel16(S* A, int64_t ld, int K, int wd, int N, int* ipiv, const LuWork& w, __half* Ut,
-                                int ldut, cudaStream_t st, int ut_col0 = -1, int ut_k0 = 0)
+                                int ldut, cudaStream_t st, int slot, int ut_col0 = -1, int ut_k0 = 0)
 {
     if (ut_col0 < 0) ut_col0 = K + wd;
     const int rest = N - K - wd;
@@ -1825,10 +1843,10 @@ static nl_status launch_panel16(S* A, int64_t ld, int K, int wd, int N, int* ipi
     unsigned long long* pub = w.pub;
     unsigned* err = tc_error_word();
     if (!err) err = (unsigned*)(w.info + 2);  // (a word of the info block nobody else uses)
-    unsigned long long* ticket = reinterpret_cast<unsigned long long*>(w.info + 8);  // bytes 32..39 of the info block
+    int* tickets = w.info + 8;  // two counters (+8, +9) of the info block; slot: the panel's index mod 2
     prof_begin("k_panel16", st);
     k_panel16<S><<<1 + 2 * nrb, kPnlThreads, kPnlSmem, st>>>(A, ld, K, wd, N, nrb, rpc, ipiv, flag, stage, Ut, ldut,
-                                                            ut_col0, ut_k0, pub, epoch, err, ticket);
+                                                            ut_col0, ut_k0, pub, epoch, err, tickets, slot);
     prof_end("k_panel16", st);
     NL_CUDA_OK(cudaGetLastError());
     return NL_OK;
@@ -1849,6 +1867,8 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         if constexpr (kHalf) {
             if (set_max_dynamic_smem((const void*)k_offdiag16<__half>) != NL_OK ||
                 set_max_dynamic_smem((const void*)k_offdiag16<float>) != NL_OK ||
+                set_max_dynamic_smem((const void*)k_offdiag16<__half, 256>) != NL_OK ||
+                set_max_dynamic_smem((const void*)k_offdiag16<float, 256>) != NL_OK ||
                 set_max_dynamic_smem((const void*)k_diag_lu16<__half>) != NL_OK ||
                 set_max_dynamic_smem((const void*)k_diag_lu16<float>) != NL_OK)
                 return NL_ECUDA;
@@ -1873,7 +1893,7 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
                         NL_CUDA_OK(cudaMemsetAsync(w.pub, 0, (size_t)128 * 128 * 8, st));
                         pub_cleared = true;
                     }
-                    NL_TRY(launch_panel16(A, ld, K, wd, N, ipiv, w, tc ? w.ut : nullptr, nb, st));
+                    NL_TRY(launch_panel16(A, ld, K, wd, N, ipiv, w, tc ? w.ut : nullptr, nb, st, (K / nb) & 1));
                     nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
                     if (s != NL_OK) return s;
                     nl += 2;
@@ -1891,11 +1911,8 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
             ++nl;
             if (rest > 0) {
                 if constexpr (kHalf) {
-                    const int nrb = (int)cdiv(rest, kO16Rows);
-                    prof_begin("k_offdiag16", st);
-                    k_offdiag16<__half><<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(
-                        A, ld, K, wd, N, nrb, tc ? w.ut : nullptr, nb, w.flag, (const float*)w.stage, -1, 0);
-                    prof_end("k_offdiag16", st);
+                    NL_TRY(launch_offdiag16<__half>(A, ld, K, wd, N, tc ? w.ut : nullptr, nb, w.flag,
+                                                    (const float*)w.stage, -1, 0, st));
                 } else {
                     const int nrb = (int)cdiv(rest, kOffThreads / kOffG);
                     const size_t sm = (size_t)wp * wp * sizeof(T) + (size_t)wp * (kOffThreads / kOffG) * sizeof(T);
@@ -2023,6 +2040,7 @@ static nl_status lu16_factor_2lvl(int N, __half* A, int64_t ld, int* ipiv, int W
     static bool smem_set = false;
     if (!smem_set) {
         if (set_max_dynamic_smem((const void*)k_offdiag16<float>) != NL_OK ||
+            set_max_dynamic_smem((const void*)k_offdiag16<float, 256>) != NL_OK ||
             set_max_dynamic_smem((const void*)k_diag_lu16<float>) != NL_OK)
             return NL_ECUDA;
         smem_set = true;
@@ -2037,7 +2055,7 @@ static nl_status lu16_factor_2lvl(int N, __half* A, int64_t ld, int* ipiv, int W
             const int K = K0 + p0, wd = std::min(128, Wd - p0), rest = N - K - wd;
             __half* ut = (tc && far > 0) ? w.ut : nullptr;
             if (rest > 0 && w.stream >= 0 && panel16_rows_per_cta(rest, w.stream) > 0) {
-                NL_TRY(launch_panel16<float>(P, ldp, K, wd, N, ipiv, w, ut, W, st, C1, p0));
+                NL_TRY(launch_panel16<float>(P, ldp, K, wd, N, ipiv, w, ut, W, st, (K / 128) & 1, C1, p0));
                 ++nl;
             } else {
                 prof_begin("k_diag_lu16", st);
@@ -2045,12 +2063,7 @@ static nl_status lu16_factor_2lvl(int N, __half* A, int64_t ld, int* ipiv, int W
                 prof_end("k_diag_lu16", st);
                 ++nl;
                 if (rest > 0) {
-                    const int nrb = (int)cdiv(rest, kO16Rows);
-                    const int wp = (int)round_up(wd, 32);
-                    prof_begin("k_offdiag16", st);
-                    k_offdiag16<float><<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(
-                        P, ldp, K, wd, N, nrb, ut, W, w.flag, (const float*)w.stage, C1, p0);
-                    prof_end("k_offdiag16", st);
+                    NL_TRY(launch_offdiag16<float>(P, ldp, K, wd, N, ut, W, w.flag, (const float*)w.stage, C1, p0, st));
                     ++nl;
                 }
             }

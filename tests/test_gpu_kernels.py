@@ -199,6 +199,39 @@ def test_lu16_random_pivoting_valid():
     assert rel <= 0.05 * np.sqrt(N) * 2.0 ** -11 * 10
 
 
+@pytest.mark.parametrize("nb", [128, 256])
+def test_lu16_wide_offdiag_launches_bitwise(nb):
+    """N = 12000: the early panels' off-diagonal solves exceed one wave of
+    128-row CTAs, so the two-launch path (path 2) takes 256 rows per CTA, and
+    the streaming path (path 0) streams the panels that fit and takes the
+    two launches for the rest.  Both give the bits of each other (every row
+    and column is solved by one thread in the same order), one level (nb 128)
+    and two levels (nb 256, inner panels on the single-precision shadow),
+    with the SIMT update.  The Jacobian of eq. (3.2) at x = 1 + sin^2,
+    formed on the GPU."""
+    N, c = 12000, 0.99
+    ld = ((N + 63) // 64) * 64
+    x = torch.as_tensor(1.0 + 0.5 * np.sin(np.arange(N) * 0.37) ** 2, device=dev())
+    F = torch.empty(N, device=dev(), dtype=torch.float64)
+    r = torch.empty(N, device=dev(), dtype=torch.float64)
+    nrm = torch.empty(1, device=dev(), dtype=torch.float64)
+    nl.k_residual(N, c, x, F, r, nrm)
+    J32 = torch.empty((N, ld), device=dev(), dtype=torch.float32)
+    J16 = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    nl.k_jacobian(N, c, r, J32, ld, J16, ld)
+    del J32
+    out = []
+    for path in (0, 2):
+        A = J16.clone()
+        ip = torch.empty(N, device=dev(), dtype=torch.int32)
+        info = nl.lu16(N, A, ld, ip, nb=nb, gemm=1, path=path)
+        assert info == 0
+        assert np.array_equal(ip.cpu().numpy(), np.arange(N))
+        out.append(A.cpu().numpy()[:, :N])
+        del A
+    assert np.array_equal(out[0].view(np.uint16), out[1].view(np.uint16))
+
+
 @pytest.mark.parametrize("N,nb", [(200, 64), (517, 128), (1024, 128), (777, 64)])
 def test_lu16_tensor_core_close_to_oracle(N, nb):
     """tcgen05 trailing update: same pivots, factors within binary16
