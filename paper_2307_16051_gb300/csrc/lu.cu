@@ -1818,8 +1818,8 @@ static int panel16_max_ctas()
 static int panel16_rows_per_cta(int rest, int pref = 0)
 {
     // 128 rows per CTA while every CTA fits at once (more CTAs in the chain's shadow), else
-    // 256; beyond what fits in one wave the two launches are faster (measured on GB300 at
-    // N = 32768: 173 us per streamed panel in two waves against 150 us for the two launches)
+    // 256; beyond what fits in one wave the two launches are as fast (measured on GB300 at
+    // N = 32768: the factorisation takes 65-66 ms either way)
     const int cap = panel16_max_ctas();
     for (int rpc : {pref == kPnlRows ? kPnlRows : 128, kPnlRows})
         if (1 + 2 * (int)cdiv(rest, rpc) <= cap) return rpc;
