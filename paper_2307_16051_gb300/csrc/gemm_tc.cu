@@ -192,37 +192,46 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
 // The same update C <- fl16(C - A Bt^T) with one CTA per SM looping over the
 // output tiles (tile = blockIdx.x + i * gridDim.x) and four warp roles, each
 // stage of work double-buffered:
-//   warp 0 (one thread): TMA loads of the A and B slabs of tile i into
-//     operand stage i % 2 once the MMAs of tile i-2 are done with it;
+//   warp 0 (one thread): TMA loads of the A and B slabs of tile i into the
+//     operand ring's slots as the MMAs free them;
 //   warp 1 (one thread): K/16 tcgen05.mma into TMEM accumulator i % 2 (128
 //     columns each) once the epilogue has read tile i-2's accumulator, then
 //     tcgen05.commit to "accumulator full" and to "operand stage free";
 //   warps 2-5: epilogue.  Each thread owns one tile row (its warp's TMEM
 //     lane quarter): tcgen05.ld of the accumulator row (then "accumulator
-//     free"), C from C buffer i % 3 (128-byte swizzle), fl16(C - acc)
+//     free"), C from C buffer i % kPCBuf (128-byte swizzle), fl16(C - acc)
 //     written back in place, a proxy fence and an arrival on "C written";
 //   warp 6 (one thread): the C tiles' traffic.  TMA load of C for tile i
-//     into buffer i % 3, and for each finished tile the TMA bulk store of its
-//     C buffer, whose completed read of the buffer frees it for tile i+3.
+//     into buffer i % kPCBuf, and for each finished tile the TMA bulk store of
+//     its C buffer, whose completed read of the buffer frees it for tile
+//     i + kPCBuf.
 // Loads, MMAs, epilogue and stores of consecutive tiles overlap, and all
 // global traffic is TMA (coalesced, asynchronous).  Per element the
 // arithmetic is the per-tile kernel's: the same K/16 MMAs in the same order,
 // then one subtraction and one rounding.  The operands stream through a ring
-// of four slots of one 64-wide K slab of A and of B each (32 KB), so K is any
+// of kPRing slots of one 64-wide K slab of A and of B each (32 KB), so K is any
 // multiple of 64 up to kPMaxK: C stays in the tensor-memory accumulator for
 // the whole K extent and is read and written once per update, whatever K
-// (the LU's outer block).  Three C buffers of 32 KB keep two C tiles in flight
-// to and from memory while the epilogue works on the third.  Every wait is bounded; a timeout marks
+// (the LU's outer block).  Two C buffers of 32 KB keep one C tile in flight
+// to or from memory while the epilogue works on the other.  Every wait is bounded; a timeout marks
 // the CTA aborted, every role leaves its loop, in-flight copies and MMAs are
 // waited for (bounded), and tensor memory is released.
 constexpr int kPThreads = 224;
 constexpr uint32_t kPSlab = 128 * 128;  // bytes of one 128-row x 64-column binary16 slab
 constexpr uint32_t kPCBytes = 2 * kPSlab;  // one C tile: two 64-column boxes
-constexpr int kPCBuf = 3;
-constexpr int kPRing = 4;                  // operand slots, each an A slab and a B slab (K = 64)
+// Ring shapes (operand slots, C buffers), 225 KB of shared memory either way.
+// Deep updates (K >= 256) stream many operand slabs per C tile and are bound by
+// the operand bytes in flight against the L2 latency (ncu, N = 8192, K = 512,
+// four slots: L2 43%, DRAM 36%, tensor pipe 35%), so they take five slots and
+// two C buffers; shallow ones (K <= 128, and the grouped update) move more C
+// than operands and keep three C buffers.  Measured on GB300: the N = 32768
+// factorisation's K = 512 updates 25.4 ms with (5, 2) against 27.8 with (4, 3)
+// and 28.3 with (6, 1); the batch's K = 64 grouped updates 4% faster with (4, 3).
+constexpr int kPRingDeep = 5, kPCBufDeep = 2;
+constexpr int kPRingShallow = 4, kPCBufShallow = 3;
 constexpr int kPMaxK = 1024;               // largest K of one update
 
-static size_t p_smem_bytes() { return 1024 + (size_t)kPRing * 2 * kPSlab + kPCBuf * (size_t)kPCBytes + 256; }
+static size_t p_smem_bytes(int ring, int cbuf) { return 1024 + (size_t)ring * 2 * kPSlab + cbuf * (size_t)kPCBytes + 256; }
 
 // Where tile `it` of a persistent CTA reads and writes: the A slabs at
 // (ax + 64 kt, ay) of map a, the B slabs at (64 kt, by) of map b, the C tile's
@@ -240,7 +249,7 @@ struct TileRef {
 // from K + w), read through the instance's whole-matrix map (A and C) and
 // its U12^T map (B); rows and columns past the instance's N read as zero and
 // are not stored.
-template <bool GROUPED>
+template <bool GROUPED, int kPRing, int kPCBuf>
 __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const CUtensorMap* tmB,
                                                    const CUtensorMap* tmC, int M, int Nc, int K,
                                                    const GInst* __restrict__ ginst, const TmapBytes* __restrict__ gmaps,
@@ -402,7 +411,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     } else if (warp == 6) {
         if (lane == 0) {
             // C traffic: loads for tiles 0..2, then per finished tile i its store
-            // and, once the store has read the buffer, the load for tile i+3
+            // and, once the store has read the buffer, the load for tile i + kPCBuf
             int loaded = 0;
             for (int it = 0; it < kPCBuf && it < nmine; ++it) {
                 const TileRef r = ref(it);
@@ -458,7 +467,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint8_t* cst = basep + ring_bytes + s * kPCBytes;  // C buffer it % 3
+            uint8_t* cst = basep + ring_bytes + s * kPCBytes;  // C buffer it % kPCBuf
 #pragma unroll
             for (int c = 0; c < kTcBN; c += 32) {
                 uint32_t v[32];
@@ -513,6 +522,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     }
 }
 
+template <int RING, int CBUF>
 __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap tmA,
                                                             const __grid_constant__ CUtensorMap tmB,
                                                             const __grid_constant__ CUtensorMap tmC, int M, int Nc,
@@ -520,7 +530,7 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
                                                             const int* __restrict__ flag)
 {
     if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
-    tc_gemm_persistent<false>(&tmA, &tmB, &tmC, M, Nc, K, nullptr, nullptr, nullptr, 0, 0, 0, err);
+    tc_gemm_persistent<false, RING, CBUF>(&tmA, &tmB, &tmC, M, Nc, K, nullptr, nullptr, nullptr, 0, 0, 0, err);
 }
 
 __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_pg(const GInst* __restrict__ inst,
@@ -528,7 +538,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_pg(const GInst* __rest
                                                              const GTask* __restrict__ tasks, int ntasks, int K, int w,
                                                              unsigned* __restrict__ err)
 {
-    tc_gemm_persistent<true>(nullptr, nullptr, nullptr, 0, 0, w, inst, maps, tasks, ntasks, K, w, err);
+    tc_gemm_persistent<true, kPRingShallow, kPCBufShallow>(nullptr, nullptr, nullptr, 0, 0, w, inst, maps, tasks, ntasks,
+                                                           K, w, err);
 }
 
 // Grouped trailing update of outer step [K, K + w) of many matrices: task
@@ -578,7 +589,8 @@ bool tc_gemm_supported()
     cudaMemset(g_tc_err, 0, sizeof(unsigned));
     if (set_max_dynamic_smem((const void*)k_tc_gemm) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_g) != NL_OK) return false;
-    if (set_max_dynamic_smem((const void*)k_tc_gemm_p) != NL_OK) return false;
+    if (set_max_dynamic_smem((const void*)k_tc_gemm_p<kPRingDeep, kPCBufDeep>) != NL_OK) return false;
+    if (set_max_dynamic_smem((const void*)k_tc_gemm_p<kPRingShallow, kPCBufShallow>) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_pg) != NL_OK) return false;
     g_tc_state = 1;
     return true;
@@ -641,7 +653,12 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         const long long ntiles = (long long)cdiv(Nc, kTcBN) * cdiv(M, kTcBM);
         const unsigned grid = (unsigned)std::min<long long>(ntiles, nsm);
         prof_begin("k_tc_gemm", st);
-        k_tc_gemm_p<<<grid, kPThreads, p_smem_bytes(), st>>>(tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
+        if (K >= 256)
+            k_tc_gemm_p<kPRingDeep, kPCBufDeep><<<grid, kPThreads, p_smem_bytes(kPRingDeep, kPCBufDeep), st>>>(
+                tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
+        else
+            k_tc_gemm_p<kPRingShallow, kPCBufShallow><<<grid, kPThreads, p_smem_bytes(kPRingShallow, kPCBufShallow),
+                                                         st>>>(tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
         prof_end("k_tc_gemm", st);
         NL_CUDA_OK(cudaGetLastError());
         return NL_OK;
@@ -877,7 +894,8 @@ nl_status tc_gemm16_grouped(const GInst* inst, const TmapBytes* maps, const GTas
             if (nsm < 1) nsm = 1;
         }
         const unsigned grid = (unsigned)std::min(ntasks, nsm);
-        k_tc_gemm_pg<<<grid, kPThreads, p_smem_bytes(), st>>>(inst, maps, tasks, ntasks, K, w, g_tc_err);
+        k_tc_gemm_pg<<<grid, kPThreads, p_smem_bytes(kPRingShallow, kPCBufShallow), st>>>(inst, maps, tasks, ntasks,
+                                                                                           K, w, g_tc_err);
     } else {
         k_tc_gemm_g<<<(unsigned)ntasks, kTcThreads, tc_smem_bytes(w), st>>>(inst, maps, tasks, K, w, g_tc_err);
     }
