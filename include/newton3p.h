@@ -443,10 +443,21 @@ void nl_server_destroy(nl_server* s);
  * arithmetic (factors bitwise those of gemm = 1), or 128 x 128 tcgen05 tiles
  * (5, nb = 64; factors bitwise those of gemm = 2).  A wait that gives up
  * returns NL_ETIMEOUT.  A, ipiv: host arrays of device pointers.
- * N[i] in [1, 32768].  Allocates its workspace with cudaMalloc.
+ * N[i] in [1, 32768].  With the tcgen05 update the entries of a row in
+ * columns N[i] .. round_up(N[i], 8) - 1 (inside the leading dimension) may be
+ * overwritten: the tensor-memory copies store whole 16-byte units at the
+ * matrix's right edge.  Allocates its workspace with cudaMalloc.
  * Synchronises. */
 nl_status nl_lu_grouped(int count, const int64_t* N, void* const* A, const int64_t* ld, int32_t* const* ipiv,
                         int fp64, int nb, int gemm, int32_t* flags_host, void* stream);
+
+/* Test hook: the number of polls after which a dependency wait of the
+ * persistent grouped LU gives up (0 = the default, about a second; negative =
+ * at the first unmet poll).  A wait that gives up records a timeout in the
+ * device error word, every later wait returns at once, the launch completes
+ * (the tasks skip their work) and the call returns NL_ETIMEOUT; the context
+ * stays usable.  Process-wide; for tests only. */
+nl_status nl_debug_grouped_wait_limit(long long polls);
 
 /* Per-task timing of the persistent grouped LU (nl_lu_grouped gemm 3 / 4 /
  * 5, batches with trailing_gemm 3 / 4 / 5), for measurement.  Returns in out9
@@ -547,6 +558,9 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
  * largest |a_ik| as pivot): the arithmetic of the paper's F16 column; nb and
  * gemm are ignored, and *info_host is also set (to -1) after a binary16
  * overflow, returned as NL_ENUMERIC.
+ * With the tcgen05 update the entries of a row in columns N ..
+ * round_up(N, 8) - 1 (inside ld) may be overwritten (the tensor-memory copies
+ * store whole 16-byte units at the matrix's right edge).
  * Allocates its workspace (and the copy) with cudaMallocAsync on
  * `stream`.  Synchronises the stream. */
 nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,

@@ -2450,13 +2450,20 @@ static_assert(sizeof(PTask) == 80, "queue entries are five 16-byte chunks");
 // both from its one acquire load)
 constexpr int kPgFail = 1 << 30;
 
+// Polls before a wait gives up: 0 = kPgSpin; negative = give up at the first
+// unmet poll (a test of the timeout path that needs no fault: a wait that runs
+// out whatever the producers do).
+__device__ long long g_pg_spin_limit = 0;
+
 __device__ __forceinline__ bool pg_wait(const int* p, int need, unsigned* err, int* val)
 {
     long long it = 0;
     int v;
+    const long long lim = g_pg_spin_limit;
+    const long long limit = lim == 0 ? kPgSpin : (lim < 0 ? 0 : lim);
     while (((v = ld_acquire_gpu(p)) & ~kPgFail) < need) {
         if (*(volatile unsigned*)err) return false;
-        if (++it > kPgSpin) {
+        if (++it > limit) {
             atomicOr(err, (unsigned)ERR_TIMEOUT_OTHER);
             return false;
         }
@@ -3209,5 +3216,12 @@ extern "C" nl_status nl_debug_grouped_task_times(int enable, double* out9)
             out9[3 * k + 2] = khz > 0 ? (double)v[3 * k + 2] / (khz * 1e-3) : 0.0;
         }
     g_pg_tstat_on.store(enable != 0);
+    return NL_OK;
+}
+
+extern "C" nl_status nl_debug_grouped_wait_limit(long long polls)
+{
+    using namespace nl;
+    NL_CUDA_OK(cudaMemcpyToSymbol(g_pg_spin_limit, &polls, sizeof(polls)));
     return NL_OK;
 }

@@ -147,6 +147,7 @@ SIGNATURES = {
     "nl_server_destroy": (None, [_P]),
     "nl_lu_grouped": (_int, [_int, _P, _P, _P, _P, _int, _int, _int, _P, _P]),
     "nl_debug_grouped_task_times": (_int, [_int, _P]),
+    "nl_debug_grouped_wait_limit": (_int, [ctypes.c_longlong]),
     "nl_k_update32": (_int, [_i64, _i64, _i64, _P, _i64, _P, _i64, _P, _i64, _P]),
     "nl_lusolve_grouped": (_int, [_int, _P, _P, _P, _P, _P, _int, _P]),
 }
@@ -444,6 +445,11 @@ def linsolve16(N, J32, ld32, LU16, ld16, ipiv, b, u, eta=1e-4, maxit=20, solver=
     check(lib().nl_linsolve16(N, _ptr(J32), ld32, _ptr(LU16), ld16, _ptr(ipiv), _ptr(b), _ptr(u), eta, maxit, solver,
                               m, gtol, gcycles, stats, ctypes.byref(rel), _stream(stream)))
     return dict(iters=stats[0], outer=stats[1], failed=stats[2], converged=stats[3], relres=rel.value)
+
+
+def grouped_wait_limit(polls: int):
+    """Test hook: polls before a persistent grouped-LU wait gives up (0 default, < 0 at once)."""
+    check(lib().nl_debug_grouped_wait_limit(int(polls)))
 
 
 def grouped_task_times(enable=True) -> dict:

@@ -98,3 +98,43 @@ def test_best_iterate_on_not_converged(c, scale, maxit):
     xo, ro = O.newton(N, c, "GMRESIR16", tol=1e-10, x0=x0, newton_maxit=maxit)
     fo = np.linalg.norm(O.F(N, c, xo))
     assert abs(fo - min(ro["hist"]) * np.linalg.norm(O.F(N, c, x0))) <= 1e-9 * fo + 1e-14
+
+
+@pytest.mark.parametrize("gemm", [3, 5])
+def test_persistent_grouped_lu_wait_runs_out(gemm):
+    """The persistent grouped LU's dependency waits are bounded: with the poll
+    limit set to give up at the first unmet poll, the off-diagonal tasks that
+    start while their diagonal block is being factored give up, the launch
+    completes, nl_lu_grouped returns NL_ETIMEOUT, and with the default limit
+    the next call on the same context factors the same matrices correctly
+    (bitwise the three-launch grouped LU with the same update)."""
+    Ns = [1500, 300, 90]
+    mats = [O.fl16(O.jacobian(N, 0.9, 1.0 + 0.3 * np.sin(np.arange(N)) ** 2).astype(np.float32).astype(np.float64))
+            for N in Ns]
+
+    def run(g):
+        As, lds, ips = [], [], []
+        for M in mats:
+            N = M.shape[0]
+            ld = ((N + 63) // 64) * 64
+            a = np.zeros((N, ld), dtype=np.float16)
+            a[:, :N] = M.astype(np.float16)
+            As.append(torch.as_tensor(a, device="cuda"))
+            lds.append(ld)
+            ips.append(torch.empty(N, dtype=torch.int32, device="cuda"))
+        flags = nl.lu_grouped(Ns, As, lds, ips, nb=64, gemm=g)
+        torch.cuda.synchronize()
+        return [A.cpu().numpy()[:, :n] for A, n in zip(As, Ns)], flags
+
+    nl.grouped_wait_limit(-1)
+    try:
+        with pytest.raises(nl.NLError) as e:
+            run(gemm)
+        assert e.value.status == nl.NL_ETIMEOUT
+    finally:
+        nl.grouped_wait_limit(0)
+    out, flags = run(gemm)
+    ref, rflags = run(1 if gemm == 3 else 2)
+    assert not flags.any() and not rflags.any()
+    for a, b in zip(out, ref):
+        assert np.array_equal(a, b)
