@@ -1390,7 +1390,7 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
                                                int nrow_blocks, __half* __restrict__ Ut, int ldut,
                                                int* __restrict__ flag, const float* stage, int bid,
                                                int ut_col0 = -1, int ut_k0 = 0, int tid_in = -1,
-                                               float* smem = nullptr)
+                                               float* smem = nullptr, int off0 = 0)
 {
     if (ut_col0 < 0) ut_col0 = K + w;
     if (tid_in < 0 && *(volatile int*)flag) return;  // (a group of a larger CTA: its caller checked)
@@ -1415,7 +1415,8 @@ __device__ __forceinline__ void offdiag16_body(S* __restrict__ A, int64_t lda, i
     __syncthreads();
     if (row_role && tid < wp) rinv[tid] = __frcp_rn(D[tid * wp + tid]);
     __syncthreads();
-    const int idx = K + w + (row_role ? bid : bid - nrow_blocks) * ROWS + tid;
+    // off0: the first off0 rows (columns) below (right of) the block are someone else's
+    const int idx = K + w + off0 + (row_role ? bid : bid - nrow_blocks) * ROWS + tid;
     const bool live = idx < N;
     float* Xt = X + tid;
     if (row_role) {
@@ -1533,9 +1534,10 @@ template <typename S, int ROWS = kO16Rows>
 __global__ void __launch_bounds__(ROWS) k_offdiag16(S* __restrict__ A, int64_t lda, int K, int w, int N,
                                                  int nrow_blocks, __half* __restrict__ Ut, int ldut,
                                                  int* __restrict__ flag, const float* __restrict__ stage,
-                                                 int ut_col0, int ut_k0)
+                                                 int ut_col0, int ut_k0, int off0)
 {
-    offdiag16_body<S, ROWS>(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x, ut_col0, ut_k0);
+    offdiag16_body<S, ROWS>(A, lda, K, w, N, nrow_blocks, Ut, ldut, flag, stage, (int)blockIdx.x, ut_col0, ut_k0, -1,
+                            nullptr, off0);
 }
 
 // The off-diagonal solves of one panel: 128 rows (columns) per CTA, or 256 for a
@@ -1544,19 +1546,19 @@ __global__ void __launch_bounds__(ROWS) k_offdiag16(S* __restrict__ A, int64_t l
 // results: every row (column) is solved by one thread in the same order.
 template <typename S>
 static nl_status launch_offdiag16(S* A, int64_t ld, int K, int wd, int N, __half* ut, int ldut, int* flag,
-                                  const float* stage, int ut_col0, int ut_k0, cudaStream_t st)
+                                  const float* stage, int ut_col0, int ut_k0, cudaStream_t st, int off0 = 0)
 {
-    const int rest = N - K - wd, wp = (int)round_up(wd, 32);
+    const int rest = N - K - wd - off0, wp = (int)round_up(wd, 32);  // rows (columns) from K + wd + off0
     const bool wide = wp > 64 && 2 * (int)cdiv(rest, kO16Rows) > num_sms();
     prof_begin("k_offdiag16", st);
     if (wide) {
         const int nrb = (int)cdiv(rest, 256);
         k_offdiag16<S, 256><<<2 * nrb, 256, offdiag16_smem(wp, 256), st>>>(A, ld, K, wd, N, nrb, ut, ldut, flag, stage,
-                                                                         ut_col0, ut_k0);
+                                                                         ut_col0, ut_k0, off0);
     } else {
         const int nrb = (int)cdiv(rest, kO16Rows);
         k_offdiag16<S><<<2 * nrb, kO16Threads, offdiag16_smem(wp), st>>>(A, ld, K, wd, N, nrb, ut, ldut, flag, stage,
-                                                                        ut_col0, ut_k0);
+                                                                        ut_col0, ut_k0, off0);
     }
     prof_end("k_offdiag16", st);
     NL_CUDA_OK(cudaGetLastError());
@@ -1826,6 +1828,16 @@ static int panel16_rows_per_cta(int rest, int pref = 0)
     return 0;
 }
 
+// Rows (and columns) of a panel the streaming launch takes: all of them when its
+// CTAs fit on the device at once, else as many as 256-row CTAs fitting at once
+// cover (the rest go to a following off-diagonal launch); 0 = none.
+static int panel16_fit_rows(int rest, int pref = 0)
+{
+    if (panel16_rows_per_cta(rest, pref) > 0) return rest;
+    const int nrb = (panel16_max_ctas() - 1) / 2;
+    return nrb >= 1 ? std::min(rest, nrb * kPnlRows) : 0;
+}
+
 static std::atomic<unsigned> g_panel_epoch{0};
 
 template <typename S>
@@ -1888,12 +1900,19 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         if (fast) {
             const int wp = (int)round_up(wd, 32);
             if constexpr (kHalf) {
-                if (rest > 0 && w.stream >= 0 && panel16_rows_per_cta(rest, w.stream) > 0) {
+                const int R = (rest > 0 && w.stream >= 0) ? panel16_fit_rows(rest, w.stream) : 0;
+                if (R > 0) {
                     if (!pub_cleared) {
                         NL_CUDA_OK(cudaMemsetAsync(w.pub, 0, (size_t)128 * 128 * 8, st));
                         pub_cleared = true;
                     }
-                    NL_TRY(launch_panel16(A, ld, K, wd, N, ipiv, w, tc ? w.ut : nullptr, nb, st, (K / nb) & 1));
+                    // the streamed rows and columns, then (if any) the rest in one off-diagonal launch
+                    NL_TRY(launch_panel16(A, ld, K, wd, K + wd + R, ipiv, w, tc ? w.ut : nullptr, nb, st, (K / nb) & 1));
+                    if (R < rest) {
+                        NL_TRY(launch_offdiag16<__half>(A, ld, K, wd, N, tc ? w.ut : nullptr, nb, w.flag,
+                                                        (const float*)w.stage, -1, 0, st, R));
+                        ++nl;
+                    }
                     nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
                     if (s != NL_OK) return s;
                     nl += 2;
@@ -2054,9 +2073,14 @@ static nl_status lu16_factor_2lvl(int N, __half* A, int64_t ld, int* ipiv, int W
         for (int p0 = 0; p0 < Wd; p0 += 128) {
             const int K = K0 + p0, wd = std::min(128, Wd - p0), rest = N - K - wd;
             __half* ut = (tc && far > 0) ? w.ut : nullptr;
-            if (rest > 0 && w.stream >= 0 && panel16_rows_per_cta(rest, w.stream) > 0) {
-                NL_TRY(launch_panel16<float>(P, ldp, K, wd, N, ipiv, w, ut, W, st, (K / 128) & 1, C1, p0));
+            const int R = (rest > 0 && w.stream >= 0) ? panel16_fit_rows(rest, w.stream) : 0;
+            if (R > 0) {
+                NL_TRY(launch_panel16<float>(P, ldp, K, wd, K + wd + R, ipiv, w, ut, W, st, (K / 128) & 1, C1, p0));
                 ++nl;
+                if (R < rest) {
+                    NL_TRY(launch_offdiag16<float>(P, ldp, K, wd, N, ut, W, w.flag, (const float*)w.stage, C1, p0, st, R));
+                    ++nl;
+                }
             } else {
                 prof_begin("k_diag_lu16", st);
                 k_diag_lu16<float><<<1, kD16Threads, kDiag16Smem, st>>>(P, ldp, K, wd, ipiv, w.flag, (float*)w.stage);

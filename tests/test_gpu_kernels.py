@@ -199,17 +199,19 @@ def test_lu16_random_pivoting_valid():
     assert rel <= 0.05 * np.sqrt(N) * 2.0 ** -11 * 10
 
 
+@pytest.mark.parametrize("N", [12000, 20480])
 @pytest.mark.parametrize("nb", [128, 256])
-def test_lu16_wide_offdiag_launches_bitwise(nb):
-    """N = 12000: the early panels' off-diagonal solves exceed one wave of
-    128-row CTAs, so the two-launch path (path 2) takes 256 rows per CTA, and
-    the streaming path (path 0) streams the panels that fit and takes the
-    two launches for the rest.  Both give the bits of each other (every row
-    and column is solved by one thread in the same order), one level (nb 128)
-    and two levels (nb 256, inner panels on the single-precision shadow),
-    with the SIMT update.  The Jacobian of eq. (3.2) at x = 1 + sin^2,
-    formed on the GPU."""
-    N, c = 12000, 0.99
+def test_lu16_wide_offdiag_launches_bitwise(N, nb):
+    """Large panels: at N = 12000 the early panels' off-diagonal solves exceed
+    one wave of 128-row CTAs, so the two-launch path (path 2) takes 256 rows
+    per CTA; at N = 20480 the early panels also have more rows than one
+    streaming launch holds at once, so the streaming path (path 0) streams
+    as many as fit and solves the rest in a following off-diagonal launch.
+    Both paths give the bits of each other (every row and column is solved
+    by one thread in the same order), one level (nb 128) and two levels
+    (nb 256, inner panels on the single-precision shadow), with the SIMT
+    update.  The Jacobian of eq. (3.2) at x = 1 + sin^2, formed on the GPU."""
+    c = 0.99
     ld = ((N + 63) // 64) * 64
     x = torch.as_tensor(1.0 + 0.5 * np.sin(np.arange(N) * 0.37) ** 2, device=dev())
     F = torch.empty(N, device=dev(), dtype=torch.float64)
