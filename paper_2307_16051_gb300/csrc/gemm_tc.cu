@@ -651,11 +651,14 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
             if (nsm < 1) nsm = 1;
         }
         const long long ntiles = (long long)cdiv(Nc, kTcBN) * cdiv(M, kTcBM);
-        // A shallow update (K <= 128, a one-level panel's) is short and bound by its C traffic;
-        // half the SMs leave the other half to concurrent solves' latency-bound panels (the
-        // sweep of five concurrent solves at N = 4096 measured 123 against 119 solves/s with
-        // every SM, 120 with a third; one solve alone is 2% slower).  Deep updates take all.
-        const unsigned grid = (unsigned)std::min<long long>(ntiles, K >= 256 ? nsm : std::max(1, nsm / 2));
+        // A small shallow update (K <= 128, at most 8 tiles per SM: a one-level panel's at
+        // N <= ~4600) is short and bound by its C traffic; half the SMs leave the other half
+        // to concurrent solves' latency-bound panels (the sweep of five concurrent solves at
+        // N = 4096 measured 123 against 119 solves/s with every SM, 120 with a third; one
+        // solve alone is 2% slower).  Larger and deep updates take every SM (capped, the
+        // N = 32768 factorisation with nb = 128 took 104 instead of 82 ms).
+        const bool small = K < 256 && ntiles <= 8LL * nsm;
+        const unsigned grid = (unsigned)std::min<long long>(ntiles, small ? std::max(1, nsm / 2) : nsm);
         prof_begin("k_tc_gemm", st);
         if (K >= 256)
             k_tc_gemm_p<kPRingDeep, kPCBufDeep><<<grid, kPThreads, p_smem_bytes(kPRingDeep, kPCBufDeep), st>>>(
