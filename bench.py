@@ -37,6 +37,11 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Hardware work queues for the concurrent solves (read when the CUDA context is
+# created): each solve has its stream and its LU look-ahead's side stream, and
+# with CUDA's default of 8 queues the sweep's ten streams (the server's up to
+# sixteen) would share queues and wait on one another's unrelated launches.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 SWEEP = (0.5, 0.9, 0.99, 0.9999, 0.999999)
 N_BENCH = 4096
@@ -111,10 +116,13 @@ class ClockSampler:
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x 2 flop/FMA x max SM clock
 
 
-def kernel_rooflines(nl, step, N, hbm_peak, tc_peak):
+def kernel_rooflines(nl, step, N, hbm_peak, tc_peak, lookahead=True):
     """Time each kernel class of one GMRES-IR16 sweep with CUDA events (the
     library brackets every launch of the class on its stream) and set the
-    algorithmic work of one launch against its roofline."""
+    algorithmic work of one launch against its roofline.  With the LU's
+    look-ahead each trailing update is two launches: the cross (the first
+    128-row and 128-column tile strips, class k_tc_gemm_x) and the rest
+    (k_tc_gemm)."""
     NB, T2 = 128, 128
     out = {}
     # algorithmic work per launch at N = 4096, nb = 128 (averaged over the 32 panels)
@@ -123,6 +131,9 @@ def kernel_rooflines(nl, step, N, hbm_peak, tc_peak):
     off = [(N - K - w, w) for K, w in panels if N - K - w > 0]
     off_flop = sum(2.0 * 2 * r * w * w / 2.0 for r, w in off) / len(off)          # L21 and U12 solves
     gemm_flop = sum(2.0 * r * r * w for r, w in off) / len(off)
+    rest = [(r, w) for r, w in off if r > T2]
+    rest_flop = sum(2.0 * (r - T2) ** 2 * w for r, w in rest) / max(1, len(rest))
+    cross_flop = sum(2.0 * (r * r - max(r - T2, 0) ** 2) * w for r, w in off) / len(off)
     nblk = (N + T2 - 1) // T2
     trsv_bytes = (N * N / 2.0) * 2 + nblk * T2 * T2 * 4 + 3 * N * 4                 # fp16 triangle + diag inverses + vectors
     gemv_bytes = 4.0 * N * N + 3 * 4.0 * N                                          # fp32 J and vectors
@@ -131,7 +142,9 @@ def kernel_rooflines(nl, step, N, hbm_peak, tc_peak):
         "k_offdiag16": ("alu", off_flop, FP32_PEAK_TFLOPS, "TFLOP/s", "derived fp32 FMA peak"),
         "k_panel16": ("alu", diag_flop + off_flop, FP32_PEAK_TFLOPS, "TFLOP/s",
                       "derived fp32 FMA peak (diagonal block and off-diagonal solves in one launch)"),
-        "k_tc_gemm": ("tensor", gemm_flop, tc_peak, "TFLOP/s", "measured bf16 dense (fp16 same rate)"),
+        "k_tc_gemm": ("tensor", rest_flop if lookahead else gemm_flop, tc_peak, "TFLOP/s",
+                      "measured bf16 dense (fp16 same rate)"),
+        "k_tc_gemm_x": ("tensor", cross_flop, tc_peak, "TFLOP/s", "measured bf16 dense (fp16 same rate)"),
         "k_trsv_cl": ("hbm", trsv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
         "k_trsv_mb": ("hbm", trsv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
         "k_gemv_residual": ("hbm", gemv_bytes, hbm_peak, "GB/s", "measured copy bandwidth"),
@@ -442,6 +455,8 @@ def main():
     ap.add_argument("--lu-nb", type=int, default=0, help="LU outer block (0: library default)")
     ap.add_argument("--lu-stream", type=int, default=0,
                     help="panel launch: 0 library default, 256 streaming CTAs of 256 rows, -1 two launches")
+    ap.add_argument("--lu-lookahead", type=int, default=0,
+                    help="LU look-ahead: 0 library default (on), -1 one trailing update per panel")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched workload")
     ap.add_argument("--no-large", action="store_true", help="skip the N=32768 single solve")
     ap.add_argument("--no-large-fp64", action="store_true", help="skip FP64-LU Newton at N=32768 (about 2 minutes)")
@@ -470,7 +485,8 @@ def main():
     # latency: its stream gets the highest priority (lower number = higher).
     order = sorted(SWEEP)
     streams = {c: torch.cuda.Stream(device=dev, priority=-order.index(c)) for c in SWEEP}
-    solvers = {c: nl.Solver(N_BENCH, c, stream=streams[c], lu_nb=args.lu_nb, lu_stream=args.lu_stream) for c in SWEEP}
+    solvers = {c: nl.Solver(N_BENCH, c, stream=streams[c], lu_nb=args.lu_nb, lu_stream=args.lu_stream,
+                            lu_lookahead=args.lu_lookahead) for c in SWEEP}
     xdev = {c: torch.empty(N_BENCH, device=dev, dtype=torch.float64) for c in SWEEP}
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev, dtype=torch.float32)
     import concurrent.futures as cf
@@ -530,7 +546,8 @@ def main():
     n_lu = sum(s["newton_iters"] for s in stats.values())
     launches = sum(s["gpu_launches"] for s in stats.values())
     # sequential solves for the per-launch kernel timing (event pairs per kernel class)
-    kern = kernel_rooflines(nl, lambda mode: step(mode, True, False), N_BENCH, hbm_peak, tc_peak)
+    kern = kernel_rooflines(nl, lambda mode: step(mode, True, False), N_BENCH, hbm_peak, tc_peak,
+                            lookahead=args.lu_lookahead == 0)
     ms_seq, _ = timed("GMRESIR16", 1, concurrent=False)
     dom = max(kern.values(), key=lambda k: k["total_ms"])
     roofline = {k: dom[k] for k in ("bound", "achieved", "peak", "unit", "frac", "traffic")}
@@ -612,7 +629,8 @@ def main():
     def alt_sweep(mode, **cfg):
         """The sweep with other handles (another configuration) on the same streams: one untimed
         pass, one timed."""
-        hs = {c: nl.Solver(N_BENCH, c, stream=streams[c], lu_nb=args.lu_nb, lu_stream=args.lu_stream, **cfg)
+        hs = {c: nl.Solver(N_BENCH, c, stream=streams[c], lu_nb=args.lu_nb, lu_stream=args.lu_stream,
+                           lu_lookahead=args.lu_lookahead, **cfg)
               for c in SWEEP}
 
         def run(c):
@@ -674,7 +692,8 @@ def main():
             "vs_baseline": None, "dtype": "f16/f32/f64", "data": "synthetic (the paper's H-equation, x0=ones)",
             "config": {"workload": WORKLOAD, "N": N_BENCH, "c": list(SWEEP), "mode": "GMRESIR16",
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{ws}",
-                       "concurrency": "the five solves of a step on five streams (one host thread each)"},
+                       "concurrency": "the five solves of a step on five streams (one host thread each)",
+                       "cuda_device_max_connections": int(os.environ.get("CUDA_DEVICE_MAX_CONNECTIONS", "8"))},
             "roofline": roofline, "roofline_lu": roofline_lu, "kernels": kern, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "per_c": per_c, **extra}
     from paper_2307_16051_gb300 import workloads as W

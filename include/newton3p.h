@@ -144,7 +144,12 @@ typedef struct {
                             table (N^2 products); 0 = the FFT for N >= 4096, where it is the faster one
                             (45 against 61 us at N = 4096, 70 us against 2.1 ms at N = 32768), the direct
                             sum below */
-    int reserved[1];
+    int lu_lookahead;    /* [0 = on] half-precision fast path with the tensor-core update (lu_nb <= 128):
+                            after each panel only the trailing matrix's first 128-row and 128-column
+                            tile strips (which hold the next panel) are updated on the solve's
+                            stream, and the rest of the update runs on a second stream of the same
+                            priority while the next panel is factored; the two are joined before
+                            the next update.  -1 = one update per panel.  Bitwise the same factors */
 } nl_config;
 
 #define NL_MAX_HIST 128
@@ -234,7 +239,8 @@ const char* nl_last_error(void);
  * "k_diag_lu", "k_offdiag" (double LU), "k_tc_update32" (the two-level
  * LU's tensor-core inner updates), "k_lu_grouped_p" (the persistent grouped
  * LU), "k_tc_gemm" (tensor-core trailing
- * update), "k_invdiag" (diagonal-block inverses), "k_trsv_cl" (cluster
+ * update), "k_tc_gemm_x" (its look-ahead part: the next panel's tile strips),
+ * "k_invdiag" (diagonal-block inverses), "k_trsv_cl" (cluster
  * triangular solve), "k_trsv_mb" (mailbox triangular solve),
  * "k_lusolve16h" (binary16-arithmetic solve), "k_gemv_residual",
  * "k_residual" (F by the direct sum), "k_fft" (F by the FFT: its four
@@ -553,6 +559,8 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
  * saved copy of A if not (same result either way); 1 = interchanging path
  * only; 2 = as 0 with the diagonal block and the off-diagonal solves of each
  * panel in two launches instead of one streaming launch (same result);
+ * 4 = as 0 with look-ahead (nl_config.lu_lookahead; same result; a second
+ * stream is created and destroyed by the call);
  * 3 = every operation rounded to binary16 instead (l_ik = fl16(a_ik/a_kk),
  * a_ij <- fl16(a_ij - fl16(l_ik a_kj)) in increasing k, the first row of
  * largest |a_ik| as pivot): the arithmetic of the paper's F16 column; nb and

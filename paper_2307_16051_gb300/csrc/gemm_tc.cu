@@ -244,7 +244,9 @@ struct TileRef {
 };
 
 // Single update: the maps are kernel parameters (tmA, tmB, tmC), tiles in
-// row-major order over the M x Nc output.  Grouped update: task t of the
+// row-major order over the M x Nc output; with cross set only the first tile
+// column (every tile row) and the rest of the first tile row, the part of the
+// trailing matrix the next panel of an LU reads.  Grouped update: task t of the
 // step's list is {instance, m0, n0} of that instance's A22 (rows and columns
 // from K + w), read through the instance's whole-matrix map (A and C) and
 // its U12^T map (B); rows and columns past the instance's N read as zero and
@@ -254,7 +256,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                                                    const CUtensorMap* tmC, int M, int Nc, int K,
                                                    const GInst* __restrict__ ginst, const TmapBytes* __restrict__ gmaps,
                                                    const GTask* __restrict__ gtasks, int ntasks, int gK, int gw,
-                                                   unsigned* __restrict__ err)
+                                                   unsigned* __restrict__ err, int cross = 0)
 {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -271,8 +273,8 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + bCDONE + kPCBuf);
     __shared__ int aborted;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_n = (Nc + kTcBN - 1) / kTcBN;
-    const int ntiles = GROUPED ? ntasks : tiles_n * ((M + kTcBM - 1) / kTcBM);
+    const int tiles_n = (Nc + kTcBN - 1) / kTcBN, tiles_m = (M + kTcBM - 1) / kTcBM;
+    const int ntiles = GROUPED ? ntasks : (cross ? tiles_m + tiles_n - 1 : tiles_n * tiles_m);
     const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto bar = [&](int k) { return smem_u32(&bars[k]); };
     auto fail = [&]() {
@@ -292,7 +294,14 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
             r.cx = gK + gw + t.b;
             r.store = *(volatile const int*)ginst[t.inst].flag == 0;
         } else {
-            const int m0 = (tile / tiles_n) * kTcBM, n0 = (tile % tiles_n) * kTcBN;
+            int m0, n0;
+            if (cross) {  // tiles (i, 0) for every i, then (0, j) for j >= 1
+                m0 = tile < tiles_m ? tile * kTcBM : 0;
+                n0 = tile < tiles_m ? 0 : (tile - tiles_m + 1) * kTcBN;
+            } else {
+                m0 = (tile / tiles_n) * kTcBM;
+                n0 = (tile % tiles_n) * kTcBN;
+            }
             r.a = tmA;
             r.b = tmB;
             r.c = tmC;
@@ -527,10 +536,10 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
                                                             const __grid_constant__ CUtensorMap tmB,
                                                             const __grid_constant__ CUtensorMap tmC, int M, int Nc,
                                                             int K, unsigned* __restrict__ err,
-                                                            const int* __restrict__ flag)
+                                                            const int* __restrict__ flag, int cross)
 {
     if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
-    tc_gemm_persistent<false, RING, CBUF>(&tmA, &tmB, &tmC, M, Nc, K, nullptr, nullptr, nullptr, 0, 0, 0, err);
+    tc_gemm_persistent<false, RING, CBUF>(&tmA, &tmB, &tmC, M, Nc, K, nullptr, nullptr, nullptr, 0, 0, 0, err, cross);
 }
 
 __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_pg(const GInst* __restrict__ inst,
@@ -617,7 +626,7 @@ static bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t 
 }
 
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
-                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile)
+                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile, bool cross)
 {
     if (M <= 0 || Nc <= 0) return NL_OK;
     if (!tc_gemm_supported()) {
@@ -650,23 +659,26 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
             if (nsm < 1) nsm = 1;
         }
-        const long long ntiles = (long long)cdiv(Nc, kTcBN) * cdiv(M, kTcBM);
+        const long long ntiles = cross ? (long long)cdiv(Nc, kTcBN) + cdiv(M, kTcBM) - 1
+                                       : (long long)cdiv(Nc, kTcBN) * cdiv(M, kTcBM);
         // A small shallow update (K <= 128, at most 8 tiles per SM: a one-level panel's at
         // N <= ~4600) is short and bound by its C traffic; half the SMs leave the other half
         // to concurrent solves' latency-bound panels (the sweep of five concurrent solves at
         // N = 4096 measured 123 against 119 solves/s with every SM, 120 with a third; one
         // solve alone is 2% slower).  Larger and deep updates take every SM (capped, the
         // N = 32768 factorisation with nb = 128 took 104 instead of 82 ms).
-        const bool small = K < 256 && ntiles <= 8LL * nsm;
+        // (The cross of a look-ahead LU is on its critical path: a tile per CTA where it can.)
+        const bool small = !cross && K < 256 && ntiles <= 8LL * nsm;
         const unsigned grid = (unsigned)std::min<long long>(ntiles, small ? std::max(1, nsm / 2) : nsm);
-        prof_begin("k_tc_gemm", st);
+        const char* cls = cross ? "k_tc_gemm_x" : "k_tc_gemm";
+        prof_begin(cls, st);
         if (K >= 256)
             k_tc_gemm_p<kPRingDeep, kPCBufDeep><<<grid, kPThreads, p_smem_bytes(kPRingDeep, kPCBufDeep), st>>>(
-                tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
+                tmA, tmB, tmC, M, Nc, K, g_tc_err, flag, cross ? 1 : 0);
         else
             k_tc_gemm_p<kPRingShallow, kPCBufShallow><<<grid, kPThreads, p_smem_bytes(kPRingShallow, kPCBufShallow),
-                                                         st>>>(tmA, tmB, tmC, M, Nc, K, g_tc_err, flag);
-        prof_end("k_tc_gemm", st);
+                                                         st>>>(tmA, tmB, tmC, M, Nc, K, g_tc_err, flag, cross ? 1 : 0);
+        prof_end(cls, st);
         NL_CUDA_OK(cudaGetLastError());
         return NL_OK;
     }
@@ -707,11 +719,6 @@ bool tc_encode_instance_maps(const __half* A, int N, int64_t ld, const __half* u
 constexpr int kUfThreads = 256;
 constexpr uint32_t kUfSlab = 128 * 128;  // bytes: 128 rows x 64 binary16
 static size_t uf_smem_bytes() { return 1024 + 4 * (size_t)kUfSlab + 64; }
-
-__device__ __forceinline__ uint32_t sw128_off(int row, int chunk)
-{
-    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
-}
 
 __device__ __forceinline__ uint4 pack8_h(const float* v)
 {

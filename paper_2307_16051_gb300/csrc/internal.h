@@ -56,7 +56,20 @@ struct LuWork {
     float* p32 = nullptr;     // two-level LU (outer block > 128): single-precision shadow of the matrix, N x ldp32,
                               // of which the current outer block's row and column strips are used
     int64_t ldp32 = 0;
+    // Look-ahead (one-level binary16 fast path with the tensor-core update): after panel p the
+    // next panel's row and column strips are updated on the caller's stream (or by the next
+    // panel's own CTAs), the rest of the trailing matrix on side, joined before the next
+    // panel's strips are updated again.  ut2: the second
+    // U12^T buffer (panels alternate, so panel p + 1 never writes what the update of panel p
+    // reads).  Owned by whoever set them; no look-ahead while side is null.
+    __half* ut2 = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};  // ev_join[q % 2]: the rest of update q
 };
+// The look-ahead's side stream and events for w (created at st's priority, or
+// re-created when the priority differs); lu_side_release destroys them.
+nl_status lu_side_prepare(LuWork* w, cudaStream_t st);
+void lu_side_release(LuWork* w);
 size_t lu_work_bytes(int N, int nb, bool fp64);
 void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w);
 // gemm: 1 = SIMT, 2 = tcgen05.  Asynchronous; *info is written on the device.
@@ -176,13 +189,15 @@ nl_status launch_jacobian_g(const BInst* inst, const BState* st, const int* row_
 nl_status launch_gemv_residual_g(const BInst* inst, BState* st, const BTask* tasks, int ntasks, cudaStream_t st_);
 
 // gemm_tc.cu: C = fl16(C - A * Bt^T), A M x K (lda), Bt Nc x K (ldbt), tcgen05 + TMA.
+// cross: only the first 128-column tile column and the first 128-row tile row of C.
 bool tc_gemm_supported();
 // C <- C - A B on the tensor cores for binary32 C and binary32 operands holding
 // binary16 values (the two-level LU's inner updates), K <= 128, any M, Nc.
 nl_status tc_update_f32(int M, int Nc, int K, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                         int64_t ldc, cudaStream_t st, const int* flag);
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
-                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile = false);
+                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile = false,
+                           bool cross = false);
 
 // trsv.cu: triangular solves with the factors.
 constexpr int kTrsvT = 64;  // diagonal block size

@@ -1633,13 +1633,14 @@ __global__ void __launch_bounds__(256) k_gemm_simt(int M, int Nc, int K, const S
 // Workspace layout: the interchanging path's working panel (N x min(nb, 128)),
 // U12^T for the tensor-core update (N x nb binary16), info/flag words, the
 // diagonal-block stage, the published columns, and for an outer block above
-// 128 (two-level LU, binary16 only) the single-precision shadow N x ld.
+// 128 (two-level LU, binary16 only) the single-precision shadow N x ld, else
+// (binary16) the look-ahead's second U12^T buffer.
 size_t lu_work_bytes(int N, int nb, bool fp64)
 {
     size_t el = fp64 ? 8 : 4;
     size_t pnl = (size_t)N * std::min(nb, 128) * el;
     size_t ut = fp64 ? 0 : (size_t)round_up(N, 128) * nb * 2;
-    size_t shadow = (!fp64 && nb > 128) ? (size_t)N * round_up(N, 64) * 4 + 256 : 0;
+    size_t shadow = fp64 ? 0 : (nb > 128 ? (size_t)N * round_up(N, 64) * 4 + 256 : round_up(ut, 256));
     return round_up(pnl, 256) + round_up(ut, 256) + 256 + (size_t)2 * 128 * 128 * 8 + 128 * 8 +
            round_up((size_t)128 * 128 * 8, 256) + shadow;
 }
@@ -1660,13 +1661,48 @@ void lu_work_carve(void* base, int N, int nb, bool fp64, LuWork* w)
     p += (size_t)2 * 128 * 128 * 8 + 128 * 8;
     w->pub = (unsigned long long*)p;
     p += round_up((size_t)128 * 128 * 8, 256);
+    w->ut2 = nullptr;
     if (!fp64 && nb > 128) {
         w->p32 = (float*)p;
         w->ldp32 = round_up(N, 64);
     } else {
         w->p32 = nullptr;
         w->ldp32 = 0;
+        if (!fp64) w->ut2 = (__half*)p;
     }
+}
+
+nl_status lu_side_prepare(LuWork* w, cudaStream_t st)
+{
+    // one step below st's priority (lower priority = larger number): the rest of an update has
+    // a panel's time of slack, so it yields SMs to the latency-bound panels of concurrent solves
+    int prio = 0, least = 0, greatest = 0;
+    NL_CUDA_OK(cudaStreamGetPriority(st, &prio));
+    NL_CUDA_OK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    prio = std::min(prio + 1, least);
+    if (w->side) {
+        int have = 0;
+        NL_CUDA_OK(cudaStreamGetPriority(w->side, &have));
+        if (have == prio) return NL_OK;
+        NL_CUDA_OK(cudaStreamSynchronize(w->side));
+        NL_CUDA_OK(cudaStreamDestroy(w->side));
+        w->side = nullptr;
+    }
+    NL_CUDA_OK(cudaStreamCreateWithPriority(&w->side, cudaStreamNonBlocking, prio));
+    if (!w->ev_fork) NL_CUDA_OK(cudaEventCreateWithFlags(&w->ev_fork, cudaEventDisableTiming));
+    for (auto& e : w->ev_join)
+        if (!e) NL_CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return NL_OK;
+}
+
+void lu_side_release(LuWork* w)
+{
+    if (w->side) cudaStreamDestroy(w->side);
+    if (w->ev_fork) cudaEventDestroy(w->ev_fork);
+    for (auto& e : w->ev_join)
+        if (e) cudaEventDestroy(e);
+    w->side = nullptr;
+    w->ev_fork = w->ev_join[0] = w->ev_join[1] = nullptr;
 }
 
 template <typename T, int NBL, int R, bool RND>
@@ -1776,7 +1812,7 @@ nl_status gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, cons
 
 // A22 <- A22 - L21 U12 for the panel [K, K+wd): tcgen05 when possible.
 template <typename T, typename S>
-static nl_status trailing_update(int N, S* A, int64_t ld, int K, int wd, int nb, bool tc, const LuWork& w,
+static nl_status trailing_update(int N, S* A, int64_t ld, int K, int wd, int nb, bool tc, const __half* ut,
                                  const int* flag, cudaStream_t st)
 {
     const int rest = N - K - wd;
@@ -1784,7 +1820,7 @@ static nl_status trailing_update(int N, S* A, int64_t ld, int K, int wd, int nb,
     S* U12 = A + (int64_t)K * ld + K + wd;
     S* A22 = A + (int64_t)(K + wd) * ld + K + wd;
     if (tc) {
-        if constexpr (std::is_same<S, __half>::value) return tc_gemm16_update(rest, rest, wd, L21, ld, w.ut, nb, A22, ld, st, flag);
+        if constexpr (std::is_same<S, __half>::value) return tc_gemm16_update(rest, rest, wd, L21, ld, ut, nb, A22, ld, st, flag);
     }
     return launch_gemm_simt<S, T>(rest, rest, wd, L21, ld, U12, ld, A22, ld, st, flag);
 }
@@ -1892,6 +1928,61 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         smem_set = true;
     }
     bool pub_cleared = false;
+    // Look-ahead (fast path, tensor-core update): the update after panel q is split into the
+    // cross (the first 128-row and 128-column tile strips of the trailing matrix, which hold
+    // panel q + 1), one launch on st, and the rest on w.side, which then runs in the shadow of
+    // panel q + 1 and is joined back (ev_join[q % 2]) before the cross of update q + 1.  The
+    // tiles are the same tcgen05 tiles as in one update, so the factors are bitwise the same.
+    // Panels alternate U12^T buffers.
+    constexpr int kLaTile = 128;  // the tcgen05 update's tile (M = N = 128)
+    const bool la = kHalf && fast && gemm == 2 && nb <= kLaTile && w.side && w.ut2 && w.ev_fork && w.ev_join[0] &&
+                    w.ev_join[1];
+    struct Join {
+        const LuWork& w;
+        cudaStream_t st;
+        int pending = 0;  // bit q % 2: the rest of update q is recorded on ev_join[q % 2], not yet joined
+        bool wait(int q)
+        {
+            if (q < 0 || !((pending >> (q & 1)) & 1)) return true;
+            pending &= ~(1 << (q & 1));
+            return cudaStreamWaitEvent(st, w.ev_join[q & 1], 0) == cudaSuccess;
+        }
+        bool all() { return wait(0) && wait(1); }
+        ~Join() { all(); }
+    } join{w, st};
+    auto join_ok = [&](bool ok) -> nl_status {
+        if (ok) return NL_OK;
+        set_error("LU look-ahead: cudaStreamWaitEvent failed");
+        return NL_ECUDA;
+    };
+    auto ut_of = [&](int K) { return (la && ((K / nb) & 1)) ? w.ut2 : w.ut; };
+    // the update after the panel at K (width wd)
+    auto update = [&](int K, int wd, bool tc, const __half* utp) -> nl_status {
+        const int rest = N - K - wd, q = K / nb;
+        if (!(la && tc)) {
+            NL_TRY(join_ok(join.all()));
+            return trailing_update<T, S>(N, A, ld, K, wd, nb, tc, utp, w.flag, st);
+        }
+        if constexpr (kHalf) {
+            S* L21 = A + (int64_t)(K + wd) * ld + K;
+            S* A22 = A + (int64_t)(K + wd) * ld + K + wd;
+            const bool side_now = rest > kLaTile;
+            if (side_now) NL_CUDA_OK(cudaEventRecord(w.ev_fork, st));
+            NL_TRY(join_ok(join.wait(q - 1)));  // the rest of update q - 1 wrote the cross's tiles
+            NL_TRY(tc_gemm16_update(rest, rest, wd, L21, ld, utp, nb, A22, ld, st, w.flag, false, true));
+            if (side_now) {
+                const int m2 = rest - kLaTile;
+                NL_TRY(join_ok(join.wait(q - 2)));  // ev_join[q % 2] is free again
+                NL_CUDA_OK(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
+                NL_TRY(tc_gemm16_update(m2, m2, wd, L21 + (int64_t)kLaTile * ld, ld, utp + (int64_t)kLaTile * nb, nb,
+                                        A22 + (int64_t)kLaTile * ld + kLaTile, ld, w.side, w.flag));
+                NL_CUDA_OK(cudaEventRecord(w.ev_join[q & 1], w.side));
+                join.pending |= 1 << (q & 1);
+                ++nl;
+            }
+        }
+        return NL_OK;
+    };
     for (int K = 0; K < N; K += nb) {
         const int wd = std::min(nb, N - K), M = N - K;
         const int rest = N - K - wd;
@@ -1907,14 +1998,14 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
                         pub_cleared = true;
                     }
                     // the streamed rows and columns, then (if any) the rest in one off-diagonal launch
-                    NL_TRY(launch_panel16(A, ld, K, wd, K + wd + R, ipiv, w, tc ? w.ut : nullptr, nb, st, (K / nb) & 1));
+                    __half* utp = tc ? ut_of(K) : nullptr;
+                    NL_TRY(launch_panel16(A, ld, K, wd, K + wd + R, ipiv, w, utp, nb, st, (K / nb) & 1));
                     if (R < rest) {
-                        NL_TRY(launch_offdiag16<__half>(A, ld, K, wd, N, tc ? w.ut : nullptr, nb, w.flag,
-                                                        (const float*)w.stage, -1, 0, st, R));
+                        NL_TRY(launch_offdiag16<__half>(A, ld, K, wd, N, utp, nb, w.flag, (const float*)w.stage, -1,
+                                                        0, st, R));
                         ++nl;
                     }
-                    nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
-                    if (s != NL_OK) return s;
+                    NL_TRY(update(K, wd, tc, utp));
                     nl += 2;
                     continue;
                 }
@@ -1930,7 +2021,7 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
             ++nl;
             if (rest > 0) {
                 if constexpr (kHalf) {
-                    NL_TRY(launch_offdiag16<__half>(A, ld, K, wd, N, tc ? w.ut : nullptr, nb, w.flag,
+                    NL_TRY(launch_offdiag16<__half>(A, ld, K, wd, N, tc ? ut_of(K) : nullptr, nb, w.flag,
                                                     (const float*)w.stage, -1, 0, st));
                 } else {
                     const int nrb = (int)cdiv(rest, kOffThreads / kOffG);
@@ -1940,8 +2031,7 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
                                                                           w.stage);
                     prof_end("k_offdiag", st);
                 }
-                nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, w.flag, st);
-                if (s != NL_OK) return s;
+                NL_TRY(update(K, wd, tc, ut_of(K)));
                 nl += 2;
             }
             NL_CUDA_OK(cudaGetLastError());
@@ -1969,12 +2059,13 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
         if (rest > 0) {
             k_trsm_u12<T, S, RND><<<(unsigned)cdiv(rest, kTrsmThreads), kTrsmThreads, trsm_smem, st>>>(
                 A, ld, K, wd, N, tc ? w.ut : nullptr, nb, nullptr);
-            nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w, nullptr, st);
+            nl_status s = trailing_update<T, S>(N, A, ld, K, wd, nb, tc, w.ut, nullptr, st);
             if (s != NL_OK) return s;
             nl += 2;
         }
         NL_CUDA_OK(cudaGetLastError());
     }
+    NL_TRY(join_ok(join.all()));
     if (launches) *launches += nl;
     return NL_OK;
 }

@@ -314,6 +314,7 @@ struct nl_solver {
     int* ipiv = nullptr;
     LinBufs lb;
     LuWork luw;
+    bool lookahead = true;  // the binary16 fast path's look-ahead (its side stream lives in luw)
     TrsvWork tw;
     // double-precision mode
     double *J64 = nullptr, *b64 = nullptr, *u64 = nullptr;
@@ -419,6 +420,7 @@ static nl_status autotune_lu(nl_solver* s)
         for (int rep = 0; rep < 2; ++rep) {
             NL_TRY(launch_jacobian(n, s->c, s->rr, s->htab, s->J32, s->ld, s->J16, s->ld, st, jrs));
             lu_work_carve(s->luw.pnl, n, nb, false, &s->luw);
+            if (s->lookahead) NL_TRY(lu_side_prepare(&s->luw, st));
             cudaEventRecord(s->ev[0], st);
             NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, nb, gemm, true, s->luw, st, nullptr));
             cudaEventRecord(s->ev[1], st);
@@ -522,7 +524,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
         d.gmres_factors32 < 0 || d.gmres_factors32 > 1 || d.lu16_arith < 0 || d.lu16_arith > 1 ||
         d.newton_maxit >= NL_MAX_HIST || (d.lu_nb > 0 && !lu16_nb_valid(d.lu_nb)) ||
         d.lu_nb < -1 || d.scale_fp16 < 0 || d.scale_fp16 > 1 || d.fft_f < -1 || d.fft_f > 1 ||
-        d.trailing_gemm < 0 || d.trailing_gemm > 2 ||
+        d.trailing_gemm < 0 || d.trailing_gemm > 2 || d.lu_lookahead < -1 || d.lu_lookahead > 0 ||
         (d.scale_fp16 && (d.ir_variant || d.gmres_factors32 || d.lu16_arith))) {
         set_error("nl_create: invalid configuration");
         return NL_EINVAL;
@@ -589,6 +591,7 @@ nl_status nl_create(int64_t N, double c, const nl_config* cfg, nl_solver** out)
     s->tw.wait_limit = d.wait_limit;
     s->tw.rs = d.scale_fp16 ? s->rs16 : nullptr;
     s->luw.stream = d.lu_stream;
+    s->lookahead = d.lu_lookahead == 0;
     bool evs_ok = true;
     for (auto& e : s->evp) evs_ok = evs_ok && cudaEventCreate(&e) == cudaSuccess;
     if (!evs_ok || cudaMallocHost((void**)&s->pin, 64) != cudaSuccess || cudaEventCreate(&s->ev[0]) != cudaSuccess ||
@@ -659,6 +662,7 @@ void nl_destroy(nl_solver* s)
     if (!s) return;
     if (s->st) cudaStreamSynchronize(s->st);
     else cudaDeviceSynchronize();
+    lu_side_release(&s->luw);
     if (s->pool) cudaFree(s->pool);
     if (s->pool64) cudaFree(s->pool64);
     if (s->pool32) cudaFree(s->pool32);
@@ -902,6 +906,7 @@ static nl_status solve_impl(nl_solver* s, const double* x0, bool x0_host, double
         } else {
             // the fast path's outcome is read once, after the triangular solves' set-up
             // has been queued behind it (redone below in the rare case of interchanges)
+            if (s->lookahead && !pivoted_only) NL_TRY(lu_side_prepare(&s->luw, st));
             NL_TRY(lu16_factor(n, s->J16, s->ld, s->ipiv, s->nb, s->gemm, !pivoted_only, s->luw, st, &launches));
             NL_CUDA_OK(cudaMemcpyAsync(s->pin, s->luw.info, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
             if (mode != NL_F16) NL_TRY(trsv_prepare16(n, s->J16, s->ld, s->ipiv, s->tw, st, &launches));
@@ -1176,6 +1181,18 @@ static nl_status lu_entry(int64_t N, S* A, int64_t ld, int32_t* ipiv, int nb, in
         w.stream = -1;
         path = 0;
     }
+    struct SideGuard {
+        LuWork* w;
+        ~SideGuard() { lu_side_release(w); }
+    } side_guard{&w};
+    if (path == 4) {  // the fast path with look-ahead (a side stream for the trailing updates)
+        const nl_status ps = lu_side_prepare(&w, st);
+        if (ps != NL_OK) {
+            cudaFreeAsync(wk, st);
+            return ps;
+        }
+        path = 0;
+    }
     S* backup = (S*)((char*)wk + round_up(lw, 256));
     int iflag[2] = {0, 0};
     nl_status s = NL_OK;
@@ -1252,7 +1269,7 @@ extern "C" {
 nl_status nl_lu16(int64_t N, void* A16, int64_t ld, int32_t* ipiv, int nb, int gemm, int path, int32_t* info_host,
                   void* stream)
 {
-    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2 || path < 0 || path > 3) {
+    if (N < 1 || N > 32768 || !A16 || !ipiv || ld < N || (ld % 8) || gemm < 0 || gemm > 2 || path < 0 || path > 4) {
         set_error("nl_lu16: bad argument");
         return NL_EINVAL;
     }

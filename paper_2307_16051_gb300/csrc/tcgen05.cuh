@@ -27,6 +27,14 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr)
     return d;
 }
 
+// Byte offset of 16-byte chunk `chunk` (0..7) of row `row` in a 128-byte-swizzled
+// K-major slab (the layout TMA writes with 128-byte swizzle), for operands staged
+// with plain shared-memory stores.
+__device__ __forceinline__ uint32_t sw128_off(int row, int chunk)
+{
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4));
+}
+
 // Instruction descriptor: kind::f16, A = B = binary16, D = binary32, both
 // operands K-major, M x N.
 __host__ __device__ constexpr uint32_t tc_idesc_mn(int M, int N)

@@ -37,7 +37,7 @@ class Config(ctypes.Structure):
                 ("lu_path", ctypes.c_int), ("trsv_cluster", ctypes.c_int), ("lu_stream", ctypes.c_int),
                 ("ir_variant", ctypes.c_int), ("gmres_factors32", ctypes.c_int), ("lu16_arith", ctypes.c_int),
                 ("wait_limit", ctypes.c_int), ("scale_fp16", ctypes.c_int), ("fft_f", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("lu_lookahead", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -57,7 +57,8 @@ def test_invalid_arguments_rejected_before_device_use():
                 {"lu_stream": -2}, {"ir_variant": 2}, {"ir_variant": -1}, {"gmres_factors32": 2},
                 {"gmres_factors32": -1}, {"lu16_arith": 2}, {"scale_fp16": 2}, {"scale_fp16": -1},
                 {"scale_fp16": 1, "ir_variant": 1}, {"scale_fp16": 1, "gmres_factors32": 1},
-                {"scale_fp16": 1, "lu16_arith": 1}, {"fft_f": 2}, {"fft_f": -2}):
+                {"scale_fp16": 1, "lu16_arith": 1}, {"fft_f": 2}, {"fft_f": -2}, {"lu_lookahead": 1},
+                {"lu_lookahead": -2}):
         assert L.nl_create(64, 0.5, nl.ctypes.byref(nl.config(**bad)), nl.ctypes.byref(h)) == nl.NL_EINVAL, bad
     # the two-precision kernel entries check their arguments before any device call
     assert L.nl_lu32(0, None, 0, None, 0, None, None) == nl.NL_EINVAL

@@ -284,6 +284,40 @@ def test_lu16_two_level_tensor_core_close_to_oracle(N, nb):
     assert np.mean(LU == LUo) >= 0.95
 
 
+@pytest.mark.parametrize("N,nb", [(300, 128), (777, 64), (1000, 128), (2049, 64), (4100, 128)])
+def test_lu16_lookahead_bitwise(N, nb):
+    """Look-ahead (nl_lu16 path 4): after each panel only the trailing
+    matrix's first tile row and column are updated on the caller's stream,
+    the rest on a second stream in the shadow of the next panel.  The same
+    tcgen05 tiles, so the factors are the bits of the one-update path (0),
+    which is itself within binary16 rounding of the oracle; N = 300 ends with
+    a trailing matrix of one tile strip (no side-stream update), N = 4100
+    with a ragged 4-column panel."""
+    J16 = _jacobian16(N, 0.99)
+    LU0, ip0, info0 = _lu16_gpu(J16, nb, 2, 0)
+    LU4, ip4, info4 = _lu16_gpu(J16, nb, 2, 4)
+    assert info0 == info4 == 0 and np.array_equal(ip0, ip4) and np.array_equal(ip4, np.arange(N))
+    assert np.array_equal(LU0.view(np.uint64), LU4.view(np.uint64))
+    if N <= 2049:
+        LUo, _, _, _ = O.lu16_dev(J16, nb)
+        scale = np.maximum(np.abs(LUo), np.abs(np.diag(LUo)).max() * 2.0 ** -11)
+        assert np.max(np.abs(LU4 - LUo) / scale) <= 8 * 2.0 ** -11
+        assert np.mean(LU4 == LUo) >= 0.95
+
+
+def test_lu16_lookahead_falls_back_to_interchanges():
+    """A matrix that needs row interchanges: the look-ahead fast path is
+    abandoned (its side-stream updates see the flag) and the interchanging
+    path gives the same factors as without look-ahead."""
+    N = 700
+    A, _ = W.pivot_forcing_matrix(N, 3101)
+    A16 = O.fl16(A)
+    LU0, ip0, info0 = _lu16_gpu(A16, 128, 2, 0)
+    LU4, ip4, info4 = _lu16_gpu(A16, 128, 2, 4)
+    assert info0 == info4 == 0 and not np.array_equal(ip0, np.arange(N))
+    assert np.array_equal(ip0, ip4) and np.array_equal(LU0.view(np.uint64), LU4.view(np.uint64))
+
+
 def test_lu16_two_level_falls_back_to_interchanges():
     """A matrix that needs row interchanges: the two-level fast path detects
     it and the factorisation is redone by the interchanging path with outer

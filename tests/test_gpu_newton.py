@@ -149,6 +149,21 @@ def test_streaming_panel_agrees(mode):
     assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
 
 
+@pytest.mark.parametrize("lu_stream", [0, -1])
+def test_lookahead_agrees(lu_stream):
+    """The LU's look-ahead (lu_lookahead = 0, the default: the rest of each
+    trailing update on a second stream in the shadow of the next panel)
+    against one update per panel (-1), with the streaming panel and with two
+    launches per panel: bitwise the same solve, and the same counts."""
+    res = []
+    for la in (0, -1):
+        with nl.Solver(2100, 0.9999, lu_stream=lu_stream, lu_lookahead=la) as s:
+            x, status = s.solve(mode="GMRESIR16")
+            assert status == nl.NL_OK
+            res.append((x, s.stats()["newton_iters"]))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
 def test_repeatable_bitwise():
     with nl.Solver(700, 0.99) as s:
         a, _ = s.solve(mode="GMRESIR16")
