@@ -234,6 +234,34 @@ def test_lu16_wide_offdiag_launches_bitwise(N, nb):
     assert np.array_equal(out[0].view(np.uint16), out[1].view(np.uint16))
 
 
+@pytest.mark.parametrize("N", [12000, 20480])
+def test_lu16_lookahead_wide_panels_bitwise(N):
+    """Look-ahead with the tcgen05 update on panels wider than one streaming
+    launch (the rows that do not fit go to a following off-diagonal launch):
+    the factors of nl_lu16 path 4 are the bits of path 0.  The Jacobian of
+    eq. (3.2) at x = 1 + sin^2, formed on the GPU."""
+    c = 0.99
+    ld = ((N + 63) // 64) * 64
+    x = torch.as_tensor(1.0 + 0.5 * np.sin(np.arange(N) * 0.37) ** 2, device=dev())
+    F = torch.empty(N, device=dev(), dtype=torch.float64)
+    r = torch.empty(N, device=dev(), dtype=torch.float64)
+    nrm = torch.empty(1, device=dev(), dtype=torch.float64)
+    nl.k_residual(N, c, x, F, r, nrm)
+    J32 = torch.empty((N, ld), device=dev(), dtype=torch.float32)
+    J16 = torch.zeros((N, ld), device=dev(), dtype=torch.float16)
+    nl.k_jacobian(N, c, r, J32, ld, J16, ld)
+    del J32
+    out = []
+    for path in (0, 4):
+        A = J16.clone()
+        ip = torch.empty(N, device=dev(), dtype=torch.int32)
+        assert nl.lu16(N, A, ld, ip, nb=128, gemm=2, path=path) == 0
+        assert np.array_equal(ip.cpu().numpy(), np.arange(N))
+        out.append(A.cpu().numpy()[:, :N])
+        del A
+    assert np.array_equal(out[0].view(np.uint16), out[1].view(np.uint16))
+
+
 @pytest.mark.parametrize("N,nb", [(200, 64), (517, 128), (1024, 128), (777, 64)])
 def test_lu16_tensor_core_close_to_oracle(N, nb):
     """tcgen05 trailing update: same pivots, factors within binary16
