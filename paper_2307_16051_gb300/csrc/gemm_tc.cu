@@ -230,8 +230,18 @@ constexpr uint32_t kPCBytes = 2 * kPSlab;  // one C tile: two 64-column boxes
 constexpr int kPRingDeep = 5, kPCBufDeep = 2;
 constexpr int kPRingShallow = 4, kPCBufShallow = 3;
 constexpr int kPMaxK = 1024;               // largest K of one update
+// Updates with K >= 512 take 128 x 256 tiles (one M = 128, N = 256 MMA per 16 of K, the two
+// accumulators in all 512 tensor-memory columns): a quarter fewer operand bytes per flop than
+// 128 x 128, in three operand slots (48 KB each) and one 64 KB C buffer.  Bitwise the same
+// results.  Measured on GB300, the N = 32768 factorisation's K = 512 updates: 23.7 ms against
+// 25.4 with 128 x 128 tiles (two slots and two C buffers: 28.8 ms); at K = 256 the single C
+// buffer serialises the C traffic (50.4 against 35.8 ms), so shallower updates keep 128 x 128.
+constexpr int kTcBNWide = 256, kPRingWide = 3, kPCBufWide = 1;
 
-static size_t p_smem_bytes(int ring, int cbuf) { return 1024 + (size_t)ring * 2 * kPSlab + cbuf * (size_t)kPCBytes + 256; }
+static size_t p_smem_bytes(int ring, int cbuf, int bn = kTcBN)
+{
+    return 1024 + (size_t)ring * (kPSlab + (size_t)bn * 128) + (size_t)cbuf * bn * 256 + 256;
+}
 
 // Where tile `it` of a persistent CTA reads and writes: the A slabs at
 // (ax + 64 kt, ay) of map a, the B slabs at (64 kt, by) of map b, the C tile's
@@ -251,7 +261,7 @@ struct TileRef {
 // from K + w), read through the instance's whole-matrix map (A and C) and
 // its U12^T map (B); rows and columns past the instance's N read as zero and
 // are not stored.
-template <bool GROUPED, int kPRing, int kPCBuf>
+template <bool GROUPED, int kPRing, int kPCBuf, int BN = kTcBN>
 __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const CUtensorMap* tmB,
                                                    const CUtensorMap* tmC, int M, int Nc, int K,
                                                    const GInst* __restrict__ ginst, const TmapBytes* __restrict__ gmaps,
@@ -263,9 +273,11 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     const uint32_t base = (raw + 1023u) & ~1023u;
     uint8_t* basep = smem_raw + (base - raw);
     const int KT = K / kTcBK;
-    const uint32_t ring_bytes = (uint32_t)kPRing * 2 * kPSlab;
+    constexpr uint32_t kSlot = kPSlab + (uint32_t)BN * 128;  // one A slab and one B slab
+    constexpr uint32_t kCB = (uint32_t)BN * 256;               // one C tile: BN / 64 boxes
+    const uint32_t ring_bytes = (uint32_t)kPRing * kSlot;
     const uint32_t sAB = base, sCb = base + ring_bytes;  // operand slots, then C buffers
-    uint64_t* bars = reinterpret_cast<uint64_t*>(basep + ring_bytes + kPCBuf * kPCBytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(basep + ring_bytes + kPCBuf * kCB);
     // bars: slot_full[4] (0..3), slot_empty[4] (4..7), tfull[2] (8, 9), tempty[2] (10, 11),
     // c_full[3] (12..14), c_done[3] (15..17); then the TMEM address
     constexpr int bFULL = 0, bEMPTY = kPRing, bTFULL = 2 * kPRing, bTEMPTY = 2 * kPRing + 2,
@@ -273,7 +285,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + bCDONE + kPCBuf);
     __shared__ int aborted;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_n = (Nc + kTcBN - 1) / kTcBN, tiles_m = (M + kTcBM - 1) / kTcBM;
+    const int tiles_n = (Nc + BN - 1) / BN, tiles_m = (M + kTcBM - 1) / kTcBM;
     const int ntiles = GROUPED ? ntasks : (cross ? tiles_m + tiles_n - 1 : tiles_n * tiles_m);
     const int nmine = ntiles > (int)blockIdx.x ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     auto bar = [&](int k) { return smem_u32(&bars[k]); };
@@ -297,10 +309,10 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
             int m0, n0;
             if (cross) {  // tiles (i, 0) for every i, then (0, j) for j >= 1
                 m0 = tile < tiles_m ? tile * kTcBM : 0;
-                n0 = tile < tiles_m ? 0 : (tile - tiles_m + 1) * kTcBN;
+                n0 = tile < tiles_m ? 0 : (tile - tiles_m + 1) * BN;
             } else {
                 m0 = (tile / tiles_n) * kTcBM;
-                n0 = (tile % tiles_n) * kTcBN;
+                n0 = (tile % tiles_n) * BN;
             }
             r.a = tmA;
             r.b = tmB;
@@ -316,7 +328,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2u * kTcBN));
+                     "r"(2u * BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (threadIdx.x == 32) {
@@ -356,9 +368,9 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                         ok = false;
                         break;
                     }
-                    const uint32_t sA = sAB + (uint32_t)s * 2 * kPSlab, sB = sA + kPSlab;
+                    const uint32_t sA = sAB + (uint32_t)s * kSlot, sB = sA + kPSlab;
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(bFULL + s)),
-                                 "r"(2 * kPSlab)
+                                 "r"(kSlot)
                                  : "memory");
                     tma_load_2d(sA, r.a, r.ax + kt * kTcBK, r.ay, bar(bFULL + s));
                     tma_load_2d(sB, r.b, kt * kTcBK, r.by, bar(bFULL + s));
@@ -372,7 +384,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
         if (lane == 0) {
             // MMA issuer: tile it accumulates its KT slabs into accumulator it % 2, each slab's
             // MMAs committed to its slot's "free" barrier, the tile's to "accumulator full"
-            const uint32_t idesc = tc_idesc();
+            const uint32_t idesc = tc_idesc_mn(kTcBM, BN);
             long long g = 0;
             bool ok = true;
             for (int it = 0; it < nmine && ok && !*(volatile int*)&aborted; ++it) {
@@ -382,7 +394,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                     fail();
                     break;
                 }
-                const uint32_t d = tmem + (uint32_t)(b * kTcBN);
+                const uint32_t d = tmem + (uint32_t)(b * BN);
                 for (int kt = 0; kt < KT; ++kt, ++g) {
                     const int s = (int)(g % kPRing);
                     const uint32_t ph = (uint32_t)(g / kPRing) & 1u;
@@ -392,7 +404,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                         break;
                     }
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sA = sAB + (uint32_t)s * 2 * kPSlab, sB = sA + kPSlab;
+                    const uint32_t sA = sAB + (uint32_t)s * kSlot, sB = sA + kPSlab;
 #pragma unroll
                     for (int kk = 0; kk < kTcBK / 16; ++kk) {
                         const uint64_t ad = sw128_desc(sA + kk * 32);
@@ -425,10 +437,10 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
             for (int it = 0; it < kPCBuf && it < nmine; ++it) {
                 const TileRef r = ref(it);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(bCFULL + it)),
-                             "r"(kPCBytes)
+                             "r"(kCB)
                              : "memory");
-                for (int j = 0; j < 2; ++j)
-                    tma_load_2d(sCb + it * kPCBytes + j * kPSlab, r.c, r.cx + j * kTcBK, r.cy, bar(bCFULL + it));
+                for (int j = 0; j < BN / 64; ++j)
+                    tma_load_2d(sCb + it * kCB + j * kPSlab, r.c, r.cx + j * kTcBK, r.cy, bar(bCFULL + it));
                 loaded = it + 1;
             }
             for (int it = 0; it < nmine && !*(volatile int*)&aborted; ++it) {
@@ -440,20 +452,20 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                 }
                 const TileRef r = ref(it);
                 if (r.store)
-                    for (int j = 0; j < 2; ++j)
+                    for (int j = 0; j < BN / 64; ++j)
                         asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                                          r.c),
-                                     "r"(r.cx + j * kTcBK), "r"(r.cy), "r"(sCb + s * kPCBytes + j * kPSlab)
+                                     "r"(r.cx + j * kTcBK), "r"(r.cy), "r"(sCb + s * kCB + j * kPSlab)
                                      : "memory");
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 if (it + kPCBuf < nmine) {
                     asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
                     const TileRef rn = ref(it + kPCBuf);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar(bCFULL + s)),
-                                 "r"(kPCBytes)
+                                 "r"(kCB)
                                  : "memory");
-                    for (int j = 0; j < 2; ++j)
-                        tma_load_2d(sCb + s * kPCBytes + j * kPSlab, rn.c, rn.cx + j * kTcBK, rn.cy, bar(bCFULL + s));
+                    for (int j = 0; j < BN / 64; ++j)
+                        tma_load_2d(sCb + s * kCB + j * kPSlab, rn.c, rn.cx + j * kTcBK, rn.cy, bar(bCFULL + s));
                     loaded = it + kPCBuf + 1;
                 }
             }
@@ -476,11 +488,11 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            uint8_t* cst = basep + ring_bytes + s * kPCBytes;  // C buffer it % kPCBuf
+            uint8_t* cst = basep + ring_bytes + s * kCB;  // C buffer it % kPCBuf
 #pragma unroll
-            for (int c = 0; c < kTcBN; c += 32) {
+            for (int c = 0; c < BN; c += 32) {
                 uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * kTcBN + c);
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + c);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
                     "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
@@ -492,7 +504,7 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
                       "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (c + 32 == kTcBN) {
+                if (c + 32 == BN) {
                     // the whole accumulator row is in registers: the buffer may be reused
                     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                     mbar_arrive(bar(bTEMPTY + b));
@@ -527,11 +539,11 @@ __device__ __forceinline__ void tc_gemm_persistent(const CUtensorMap* tmA, const
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * kTcBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2u * BN));
     }
 }
 
-template <int RING, int CBUF>
+template <int RING, int CBUF, int BN = kTcBN>
 __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constant__ CUtensorMap tmA,
                                                             const __grid_constant__ CUtensorMap tmB,
                                                             const __grid_constant__ CUtensorMap tmC, int M, int Nc,
@@ -539,7 +551,8 @@ __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_p(const __grid_constan
                                                             const int* __restrict__ flag, int cross)
 {
     if (flag && *(volatile const int*)flag) return;  // the LU's fast path was abandoned
-    tc_gemm_persistent<false, RING, CBUF>(&tmA, &tmB, &tmC, M, Nc, K, nullptr, nullptr, nullptr, 0, 0, 0, err, cross);
+    tc_gemm_persistent<false, RING, CBUF, BN>(&tmA, &tmB, &tmC, M, Nc, K, nullptr, nullptr, nullptr, 0, 0, 0, err,
+                                              cross);
 }
 
 __global__ void __launch_bounds__(kPThreads, 1) k_tc_gemm_pg(const GInst* __restrict__ inst,
@@ -600,6 +613,7 @@ bool tc_gemm_supported()
     if (set_max_dynamic_smem((const void*)k_tc_gemm_g) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_p<kPRingDeep, kPCBufDeep>) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_p<kPRingShallow, kPCBufShallow>) != NL_OK) return false;
+    if (set_max_dynamic_smem((const void*)k_tc_gemm_p<kPRingWide, kPCBufWide, kTcBNWide>) != NL_OK) return false;
     if (set_max_dynamic_smem((const void*)k_tc_gemm_pg) != NL_OK) return false;
     g_tc_state = 1;
     return true;
@@ -639,9 +653,11 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
                   "multiples of 8, pointers 16-byte aligned");
         return NL_EINVAL;
     }
+    const bool wide = !per_tile && !cross && K >= 512;
+    const int bn = wide ? kTcBNWide : kTcBN;
     CUtensorMap tmA, tmB;
     if (!encode_2d(&tmA, A, (uint64_t)K, (uint64_t)M, (uint64_t)lda, kTcBK, kTcBM) ||
-        !encode_2d(&tmB, Bt, (uint64_t)K, (uint64_t)Nc, (uint64_t)ldbt, kTcBK, kTcBN)) {
+        !encode_2d(&tmB, Bt, (uint64_t)K, (uint64_t)Nc, (uint64_t)ldbt, kTcBK, (uint32_t)bn)) {
         set_error("tcgen05 GEMM: cuTensorMapEncodeTiled failed");
         return NL_ECUDA;
     }
@@ -660,7 +676,7 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
             if (nsm < 1) nsm = 1;
         }
         const long long ntiles = cross ? (long long)cdiv(Nc, kTcBN) + cdiv(M, kTcBM) - 1
-                                       : (long long)cdiv(Nc, kTcBN) * cdiv(M, kTcBM);
+                                       : (long long)cdiv(Nc, bn) * cdiv(M, kTcBM);
         // A small shallow update (K <= 128, at most 8 tiles per SM: a one-level panel's at
         // N <= ~4600) is short and bound by its C traffic; half the SMs leave the other half
         // to concurrent solves' latency-bound panels (the sweep of five concurrent solves at
@@ -672,7 +688,11 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         const unsigned grid = (unsigned)std::min<long long>(ntiles, small ? std::max(1, nsm / 2) : nsm);
         const char* cls = cross ? "k_tc_gemm_x" : "k_tc_gemm";
         prof_begin(cls, st);
-        if (K >= 256)
+        if (wide)
+            k_tc_gemm_p<kPRingWide, kPCBufWide, kTcBNWide>
+                <<<grid, kPThreads, p_smem_bytes(kPRingWide, kPCBufWide, kTcBNWide), st>>>(tmA, tmB, tmC, M, Nc, K,
+                                                                                         g_tc_err, flag, 0);
+        else if (K >= 256)
             k_tc_gemm_p<kPRingDeep, kPCBufDeep><<<grid, kPThreads, p_smem_bytes(kPRingDeep, kPCBufDeep), st>>>(
                 tmA, tmB, tmC, M, Nc, K, g_tc_err, flag, cross ? 1 : 0);
         else
