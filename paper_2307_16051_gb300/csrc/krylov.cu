@@ -64,7 +64,25 @@ __device__ __forceinline__ double gemv_row(int N, const float* __restrict__ A, i
         const float4* A4 = reinterpret_cast<const float4*>(Ai);
         const float4* u4 = reinterpret_cast<const float4*>(u);
         DF s = {0.0f, 0.0f};
-        for (int k = lane; k < n4; k += 32) {
+        int k = lane;
+        // four iterations' loads in flight before their products (the same order of terms): at
+        // N = 4096 a warp per row has 32 iterations, too few warps to hide the latency one at a time
+        for (; k + 96 < n4; k += 128) {
+            float4 a[4], x[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = __ldcs(A4 + k + 32 * q);
+                x[q] = __ldg(u4 + k + 32 * q);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                df_add_prod(s, a[q].x, x[q].x);
+                df_add_prod(s, a[q].y, x[q].y);
+                df_add_prod(s, a[q].z, x[q].z);
+                df_add_prod(s, a[q].w, x[q].w);
+            }
+        }
+        for (; k < n4; k += 32) {
             float4 a = __ldcs(A4 + k);
             float4 x = __ldg(u4 + k);
             df_add_prod(s, a.x, x.x);
@@ -97,6 +115,27 @@ __device__ __forceinline__ double gemv_row(int N, const float* __restrict__ A, i
     return sq;
 }
 
+// The sum of part[0 .. n) in index order, by every thread of the block (the
+// last block of a grid-wide reduction): the partials are staged through
+// shared memory a block's width at a time (parallel loads from L2) and thread
+// 0 adds them in order, so the result is that of one thread's sequential
+// loop; valid in thread 0.
+__device__ __forceinline__ double ordered_sum_staged(const double* part, int n, double* buf)
+{
+    double t = 0.0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int q = base + threadIdx.x;
+        if (q < n) buf[threadIdx.x] = __ldcg(part + q);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int m = min((int)blockDim.x, n - base);
+            for (int e = 0; e < m; ++e) t += buf[e];
+        }
+        __syncthreads();
+    }
+    return t;
+}
+
 __global__ void __launch_bounds__(kGemvWarps * 32)
     k_gemv_residual(int N, const float* __restrict__ A, int64_t ld, const float* __restrict__ b,
                     const float* __restrict__ u, float* __restrict__ r, double* __restrict__ partial,
@@ -118,11 +157,11 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
         last = (done == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0 && rnorm) {
+    if (last && rnorm) {
+        __shared__ double buf[kGemvWarps * 32];
         __threadfence();
-        double t = 0.0;
-        for (unsigned q = 0; q < gridDim.x; ++q) t += __ldcg(&partial[q]);
-        *rnorm = sqrt(t);
+        const double t = ordered_sum_staged(partial, (int)gridDim.x, buf);
+        if (threadIdx.x == 0) *rnorm = sqrt(t);
     }
     if (last && threadIdx.x == 0) *counter = 0u;
 }
@@ -155,12 +194,14 @@ __global__ void __launch_bounds__(kGemvWarps * 32)
         last = (atomicAdd(&I.cnt[1], 1u) == (unsigned)(nblk - 1));
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
+        __shared__ double buf[kGemvWarps * 32];
         __threadfence();
-        double t = 0.0;
-        for (int q = 0; q < nblk; ++q) t += __ldcg(&I.part[q]);
-        S.nr_new = sqrt(t);
-        I.cnt[1] = 0u;
+        const double t = ordered_sum_staged(I.part, nblk, buf);
+        if (threadIdx.x == 0) {
+            S.nr_new = sqrt(t);
+            I.cnt[1] = 0u;
+        }
     }
 }
 
