@@ -130,6 +130,27 @@ __device__ __forceinline__ float div_round_h_fast(float a, float rb, bool* unsur
     return __half2float(h);
 }
 
+// The sum of part[0 .. n) in index order, by every thread of the block (the
+// last block of a grid-wide reduction): the partials are staged through
+// shared memory a block's width at a time (parallel loads from L2) and thread
+// 0 adds them in order, so the result is that of one thread's sequential
+// loop; valid in thread 0.
+__device__ __forceinline__ double ordered_sum_staged(const double* part, int n, double* buf)
+{
+    double t = 0.0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int q = base + threadIdx.x;
+        if (q < n) buf[threadIdx.x] = __ldcg(part + q);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int m = min((int)blockDim.x, n - base);
+            for (int e = 0; e < m; ++e) t += buf[e];
+        }
+        __syncthreads();
+    }
+    return t;
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v)
 {

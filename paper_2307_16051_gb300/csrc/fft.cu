@@ -159,12 +159,14 @@ __global__ void __launch_bounds__(128) k_fft_pass_b(int N, int L, int L1, int L2
             last = (atomicAdd(cnt, 1u) == (unsigned)(L1 - 1));
         }
         __syncthreads();
-        if (last && threadIdx.x == 0) {
+        if (last) {
+            __shared__ double buf[128];
             __threadfence();
-            double sum = 0.0;
-            for (int b = 0; b < L1; ++b) sum += __ldcg(&part[b]);
-            *fnorm = sqrt(sum);
-            *cnt = 0u;
+            const double sum = ordered_sum_staged(part, L1, buf);
+            if (threadIdx.x == 0) {
+                *fnorm = sqrt(sum);
+                *cnt = 0u;
+            }
         }
     }
 }

@@ -115,27 +115,6 @@ __device__ __forceinline__ double gemv_row(int N, const float* __restrict__ A, i
     return sq;
 }
 
-// The sum of part[0 .. n) in index order, by every thread of the block (the
-// last block of a grid-wide reduction): the partials are staged through
-// shared memory a block's width at a time (parallel loads from L2) and thread
-// 0 adds them in order, so the result is that of one thread's sequential
-// loop; valid in thread 0.
-__device__ __forceinline__ double ordered_sum_staged(const double* part, int n, double* buf)
-{
-    double t = 0.0;
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int q = base + threadIdx.x;
-        if (q < n) buf[threadIdx.x] = __ldcg(part + q);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int m = min((int)blockDim.x, n - base);
-            for (int e = 0; e < m; ++e) t += buf[e];
-        }
-        __syncthreads();
-    }
-    return t;
-}
-
 __global__ void __launch_bounds__(kGemvWarps * 32)
     k_gemv_residual(int N, const float* __restrict__ A, int64_t ld, const float* __restrict__ b,
                     const float* __restrict__ u, float* __restrict__ r, double* __restrict__ partial,
@@ -247,12 +226,14 @@ __global__ void __launch_bounds__(256) k_norm32(int N, const float* __restrict__
         last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
+        __shared__ double buf[256];
         __threadfence();
-        double t = 0.0;
-        for (unsigned q = 0; q < gridDim.x; ++q) t += __ldcg(&partial[q]);
-        *out = sqrt(t);
-        *counter = 0u;
+        const double t = ordered_sum_staged(partial, (int)gridDim.x, buf);
+        if (threadIdx.x == 0) {
+            *out = sqrt(t);
+            *counter = 0u;
+        }
     }
 }
 

@@ -93,12 +93,14 @@ __global__ void __launch_bounds__(kFRows* kFSlices)
         last = (done == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
+    if (last) {
+        __shared__ double buf[kFRows * kFSlices];
         __threadfence();
-        double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(&partial[b]);
-        *fnorm = sqrt(s);
-        *counter = 0u;
+        const double s = ordered_sum_staged(partial, (int)gridDim.x, buf);
+        if (threadIdx.x == 0) {
+            *fnorm = sqrt(s);
+            *counter = 0u;
+        }
     }
 }
 
