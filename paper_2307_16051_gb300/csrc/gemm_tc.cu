@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
 // stage of work double-buffered:
 //   warp 0 (one thread): TMA loads of the A and B slabs of tile i into the
 //     operand ring's slots as the MMAs free them;
-//   warp 1 (one thread): K/16 tcgen05.mma into TMEM accumulator i % 2 (128
+//   warp 1 (one thread): K/16 tcgen05.mma into TMEM accumulator i % 2 (BN
 //     columns each) once the epilogue has read tile i-2's accumulator, then
 //     tcgen05.commit to "accumulator full" and to "operand stage free";
 //   warps 2-5: epilogue.  Each thread owns one tile row (its warp's TMEM
@@ -208,19 +208,21 @@ __global__ void __launch_bounds__(kTcThreads) k_tc_gemm(const __grid_constant__ 
 // Loads, MMAs, epilogue and stores of consecutive tiles overlap, and all
 // global traffic is TMA (coalesced, asynchronous).  Per element the
 // arithmetic is the per-tile kernel's: the same K/16 MMAs in the same order,
-// then one subtraction and one rounding.  The operands stream through a ring
-// of kPRing slots of one 64-wide K slab of A and of B each (32 KB), so K is any
-// multiple of 64 up to kPMaxK: C stays in the tensor-memory accumulator for
-// the whole K extent and is read and written once per update, whatever K
-// (the LU's outer block).  Two C buffers of 32 KB keep one C tile in flight
-// to or from memory while the epilogue works on the other.  Every wait is bounded; a timeout marks
-// the CTA aborted, every role leaves its loop, in-flight copies and MMAs are
-// waited for (bounded), and tensor memory is released.
+// then one subtraction and one rounding.  Tiles are 128 x BN (BN = 128, or
+// 256 for deep updates: one N = 256 MMA per 16 of K).  The operands stream
+// through a ring of kPRing slots of one 64-wide K slab of A and of B each
+// (16 KB + BN x 128 B), so K is any multiple of 64 up to kPMaxK: C stays in
+// the tensor-memory accumulator for the whole K extent and is read and
+// written once per update, whatever K (the LU's outer block).  With two or
+// more C buffers one C tile is in flight to or from memory while the epilogue
+// works on another.  Every wait is bounded; a timeout marks the CTA aborted,
+// every role leaves its loop, in-flight copies and MMAs are waited for
+// (bounded), and tensor memory is released.
 constexpr int kPThreads = 224;
 constexpr uint32_t kPSlab = 128 * 128;  // bytes of one 128-row x 64-column binary16 slab
-constexpr uint32_t kPCBytes = 2 * kPSlab;  // one C tile: two 64-column boxes
-// Ring shapes (operand slots, C buffers), 225 KB of shared memory either way.
-// Deep updates (K >= 256) stream many operand slabs per C tile and are bound by
+// Ring shapes (operand slots, C buffers) of the 128 x 128 form, 225 KB of shared
+// memory either way.  Deep updates (K = 256; from K = 512 the wide form below)
+// stream many operand slabs per C tile and are bound by
 // the operand bytes in flight against the L2 latency (ncu, N = 8192, K = 512,
 // four slots: L2 43%, DRAM 36%, tensor pipe 35%), so they take five slots and
 // two C buffers; shallow ones (K <= 128, and the grouped update) move more C
