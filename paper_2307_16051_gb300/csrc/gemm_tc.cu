@@ -642,7 +642,8 @@ static bool encode_2d(CUtensorMap* m, const void* ptr, uint64_t inner, uint64_t 
 }
 
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
-                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile, bool cross)
+                           __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile, bool cross,
+                           int max_ctas)
 {
     if (M <= 0 || Nc <= 0) return NL_OK;
     if (!tc_gemm_supported()) {
@@ -687,7 +688,8 @@ nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, c
         // N = 32768 factorisation with nb = 128 took 104 instead of 82 ms).
         // (The cross of a look-ahead LU is on its critical path: a tile per CTA where it can.)
         const bool small = !cross && K < 256 && ntiles <= 8LL * nsm;
-        const unsigned grid = (unsigned)std::min<long long>(ntiles, small ? std::max(1, nsm / 2) : nsm);
+        unsigned grid = (unsigned)std::min<long long>(ntiles, small ? std::max(1, nsm / 2) : nsm);
+        if (small && max_ctas > 0) grid = std::min<unsigned>(grid, (unsigned)max_ctas);
         const char* cls = cross ? "k_tc_gemm_x" : "k_tc_gemm";
         prof_begin(cls, st);
         if (wide)

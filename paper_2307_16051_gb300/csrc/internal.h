@@ -190,6 +190,7 @@ nl_status launch_gemv_residual_g(const BInst* inst, BState* st, const BTask* tas
 
 // gemm_tc.cu: C = fl16(C - A * Bt^T), A M x K (lda), Bt Nc x K (ldbt), tcgen05 + TMA.
 // cross: only the first 128-column tile column and the first 128-row tile row of C.
+// max_ctas > 0 caps the grid of a small shallow update (K < 256, at most 8 tiles per SM).
 bool tc_gemm_supported();
 // C <- C - A B on the tensor cores for binary32 C and binary32 operands holding
 // binary16 values (the two-level LU's inner updates), K <= 128, any M, Nc.
@@ -197,7 +198,7 @@ nl_status tc_update_f32(int M, int Nc, int K, const float* A, int64_t lda, const
                         int64_t ldc, cudaStream_t st, const int* flag);
 nl_status tc_gemm16_update(int M, int Nc, int K, const __half* A, int64_t lda, const __half* Bt, int64_t ldbt,
                            __half* C, int64_t ldc, cudaStream_t st, const int* flag, bool per_tile = false,
-                           bool cross = false);
+                           bool cross = false, int max_ctas = 0);
 
 // trsv.cu: triangular solves with the factors.
 constexpr int kTrsvT = 64;  // diagonal block size

@@ -1974,8 +1974,10 @@ static nl_status lu_factor_impl(int N, S* A, int64_t ld, int* ipiv, int nb, int 
                 const int m2 = rest - kLaTile;
                 NL_TRY(join_ok(join.wait(q - 2)));  // ev_join[q % 2] is free again
                 NL_CUDA_OK(cudaStreamWaitEvent(w.side, w.ev_fork, 0));
+                // (a panel's time of slack: a quarter of the SMs, the rest left to concurrent solves' panels)
                 NL_TRY(tc_gemm16_update(m2, m2, wd, L21 + (int64_t)kLaTile * ld, ld, utp + (int64_t)kLaTile * nb, nb,
-                                        A22 + (int64_t)kLaTile * ld + kLaTile, ld, w.side, w.flag));
+                                        A22 + (int64_t)kLaTile * ld + kLaTile, ld, w.side, w.flag, false, false,
+                                        std::max(1, num_sms() / 4)));
                 NL_CUDA_OK(cudaEventRecord(w.ev_join[q & 1], w.side));
                 join.pending |= 1 << (q & 1);
                 ++nl;
