@@ -559,13 +559,13 @@ nl_status nl_k_jacobian64(int64_t N, double c, const double* r, double* J64, int
  * saved copy of A if not (same result either way); 1 = interchanging path
  * only; 2 = as 0 with the diagonal block and the off-diagonal solves of each
  * panel in two launches instead of one streaming launch (same result);
- * 4 = as 0 with look-ahead (nl_config.lu_lookahead; same result; a second
- * stream is created and destroyed by the call);
  * 3 = every operation rounded to binary16 instead (l_ik = fl16(a_ik/a_kk),
  * a_ij <- fl16(a_ij - fl16(l_ik a_kj)) in increasing k, the first row of
  * largest |a_ik| as pivot): the arithmetic of the paper's F16 column; nb and
  * gemm are ignored, and *info_host is also set (to -1) after a binary16
- * overflow, returned as NL_ENUMERIC.
+ * overflow, returned as NL_ENUMERIC; 4 = as 0 with look-ahead
+ * (nl_config.lu_lookahead; same result; the call creates and destroys a
+ * second stream).
  * With the tcgen05 update the entries of a row in columns N ..
  * round_up(N, 8) - 1 (inside ld) may be overwritten (the tensor-memory copies
  * store whole 16-byte units at the matrix's right edge).

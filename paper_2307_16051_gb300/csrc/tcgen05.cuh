@@ -1,8 +1,8 @@
 // tcgen05.cuh — the pieces of the 5th-generation tensor-core path shared by
 // the trailing-update kernels (gemm_tc.cu) and the persistent grouped LU
 // (lu.cu): shared-memory operand descriptors for 128-byte-swizzled K-major
-// slabs written by TMA, the kind::f16 instruction descriptor, bounded
-// mbarrier waits and the 2-D TMA load.
+// slabs (written by TMA, or with plain stores at sw128_off), the kind::f16
+// instruction descriptor, bounded mbarrier waits and the 2-D TMA load.
 #pragma once
 #include <cuda.h>
 #include <cstdint>
